@@ -1,0 +1,322 @@
+"""Pins of the FP64 oracle's method steps against invariants, hand-built cases
+and scenes whose answer is known.
+
+* PatchMatch: the exhaustive-search NNF (independent numpy brute force) is a
+  fixed point of a red-black iteration, and PatchMatch from a random start
+  reaches it on most pixels.
+* A single global homography scene: every window fits the generating plane
+  (to the integer-NNF rounding limit), every mapped pixel is assigned, the
+  symmetry cue passes, the flow matches the generating map.
+* Cues, merge, NNF update and fill on hand-built label maps.
+* Whole method on synthetic scenes with exact ground truth.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_03787_gb300 import scene
+
+
+# ---------------------------------------------------------------- PatchMatch
+def _brute_nnf(src, tgt, r):
+    """Exhaustive square-patch NNF by numpy: argmin over every in-frame target,
+    ties to the lowest (ty, tx)."""
+    H, W, _ = src.shape
+    pad_s = np.pad(src, ((r, r), (r, r), (0, 0)), mode="edge")
+    # patches of the source, clamped at the border
+    ps = np.stack([pad_s[r + dy:r + dy + H, r + dx:r + dx + W] for dy in range(-r, r + 1) for dx in range(-r, r + 1)], 0)
+    vx = np.zeros((H, W), np.int32)
+    vy = np.zeros((H, W), np.int32)
+    best = np.full((H, W), np.inf)
+    ys, xs = np.mgrid[0:H, 0:W]
+    taps = [(dy, dx) for dy in range(-r, r + 1) for dx in range(-r, r + 1)]
+    for ty in range(H):
+        for tx in range(W):
+            ox, oy = tx - xs, ty - ys
+            acc = np.zeros((H, W))
+            for k, (dy, dx) in enumerate(taps):
+                sx, sy = np.clip(xs + dx, 0, W - 1), np.clip(ys + dy, 0, H - 1)
+                qx, qy = np.clip(sx + ox, 0, W - 1), np.clip(sy + oy, 0, H - 1)
+                acc += np.abs(ps[k] - tgt[qy, qx]).sum(-1)
+            acc /= 3 * len(taps)
+            upd = acc < best
+            best[upd] = acc[upd]
+            vx[upd] = ox[upd]
+            vy[upd] = oy[upd]
+    return vx.reshape(-1), vy.reshape(-1), best.reshape(-1)
+
+
+@pytest.mark.parametrize("r", [1, 2, 3])
+def test_exhaustive_nnf_is_patchmatch_fixed_point(r):
+    rng = np.random.default_rng(10 + r)
+    H, W = 12, 16
+    src = rng.random((H, W, 3))
+    tgt = np.roll(src, (1, 2), axis=(0, 1)) * 0.9 + 0.1 * rng.random((H, W, 3))
+    vx, vy, best = _brute_nnf(src, tgt, r)
+    P = O.Params(W, H, patch_radius=r)
+    cost = np.zeros(W * H)
+    O.pm_recost(P, src, tgt, 0, None, None, None, vx, vy, cost)
+    np.testing.assert_allclose(cost, best, rtol=1e-12, atol=0)
+    vx2, vy2, c2 = vx.copy(), vy.copy(), cost.copy()
+    for it in range(2):
+        for ph in range(2):
+            O.pm_sweep(P, src, tgt, 0, 0, it, ph, None, None, None, vx2, vy2, c2)
+    np.testing.assert_array_equal(vx2, vx)
+    np.testing.assert_array_equal(vy2, vy)
+
+
+def test_patchmatch_converges_toward_exhaustive_nnf():
+    """From random offsets, 8 red-black iterations reach the exhaustive NNF on
+    most pixels of a textured pair; costs never increase."""
+    s = scene.make_scene(32, 24, seed=3, n_layers=1, max_disp=4.0, affine=True, noise=0.0, gain=(1, 1))
+    src, tgt = s.frame1.astype(np.float64), s.frame2.astype(np.float64)
+    r = 2
+    vx, vy, best = _brute_nnf(src, tgt, r)
+    P = O.Params(32, 24, patch_radius=r)
+    ux, uy, c = O.pm_init(P, src, tgt, 0)
+    prev = c.copy()
+    for it in range(8):
+        for ph in range(2):
+            O.pm_sweep(P, src, tgt, 0, 0, it, ph, None, None, None, ux, uy, c)
+        assert np.all(c <= prev + 1e-15)
+        prev = c.copy()
+    agree = np.mean((ux == vx) & (uy == vy))
+    assert agree >= 0.9, agree
+    assert np.all(c >= best - 1e-12)
+
+
+def test_pm_init_targets_inside_frame_and_deterministic():
+    P = O.Params(40, 30, patch_radius=1, seed=77)
+    f = np.random.default_rng(0).random((30, 40, 3))
+    a = O.pm_init(P, f, f, 0)
+    b = O.pm_init(P, f, f, 0)
+    c = O.pm_init(P, f, f, 1)
+    ys, xs = np.divmod(np.arange(40 * 30), 40)
+    assert np.all((xs + a[0] >= 0) & (xs + a[0] < 40) & (ys + a[1] >= 0) & (ys + a[1] < 30))
+    np.testing.assert_array_equal(a[0], b[0])
+    assert np.mean(a[0] == c[0]) < 0.2   # the two directions draw independent streams
+
+
+# ---------------------------------------------------------------- single-plane scene
+def _plane_scene(W, H, Hm, key=12345):
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    tex = lambda x, y: np.stack([scene.value_noise(x, y, key + 17 * c, period=16.0) for c in range(3)], -1)
+    f1 = tex(xs, ys)
+    Hi = np.linalg.inv(Hm)
+    qx, qy = scene.apply_h(Hi, xs, ys)
+    f2 = tex(qx, qy)
+    return f1, f2
+
+
+def _round_nnf(Hm, W, H):
+    ys, xs = np.divmod(np.arange(W * H), W)
+    X, Y = scene.apply_h(Hm, xs.astype(float), ys.astype(float))
+    vx = np.floor(X - xs + 0.5).astype(np.int32)
+    vy = np.floor(Y - ys + 0.5).astype(np.int32)
+    ok = (xs + vx >= 0) & (xs + vx < W) & (ys + vy >= 0) & (ys + vy < H)
+    vx[~ok] = 0
+    vy[~ok] = 0
+    return vx, vy, X - xs, Y - ys
+
+
+def test_single_plane_scene_is_recovered_and_assigned():
+    W, H = 96, 64
+    Hm = scene.h_from_points(np.array([[0, 0], [95, 0], [95, 63], [0, 63]], float),
+                             np.array([[2, 1], [97, -1], [94, 66], [-1, 62]], float))
+    f1, f2 = _plane_scene(W, H, Hm)
+    P = O.Params(W, H, patch_radius=2, cells=(32,), num_hyp=128, eps=0.03)
+    vx0, vy0, fx, fy = _round_nnf(Hm, W, H)
+    vx1, vy1, _, _ = _round_nnf(np.linalg.inv(Hm), W, H)
+    mh, mi = [O.empty_models(P) for _ in range(2)], None
+    labs = []
+    for d, (vx, vy, src, tgt) in enumerate([(vx0, vy0, f1, f2), (vx1, vy1, f2, f1)]):
+        mh_d, mi_d = mh[d]
+        O.fit_level(P, src, tgt, d, 1, 1, vx, vy, None, mh_d, mi_d)
+        lab = O.Labels.empty(W * H, P.eps)
+        O.assign(P, src, tgt, 1, 1, mh_d, mi_d, None, lab)
+        labs.append(lab)
+    mh0, mi0 = mh[0]
+    fitted = mi0[::2, O.MI_FLAGS] & O.F_FITTED
+    assert fitted.all()
+    assert mi0[::2, O.MI_VALID].all()
+    # every window's plane is the generating map to the integer-rounding limit
+    ys, xs = np.divmod(np.arange(W * H), W)
+    gx, gy = O.grid_axis(W, 32), O.grid_axis(H, 32)
+    for c in range(mi0.shape[0] // 2):
+        x0, y0 = gx[c % len(gx)], gy[c // len(gx)]
+        win = (xs >= x0) & (xs < x0 + 32) & (ys >= y0) & (ys < y0 + 32)
+        Hc = mh0[2 * c].reshape(3, 3)
+        X, Y = scene.apply_h(Hc, xs.astype(float), ys.astype(float))
+        err = np.hypot(X - xs - fx, Y - ys - fy)[win]
+        # the matches are rounded to integers (error up to 0.71 px each)
+        assert err.max() < 1.0 and err.mean() < 0.3, (c, err.max(), err.mean())
+    # every pixel whose true target lies inside the frame (1 px margin) is assigned
+    X, Y = xs + fx, ys + fy
+    inside = (X >= 1) & (X <= W - 2) & (Y >= 1) & (Y <= H - 2)
+    assert np.all(labs[0].m[inside] >= 0)
+    err = np.hypot(labs[0].fx - fx, labs[0].fy - fy)[labs[0].m >= 0]
+    assert err.max() < 1.0 and err.mean() < 0.3
+    # the symmetry cue passes for every plane
+    O.cue_counts(P, 1, 1, labs[0], labs[1], mi0)
+    nas, nsy = mi0[::2, O.MI_NASSIGN], mi0[::2, O.MI_NSYM]
+    assert np.all(nsy >= P.eta * nas) and nas.sum() >= inside.sum()
+    O.cue_invalidate(P, 1, 1, mi0)
+    assert mi0[::2, O.MI_VALID].all()
+
+
+def test_overlap_cue_discards_colour_inconsistent_plane():
+    """Geometrically perfect matches between unrelated frames: RANSAC accepts the
+    plane, but almost none of its inliers are colour inliers, so kappa discards it."""
+    rng = np.random.default_rng(8)
+    W, H = 32, 32
+    f1, f2 = rng.random((H, W, 3)), rng.random((H, W, 3))
+    P = O.Params(W, H, patch_radius=1, cells=(16,), num_hyp=64)
+    T = np.array([[1, 0, 2], [0, 1, 1], [0, 0, 1.0]])
+    vx, vy, _, _ = _round_nnf(T, W, H)
+    mh, mi = O.empty_models(P)
+    O.fit_level(P, f1, f2, 0, 1, 1, vx, vy, None, mh, mi)
+    assert mi[0, O.MI_VALID] == 1 and mi[0, O.MI_NRC] < P.kappa * mi[0, O.MI_COUNT]
+    O.cue_invalidate(P, 1, 1, mi)
+    assert mi[0, O.MI_VALID] == 0 and mi[0, O.MI_FLAGS] & O.F_BAD_KAPPA
+
+
+def test_symmetry_cue_discards_asymmetric_plane():
+    """Forward labels say +3 px, backward labels say +3 px too (not -3): no pixel
+    is forward-backward symmetric, the plane is discarded (eta)."""
+    W, H = 32, 16
+    P = O.Params(W, H, cells=(16,))
+    n = W * H
+    lab = O.Labels(np.zeros(n, np.int32), np.full(n, 0.01), np.full(n, 3.0), np.zeros(n))
+    other = O.Labels(np.zeros(n, np.int32), np.full(n, 0.01), np.full(n, 3.0), np.zeros(n))
+    mh, mi = O.empty_models(P)
+    mi[:, O.MI_VALID] = 1
+    mi[:, O.MI_COUNT] = 10
+    mi[:, O.MI_NRC] = 10
+    O.cue_counts(P, 1, 1, lab, other, mi)
+    assert mi[0, O.MI_NASSIGN] == n and mi[0, O.MI_NSYM] == 0
+    other.fx[:] = -3.0
+    O.cue_counts(P, 1, 1, lab, other, mi)
+    assert mi[0, O.MI_NSYM] == n - 3 * H     # the last 3 columns land outside the frame
+    other.fx[:] = 3.0
+    O.cue_counts(P, 1, 1, lab, other, mi)
+    O.cue_invalidate(P, 1, 1, mi)
+    assert mi[0, O.MI_VALID] == 0 and mi[0, O.MI_FLAGS] & O.F_BAD_FB
+
+
+# ---------------------------------------------------------------- hand-built label maps
+def test_many_to_one_flags_the_worse_of_two_motions():
+    W, H = 10, 1
+    P = O.Params(W, H, patch_radius=1, cells=(2,))
+    n = W
+    lab = O.Labels.empty(n, P.eps)
+    # p=1 (flow +4) and p=7 (flow -2) both land on q=5; p=7 has the lower L -> p=1 occluded
+    # p=4 (flow +1.2) also rounds to q=5 with a flow close to p=7's? no: 1.2 vs -2 differ -> flagged
+    # p=6 (flow -1.4, rounds to 5) differs from p=7's flow by 0.6 < t_fb -> same motion, kept
+    for p, f, L, m in [(1, 4.0, 0.03, 2), (7, -2.0, 0.01, 4), (4, 1.2, 0.02, 6), (6, -1.4, 0.02, 4), (8, 1.0, 0.05, 8)]:
+        lab.m[p], lab.fx[p], lab.L[p] = m, f, L
+    cue = np.zeros(n, np.uint8)
+    O.many_to_one(P, lab, cue)
+    assert list(np.flatnonzero(cue)) == [1, 4]
+    assert lab.m[1] == -1 and lab.m[4] == -1 and lab.m[7] == 4 and lab.m[6] == 4 and lab.m[8] == 8
+
+
+def test_merge_keeps_coarse_unless_clearly_better_and_nnf_update_rounds_half_up():
+    P = O.Params(4, 1, cells=(2,), beta=0.015)
+    acc = O.Labels(np.array([-1, 5, 5, 5], np.int32), np.array([0.06, 0.03, 0.03, 0.03]),
+                   np.array([0, 1.0, 1.0, 1.0]), np.zeros(4))
+    lab = O.Labels(np.array([7, 7, 7, -1], np.int32), np.array([0.04, 0.02, 0.01, 0.0]),
+                   np.array([2.5, -1.5, 0.49, 9.0]), np.array([-0.5, 0.5, -2.5, 0.0]))
+    O.merge(P, lab, acc)
+    assert list(acc.m) == [7, 5, 7, 5]
+    vx, vy, fr = np.zeros(4, np.int32), np.zeros(4, np.int32), np.zeros(4, np.uint8)
+    O.nnf_update(P, acc, vx, vy, fr)
+    assert list(vx) == [3, 1, 0, 1] and list(vy) == [0, 0, -2, 0] and list(fr) == [1, 1, 1, 1]
+
+
+def test_fill_front_advances_one_pixel_per_jacobi_iteration():
+    """A global plane assigned everywhere except a hole: after k iterations
+    exactly the hole pixels within 4-neighbour distance k of the assigned region
+    are filled (cue-flagged pixels never are)."""
+    W, H = 24, 20
+    Hm = np.array([[1, 0, 2.0], [0, 1, 1.0], [0, 0, 1.0]])
+    f1, f2 = _plane_scene(W, H, Hm)
+    P = O.Params(W, H, cells=(8,), eps=0.05)
+    mh, mi = O.empty_models(P)
+    mh[0] = Hm.reshape(9) / np.linalg.norm(Hm)
+    mi[0, O.MI_VALID] = 1
+    n = W * H
+    ys, xs = np.divmod(np.arange(n), W)
+    hole = (xs >= 6) & (xs < 16) & (ys >= 5) & (ys < 15)
+    acc = O.Labels(np.where(hole, -1, 0).astype(np.int32), np.full(n, 0.001), np.full(n, 2.0), np.full(n, 1.0))
+    cue = np.zeros(n, np.uint8)
+    cue[(xs == 10) & (ys == 10)] = O.CUE_M2O
+    # city-block distance from the assigned region
+    dist = np.minimum.reduce([xs - 5, 16 - xs, ys - 4, 15 - ys])
+    for k in (1, 2, 3):
+        a = acc.copy()
+        P.fill_iters = k
+        O.fill(P, f1, f2, mh, mi, cue, a)
+        want = ~hole | (dist <= k)
+        want[(xs == 10) & (ys == 10)] = False
+        np.testing.assert_array_equal(a.m >= 0, want)
+        np.testing.assert_allclose(a.fx[hole & want], 2.0, atol=1e-12)
+
+
+# ---------------------------------------------------------------- whole method on known scenes
+def _evaluate(s, R):
+    H, W = s.occ.shape
+    f = R.flow[0].reshape(H, W, 2)
+    occ = R.occ[0].reshape(H, W)
+    epe = np.hypot(*(f - s.flow).transpose(2, 0, 1))
+    tp = ((occ == 1) & (s.occ == 1)).sum()
+    return dict(epe_nocc=float(epe[s.occ == 0].mean()), assigned=float((R.acc[0].m >= 0).mean()),
+                prec=tp / max(occ.sum(), 1), rec=tp / max(s.occ.sum(), 1))
+
+
+def test_translating_layer_scene_occlusion_and_flow():
+    """Static background, one textured layer translated by an integer vector:
+    the plane flow is exact on non-occluded pixels and the occluded strip is found."""
+    W, H = 96, 72
+    key = 999
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    tex = lambda k, x, y: np.stack([0.2 + 0.6 * scene.value_noise(x, y, k + 31 * c, period=12.0) for c in range(3)], -1)
+    rect = lambda x, y: (x >= 30) & (x < 62) & (y >= 20) & (y < 52)
+    t = 6
+    f1 = np.where(rect(xs, ys)[..., None], tex(key, xs, ys), tex(key + 1, xs, ys))
+    f2 = np.where(rect(xs - t, ys)[..., None], tex(key, xs - t, ys), tex(key + 1, xs, ys))
+    gt = np.zeros((H, W, 2))
+    gt[rect(xs, ys), 0] = t
+    occ_gt = (~rect(xs, ys)) & rect(xs - t, ys)   # background covered in frame 2
+    s = scene.Scene(frame1=f1.astype(np.float32), frame2=f2.astype(np.float32), flow=gt.astype(np.float32),
+                    occ=occ_gt.astype(np.uint8), layer_id=rect(xs, ys).astype(np.int16))
+    P = O.Params(W, H, patch_radius=3, cells=(32, 16, 8), gain_normalize=0)
+    R = O.run(P, s.frame1, s.frame2)
+    m = _evaluate(s, R)
+    assert m["epe_nocc"] < 0.05, m
+    assert m["rec"] > 0.9 and m["prec"] > 0.6, m
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tiny_config_accuracy_against_ground_truth(seed):
+    """128x96 scenes (2 layers, affine motion up to 8 px), r=3, cells 32/16/8,
+    4 iterations, 256 hypotheses.  Accuracy bounds recorded from the first
+    runs with margin: planes cover most pixels, EPE on visible pixels stays
+    at the integer-NNF fitting limit."""
+    s = scene.tiny_scene(seed)
+    P = O.Params(128, 96)
+    R = O.run(P, s.frame1, s.frame2)
+    m = _evaluate(s, R)
+    assert m["assigned"] > 0.9, m
+    assert m["epe_nocc"] < 0.6, m
+    if s.occ.mean() > 0.05:
+        assert m["rec"] > 0.5, m
+
+
+def test_run_is_deterministic():
+    s = scene.make_scene(64, 48, seed=4, n_layers=2, max_disp=5.0)
+    P = O.Params(64, 48, patch_radius=2, cells=(16, 8), num_hyp=64, pm_iters=2)
+    a = O.run(P, s.frame1, s.frame2)
+    b = O.run(P, s.frame1, s.frame2)
+    for d in range(2):
+        np.testing.assert_array_equal(a.flow[d], b.flow[d])
+        np.testing.assert_array_equal(a.mi[d], b.mi[d])

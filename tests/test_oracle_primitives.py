@@ -1,0 +1,246 @@
+"""Pins of the FP64 oracle's primitives against facts fixed outside the oracle.
+
+Each test names what it pins and against what: published known-answer
+vectors, closed forms (bilinear interpolation reproduces affine functions),
+independent brute force, and exact recovery of generating homographies.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the Random123 known-answer vectors."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+# ---------------------------------------------------------------- window grid
+def _grid_closed_form(n, s):
+    """Positions 0, s/2, ... with pos + s <= n, then n - s if not yet flush."""
+    h = s // 2
+    k = (n - s) // h + 1
+    extra = 1 if (k - 1) * h + s < n else 0
+    return k + extra
+
+
+@pytest.mark.parametrize("n,s", [(128, 32), (96, 32), (128, 8), (96, 16), (1024, 64), (436, 64), (436, 8),
+                                 (1920, 16), (1080, 64), (64, 64), (65, 64)])
+def test_grid_counts_and_overlap(n, s):
+    """Sec. 3.1.2: windows overlap their predecessor by half and cover the frame."""
+    pos = O.grid_axis(n, s)
+    assert len(pos) == _grid_closed_form(n, s)
+    assert pos[0] == 0 and pos[-1] + s == n
+    d = np.diff(pos)
+    if len(d):
+        assert np.all(d[:-1] == s // 2) and 0 < d[-1] <= s // 2
+    cover = np.zeros(n, int)
+    for p in pos:
+        cover[p:p + s] += 1
+    assert cover.min() >= 1 and cover.max() <= 3
+
+
+def test_cell_totals_of_the_two_workloads():
+    """Cell counts: 128x96 with cells 32/16/8 -> 35+165+713; 1024x436 with 64/32/16/8 -> 36,502."""
+    P = O.Params(128, 96, cells=(32, 16, 8))
+    assert list(O.cell_base(P)) == [0, 35, 200, 913]
+    P = O.Params(1024, 436, cells=(64, 32, 16, 8))
+    cb = O.cell_base(P)
+    assert list(np.diff(cb)) == [403, 1701, 6858, 27540] and cb[-1] == 36502
+
+
+# ---------------------------------------------------------------- bilinear sampling
+def test_bilinear_reproduces_affine_ramp():
+    """Bilinear interpolation is exact for affine images: I(x,y) = a x + b y + e."""
+    H, W = 9, 13
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    a, b, e = np.array([0.03, -0.01, 0.02]), np.array([0.015, 0.02, -0.005]), np.array([0.2, 0.5, 0.4])
+    img = xs[..., None] * a + ys[..., None] * b + e
+    rng = np.random.default_rng(0)
+    for _ in range(50):
+        X, Y = rng.uniform(0, W - 1), rng.uniform(0, H - 1)
+        np.testing.assert_allclose(O.sample_bilinear(img, X, Y), a * X + b * Y + e, rtol=0, atol=1e-14)
+
+
+def test_bilinear_integer_points_and_clamping():
+    rng = np.random.default_rng(1)
+    img = rng.random((7, 5, 3))
+    for y in range(7):
+        for x in range(5):
+            np.testing.assert_array_equal(O.sample_bilinear(img, x, y), img[y, x])
+    np.testing.assert_array_equal(O.sample_bilinear(img, -3.2, 2), img[2, 0])
+    np.testing.assert_array_equal(O.sample_bilinear(img, 10.0, 100.0), img[6, 4])
+
+
+# ---------------------------------------------------------------- warped patch cost
+def _square_cost(src, tgt, r, px, py, vx, vy):
+    """Independent square-patch PatchMatch cost: mean |I1(clamp(p+d)) - I2(clamp(clamp(p+d)+v))|."""
+    H, W, _ = src.shape
+    acc = 0.0
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            sx, sy = min(max(px + dx, 0), W - 1), min(max(py + dy, 0), H - 1)
+            tx, ty = min(max(sx + vx, 0), W - 1), min(max(sy + vy, 0), H - 1)
+            acc += np.abs(src[sy, sx] - tgt[ty, tx]).sum()
+    return acc / (3 * (2 * r + 1) ** 2)
+
+
+def test_identity_and_translation_planes_reduce_to_square_patch():
+    """An identity (or pure translation) plane gives exactly the square-patch cost."""
+    rng = np.random.default_rng(2)
+    H, W, r = 20, 24, 3
+    src, tgt = rng.random((H, W, 3)), rng.random((H, W, 3))
+    P = O.Params(W, H, patch_radius=r)
+    T = np.array([[1, 0, 7.25], [0, 1, -3.5], [0, 0, 1.0]])
+    for px, py, vx, vy in [(0, 0, 3, 4), (10, 10, -5, 2), (23, 19, -20, -15), (5, 18, 7, -1), (12, 3, 0, 0)]:
+        ref = _square_cost(src, tgt, r, px, py, vx, vy)
+        assert O.patch_cost(P, src, tgt, px, py, vx, vy) == pytest.approx(ref, rel=1e-14, abs=0)
+        assert O.patch_cost(P, src, tgt, px, py, vx, vy, np.eye(3)) == pytest.approx(ref, rel=1e-14, abs=0)
+        assert O.patch_cost(P, src, tgt, px, py, vx, vy, T) == pytest.approx(ref, rel=1e-12, abs=0)
+
+
+def test_warped_cost_closed_form_on_projective_ramp():
+    """Target frame = affine ramp R, source frame I1(p) = R(G p) for a homography G.
+
+    The patch of p warped by G with integer offset v samples R at
+    G(s) + e, e = p + v - G(p) the same for every tap, so the cost is
+    mean_c |a_c e_x + b_c e_y| exactly (bilinear reproduces the ramp).
+    """
+    H, W, r = 40, 48, 3
+    a, b, e0 = np.array([0.004, -0.003, 0.002]), np.array([0.002, 0.003, -0.004]), np.array([0.4, 0.5, 0.6])
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    tgt = xs[..., None] * a + ys[..., None] * b + e0
+    G = np.array([[1.05, 0.03, 2.3], [-0.02, 0.97, 1.7], [4e-4, -3e-4, 1.0]])
+    w = G[2, 0] * xs + G[2, 1] * ys + G[2, 2]
+    gx, gy = (G[0, 0] * xs + G[0, 1] * ys + G[0, 2]) / w, (G[1, 0] * xs + G[1, 1] * ys + G[1, 2]) / w
+    src = gx[..., None] * a + gy[..., None] * b + e0
+    P = O.Params(W, H, patch_radius=r)
+    for px, py in [(10, 10), (20, 15), (30, 25), (12, 28)]:
+        wp = G[2, 0] * px + G[2, 1] * py + G[2, 2]
+        Gx, Gy = (G[0, 0] * px + G[0, 1] * py + G[0, 2]) / wp, (G[1, 0] * px + G[1, 1] * py + G[1, 2]) / wp
+        for vx, vy in [(round(Gx - px), round(Gy - py)), (round(Gx - px) + 1, round(Gy - py) - 2)]:
+            ex, ey = px + vx - Gx, py + vy - Gy
+            want = np.abs(a * ex + b * ey).mean()
+            got = O.patch_cost(P, src, tgt, px, py, vx, vy, G)
+            assert got == pytest.approx(want, rel=1e-9, abs=1e-15)
+
+
+# ---------------------------------------------------------------- homography solvers
+def _norm(H):
+    H = np.asarray(H, float)
+    return H / np.linalg.norm(H) * np.sign(H[2, 2])
+
+
+def _rand_h(rng):
+    src = np.array([[0, 0], [40, 0], [40, 40], [0, 40]], float)
+    dst = src + rng.uniform(-8, 8, size=(4, 2))
+    from paper_1804_03787_gb300.scene import h_from_points
+    return h_from_points(src, dst)
+
+
+def _apply(H, p):
+    w = H[2, 0] * p[:, 0] + H[2, 1] * p[:, 1] + H[2, 2]
+    return np.stack([(H[0, 0] * p[:, 0] + H[0, 1] * p[:, 1] + H[0, 2]) / w,
+                     (H[1, 0] * p[:, 0] + H[1, 1] * p[:, 1] + H[1, 2]) / w], 1)
+
+
+def test_minimal_and_refit_recover_generating_homography():
+    """Noise-free real-valued correspondences give back the generating H to 1e-9."""
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        Hg = _rand_h(rng)
+        p = rng.uniform(0, 40, size=(50, 2))
+        q = _apply(Hg, p)
+        np.testing.assert_allclose(_norm(O.h_minimal(p[:4], q[:4])), _norm(Hg), atol=1e-9)
+        np.testing.assert_allclose(_norm(O.h_dlt(p, q)), _norm(Hg), atol=1e-9)
+
+
+def test_minimal_solver_rejects_collinear_sample():
+    p = np.array([[0, 0], [1, 1], [2, 2], [5, 0]], float)
+    assert O.h_minimal(p, p + 1) is None
+
+
+def test_dlt_is_least_squares_optimal_under_noise():
+    """With noise, the refit has smaller algebraic residual than the generating H
+    (it minimises ||A h|| over unit h in normalised coordinates)."""
+    rng = np.random.default_rng(4)
+    Hg = _rand_h(rng)
+    p = rng.uniform(0, 40, size=(200, 2))
+    q = _apply(Hg, p) + rng.normal(0, 0.3, size=(200, 2))
+    Hd = O.h_dlt(p, q)
+    err_d = np.linalg.norm(_apply(Hd, p) - q, axis=1).mean()
+    err_g = np.linalg.norm(_apply(Hg, p) - q, axis=1).mean()
+    assert err_d <= err_g * 1.01
+    assert np.abs(_apply(Hd, p) - _apply(Hg, p)).max() < 0.3
+
+
+def _affine_nnf(W, H, A):
+    ys, xs = np.divmod(np.arange(W * H), W)
+    q = _apply(A, np.stack([xs, ys], 1).astype(float))
+    return xs, ys, np.round(q[:, 0] - xs).astype(np.int32), np.round(q[:, 1] - ys).astype(np.int32)
+
+
+# an integer shear + translation: maps integer pixels to integer pixels
+A_INT = np.array([[1, 1, 2], [0, 1, -1], [0, 0, 1]], float)
+
+
+def test_exhaustive_consensus_matches_brute_force():
+    """On a tiny match set, RANSAC with many hypotheses reaches the best
+    consensus that brute force over all C(N,4) subsets reaches."""
+    rng = np.random.default_rng(5)
+    W, H, s = 8, 8, 4
+    P = O.Params(W, H, patch_radius=1, cells=(s,), num_hyp=4000, min_inliers=4, ransac_px=1.5)
+    xs, ys, vx, vy = _affine_nnf(W, H, A_INT)
+    win = (xs < s) & (ys < s)
+    out = np.flatnonzero(win)[rng.permutation(s * s)[:6]]
+    vx[out] += (rng.integers(3, 6, size=6) * rng.choice([-1, 1], size=6)).astype(np.int32)
+    vy[out] += (rng.integers(3, 6, size=6) * rng.choice([-1, 1], size=6)).astype(np.int32)
+    mh, mi = O.empty_models(P)
+    frame = np.zeros((H, W, 3))
+    O.fit_level(P, frame, frame, 0, 1, 1, vx, vy, None, mh, mi)
+    idx = np.flatnonzero(win)
+    ps = np.stack([xs[idx], ys[idx]], 1).astype(float)
+    qs = ps + np.stack([vx[idx], vy[idx]], 1)
+    best = 0
+    for comb in itertools.combinations(range(len(idx)), 4):
+        Hc = O.h_minimal(ps[list(comb)], qs[list(comb)])
+        if Hc is None:
+            continue
+        # orientation: denominator positive at the window centre
+        c = (s - 1) / 2.0
+        Hc = Hc * np.sign(Hc[2, 0] * c + Hc[2, 1] * c + Hc[2, 2])
+        with np.errstate(all="ignore"):
+            w = Hc[2, 0] * ps[:, 0] + Hc[2, 1] * ps[:, 1] + Hc[2, 2]
+            r2 = ((_apply(Hc, ps) - qs) ** 2).sum(1)
+        best = max(best, int(((r2 < 2.25) & (w > 0)).sum()))
+    assert best >= 10
+    assert mi[0, O.MI_BESTSCORE] == best and mi[0, O.MI_NIN] == 16
+
+
+def test_ransac_recovers_integer_affine_with_outliers():
+    """30 % gross outliers: the refit on the consensus set is the generating map to 1e-9."""
+    rng = np.random.default_rng(6)
+    W, H, s = 32, 32, 16
+    P = O.Params(W, H, patch_radius=1, cells=(s,), num_hyp=256)
+    xs, ys, vx, vy = _affine_nnf(W, H, A_INT)
+    win = (xs < s) & (ys < s)
+    out = np.flatnonzero(win)[rng.permutation(s * s)[:77]]
+    vx[out] += (rng.integers(4, 9, size=77) * rng.choice([-1, 1], size=77)).astype(np.int32)
+    vy[out] += (rng.integers(4, 9, size=77) * rng.choice([-1, 1], size=77)).astype(np.int32)
+    mh, mi = O.empty_models(P)
+    frame = np.zeros((H, W, 3))
+    O.fit_level(P, frame, frame, 0, 1, 1, vx, vy, None, mh, mi)
+    assert mi[0, O.MI_COUNT] == 256 - 77 and mi[0, O.MI_NIN] == 256 and mi[0, O.MI_VALID] == 1
+    assert mi[0, O.MI_FLAGS] & O.F_REFIT
+    np.testing.assert_allclose(_norm(mh[0].reshape(3, 3)), _norm(A_INT), atol=1e-9)
