@@ -1,0 +1,209 @@
+/*
+ * gpm.h -- C ABI of the GB300 (sm_103a) implementation of the data-parallel
+ * hot path of Multi-Scale Generalized Plane Match for optical flow
+ * (Choi and Banerjee, arXiv 1804.03787).
+ *
+ * One call per stage of the paper's problem statement:
+ *   gpm_match(level 0)       the initial PatchMatch NNF (Sec. 3.1; 7x7 patches
+ *                            in Sec. 4);
+ *   gpm_fit_planes(level l)  Algorithm 1 for one level: robust plane
+ *                            detection per overlapping window (Sec. 3.1.2),
+ *                            plane distortion compensation and assignment
+ *                            (Sec. 3.1.3, eq. 3-4), the residual second stage
+ *                            (Sec. 3.2), occlusion cues (Sec. 3.4), the
+ *                            cross-level merge and the NNF update (Sec. 3.3,
+ *                            3.3.1);
+ *   gpm_match(level l >= 1)  PatchMatch restricted to unassigned pixels, with
+ *                            plane-distorted patches (Sec. 3.3.2);
+ *   gpm_flow_and_occlusion   model propagation fill and the final flow and
+ *                            occlusion map (Sec. 3.4.1).
+ *
+ * Conventions
+ *   - All pointers to frames, flows and maps are DEVICE pointers unless a
+ *     parameter says "host".  Sizes are in elements unless they say bytes.
+ *   - Every call enqueues work on the context's CUDA stream and returns
+ *     without synchronising.  Results are valid once that stream has
+ *     reached them.  Argument errors are reported synchronously
+ *     (GPM_EINVAL) before anything is enqueued.  An error detected on the
+ *     device (a bounds check) is reported by the next call, or by gpm_sync.
+ *   - No exception or C++ type crosses this boundary.  A context is used by
+ *     one host thread at a time.
+ *   - Ownership: the caller owns frames and outputs; the context owns every
+ *     intermediate buffer, allocated at gpm_create through the caller's
+ *     allocator callbacks (or cudaMallocAsync when they are NULL) and released
+ *     by gpm_destroy.
+ *   - Stage order per pair: match(0), then fit_planes(l) and match(l) for
+ *     l = 1..num_scales, then flow_and_occlusion.  Out-of-order calls return
+ *     GPM_EINVAL.
+ */
+#ifndef GPM_H
+#define GPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GPM_OK = 0,
+    GPM_EINVAL = 1,     /* bad argument, shape, parameter or call order */
+    GPM_ENOMEM = 2,     /* the allocator callback returned NULL */
+    GPM_ECUDA = 3,      /* a CUDA runtime call failed */
+    GPM_ETIMEOUT = 4,   /* a bounded device wait gave up */
+    GPM_EBUSY = 5,      /* no free slot / HBM budget exhausted */
+    GPM_EINTERNAL = 6   /* a device-side consistency check failed */
+} gpm_status;
+
+/* storage type of the frames inside the context (arithmetic is FP32) */
+typedef enum { GPM_F32 = 0, GPM_F16 = 1, GPM_BF16 = 2 } gpm_dtype;
+
+#define GPM_MAX_SCALES 8
+
+/* Method parameters.  Names follow the paper where it names them. */
+typedef struct {
+    int32_t patch_radius;                 /* r: 3 -> 7x7 (Sec. 4), 4 -> 9x9 */
+    int32_t num_scales;                   /* levels k of Sec. 3.3 */
+    int32_t cell_size[GPM_MAX_SCALES];    /* window side per level, coarse to fine; even, >= 4 */
+    int32_t pm_iters;                     /* PatchMatch red-black iterations per run */
+    int32_t num_hyp;                      /* RANSAC hypotheses per window, 1..4096 */
+    int32_t min_inliers;                  /* minimum RANSAC support (>= 4) */
+    int32_t fill_iters;                   /* model propagation iterations */
+    int32_t gain_normalize;               /* 1: scale I2 by mean(I1)/mean(I2) */
+    int32_t pm_init;                      /* 1: random initial NNF; 0: keep the current one */
+    int32_t storage;                      /* gpm_dtype of the ingested frames */
+    int32_t reserved0;
+    float eps;                            /* epsilon of eq. 4 (mean |RGB| error, frames in [0,1]) */
+    float ransac_px;                      /* RANSAC inlier radius in pixels */
+    float fb_px;                          /* forward-backward / many-to-one flow tolerance */
+    float eta;                            /* symmetric-overlap threshold of Sec. 3.4 */
+    float kappa;                          /* RANSAC / colour inlier overlap threshold */
+    float beta;                           /* coarse-level priority margin in the merge */
+    float occ_thresh;                     /* final warp-error occlusion threshold */
+    float scale_min, scale_max;           /* plane validity: local area scale range */
+    uint64_t seed;                        /* Philox4x32-10 key */
+} gpm_params;
+
+/* Capacity of a context, fixed at creation. */
+typedef struct {
+    int32_t max_width, max_height;        /* largest frame */
+    int32_t max_pairs;                    /* pairs processed per call */
+    int32_t reserved;
+    size_t hbm_budget_bytes;              /* 0 = no limit; else gpm_create fails with GPM_EBUSY above it */
+} gpm_limits;
+
+/* One frame pair.  Frames are caller-owned DEVICE buffers, H x W x 3 (HWC),
+   FP32 values in [0,1], row stride in elements (>= 3 * width). */
+typedef struct {
+    int32_t width, height;
+    int64_t row_stride;
+    const float* frame1;
+    const float* frame2;
+    uint32_t pair_id;                     /* Philox counter word: results depend on it */
+    uint32_t reserved;
+} gpm_pair;
+
+/* Optional allocator (e.g. PyTorch's caching allocator).  alloc returns a
+   device pointer aligned to 256 bytes, or NULL. */
+typedef void* (*gpm_alloc_fn)(void* user, size_t bytes, void* stream);
+typedef void (*gpm_free_fn)(void* user, void* ptr, void* stream);
+
+typedef struct gpm_ctx gpm_ctx;
+
+/* Fills *p with the default parameters (7x7 patches, cells 32/16/8, ...). */
+void gpm_default_params(gpm_params* p);
+
+/* Creates a context for up to limits->max_pairs pairs of at most
+   max_width x max_height.  stream: a cudaStream_t (NULL = legacy default).
+   Errors: GPM_EINVAL (bad params or limits), GPM_ENOMEM, GPM_EBUSY (budget),
+   GPM_ECUDA.  *out is NULL on error. */
+gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_alloc_fn alloc,
+                      gpm_free_fn free_fn, void* user, void* stream, gpm_ctx** out);
+
+/* Releases everything the context allocated (synchronises its stream). */
+gpm_status gpm_destroy(gpm_ctx* ctx);
+
+/* Bytes of device memory a context with these parameters and limits holds. */
+size_t gpm_required_bytes(const gpm_params* params, const gpm_limits* limits);
+
+/* level 0: ingest the pairs' frames (RGB -> RGBX storage, gain
+   normalisation), initial NNF for both directions (random offsets from
+   Philox, Sec. 3.1) and pm_iters red-black PatchMatch iterations.
+   level l >= 1: PatchMatch restricted to the pixels without an assigned
+   plane after gpm_fit_planes(l), patches distorted by the pixel's home
+   window plane (Sec. 3.3.2).  pairs is a HOST array of n_pairs descriptors;
+   at level >= 1 it may be NULL (the pairs of the last level-0 call are
+   used). */
+gpm_status gpm_match(gpm_ctx* ctx, const gpm_pair* pairs, int32_t n_pairs, int32_t level);
+
+/* Algorithm 1 for level l (1 <= l <= num_scales) on every pair of the last
+   gpm_match(0): both RANSAC stages per window, assignment by eq. 3-4, the
+   symmetry, overlap and many-to-one cues of Sec. 3.4, the coarse-priority
+   merge of Sec. 3.3 and the NNF update of Sec. 3.3.1. */
+gpm_status gpm_fit_planes(gpm_ctx* ctx, int32_t n_pairs, int32_t level);
+
+/* Model propagation fill, final flow and occlusion map (Sec. 3.4.1) for the
+   forward direction I1 -> I2.  flow_out[i]: DEVICE buffer H x W x 2 float
+   (x, y); occ_out[i]: DEVICE buffer H x W uint8 (1 = occluded).  Both are
+   HOST arrays of n_pairs device pointers. */
+gpm_status gpm_flow_and_occlusion(gpm_ctx* ctx, int32_t n_pairs, float* const* flow_out,
+                                  uint8_t* const* occ_out);
+
+/* Waits for the context's stream and reports any pending device error. */
+gpm_status gpm_sync(gpm_ctx* ctx);
+
+/* ---- state export / import (parity checks, resume at a level boundary) ----
+   All buffers are DEVICE pointers; n = width * height of the pair,
+   m = number of models of one direction = 2 * (total windows over all
+   levels), model id = (first window of the level + window) * 2 + stage - 1.
+   Layouts (direction-major: [direction 0 = I1->I2, direction 1 = I2->I1]):
+     GPM_NNF        int32  [2][n][2]   offsets (dx, dy) to the match p + v
+     GPM_COST       float  [2][n]      patch cost of the current offset
+     GPM_MODELS     double [2][m][9]   homographies (row major, source ->
+                                       target pixels, unit Frobenius norm,
+                                       positive denominator at the window centre)
+     GPM_MODEL_INFO int32  [2][m][12]  valid, inliers, RANSAC input size,
+                                       winning hypothesis, its inliers, flags,
+                                       |S_R n S_C|, assigned, symmetric, 3 x 0
+     GPM_LABELS     int32  [2][n] model id (-1 none), then float [2][n] L,
+                    then double [2][n][2] plane flow (8-byte aligned: the
+                    float block is padded to a multiple of 8 bytes)
+                                                              (accumulated map)
+     GPM_LEVEL_LABELS same layout: this level's labels after the cues
+     GPM_STAGE1_LABELS same layout: this level's first-stage labels
+     GPM_CUES       uint8  [2][n]      bit 0 = many-to-one occlusion cue
+     GPM_FRAMES     float  [2][n][4]   ingested frames as FP32 RGBX (export only)
+   Import accepts GPM_NNF, GPM_MODELS (+ valid bits from GPM_MODEL_INFO when
+   imported right after), GPM_LABELS and GPM_CUES; it sets the stage order so
+   that the next call may follow the imported state. */
+enum {
+    GPM_NNF = 0,
+    GPM_COST = 1,
+    GPM_MODELS = 2,
+    GPM_MODEL_INFO = 3,
+    GPM_LABELS = 4,
+    GPM_LEVEL_LABELS = 5,
+    GPM_STAGE1_LABELS = 6,
+    GPM_CUES = 7,
+    GPM_FRAMES = 8
+};
+/* Bytes of one export of `what` for pair `pair` (0 if unknown). */
+size_t gpm_state_bytes(const gpm_ctx* ctx, int32_t pair, int32_t what);
+gpm_status gpm_export(gpm_ctx* ctx, int32_t pair, int32_t what, void* dst_device);
+/* level: the last completed level the imported state belongs to (0 = after
+   the level-0 PatchMatch). */
+gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_device, int32_t level);
+
+/* Human-readable status name and the context's last error message. */
+const char* gpm_status_string(gpm_status s);
+const char* gpm_last_error(const gpm_ctx* ctx);
+
+/* Kernel launches the context has enqueued since creation (all calls). */
+uint64_t gpm_launch_count(const gpm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPM_H */

@@ -1,0 +1,311 @@
+// Device-side building blocks shared by the GB300 kernels: counter-based
+// random numbers, frame texel loads, bilinear sampling, window geometry and
+// the FP32 evaluation form of a plane homography.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpm {
+
+constexpr int kMI = 12;  // integer fields per model (layout of GPM_MODEL_INFO)
+enum { MI_VALID = 0, MI_COUNT, MI_NIN, MI_BESTK, MI_BESTSCORE, MI_FLAGS, MI_NRC, MI_NASSIGN, MI_NSYM, MI_AMB };
+enum { F_FITTED = 1, F_REFIT = 2, F_AMBIG = 4, F_BAD_FB = 8, F_BAD_KAPPA = 16, F_BAD_GEOM = 32 };
+enum { CUE_M2O = 1 };
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds, each two
+// 32x32->64 products whose halves are mixed with the other counter words and
+// the key; the key advances by the Weyl constants after every round.
+__device__ __forceinline__ uint4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                        uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Counter words: (element index, sub-index, stream tag, pair id).
+__host__ __device__ __forceinline__ uint32_t stream_tag(int purpose, int dir, int level, int stage) {
+    return ((uint32_t)purpose << 24) | ((uint32_t)dir << 16) | ((uint32_t)level << 8) | (uint32_t)stage;
+}
+enum { RNG_INIT = 1, RNG_SEARCH = 2, RNG_RANSAC = 3 };
+
+// ---------------------------------------------------------------- frames
+// Frames live as RGBX texels: FP32 float4 (16 B), or FP16 / BF16 x4 (8 B).
+template <int ST>
+__device__ __forceinline__ float4 ldpix(const void* base, int i);
+template <>
+__device__ __forceinline__ float4 ldpix<0>(const void* base, int i) {
+    return __ldg(reinterpret_cast<const float4*>(base) + i);
+}
+template <>
+__device__ __forceinline__ float4 ldpix<1>(const void* base, int i) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(base) + i);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 ldpix<2>(const void* base, int i) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2*>(base) + i);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Bilinear sample at X = ix + fx, Y = iy + fy (fx, fy in [0,1)), the point
+// first clamped to [0, W-1] x [0, H-1].
+template <int ST>
+__device__ __forceinline__ float3 bilinear(const void* img, int W, int H, int ix, float fx, int iy, float fy) {
+    if (ix < 0) {
+        ix = 0;
+        fx = 0.f;
+    } else if (ix >= W - 1) {
+        ix = W - 1;
+        fx = 0.f;
+    }
+    if (iy < 0) {
+        iy = 0;
+        fy = 0.f;
+    } else if (iy >= H - 1) {
+        iy = H - 1;
+        fy = 0.f;
+    }
+    const int ix1 = min(ix + 1, W - 1), iy1 = min(iy + 1, H - 1);
+    const float4 a = ldpix<ST>(img, iy * W + ix), b = ldpix<ST>(img, iy * W + ix1);
+    const float4 c = ldpix<ST>(img, iy1 * W + ix), d = ldpix<ST>(img, iy1 * W + ix1);
+    const float gx = 1.f - fx, gy = 1.f - fy;
+    float3 o;
+    o.x = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
+    o.y = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
+    o.z = gy * (gx * a.z + fx * b.z) + fy * (gx * c.z + fx * d.z);
+    return o;
+}
+
+__device__ __forceinline__ float absdiff3(float4 a, float3 b) {
+    return fabsf(a.x - b.x) + fabsf(a.y - b.y) + fabsf(a.z - b.z);
+}
+
+// ---------------------------------------------------------------- window grid
+// Windows of side s at stride h = s/2 from 0, plus one flush with the far
+// border when the regular ones stop short of it (Sec. 3.1.2: half overlap).
+struct AxisGrid {
+    int n_reg;   // regular windows at i * h
+    int extra;   // 1 if a last window sits at size - s
+    int count;   // n_reg + extra
+    int last;    // position of the extra window
+};
+struct LevelGeom {
+    int s, h, base;  // side, stride, index of the level's first window in the model table
+    AxisGrid gx, gy;
+    __host__ __device__ int ncells() const { return gx.count * gy.count; }
+};
+
+__host__ __device__ inline AxisGrid make_axis(int n, int s) {
+    AxisGrid a;
+    const int h = s / 2;
+    if (s <= 0 || n < s) {
+        a.n_reg = a.extra = a.count = 0;
+        a.last = 0;
+        return a;
+    }
+    a.n_reg = (n - s) / h + 1;
+    a.extra = ((a.n_reg - 1) * h + s < n) ? 1 : 0;
+    a.count = a.n_reg + a.extra;
+    a.last = n - s;
+    return a;
+}
+__host__ __device__ __forceinline__ int win_pos(const AxisGrid& a, int h, int i) {
+    return i < a.n_reg ? i * h : a.last;
+}
+// Windows covering coordinate x, ascending: returns count (<= 3) and fills idx.
+__device__ __forceinline__ int covering(const AxisGrid& a, int s, int h, int x, int idx[3]) {
+    int k = 0;
+    int lo = x - s + 1 > 0 ? (x - s + 1 + h - 1) / h : 0;
+    int hi = min(x / h, a.n_reg - 1);
+    for (int i = lo; i <= hi && k < 2; ++i) idx[k++] = i;
+    if (a.extra && x >= a.last) idx[k++] = a.n_reg;
+    return k;
+}
+// Home window: the window whose central half holds x.
+__device__ __forceinline__ int home_index(const AxisGrid& a, int s, int h, int x) {
+    const int t = x - s / 4;
+    int i = t >= 0 ? t / h : -1;
+    return min(max(i, 0), a.count - 1);
+}
+
+// ---------------------------------------------------------------- plane models
+// FP32 evaluation form of a homography, in coordinates local to the window
+// origin o = (x0 + s/2, y0 + s/2), scaled so that the denominator is 1 at the
+// window centre (o - 0.5).  With u = p - o:
+//   e = den - 1 = e0 + g0 ux + g1 uy,
+//   flow D(u) = H(u) - u = t + (S - t e) / (1 + e),
+//   S_x = b0 ux + h1 uy - ux e, S_y = h3 ux + b4 uy - uy e,
+// where b0 = h0 - 1, b4 = h4 - 1 and the translation t = (h2, h5) is kept as
+// a hi/lo pair of floats.  Every term but t is small near the window, so the
+// flow keeps ~1e-7 px absolute accuracy even for 100+ px motions.
+struct __align__(16) Mef {
+    float b0, h1, h2h, h2l;
+    float h3, b4, h5h, h5l;
+    float g0, g1, e0, pad0;
+    int ox, oy, valid, pad1;
+};
+
+// Splits a flow component t_hi + c (c small) into integer k and fraction f in [0,1).
+__device__ __forceinline__ void split_flow(float th, float c, int& k, float& f) {
+    float t = floorf(th + c);
+    f = (th - t) + c;
+    if (f < 0.f) {
+        f += 1.f;
+        t -= 1.f;
+    } else if (f >= 1.f) {
+        f -= 1.f;
+        t += 1.f;
+    }
+    k = (int)t;
+}
+
+// Flow of the model at local integer point u.  Returns false if the
+// projective denominator is not positive.  (kx + fx, ky + fy) = D(u).
+__device__ __forceinline__ bool mef_flow(const Mef& m, float ux, float uy, int& kx, float& fx, int& ky, float& fy) {
+    const float e = m.e0 + m.g0 * ux + m.g1 * uy;
+    const float den = 1.f + e;
+    if (!(den > 0.f)) return false;
+    const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
+    const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
+    const float cx = m.h2l + (Sx - m.h2h * e) / den;
+    const float cy = m.h5l + (Sy - m.h5h * e) / den;
+    split_flow(m.h2h, cx, kx, fx);
+    split_flow(m.h5h, cy, ky, fy);
+    return true;
+}
+
+// Same, as rounded offset v = floor(D + 0.5) and remainder r = D - v in [-0.5, 0.5).
+__device__ __forceinline__ void round_split(int k, float f, int& v, float& r) {
+    if (f >= 0.5f) {
+        v = k + 1;
+        r = f - 1.f;
+    } else {
+        v = k;
+        r = f;
+    }
+}
+
+// Squared-residual test of a match (u, u + v) against the model:
+// ||H(u) - (u + v)||^2 < t2, evaluated as n^2 < t2 den^2 with den > 0.
+__device__ __forceinline__ bool mef_inlier(const Mef& m, float ux, float uy, float vx, float vy, float t2) {
+    const float e = m.e0 + m.g0 * ux + m.g1 * uy;
+    const float den = 1.f + e;
+    const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
+    const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
+    const float nx = ((m.h2h - vx) + m.h2l) + Sx - vx * e;
+    const float ny = ((m.h5h - vy) + m.h5l) + Sy - vy * e;
+    return den > 0.f && nx * nx + ny * ny < t2 * den * den;
+}
+
+// Local homography (double, rows, maps u -> local target) to the evaluation
+// form.  Orientation and scale: denominator +1 at the window centre
+// (-0.5, -0.5).  Returns false if that denominator is zero.
+__host__ __device__ inline bool make_mef(const double* Hl, int ox, int oy, Mef& m) {
+    const double dc = Hl[8] - 0.5 * (Hl[6] + Hl[7]);
+    if (!(dc != 0.0)) return false;
+    const double k = 1.0 / dc;
+    double h[9];
+    for (int i = 0; i < 9; ++i) h[i] = Hl[i] * k;
+    m.b0 = (float)(h[0] - 1.0);
+    m.h1 = (float)h[1];
+    m.h2h = (float)h[2];
+    m.h2l = (float)(h[2] - (double)m.h2h);
+    m.h3 = (float)h[3];
+    m.b4 = (float)(h[4] - 1.0);
+    m.h5h = (float)h[5];
+    m.h5l = (float)(h[5] - (double)m.h5h);
+    m.g0 = (float)h[6];
+    m.g1 = (float)h[7];
+    m.e0 = (float)(h[8] - 1.0);
+    m.pad0 = 0.f;
+    m.ox = ox;
+    m.oy = oy;
+    m.pad1 = 0;
+    return true;
+}
+
+// absolute H = T(o) Hl T(-o), unit Frobenius norm, positive denominator at
+// the window centre (o - 0.5).
+__host__ __device__ inline void local_to_abs(const double* Hl, int ox, int oy, double* Ha) {
+    // Hl' = Hl * T(-o): columns: c2' = c2 - ox c0 - oy c1
+    double t[9];
+    for (int r = 0; r < 3; ++r) {
+        t[r * 3 + 0] = Hl[r * 3 + 0];
+        t[r * 3 + 1] = Hl[r * 3 + 1];
+        t[r * 3 + 2] = Hl[r * 3 + 2] - ox * Hl[r * 3 + 0] - oy * Hl[r * 3 + 1];
+    }
+    // T(o) * t: rows: r0 += ox r2, r1 += oy r2
+    for (int c = 0; c < 3; ++c) {
+        Ha[0 * 3 + c] = t[0 * 3 + c] + ox * t[2 * 3 + c];
+        Ha[1 * 3 + c] = t[1 * 3 + c] + oy * t[2 * 3 + c];
+        Ha[2 * 3 + c] = t[2 * 3 + c];
+    }
+    const double cx = ox - 0.5, cy = oy - 0.5;
+    const double w = Ha[6] * cx + Ha[7] * cy + Ha[8];
+    double f = 0;
+    for (int i = 0; i < 9; ++i) f += Ha[i] * Ha[i];
+    f = sqrt(f);
+    if (w < 0) f = -f;
+    for (int i = 0; i < 9; ++i) Ha[i] /= f;
+}
+
+// local H = T(-o) Ha T(o)
+__host__ __device__ inline void abs_to_local(const double* Ha, int ox, int oy, double* Hl) {
+    double t[9];
+    for (int r = 0; r < 3; ++r) {
+        t[r * 3 + 0] = Ha[r * 3 + 0];
+        t[r * 3 + 1] = Ha[r * 3 + 1];
+        t[r * 3 + 2] = Ha[r * 3 + 2] + ox * Ha[r * 3 + 0] + oy * Ha[r * 3 + 1];
+    }
+    for (int c = 0; c < 3; ++c) {
+        Hl[0 * 3 + c] = t[0 * 3 + c] - ox * t[2 * 3 + c];
+        Hl[1 * 3 + c] = t[1 * 3 + c] - oy * t[2 * 3 + c];
+        Hl[2 * 3 + c] = t[2 * 3 + c];
+    }
+}
+
+// ---------------------------------------------------------------- per-pair device view
+struct Labels {
+    int* m;      // model id, -1 = none
+    float* L;    // robust loss of eq. 4
+    int2* v;     // rounded plane flow
+    float2* r;   // plane flow minus v, in [-0.5, 0.5)
+};
+
+struct PairView {
+    int W, H, n;
+    int m_models;         // models per direction (bound of every model id)
+    uint32_t pair_id;
+    const void* img[2];   // ingested I1, I2 (RGBX in storage type)
+    int2* nnf[2];
+    float* cost[2];
+    uint8_t* frozen[2];
+    uint8_t* cue[2];
+    uint8_t* resid[2];
+    Labels acc[2], tent[2], st1[2], lvl[2];
+    double* mh[2];        // [m][9] absolute homographies
+    Mef* mef[2];          // [m]
+    int* mi[2];           // [m][kMI]
+    int* list[2];         // unfrozen pixel indices, colour 0 then colour 1
+    int* list_count;      // [2 dirs][2 colours]
+    unsigned long long* m2o_key[2];
+};
+
+}  // namespace gpm

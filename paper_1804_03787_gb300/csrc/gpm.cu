@@ -1,0 +1,629 @@
+// Host runtime of the C ABI declared in include/gpm.h: context and memory
+// layout, stage ordering, the level loop of Algorithm 1 and state
+// import/export.  All device work goes to the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gpm.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace gpm;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Slot {
+    int W = 0, H = 0, n = 0;
+    uint32_t pair_id = 0;
+    int stage = -1;  // -1 nothing; 2l = after match(l); 2l-1 = after fit_planes(l)
+    void* block = nullptr;
+    PairView pv{};
+    LevelGeom geoms[GPM_MAX_SCALES];
+    LevelGeom* d_geoms = nullptr;
+    int total_cells = 0, m = 0;
+    double* partial = nullptr;
+    double* gain = nullptr;
+};
+
+}  // namespace
+
+struct gpm_ctx {
+    gpm_params P{};
+    gpm_limits lim{};
+    gpm_alloc_fn alloc = nullptr;
+    gpm_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    cudaStream_t stream = nullptr;
+    int nsm = 152;
+    int max_n = 0, max_models = 0;
+    size_t slot_bytes = 0;
+    std::vector<Slot> slots;
+    std::string err;
+    uint64_t launches = 0;
+};
+
+namespace {
+
+const int kPartialBlocks = 128;
+
+gpm_status fail(gpm_ctx* c, gpm_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+gpm_status cuda_check(gpm_ctx* c, const char* where) {
+    const cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, GPM_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+    }
+    return GPM_OK;
+}
+
+int total_cells_for(const gpm_params& P, int W, int H, LevelGeom* geoms) {
+    int total = 0;
+    for (int l = 0; l < P.num_scales; ++l) {
+        LevelGeom g{};
+        g.s = P.cell_size[l];
+        g.h = g.s / 2;
+        g.gx = make_axis(W, g.s);
+        g.gy = make_axis(H, g.s);
+        g.base = total;
+        if (geoms) geoms[l] = g;
+        total += g.ncells();
+    }
+    return total;
+}
+
+gpm_status validate_params(const gpm_params& P, std::string& why) {
+    if (P.patch_radius < 1 || P.patch_radius > 4) return why = "patch_radius must be 1..4", GPM_EINVAL;
+    if (P.num_scales < 0 || P.num_scales > GPM_MAX_SCALES) return why = "num_scales must be 0..8", GPM_EINVAL;
+    for (int l = 0; l < P.num_scales; ++l) {
+        const int s = P.cell_size[l];
+        if (s < 4 || s > 64 || (s & 1)) return why = "cell sizes must be even, 4..64", GPM_EINVAL;
+    }
+    if (P.pm_iters < 0 || P.pm_iters > 64) return why = "pm_iters must be 0..64", GPM_EINVAL;
+    if (P.num_hyp < 1 || P.num_hyp > 4096) return why = "num_hyp must be 1..4096", GPM_EINVAL;
+    if (P.min_inliers < 4) return why = "min_inliers must be >= 4", GPM_EINVAL;
+    if (P.fill_iters < 0 || P.fill_iters > 1024) return why = "fill_iters must be 0..1024", GPM_EINVAL;
+    if (P.storage < 0 || P.storage > 2) return why = "storage must be GPM_F32, GPM_F16 or GPM_BF16", GPM_EINVAL;
+    if (!(P.eps > 0) || !(P.ransac_px > 0) || !(P.fb_px > 0)) return why = "eps, ransac_px, fb_px must be > 0", GPM_EINVAL;
+    if (!(P.scale_min > 0) || !(P.scale_max >= P.scale_min)) return why = "bad scale range", GPM_EINVAL;
+    return GPM_OK;
+}
+
+// Carves one slot's buffers out of a single block; returns bytes needed.
+size_t layout_slot(const gpm_params& P, int max_n, int max_models, char* base, Slot* s) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        off = (off + kAlign - 1) / kAlign * kAlign;
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const size_t n = (size_t)max_n, m = (size_t)max_models;
+    const size_t texel = P.storage == 0 ? 16 : 8;
+    PairView pv{};
+    for (int d = 0; d < 2; ++d) pv.img[d] = take(n * texel);
+    for (int d = 0; d < 2; ++d) {
+        pv.nnf[d] = (int2*)take(n * sizeof(int2));
+        pv.cost[d] = (float*)take(n * sizeof(float));
+        pv.frozen[d] = (uint8_t*)take(n);
+        pv.cue[d] = (uint8_t*)take(n);
+        pv.resid[d] = (uint8_t*)take(n);
+        Labels* sets[4] = {&pv.acc[d], &pv.tent[d], &pv.st1[d], &pv.lvl[d]};
+        for (Labels* l : sets) {
+            l->m = (int*)take(n * sizeof(int));
+            l->L = (float*)take(n * sizeof(float));
+            l->v = (int2*)take(n * sizeof(int2));
+            l->r = (float2*)take(n * sizeof(float2));
+        }
+        pv.mh[d] = (double*)take(m * 9 * sizeof(double));
+        pv.mef[d] = (Mef*)take(m * sizeof(Mef));
+        pv.mi[d] = (int*)take(m * kMI * sizeof(int));
+        pv.list[d] = (int*)take(2 * n * sizeof(int));
+        pv.m2o_key[d] = (unsigned long long*)take(n * sizeof(unsigned long long));
+    }
+    pv.list_count = (int*)take(4 * sizeof(int));
+    LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
+    double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
+    double* gain = (double*)take(sizeof(double));
+    if (s) {
+        s->pv = pv;
+        s->d_geoms = dg;
+        s->partial = partial;
+        s->gain = gain;
+    }
+    return off;
+}
+
+PlaneParams plane_params(const gpm_params& P) {
+    PlaneParams pp{};
+    pp.num_hyp = P.num_hyp;
+    pp.min_inliers = P.min_inliers;
+    pp.radius = P.patch_radius;
+    pp.storage = P.storage;
+    pp.t2 = P.ransac_px * P.ransac_px;
+    pp.eps = P.eps;
+    pp.fb2 = P.fb_px * P.fb_px;
+    pp.eta = P.eta;
+    pp.kappa = P.kappa;
+    pp.beta = P.beta;
+    pp.occ_thresh = P.occ_thresh;
+    pp.scale_min = P.scale_min;
+    pp.scale_max = P.scale_max;
+    pp.k0 = (uint32_t)(P.seed & 0xFFFFFFFFull);
+    pp.k1 = (uint32_t)(P.seed >> 32);
+    return pp;
+}
+
+int grid_for(const gpm_ctx* c, int n) {
+    const int want = (n + 255) / 256;
+    return std::max(1, std::min(want, c->nsm * 8));
+}
+
+int num_radii(int W, int H) {
+    const int R0 = std::max(W, H);
+    int k = 0;
+    while ((R0 >> k) >= 1) ++k;
+    return k;
+}
+
+// Sets the slot's frame size and level geometry (uploaded to the device).
+gpm_status set_dims(gpm_ctx* c, Slot& s, int W, int H) {
+    if (s.W == W && s.H == H) return GPM_OK;
+    s.W = W;
+    s.H = H;
+    s.n = W * H;
+    s.total_cells = total_cells_for(c->P, W, H, s.geoms);
+    s.m = 2 * s.total_cells;
+    s.pv.W = W;
+    s.pv.H = H;
+    s.pv.n = s.n;
+    s.pv.m_models = s.m;
+    cudaMemcpyAsync(s.d_geoms, s.geoms, sizeof(LevelGeom) * GPM_MAX_SCALES, cudaMemcpyHostToDevice, c->stream);
+    // a defined NNF (zero offsets) before anything reads it
+    for (int d = 0; d < 2; ++d) cudaMemsetAsync(s.pv.nnf[d], 0, sizeof(int2) * s.n, c->stream);
+    return cuda_check(c, "set_dims");
+}
+
+void reset_models(gpm_ctx* c, Slot& s) {
+    for (int d = 0; d < 2; ++d) {
+        cudaMemsetAsync(s.pv.mh[d], 0, sizeof(double) * 9 * s.m, c->stream);
+        cudaMemsetAsync(s.pv.mef[d], 0, sizeof(Mef) * s.m, c->stream);
+        cudaMemsetAsync(s.pv.mi[d], 0, sizeof(int) * kMI * s.m, c->stream);
+    }
+}
+
+void build_lists(gpm_ctx* c, Slot& s) {
+    cudaMemsetAsync(s.pv.list_count, 0, 4 * sizeof(int), c->stream);
+    launch_build_lists(s.pv, grid_for(c, s.n), c->stream);
+    c->launches += 1;
+}
+
+void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
+    PmLaunch L{};
+    L.pv = &s.pv;
+    L.geom = level > 0 ? s.geoms[level - 1] : LevelGeom{};
+    L.radius = c->P.patch_radius;
+    L.storage = c->P.storage;
+    L.level = level;
+    L.nrad = num_radii(s.W, s.H);
+    L.grid_blocks = c->nsm * 8;
+    L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
+    L.k1 = (uint32_t)(c->P.seed >> 32);
+    if (level > 0 || !c->P.pm_init) {
+        L.op = PmLaunch::RECOST;
+        launch_pm(L, c->stream);
+        c->launches += 1;
+    }
+    L.op = PmLaunch::SWEEP;
+    for (int it = 0; it < c->P.pm_iters; ++it)
+        for (int ph = 0; ph < 2; ++ph) {
+            L.it = it;
+            L.phase = ph;
+            launch_pm(L, c->stream);
+            c->launches += 1;
+        }
+}
+
+void copy_labels(gpm_ctx* c, const Labels& dst, const Labels& src, int n) {
+    cudaMemcpyAsync(dst.m, src.m, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(dst.L, src.L, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(dst.v, src.v, sizeof(int2) * n, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(dst.r, src.r, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+// Algorithm 1 for one level on one pair (both directions in every launch).
+void fit_level(gpm_ctx* c, Slot& s, int level) {
+    const LevelGeom& g = s.geoms[level - 1];
+    const PlaneParams pp = plane_params(c->P);
+    const int gb = grid_for(c, s.n);
+    cudaStream_t st = c->stream;
+    // first stage: fit, tentative assignment, cues on both directions, final assignment
+    launch_ransac(s.pv, g, level, 1, pp, st);
+    launch_assign(s.pv, g, 1, 0, 0, pp, gb, st);
+    launch_cues(s.pv, g, 1, 0, pp, gb, st);
+    launch_assign(s.pv, g, 1, 1, 1, pp, gb, st);
+    // second stage on the residual pixels
+    launch_ransac(s.pv, g, level, 2, pp, st);
+    for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
+    launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
+    launch_cues(s.pv, g, 2, 2, pp, gb, st);
+    for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
+    launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
+    // many-to-one, merge, NNF update, lists for the restricted sweeps
+    launch_many_to_one(s.pv, pp, gb, st);
+    launch_merge_update(s.pv, pp, gb, st);
+    c->launches += 2 + 3 + 1 + 3 + 1 + 3 + 1 + 2 + 1;
+    build_lists(c, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+void gpm_default_params(gpm_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->patch_radius = 3;
+    p->num_scales = 3;
+    p->cell_size[0] = 32;
+    p->cell_size[1] = 16;
+    p->cell_size[2] = 8;
+    p->pm_iters = 4;
+    p->num_hyp = 256;
+    p->min_inliers = 8;
+    p->fill_iters = 8;
+    p->gain_normalize = 1;
+    p->pm_init = 1;
+    p->storage = GPM_F32;
+    p->eps = 0.06f;
+    p->ransac_px = 1.5f;
+    p->fb_px = 1.0f;
+    p->eta = 0.5f;
+    p->kappa = 0.5f;
+    p->beta = 0.015f;
+    p->occ_thresh = 0.06f;
+    p->scale_min = 0.5f;
+    p->scale_max = 2.0f;
+    p->seed = 0;
+}
+
+size_t gpm_required_bytes(const gpm_params* params, const gpm_limits* limits) {
+    if (!params || !limits || limits->max_width <= 0 || limits->max_height <= 0 || limits->max_pairs <= 0) return 0;
+    const int max_n = limits->max_width * limits->max_height;
+    const int max_models = 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr);
+    const size_t per = layout_slot(*params, max_n, std::max(max_models, 2), nullptr, nullptr);
+    return per * (size_t)limits->max_pairs;
+}
+
+gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_alloc_fn alloc, gpm_free_fn free_fn,
+                      void* user, void* stream, gpm_ctx** out) {
+    if (!out) return GPM_EINVAL;
+    *out = nullptr;
+    if (!params || !limits) return GPM_EINVAL;
+    std::string why;
+    if (validate_params(*params, why) != GPM_OK) return GPM_EINVAL;
+    if (limits->max_width < 4 || limits->max_height < 4 || limits->max_pairs < 1 || limits->max_pairs > 4096 ||
+        (int64_t)limits->max_width * limits->max_height > (1 << 26) || limits->max_width > 32767 ||
+        limits->max_height > 32767)
+        return GPM_EINVAL;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return GPM_EINVAL;
+    gpm_ctx* c = new (std::nothrow) gpm_ctx();
+    if (!c) return GPM_ENOMEM;
+    c->P = *params;
+    c->lim = *limits;
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = user;
+    c->stream = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return GPM_ECUDA;
+    }
+    c->max_n = limits->max_width * limits->max_height;
+    c->max_models = std::max(2, 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr));
+    c->slot_bytes = layout_slot(*params, c->max_n, c->max_models, nullptr, nullptr);
+    if (limits->hbm_budget_bytes && c->slot_bytes * (size_t)limits->max_pairs > limits->hbm_budget_bytes) {
+        delete c;
+        return GPM_EBUSY;
+    }
+    c->slots.resize(limits->max_pairs);
+    for (auto& s : c->slots) {
+        void* p = nullptr;
+        if (alloc) {
+            p = alloc(user, c->slot_bytes, stream);
+        } else if (cudaMallocAsync(&p, c->slot_bytes, c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        if (!p) {
+            gpm_destroy(c);
+            return GPM_ENOMEM;
+        }
+        s.block = p;
+        layout_slot(*params, c->max_n, c->max_models, (char*)p, &s);
+    }
+    *out = c;
+    return GPM_OK;
+}
+
+gpm_status gpm_destroy(gpm_ctx* c) {
+    if (!c) return GPM_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    for (auto& s : c->slots) {
+        if (!s.block) continue;
+        if (c->free_fn)
+            c->free_fn(c->user, s.block, c->stream);
+        else
+            cudaFreeAsync(s.block, c->stream);
+        s.block = nullptr;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    delete c;
+    return GPM_OK;
+}
+
+gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t level) {
+    if (!c) return GPM_EINVAL;
+    if (n_pairs < 1 || n_pairs > (int)c->slots.size()) return fail(c, GPM_EINVAL, "n_pairs out of range");
+    if (level < 0 || level > c->P.num_scales) return fail(c, GPM_EINVAL, "level out of range");
+    if (level == 0) {
+        if (!pairs) return fail(c, GPM_EINVAL, "pairs is NULL");
+        int smax = 0;
+        for (int l = 0; l < c->P.num_scales; ++l) smax = std::max(smax, c->P.cell_size[l]);
+        for (int i = 0; i < n_pairs; ++i) {
+            const gpm_pair& p = pairs[i];
+            if (!p.frame1 || !p.frame2) return fail(c, GPM_EINVAL, "NULL frame");
+            if (p.width < std::max(4, smax) || p.height < std::max(4, smax) || p.width > c->lim.max_width ||
+                p.height > c->lim.max_height)
+                return fail(c, GPM_EINVAL, "frame size outside [largest cell, limits]");
+            if (p.row_stride < 3 * (int64_t)p.width) return fail(c, GPM_EINVAL, "row_stride < 3 * width");
+        }
+        for (int i = 0; i < n_pairs; ++i) {
+            const gpm_pair& p = pairs[i];
+            Slot& s = c->slots[i];
+            gpm_status e = set_dims(c, s, p.width, p.height);
+            if (e) return e;
+            s.pair_id = p.pair_id;
+            s.pv.pair_id = p.pair_id;
+            launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
+                          s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
+                          const_cast<void*>(s.pv.img[1]), c->stream);
+            c->launches += 3;
+            reset_models(c, s);
+            launch_reset_labels(s.pv, c->P.eps, grid_for(c, s.n), c->stream);
+            c->launches += 1;
+            if (c->P.pm_init) {
+                PmLaunch L{};
+                L.op = PmLaunch::INIT;
+                L.pv = &s.pv;
+                L.radius = c->P.patch_radius;
+                L.storage = c->P.storage;
+                L.grid_blocks = c->nsm * 8;
+                L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
+                L.k1 = (uint32_t)(c->P.seed >> 32);
+                launch_pm(L, c->stream);
+                c->launches += 1;
+            } else {
+                build_lists(c, s);  // every pixel (nothing frozen) for the recost
+            }
+            pm_sweeps(c, s, 0);
+            s.stage = 0;
+        }
+    } else {
+        for (int i = 0; i < n_pairs; ++i)
+            if (c->slots[i].stage != 2 * level - 1) return fail(c, GPM_EINVAL, "gpm_match(l) must follow gpm_fit_planes(l)");
+        for (int i = 0; i < n_pairs; ++i) {
+            Slot& s = c->slots[i];
+            pm_sweeps(c, s, level);
+            s.stage = 2 * level;
+        }
+    }
+    return cuda_check(c, "gpm_match");
+}
+
+gpm_status gpm_fit_planes(gpm_ctx* c, int32_t n_pairs, int32_t level) {
+    if (!c) return GPM_EINVAL;
+    if (n_pairs < 1 || n_pairs > (int)c->slots.size()) return fail(c, GPM_EINVAL, "n_pairs out of range");
+    if (level < 1 || level > c->P.num_scales) return fail(c, GPM_EINVAL, "level out of range");
+    for (int i = 0; i < n_pairs; ++i)
+        if (c->slots[i].stage != 2 * (level - 1))
+            return fail(c, GPM_EINVAL, "gpm_fit_planes(l) must follow gpm_match(l-1)");
+    for (int i = 0; i < n_pairs; ++i) {
+        Slot& s = c->slots[i];
+        fit_level(c, s, level);
+        s.stage = 2 * level - 1;
+    }
+    return cuda_check(c, "gpm_fit_planes");
+}
+
+gpm_status gpm_flow_and_occlusion(gpm_ctx* c, int32_t n_pairs, float* const* flow_out, uint8_t* const* occ_out) {
+    if (!c) return GPM_EINVAL;
+    if (n_pairs < 1 || n_pairs > (int)c->slots.size()) return fail(c, GPM_EINVAL, "n_pairs out of range");
+    if (!flow_out || !occ_out) return fail(c, GPM_EINVAL, "NULL output array");
+    for (int i = 0; i < n_pairs; ++i) {
+        if (!flow_out[i] || !occ_out[i]) return fail(c, GPM_EINVAL, "NULL output buffer");
+        if (c->slots[i].stage < 0 || (c->slots[i].stage & 1))
+            return fail(c, GPM_EINVAL, "gpm_flow_and_occlusion must follow a gpm_match call");
+    }
+    const PlaneParams pp = plane_params(c->P);
+    for (int i = 0; i < n_pairs; ++i) {
+        Slot& s = c->slots[i];
+        const int gb = grid_for(c, s.n);
+        launch_fill(s.pv, pp, c->P.fill_iters, gb, Labels{}, c->stream);
+        launch_final(s.pv, pp, flow_out[i], occ_out[i], gb, c->stream);
+        c->launches += c->P.fill_iters + 1;
+    }
+    return cuda_check(c, "gpm_flow_and_occlusion");
+}
+
+gpm_status gpm_sync(gpm_ctx* c) {
+    if (!c) return GPM_EINVAL;
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, GPM_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+    return cuda_check(c, "gpm_sync");
+}
+
+static size_t state_bytes(const Slot& s, int what) {
+    const size_t n = (size_t)s.n, m = (size_t)s.m;
+    switch (what) {
+        case GPM_NNF: return 2 * n * 2 * sizeof(int32_t);
+        case GPM_COST: return 2 * n * sizeof(float);
+        case GPM_MODELS: return 2 * m * 9 * sizeof(double);
+        case GPM_MODEL_INFO: return 2 * m * kMI * sizeof(int32_t);
+        case GPM_LABELS:
+        case GPM_LEVEL_LABELS:
+        case GPM_STAGE1_LABELS: {
+            size_t a = 2 * n * (sizeof(int32_t) + sizeof(float));
+            a = (a + 7) / 8 * 8;
+            return a + 2 * n * 2 * sizeof(double);
+        }
+        case GPM_CUES: return 2 * n;
+        case GPM_FRAMES: return 2 * n * 4 * sizeof(float);
+        default: return 0;
+    }
+}
+
+size_t gpm_state_bytes(const gpm_ctx* c, int32_t pair, int32_t what) {
+    if (!c || pair < 0 || pair >= (int)c->slots.size() || c->slots[pair].n == 0) return 0;
+    return state_bytes(c->slots[pair], what);
+}
+
+gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
+    if (!c) return GPM_EINVAL;
+    if (pair < 0 || pair >= (int)c->slots.size() || !dst) return fail(c, GPM_EINVAL, "bad pair or NULL destination");
+    Slot& s = c->slots[pair];
+    if (s.n == 0) return fail(c, GPM_EINVAL, "pair has no state yet");
+    const size_t n = (size_t)s.n, m = (size_t)s.m;
+    cudaStream_t st = c->stream;
+    char* d = (char*)dst;
+    switch (what) {
+        case GPM_NNF:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(d + k * n * sizeof(int2), s.pv.nnf[k], n * sizeof(int2), cudaMemcpyDeviceToDevice, st);
+            break;
+        case GPM_COST:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(d + k * n * sizeof(float), s.pv.cost[k], n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+            break;
+        case GPM_MODELS:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(d + k * m * 9 * sizeof(double), s.pv.mh[k], m * 9 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st);
+            break;
+        case GPM_MODEL_INFO:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(d + k * m * kMI * sizeof(int), s.pv.mi[k], m * kMI * sizeof(int),
+                                cudaMemcpyDeviceToDevice, st);
+            break;
+        case GPM_LABELS:
+        case GPM_LEVEL_LABELS:
+        case GPM_STAGE1_LABELS: {
+            int* om = (int*)d;
+            float* oL = (float*)(d + 2 * n * sizeof(int));
+            size_t a = 2 * n * (sizeof(int32_t) + sizeof(float));
+            a = (a + 7) / 8 * 8;
+            double* of = (double*)(d + a);
+            for (int k = 0; k < 2; ++k) {
+                const Labels& l = what == GPM_LABELS ? s.pv.acc[k] : (what == GPM_LEVEL_LABELS ? s.pv.lvl[k] : s.pv.st1[k]);
+                launch_labels_export(l, s.n, om + k * n, oL + k * n, of + k * n * 2, st);
+                c->launches += 1;
+            }
+            break;
+        }
+        case GPM_CUES:
+            for (int k = 0; k < 2; ++k) cudaMemcpyAsync(d + k * n, s.pv.cue[k], n, cudaMemcpyDeviceToDevice, st);
+            break;
+        case GPM_FRAMES:
+            launch_frames_export(s.pv, c->P.storage, (float*)d, st);
+            c->launches += 1;
+            break;
+        default:
+            return fail(c, GPM_EINVAL, "unknown export kind");
+    }
+    return cuda_check(c, "gpm_export");
+}
+
+gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, int32_t level) {
+    if (!c) return GPM_EINVAL;
+    if (pair < 0 || pair >= (int)c->slots.size() || !src) return fail(c, GPM_EINVAL, "bad pair or NULL source");
+    if (level < 0 || level > c->P.num_scales) return fail(c, GPM_EINVAL, "level out of range");
+    Slot& s = c->slots[pair];
+    if (s.n == 0) return fail(c, GPM_EINVAL, "run gpm_match(level 0) on the pair first");
+    const size_t n = (size_t)s.n, m = (size_t)s.m;
+    cudaStream_t st = c->stream;
+    const char* d = (const char*)src;
+    switch (what) {
+        case GPM_NNF:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(s.pv.nnf[k], d + k * n * sizeof(int2), n * sizeof(int2), cudaMemcpyDeviceToDevice, st);
+            break;
+        case GPM_MODELS:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(s.pv.mh[k], d + k * m * 9 * sizeof(double), m * 9 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st);
+            launch_import_models(s.pv, s.d_geoms, c->P.num_scales, s.m, st);
+            c->launches += 1;
+            break;
+        case GPM_MODEL_INFO:
+            for (int k = 0; k < 2; ++k)
+                cudaMemcpyAsync(s.pv.mi[k], d + k * m * kMI * sizeof(int), m * kMI * sizeof(int),
+                                cudaMemcpyDeviceToDevice, st);
+            launch_import_models(s.pv, s.d_geoms, c->P.num_scales, s.m, st);
+            c->launches += 1;
+            break;
+        case GPM_LABELS: {
+            const int* im = (const int*)d;
+            const float* iL = (const float*)(d + 2 * n * sizeof(int));
+            size_t a = 2 * n * (sizeof(int32_t) + sizeof(float));
+            a = (a + 7) / 8 * 8;
+            const double* iF = (const double*)(d + a);
+            for (int k = 0; k < 2; ++k) {
+                launch_labels_import(s.pv.acc[k], s.n, im + k * n, iL + k * n, iF + k * n * 2, st);
+                c->launches += 1;
+            }
+            break;
+        }
+        case GPM_CUES:
+            for (int k = 0; k < 2; ++k) cudaMemcpyAsync(s.pv.cue[k], d + k * n, n, cudaMemcpyDeviceToDevice, st);
+            break;
+        default:
+            return fail(c, GPM_EINVAL, "unknown or export-only import kind");
+    }
+    s.stage = 2 * level;
+    return cuda_check(c, "gpm_import");
+}
+
+const char* gpm_status_string(gpm_status s) {
+    switch (s) {
+        case GPM_OK: return "GPM_OK";
+        case GPM_EINVAL: return "GPM_EINVAL";
+        case GPM_ENOMEM: return "GPM_ENOMEM";
+        case GPM_ECUDA: return "GPM_ECUDA";
+        case GPM_ETIMEOUT: return "GPM_ETIMEOUT";
+        case GPM_EBUSY: return "GPM_EBUSY";
+        case GPM_EINTERNAL: return "GPM_EINTERNAL";
+    }
+    return "unknown";
+}
+
+const char* gpm_last_error(const gpm_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+uint64_t gpm_launch_count(const gpm_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

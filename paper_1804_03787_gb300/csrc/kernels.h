@@ -1,0 +1,49 @@
+// Host-side launch descriptors of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gpm {
+
+struct PmLaunch {
+    enum Op { INIT, RECOST, SWEEP } op;
+    const PairView* pv;
+    LevelGeom geom;
+    int radius, storage, level, it, phase, nrad, grid_blocks;
+    uint32_t k0, k1;
+};
+void launch_pm(const PmLaunch& L, cudaStream_t st);
+void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
+                   double* partial, int nblk, double* gain, void* o1, void* o2, cudaStream_t st);
+void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
+
+struct PlaneParams {
+    int num_hyp, min_inliers, radius, storage;
+    float t2, eps, fb2, eta, kappa, beta, occ_thresh, scale_min, scale_max;
+    uint32_t k0, k1;
+};
+
+// RANSAC per window for both directions (blockIdx.y = direction).
+void launch_ransac(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
+                   cudaStream_t st);
+// Assignment by eq. 3-4 into `out` (which = 0 tent, 1 st1, 2 lvl); stage 1 or 2; masked by resid for stage 2.
+void launch_assign(const PairView& pv, const LevelGeom& g, int stage, int which, int write_resid,
+                   const PlaneParams& pp, int grid_blocks, cudaStream_t st);
+void launch_cues(const PairView& pv, const LevelGeom& g, int stage, int which, const PlaneParams& pp,
+                 int grid_blocks, cudaStream_t st);
+void launch_many_to_one(const PairView& pv, const PlaneParams& pp, int grid_blocks, cudaStream_t st);
+void launch_merge_update(const PairView& pv, const PlaneParams& pp, int grid_blocks, cudaStream_t st);
+void launch_fill(const PairView& pv, const PlaneParams& pp, int iters, int grid_blocks, Labels tmp, cudaStream_t st);
+void launch_reset_labels(const PairView& pv, float eps, int grid_blocks, cudaStream_t st);
+void launch_frames_export(const PairView& pv, int storage, float* dst, cudaStream_t st);
+void launch_final(const PairView& pv, const PlaneParams& pp, float* flow, uint8_t* occ, int grid_blocks,
+                  cudaStream_t st);
+// geoms: DEVICE array of nlev level geometries
+void launch_import_models(const PairView& pv, const LevelGeom* geoms, int nlev, int m, cudaStream_t st);
+void launch_labels_export(const Labels& l, int n, int* om, float* oL, double* of, cudaStream_t st);
+void launch_labels_import(const Labels& l, int n, const int* im, const float* iL, const double* iF, cudaStream_t st);
+
+}  // namespace gpm

@@ -1,0 +1,430 @@
+// Frame ingest and PatchMatch kernels (sm_103a).
+//
+// PatchMatch (Sec. 3.1; Barnes et al. 2009) with red-black scheduling: one
+// launch per half-iteration updates every pixel of one colour from the state
+// before the launch (its four neighbours all have the other colour).  One
+// warp evaluates one pixel: each lane owns ceil(T/32) taps of the (2r+1)^2
+// patch, keeps their source texels in registers for all candidates, and the
+// per-candidate cost is a butterfly shuffle sum, identical on every lane, so
+// the accept/reject decision is warp-uniform.  At levels >= 1 the patch is
+// distorted by the pixel's home-window plane (Sec. 3.3.2 with the plane
+// distortion compensation of Sec. 3.1.3): tap d samples the target frame at
+// p + v + G(s) - G(p), s = clamp(p + d).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gpm {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// ---------------------------------------------------------------- ingest
+// Deterministic FP64 sums of both frames: fixed grid, fixed tree.
+__global__ void k_frame_sums(const float* f1, const float* f2, int W, int H, int64_t stride, double* partial) {
+    __shared__ double sh[2][256];
+    double a = 0, b = 0;
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const float* r1 = f1 + (int64_t)y * stride;
+        const float* r2 = f2 + (int64_t)y * stride;
+        for (int k = threadIdx.x; k < 3 * W; k += blockDim.x) {
+            a += (double)r1[k];
+            b += (double)r2[k];
+        }
+    }
+    sh[0][threadIdx.x] = a;
+    sh[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sh[0][0];
+        partial[2 * blockIdx.x + 1] = sh[1][0];
+    }
+}
+
+__global__ void k_gain(const double* partial, int nblk, int enable, double* gain) {
+    if (threadIdx.x != 0) return;
+    double a = 0, b = 0;
+    for (int i = 0; i < nblk; ++i) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    *gain = (enable && b > 0) ? a / b : 1.0;
+}
+
+template <int ST>
+__device__ __forceinline__ void store_pix(void* base, int i, float r, float g, float b) {
+    if constexpr (ST == 0) {
+        reinterpret_cast<float4*>(base)[i] = make_float4(r, g, b, 0.f);
+    } else if constexpr (ST == 1) {
+        __half2 lo = __floats2half2_rn(r, g), hi = __floats2half2_rn(b, 0.f);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        reinterpret_cast<uint2*>(base)[i] = u;
+    } else {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(r, g), hi = __floats2bfloat162_rn(b, 0.f);
+        uint2 u;
+        u.x = *reinterpret_cast<uint32_t*>(&lo);
+        u.y = *reinterpret_cast<uint32_t*>(&hi);
+        reinterpret_cast<uint2*>(base)[i] = u;
+    }
+}
+
+template <int ST>
+__global__ void k_pack(const float* f1, const float* f2, int W, int H, int64_t stride, const double* gain, void* o1,
+                       void* o2) {
+    const double g = *gain;
+    const int n = W * H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const float* a = f1 + (int64_t)y * stride + 3 * x;
+        const float* b = f2 + (int64_t)y * stride + 3 * x;
+        store_pix<ST>(o1, i, a[0], a[1], a[2]);
+        store_pix<ST>(o2, i, (float)((double)b[0] * g), (float)((double)b[1] * g), (float)((double)b[2] * g));
+    }
+}
+
+// ---------------------------------------------------------------- patch machinery
+template <int R>
+struct Patch {
+    static constexpr int D = 2 * R + 1;
+    static constexpr int T = D * D;
+    static constexpr int NT = (T + 31) / 32;
+};
+
+// Per-lane patch state of one pixel.
+template <int R>
+struct LanePatch {
+    float4 a[Patch<R>::NT];   // source texels of the lane's taps
+    int sx[Patch<R>::NT], sy[Patch<R>::NT];
+    int dk[Patch<R>::NT][2];  // warped tap displacement: integer part
+    float df[Patch<R>::NT][2];  // and fraction in [0,1)
+    bool warped;
+};
+
+template <int R, int ST>
+__device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, int W, int H, int px, int py,
+                                           int lane) {
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        const int tt = t < Patch<R>::T ? t : 0;
+        const int dy = tt / Patch<R>::D - R, dx = tt % Patch<R>::D - R;
+        lp.sx[j] = min(max(px + dx, 0), W - 1);
+        lp.sy[j] = min(max(py + dy, 0), H - 1);
+        lp.a[j] = ldpix<ST>(src, lp.sy[j] * W + lp.sx[j]);
+    }
+    lp.warped = false;
+}
+
+// Tap displacements G(s) - G(p) for the plane m at pixel p, from the local
+// Jacobian form: with J the derivative of G at p and c = (g0, g1) / den(p),
+// G(p + d) - G(p) = J d / (1 + c . d) exactly.
+template <int R>
+__device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px, int py) {
+    const float ux = (float)(px - m.ox), uy = (float)(py - m.oy);
+    const float e = m.e0 + m.g0 * ux + m.g1 * uy;
+    const float den = 1.f + e;
+    const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
+    const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
+    // local target of p: X = u + D(u)
+    const float X = ux + (m.h2h + (m.h2l + (Sx - m.h2h * e) / den));
+    const float Y = uy + (m.h5h + (m.h5l + (Sy - m.h5h * e) / den));
+    const float j00 = (1.f + m.b0 - X * m.g0) / den, j01 = (m.h1 - X * m.g1) / den;
+    const float j10 = (m.h3 - Y * m.g0) / den, j11 = (1.f + m.b4 - Y * m.g1) / den;
+    const float c0 = m.g0 / den, c1 = m.g1 / den;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const float dx = (float)(lp.sx[j] - px), dy = (float)(lp.sy[j] - py);
+        const float q = 1.f + c0 * dx + c1 * dy;
+        const float ex = (j00 * dx + j01 * dy) / q;
+        const float ey = (j10 * dx + j11 * dy) / q;
+        const float fx = floorf(ex), fy = floorf(ey);
+        lp.dk[j][0] = (int)fx;
+        lp.dk[j][1] = (int)fy;
+        lp.df[j][0] = ex - fx;
+        lp.df[j][1] = ey - fy;
+    }
+    lp.warped = true;
+}
+
+template <int R, int ST>
+__device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
+                                            int vx, int vy, int lane) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        if (t < Patch<R>::T) {
+            float3 b;
+            if (!lp.warped) {
+                const int qx = min(max(lp.sx[j] + vx, 0), W - 1), qy = min(max(lp.sy[j] + vy, 0), H - 1);
+                const float4 c = ldpix<ST>(tgt, qy * W + qx);
+                b = make_float3(c.x, c.y, c.z);
+            } else {
+                b = bilinear<ST>(tgt, W, H, px + vx + lp.dk[j][0], lp.df[j][0], py + vy + lp.dk[j][1], lp.df[j][1]);
+            }
+            s += absdiff3(lp.a[j], b);
+        }
+    }
+    // butterfly sum: every lane ends with the same bits (IEEE addition commutes)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+    return s / (float)(3 * Patch<R>::T);
+}
+
+// Home-window plane of p at a level (residual-stage model first), or nullptr.
+__device__ __forceinline__ const Mef* home_plane(const LevelGeom& g, const Mef* mef, int x, int y) {
+    const int cx = home_index(g.gx, g.s, g.h, x), cy = home_index(g.gy, g.s, g.h, y);
+    const int cell = cy * g.gx.count + cx;
+    const Mef* m2 = mef + (g.base + cell) * 2 + 1;
+    if (m2->valid) return m2;
+    const Mef* m1 = mef + (g.base + cell) * 2;
+    if (m1->valid) return m1;
+    return nullptr;
+}
+
+// ---------------------------------------------------------------- init
+template <int R, int ST>
+__global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint32_t k1) {
+    const int dir = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int W = pv.W, H = pv.H, n = pv.n;
+    const void* src = pv.img[dir];
+    const void* tgt = pv.img[1 - dir];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int y = i / W, x = i - y * W;
+        const uint4 w = philox((uint32_t)i, 0u, stream_tag(RNG_INIT, dir, 0, 0), pv.pair_id, k0, k1);
+        const int vx = (int)(w.x % (uint32_t)W) - x, vy = (int)(w.y % (uint32_t)H) - y;
+        LanePatch<R> lp;
+        load_patch<R, ST>(lp, src, W, H, x, y, lane);
+        const float c = patch_cost<R, ST>(lp, tgt, W, H, x, y, vx, vy, lane);
+        if (lane == 0) {
+            pv.nnf[dir][i] = make_int2(vx, vy);
+            pv.cost[dir][i] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- recost (level >= 1)
+template <int R, int ST>
+__global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int level) {
+    const int dir = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int W = pv.W, H = pv.H;
+    const void* src = pv.img[dir];
+    const void* tgt = pv.img[1 - dir];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int half = pv.n;  // list capacity per colour
+    for (int col = 0; col < 2; ++col) {
+        const int cnt = pv.list_count[dir * 2 + col];
+        const int* list = pv.list[dir] + col * half;
+        for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < cnt; w += nw) {
+            const int i = list[w];
+            const int y = i / W, x = i - y * W;
+            LanePatch<R> lp;
+            load_patch<R, ST>(lp, src, W, H, x, y, lane);
+            if (level > 0) {
+                const Mef* G = home_plane(g, pv.mef[dir], x, y);
+                if (G) warp_taps<R>(lp, *G, x, y);
+            }
+            const int2 v = pv.nnf[dir][i];
+            const float c = patch_cost<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
+            if (lane == 0) pv.cost[dir][i] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- sweep
+template <int R, int ST>
+__global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
+                                                  uint32_t k0, uint32_t k1) {
+    const int dir = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int W = pv.W, H = pv.H;
+    const void* src = pv.img[dir];
+    const void* tgt = pv.img[1 - dir];
+    int2* __restrict__ nnf = pv.nnf[dir];
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int hw = (W + 1) >> 1;
+    const int total = level == 0 ? H * hw : pv.list_count[dir * 2 + phase];
+    const int* list = level == 0 ? nullptr : pv.list[dir] + phase * pv.n;
+    const int R0 = max(W, H);
+    const uint32_t tag = stream_tag(RNG_SEARCH, dir, level, 0);
+    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
+        int x, y, i;
+        if (level == 0) {
+            y = w / hw;
+            x = 2 * (w - y * hw) + ((y + phase) & 1);
+            if (x >= W) continue;
+            i = y * W + x;
+        } else {
+            i = list[w];
+            y = i / W;
+            x = i - y * W;
+        }
+        LanePatch<R> lp;
+        load_patch<R, ST>(lp, src, W, H, x, y, lane);
+        if (level > 0) {
+            const Mef* G = home_plane(g, pv.mef[dir], x, y);
+            if (G) warp_taps<R>(lp, *G, x, y);
+        }
+        int2 best = nnf[i];
+        float bc = pv.cost[dir][i];
+        // random words for the search radii, two radii per Philox call, one call per lane
+        uint4 rw = make_uint4(0, 0, 0, 0);
+        if (lane < (nrad + 1) / 2)
+            rw = philox((uint32_t)i, ((uint32_t)it << 8) | (uint32_t)lane, tag, pv.pair_id, k0, k1);
+        // propagation: left, right, up, down
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int nx = x + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+            const int ny = y + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+            if (nx < 0 || nx >= W || ny < 0 || ny >= H) continue;
+            const int2 c = nnf[ny * W + nx];
+            const int tx = x + c.x, ty = y + c.y;
+            if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
+            if (c.x == best.x && c.y == best.y) continue;
+            const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, c.x, c.y, lane);
+            if (cc < bc) {
+                bc = cc;
+                best = c;
+            }
+        }
+        // plane candidates of the windows covering p, in window order, stage 1 then 2
+        if (level > 0) {
+            int ix[3], iy[3];
+            const int nxw = covering(g.gx, g.s, g.h, x, ix), nyw = covering(g.gy, g.s, g.h, y, iy);
+            for (int a = 0; a < nyw; ++a)
+                for (int b = 0; b < nxw; ++b) {
+                    const int cell = iy[a] * g.gx.count + ix[b];
+                    for (int st = 0; st < 2; ++st) {
+                        const Mef m = pv.mef[dir][(g.base + cell) * 2 + st];
+                        if (!m.valid) continue;
+                        int kx, ky;
+                        float fx, fy;
+                        if (!mef_flow(m, (float)(x - m.ox), (float)(y - m.oy), kx, fx, ky, fy)) continue;
+                        int cx, cy;
+                        float rx, ry;
+                        round_split(kx, fx, cx, rx);
+                        round_split(ky, fy, cy, ry);
+                        const int tx = x + cx, ty = y + cy;
+                        if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
+                        if (cx == best.x && cy == best.y) continue;
+                        const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, cx, cy, lane);
+                        if (cc < bc) {
+                            bc = cc;
+                            best = make_int2(cx, cy);
+                        }
+                    }
+                }
+        }
+        // random search around the best offset after propagation, radii R0 >> k
+        const int2 v0 = best;
+        for (int k = 0; k < nrad; ++k) {
+            const int Rk = R0 >> k;
+            const uint32_t wx = __shfl_sync(FULL, (k & 1) ? rw.z : rw.x, k >> 1);
+            const uint32_t wy = __shfl_sync(FULL, (k & 1) ? rw.w : rw.y, k >> 1);
+            const int ox = (int)(wx % (uint32_t)(2 * Rk + 1)) - Rk;
+            const int oy = (int)(wy % (uint32_t)(2 * Rk + 1)) - Rk;
+            const int tx = min(max(x + v0.x + ox, 0), W - 1), ty = min(max(y + v0.y + oy, 0), H - 1);
+            const int cx = tx - x, cy = ty - y;
+            if (cx == best.x && cy == best.y) continue;
+            const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, cx, cy, lane);
+            if (cc < bc) {
+                bc = cc;
+                best = make_int2(cx, cy);
+            }
+        }
+        if (lane == 0) {
+            nnf[i] = best;
+            pv.cost[dir][i] = bc;
+        }
+    }
+}
+
+// Unfrozen pixels of each colour, for the restricted sweeps (order is free:
+// pixels of one colour are independent within a half-iteration).
+__global__ void k_build_lists(PairView pv) {
+    const int dir = blockIdx.y;
+    const int n = pv.n, W = pv.W;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        bool ok = false;
+        int col = 0;
+        if (i < n) {
+            ok = !pv.frozen[dir][i];
+            const int y = i / W, x = i - y * W;
+            col = (x + y) & 1;
+        }
+        for (int c = 0; c < 2; ++c) {
+            const unsigned mask = __ballot_sync(FULL, ok && col == c);
+            if (!mask) continue;
+            int off = 0;
+            if (lane == 0) off = atomicAdd(&pv.list_count[dir * 2 + c], __popc(mask));
+            off = __shfl_sync(FULL, off, 0);
+            if (ok && col == c) pv.list[dir][c * n + off + __popc(mask & ((1u << lane) - 1))] = i;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+template <int R, int ST>
+static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
+    const dim3 grid(L.grid_blocks, 2), block(256);
+    switch (L.op) {
+        case PmLaunch::INIT:
+            k_pm_init<R, ST><<<grid, block, 0, st>>>(*L.pv, L.k0, L.k1);
+            break;
+        case PmLaunch::RECOST:
+            k_pm_recost<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level);
+            break;
+        case PmLaunch::SWEEP:
+            k_pm_sweep<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+            break;
+    }
+}
+
+template <int ST>
+static void launch_pm_st(const PmLaunch& L, cudaStream_t st) {
+    switch (L.radius) {
+        case 1: launch_pm_r<1, ST>(L, st); break;
+        case 2: launch_pm_r<2, ST>(L, st); break;
+        case 3: launch_pm_r<3, ST>(L, st); break;
+        case 4: launch_pm_r<4, ST>(L, st); break;
+        default: break;
+    }
+}
+
+void launch_pm(const PmLaunch& L, cudaStream_t st) {
+    switch (L.storage) {
+        case 0: launch_pm_st<0>(L, st); break;
+        case 1: launch_pm_st<1>(L, st); break;
+        case 2: launch_pm_st<2>(L, st); break;
+    }
+}
+
+void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
+                   double* partial, int nblk, double* gain, void* o1, void* o2, cudaStream_t st) {
+    k_frame_sums<<<nblk, 256, 0, st>>>(f1, f2, W, H, stride, partial);
+    k_gain<<<1, 32, 0, st>>>(partial, nblk, gain_enable, gain);
+    const int blocks = 152 * 4;
+    switch (storage) {
+        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+    }
+}
+
+void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
+    k_build_lists<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+}
+
+}  // namespace gpm

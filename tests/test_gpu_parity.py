@@ -1,0 +1,349 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+the same seeded inputs.
+
+Bars (from the method's tolerances): integer NNF offsets, labels and
+occlusion bits bit-exact except where the oracle logged a near tie
+(|a - b| < 1e-5 relative at a decision) upstream; patch costs within 1e-5
+relative; homographies within 1e-6 after normalisation; plane flows within
+1e-5 px.  Lock-step tests feed the oracle's own state into the GPU (never the
+other way) so that one near tie does not cascade.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_03787_gb300 import gpm, scene
+
+from _parity import TIE, dilate, norm_h, oracle_frames, oracle_params, rel_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    gpm.load()
+    return t
+
+
+def _scene(W, H, seed, layers=2, disp=5.0):
+    return scene.make_scene(W, H, seed=seed, n_layers=layers, max_disp=disp, affine=True)
+
+
+def _ctx(torch, gp, W, H, pairs=1):
+    return gpm.Context(gp, W, H, pairs)
+
+
+def _dev(torch, s):
+    return torch.from_numpy(s.frame1).cuda(), torch.from_numpy(s.frame2).cuda()
+
+
+CASES = [(64, 48, 2, (16, 8)), (70, 45, 3, (16, 8))]
+
+
+# ---------------------------------------------------------------- ingest and init
+@pytest.mark.parametrize("W,H,r,cells", CASES)
+def test_ingest_and_init_exact(torch, W, H, r, cells):
+    s = _scene(W, H, seed=W)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=0, num_hyp=64, seed=1234567890123)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)], pair_ids=[7])
+    P = oracle_params(gp, W, H, pair_id=7)
+    frames, g = oracle_frames(P, s.frame1, s.frame2)
+    fr = ctx.export(gpm.FRAMES)
+    for d in range(2):
+        want = frames[0][d]
+        np.testing.assert_allclose(fr[d, ..., :3], want, rtol=1.2e-7, atol=1e-12)
+    nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
+    for d in range(2):
+        vx, vy, c = O.pm_init(P, frames[d][0], frames[d][1], d)
+        np.testing.assert_array_equal(nnf[d, :, 0], vx)
+        np.testing.assert_array_equal(nnf[d, :, 1], vy)
+        assert rel_close(cost[d], c).all(), np.abs(cost[d] - c).max()
+    ctx.close()
+
+
+# ---------------------------------------------------------------- level-0 PatchMatch
+def _oracle_pm(P, frames, d, level=0, mh=None, mi=None, frozen=None, state=None):
+    """Oracle sweeps half-step by half-step with the near-tie log; returns
+    (vx, vy, cost, cone) where cone holds every pixel a logged near tie may reach."""
+    W, H = P.width, P.height
+    if state is None:
+        vx, vy, c = O.pm_init(P, frames[d][0], frames[d][1], d)
+    else:
+        vx, vy, c = (a.copy() for a in state)
+    nh = 2 * P.pm_iters
+    cone = np.zeros((H, W), bool)
+    k = 0
+    for it in range(P.pm_iters):
+        for ph in range(2):
+            amb = np.full(W * H, np.inf)
+            O.pm_sweep(P, frames[d][0], frames[d][1], d, level, it, ph, mh, mi, frozen, vx, vy, c, amb)
+            cone |= dilate((amb < TIE).reshape(H, W), nh - 1 - k)
+            k += 1
+    return vx, vy, c, cone
+
+
+@pytest.mark.parametrize("W,H,r,cells", CASES)
+def test_level0_patchmatch_matches_oracle_up_to_near_ties(torch, W, H, r, cells):
+    s = _scene(W, H, seed=W + 1)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=3, num_hyp=64)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    for d in range(2):
+        vx, vy, c, cone = _oracle_pm(P, frames, d)
+        diff = ((nnf[d, :, 0] != vx) | (nnf[d, :, 1] != vy)).reshape(H, W)
+        assert not (diff & ~cone).any(), f"dir {d}: {int((diff & ~cone).sum())} unexplained NNF differences"
+        assert diff.mean() < 0.01
+        same = ~diff.reshape(-1)
+        assert rel_close(cost[d][same], c[same]).all()
+    ctx.close()
+
+
+# ---------------------------------------------------------------- one level of Algorithm 1, lock-step
+def _oracle_level(P, frames, l, vx, vy, mh, mi, acc, cue):
+    """One level of the oracle, stage by stage, with the per-pixel near-tie logs."""
+    n = P.width * P.height
+    T, S1, C, amb = [], [], [], []
+    for d in range(2):
+        O.fit_level(P, frames[d][0], frames[d][1], d, l, 1, vx[d], vy[d], None, mh[d], mi[d])
+    for d in range(2):
+        t = O.Labels.empty(n, P.eps)
+        a = np.zeros(n, np.uint8)
+        O.assign(P, frames[d][0], frames[d][1], l, 1, mh[d], mi[d], None, t, a)
+        T.append(t)
+        amb.append(a)
+    for d in range(2):
+        O.cue_counts(P, l, 1, T[d], T[1 - d], mi[d], amb[d])
+    for d in range(2):
+        O.cue_invalidate(P, l, 1, mi[d])
+    resid = []
+    for d in range(2):
+        t = O.Labels.empty(n, P.eps)
+        O.assign(P, frames[d][0], frames[d][1], l, 1, mh[d], mi[d], None, t, amb[d])
+        S1.append(t)
+        resid.append((t.m < 0).astype(np.uint8))
+    for d in range(2):
+        O.fit_level(P, frames[d][0], frames[d][1], d, l, 2, vx[d], vy[d], resid[d], mh[d], mi[d])
+    for d in range(2):
+        c = S1[d].copy()
+        O.assign(P, frames[d][0], frames[d][1], l, 2, mh[d], mi[d], resid[d], c, amb[d])
+        C.append(c)
+    for d in range(2):
+        O.cue_counts(P, l, 2, C[d], C[1 - d], mi[d], amb[d])
+    for d in range(2):
+        O.cue_invalidate(P, l, 2, mi[d])
+    for d in range(2):
+        c = S1[d].copy()
+        O.assign(P, frames[d][0], frames[d][1], l, 2, mh[d], mi[d], resid[d], c, amb[d])
+        C[d] = c
+    frozen = []
+    for d in range(2):
+        O.many_to_one(P, C[d], cue[d], amb[d])
+        O.merge(P, C[d], acc[d], amb[d])
+        f = np.zeros(n, np.uint8)
+        O.nnf_update(P, acc[d], vx[d], vy[d], f)
+        frozen.append(f)
+    return S1, C, frozen, amb
+
+
+def _models_equal(gmh, gmi, omh, omi, ids):
+    """Per model: same integer fields (ignoring the oracle-only ambiguity flag) and H within 1e-6."""
+    ok = np.ones(len(ids), bool)
+    for k, m in enumerate(ids):
+        a, b = gmi[m], omi[m]
+        fields = [O.MI_VALID, O.MI_COUNT, O.MI_NIN, O.MI_BESTK, O.MI_BESTSCORE, O.MI_NRC, O.MI_NASSIGN, O.MI_NSYM]
+        if any(a[f] != b[f] for f in fields) or (a[O.MI_FLAGS] & ~O.F_AMBIG) != (b[O.MI_FLAGS] & ~O.F_AMBIG):
+            ok[k] = False
+            continue
+        if b[O.MI_FLAGS] & O.F_FITTED:
+            if np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() > 1e-6:
+                ok[k] = False
+    return ok
+
+
+@pytest.mark.parametrize("W,H,r,cells", CASES)
+def test_fit_planes_level1_lockstep(torch, W, H, r, cells):
+    s = _scene(W, H, seed=W + 2)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=3, num_hyp=96)
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    R0 = O.run(P, s.frame1, s.frame2, stop_after=0)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    nnf0 = np.stack([np.stack([R0.vx[d], R0.vy[d]], 1) for d in range(2)]).astype(np.int32)
+    ctx.import_state(gpm.NNF, nnf0, level=0)
+    ctx.fit_planes(1)
+    gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+    gs1 = ctx.export(gpm.STAGE1_LABELS)
+    glv = ctx.export(gpm.LEVEL_LABELS)
+    gacc = ctx.export(gpm.LABELS)
+    gcue = ctx.export(gpm.CUES)
+    gnnf = ctx.export(gpm.NNF)
+    n = W * H
+    vx = [R0.vx[d].copy() for d in range(2)]
+    vy = [R0.vy[d].copy() for d in range(2)]
+    mh = [np.zeros_like(R0.mh[d]) for d in range(2)]
+    mi = [np.zeros_like(R0.mi[d]) for d in range(2)]
+    acc = [O.Labels.empty(n, P.eps) for _ in range(2)]
+    cue = [np.zeros(n, np.uint8) for _ in range(2)]
+    S1, C, frozen, amb = _oracle_level(P, frames, 1, vx, vy, mh, mi, acc, cue)
+    cb = O.cell_base(P)
+    ncell = cb[1] - cb[0]
+    gx, gy = O.grid_axis(W, cells[0]), O.grid_axis(H, cells[0])
+    for d in range(2):
+        ids1 = np.arange(ncell) * 2
+        ids2 = ids1 + 1
+        amb_cell = (mi[d][:, O.MI_FLAGS] & O.F_AMBIG) > 0
+        ok1 = _models_equal(gmh[d], gmi[d], mh[d], mi[d], ids1)
+        bad1 = ids1[~ok1]
+        # a first-stage model may differ only on a logged near tie of its RANSAC, or through the
+        # symmetry counts, which read the tentative labels of both directions
+        assert len(bad1) <= max(1, int(0.02 * ncell)), f"dir {d}: stage-1 models differ in cells {bad1 // 2}"
+        # labels: differences must sit on near-tie pixels or in windows of differing models
+        expl = amb[d].reshape(H, W).astype(bool)
+        okall = _models_equal(gmh[d], gmi[d], mh[d], mi[d], np.arange(2 * ncell))
+        for m in np.flatnonzero(~okall):
+            c = m // 2
+            x0, y0 = gx[c % len(gx)], gy[c // len(gx)]
+            expl[y0:y0 + cells[0], x0:x0 + cells[0]] = True
+        for name, g, o in (("stage-1", gs1, S1[d]), ("level", glv, C[d])):
+            diff = (g[0][d] != o.m).reshape(H, W)
+            assert not (diff & ~expl).any(), f"dir {d} {name} labels: {int((diff & ~expl).sum())} unexplained"
+            assert diff.mean() < 0.01
+            same = (~diff.reshape(-1)) & (o.m >= 0)
+            flo = np.stack([o.fx, o.fy], 1)
+            assert np.abs(g[2][d][same] - flo[same]).max(initial=0) < 1e-5
+            assert rel_close(g[1][d][same], o.L[same]).all()
+        diff = (gacc[0][d] != acc[d].m) | (gcue[d] != cue[d])
+        assert not (diff.reshape(H, W) & ~expl).any()
+        nd = ((gnnf[d, :, 0] != vx[d]) | (gnnf[d, :, 1] != vy[d])).reshape(H, W)
+        assert not (nd & ~expl).any()
+        assert gmi[d][ids2, O.MI_NIN].sum() > 0 or mi[d][ids2, O.MI_NIN].sum() == 0
+    ctx.close()
+
+
+# ---------------------------------------------------------------- restricted, plane-distorted PatchMatch
+def test_restricted_patchmatch_level1_lockstep(torch):
+    W, H, r, cells = 64, 48, 2, (16, 8)
+    s = _scene(W, H, seed=11, disp=6.0)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=2, num_hyp=96)
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    R1 = O.run(P, s.frame1, s.frame2, stop_after=1)   # oracle after level 1 (incl. its restricted PM)
+    R0 = O.run(P, s.frame1, s.frame2, stop_after=0)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    nnf0 = np.stack([np.stack([R0.vx[d], R0.vy[d]], 1) for d in range(2)]).astype(np.int32)
+    ctx.import_state(gpm.NNF, nnf0, level=0)
+    ctx.fit_planes(1)
+    gpre = ctx.export(gpm.NNF)
+    gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+    ctx.match(None, 1)
+    gnnf = ctx.export(gpm.NNF)
+    # oracle: the same level-1 fit, then its restricted sweeps with the near-tie log
+    n = W * H
+    vx = [R0.vx[d].copy() for d in range(2)]
+    vy = [R0.vy[d].copy() for d in range(2)]
+    mh = [np.zeros_like(R0.mh[d]) for d in range(2)]
+    mi = [np.zeros_like(R0.mi[d]) for d in range(2)]
+    acc = [O.Labels.empty(n, P.eps) for _ in range(2)]
+    cue = [np.zeros(n, np.uint8) for _ in range(2)]
+    S1, C, frozen, amb = _oracle_level(P, frames, 1, vx, vy, mh, mi, acc, cue)
+    for d in range(2):
+        pre = ((gpre[d, :, 0] != vx[d]) | (gpre[d, :, 1] != vy[d])).reshape(H, W)
+        okm = _models_equal(gmh[d], gmi[d], mh[d], mi[d], np.arange(len(mi[d])))
+        if pre.any() or not okm.all():
+            pytest.skip("level-1 fit diverged on a near tie; covered by the lock-step fit test")
+        cost = np.zeros(n)
+        O.pm_recost(P, frames[d][0], frames[d][1], 1, mh[d], mi[d], frozen[d], vx[d], vy[d], cost)
+        ox, oy, oc, cone = _oracle_pm(P, frames, d, level=1, mh=mh[d], mi=mi[d], frozen=frozen[d],
+                                      state=(vx[d], vy[d], cost))
+        np.testing.assert_array_equal(ox, R1.vx[d])   # the stage-by-stage oracle equals its own pipeline
+        diff = ((gnnf[d, :, 0] != ox) | (gnnf[d, :, 1] != oy)).reshape(H, W)
+        assert not (diff & ~cone).any(), int((diff & ~cone).sum())
+    ctx.close()
+
+
+# ---------------------------------------------------------------- fill and final map, lock-step
+@pytest.mark.parametrize("W,H,r,cells", CASES)
+def test_fill_and_final_lockstep(torch, W, H, r, cells):
+    s = _scene(W, H, seed=W + 3)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=2, num_hyp=64, fill_iters=5)
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    L = len(cells)
+    R = O.run(P, s.frame1, s.frame2, stop_after=L)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    n = W * H
+    ctx.import_state(gpm.NNF, np.stack([np.stack([R.vx[d], R.vy[d]], 1) for d in range(2)]).astype(np.int32), L)
+    ctx.import_state(gpm.MODELS, np.stack(R.mh), L)
+    ctx.import_state(gpm.MODEL_INFO, np.stack(R.mi), L)
+    ctx.import_state(gpm.LABELS, (np.stack([R.acc[d].m for d in range(2)]),
+                                  np.stack([R.acc[d].L for d in range(2)]).astype(np.float32),
+                                  np.stack([np.stack([R.acc[d].fx, R.acc[d].fy], 1) for d in range(2)])), L)
+    ctx.import_state(gpm.CUES, np.stack(R.cue), L)
+    flows, occs = ctx.flow_and_occlusion()
+    torch.cuda.synchronize()
+    gflow, gocc = flows[0].cpu().numpy().reshape(n, 2), occs[0].cpu().numpy().reshape(n)
+    acc = R.acc[0].copy()
+    O.fill(P, frames[0][0], frames[0][1], R.mh[0], R.mi[0], R.cue[0], acc)
+    oflow, oocc = O.final(P, frames[0][0], frames[0][1], acc, R.vx[0], R.vy[0], R.cue[0])
+    # near ties: final colour error within 1e-5 of the threshold, or fill choices within 1e-5
+    d_occ = np.flatnonzero(gocc != oocc)
+    for i in d_occ:
+        y, x = divmod(int(i), W)
+        X, Y = x + oflow[i, 0], y + oflow[i, 1]
+        if 0 <= X <= W - 1 and 0 <= Y <= H - 1:
+            smp = O.sample_bilinear(frames[0][1], X, Y)
+            dl = np.abs(frames[0][0][y, x] - smp).mean()
+            assert abs(dl - P.occ_thresh) < TIE * P.occ_thresh, (x, y, dl)
+        else:
+            pytest.fail(f"occlusion differs at out-of-frame target ({x}, {y})")
+    fd = np.hypot(*(gflow - oflow).T)
+    assert np.mean(fd > 1e-5) < 0.005, np.mean(fd > 1e-5)
+    ctx.close()
+
+
+# ---------------------------------------------------------------- whole method
+def test_tiny_config_end_to_end(torch):
+    """128x96, 2 layers, r=3, cells 32/16/8, 4 iterations, 256 hypotheses."""
+    s = scene.tiny_scene(0)
+    gp = gpm.default_params()
+    ctx = _ctx(torch, gp, 128, 96)
+    f1, f2 = _dev(torch, s)
+    flows, occs = ctx.run([(f1, f2)])
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy()
+    gocc = occs[0].cpu().numpy()
+    P = oracle_params(gp, 128, 96)
+    R = O.run(P, s.frame1, s.frame2)
+    oflow = R.flow[0].reshape(96, 128, 2)
+    oocc = R.occ[0].reshape(96, 128)
+    epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))
+    epe_o = np.hypot(*(oflow - s.flow).transpose(2, 0, 1))
+    vis = s.occ == 0
+    agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-4)
+    print(f"tiny: flow agreement {agree:.4f}, occ agreement {np.mean(gocc == oocc):.4f}, "
+          f"EPE nocc gpu {epe_g[vis].mean():.4f} oracle {epe_o[vis].mean():.4f}")
+    assert agree > 0.95
+    assert abs(epe_g[vis].mean() - epe_o[vis].mean()) < 0.01
+    ctx.close()
+
+
+def test_repeatable_bitwise(torch):
+    s = _scene(70, 45, seed=5)
+    gp = gpm.default_params(patch_radius=3, cells=(16, 8), pm_iters=2, num_hyp=64)
+    outs = []
+    for _ in range(2):
+        ctx = _ctx(torch, gp, 70, 45)
+        flows, occs = ctx.run([_dev(torch, s)])
+        outs.append((flows[0].cpu().numpy(), occs[0].cpu().numpy(), ctx.export(gpm.MODELS)))
+        ctx.close()
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
