@@ -1,0 +1,345 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 MSGPM hot path on the 1024x436 benchmark shape.
+
+One step = the whole method (ingest, level-0 PatchMatch, every level of
+Algorithm 1 with its restricted PatchMatch, fill, final flow and occlusion)
+for both directions of `--pairs` frame pairs.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank processes its own pairs (weak scaling, no data-path
+collective); value = all pairs / max-over-ranks time.  `--impl reference`
+times the FP64 CPU oracle on a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1024x436 pairs/s & warped-patch evals/s vs plain FP32; p50/p99 served latency"
+W, H = 1024, 436
+CELLS = (64, 32, 16, 8)
+RADIUS, ITERS, HYP = 4, 8, 512
+WORKLOAD = ("1024x436 benchmark-shaped plain FP32 pair (6 planar layers, homographies up to 64 px, gain "
+            "U[0.8,1.2], noise 2/255); 9x9 patches, cells 64/32/16/8, 8 PatchMatch iterations, 512 RANSAC "
+            "hypotheses per window, both directions")
+# sizes of the bounded oracle sample: a 256x218 crop holds 1/8 of the pixels
+CROP = (256, 218)
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_params():
+    import oracle as O
+    f = lambda x: float(np.float32(x))
+    return O.Params(CROP[0], CROP[1], patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, eps=f(0.06),
+                    beta=f(0.015), occ_thresh=f(0.06))
+
+
+def oracle_sample(scene_obj):
+    """One oracle run of the whole method on the 256x218 crop; returns seconds."""
+    import oracle as O
+    P = oracle_params()
+    f1 = np.ascontiguousarray(scene_obj.frame1[: CROP[1], : CROP[0]])
+    f2 = np.ascontiguousarray(scene_obj.frame2[: CROP[1], : CROP[0]])
+    t0 = time.perf_counter()
+    O.run(P, f1, f2)
+    return time.perf_counter() - t0
+
+
+def oracle_threads() -> int:
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def cpu_baseline_block(scene_obj, samples: int = 1):
+    ts = [oracle_sample(scene_obj) for _ in range(samples)]
+    t = statistics.median(ts)
+    scale = (W * H) / (CROP[0] * CROP[1])
+    return {"value": 1.0 / (t * scale), "unit": "pairs/s", "cores": oracle_threads(), "kind": "oracle",
+            "sample": f"whole method on a {CROP[0]}x{CROP[1]} crop (1/8 of the pixels) of benchmark scene 0, "
+                      f"{samples} run(s) of {t:.2f} s, scaled to a full 1024x436 pair by pixel count"}
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu_id], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline model
+def fp32_peak_tops(sm_mhz: float, nsm: int) -> float:
+    """FP32 lane-operation peak: 128 FP32 lanes per SM, one operation per lane per clock."""
+    return nsm * 128 * sm_mhz * 1e6 / 1e12
+
+
+def roofline_block(prof, evals, nsm, clocks, peaks, steps):
+    """Roofline of the kernel class with the largest share of device time."""
+    total = sum(ms for ms, _ in prof.values()) or 1.0
+    top = max(prof, key=lambda k: prof[k][0])
+    ms, launches = prof[top]
+    T = (2 * RADIUS + 1) ** 2
+    mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = fp32_peak_tops(mhz, nsm)
+    block = {"kernel": top, "share": ms / total, "launches": launches, "avg_launch_ms": ms / max(launches, 1)}
+    if top in ("pm_sweep", "pm_init", "pm_recost"):
+        # square-patch evaluation: per tap 3 channels x (subtract, |.| accumulate) = 6 FP32 operations
+        ops = evals[0] * T * 6
+        ach = ops / (ms * 1e-3) / 1e12
+        block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
+                      "units": "FP32 lane operations (6 per tap, 81 taps per evaluation)"})
+    elif top == "pm_sweep_plane":
+        # warped evaluation: per tap and channel 6 for the bilinear blend + 2 for the absolute difference
+        ops = evals[1] * T * 3 * 8
+        ach = ops / (ms * 1e-3) / 1e12
+        block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
+                      "units": "FP32 lane operations (24 per tap)"})
+    else:
+        block.update({"bound": "alu", "achieved": None, "peak": peak_ops, "unit": "TFLOP/s", "frac": None})
+    block["traffic"] = None
+    return block
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import build as ob
+    ob.build()
+    from paper_1804_03787_gb300 import scene
+    s = scene.benchmark_scene(0)
+    for _ in range(args.warmup):
+        oracle_sample(s)
+    ts = [oracle_sample(s) for _ in range(args.steps)]
+    scale = (W * H) / (CROP[0] * CROP[1])
+    step_s = sum(ts) * scale
+    value = args.steps / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": 1, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle_threads(), "kind": "oracle",
+                             "sample": f"each step: the whole method on a {CROP[0]}x{CROP[1]} crop (1/8 of the "
+                                       f"pixels) of benchmark scene 0, scaled by pixel count"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_1804_03787_gb300 import gpm, scene
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    props = torch.cuda.get_device_properties(local)
+    nsm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+
+    # inputs: seeded benchmark scenes, resident in HBM before timing
+    nscenes = 3
+    scenes = [scene.benchmark_scene(100 * rank + k) for k in range(nscenes)]
+    dev = [(torch.from_numpy(s.frame1).cuda(), torch.from_numpy(s.frame2).cuda()) for s in scenes]
+    gp = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP)
+    P = args.pairs
+    ctx = gpm.Context(gp, W, H, max_pairs=P)
+    flows = [torch.empty((H, W, 2), dtype=torch.float32, device="cuda") for _ in range(P)]
+    occs = [torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in range(P)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        batch = [dev[(k * P + j) % nscenes] for j in range(P)]
+        ctx.match(batch, 0, pair_ids=[(k * P + j) % nscenes for j in range(P)])
+        for l in range(1, len(CELLS) + 1):
+            ctx.fit_planes(l)
+            ctx.match(None, l)
+        ctx.flow_and_occlusion(flows, occs)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    gpu_id = getattr(props, "uuid", None)
+    gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else str(gpu_id or local)
+    clk = Clocks(gpu_id)
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    launches0 = ctx.launch_count()
+    clk.start()
+    times = []
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the timed interval)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clocks = clk.stop()
+    launches = ctx.launch_count() - launches0
+    prof, evals = ctx.profile_read()
+    ctx.profile_enable(False)
+    total_ms = sum(times)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pairs = args.steps * P * ws
+    value = pairs / (total_ms * 1e-3)
+    pm_ms = prof["pm_sweep"][0] + prof["pm_init"][0] + prof["pm_sweep_plane"][0] + prof["pm_recost"][0]
+    evals_per_s = (evals[0] + evals[1]) * ws / (pm_ms * 1e-3) if pm_ms > 0 else None
+
+    # end to end through the public API: pinned host frames in, flow and occlusion back to pinned host memory
+    host_in = [(s.frame1, s.frame2) for s in scenes]
+    pin_in = [(torch.from_numpy(a).pin_memory(), torch.from_numpy(b).pin_memory()) for a, b in host_in]
+    pin_flow = [torch.empty((H, W, 2), dtype=torch.float32).pin_memory() for _ in range(P)]
+    pin_occ = [torch.empty((H, W), dtype=torch.uint8).pin_memory() for _ in range(P)]
+    staged = [(torch.empty_like(dev[0][0]), torch.empty_like(dev[0][1])) for _ in range(P)]
+    e2e_times = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for j in range(P):
+            a, b = pin_in[(k * P + j) % nscenes]
+            staged[j][0].copy_(a, non_blocking=True)
+            staged[j][1].copy_(b, non_blocking=True)
+        ctx.match(staged, 0, pair_ids=[(k * P + j) % nscenes for j in range(P)])
+        for l in range(1, len(CELLS) + 1):
+            ctx.fit_planes(l)
+            ctx.match(None, l)
+        ctx.flow_and_occlusion(flows, occs)
+        for j in range(P):
+            pin_flow[j].copy_(flows[j], non_blocking=True)
+            pin_occ[j].copy_(occs[j], non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = sum(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = P * 2 * W * H * 3 * 4
+    d2h = P * (W * H * 2 * 4 + W * H)
+
+    roof = roofline_block(prof, evals, nsm, clocks, peaks, args.steps)
+    line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "pairs_per_step": P, "scenes": f"{nscenes} seeded scenes per rank, cycled",
+                       "l2": "flushed between timed steps by a 256 MiB device write", "parallelism": "replicas"},
+            "warped_patch_evals_per_s": evals_per_s,
+            "evals_per_step": (evals[0] + evals[1]) / args.steps,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "roofline": roof,
+            "e2e": {"value": args.steps * P * ws / (e2e_ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import build as ob
+        ob.build()
+        line["cpu_baseline"] = cpu_baseline_block(scenes[0])
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--pairs", type=int, default=1, help="frame pairs per step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    return run_reference(args) if args.impl == "reference" else run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

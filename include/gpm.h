@@ -195,6 +195,33 @@ gpm_status gpm_export(gpm_ctx* ctx, int32_t pair, int32_t what, void* dst_device
    the level-0 PatchMatch). */
 gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_device, int32_t level);
 
+/* ---- measurement ----
+   With profiling on, every kernel launch of the context is bracketed by CUDA
+   events on the context's stream, and the PatchMatch kernels count the
+   candidate offsets they evaluate (one evaluation = one (2r+1)^2-tap,
+   3-channel patch cost).  gpm_profile_read synchronises the stream, returns
+   per kernel class the summed device milliseconds and the launch count, and
+   the evaluation counts [level 0, levels >= 1], then clears them.  Host
+   arrays: ms[GPM_PROF_CLASSES], launches[GPM_PROF_CLASSES], evals[2]. */
+enum {
+    GPM_PROF_INGEST = 0,
+    GPM_PROF_PM_INIT = 1,
+    GPM_PROF_PM_SWEEP = 2,        /* level-0 square-patch sweeps */
+    GPM_PROF_PM_SWEEP_PLANE = 3,  /* restricted, plane-distorted sweeps */
+    GPM_PROF_PM_RECOST = 4,
+    GPM_PROF_RANSAC = 5,
+    GPM_PROF_ASSIGN = 6,
+    GPM_PROF_CUES = 7,
+    GPM_PROF_MANY_TO_ONE = 8,
+    GPM_PROF_MERGE = 9,
+    GPM_PROF_LISTS = 10,
+    GPM_PROF_FILL = 11,
+    GPM_PROF_FINAL = 12,
+    GPM_PROF_CLASSES = 13
+};
+gpm_status gpm_profile_enable(gpm_ctx* ctx, int32_t enable);
+gpm_status gpm_profile_read(gpm_ctx* ctx, double* ms, uint64_t* launches, uint64_t* evals);
+
 /* Human-readable status name and the context's last error message. */
 const char* gpm_status_string(gpm_status s);
 const char* gpm_last_error(const gpm_ctx* ctx);

@@ -65,6 +65,13 @@ enum { ORC_CUE_M2O = 1 };
 
 /* near-tie band (relative) used for the ambiguity logs */
 #define ORC_TIE_REL 1e-5
+/* a warped sample point counts as inside the frame up to this far beyond the
+   border (clamped bilinear sampling is continuous there) */
+#define ORC_FRAME_TOL 1e-3
+/* a later plane displaces the current best one only if its robust loss L is
+   lower by more than this (planes of one surface fitted in overlapping windows
+   give equal L up to rounding; the first window keeps the pixel) */
+#define ORC_L_TIE 1e-6
 
 /* ---- counter-based RNG: Philox4x32-10 (Salmon et al., SC'11) ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -258,7 +258,14 @@ static inline int map_h(const double* H, double x, double y, double* X, double* 
 }
 
 static inline int in_frame(const orc_params* P, double X, double Y) {
-    return X >= 0 && X <= P->W - 1 && Y >= 0 && Y <= P->H - 1;
+    return X >= -ORC_FRAME_TOL && X <= P->W - 1 + ORC_FRAME_TOL && Y >= -ORC_FRAME_TOL && Y <= P->H - 1 + ORC_FRAME_TOL;
+}
+
+/* near the in-frame boundary (for the ambiguity logs) */
+static inline int near_frame_edge(const orc_params* P, double X, double Y) {
+    const double t = ORC_TIE_REL;
+    return fabs(X + ORC_FRAME_TOL) < t * fmax(1, fabs(X)) || fabs(X - (P->W - 1 + ORC_FRAME_TOL)) < t * fabs(X) ||
+           fabs(Y + ORC_FRAME_TOL) < t * fmax(1, fabs(Y)) || fabs(Y - (P->H - 1 + ORC_FRAME_TOL)) < t * fabs(Y);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -457,7 +464,9 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
         for (int j = 0; j < N; ++j) {
             if (!fl[j]) continue;
             double X, Y;
-            if (!map_h(Hb, M.p[2 * j], M.p[2 * j + 1], &X, &Y) || !in_frame(P, X, Y)) continue;
+            if (!map_h(Hb, M.p[2 * j], M.p[2 * j + 1], &X, &Y)) continue;
+            if (near_frame_edge(P, X, Y)) ambig = 1;
+            if (!in_frame(P, X, Y)) continue;
             double d = delta_at(P, src, tgt, ix[j], iy[j], X, Y);
             if (d < P->eps) ++nrc;
             if (rel_gap(d, P->eps) < ORC_TIE_REL) ambig = 1;
@@ -492,7 +501,8 @@ void orc_fit_level(const orc_params* P, const double* src, const double* tgt, in
 /* colour error delta (eq. 3), robust loss L = |delta| if |delta| < eps else */
 /* eps (eq. 4); a pixel is an inlier iff |delta| < eps and is assigned the   */
 /* inlier plane with the smallest L among the overlapping windows (lowest   */
-/* window index on ties), with the homography-induced flow H p - p.          */
+/* window index on ties, L closer than ORC_L_TIE counting as a tie), with    */
+/* the homography-induced flow H p - p.                                     */
 /* ------------------------------------------------------------------------ */
 void orc_assign(const orc_params* P, const double* src, const double* tgt, int level, int stage,
                 const double* mh, const int32_t* mi, const uint8_t* mask,
@@ -517,15 +527,13 @@ void orc_assign(const orc_params* P, const double* src, const double* tgt, int l
                     const double* Hm = mh + (size_t)id * 9;
                     double X, Y;
                     if (!map_h(Hm, x, y, &X, &Y)) continue;
-                    if (fabs(X) < 1e-5 || fabs(Y) < 1e-5 || rel_gap(X, W - 1) < ORC_TIE_REL ||
-                        rel_gap(Y, H - 1) < ORC_TIE_REL)
-                        a = 1;
+                    if (near_frame_edge(P, X, Y)) a = 1;
                     if (!in_frame(P, X, Y)) continue;
                     double d = delta_at(P, src, tgt, x, y, X, Y);
                     if (rel_gap(d, P->eps) < ORC_TIE_REL) a = 1;
                     if (!(d < P->eps)) continue;
-                    if (bm >= 0 && rel_gap(d, bL) < ORC_TIE_REL) a = 1;
-                    if (d < bL) {
+                    if (bm >= 0 && fabs(d - (bL - ORC_L_TIE)) < ORC_TIE_REL * bL) a = 1;
+                    if (d < bL - ORC_L_TIE) {
                         bL = d;
                         bm = id;
                         bfx = X - x;
@@ -701,7 +709,8 @@ void orc_nnf_update(const orc_params* P, const int32_t* am, const double* afx, c
 /* Sec. 3.4.1: homography model propagation spreads the best plane (by      */
 /* colour cost) of the 4-neighbours into unfilled pixels, here as fill_iters */
 /* Jacobi iterations; a neighbour's plane is taken only if it is a colour    */
-/* inlier at the pixel (smallest L wins, lowest model id on ties).          */
+/* inlier at the pixel (smallest L wins, lowest model id on ties, L closer  */
+/* than ORC_L_TIE counting as a tie).                                        */
 /* ------------------------------------------------------------------------ */
 void orc_fill(const orc_params* P, const double* src, const double* tgt, const double* mh,
               const int32_t* mi, const uint8_t* cue, int32_t* am, double* aL, double* afx, double* afy) {
@@ -731,7 +740,7 @@ void orc_fill(const orc_params* P, const double* src, const double* tgt, const d
                     if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y) || !in_frame(P, X, Y)) continue;
                     double d = delta_at(P, src, tgt, x, y, X, Y);
                     if (!(d < P->eps)) continue;
-                    if (d < bL || (d == bL && m < bm)) {
+                    if (d < bL - ORC_L_TIE || (fabs(d - bL) <= ORC_L_TIE && m < bm)) {
                         bL = d;
                         bm = m;
                         bfx = X - x;

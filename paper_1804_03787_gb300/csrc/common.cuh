@@ -11,6 +11,14 @@
 namespace gpm {
 
 constexpr int kMI = 12;  // integer fields per model (layout of GPM_MODEL_INFO)
+// A warped sample point counts as inside the frame up to this far (px)
+// beyond the border: clamped bilinear sampling is continuous there, and
+// identity planes on the border then never split on rounding.
+constexpr float kFrameTol = 1e-3f;
+// A later plane displaces the current best one only if its robust loss is
+// lower by more than this: planes of one surface fitted in overlapping
+// windows give equal losses up to rounding, and the first window keeps them.
+constexpr float kLTie = 1e-6f;
 enum { MI_VALID = 0, MI_COUNT, MI_NIN, MI_BESTK, MI_BESTSCORE, MI_FLAGS, MI_NRC, MI_NASSIGN, MI_NSYM, MI_AMB };
 enum { F_FITTED = 1, F_REFIT = 2, F_AMBIG = 4, F_BAD_FB = 8, F_BAD_KAPPA = 16, F_BAD_GEOM = 32 };
 enum { CUE_M2O = 1 };
@@ -306,6 +314,7 @@ struct PairView {
     int* list[2];         // unfrozen pixel indices, colour 0 then colour 1
     int* list_count;      // [2 dirs][2 colours]
     unsigned long long* m2o_key[2];
+    unsigned long long* evals;  // [level 0, levels >= 1] evaluated candidates, or nullptr
 };
 
 }  // namespace gpm

@@ -32,6 +32,7 @@ struct Slot {
     int total_cells = 0, m = 0;
     double* partial = nullptr;
     double* gain = nullptr;
+    unsigned long long* d_evals = nullptr;
 };
 
 }  // namespace
@@ -49,11 +50,46 @@ struct gpm_ctx {
     std::vector<Slot> slots;
     std::string err;
     uint64_t launches = 0;
+    // measurement: CUDA events around every launch, per kernel class
+    struct ProfRec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> pool;
+    uint64_t prof_launches[GPM_PROF_CLASSES] = {};
 };
 
 namespace {
 
 const int kPartialBlocks = 128;
+
+cudaEvent_t take_event(gpm_ctx* c) {
+    if (c->pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+}
+
+// Counts `n` kernel launches of class `cls` and, with profiling on, opens an
+// event bracket on the context's stream (closed by pend).
+void pbeg(gpm_ctx* c, int cls, int n) {
+    c->launches += n;
+    if (!c->prof) return;
+    c->prof_launches[cls] += n;
+    gpm_ctx::ProfRec r{cls, take_event(c), take_event(c)};
+    cudaEventRecord(r.a, c->stream);
+    c->recs.push_back(r);
+}
+void pend(gpm_ctx* c) {
+    if (!c->prof) return;
+    cudaEventRecord(c->recs.back().b, c->stream);
+}
 
 gpm_status fail(gpm_ctx* c, gpm_status s, const std::string& msg) {
     if (c) c->err = msg;
@@ -137,7 +173,9 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, char* base, S
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
     double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
     double* gain = (double*)take(sizeof(double));
+    unsigned long long* evals = (unsigned long long*)take(2 * sizeof(unsigned long long));
     if (s) {
+        s->d_evals = evals;
         s->pv = pv;
         s->d_geoms = dg;
         s->partial = partial;
@@ -205,9 +243,10 @@ void reset_models(gpm_ctx* c, Slot& s) {
 }
 
 void build_lists(gpm_ctx* c, Slot& s) {
+    pbeg(c, GPM_PROF_LISTS, 1);
     cudaMemsetAsync(s.pv.list_count, 0, 4 * sizeof(int), c->stream);
     launch_build_lists(s.pv, grid_for(c, s.n), c->stream);
-    c->launches += 1;
+    pend(c);
 }
 
 void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
@@ -223,16 +262,18 @@ void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
     L.k1 = (uint32_t)(c->P.seed >> 32);
     if (level > 0 || !c->P.pm_init) {
         L.op = PmLaunch::RECOST;
+        pbeg(c, GPM_PROF_PM_RECOST, 1);
         launch_pm(L, c->stream);
-        c->launches += 1;
+        pend(c);
     }
     L.op = PmLaunch::SWEEP;
     for (int it = 0; it < c->P.pm_iters; ++it)
         for (int ph = 0; ph < 2; ++ph) {
             L.it = it;
             L.phase = ph;
+            pbeg(c, level == 0 ? GPM_PROF_PM_SWEEP : GPM_PROF_PM_SWEEP_PLANE, 1);
             launch_pm(L, c->stream);
-            c->launches += 1;
+            pend(c);
         }
 }
 
@@ -250,21 +291,24 @@ void fit_level(gpm_ctx* c, Slot& s, int level) {
     const int gb = grid_for(c, s.n);
     cudaStream_t st = c->stream;
     // first stage: fit, tentative assignment, cues on both directions, final assignment
-    launch_ransac(s.pv, g, level, 1, pp, st);
-    launch_assign(s.pv, g, 1, 0, 0, pp, gb, st);
-    launch_cues(s.pv, g, 1, 0, pp, gb, st);
-    launch_assign(s.pv, g, 1, 1, 1, pp, gb, st);
+    pbeg(c, GPM_PROF_RANSAC, 1), launch_ransac(s.pv, g, level, 1, pp, st), pend(c);
+    pbeg(c, GPM_PROF_ASSIGN, 1), launch_assign(s.pv, g, 1, 0, 0, pp, gb, st), pend(c);
+    pbeg(c, GPM_PROF_CUES, 3), launch_cues(s.pv, g, 1, 0, pp, gb, st), pend(c);
+    pbeg(c, GPM_PROF_ASSIGN, 1), launch_assign(s.pv, g, 1, 1, 1, pp, gb, st), pend(c);
     // second stage on the residual pixels
-    launch_ransac(s.pv, g, level, 2, pp, st);
+    pbeg(c, GPM_PROF_RANSAC, 1), launch_ransac(s.pv, g, level, 2, pp, st), pend(c);
+    pbeg(c, GPM_PROF_ASSIGN, 1);
     for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
     launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
-    launch_cues(s.pv, g, 2, 2, pp, gb, st);
+    pend(c);
+    pbeg(c, GPM_PROF_CUES, 3), launch_cues(s.pv, g, 2, 2, pp, gb, st), pend(c);
+    pbeg(c, GPM_PROF_ASSIGN, 1);
     for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
     launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
+    pend(c);
     // many-to-one, merge, NNF update, lists for the restricted sweeps
-    launch_many_to_one(s.pv, pp, gb, st);
-    launch_merge_update(s.pv, pp, gb, st);
-    c->launches += 2 + 3 + 1 + 3 + 1 + 3 + 1 + 2 + 1;
+    pbeg(c, GPM_PROF_MANY_TO_ONE, 2), launch_many_to_one(s.pv, pp, gb, st), pend(c);
+    pbeg(c, GPM_PROF_MERGE, 1), launch_merge_update(s.pv, pp, gb, st), pend(c);
     build_lists(c, s);
 }
 
@@ -364,6 +408,11 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
 gpm_status gpm_destroy(gpm_ctx* c) {
     if (!c) return GPM_EINVAL;
     cudaStreamSynchronize(c->stream);
+    for (auto& r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
     for (auto& s : c->slots) {
         if (!s.block) continue;
         if (c->free_fn)
@@ -401,13 +450,13 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
             if (e) return e;
             s.pair_id = p.pair_id;
             s.pv.pair_id = p.pair_id;
+            pbeg(c, GPM_PROF_INGEST, 4);
             launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
                           s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
                           const_cast<void*>(s.pv.img[1]), c->stream);
-            c->launches += 3;
             reset_models(c, s);
             launch_reset_labels(s.pv, c->P.eps, grid_for(c, s.n), c->stream);
-            c->launches += 1;
+            pend(c);
             if (c->P.pm_init) {
                 PmLaunch L{};
                 L.op = PmLaunch::INIT;
@@ -417,8 +466,9 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
                 L.grid_blocks = c->nsm * 8;
                 L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
                 L.k1 = (uint32_t)(c->P.seed >> 32);
+                pbeg(c, GPM_PROF_PM_INIT, 1);
                 launch_pm(L, c->stream);
-                c->launches += 1;
+                pend(c);
             } else {
                 build_lists(c, s);  // every pixel (nothing frozen) for the recost
             }
@@ -465,9 +515,12 @@ gpm_status gpm_flow_and_occlusion(gpm_ctx* c, int32_t n_pairs, float* const* flo
     for (int i = 0; i < n_pairs; ++i) {
         Slot& s = c->slots[i];
         const int gb = grid_for(c, s.n);
+        pbeg(c, GPM_PROF_FILL, c->P.fill_iters);
         launch_fill(s.pv, pp, c->P.fill_iters, gb, Labels{}, c->stream);
+        pend(c);
+        pbeg(c, GPM_PROF_FINAL, 1);
         launch_final(s.pv, pp, flow_out[i], occ_out[i], gb, c->stream);
-        c->launches += c->P.fill_iters + 1;
+        pend(c);
     }
     return cuda_check(c, "gpm_flow_and_occlusion");
 }
@@ -542,7 +595,6 @@ gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
             for (int k = 0; k < 2; ++k) {
                 const Labels& l = what == GPM_LABELS ? s.pv.acc[k] : (what == GPM_LEVEL_LABELS ? s.pv.lvl[k] : s.pv.st1[k]);
                 launch_labels_export(l, s.n, om + k * n, oL + k * n, of + k * n * 2, st);
-                c->launches += 1;
             }
             break;
         }
@@ -607,6 +659,50 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
     }
     s.stage = 2 * level;
     return cuda_check(c, "gpm_import");
+}
+
+gpm_status gpm_profile_enable(gpm_ctx* c, int32_t enable) {
+    if (!c) return GPM_EINVAL;
+    c->prof = enable != 0;
+    for (auto& s : c->slots) {
+        s.pv.evals = c->prof ? s.d_evals : nullptr;
+        if (c->prof) cudaMemsetAsync(s.d_evals, 0, 2 * sizeof(unsigned long long), c->stream);
+    }
+    return cuda_check(c, "gpm_profile_enable");
+}
+
+gpm_status gpm_profile_read(gpm_ctx* c, double* ms, uint64_t* launches, uint64_t* evals) {
+    if (!c) return GPM_EINVAL;
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(c, GPM_ECUDA, std::string("profile sync: ") + cudaGetErrorString(e));
+    double acc[GPM_PROF_CLASSES] = {};
+    for (auto& r : c->recs) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, r.a, r.b);
+        acc[r.cls] += t;
+        c->pool.push_back(r.a);
+        c->pool.push_back(r.b);
+    }
+    c->recs.clear();
+    for (int k = 0; k < GPM_PROF_CLASSES; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (launches) launches[k] = c->prof_launches[k];
+        c->prof_launches[k] = 0;
+    }
+    uint64_t ev[2] = {0, 0};
+    for (auto& s : c->slots) {
+        if (!s.d_evals) continue;
+        unsigned long long h[2] = {0, 0};
+        cudaMemcpy(h, s.d_evals, sizeof h, cudaMemcpyDeviceToHost);
+        ev[0] += h[0];
+        ev[1] += h[1];
+        cudaMemset(s.d_evals, 0, sizeof h);
+    }
+    if (evals) {
+        evals[0] = ev[0];
+        evals[1] = ev[1];
+    }
+    return cuda_check(c, "gpm_profile_read");
 }
 
 const char* gpm_status_string(gpm_status s) {

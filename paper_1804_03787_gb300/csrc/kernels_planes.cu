@@ -152,6 +152,14 @@ __device__ __forceinline__ void mat3_mul(const double* A, const double* B, doubl
         for (int j = 0; j < 3; ++j) C[i * 3 + j] = A[i * 3] * B[j] + A[i * 3 + 1] * B[3 + j] + A[i * 3 + 2] * B[6 + j];
 }
 
+// X = i + f (f in [0,1)) lies in [-kFrameTol, n - 1 + kFrameTol].
+__device__ __forceinline__ bool in_frame_tol(int i, float f, int n) {
+    if (i >= 0 && i < n - 1) return true;
+    if (i == n - 1) return f <= kFrameTol;
+    if (i == -1) return f >= 1.f - kFrameTol;
+    return false;
+}
+
 // Target sample position of pixel (px, py) under a plane: integer base and
 // fraction; false if the denominator is not positive or the point leaves
 // [0, W-1] x [0, H-1].
@@ -160,9 +168,7 @@ __device__ __forceinline__ bool plane_target(const Mef& m, int px, int py, int W
     if (!mef_flow(m, (float)(px - m.ox), (float)(py - m.oy), kx, fx, ky, fy)) return false;
     ix = px + kx;
     iy = py + ky;
-    if (ix < 0 || iy < 0 || ix > W - 1 || iy > H - 1) return false;
-    if ((ix == W - 1 && fx > 0.f) || (iy == H - 1 && fy > 0.f)) return false;
-    return true;
+    return in_frame_tol(ix, fx, W) && in_frame_tol(iy, fy, H);
 }
 
 template <int ST>
@@ -499,7 +505,7 @@ __global__ void k_assign(PairView pv, LevelGeom g, int stage, int which, int wri
                 if (!plane_target(m, x, y, W, H, ix, fx, iy, fy, kx, ky)) continue;
                 const float d = colour_delta<ST>(src, tgt, W, H, x, y, ix, fx, iy, fy);
                 if (!(d < pp.eps)) continue;
-                if (d < bL) {
+                if (d < bL - kLTie) {
                     bL = d;
                     bm = id;
                     bkx = kx;
@@ -672,7 +678,7 @@ __global__ void k_fill(PairView pv, Labels cur0, Labels cur1, Labels nxt0, Label
                 if (!plane_target(mm, x, y, W, H, ix, fx, iy, fy, kx, ky)) continue;
                 const float d = colour_delta<ST>(src, tgt, W, H, x, y, ix, fx, iy, fy);
                 if (!(d < pp.eps)) continue;
-                if (d < bL || (d == bL && m < bm)) {
+                if (d < bL - kLTie || (fabsf(d - bL) <= kLTie && m < bm)) {
                     bL = d;
                     bm = m;
                     bkx = kx;
@@ -731,7 +737,7 @@ __global__ void k_final(PairView pv, int dir, PlaneParams pp, float* flow, uint8
             fx = fy = 0.f;
         }
         bool o = !as || (pv.cue[dir][i] & CUE_M2O);
-        if (bx < 0 || by < 0 || bx > W - 1 || by > H - 1 || (bx == W - 1 && fx > 0.f) || (by == H - 1 && fy > 0.f))
+        if (!in_frame_tol(bx, fx, W) || !in_frame_tol(by, fy, H))
             o = true;
         else if (!(colour_delta<ST>(src, tgt, W, H, x, y, bx, fx, by, fy) < pp.occ_thresh))
             o = true;

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
         if (lane == 0) {
             pv.nnf[dir][i] = make_int2(vx, vy);
             pv.cost[dir][i] = c;
+            if (pv.evals) atomicAdd(&pv.evals[0], 1ull);
         }
     }
 }
@@ -236,7 +237,10 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
             }
             const int2 v = pv.nnf[dir][i];
             const float c = patch_cost<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
-            if (lane == 0) pv.cost[dir][i] = c;
+            if (lane == 0) {
+                pv.cost[dir][i] = c;
+                if (pv.evals) atomicAdd(&pv.evals[level > 0], 1ull);
+            }
         }
     }
 }
@@ -277,6 +281,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
         }
         int2 best = nnf[i];
         float bc = pv.cost[dir][i];
+        int nev = 0;
         // random words for the search radii, two radii per Philox call, one call per lane
         uint4 rw = make_uint4(0, 0, 0, 0);
         if (lane < (nrad + 1) / 2)
@@ -292,6 +297,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
             if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
             if (c.x == best.x && c.y == best.y) continue;
             const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, c.x, c.y, lane);
+            ++nev;
             if (cc < bc) {
                 bc = cc;
                 best = c;
@@ -318,6 +324,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
                         if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
                         if (cx == best.x && cy == best.y) continue;
                         const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, cx, cy, lane);
+                        ++nev;
                         if (cc < bc) {
                             bc = cc;
                             best = make_int2(cx, cy);
@@ -337,6 +344,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
             const int cx = tx - x, cy = ty - y;
             if (cx == best.x && cy == best.y) continue;
             const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, cx, cy, lane);
+            ++nev;
             if (cc < bc) {
                 bc = cc;
                 best = make_int2(cx, cy);
@@ -345,6 +353,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
         if (lane == 0) {
             nnf[i] = best;
             pv.cost[dir][i] = bc;
+            if (pv.evals) atomicAdd(&pv.evals[level > 0], (unsigned long long)nev);
         }
     }
 }

@@ -23,7 +23,10 @@ GPM_F32, GPM_F16, GPM_BF16 = 0, 1, 2
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["gpm_default_params", "gpm_create", "gpm_destroy", "gpm_required_bytes", "gpm_match",
             "gpm_fit_planes", "gpm_flow_and_occlusion", "gpm_sync", "gpm_state_bytes", "gpm_export",
-            "gpm_import", "gpm_status_string", "gpm_last_error", "gpm_launch_count"]
+            "gpm_import", "gpm_status_string", "gpm_last_error", "gpm_launch_count", "gpm_profile_enable",
+            "gpm_profile_read"]
+PROF_CLASSES = ["ingest", "pm_init", "pm_sweep", "pm_sweep_plane", "pm_recost", "ransac", "assign", "cues",
+                "many_to_one", "merge", "lists", "fill", "final"]
 
 
 class GpmError(RuntimeError):
@@ -90,6 +93,8 @@ def load(build: bool = True) -> C.CDLL:
         "gpm_status_string": (C.c_char_p, [C.c_int]),
         "gpm_last_error": (C.c_char_p, [C.c_void_p]),
         "gpm_launch_count": (C.c_uint64, [C.c_void_p]),
+        "gpm_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+        "gpm_profile_read": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_uint64), P(C.c_uint64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -202,6 +207,18 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.gpm_launch_count(self.h))
+
+    def profile_enable(self, on: bool = True):
+        self._check(self.lib.gpm_profile_enable(self.h, 1 if on else 0), "gpm_profile_enable")
+
+    def profile_read(self):
+        """{class: (ms, launches)}, (evals at level 0, evals at levels >= 1); clears the counters."""
+        k = len(PROF_CLASSES)
+        ms = (C.c_double * k)()
+        ln = (C.c_uint64 * k)()
+        ev = (C.c_uint64 * 2)()
+        self._check(self.lib.gpm_profile_read(self.h, ms, ln, ev), "gpm_profile_read")
+        return {PROF_CLASSES[i]: (ms[i], int(ln[i])) for i in range(k)}, (int(ev[0]), int(ev[1]))
 
     # ------------------------------------------------------------ state
     def export(self, what: int, pair: int = 0):

@@ -151,23 +151,43 @@ def _oracle_level(P, frames, l, vx, vy, mh, mi, acc, cue):
     return S1, C, frozen, amb
 
 
-def _models_equal(gmh, gmi, omh, omi, ids):
-    """Per model: same integer fields (ignoring the oracle-only ambiguity flag) and H within 1e-6."""
+RANSAC_FIELDS = [O.MI_COUNT, O.MI_NIN, O.MI_BESTK, O.MI_BESTSCORE, O.MI_NRC]
+CUE_FIELDS = [O.MI_VALID, O.MI_NASSIGN, O.MI_NSYM]
+
+
+def _ransac_equal(gmh, gmi, omh, omi, ids):
+    """Per model: the RANSAC outputs (support, input size, winner, refit/geometry flags, colour overlap) and
+    H within 1e-6 after normalisation."""
     ok = np.ones(len(ids), bool)
+    geo = O.F_FITTED | O.F_REFIT | O.F_BAD_GEOM
     for k, m in enumerate(ids):
         a, b = gmi[m], omi[m]
-        fields = [O.MI_VALID, O.MI_COUNT, O.MI_NIN, O.MI_BESTK, O.MI_BESTSCORE, O.MI_NRC, O.MI_NASSIGN, O.MI_NSYM]
-        if any(a[f] != b[f] for f in fields) or (a[O.MI_FLAGS] & ~O.F_AMBIG) != (b[O.MI_FLAGS] & ~O.F_AMBIG):
+        if any(a[f] != b[f] for f in RANSAC_FIELDS) or (a[O.MI_FLAGS] & geo) != (b[O.MI_FLAGS] & geo):
             ok[k] = False
-            continue
-        if b[O.MI_FLAGS] & O.F_FITTED:
-            if np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() > 1e-6:
-                ok[k] = False
+        elif b[O.MI_FLAGS] & O.F_FITTED and np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() > 1e-6:
+            ok[k] = False
     return ok
+
+
+def _cues_equal(gmi, omi, ids):
+    return np.array([all(gmi[m][f] == omi[m][f] for f in CUE_FIELDS) for m in ids])
+
+
+def _window_box(P, cells, c, margin):
+    gx, gy = O.grid_axis(P.width, cells[0]), O.grid_axis(P.height, cells[0])
+    x0, y0 = gx[c % len(gx)], gy[c // len(gx)]
+    return slice(max(0, y0 - margin), y0 + cells[0] + margin), slice(max(0, x0 - margin), x0 + cells[0] + margin)
 
 
 @pytest.mark.parametrize("W,H,r,cells", CASES)
 def test_fit_planes_level1_lockstep(torch, W, H, r, cells):
+    """One level of Algorithm 1 from the oracle's level-0 NNF.
+
+    RANSAC outputs must match for every window whose fit the oracle did not
+    flag as a near tie.  Cue counts (pixels assigned / symmetric) read the
+    tentative labels of both directions: they may differ only in windows that
+    hold a pixel with a logged near tie (within the motion margin), and labels
+    only on such pixels or in windows whose model differs."""
     s = _scene(W, H, seed=W + 2)
     gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=3, num_hyp=96)
     P = oracle_params(gp, W, H)
@@ -192,29 +212,34 @@ def test_fit_planes_level1_lockstep(torch, W, H, r, cells):
     acc = [O.Labels.empty(n, P.eps) for _ in range(2)]
     cue = [np.zeros(n, np.uint8) for _ in range(2)]
     S1, C, frozen, amb = _oracle_level(P, frames, 1, vx, vy, mh, mi, acc, cue)
-    cb = O.cell_base(P)
-    ncell = cb[1] - cb[0]
-    gx, gy = O.grid_axis(W, cells[0]), O.grid_axis(H, cells[0])
+    ncell = int(O.cell_base(P)[1])
+    margin = 8   # motion bound of the scene plus rounding
+    amb_any = (amb[0] | amb[1]).reshape(H, W).astype(bool)
+    first = np.arange(ncell) * 2
     for d in range(2):
-        ids1 = np.arange(ncell) * 2
-        ids2 = ids1 + 1
-        amb_cell = (mi[d][:, O.MI_FLAGS] & O.F_AMBIG) > 0
-        ok1 = _models_equal(gmh[d], gmi[d], mh[d], mi[d], ids1)
-        bad1 = ids1[~ok1]
-        # a first-stage model may differ only on a logged near tie of its RANSAC, or through the
-        # symmetry counts, which read the tentative labels of both directions
-        assert len(bad1) <= max(1, int(0.02 * ncell)), f"dir {d}: stage-1 models differ in cells {bad1 // 2}"
-        # labels: differences must sit on near-tie pixels or in windows of differing models
+        ids = np.arange(2 * ncell)
+        okr = _ransac_equal(gmh[d], gmi[d], mh[d], mi[d], ids)
+        oracle_tie = (mi[d][ids, O.MI_FLAGS] & O.F_AMBIG) > 0
+        # stage-1 fits see identical inputs: only oracle-flagged near ties may differ
+        bad1 = first[~okr[first] & ~oracle_tie[first]]
+        assert len(bad1) == 0, f"dir {d}: stage-1 RANSAC differs in windows {bad1 // 2}"
+        # cue counts: explained by a logged near tie near the window
+        okc = _cues_equal(gmi[d], mi[d], ids)
+        expl_w = np.zeros(2 * ncell, bool)
+        for m in ids:
+            ys, xs = _window_box(P, cells, m // 2, margin)
+            expl_w[m] = amb_any[ys, xs].any() or oracle_tie[m]
+        bad_c = ids[~okc & ~expl_w & okr]
+        assert len(bad_c) == 0, f"dir {d}: cue counts differ without a near tie in models {bad_c}"
+        # labels: differences on near-tie pixels or inside windows whose model differs
         expl = amb[d].reshape(H, W).astype(bool)
-        okall = _models_equal(gmh[d], gmi[d], mh[d], mi[d], np.arange(2 * ncell))
-        for m in np.flatnonzero(~okall):
-            c = m // 2
-            x0, y0 = gx[c % len(gx)], gy[c // len(gx)]
-            expl[y0:y0 + cells[0], x0:x0 + cells[0]] = True
+        for m in ids[~(okr & okc)]:
+            ys, xs = _window_box(P, cells, m // 2, 0)
+            expl[ys, xs] = True
         for name, g, o in (("stage-1", gs1, S1[d]), ("level", glv, C[d])):
             diff = (g[0][d] != o.m).reshape(H, W)
             assert not (diff & ~expl).any(), f"dir {d} {name} labels: {int((diff & ~expl).sum())} unexplained"
-            assert diff.mean() < 0.01
+            assert diff.mean() < 0.05
             same = (~diff.reshape(-1)) & (o.m >= 0)
             flo = np.stack([o.fx, o.fy], 1)
             assert np.abs(g[2][d][same] - flo[same]).max(initial=0) < 1e-5
@@ -223,7 +248,6 @@ def test_fit_planes_level1_lockstep(torch, W, H, r, cells):
         assert not (diff.reshape(H, W) & ~expl).any()
         nd = ((gnnf[d, :, 0] != vx[d]) | (gnnf[d, :, 1] != vy[d])).reshape(H, W)
         assert not (nd & ~expl).any()
-        assert gmi[d][ids2, O.MI_NIN].sum() > 0 or mi[d][ids2, O.MI_NIN].sum() == 0
     ctx.close()
 
 
@@ -256,7 +280,8 @@ def test_restricted_patchmatch_level1_lockstep(torch):
     S1, C, frozen, amb = _oracle_level(P, frames, 1, vx, vy, mh, mi, acc, cue)
     for d in range(2):
         pre = ((gpre[d, :, 0] != vx[d]) | (gpre[d, :, 1] != vy[d])).reshape(H, W)
-        okm = _models_equal(gmh[d], gmi[d], mh[d], mi[d], np.arange(len(mi[d])))
+        ids = np.arange(len(mi[d]))
+        okm = _ransac_equal(gmh[d], gmi[d], mh[d], mi[d], ids) & _cues_equal(gmi[d], mi[d], ids)
         if pre.any() or not okm.all():
             pytest.skip("level-1 fit diverged on a near tie; covered by the lock-step fit test")
         cost = np.zeros(n)
