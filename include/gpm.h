@@ -175,8 +175,9 @@ gpm_status gpm_sync(gpm_ctx* ctx);
      GPM_CUES       uint8  [2][n]      bit 0 = many-to-one occlusion cue
      GPM_FRAMES     float  [2][n][4]   ingested frames as FP32 RGBX (export only)
    Import accepts GPM_NNF, GPM_MODELS (+ valid bits from GPM_MODEL_INFO when
-   imported right after), GPM_LABELS and GPM_CUES; it sets the stage order so
-   that the next call may follow the imported state. */
+   imported right after), GPM_LABELS (also sets the frozen pixels: those with
+   a plane) and GPM_CUES; it sets the stage order so that the next call may
+   follow the imported state. */
 enum {
     GPM_NNF = 0,
     GPM_COST = 1,
@@ -191,9 +192,10 @@ enum {
 /* Bytes of one export of `what` for pair `pair` (0 if unknown). */
 size_t gpm_state_bytes(const gpm_ctx* ctx, int32_t pair, int32_t what);
 gpm_status gpm_export(gpm_ctx* ctx, int32_t pair, int32_t what, void* dst_device);
-/* level: the last completed level the imported state belongs to (0 = after
-   the level-0 PatchMatch). */
-gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_device, int32_t level);
+/* stage: where in the stage order the imported state belongs: 2l = after
+   gpm_match(l) (0 = after the level-0 PatchMatch), 2l - 1 = after
+   gpm_fit_planes(l). */
+gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_device, int32_t stage);
 
 /* ---- measurement ----
    With profiling on, every kernel launch of the context is bracketed by CUDA

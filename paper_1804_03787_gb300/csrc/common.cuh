@@ -72,6 +72,16 @@ __device__ __forceinline__ float4 ldpix<2>(const void* base, int i) {
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// Bilinear blend of the four texels around a point with fractions (fx, fy).
+__device__ __forceinline__ float3 blend4(float4 a, float4 b, float4 c, float4 d, float fx, float fy) {
+    const float gx = 1.f - fx, gy = 1.f - fy;
+    float3 o;
+    o.x = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
+    o.y = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
+    o.z = gy * (gx * a.z + fx * b.z) + fy * (gx * c.z + fx * d.z);
+    return o;
+}
+
 // Bilinear sample at X = ix + fx, Y = iy + fy (fx, fy in [0,1)), the point
 // first clamped to [0, W-1] x [0, H-1].
 template <int ST>
@@ -93,12 +103,7 @@ __device__ __forceinline__ float3 bilinear(const void* img, int W, int H, int ix
     const int ix1 = min(ix + 1, W - 1), iy1 = min(iy + 1, H - 1);
     const float4 a = ldpix<ST>(img, iy * W + ix), b = ldpix<ST>(img, iy * W + ix1);
     const float4 c = ldpix<ST>(img, iy1 * W + ix), d = ldpix<ST>(img, iy1 * W + ix1);
-    const float gx = 1.f - fx, gy = 1.f - fy;
-    float3 o;
-    o.x = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
-    o.y = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
-    o.z = gy * (gx * a.z + fx * b.z) + fy * (gx * c.z + fx * d.z);
-    return o;
+    return blend4(a, b, c, d, fx, fy);
 }
 
 __device__ __forceinline__ float absdiff3(float4 a, float3 b) {

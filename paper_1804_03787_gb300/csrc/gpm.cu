@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -45,6 +46,7 @@ struct gpm_ctx {
     void* user = nullptr;
     cudaStream_t stream = nullptr;
     int nsm = 152;
+    int pm_batch = 1;  // PatchMatch candidates per warp batch (tuning: GPM_PM_BATCH = 1, 2 or 4)
     int max_n = 0, max_models = 0;
     size_t slot_bytes = 0;
     std::vector<Slot> slots;
@@ -258,6 +260,7 @@ void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
     L.level = level;
     L.nrad = num_radii(s.W, s.H);
     L.grid_blocks = c->nsm * 8;
+    L.batch = c->pm_batch;
     L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
     L.k1 = (uint32_t)(c->P.seed >> 32);
     if (level > 0 || !c->P.pm_init) {
@@ -377,6 +380,10 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
         cudaGetLastError();
         delete c;
         return GPM_ECUDA;
+    }
+    if (const char* e = std::getenv("GPM_PM_BATCH")) {
+        const int b = std::atoi(e);
+        if (b == 1 || b == 2 || b == 4) c->pm_batch = b;
     }
     c->max_n = limits->max_width * limits->max_height;
     c->max_models = std::max(2, 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr));
@@ -611,10 +618,10 @@ gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
     return cuda_check(c, "gpm_export");
 }
 
-gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, int32_t level) {
+gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, int32_t stage) {
     if (!c) return GPM_EINVAL;
     if (pair < 0 || pair >= (int)c->slots.size() || !src) return fail(c, GPM_EINVAL, "bad pair or NULL source");
-    if (level < 0 || level > c->P.num_scales) return fail(c, GPM_EINVAL, "level out of range");
+    if (stage < 0 || stage > 2 * c->P.num_scales) return fail(c, GPM_EINVAL, "stage out of range");
     Slot& s = c->slots[pair];
     if (s.n == 0) return fail(c, GPM_EINVAL, "run gpm_match(level 0) on the pair first");
     const size_t n = (size_t)s.n, m = (size_t)s.m;
@@ -649,6 +656,10 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
                 launch_labels_import(s.pv.acc[k], s.n, im + k * n, iL + k * n, iF + k * n * 2, st);
                 c->launches += 1;
             }
+            // frozen pixels and the restricted PatchMatch lists follow the accumulated map
+            launch_frozen_from_labels(s.pv, grid_for(c, s.n), st);
+            c->launches += 1;
+            build_lists(c, s);
             break;
         }
         case GPM_CUES:
@@ -657,7 +668,7 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
         default:
             return fail(c, GPM_EINVAL, "unknown or export-only import kind");
     }
-    s.stage = 2 * level;
+    s.stage = stage;
     return cuda_check(c, "gpm_import");
 }
 

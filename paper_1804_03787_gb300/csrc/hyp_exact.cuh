@@ -1,0 +1,162 @@
+// RANSAC hypotheses without double precision.
+//
+// GB300 runs FP64 at a small fraction of its FP32 rate, and a 4-point
+// homography in FP64 was the bottleneck of the per-window fit.  Here the
+// projective-basis solution H ~ B adj(A) (see minimal_h in
+// kernels_planes.cu) is formed exactly in 128-bit integers -- window-local
+// coordinates keep every entry below 2^78 -- and the FP32 evaluation form is
+// derived from exact integer numerators with one rounding each; the
+// translation, which needs ~1e-7 px absolute accuracy on flows of hundreds of
+// pixels, is split into hi + lo with an exact integer remainder.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace gpm {
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+__host__ __device__ __forceinline__ int clz64(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __clzll((long long)v);
+#else
+    return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
+__host__ __device__ __forceinline__ float u64_to_float_rn(uint64_t v) {
+#ifdef __CUDA_ARCH__
+    return __ull2float_rn(v);
+#else
+    return (float)v;
+#endif
+}
+
+// Nearest float to a 128-bit integer (sticky bit keeps the rounding exact).
+__host__ __device__ inline float i128_to_float(i128 x) {
+    if (x == 0) return 0.f;
+    const bool neg = x < 0;
+    u128 u = neg ? (u128)0 - (u128)x : (u128)x;
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    float f;
+    if (hi == 0) {
+        f = u64_to_float_rn(lo);
+    } else {
+        const int msb = 127 - clz64(hi);           // >= 64
+        const int sh = msb - 63;                   // bring the top 64 bits down
+        const u128 mask = (((u128)1) << sh) - 1;
+        uint64_t top = (uint64_t)(u >> sh);
+        if ((u & mask) != 0) top |= 1;             // sticky
+        f = u64_to_float_rn(top);
+#ifdef __CUDA_ARCH__
+        f = __fmul_rn(f, __int_as_float((127 + sh) << 23));
+#else
+        f = f * __builtin_ldexpf(1.f, sh);
+#endif
+    }
+    return neg ? -f : f;
+}
+
+// 4-point homography, exact: H = B adj(A) with the projective bases of the
+// source points (A) and target points (B); window-local integer coordinates
+// (|source| <= 32, |target| <= 2080).
+__host__ __device__ inline void minimal_h_exact(const int* px, const int* py, const int* qx, const int* qy,
+                                                i128* H) {
+    int A[9];
+    {
+        const int x1 = px[0], x2 = px[1], x3 = px[2], y1 = py[0], y2 = py[1], y3 = py[2];
+        const int l0 = (y2 - y3) * px[3] + (x3 - x2) * py[3] + (x2 * y3 - x3 * y2);
+        const int l1 = (y3 - y1) * px[3] + (x1 - x3) * py[3] + (x3 * y1 - x1 * y3);
+        const int l2 = (y1 - y2) * px[3] + (x2 - x1) * py[3] + (x1 * y2 - x2 * y1);
+        A[0] = l0 * x1; A[1] = l1 * x2; A[2] = l2 * x3;
+        A[3] = l0 * y1; A[4] = l1 * y2; A[5] = l2 * y3;
+        A[6] = l0;      A[7] = l1;      A[8] = l2;
+    }
+    int64_t mu[3];
+    {
+        const int64_t x1 = qx[0], x2 = qx[1], x3 = qx[2], y1 = qy[0], y2 = qy[1], y3 = qy[2];
+        mu[0] = (y2 - y3) * qx[3] + (x3 - x2) * qy[3] + (x2 * y3 - x3 * y2);
+        mu[1] = (y3 - y1) * qx[3] + (x1 - x3) * qy[3] + (x3 * y1 - x1 * y3);
+        mu[2] = (y1 - y2) * qx[3] + (x2 - x1) * qy[3] + (x1 * y2 - x2 * y1);
+    }
+    int64_t adj[9];
+    adj[0] = (int64_t)A[4] * A[8] - (int64_t)A[5] * A[7];
+    adj[1] = (int64_t)A[2] * A[7] - (int64_t)A[1] * A[8];
+    adj[2] = (int64_t)A[1] * A[5] - (int64_t)A[2] * A[4];
+    adj[3] = (int64_t)A[5] * A[6] - (int64_t)A[3] * A[8];
+    adj[4] = (int64_t)A[0] * A[8] - (int64_t)A[2] * A[6];
+    adj[5] = (int64_t)A[2] * A[3] - (int64_t)A[0] * A[5];
+    adj[6] = (int64_t)A[3] * A[7] - (int64_t)A[4] * A[6];
+    adj[7] = (int64_t)A[1] * A[6] - (int64_t)A[0] * A[7];
+    adj[8] = (int64_t)A[0] * A[4] - (int64_t)A[1] * A[3];
+    const int64_t B[9] = {mu[0] * qx[0], mu[1] * qx[1], mu[2] * qx[2], mu[0] * qy[0], mu[1] * qy[1],
+                          mu[2] * qy[2], mu[0], mu[1], mu[2]};
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            H[r * 3 + c] = (i128)B[r * 3] * adj[c] + (i128)B[r * 3 + 1] * adj[3 + c] + (i128)B[r * 3 + 2] * adj[6 + c];
+}
+
+// num / den (den > 0) as hi + lo floats: hi the rounded quotient, lo the
+// quotient of the exact integer remainder.
+__host__ __device__ inline void split_ratio(i128 num, i128 den, float fden, float& hi, float& lo) {
+    hi = i128_to_float(num) / fden;
+    lo = 0.f;
+    const float a = hi < 0 ? -hi : hi;
+    if (!(a >= 9.5367431640625e-07f && a < 1048576.f)) return;  // 2^-20 <= |hi| < 2^20, else hi alone
+    int e;
+#ifdef __CUDA_ARCH__
+    const float mant = frexpf(hi, &e);
+#else
+    const float mant = __builtin_frexpf(hi, &e);
+#endif
+    const int m = (int)(mant * 16777216.f);  // hi = m * 2^(e - 24), exactly
+    const int sh = 24 - e;                   // in [4, 44]
+    const i128 R = num * ((i128)1 << sh) - (i128)m * den;
+#ifdef __CUDA_ARCH__
+    lo = __fmul_rn(i128_to_float(R) / fden, __int_as_float((127 - sh) << 23));
+#else
+    lo = (i128_to_float(R) / fden) * __builtin_ldexpf(1.f, -sh);
+#endif
+}
+
+// Evaluation form (origin 0) of the exact homography; false if its
+// denominator vanishes at the window centre.
+__host__ __device__ inline bool make_mef_exact(const i128* Hin, Mef& m) {
+    i128 H[9];
+    i128 dc2 = 2 * Hin[8] - (Hin[6] + Hin[7]);  // twice the denominator at the centre (-0.5, -0.5)
+    if (dc2 == 0) return false;
+    const bool flip = dc2 < 0;
+    for (int k = 0; k < 9; ++k) H[k] = flip ? -Hin[k] : Hin[k];
+    if (flip) dc2 = -dc2;
+    const float fd = i128_to_float(dc2);
+    m.b0 = i128_to_float(2 * H[0] - dc2) / fd;
+    m.h1 = i128_to_float(2 * H[1]) / fd;
+    split_ratio(2 * H[2], dc2, fd, m.h2h, m.h2l);
+    m.h3 = i128_to_float(2 * H[3]) / fd;
+    m.b4 = i128_to_float(2 * H[4] - dc2) / fd;
+    split_ratio(2 * H[5], dc2, fd, m.h5h, m.h5l);
+    m.g0 = i128_to_float(2 * H[6]) / fd;
+    m.g1 = i128_to_float(2 * H[7]) / fd;
+    m.e0 = i128_to_float(2 * H[8] - dc2) / fd;
+    m.pad0 = 0.f;
+    m.ox = 0;
+    m.oy = 0;
+    m.valid = 0;
+    m.pad1 = 0;
+    return true;
+}
+
+// The exact homography as doubles (unnormalised).
+__host__ __device__ inline void exact_to_double(const i128* H, double* D) {
+    for (int k = 0; k < 9; ++k) {
+        const bool neg = H[k] < 0;
+        const u128 u = neg ? (u128)0 - (u128)H[k] : (u128)H[k];
+        const double v = (double)(uint64_t)(u >> 64) * 18446744073709551616.0 + (double)(uint64_t)u;
+        D[k] = neg ? -v : v;
+    }
+}
+
+}  // namespace gpm

@@ -13,6 +13,7 @@ struct PmLaunch {
     const PairView* pv;
     LevelGeom geom;
     int radius, storage, level, it, phase, nrad, grid_blocks;
+    int batch;  // candidates evaluated together per warp (1, 2 or 4)
     uint32_t k0, k1;
 };
 void launch_pm(const PmLaunch& L, cudaStream_t st);
@@ -38,6 +39,7 @@ void launch_many_to_one(const PairView& pv, const PlaneParams& pp, int grid_bloc
 void launch_merge_update(const PairView& pv, const PlaneParams& pp, int grid_blocks, cudaStream_t st);
 void launch_fill(const PairView& pv, const PlaneParams& pp, int iters, int grid_blocks, Labels tmp, cudaStream_t st);
 void launch_reset_labels(const PairView& pv, float eps, int grid_blocks, cudaStream_t st);
+void launch_frozen_from_labels(const PairView& pv, int grid_blocks, cudaStream_t st);
 void launch_frames_export(const PairView& pv, int storage, float* dst, cudaStream_t st);
 void launch_final(const PairView& pv, const PlaneParams& pp, float* flow, uint8_t* occ, int grid_blocks,
                   cudaStream_t st);

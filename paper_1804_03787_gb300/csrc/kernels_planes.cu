@@ -4,114 +4,38 @@
 #include <float.h>
 
 #include "common.cuh"
+#include "hyp_exact.cuh"
 #include "kernels.h"
 
 namespace gpm {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-// ---------------------------------------------------------------- block reductions
-template <int NT>
-__device__ __forceinline__ double block_sum(double v, double* red) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0;
-    for (int w = 0; w < NT / 32; ++w) t += red[w];  // fixed order: same bits on every thread
-    return t;
-}
-template <int NT>
-__device__ __forceinline__ int block_count(int v, int* red) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    int t = 0;
-    for (int w = 0; w < NT / 32; ++w) t += red[w];
-    return t;
-}
-
 // ---------------------------------------------------------------- 4-point homography
-// Exact projective basis construction: with P = [p1 p2 p3] (homogeneous
-// columns) and lambda = adj(P) p4, A = P diag(lambda) maps the projective
-// basis e1, e2, e3, (1,1,1) onto p1..p4 up to scale; likewise B for the
-// targets, and H ~ B adj(A).  Coordinates are window-local integers, so all
-// of it up to adj(A) and B is exact integer arithmetic; only the final
-// product is rounded (FP64).  Sign and scale are fixed later.
-__device__ __forceinline__ void minimal_h(const int* px, const int* py, const int* qx, const int* qy, double* H) {
-    long long aP[9], aQ[9];
-    {
-        const long long x1 = px[0], x2 = px[1], x3 = px[2], y1 = py[0], y2 = py[1], y3 = py[2];
-        aP[0] = y2 - y3; aP[1] = x3 - x2; aP[2] = x2 * y3 - x3 * y2;
-        aP[3] = y3 - y1; aP[4] = x1 - x3; aP[5] = x3 * y1 - x1 * y3;
-        aP[6] = y1 - y2; aP[7] = x2 - x1; aP[8] = x1 * y2 - x2 * y1;
-    }
-    {
-        const long long x1 = qx[0], x2 = qx[1], x3 = qx[2], y1 = qy[0], y2 = qy[1], y3 = qy[2];
-        aQ[0] = y2 - y3; aQ[1] = x3 - x2; aQ[2] = x2 * y3 - x3 * y2;
-        aQ[3] = y3 - y1; aQ[4] = x1 - x3; aQ[5] = x3 * y1 - x1 * y3;
-        aQ[6] = y1 - y2; aQ[7] = x2 - x1; aQ[8] = x1 * y2 - x2 * y1;
-    }
-    long long l[3], mu[3];
-    for (int i = 0; i < 3; ++i) {
-        l[i] = aP[3 * i] * px[3] + aP[3 * i + 1] * py[3] + aP[3 * i + 2];
-        mu[i] = aQ[3 * i] * qx[3] + aQ[3 * i + 1] * qy[3] + aQ[3 * i + 2];
-    }
-    long long A[9];
-    for (int c = 0; c < 3; ++c) {
-        A[0 * 3 + c] = l[c] * px[c];
-        A[1 * 3 + c] = l[c] * py[c];
-        A[2 * 3 + c] = l[c];
-    }
-    long long adjA[9];
-    adjA[0] = A[4] * A[8] - A[5] * A[7];
-    adjA[1] = A[2] * A[7] - A[1] * A[8];
-    adjA[2] = A[1] * A[5] - A[2] * A[4];
-    adjA[3] = A[5] * A[6] - A[3] * A[8];
-    adjA[4] = A[0] * A[8] - A[2] * A[6];
-    adjA[5] = A[2] * A[3] - A[0] * A[5];
-    adjA[6] = A[3] * A[7] - A[4] * A[6];
-    adjA[7] = A[1] * A[6] - A[0] * A[7];
-    adjA[8] = A[0] * A[4] - A[1] * A[3];
-    double B[9], dA[9];
-    for (int c = 0; c < 3; ++c) {
-        B[0 * 3 + c] = (double)(mu[c] * qx[c]);
-        B[1 * 3 + c] = (double)(mu[c] * qy[c]);
-        B[2 * 3 + c] = (double)mu[c];
-    }
-    for (int k = 0; k < 9; ++k) dA[k] = (double)adjA[k];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-            H[r * 3 + c] = fma(B[r * 3], dA[c], fma(B[r * 3 + 1], dA[3 + c], B[r * 3 + 2] * dA[6 + c]));
-}
-
+// Exact projective basis construction (hyp_exact.cuh): with P = [p1 p2 p3]
+// (homogeneous columns) and lambda = adj(P) p4, A = P diag(lambda) maps the
+// projective basis e1, e2, e3, (1,1,1) onto p1..p4 up to scale; likewise B
+// for the targets, and H ~ B adj(A).
 __device__ __forceinline__ bool collinear3(int ax, int ay, int bx, int by, int cx, int cy) {
     return (long long)(bx - ax) * (cy - ay) - (long long)(by - ay) * (cx - ax) == 0;
 }
 
 // Smallest-eigenvalue eigenvector of a symmetric positive semi-definite 9x9
-// matrix by inverse iteration on M + sigma I (one Cholesky factorisation,
-// then repeated triangular solves), started from x.
-__device__ void min_eigvec_inverse_iteration(const double* M, double* x) {
+// matrix M (shared memory, overwritten by its Cholesky factor) by inverse
+// iteration on M + sigma I, started from x.
+__device__ void min_eigvec_inverse_iteration(double* M, double* x) {
     double tr = 0;
     for (int i = 0; i < 9; ++i) tr += M[i * 9 + i];
     const double sigma = 1e-13 * tr + 1e-300;
-    double L[81];
-    for (int i = 0; i < 81; ++i) L[i] = 0;
-    for (int j = 0; j < 9; ++j) {
+    for (int j = 0; j < 9; ++j) {  // in-place Cholesky, lower triangle
         double d = M[j * 9 + j] + sigma;
-        for (int k = 0; k < j; ++k) d -= L[j * 9 + k] * L[j * 9 + k];
+        for (int k = 0; k < j; ++k) d -= M[j * 9 + k] * M[j * 9 + k];
         d = d > 0 ? sqrt(d) : 1e-150;
-        L[j * 9 + j] = d;
+        M[j * 9 + j] = d;
         for (int i = j + 1; i < 9; ++i) {
-            double s = M[i * 9 + j];
-            for (int k = 0; k < j; ++k) s -= L[i * 9 + k] * L[j * 9 + k];
-            L[i * 9 + j] = s / d;
+            double t = M[i * 9 + j];
+            for (int k = 0; k < j; ++k) t -= M[i * 9 + k] * M[j * 9 + k];
+            M[i * 9 + j] = t / d;
         }
     }
     double nx = 0;
@@ -121,14 +45,14 @@ __device__ void min_eigvec_inverse_iteration(const double* M, double* x) {
     for (int it = 0; it < 60; ++it) {
         double y[9];
         for (int i = 0; i < 9; ++i) {  // L y = x
-            double s = x[i];
-            for (int k = 0; k < i; ++k) s -= L[i * 9 + k] * y[k];
-            y[i] = s / L[i * 9 + i];
+            double t = x[i];
+            for (int k = 0; k < i; ++k) t -= M[i * 9 + k] * y[k];
+            y[i] = t / M[i * 9 + i];
         }
         for (int i = 8; i >= 0; --i) {  // L^T z = y
-            double s = y[i];
-            for (int k = i + 1; k < 9; ++k) s -= L[k * 9 + i] * y[k];
-            y[i] = s / L[i * 9 + i];
+            double t = y[i];
+            for (int k = i + 1; k < 9; ++k) t -= M[k * 9 + i] * y[k];
+            y[i] = t / M[i * 9 + i];
         }
         double n = 0, dot = 0;
         for (int i = 0; i < 9; ++i) {
@@ -161,8 +85,8 @@ __device__ __forceinline__ bool in_frame_tol(int i, float f, int n) {
 }
 
 // Target sample position of pixel (px, py) under a plane: integer base and
-// fraction; false if the denominator is not positive or the point leaves
-// [0, W-1] x [0, H-1].
+// fraction; false if the denominator is not positive or the point leaves the
+// frame (tolerance kFrameTol).
 __device__ __forceinline__ bool plane_target(const Mef& m, int px, int py, int W, int H, int& ix, float& fx, int& iy,
                                              float& fy, int& kx, int& ky) {
     if (!mef_flow(m, (float)(px - m.ox), (float)(py - m.oy), kx, fx, ky, fy)) return false;
@@ -179,28 +103,143 @@ __device__ __forceinline__ float colour_delta(const void* src, const void* tgt, 
     return absdiff3(a, b) / 3.f;
 }
 
-// ---------------------------------------------------------------- RANSAC per window
-// Sec. 3.1.2 / 3.2: one block per window and direction.  The window's
-// matches (u, u + v(u)) -- all pixels at stage 1, the still-unassigned ones in
-// raster order at stage 2 -- sit in shared memory as exact floats; each
-// thread draws, solves and scores hypotheses k = tid, tid + NT, ...; the
-// block keeps the largest support (lowest k on ties), refits it by the
-// normalised DLT on its inliers and keeps the refit unless it has fewer.
-template <int NT, int ST>
-__global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int level, int stage, PlaneParams pp) {
-    extern __shared__ float4 sm_match[];
-    __shared__ double red_d[NT / 32];
-    __shared__ int red_i[NT / 32];
-    __shared__ unsigned long long s_best;
-    __shared__ double s_Hw[9], s_Hr[9];
-    __shared__ double s_M[81];
-    __shared__ Mef s_mef[2];
-    __shared__ int s_woff[NT / 32 + 1];
-    __shared__ int s_refit_ok;
+// ---------------------------------------------------------------- cooperating groups
+// One window is processed by a group: a warp (windows up to 16 x 16) or a
+// whole block.  The group provides rank, size, barrier, sums and the scan
+// used to compact the residual matches in raster order.
+struct WarpGroup {
+    static constexpr int size = 32;
+    __device__ int rank() const { return threadIdx.x & 31; }
+    __device__ void sync() const { __syncwarp(); }
+    __device__ double sum(double v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        return v;
+    }
+    __device__ int sum(int v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        return v;
+    }
+    __device__ unsigned long long max(unsigned long long v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, v, off);
+            v = o > v ? o : v;
+        }
+        return v;
+    }
+    // exclusive prefix of `take` over the group and the total
+    __device__ int scan(bool take, int& total) const {
+        const unsigned b = __ballot_sync(FULL, take);
+        total = __popc(b);
+        return __popc(b & ((1u << rank()) - 1));
+    }
+};
 
-    const int dir = blockIdx.y;
-    const int cell = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+template <int NT>
+struct BlockGroup {
+    static constexpr int size = NT;
+    double* red_d;
+    int* red_i;
+    unsigned long long* red_u;
+    __device__ int rank() const { return threadIdx.x; }
+    __device__ void sync() const { __syncthreads(); }
+    __device__ double sum(double v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red_d[threadIdx.x >> 5] = v;
+        __syncthreads();
+        double t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += red_d[w];  // fixed order: same bits on every thread
+        return t;
+    }
+    __device__ int sum(int v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red_i[threadIdx.x >> 5] = v;
+        __syncthreads();
+        int t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += red_i[w];
+        return t;
+    }
+    __device__ unsigned long long max(unsigned long long v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, v, off);
+            v = o > v ? o : v;
+        }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red_u[threadIdx.x >> 5] = v;
+        __syncthreads();
+        unsigned long long t = 0;
+        for (int w = 0; w < NT / 32; ++w) t = red_u[w] > t ? red_u[w] : t;
+        return t;
+    }
+    __device__ int scan(bool take, int& total) const {
+        const unsigned b = __ballot_sync(FULL, take);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) red_i[warp] = __popc(b);
+        __syncthreads();
+        int off = 0;
+        total = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            if (w < warp) off += red_i[w];
+            total += red_i[w];
+        }
+        return off + __popc(b & ((1u << lane) - 1));
+    }
+};
+
+struct RansacScratch {
+    double Hw[9], Hr[9], M[81];
+    Mef mef[2];
+    int refit_ok;
+};
+
+// Draws hypothesis k of a window: Philox indices into the N matches; false if
+// the sample is degenerate (three source or three target points collinear).
+// The homography is exact (128-bit integers, see hyp_exact.cuh).
+__device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int cell, int k, uint32_t tag,
+                                                uint32_t pair_id, uint32_t k0, uint32_t k1, i128* Hk) {
+    const uint4 w = philox((uint32_t)cell, (uint32_t)k, tag, pair_id, k0, k1);
+    const uint32_t idx[4] = {w.x % (uint32_t)N, w.y % (uint32_t)N, w.z % (uint32_t)N, w.w % (uint32_t)N};
+    int px[4], py[4], qx[4], qy[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float4 m = match[idx[j]];
+        px[j] = (int)m.x;
+        py[j] = (int)m.y;
+        qx[j] = (int)(m.x + m.z);
+        qy[j] = (int)(m.y + m.w);
+    }
+    bool degen = false;
+    const int T3[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int a = T3[t][0], b = T3[t][1], c = T3[t][2];
+        degen |= collinear3(px[a], py[a], px[b], py[b], px[c], py[c]);
+        degen |= collinear3(qx[a], qy[a], qx[b], qy[b], qx[c], qy[c]);
+    }
+    if (degen) return false;
+    minimal_h_exact(px, py, qx, qy, Hk);
+    return true;
+}
+
+// ---------------------------------------------------------------- RANSAC per window
+// Sec. 3.1.2 / 3.2.  The window's matches (u, u + v(u)) -- all pixels at stage
+// 1, the still-unassigned ones in raster order at stage 2 -- sit in shared
+// memory as exact floats; the group's threads draw, solve and score the
+// hypotheses k = rank, rank + size, ...; the group keeps the largest support
+// (lowest k on ties), refits it by the normalised DLT on its inliers and keeps
+// the refit unless it has fewer inliers.
+template <class G, int ST>
+__device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
+                              const PlaneParams& pp, int dir, int cell, float4* match, RansacScratch* sc) {
+    const int tid = grp.rank();
     const int cxw = cell % g.gx.count, cyw = cell / g.gx.count;
     const int s = g.s;
     const int x0 = win_pos(g.gx, g.h, cxw), y0 = win_pos(g.gy, g.h, cyw);
@@ -213,7 +252,7 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
 
     // gather the window's matches in raster order
     int N = 0;
-    for (int base = 0; base < s * s; base += NT) {
+    for (int base = 0; base < s * s; base += G::size) {
         const int j = base + tid;
         bool take = false;
         float4 mt = make_float4(0, 0, 0, 0);
@@ -224,24 +263,12 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
             const int2 v = nnf[i];
             mt = make_float4((float)(xx - ox), (float)(yy - oy), (float)v.x, (float)v.y);
         }
-        const unsigned b = __ballot_sync(FULL, take);
-        if (lane == 0) s_woff[warp] = __popc(b);
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int w = 0; w < NT / 32; ++w) {
-                const int c = s_woff[w];
-                s_woff[w] = acc;
-                acc += c;
-            }
-            s_woff[NT / 32] = acc;
-        }
-        __syncthreads();
-        if (take) sm_match[N + s_woff[warp] + __popc(b & ((1u << lane) - 1))] = mt;
-        N += s_woff[NT / 32];
-        __syncthreads();
+        int total;
+        const int off = grp.scan(take, total);
+        if (take) match[N + off] = mt;
+        N += total;
     }
-
+    grp.sync();
     if (tid == 0) {
         for (int k = 0; k < kMI; ++k) mi[k] = 0;
         mi[MI_NIN] = N;
@@ -256,71 +283,50 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
     const float t2 = pp.t2;
     const uint32_t tag = stream_tag(RNG_RANSAC, dir, level, stage);
     int best_score = -1, best_k = 0x7fffffff;
-    double bH[9];
-    for (int k = tid; k < pp.num_hyp; k += NT) {
-        const uint4 w = philox((uint32_t)cell, (uint32_t)k, tag, pv.pair_id, pp.k0, pp.k1);
-        const uint32_t idx[4] = {w.x % (uint32_t)N, w.y % (uint32_t)N, w.z % (uint32_t)N, w.w % (uint32_t)N};
-        int px[4], py[4], qx[4], qy[4];
-        for (int j = 0; j < 4; ++j) {
-            const float4 m = sm_match[idx[j]];
-            px[j] = (int)m.x;
-            py[j] = (int)m.y;
-            qx[j] = (int)(m.x + m.z);
-            qy[j] = (int)(m.y + m.w);
-        }
-        bool degen = false;
-        const int T3[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            const int a = T3[t][0], b = T3[t][1], c = T3[t][2];
-            degen |= collinear3(px[a], py[a], px[b], py[b], px[c], py[c]);
-            degen |= collinear3(qx[a], qy[a], qx[b], qy[b], qx[c], qy[c]);
-        }
-        if (degen) continue;
-        double Hk[9];
-        minimal_h(px, py, qx, qy, Hk);
+    for (int k = tid; k < pp.num_hyp; k += G::size) {
+        i128 Hk[9];
+        if (!draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk)) continue;
         Mef m;
-        if (!make_mef(Hk, 0, 0, m)) continue;
+        if (!make_mef_exact(Hk, m)) continue;
         int score = 0;
         for (int j = 0; j < N; ++j) {
-            const float4 mt = sm_match[j];
+            const float4 mt = match[j];
             score += mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
         }
         if (score > best_score) {
             best_score = score;
             best_k = k;
-            for (int q = 0; q < 9; ++q) bH[q] = Hk[q];
         }
     }
-    // block argmax: most inliers, then lowest hypothesis index
-    if (tid == 0) s_best = 0ull;
-    __syncthreads();
+    // most inliers, then lowest hypothesis index
     const unsigned long long key =
         best_score < 0 ? 0ull
                        : (((unsigned long long)(best_score + 1)) << 32) |
                              (unsigned long long)(0xFFFFFFFFu - (uint32_t)best_k);
-    if (key) atomicMax(&s_best, key);
-    __syncthreads();
-    const unsigned long long wkey = s_best;
+    const unsigned long long wkey = grp.max(key);
     if (wkey == 0ull) return;
     const int wscore = (int)(wkey >> 32) - 1;
     const int wk = (int)(0xFFFFFFFFu - (uint32_t)(wkey & 0xFFFFFFFFull));
-    if (best_k == wk) {
-        for (int q = 0; q < 9; ++q) s_Hw[q] = bH[q];
-        make_mef(bH, 0, 0, s_mef[0]);
-    }
-    __syncthreads();
     if (tid == 0) {
+        i128 Hk[9];
+        draw_hypothesis(match, N, cell, wk, tag, pv.pair_id, pp.k0, pp.k1, Hk);
+        make_mef_exact(Hk, sc->mef[0]);
+        double D[9];
+        exact_to_double(Hk, D);
+        double f = 0;
+        for (int q = 0; q < 9; ++q) f = fmax(f, fabs(D[q]));
+        for (int q = 0; q < 9; ++q) sc->Hw[q] = D[q] / f;
         mi[MI_BESTK] = wk;
         mi[MI_BESTSCORE] = wscore;
     }
+    grp.sync();
     if (wscore < 4) return;
 
     // least-squares refit: Hartley normalisation of the winner's inliers
-    const Mef wm = s_mef[0];
+    const Mef wm = sc->mef[0];
     double sx = 0, sy = 0, tx = 0, ty = 0;
-    for (int j = tid; j < N; j += NT) {
-        const float4 mt = sm_match[j];
+    for (int j = tid; j < N; j += G::size) {
+        const float4 mt = match[j];
         if (mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) {
             sx += mt.x;
             sy += mt.y;
@@ -328,15 +334,15 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
             ty += mt.y + mt.w;
         }
     }
-    sx = block_sum<NT>(sx, red_d);
-    sy = block_sum<NT>(sy, red_d);
-    tx = block_sum<NT>(tx, red_d);
-    ty = block_sum<NT>(ty, red_d);
+    sx = grp.sum(sx);
+    sy = grp.sum(sy);
+    tx = grp.sum(tx);
+    ty = grp.sum(ty);
     const double inv_n = 1.0 / (double)wscore;
     const double mx = sx * inv_n, my = sy * inv_n, mqx = tx * inv_n, mqy = ty * inv_n;
     double ds = 0, dt = 0;
-    for (int j = tid; j < N; j += NT) {
-        const float4 mt = sm_match[j];
+    for (int j = tid; j < N; j += G::size) {
+        const float4 mt = match[j];
         if (mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) {
             const double a = mt.x - mx, b = mt.y - my;
             ds += sqrt(a * a + b * b);
@@ -344,35 +350,38 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
             dt += sqrt(c * c + d * d);
         }
     }
-    ds = block_sum<NT>(ds, red_d) * inv_n;
-    dt = block_sum<NT>(dt, red_d) * inv_n;
+    ds = grp.sum(ds) * inv_n;
+    dt = grp.sum(dt) * inv_n;
     const bool norm_ok = ds > 1e-12 && dt > 1e-12;
     const double ss = norm_ok ? sqrt(2.0) / ds : 1.0, sq = norm_ok ? sqrt(2.0) / dt : 1.0;
     // The normalised DLT rows of a pair (z = (x, y, 1) source, (u, v) target)
     // are a = (0, -z, v z) and b = (z, 0, -u z); their outer products sum to
     // blocks of S[w] = sum w z z^T with w in {1, u, v, u^2 + v^2}: 24 moments.
+    // (one pass per weight keeps six accumulators live instead of 24)
     double mom[24];
+    for (int a = 0; a < 4; ++a) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int j = tid; j < N; j += G::size) {
+            const float4 mt = match[j];
+            if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
+            const double x = ss * (mt.x - mx), y = ss * (mt.y - my);
+            const double u = sq * ((double)mt.x + mt.z - mqx), v = sq * ((double)mt.y + mt.w - mqy);
+            const double w = a == 0 ? 1.0 : (a == 1 ? u : (a == 2 ? v : u * u + v * v));
+            acc[0] = fma(w, x * x, acc[0]);
+            acc[1] = fma(w, x * y, acc[1]);
+            acc[2] = fma(w, x, acc[2]);
+            acc[3] = fma(w, y * y, acc[3]);
+            acc[4] = fma(w, y, acc[4]);
+            acc[5] += w;
+        }
 #pragma unroll
-    for (int q = 0; q < 24; ++q) mom[q] = 0;
-    for (int j = tid; j < N; j += NT) {
-        const float4 mt = sm_match[j];
-        if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
-        const double x = ss * (mt.x - mx), y = ss * (mt.y - my);
-        const double u = sq * ((double)mt.x + mt.z - mqx), v = sq * ((double)mt.y + mt.w - mqy);
-        const double mm[6] = {x * x, x * y, x, y * y, y, 1.0};
-        const double ww[4] = {1.0, u, v, u * u + v * v};
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 6; ++b) mom[a * 6 + b] = fma(ww[a], mm[b], mom[a * 6 + b]);
+        for (int b = 0; b < 6; ++b) mom[a * 6 + b] = grp.sum(acc[b]);
     }
-#pragma unroll
-    for (int q = 0; q < 24; ++q) mom[q] = block_sum<NT>(mom[q], red_d);
     if (tid == 0) {
-        s_refit_ok = 0;
+        sc->refit_ok = 0;
         if (norm_ok) {
             const int map[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-            double* M = s_M;
+            double* M = sc->M;
             for (int q = 0; q < 81; ++q) M[q] = 0;
             for (int r = 0; r < 3; ++r)
                 for (int c = 0; c < 3; ++c) {
@@ -392,29 +401,29 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
             const double Tq[9] = {sq, 0, -sq * mqx, 0, sq, -sq * mqy, 0, 0, 1};
             const double Tpi[9] = {1 / ss, 0, mx, 0, 1 / ss, my, 0, 0, 1};
             double t1[9], h0[9];
-            mat3_mul(Tq, s_Hw, t1);
+            mat3_mul(Tq, sc->Hw, t1);
             mat3_mul(t1, Tpi, h0);
             min_eigvec_inverse_iteration(M, h0);
             double Hr[9];
             mat3_mul(Tqi, h0, t1);
             mat3_mul(t1, Tp, Hr);
-            for (int q = 0; q < 9; ++q) s_Hr[q] = Hr[q];
-            s_refit_ok = make_mef(Hr, 0, 0, s_mef[1]) ? 1 : 0;
+            for (int q = 0; q < 9; ++q) sc->Hr[q] = Hr[q];
+            sc->refit_ok = make_mef(Hr, 0, 0, sc->mef[1]) ? 1 : 0;
         }
     }
-    __syncthreads();
+    grp.sync();
     int rcount = 0;
-    const bool have_refit = s_refit_ok != 0;
+    const bool have_refit = sc->refit_ok != 0;
     if (have_refit) {
-        const Mef rm = s_mef[1];
-        for (int j = tid; j < N; j += NT) {
-            const float4 mt = sm_match[j];
+        const Mef rm = sc->mef[1];
+        for (int j = tid; j < N; j += G::size) {
+            const float4 mt = match[j];
             rcount += mef_inlier(rm, mt.x, mt.y, mt.z, mt.w, t2);
         }
     }
-    rcount = block_count<NT>(rcount, red_i);
+    rcount = grp.sum(rcount);
     const bool use_refit = have_refit && rcount >= wscore;
-    Mef fm = s_mef[use_refit ? 1 : 0];
+    Mef fm = sc->mef[use_refit ? 1 : 0];
     const int count = use_refit ? rcount : wscore;
 
     // colour inliers among the RANSAC inliers: |S_R n S_C| (Sec. 3.4, third cue)
@@ -423,8 +432,8 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
     fm.ox = ox;
     fm.oy = oy;
     int nrc = 0;
-    for (int j = tid; j < N; j += NT) {
-        const float4 mt = sm_match[j];
+    for (int j = tid; j < N; j += G::size) {
+        const float4 mt = match[j];
         if (!mef_inlier(fm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
         const int px = ox + (int)mt.x, py = oy + (int)mt.y;
         int ix, iy, kx, ky;
@@ -432,10 +441,10 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
         if (!plane_target(fm, px, py, W, H, ix, fx, iy, fy, kx, ky)) continue;
         nrc += colour_delta<ST>(src, tgt, W, H, px, py, ix, fx, iy, fy) < pp.eps;
     }
-    nrc = block_count<NT>(nrc, red_i);
+    nrc = grp.sum(nrc);
 
     if (tid == 0) {
-        const double* Hl = use_refit ? s_Hr : s_Hw;
+        const double* Hl = use_refit ? sc->Hr : sc->Hw;
         // orientation/scale of the evaluation form: denominator 1 at the window centre
         const double dc = Hl[8] - 0.5 * (Hl[6] + Hl[7]);
         double hn[9];
@@ -456,8 +465,8 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
             const double det = j00 * j11 - j01 * j10;
             if (!(det > 0)) valid = false;
             else {
-                const double sc = sqrt(det);
-                if (!(sc >= (double)pp.scale_min && sc <= (double)pp.scale_max)) valid = false;
+                const double sc2 = sqrt(det);
+                if (!(sc2 >= (double)pp.scale_min && sc2 <= (double)pp.scale_max)) valid = false;
             }
         }
         double Ha[9];
@@ -470,6 +479,32 @@ __global__ void __launch_bounds__(NT) k_ransac(PairView pv, LevelGeom g, int lev
         mi[MI_FLAGS] = F_FITTED | (use_refit ? F_REFIT : 0) | (valid ? 0 : F_BAD_GEOM);
         mi[MI_NRC] = nrc;
     }
+}
+
+// Windows up to 16 x 16: one warp per window, eight windows per block.
+template <int ST>
+__global__ void __launch_bounds__(256, 2) k_ransac_warp(PairView pv, LevelGeom g, int level, int stage,
+                                                     PlaneParams pp) {
+    __shared__ float4 match[8][256];
+    __shared__ RansacScratch scratch[8];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * 8 + warp;
+    if (cell >= g.ncells()) return;
+    WarpGroup grp;
+    ransac_window<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match[warp], &scratch[warp]);
+}
+
+// Larger windows: one 256-thread block per window.
+template <int ST>
+__global__ void __launch_bounds__(256, 2) k_ransac_block(PairView pv, LevelGeom g, int level, int stage,
+                                                      PlaneParams pp) {
+    extern __shared__ float4 match_dyn[];
+    __shared__ RansacScratch scratch;
+    __shared__ double red_d[8];
+    __shared__ int red_i[8];
+    __shared__ unsigned long long red_u[8];
+    BlockGroup<256> grp{red_d, red_i, red_u};
+    ransac_window<BlockGroup<256>, ST>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, &scratch);
 }
 
 // ---------------------------------------------------------------- assignment (eq. 3-4)
@@ -790,14 +825,17 @@ __global__ void k_labels_import(Labels l, int n, const int* im, const float* iL,
 template <int ST>
 static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
                              cudaStream_t st) {
-    constexpr int NT = 256;
+    if (g.s <= 16) {
+        k_ransac_warp<ST><<<dim3((g.ncells() + 7) / 8, 2), 256, 0, st>>>(pv, g, level, stage, pp);
+        return;
+    }
     const size_t smem = (size_t)g.s * g.s * sizeof(float4);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_ransac<NT, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        cudaFuncSetAttribute(k_ransac_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
         attr_set = true;
     }
-    k_ransac<NT, ST><<<dim3(g.ncells(), 2), NT, smem, st>>>(pv, g, level, stage, pp);
+    k_ransac_block<ST><<<dim3(g.ncells(), 2), 256, smem, st>>>(pv, g, level, stage, pp);
 }
 void launch_ransac(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
                    cudaStream_t st) {
@@ -885,6 +923,15 @@ __global__ void k_reset_labels(PairView pv, float eps) {
         pv.frozen[dir][i] = 0;
     }
 }
+__global__ void k_frozen_from_labels(PairView pv) {
+    const int dir = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x)
+        pv.frozen[dir][i] = pv.acc[dir].m[i] >= 0;
+}
+void launch_frozen_from_labels(const PairView& pv, int grid_blocks, cudaStream_t st) {
+    k_frozen_from_labels<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+}
+
 void launch_reset_labels(const PairView& pv, float eps, int grid_blocks, cudaStream_t st) {
     k_reset_labels<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv, eps);
 }

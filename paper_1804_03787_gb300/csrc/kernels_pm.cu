@@ -97,13 +97,19 @@ struct Patch {
     static constexpr int NT = (T + 31) / 32;
 };
 
-// Per-lane patch state of one pixel.
+// Per-lane patch state of one pixel.  Tap j of the lane reads the target at
+// (tx + cx, ty + cy) for candidate offset c -- the clamped source pixel for a
+// square patch, or the integer part of p + G(s) - G(p) with fraction (fx, fy)
+// for a plane-distorted one -- and tidx = ty * W + tx.  [xlo, xhi] x [ylo, yhi]
+// bounds every texel the patch touches at offset 0 (including the +1 column
+// and row of bilinear taps), so a candidate whose shifted bounds stay inside
+// the frame needs no clamping: one add per tap gives the texel index.
 template <int R>
 struct LanePatch {
     float4 a[Patch<R>::NT];   // source texels of the lane's taps
-    int sx[Patch<R>::NT], sy[Patch<R>::NT];
-    int dk[Patch<R>::NT][2];  // warped tap displacement: integer part
-    float df[Patch<R>::NT][2];  // and fraction in [0,1)
+    int tx[Patch<R>::NT], ty[Patch<R>::NT], tidx[Patch<R>::NT];
+    float fx[Patch<R>::NT], fy[Patch<R>::NT];
+    int xlo, xhi, ylo, yhi;
     bool warped;
 };
 
@@ -115,18 +121,36 @@ __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, in
         const int t = lane + 32 * j;
         const int tt = t < Patch<R>::T ? t : 0;
         const int dy = tt / Patch<R>::D - R, dx = tt % Patch<R>::D - R;
-        lp.sx[j] = min(max(px + dx, 0), W - 1);
-        lp.sy[j] = min(max(py + dy, 0), H - 1);
-        lp.a[j] = ldpix<ST>(src, lp.sy[j] * W + lp.sx[j]);
+        lp.tx[j] = min(max(px + dx, 0), W - 1);
+        lp.ty[j] = min(max(py + dy, 0), H - 1);
+        lp.tidx[j] = lp.ty[j] * W + lp.tx[j];
+        lp.a[j] = ldpix<ST>(src, lp.tidx[j]);
+        lp.fx[j] = 0.f;
+        lp.fy[j] = 0.f;
     }
+    lp.xlo = max(px - R, 0);
+    lp.xhi = min(px + R, W - 1);
+    lp.ylo = max(py - R, 0);
+    lp.yhi = min(py + R, H - 1);
     lp.warped = false;
+}
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = min(v, __shfl_xor_sync(FULL, v, off));
+    return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = max(v, __shfl_xor_sync(FULL, v, off));
+    return v;
 }
 
 // Tap displacements G(s) - G(p) for the plane m at pixel p, from the local
 // Jacobian form: with J the derivative of G at p and c = (g0, g1) / den(p),
 // G(p + d) - G(p) = J d / (1 + c . d) exactly.
 template <int R>
-__device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px, int py) {
+__device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px, int py, int W, int lane) {
     const float ux = (float)(px - m.ox), uy = (float)(py - m.oy);
     const float e = m.e0 + m.g0 * ux + m.g1 * uy;
     const float den = 1.f + e;
@@ -138,45 +162,149 @@ __device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px
     const float j00 = (1.f + m.b0 - X * m.g0) / den, j01 = (m.h1 - X * m.g1) / den;
     const float j10 = (m.h3 - Y * m.g0) / den, j11 = (1.f + m.b4 - Y * m.g1) / den;
     const float c0 = m.g0 / den, c1 = m.g1 / den;
+    int xlo = 1 << 30, xhi = -(1 << 30), ylo = 1 << 30, yhi = -(1 << 30);
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
-        const float dx = (float)(lp.sx[j] - px), dy = (float)(lp.sy[j] - py);
+        const float dx = (float)(lp.tx[j] - px), dy = (float)(lp.ty[j] - py);
         const float q = 1.f + c0 * dx + c1 * dy;
         const float ex = (j00 * dx + j01 * dy) / q;
         const float ey = (j10 * dx + j11 * dy) / q;
         const float fx = floorf(ex), fy = floorf(ey);
-        lp.dk[j][0] = (int)fx;
-        lp.dk[j][1] = (int)fy;
-        lp.df[j][0] = ex - fx;
-        lp.df[j][1] = ey - fy;
+        lp.tx[j] = px + (int)fx;
+        lp.ty[j] = py + (int)fy;
+        lp.tidx[j] = lp.ty[j] * W + lp.tx[j];
+        lp.fx[j] = ex - fx;
+        lp.fy[j] = ey - fy;
+        if (lane + 32 * j < Patch<R>::T) {
+            xlo = min(xlo, lp.tx[j]);
+            xhi = max(xhi, lp.tx[j] + 1);
+            ylo = min(ylo, lp.ty[j]);
+            yhi = max(yhi, lp.ty[j] + 1);
+        }
     }
+    lp.xlo = warp_min(xlo);
+    lp.xhi = warp_max(xhi);
+    lp.ylo = warp_min(ylo);
+    lp.yhi = warp_max(yhi);
     lp.warped = true;
+}
+
+// Target sample of tap j for candidate offset c (off = c.y * W + c.x).
+template <int R, int ST>
+__device__ __forceinline__ float3 tap_sample(const LanePatch<R>& lp, const void* tgt, int W, int H, int j, int2 c,
+                                             int off, bool interior) {
+    if (!lp.warped) {
+        const int idx = interior ? lp.tidx[j] + off
+                                 : min(max(lp.ty[j] + c.y, 0), H - 1) * W + min(max(lp.tx[j] + c.x, 0), W - 1);
+        const float4 v = ldpix<ST>(tgt, idx);
+        return make_float3(v.x, v.y, v.z);
+    }
+    if (interior) {
+        const int i0 = lp.tidx[j] + off;
+        return blend4(ldpix<ST>(tgt, i0), ldpix<ST>(tgt, i0 + 1), ldpix<ST>(tgt, i0 + W), ldpix<ST>(tgt, i0 + W + 1),
+                      lp.fx[j], lp.fy[j]);
+    }
+    return bilinear<ST>(tgt, W, H, lp.tx[j] + c.x, lp.fx[j], lp.ty[j] + c.y, lp.fy[j]);
+}
+
+__device__ __forceinline__ bool interior_of(int xlo, int xhi, int ylo, int yhi, int2 c, int W, int H) {
+    return xlo + c.x >= 0 && xhi + c.x <= W - 1 && ylo + c.y >= 0 && yhi + c.y <= H - 1;
 }
 
 template <int R, int ST>
 __device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
                                             int vx, int vy, int lane) {
+    const int2 c = make_int2(vx, vy);
+    const bool in = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c, W, H);
+    const int off = vy * W + vx;
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
-        if (t < Patch<R>::T) {
-            float3 b;
-            if (!lp.warped) {
-                const int qx = min(max(lp.sx[j] + vx, 0), W - 1), qy = min(max(lp.sy[j] + vy, 0), H - 1);
-                const float4 c = ldpix<ST>(tgt, qy * W + qx);
-                b = make_float3(c.x, c.y, c.z);
-            } else {
-                b = bilinear<ST>(tgt, W, H, px + vx + lp.dk[j][0], lp.df[j][0], py + vy + lp.dk[j][1], lp.df[j][1]);
-            }
-            s += absdiff3(lp.a[j], b);
-        }
+        if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST>(lp, tgt, W, H, j, c, off, in));
     }
     // butterfly sum: every lane ends with the same bits (IEEE addition commutes)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+    for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_xor_sync(FULL, s, off2);
     return s / (float)(3 * Patch<R>::T);
 }
+
+// Costs of B candidate offsets at once: each lane issues the loads of its
+// taps for all B before reducing, so a warp keeps B x ceil(T/32) texel loads
+// in flight.  Per candidate the lane accumulates its taps in the same order
+// as patch_cost, so the costs are bitwise the same.
+template <int R, int ST, int B>
+__device__ __forceinline__ void patch_costB(const LanePatch<R>& lp, const void* tgt, int W, int H,
+                                            const int2 (&c)[B], float (&out)[B], int lane) {
+    float s[B];
+    bool in[B];
+    int off[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        s[k] = 0.f;
+        in[k] = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c[k], W, H);
+        off[k] = c[k].y * W + c[k].x;
+    }
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        if (t < Patch<R>::T) {
+            float3 b[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) b[k] = tap_sample<R, ST>(lp, tgt, W, H, j, c[k], off[k], in[k]);
+#pragma unroll
+            for (int k = 0; k < B; ++k) s[k] += absdiff3(lp.a[j], b[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(FULL, s[k], o);
+        out[k] = s[k] / (float)(3 * Patch<R>::T);
+    }
+}
+
+// Candidate queue of one pixel: candidates are evaluated B at a time and then
+// accepted in their fixed order with the strict-less rule, which gives the
+// same result as evaluating them one by one (a candidate equal to the current
+// best, or to an earlier one, can never be strictly cheaper).
+template <int R, int ST, int B>
+struct CandQueue {
+    int2 c[B];
+    int n;
+    int2 best;
+    float bc;
+    int nev;
+    __device__ __forceinline__ void flush(const LanePatch<R>& lp, const void* tgt, int W, int H, int lane) {
+        if (n == 0) return;
+#pragma unroll
+        for (int k = 1; k < B; ++k)
+            if (k >= n) c[k] = c[0];
+        float cc[B];
+        patch_costB<R, ST, B>(lp, tgt, W, H, c, cc, lane);
+#pragma unroll
+        for (int k = 0; k < B; ++k)
+            if (k < n && cc[k] < bc) {
+                bc = cc[k];
+                best = c[k];
+            }
+        nev += n;
+        n = 0;
+    }
+    __device__ __forceinline__ void push(int2 cand, const LanePatch<R>& lp, const void* tgt, int W, int H,
+                                         int lane) {
+        if (cand.x == best.x && cand.y == best.y) return;
+        bool dup = false;
+#pragma unroll
+        for (int k = 0; k < B; ++k) dup |= k < n && c[k].x == cand.x && c[k].y == cand.y;
+        if (dup) return;
+#pragma unroll
+        for (int k = 0; k < B; ++k)  // c[n] = cand with compile-time indices (keeps c in registers)
+            if (k == n) c[k] = cand;
+        ++n;
+        if (n == B) flush(lp, tgt, W, H, lane);
+    }
+};
 
 // Home-window plane of p at a level (residual-stage model first), or nullptr.
 __device__ __forceinline__ const Mef* home_plane(const LevelGeom& g, const Mef* mef, int x, int y) {
@@ -233,7 +361,7 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
             load_patch<R, ST>(lp, src, W, H, x, y, lane);
             if (level > 0) {
                 const Mef* G = home_plane(g, pv.mef[dir], x, y);
-                if (G) warp_taps<R>(lp, *G, x, y);
+                if (G) warp_taps<R>(lp, *G, x, y, W, lane);
             }
             const int2 v = pv.nnf[dir][i];
             const float c = patch_cost<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
@@ -246,7 +374,7 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
 }
 
 // ---------------------------------------------------------------- sweep
-template <int R, int ST>
+template <int R, int ST, int B>
 __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
                                                   uint32_t k0, uint32_t k1) {
     const int dir = blockIdx.y;
@@ -277,11 +405,13 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
         load_patch<R, ST>(lp, src, W, H, x, y, lane);
         if (level > 0) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
-            if (G) warp_taps<R>(lp, *G, x, y);
+            if (G) warp_taps<R>(lp, *G, x, y, W, lane);
         }
-        int2 best = nnf[i];
-        float bc = pv.cost[dir][i];
-        int nev = 0;
+        CandQueue<R, ST, B> q;
+        q.best = nnf[i];
+        q.bc = pv.cost[dir][i];
+        q.n = 0;
+        q.nev = 0;
         // random words for the search radii, two radii per Philox call, one call per lane
         uint4 rw = make_uint4(0, 0, 0, 0);
         if (lane < (nrad + 1) / 2)
@@ -295,13 +425,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
             const int2 c = nnf[ny * W + nx];
             const int tx = x + c.x, ty = y + c.y;
             if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
-            if (c.x == best.x && c.y == best.y) continue;
-            const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, c.x, c.y, lane);
-            ++nev;
-            if (cc < bc) {
-                bc = cc;
-                best = c;
-            }
+            q.push(c, lp, tgt, W, H, lane);
         }
         // plane candidates of the windows covering p, in window order, stage 1 then 2
         if (level > 0) {
@@ -322,18 +446,13 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
                         round_split(ky, fy, cy, ry);
                         const int tx = x + cx, ty = y + cy;
                         if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
-                        if (cx == best.x && cy == best.y) continue;
-                        const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, cx, cy, lane);
-                        ++nev;
-                        if (cc < bc) {
-                            bc = cc;
-                            best = make_int2(cx, cy);
-                        }
+                        q.push(make_int2(cx, cy), lp, tgt, W, H, lane);
                     }
                 }
         }
+        q.flush(lp, tgt, W, H, lane);
         // random search around the best offset after propagation, radii R0 >> k
-        const int2 v0 = best;
+        const int2 v0 = q.best;
         for (int k = 0; k < nrad; ++k) {
             const int Rk = R0 >> k;
             const uint32_t wx = __shfl_sync(FULL, (k & 1) ? rw.z : rw.x, k >> 1);
@@ -341,15 +460,12 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
             const int ox = (int)(wx % (uint32_t)(2 * Rk + 1)) - Rk;
             const int oy = (int)(wy % (uint32_t)(2 * Rk + 1)) - Rk;
             const int tx = min(max(x + v0.x + ox, 0), W - 1), ty = min(max(y + v0.y + oy, 0), H - 1);
-            const int cx = tx - x, cy = ty - y;
-            if (cx == best.x && cy == best.y) continue;
-            const float cc = patch_cost<R, ST>(lp, tgt, W, H, x, y, cx, cy, lane);
-            ++nev;
-            if (cc < bc) {
-                bc = cc;
-                best = make_int2(cx, cy);
-            }
+            q.push(make_int2(tx - x, ty - y), lp, tgt, W, H, lane);
         }
+        q.flush(lp, tgt, W, H, lane);
+        const int2 best = q.best;
+        const float bc = q.bc;
+        const int nev = q.nev;
         if (lane == 0) {
             nnf[i] = best;
             pv.cost[dir][i] = bc;
@@ -396,7 +512,12 @@ static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
             k_pm_recost<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level);
             break;
         case PmLaunch::SWEEP:
-            k_pm_sweep<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+            if (L.batch >= 4)
+                k_pm_sweep<R, ST, 4><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+            else if (L.batch == 2)
+                k_pm_sweep<R, ST, 2><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+            else
+                k_pm_sweep<R, ST, 1><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
             break;
     }
 }

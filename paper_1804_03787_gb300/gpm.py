@@ -253,7 +253,8 @@ class Context:
             return raw.view(np.float32).reshape(2, H, W, 4)
         raise ValueError(what)
 
-    def import_state(self, what: int, data, level: int, pair: int = 0):
+    def import_state(self, what: int, data, level: int, pair: int = 0, after_fit: bool = False):
+        """Imports state that belongs after gpm_match(level), or after gpm_fit_planes(level) with after_fit."""
         torch = self._torch
         if what in (LABELS,):
             m, L, f = data
@@ -266,7 +267,8 @@ class Context:
         else:
             raw = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
         buf = torch.from_numpy(raw.copy()).to("cuda")
-        self._check(self.lib.gpm_import(self.h, pair, what, C.c_void_p(buf.data_ptr()), level), "gpm_import")
+        stage = 2 * level - 1 if after_fit else 2 * level
+        self._check(self.lib.gpm_import(self.h, pair, what, C.c_void_p(buf.data_ptr()), stage), "gpm_import")
         self.sync()
 
     def close(self):

@@ -55,7 +55,13 @@ def norm_h(H):
     return H / np.linalg.norm(H)
 
 
-def rel_close(a, b, rel=1e-5, floor=1e-7):
+def rel_close(a, b, rel=1e-5, floor=1e-7, atol=0.0):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
-    return np.abs(a - b) <= rel * np.maximum(np.maximum(np.abs(a), np.abs(b)), floor)
+    return np.abs(a - b) <= rel * np.maximum(np.maximum(np.abs(a), np.abs(b)), floor) + atol
+
+
+# A colour error (eq. 3) is a mean of |texel - bilinear sample| over 3
+# channels of values in [0, 1]; in FP32 each sample carries a few ulp(1)
+# (~6e-8 each) of rounding, so its bound is absolute: 1e-6.
+COLOUR_ATOL = 1e-6
