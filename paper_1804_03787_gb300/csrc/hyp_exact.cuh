@@ -4,7 +4,7 @@
 // homography in FP64 was the bottleneck of the per-window fit.  Here the
 // projective-basis solution H ~ B adj(A) (see minimal_h in
 // kernels_planes.cu) is formed exactly in 128-bit integers -- window-local
-// coordinates keep every entry below 2^78 -- and the FP32 evaluation form is
+// coordinates keep every entry below 2^75 -- and the FP32 evaluation form is
 // derived from exact integer numerators with one rounding each; the
 // translation, which needs ~1e-7 px absolute accuracy on flows of hundreds of
 // pixels, is split into hi + lo with an exact integer remainder.
@@ -19,44 +19,18 @@ namespace gpm {
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
-__host__ __device__ __forceinline__ int clz64(uint64_t v) {
-#ifdef __CUDA_ARCH__
-    return __clzll((long long)v);
-#else
-    return v ? __builtin_clzll(v) : 64;
-#endif
-}
-
-__host__ __device__ __forceinline__ float u64_to_float_rn(uint64_t v) {
-#ifdef __CUDA_ARCH__
-    return __ull2float_rn(v);
-#else
-    return (float)v;
-#endif
-}
-
-// Nearest float to a 128-bit integer (sticky bit keeps the rounding exact).
-__host__ __device__ inline float i128_to_float(i128 x) {
-    if (x == 0) return 0.f;
+// Float near a 128-bit integer: both 64-bit halves converted, then one fused
+// multiply-add (within ~1 ulp; every caller tolerates that -- the translation
+// is corrected by an exact remainder).
+__host__ __device__ __forceinline__ float i128_to_float(i128 x) {
     const bool neg = x < 0;
-    u128 u = neg ? (u128)0 - (u128)x : (u128)x;
+    const u128 u = neg ? (u128)0 - (u128)x : (u128)x;  // magnitude: no cancellation between the halves
     const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
-    float f;
-    if (hi == 0) {
-        f = u64_to_float_rn(lo);
-    } else {
-        const int msb = 127 - clz64(hi);           // >= 64
-        const int sh = msb - 63;                   // bring the top 64 bits down
-        const u128 mask = (((u128)1) << sh) - 1;
-        uint64_t top = (uint64_t)(u >> sh);
-        if ((u & mask) != 0) top |= 1;             // sticky
-        f = u64_to_float_rn(top);
 #ifdef __CUDA_ARCH__
-        f = __fmul_rn(f, __int_as_float((127 + sh) << 23));
+    const float f = __fmaf_rn(__ull2float_rn(hi), 18446744073709551616.f, __ull2float_rn(lo));
 #else
-        f = f * __builtin_ldexpf(1.f, sh);
+    const float f = (float)hi * 18446744073709551616.f + (float)lo;
 #endif
-    }
     return neg ? -f : f;
 }
 
@@ -92,11 +66,19 @@ __host__ __device__ inline void minimal_h_exact(const int* px, const int* py, co
     adj[6] = (int64_t)A[3] * A[7] - (int64_t)A[4] * A[6];
     adj[7] = (int64_t)A[1] * A[6] - (int64_t)A[0] * A[7];
     adj[8] = (int64_t)A[0] * A[4] - (int64_t)A[1] * A[3];
-    const int64_t B[9] = {mu[0] * qx[0], mu[1] * qx[1], mu[2] * qx[2], mu[0] * qy[0], mu[1] * qy[1],
-                          mu[2] * qy[2], mu[0], mu[1], mu[2]};
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-            H[r * 3 + c] = (i128)B[r * 3] * adj[c] + (i128)B[r * 3 + 1] * adj[3 + c] + (i128)B[r * 3 + 2] * adj[6 + c];
+    // H = Q diag(mu) adj(A) = Q C with C = diag(mu) adj(A): |mu| < 2^25 and
+    // |adj| < 2^37 keep C in 64 bits, and Q holds 12-bit coordinates (last row 1).
+    int64_t Cm[9];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Cm[k * 3 + c] = mu[k] * adj[k * 3 + c];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        H[0 * 3 + c] = (i128)Cm[c] * qx[0] + (i128)Cm[3 + c] * qx[1] + (i128)Cm[6 + c] * qx[2];
+        H[1 * 3 + c] = (i128)Cm[c] * qy[0] + (i128)Cm[3 + c] * qy[1] + (i128)Cm[6 + c] * qy[2];
+        H[2 * 3 + c] = (i128)Cm[c] + (i128)Cm[3 + c] + (i128)Cm[6 + c];
+    }
 }
 
 // num / den (den > 0) as hi + lo floats: hi the rounded quotient, lo the

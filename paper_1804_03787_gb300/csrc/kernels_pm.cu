@@ -229,6 +229,35 @@ __device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* 
     return s / (float)(3 * Patch<R>::T);
 }
 
+// Cost of one candidate, abandoned early when it cannot win: after each
+// 32-tap chunk the warp sums what it has; the terms are non-negative and FP32
+// addition is monotonic, so a partial sum that already reaches the best cost
+// bounds the full sum from below and the strict-less test would reject the
+// candidate anyway.  Returns the full cost, or +inf if abandoned -- the
+// accept/reject decision is exactly that of patch_cost.
+template <int R, int ST>
+__device__ __forceinline__ float patch_cost_bounded(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c,
+                                                    float best, int lane) {
+    const bool in = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c, W, H);
+    const int off = c.y * W + c.x;
+    const float scale = (float)(3 * Patch<R>::T);
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST>(lp, tgt, W, H, j, c, off, in));
+        if (j + 1 < Patch<R>::NT) {
+            float p = s;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
+            if (p / scale >= best) return __int_as_float(0x7f800000);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    return s / scale;
+}
+
 // Costs of B candidate offsets at once: each lane issues the loads of its
 // taps for all B before reducing, so a warp keeps B x ceil(T/32) texel loads
 // in flight.  Per candidate the lane accumulates its taps in the same order
@@ -277,6 +306,16 @@ struct CandQueue {
     int nev;
     __device__ __forceinline__ void flush(const LanePatch<R>& lp, const void* tgt, int W, int H, int lane) {
         if (n == 0) return;
+        if (B == 1) {  // one at a time: abandon hopeless candidates early
+            const float cc = patch_cost_bounded<R, ST>(lp, tgt, W, H, c[0], bc, lane);
+            if (cc < bc) {
+                bc = cc;
+                best = c[0];
+            }
+            nev += 1;
+            n = 0;
+            return;
+        }
 #pragma unroll
         for (int k = 1; k < B; ++k)
             if (k >= n) c[k] = c[0];
@@ -374,8 +413,10 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
 }
 
 // ---------------------------------------------------------------- sweep
-template <int R, int ST, int B>
-__global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
+// PLANES: levels >= 1 (restricted pixel list, plane-distorted patches, plane
+// candidates); level 0 is compiled without any of that.
+template <int R, int ST, int B, bool PLANES>
+__global__ void __launch_bounds__(256, PLANES ? 3 : 4) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
                                                   uint32_t k0, uint32_t k1) {
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
@@ -385,13 +426,13 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
     int2* __restrict__ nnf = pv.nnf[dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int hw = (W + 1) >> 1;
-    const int total = level == 0 ? H * hw : pv.list_count[dir * 2 + phase];
-    const int* list = level == 0 ? nullptr : pv.list[dir] + phase * pv.n;
+    const int total = !PLANES ? H * hw : pv.list_count[dir * 2 + phase];
+    const int* list = !PLANES ? nullptr : pv.list[dir] + phase * pv.n;
     const int R0 = max(W, H);
     const uint32_t tag = stream_tag(RNG_SEARCH, dir, level, 0);
     for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         int x, y, i;
-        if (level == 0) {
+        if (!PLANES) {
             y = w / hw;
             x = 2 * (w - y * hw) + ((y + phase) & 1);
             if (x >= W) continue;
@@ -403,7 +444,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
         }
         LanePatch<R> lp;
         load_patch<R, ST>(lp, src, W, H, x, y, lane);
-        if (level > 0) {
+        if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, lane);
         }
@@ -428,7 +469,7 @@ __global__ void __launch_bounds__(256) k_pm_sweep(PairView pv, LevelGeom g, int 
             q.push(c, lp, tgt, W, H, lane);
         }
         // plane candidates of the windows covering p, in window order, stage 1 then 2
-        if (level > 0) {
+        if (PLANES) {
             int ix[3], iy[3];
             const int nxw = covering(g.gx, g.s, g.h, x, ix), nyw = covering(g.gy, g.s, g.h, y, iy);
             for (int a = 0; a < nyw; ++a)
@@ -512,12 +553,17 @@ static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
             k_pm_recost<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level);
             break;
         case PmLaunch::SWEEP:
-            if (L.batch >= 4)
-                k_pm_sweep<R, ST, 4><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
-            else if (L.batch == 2)
-                k_pm_sweep<R, ST, 2><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
-            else
-                k_pm_sweep<R, ST, 1><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+            if (L.level == 0) {
+                if (L.batch >= 2)
+                    k_pm_sweep<R, ST, 2, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0, L.k1);
+                else
+                    k_pm_sweep<R, ST, 1, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0, L.k1);
+            } else {
+                if (L.batch >= 2)
+                    k_pm_sweep<R, ST, 2, true><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+                else
+                    k_pm_sweep<R, ST, 1, true><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+            }
             break;
     }
 }

@@ -385,3 +385,47 @@ def test_repeatable_bitwise(torch):
         ctx.close()
     for a, b in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------- reduced-precision storage
+def _quantise(a, kind):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+    return (t.to(torch.float16 if kind == "f16" else torch.bfloat16).to(torch.float32)).numpy()
+
+
+@pytest.mark.parametrize("kind,storage", [("f16", gpm.GPM_F16), ("bf16", gpm.GPM_BF16)])
+def test_reduced_precision_storage(torch, kind, storage):
+    """Frames stored as FP16/BF16 texels, FP32 arithmetic: against the oracle run
+    on the dequantised frames the level-0 NNF follows the near-tie rule; against
+    the oracle on the original frames the error is reported and bounded."""
+    W, H, r, cells = 64, 48, 2, (16, 8)
+    s = _scene(W, H, seed=21)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=3, num_hyp=64, storage=storage)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
+    fr = ctx.export(gpm.FRAMES)
+    P = oracle_params(gp, W, H)
+    frames32, g = oracle_frames(P, s.frame1, s.frame2)
+    # the GPU stores round(I1) and round(gain * I2): the oracle sees exactly those values
+    q1 = _quantise(s.frame1, kind).astype(np.float64)
+    q2 = _quantise((s.frame2.astype(np.float64) * g).astype(np.float32), kind).astype(np.float64)
+    np.testing.assert_array_equal(fr[0, ..., :3], q1)
+    np.testing.assert_array_equal(fr[1, ..., :3], q2)
+    Pq = oracle_params(gp, W, H)
+    Pq.gain_normalize = 0
+    framesq = [(q1, q2), (q2, q1)]
+    agree = []
+    for d in range(2):
+        vx, vy, c, cone = _oracle_pm(Pq, framesq, d)
+        diff = ((nnf[d, :, 0] != vx) | (nnf[d, :, 1] != vy)).reshape(H, W)
+        assert not (diff & ~cone).any()
+        same = ~diff.reshape(-1)
+        assert rel_close(cost[d][same], c[same]).all()
+        # against the FP64 oracle on the original frames
+        vx0, vy0, c0, _ = _oracle_pm(P, frames32, d)
+        agree.append(np.mean((nnf[d, :, 0] == vx0) & (nnf[d, :, 1] == vy0)))
+    print(f"{kind}: level-0 NNF agreement with the FP64 oracle on FP32 frames {np.mean(agree):.4f}")
+    assert np.mean(agree) > 0.8
+    ctx.close()
