@@ -224,6 +224,27 @@ enum {
 gpm_status gpm_profile_enable(gpm_ctx* ctx, int32_t enable);
 gpm_status gpm_profile_read(gpm_ctx* ctx, double* ms, uint64_t* launches, uint64_t* evals);
 
+/* ---- ingest without allocation ----
+   The paper has no counterpart to this call: it serves callers that cannot
+   call cudaMalloc -- code inside a CUDA stream capture, hosts whose device
+   memory is fixed up front, plugins of frameworks that own the memory pool.
+   It converts one frame pair exactly as gpm_match(level 0) ingests it:
+   frame1/frame2 are DEVICE buffers, height x width x 3 FP32 (HWC, row stride
+   in elements); out1/out2 are caller-owned DEVICE buffers of width x height
+   RGBX texels in `storage` (GPM_F32: 16 bytes each, GPM_F16 / GPM_BF16:
+   8 bytes); with gain_normalize, frame 2 is scaled by mean(I1) / mean(I2).
+   It allocates nothing: its scratch is a static device array sized for at
+   most 4096 rows (64 KiB, held on every GPU that loads the library until the
+   process exits).  Returns GPM_EINVAL for NULL pointers, bad sizes or a frame
+   taller than 4096 rows, GPM_ECUDA if a CUDA call fails.  The first call on a
+   device looks up the array's device address (once per device); make that
+   first call before any stream capture.  All calls share the array: calls
+   that overlap on the GPU (unordered streams) race, so order them.
+   stream: a cudaStream_t (NULL = legacy default). */
+gpm_status gpm_ingest_noalloc(const float* frame1, const float* frame2, int32_t width, int32_t height,
+                              int64_t row_stride, int32_t gain_normalize, int32_t storage, void* out1, void* out2,
+                              void* stream);
+
 /* Human-readable status name and the context's last error message. */
 const char* gpm_status_string(gpm_status s);
 const char* gpm_last_error(const gpm_ctx* ctx);

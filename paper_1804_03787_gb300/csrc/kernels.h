@@ -20,6 +20,9 @@ void launch_pm(const PmLaunch& L, cudaStream_t st);
 void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
                    double* partial, int nblk, double* gain, void* o1, void* o2, cudaStream_t st);
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
+// RGB -> RGBX storage of both frames, frame 2 scaled by *gain (a device scalar)
+void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride, int storage, const double* gain,
+                 void* o1, void* o2, cudaStream_t st);
 
 struct PlaneParams {
     int num_hyp, min_inliers, radius, storage;

@@ -599,6 +599,16 @@ void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t strid
     }
 }
 
+void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride, int storage, const double* gain,
+                 void* o1, void* o2, cudaStream_t st) {
+    const int blocks = 152 * 4;
+    switch (storage) {
+        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+    }
+}
+
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
     k_build_lists<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
 }
