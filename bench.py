@@ -44,6 +44,21 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value over all ranks (the whole job ends when the slowest rank does)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world_size: int, max_ms: float) -> float:
+    """Whole-job rate: every rank's units over the slowest rank's time (weak scaling)."""
+    return units_per_rank * world_size / (max_ms * 1e-3)
+
+
 def oracle_params():
     import oracle as O
     f = lambda x: float(np.float32(x))
@@ -152,6 +167,12 @@ def roofline_block(prof, evals, nsm, clocks, peaks, steps):
         ach = ops / (ms * 1e-3) / 1e12
         block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
                       "units": "FP32 lane operations (24 per tap)"})
+    elif top == "ransac":
+        # one residual test ||H u - (u + v)||^2 < t^2 in the evaluation form: 14 FP32 operations
+        ops = evals[2] * 14
+        ach = ops / (ms * 1e-3) / 1e12
+        block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
+                      "units": "FP32 lane operations (14 per residual test; hypothesis solves not counted)"})
     else:
         block.update({"bound": "alu", "achieved": None, "peak": peak_ops, "unit": "TFLOP/s", "frac": None})
     block["traffic"] = None
@@ -254,13 +275,8 @@ def run_ours(args):
     launches = ctx.launch_count() - launches0
     prof, evals = ctx.profile_read()
     ctx.profile_enable(False)
-    total_ms = sum(times)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    pairs = args.steps * P * ws
-    value = pairs / (total_ms * 1e-3)
+    total_ms = max_over_ranks(sum(times), dist, "cuda")
+    value = job_throughput(args.steps * P, ws, total_ms)
     pm_ms = prof["pm_sweep"][0] + prof["pm_init"][0] + prof["pm_sweep_plane"][0] + prof["pm_recost"][0]
     evals_per_s = (evals[0] + evals[1]) * ws / (pm_ms * 1e-3) if pm_ms > 0 else None
 
@@ -293,11 +309,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
-    e2e_ms = sum(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(sum(e2e_times), dist, "cuda")
     h2d = P * 2 * W * H * 3 * 4
     d2h = P * (W * H * 2 * 4 + W * H)
 
@@ -309,9 +321,10 @@ def run_ours(args):
                        "l2": "flushed between timed steps by a 256 MiB device write", "parallelism": "replicas"},
             "warped_patch_evals_per_s": evals_per_s,
             "evals_per_step": (evals[0] + evals[1]) / args.steps,
+            "ransac_tests_per_step": evals[2] / args.steps,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "roofline": roof,
-            "e2e": {"value": args.steps * P * ws / (e2e_ms * 1e-3), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_throughput(args.steps * P, ws, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -201,10 +201,12 @@ gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_
    With profiling on, every kernel launch of the context is bracketed by CUDA
    events on the context's stream, and the PatchMatch kernels count the
    candidate offsets they evaluate (one evaluation = one (2r+1)^2-tap,
-   3-channel patch cost).  gpm_profile_read synchronises the stream, returns
-   per kernel class the summed device milliseconds and the launch count, and
-   the evaluation counts [level 0, levels >= 1], then clears them.  Host
-   arrays: ms[GPM_PROF_CLASSES], launches[GPM_PROF_CLASSES], evals[2]. */
+   3-channel patch cost) and RANSAC counts its residual tests (scored
+   hypotheses x window matches).  gpm_profile_read synchronises the stream,
+   returns per kernel class the summed device milliseconds and the launch
+   count, and the counts [PatchMatch evaluations at level 0, at levels >= 1,
+   RANSAC residual tests], then clears them.  Host arrays:
+   ms[GPM_PROF_CLASSES], launches[GPM_PROF_CLASSES], evals[3]. */
 enum {
     GPM_PROF_INGEST = 0,
     GPM_PROF_PM_INIT = 1,

@@ -274,9 +274,9 @@ __host__ __device__ inline void local_to_abs(const double* Hl, int ox, int oy, d
     const double w = Ha[6] * cx + Ha[7] * cy + Ha[8];
     double f = 0;
     for (int i = 0; i < 9; ++i) f += Ha[i] * Ha[i];
-    f = sqrt(f);
+    f = 1.0 / sqrt(f);
     if (w < 0) f = -f;
-    for (int i = 0; i < 9; ++i) Ha[i] /= f;
+    for (int i = 0; i < 9; ++i) Ha[i] *= f;
 }
 
 // local H = T(-o) Ha T(o)
@@ -319,7 +319,7 @@ struct PairView {
     int* list[2];         // unfrozen pixel indices, colour 0 then colour 1
     int* list_count;      // [2 dirs][2 colours]
     unsigned long long* m2o_key[2];
-    unsigned long long* evals;  // [level 0, levels >= 1] evaluated candidates, or nullptr
+    unsigned long long* evals;  // [PM evaluations level 0, levels >= 1, RANSAC residual tests], or nullptr
 };
 
 }  // namespace gpm

@@ -175,7 +175,7 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, char* base, S
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
     double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
     double* gain = (double*)take(sizeof(double));
-    unsigned long long* evals = (unsigned long long*)take(2 * sizeof(unsigned long long));
+    unsigned long long* evals = (unsigned long long*)take(3 * sizeof(unsigned long long));
     if (s) {
         s->d_evals = evals;
         s->pv = pv;
@@ -677,7 +677,7 @@ gpm_status gpm_profile_enable(gpm_ctx* c, int32_t enable) {
     c->prof = enable != 0;
     for (auto& s : c->slots) {
         s.pv.evals = c->prof ? s.d_evals : nullptr;
-        if (c->prof) cudaMemsetAsync(s.d_evals, 0, 2 * sizeof(unsigned long long), c->stream);
+        if (c->prof) cudaMemsetAsync(s.d_evals, 0, 3 * sizeof(unsigned long long), c->stream);
     }
     return cuda_check(c, "gpm_profile_enable");
 }
@@ -700,19 +700,16 @@ gpm_status gpm_profile_read(gpm_ctx* c, double* ms, uint64_t* launches, uint64_t
         if (launches) launches[k] = c->prof_launches[k];
         c->prof_launches[k] = 0;
     }
-    uint64_t ev[2] = {0, 0};
+    uint64_t ev[3] = {0, 0, 0};
     for (auto& s : c->slots) {
         if (!s.d_evals) continue;
-        unsigned long long h[2] = {0, 0};
+        unsigned long long h[3] = {0, 0, 0};
         cudaMemcpy(h, s.d_evals, sizeof h, cudaMemcpyDeviceToHost);
-        ev[0] += h[0];
-        ev[1] += h[1];
+        for (int k = 0; k < 3; ++k) ev[k] += h[k];
         cudaMemset(s.d_evals, 0, sizeof h);
     }
-    if (evals) {
-        evals[0] = ev[0];
-        evals[1] = ev[1];
-    }
+    if (evals)
+        for (int k = 0; k < 3; ++k) evals[k] = ev[k];
     return cuda_check(c, "gpm_profile_read");
 }
 

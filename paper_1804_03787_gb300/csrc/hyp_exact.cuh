@@ -19,17 +19,37 @@ namespace gpm {
 typedef __int128 i128;
 typedef unsigned __int128 u128;
 
-// Float near a 128-bit integer: both 64-bit halves converted, then one fused
-// multiply-add (within ~1 ulp; every caller tolerates that -- the translation
-// is corrected by an exact remainder).
+// Integer -> float without conversion instructions (on GB300 conversions
+// from 64-bit integers issue on the slow FP64 pipe): a value below 2^23 ORed
+// into the mantissa of 2^23 is exact, so a 32-bit limb is two 16-bit halves
+// and one fused multiply-add (correctly rounded).
+__host__ __device__ __forceinline__ float u16_to_float(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __int_as_float(0x4B000000u | v) - 8388608.f;
+#else
+    return (float)v;
+#endif
+}
+__host__ __device__ __forceinline__ float u32_to_float(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __fmaf_rn(u16_to_float(v >> 16), 65536.f, u16_to_float(v & 0xFFFFu));
+#else
+    return (float)v;
+#endif
+}
+
+// Float near a 128-bit integer below 2^96 in magnitude (ours stay below 2^76):
+// the 32-bit limbs combined by fused multiply-adds, within about 1 ulp -- every
+// caller tolerates that (the translation is corrected by an exact remainder).
 __host__ __device__ __forceinline__ float i128_to_float(i128 x) {
     const bool neg = x < 0;
-    const u128 u = neg ? (u128)0 - (u128)x : (u128)x;  // magnitude: no cancellation between the halves
-    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+    const u128 u = neg ? (u128)0 - (u128)x : (u128)x;  // magnitude: no cancellation between limbs
+    const uint32_t l0 = (uint32_t)u, l1 = (uint32_t)(u >> 32), l2 = (uint32_t)(u >> 64);
 #ifdef __CUDA_ARCH__
-    const float f = __fmaf_rn(__ull2float_rn(hi), 18446744073709551616.f, __ull2float_rn(lo));
+    const float f = __fmaf_rn(u32_to_float(l2), 18446744073709551616.f,
+                              __fmaf_rn(u32_to_float(l1), 4294967296.f, u32_to_float(l0)));
 #else
-    const float f = (float)hi * 18446744073709551616.f + (float)lo;
+    const float f = (float)l2 * 18446744073709551616.f + (float)l1 * 4294967296.f + (float)l0;
 #endif
     return neg ? -f : f;
 }
@@ -83,8 +103,8 @@ __host__ __device__ inline void minimal_h_exact(const int* px, const int* py, co
 
 // num / den (den > 0) as hi + lo floats: hi the rounded quotient, lo the
 // quotient of the exact integer remainder.
-__host__ __device__ inline void split_ratio(i128 num, i128 den, float fden, float& hi, float& lo) {
-    hi = i128_to_float(num) / fden;
+__host__ __device__ inline void split_ratio(i128 num, i128 den, float rden, float& hi, float& lo) {
+    hi = i128_to_float(num) * rden;
     lo = 0.f;
     const float a = hi < 0 ? -hi : hi;
     if (!(a >= 9.5367431640625e-07f && a < 1048576.f)) return;  // 2^-20 <= |hi| < 2^20, else hi alone
@@ -98,9 +118,9 @@ __host__ __device__ inline void split_ratio(i128 num, i128 den, float fden, floa
     const int sh = 24 - e;                   // in [4, 44]
     const i128 R = num * ((i128)1 << sh) - (i128)m * den;
 #ifdef __CUDA_ARCH__
-    lo = __fmul_rn(i128_to_float(R) / fden, __int_as_float((127 - sh) << 23));
+    lo = __fmul_rn(i128_to_float(R) * rden, __int_as_float((127 - sh) << 23));
 #else
-    lo = (i128_to_float(R) / fden) * __builtin_ldexpf(1.f, -sh);
+    lo = (i128_to_float(R) * rden) * __builtin_ldexpf(1.f, -sh);
 #endif
 }
 
@@ -113,16 +133,16 @@ __host__ __device__ inline bool make_mef_exact(const i128* Hin, Mef& m) {
     const bool flip = dc2 < 0;
     for (int k = 0; k < 9; ++k) H[k] = flip ? -Hin[k] : Hin[k];
     if (flip) dc2 = -dc2;
-    const float fd = i128_to_float(dc2);
-    m.b0 = i128_to_float(2 * H[0] - dc2) / fd;
-    m.h1 = i128_to_float(2 * H[1]) / fd;
-    split_ratio(2 * H[2], dc2, fd, m.h2h, m.h2l);
-    m.h3 = i128_to_float(2 * H[3]) / fd;
-    m.b4 = i128_to_float(2 * H[4] - dc2) / fd;
-    split_ratio(2 * H[5], dc2, fd, m.h5h, m.h5l);
-    m.g0 = i128_to_float(2 * H[6]) / fd;
-    m.g1 = i128_to_float(2 * H[7]) / fd;
-    m.e0 = i128_to_float(2 * H[8] - dc2) / fd;
+    const float rd = 1.f / i128_to_float(dc2);  // one reciprocal, then products (about 1 ulp each)
+    m.b0 = i128_to_float(2 * H[0] - dc2) * rd;
+    m.h1 = i128_to_float(2 * H[1]) * rd;
+    split_ratio(2 * H[2], dc2, rd, m.h2h, m.h2l);
+    m.h3 = i128_to_float(2 * H[3]) * rd;
+    m.b4 = i128_to_float(2 * H[4] - dc2) * rd;
+    split_ratio(2 * H[5], dc2, rd, m.h5h, m.h5l);
+    m.g0 = i128_to_float(2 * H[6]) * rd;
+    m.g1 = i128_to_float(2 * H[7]) * rd;
+    m.e0 = i128_to_float(2 * H[8] - dc2) * rd;
     m.pad0 = 0.f;
     m.ox = 0;
     m.oy = 0;
@@ -131,9 +151,9 @@ __host__ __device__ inline bool make_mef_exact(const i128* Hin, Mef& m) {
     return true;
 }
 
-// The exact homography as doubles (unnormalised).
-__host__ __device__ inline void exact_to_double(const i128* H, double* D) {
-    for (int k = 0; k < 9; ++k) {
+// The first n entries of an exact homography as doubles (unnormalised).
+__host__ __device__ inline void exact_to_double(const i128* H, double* D, int n = 9) {
+    for (int k = 0; k < n; ++k) {
         const bool neg = H[k] < 0;
         const u128 u = neg ? (u128)0 - (u128)H[k] : (u128)H[k];
         const double v = (double)(uint64_t)(u >> 64) * 18446744073709551616.0 + (double)(uint64_t)u;

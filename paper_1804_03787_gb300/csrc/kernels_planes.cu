@@ -20,57 +20,6 @@ __device__ __forceinline__ bool collinear3(int ax, int ay, int bx, int by, int c
     return (long long)(bx - ax) * (cy - ay) - (long long)(by - ay) * (cx - ax) == 0;
 }
 
-// Smallest-eigenvalue eigenvector of a symmetric positive semi-definite 9x9
-// matrix M (shared memory, overwritten by its Cholesky factor) by inverse
-// iteration on M + sigma I, started from x.
-__device__ void min_eigvec_inverse_iteration(double* M, double* x) {
-    double tr = 0;
-    for (int i = 0; i < 9; ++i) tr += M[i * 9 + i];
-    const double sigma = 1e-13 * tr + 1e-300;
-    for (int j = 0; j < 9; ++j) {  // in-place Cholesky, lower triangle
-        double d = M[j * 9 + j] + sigma;
-        for (int k = 0; k < j; ++k) d -= M[j * 9 + k] * M[j * 9 + k];
-        d = d > 0 ? sqrt(d) : 1e-150;
-        M[j * 9 + j] = d;
-        for (int i = j + 1; i < 9; ++i) {
-            double t = M[i * 9 + j];
-            for (int k = 0; k < j; ++k) t -= M[i * 9 + k] * M[j * 9 + k];
-            M[i * 9 + j] = t / d;
-        }
-    }
-    double nx = 0;
-    for (int i = 0; i < 9; ++i) nx += x[i] * x[i];
-    nx = 1.0 / sqrt(nx);
-    for (int i = 0; i < 9; ++i) x[i] *= nx;
-    for (int it = 0; it < 60; ++it) {
-        double y[9];
-        for (int i = 0; i < 9; ++i) {  // L y = x
-            double t = x[i];
-            for (int k = 0; k < i; ++k) t -= M[i * 9 + k] * y[k];
-            y[i] = t / M[i * 9 + i];
-        }
-        for (int i = 8; i >= 0; --i) {  // L^T z = y
-            double t = y[i];
-            for (int k = i + 1; k < 9; ++k) t -= M[k * 9 + i] * y[k];
-            y[i] = t / M[i * 9 + i];
-        }
-        double n = 0, dot = 0;
-        for (int i = 0; i < 9; ++i) {
-            n += y[i] * y[i];
-            dot += y[i] * x[i];
-        }
-        n = 1.0 / sqrt(n);
-        if (dot < 0) n = -n;
-        double diff = 0;
-        for (int i = 0; i < 9; ++i) {
-            y[i] *= n;
-            diff = fmax(diff, fabs(y[i] - x[i]));
-            x[i] = y[i];
-        }
-        if (diff < 1e-15) break;
-    }
-}
-
 __device__ __forceinline__ void mat3_mul(const double* A, const double* B, double* C) {
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) C[i * 3 + j] = A[i * 3] * B[j] + A[i * 3 + 1] * B[3 + j] + A[i * 3 + 2] * B[6 + j];
@@ -195,10 +144,90 @@ struct BlockGroup {
 };
 
 struct RansacScratch {
-    double Hw[9], Hr[9], M[81];
+    double Hw[9], Hr[9], M[81], Li[81], x[9], rd[9], h0[9];
     Mef mef[2];
     int refit_ok;
 };
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, off));
+    return v;
+}
+
+// Smallest-eigenvalue eigenvector of the symmetric positive semi-definite 9x9
+// matrix sc->M, started from sc->x, by one warp: M + sigma I is factored
+// column by column (Cholesky, rows in parallel), its inverse formed
+// explicitly (columns in parallel), and inverse iteration then costs one
+// lane-parallel matrix-vector product per step.  A single-lane FP64 chain
+// would hold GB300's FP64 pipe for a whole warp instruction per operation.
+__device__ void min_eigvec_warp(RansacScratch* sc, int lane) {
+    double* M = sc->M;
+    double* Li = sc->Li;
+    const double tr = warp_sum_d(lane < 9 ? M[lane * 9 + lane] : 0.0);
+    const double sigma = 1e-13 * tr + 1e-300;
+    if (lane < 9) M[lane * 9 + lane] += sigma;
+    __syncwarp();
+    for (int j = 0; j < 9; ++j) {  // Cholesky, lower triangle in place
+        if (lane == j) {
+            double d = M[j * 9 + j];
+            for (int k = 0; k < j; ++k) d -= M[j * 9 + k] * M[j * 9 + k];
+            d = d > 0 ? sqrt(d) : 1e-150;
+            M[j * 9 + j] = d;
+            sc->rd[j] = 1.0 / d;
+        }
+        __syncwarp();
+        if (lane > j && lane < 9) {
+            double t = M[lane * 9 + j];
+            for (int k = 0; k < j; ++k) t -= M[lane * 9 + k] * M[j * 9 + k];
+            M[lane * 9 + j] = t * sc->rd[j];
+        }
+        __syncwarp();
+    }
+    if (lane < 9) {  // column `lane` of L^-1 by forward substitution
+        const int c = lane;
+        for (int i = 0; i < 9; ++i) {
+            double t = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) t -= M[i * 9 + k] * Li[k * 9 + c];
+            Li[i * 9 + c] = i < c ? 0.0 : t * sc->rd[i];
+        }
+    }
+    __syncwarp();
+    // (M + sigma I)^-1 = L^-T L^-1, kept in M
+    for (int e = lane; e < 81; e += 32) {
+        const int i = e / 9, j = e % 9;
+        double t = 0;
+        for (int k = (i > j ? i : j); k < 9; ++k) t += Li[k * 9 + i] * Li[k * 9 + j];
+        sc->M[e] = t;
+    }
+    __syncwarp();
+    double xi = lane < 9 ? sc->x[lane] : 0.0;
+    const double n0 = warp_sum_d(xi * xi);
+    xi *= 1.0 / sqrt(n0);
+    if (lane < 9) sc->x[lane] = xi;
+    __syncwarp();
+    for (int it = 0; it < 60; ++it) {
+        double yi = 0;
+        if (lane < 9)
+            for (int j = 0; j < 9; ++j) yi += M[lane * 9 + j] * sc->x[j];
+        const double n = warp_sum_d(yi * yi), dot = warp_sum_d(yi * xi);
+        double sc_ = 1.0 / sqrt(n);
+        if (dot < 0) sc_ = -sc_;
+        yi *= sc_;
+        const double diff = warp_max_d(lane < 9 ? fabs(yi - xi) : 0.0);
+        __syncwarp();
+        if (lane < 9) sc->x[lane] = yi;
+        xi = yi;
+        __syncwarp();
+        if (diff < 1e-15) break;
+    }
+}
+
 
 // Draws hypothesis k of a window: Philox indices into the N matches; false if
 // the sample is degenerate (three source or three target points collinear).
@@ -210,11 +239,13 @@ __device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int 
     int px[4], py[4], qx[4], qy[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
+        // the match coordinates are small exact integers held as floats: adding
+        // 1.5 * 2^23 puts the integer in the low mantissa bits (no conversion op)
         const float4 m = match[idx[j]];
-        px[j] = (int)m.x;
-        py[j] = (int)m.y;
-        qx[j] = (int)(m.x + m.z);
-        qy[j] = (int)(m.y + m.w);
+        px[j] = __float_as_int(m.x + 12582912.f) - 0x4B400000;
+        py[j] = __float_as_int(m.y + 12582912.f) - 0x4B400000;
+        qx[j] = __float_as_int((m.x + m.z) + 12582912.f) - 0x4B400000;
+        qy[j] = __float_as_int((m.y + m.w) + 12582912.f) - 0x4B400000;
     }
     bool degen = false;
     const int T3[4][3] = {{0, 1, 2}, {0, 1, 3}, {0, 2, 3}, {1, 2, 3}};
@@ -282,12 +313,13 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
     // hypotheses
     const float t2 = pp.t2;
     const uint32_t tag = stream_tag(RNG_RANSAC, dir, level, stage);
-    int best_score = -1, best_k = 0x7fffffff;
+    int best_score = -1, best_k = 0x7fffffff, scored = 0;
     for (int k = tid; k < pp.num_hyp; k += G::size) {
         i128 Hk[9];
         if (!draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk)) continue;
         Mef m;
         if (!make_mef_exact(Hk, m)) continue;
+        ++scored;
         int score = 0;
         for (int j = 0; j < N; ++j) {
             const float4 mt = match[j];
@@ -298,6 +330,10 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
             best_k = k;
         }
     }
+    if (pv.evals) {  // residual tests (profiling)
+        const int tests = grp.sum(scored);
+        if (tid == 0) atomicAdd(&pv.evals[2], (unsigned long long)tests * (unsigned long long)N);
+    }
     // most inliers, then lowest hypothesis index
     const unsigned long long key =
         best_score < 0 ? 0ull
@@ -307,17 +343,22 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
     if (wkey == 0ull) return;
     const int wscore = (int)(wkey >> 32) - 1;
     const int wk = (int)(0xFFFFFFFFu - (uint32_t)(wkey & 0xFFFFFFFFull));
-    if (tid == 0) {
+    if (tid < 32) {  // first warp: the winner again, converted to double lane by lane
         i128 Hk[9];
         draw_hypothesis(match, N, cell, wk, tag, pv.pair_id, pp.k0, pp.k1, Hk);
-        make_mef_exact(Hk, sc->mef[0]);
-        double D[9];
-        exact_to_double(Hk, D);
-        double f = 0;
-        for (int q = 0; q < 9; ++q) f = fmax(f, fabs(D[q]));
-        for (int q = 0; q < 9; ++q) sc->Hw[q] = D[q] / f;
-        mi[MI_BESTK] = wk;
-        mi[MI_BESTSCORE] = wscore;
+        if (tid == 0) {
+            make_mef_exact(Hk, sc->mef[0]);
+            mi[MI_BESTK] = wk;
+            mi[MI_BESTSCORE] = wscore;
+        }
+        double dk = 0;
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            if (tid == q) {
+                exact_to_double(&Hk[q], &dk, 1);
+            }
+        const double f = warp_max_d(fabs(dk));
+        if (tid < 9) sc->Hw[tid] = dk * (1.0 / f);
     }
     grp.sync();
     if (wscore < 4) return;
@@ -340,14 +381,15 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
     ty = grp.sum(ty);
     const double inv_n = 1.0 / (double)wscore;
     const double mx = sx * inv_n, my = sy * inv_n, mqx = tx * inv_n, mqy = ty * inv_n;
+    const float fmx = (float)mx, fmy = (float)my, fmqx = (float)mqx, fmqy = (float)mqy;
     double ds = 0, dt = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
         if (mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) {
-            const double a = mt.x - mx, b = mt.y - my;
-            ds += sqrt(a * a + b * b);
-            const double c = (double)mt.x + mt.z - mqx, d = (double)mt.y + mt.w - mqy;
-            dt += sqrt(c * c + d * d);
+            // FP32 roots summed in FP64: the mean distance only sets the normalising scale
+            const float a = mt.x - fmx, b = mt.y - fmy, c = (mt.x + mt.z) - fmqx, d = (mt.y + mt.w) - fmqy;
+            ds += (double)sqrtf(a * a + b * b);
+            dt += (double)sqrtf(c * c + d * d);
         }
     }
     ds = grp.sum(ds) * inv_n;
@@ -377,38 +419,44 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
 #pragma unroll
         for (int b = 0; b < 6; ++b) mom[a * 6 + b] = grp.sum(acc[b]);
     }
-    if (tid == 0) {
-        sc->refit_ok = 0;
+    if (tid < 32) {  // first warp: assemble A^T A, solve, back to pixel coordinates
+        const int lane = tid;
+        if (lane == 0) sc->refit_ok = 0;
         if (norm_ok) {
+            // entry (r, c) of the 9x9 from the moment blocks: rows/cols 0-2 b b^T, 3-5 a a^T, 6-8 the u,v blocks
             const int map[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-            double* M = sc->M;
-            for (int q = 0; q < 81; ++q) M[q] = 0;
-            for (int r = 0; r < 3; ++r)
-                for (int c = 0; c < 3; ++c) {
-                    const int e = map[r][c];
-                    const double S = mom[e], Su = mom[6 + e], Sv = mom[12 + e], Suv = mom[18 + e];
-                    M[r * 9 + c] = S;
-                    M[(3 + r) * 9 + (3 + c)] = S;
-                    M[r * 9 + (6 + c)] = -Su;
-                    M[(6 + c) * 9 + r] = -Su;
-                    M[(3 + r) * 9 + (6 + c)] = -Sv;
-                    M[(6 + c) * 9 + (3 + r)] = -Sv;
-                    M[(6 + r) * 9 + (6 + c)] = Suv;
-                }
-            // start from the winning hypothesis in the normalised frames
-            const double Tp[9] = {ss, 0, -ss * mx, 0, ss, -ss * my, 0, 0, 1};
-            const double Tqi[9] = {1 / sq, 0, mqx, 0, 1 / sq, mqy, 0, 0, 1};
-            const double Tq[9] = {sq, 0, -sq * mqx, 0, sq, -sq * mqy, 0, 0, 1};
-            const double Tpi[9] = {1 / ss, 0, mx, 0, 1 / ss, my, 0, 0, 1};
-            double t1[9], h0[9];
-            mat3_mul(Tq, sc->Hw, t1);
-            mat3_mul(t1, Tpi, h0);
-            min_eigvec_inverse_iteration(M, h0);
-            double Hr[9];
-            mat3_mul(Tqi, h0, t1);
-            mat3_mul(t1, Tp, Hr);
-            for (int q = 0; q < 9; ++q) sc->Hr[q] = Hr[q];
-            sc->refit_ok = make_mef(Hr, 0, 0, sc->mef[1]) ? 1 : 0;
+            for (int e = lane; e < 81; e += 32) {
+                const int r = e / 9, c = e % 9, br = r / 3, bc = c / 3, ir = r % 3, ic = c % 3;
+                const int q = map[ir][ic];
+                double v = 0;
+                if (br == bc) v = br < 2 ? mom[q] : mom[18 + q];
+                else if ((br == 0 && bc == 2) || (br == 2 && bc == 0)) v = -mom[6 + q];
+                else if ((br == 1 && bc == 2) || (br == 2 && bc == 1)) v = -mom[12 + q];
+                sc->M[e] = v;
+            }
+            // start: the winning hypothesis in the normalised frames, h0 = Tq Hw Tp^-1
+            if (lane < 9) {
+                const int r = lane / 3, c = lane % 3;
+                const double* Hw = sc->Hw;
+                // (Hw Tp^-1)[k][c] for Tp^-1 = [1/ss 0 mx; 0 1/ss my; 0 0 1]
+                double b[3];
+                for (int k = 0; k < 3; ++k)
+                    b[k] = c == 0 ? Hw[k * 3] / ss : (c == 1 ? Hw[k * 3 + 1] / ss : Hw[k * 3] * mx + Hw[k * 3 + 1] * my + Hw[k * 3 + 2]);
+                sc->x[lane] = r == 0 ? sq * (b[0] - mqx * b[2]) : (r == 1 ? sq * (b[1] - mqy * b[2]) : b[2]);
+            }
+            __syncwarp();
+            min_eigvec_warp(sc, lane);
+            // Hr = Tq^-1 h Tp
+            if (lane < 9) {
+                const int r = lane / 3, c = lane % 3;
+                const double* h = sc->x;
+                double b[3];
+                for (int k = 0; k < 3; ++k)
+                    b[k] = c == 0 ? h[k * 3] * ss : (c == 1 ? h[k * 3 + 1] * ss : h[k * 3 + 2] - ss * (mx * h[k * 3] + my * h[k * 3 + 1]));
+                sc->Hr[lane] = r == 0 ? b[0] / sq + mqx * b[2] : (r == 1 ? b[1] / sq + mqy * b[2] : b[2]);
+            }
+            __syncwarp();
+            if (lane == 0) sc->refit_ok = make_mef(sc->Hr, 0, 0, sc->mef[1]) ? 1 : 0;
         }
     }
     grp.sync();
@@ -447,8 +495,9 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
         const double* Hl = use_refit ? sc->Hr : sc->Hw;
         // orientation/scale of the evaluation form: denominator 1 at the window centre
         const double dc = Hl[8] - 0.5 * (Hl[6] + Hl[7]);
+        const double rdc = 1.0 / dc;
         double hn[9];
-        for (int q = 0; q < 9; ++q) hn[q] = Hl[q] / dc;
+        for (int q = 0; q < 9; ++q) hn[q] = Hl[q] * rdc;
         // plane validity: support, positive denominator on the window grown by
         // the patch radius, local area scale at the centre within range
         bool valid = count >= pp.min_inliers && 5 * count >= N;

@@ -214,13 +214,13 @@ class Context:
         self._check(self.lib.gpm_profile_enable(self.h, 1 if on else 0), "gpm_profile_enable")
 
     def profile_read(self):
-        """{class: (ms, launches)}, (evals at level 0, evals at levels >= 1); clears the counters."""
+        """{class: (ms, launches)}, (PM evals at level 0, at levels >= 1, RANSAC residual tests); clears them."""
         k = len(PROF_CLASSES)
         ms = (C.c_double * k)()
         ln = (C.c_uint64 * k)()
-        ev = (C.c_uint64 * 2)()
+        ev = (C.c_uint64 * 3)()
         self._check(self.lib.gpm_profile_read(self.h, ms, ln, ev), "gpm_profile_read")
-        return {PROF_CLASSES[i]: (ms[i], int(ln[i])) for i in range(k)}, (int(ev[0]), int(ev[1]))
+        return {PROF_CLASSES[i]: (ms[i], int(ln[i])) for i in range(k)}, (int(ev[0]), int(ev[1]), int(ev[2]))
 
     # ------------------------------------------------------------ state
     def export(self, what: int, pair: int = 0):
