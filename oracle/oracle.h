@@ -72,6 +72,10 @@ enum { ORC_CUE_M2O = 1 };
    lower by more than this (planes of one surface fitted in overlapping windows
    give equal L up to rounding; the first window keeps the pixel) */
 #define ORC_L_TIE 1e-6
+/* absolute floor of the near-tie band for decisions on a colour error (eq. 3):
+   an FP32 evaluation of one carries up to ~1e-6 of rounding, and a decision
+   compares two of them */
+#define ORC_L_ATOL 2e-6
 
 /* ---- counter-based RNG: Philox4x32-10 (Salmon et al., SC'11) ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

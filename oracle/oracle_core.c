@@ -47,6 +47,9 @@ static uint32_t stream_tag(int purpose, int dir, int level, int stage) {
     return ((uint32_t)purpose << 24) | ((uint32_t)dir << 16) | ((uint32_t)level << 8) | (uint32_t)stage;
 }
 
+/* Uniform integer in [0, n) from a 32-bit random word: floor(u * n / 2^32). */
+static inline uint32_t bounded_u32(uint32_t u, uint32_t n) { return (uint32_t)(((uint64_t)u * n) >> 32); }
+
 static void rng4(const orc_params* P, uint32_t c0, uint32_t c1, uint32_t tag, uint32_t out[4]) {
     uint32_t ctr[4] = {c0, c1, tag, P->pair_id};
     uint32_t key[2] = {(uint32_t)(P->seed & 0xFFFFFFFFu), (uint32_t)(P->seed >> 32)};
@@ -322,8 +325,8 @@ void orc_pm_sweep(const orc_params* P, const double* src, const double* tgt, int
                 uint32_t w[4];
                 rng4(P, (uint32_t)i, ((uint32_t)it << 8) | (uint32_t)(k >> 1), stream_tag(2, dir, level, 0), w);
                 uint32_t ux = (k & 1) ? w[2] : w[0], uy = (k & 1) ? w[3] : w[1];
-                int ox = (int)(ux % (uint32_t)(2 * R + 1)) - R;
-                int oy = (int)(uy % (uint32_t)(2 * R + 1)) - R;
+                int ox = (int)bounded_u32(ux, (uint32_t)(2 * R + 1)) - R;
+                int oy = (int)bounded_u32(uy, (uint32_t)(2 * R + 1)) - R;
                 int tx = clampi(x + v0x + ox, 0, W - 1), ty = clampi(y + v0y + oy, 0, H - 1);
                 TRY(tx - x, ty - y);
             }

@@ -18,11 +18,21 @@ static inline double rel_gap(double a, double b) {
     return fabs(a - b) / m;
 }
 
+/* a and b (colour errors, eq. 3, or values compared with one) are within the
+   near-tie band: relative ORC_TIE_REL, at least ORC_L_ATOL absolute */
+static inline int near_colour(double a, double b) {
+    double m = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    return fabs(a - b) < fmax(ORC_TIE_REL * m, ORC_L_ATOL);
+}
+
 static void rng4(const orc_params* P, uint32_t c0, uint32_t c1, uint32_t tag, uint32_t out[4]) {
     uint32_t ctr[4] = {c0, c1, tag, P->pair_id};
     uint32_t key[2] = {(uint32_t)(P->seed & 0xFFFFFFFFu), (uint32_t)(P->seed >> 32)};
     orc_philox4x32_10(ctr, key, out);
 }
+
+/* Uniform integer in [0, n) from a 32-bit random word: floor(u * n / 2^32). */
+static inline uint32_t bounded_u32(uint32_t u, uint32_t n) { return (uint32_t)(((uint64_t)u * n) >> 32); }
 
 static uint32_t stream_tag(int purpose, int dir, int level, int stage) {
     return ((uint32_t)purpose << 24) | ((uint32_t)dir << 16) | ((uint32_t)level << 8) | (uint32_t)stage;
@@ -359,7 +369,7 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
             uint32_t w[4];
             rng4(P, (uint32_t)cell, (uint32_t)k, stream_tag(3, dir, level, stage), w);
             int id[4];
-            for (int j = 0; j < 4; ++j) id[j] = (int)(w[j] % (uint32_t)N);
+            for (int j = 0; j < 4; ++j) id[j] = (int)bounded_u32(w[j], (uint32_t)N);
             scores[k] = -1;
             ambs[k] = 0;
             /* degenerate sample: three of the four source (or target) points on one line */
@@ -469,7 +479,7 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
             if (!in_frame(P, X, Y)) continue;
             double d = delta_at(P, src, tgt, ix[j], iy[j], X, Y);
             if (d < P->eps) ++nrc;
-            if (rel_gap(d, P->eps) < ORC_TIE_REL) ambig = 1;
+            if (near_colour(d, P->eps)) ambig = 1;
         }
         mi[ORC_MI_NRC] = nrc;
         if (ambig) mi[ORC_MI_FLAGS] |= ORC_F_AMBIG;
@@ -530,9 +540,9 @@ void orc_assign(const orc_params* P, const double* src, const double* tgt, int l
                     if (near_frame_edge(P, X, Y)) a = 1;
                     if (!in_frame(P, X, Y)) continue;
                     double d = delta_at(P, src, tgt, x, y, X, Y);
-                    if (rel_gap(d, P->eps) < ORC_TIE_REL) a = 1;
+                    if (near_colour(d, P->eps)) a = 1;
                     if (!(d < P->eps)) continue;
-                    if (bm >= 0 && fabs(d - (bL - ORC_L_TIE)) < ORC_TIE_REL * bL) a = 1;
+                    if (bm >= 0 && near_colour(d, bL - ORC_L_TIE)) a = 1;
                     if (d < bL - ORC_L_TIE) {
                         bL = d;
                         bm = id;
@@ -635,11 +645,14 @@ void orc_many_to_one(const orc_params* P, int32_t* lm, const double* lL, const d
         tq[i] = -1;
         if (lm[i] < 0) continue;
         int x = i % W, y = i / W;
-        int qx = (int)floor(x + lfx[i] + 0.5), qy = (int)floor(y + lfy[i] + 0.5);
+        double tx = x + lfx[i] + 0.5, ty = y + lfy[i] + 0.5;
+        double gx = fmin(tx - floor(tx), floor(tx) + 1 - tx), gy = fmin(ty - floor(ty), floor(ty) + 1 - ty);
+        if (amb && (gx < 1e-5 * fmax(1, fabs(tx)) || gy < 1e-5 * fmax(1, fabs(ty)))) amb[i] = 1;
+        int qx = (int)floor(tx), qy = (int)floor(ty);
         if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
         int q = qy * W + qx;
         tq[i] = q;
-        if (bi[q] >= 0 && amb && rel_gap(lL[i], bL[q]) < ORC_TIE_REL) {
+        if (bi[q] >= 0 && amb && near_colour(lL[i], bL[q])) {
             amb[i] = 1;
             amb[bi[q]] = 1;
         }
@@ -681,7 +694,7 @@ void orc_merge(const orc_params* P, const int32_t* lm, const double* lL, const d
     const int n = P->W * P->H;
     for (int i = 0; i < n; ++i) {
         if (lm[i] < 0) continue;
-        if (am[i] >= 0 && amb && rel_gap(lL[i], aL[i] - P->beta) < ORC_TIE_REL) amb[i] = 1;
+        if (am[i] >= 0 && amb && near_colour(lL[i], aL[i] - P->beta)) amb[i] = 1;
         if (am[i] < 0 || lL[i] < aL[i] - P->beta) {
             am[i] = lm[i];
             aL[i] = lL[i];

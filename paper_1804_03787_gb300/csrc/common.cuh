@@ -49,6 +49,10 @@ __host__ __device__ __forceinline__ uint32_t stream_tag(int purpose, int dir, in
 }
 enum { RNG_INIT = 1, RNG_SEARCH = 2, RNG_RANSAC = 3 };
 
+// Uniform integer in [0, n) from a 32-bit random word: floor(u * n / 2^32)
+// (one multiply-high instead of an integer division).
+__device__ __forceinline__ uint32_t bounded_u32(uint32_t u, uint32_t n) { return __umulhi(u, n); }
+
 // ---------------------------------------------------------------- frames
 // Frames live as RGBX texels: FP32 float4 (16 B), or FP16 / BF16 x4 (8 B).
 template <int ST>
@@ -151,6 +155,18 @@ __device__ __forceinline__ int covering(const AxisGrid& a, int s, int h, int x, 
     if (a.extra && x >= a.last) idx[k++] = a.n_reg;
     return k;
 }
+// The same windows as a range (no array, so it stays in registers): window
+// k < count is first + k while k < nreg, then the extra window.
+__device__ __forceinline__ int covering_range(const AxisGrid& a, int s, int h, int x, int& first, int& nreg) {
+    const int lo = x - s + 1 > 0 ? (x - s + 1 + h - 1) / h : 0;
+    const int hi = min(x / h, a.n_reg - 1);
+    first = lo;
+    nreg = max(0, min(hi - lo + 1, 2));
+    return nreg + ((a.extra && x >= a.last) ? 1 : 0);
+}
+__device__ __forceinline__ int covering_at(const AxisGrid& a, int first, int nreg, int k) {
+    return k < nreg ? first + k : a.n_reg;
+}
 // Home window: the window whose central half holds x.
 __device__ __forceinline__ int home_index(const AxisGrid& a, int s, int h, int x) {
     const int t = x - s / 4;
@@ -197,8 +213,9 @@ __device__ __forceinline__ bool mef_flow(const Mef& m, float ux, float uy, int& 
     if (!(den > 0.f)) return false;
     const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
     const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
-    const float cx = m.h2l + (Sx - m.h2h * e) / den;
-    const float cy = m.h5l + (Sy - m.h5h * e) / den;
+    const float rden = __frcp_rn(den);  // one reciprocal (about 1e-7 px on these small terms)
+    const float cx = m.h2l + (Sx - m.h2h * e) * rden;
+    const float cy = m.h5l + (Sy - m.h5h * e) * rden;
     split_flow(m.h2h, cx, kx, fx);
     split_flow(m.h5h, cy, ky, fy);
     return true;

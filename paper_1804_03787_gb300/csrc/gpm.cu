@@ -46,7 +46,6 @@ struct gpm_ctx {
     void* user = nullptr;
     cudaStream_t stream = nullptr;
     int nsm = 152;
-    int pm_batch = 1;  // PatchMatch candidates per warp batch (tuning: GPM_PM_BATCH = 1, 2 or 4)
     int max_n = 0, max_models = 0;
     size_t slot_bytes = 0;
     std::vector<Slot> slots;
@@ -260,7 +259,6 @@ void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
     L.level = level;
     L.nrad = num_radii(s.W, s.H);
     L.grid_blocks = c->nsm * 8;
-    L.batch = c->pm_batch;
     L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
     L.k1 = (uint32_t)(c->P.seed >> 32);
     if (level > 0 || !c->P.pm_init) {
@@ -380,10 +378,6 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
         cudaGetLastError();
         delete c;
         return GPM_ECUDA;
-    }
-    if (const char* e = std::getenv("GPM_PM_BATCH")) {
-        const int b = std::atoi(e);
-        if (b == 1 || b == 2 || b == 4) c->pm_batch = b;
     }
     c->max_n = limits->max_width * limits->max_height;
     c->max_models = std::max(2, 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr));

@@ -13,7 +13,6 @@ struct PmLaunch {
     const PairView* pv;
     LevelGeom geom;
     int radius, storage, level, it, phase, nrad, grid_blocks;
-    int batch;  // candidates evaluated together per warp (1, 2 or 4)
     uint32_t k0, k1;
 };
 void launch_pm(const PmLaunch& L, cudaStream_t st);

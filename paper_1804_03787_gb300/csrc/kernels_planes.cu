@@ -235,7 +235,8 @@ __device__ void min_eigvec_warp(RansacScratch* sc, int lane) {
 __device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int cell, int k, uint32_t tag,
                                                 uint32_t pair_id, uint32_t k0, uint32_t k1, i128* Hk) {
     const uint4 w = philox((uint32_t)cell, (uint32_t)k, tag, pair_id, k0, k1);
-    const uint32_t idx[4] = {w.x % (uint32_t)N, w.y % (uint32_t)N, w.z % (uint32_t)N, w.w % (uint32_t)N};
+    const uint32_t idx[4] = {bounded_u32(w.x, (uint32_t)N), bounded_u32(w.y, (uint32_t)N),
+                             bounded_u32(w.z, (uint32_t)N), bounded_u32(w.w, (uint32_t)N)};
     int px[4], py[4], qx[4], qy[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {

@@ -157,18 +157,19 @@ __device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px
     const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
     const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
     // local target of p: X = u + D(u)
-    const float X = ux + (m.h2h + (m.h2l + (Sx - m.h2h * e) / den));
-    const float Y = uy + (m.h5h + (m.h5l + (Sy - m.h5h * e) / den));
-    const float j00 = (1.f + m.b0 - X * m.g0) / den, j01 = (m.h1 - X * m.g1) / den;
-    const float j10 = (m.h3 - Y * m.g0) / den, j11 = (1.f + m.b4 - Y * m.g1) / den;
-    const float c0 = m.g0 / den, c1 = m.g1 / den;
+    const float rden = __frcp_rn(den);
+    const float X = ux + (m.h2h + (m.h2l + (Sx - m.h2h * e) * rden));
+    const float Y = uy + (m.h5h + (m.h5l + (Sy - m.h5h * e) * rden));
+    const float j00 = (1.f + m.b0 - X * m.g0) * rden, j01 = (m.h1 - X * m.g1) * rden;
+    const float j10 = (m.h3 - Y * m.g0) * rden, j11 = (1.f + m.b4 - Y * m.g1) * rden;
+    const float c0 = m.g0 * rden, c1 = m.g1 * rden;
     int xlo = 1 << 30, xhi = -(1 << 30), ylo = 1 << 30, yhi = -(1 << 30);
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const float dx = (float)(lp.tx[j] - px), dy = (float)(lp.ty[j] - py);
-        const float q = 1.f + c0 * dx + c1 * dy;
-        const float ex = (j00 * dx + j01 * dy) / q;
-        const float ey = (j10 * dx + j11 * dy) / q;
+        const float rq = __frcp_rn(1.f + c0 * dx + c1 * dy);
+        const float ex = (j00 * dx + j01 * dy) * rq;
+        const float ey = (j10 * dx + j11 * dy) * rq;
         const float fx = floorf(ex), fy = floorf(ey);
         lp.tx[j] = px + (int)fx;
         lp.ty[j] = py + (int)fy;
@@ -229,121 +230,54 @@ __device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* 
     return s / (float)(3 * Patch<R>::T);
 }
 
-// Cost of one candidate, abandoned early when it cannot win: after each
+// Raw tap sum of candidate offset c (over taps and channels of |difference|,
+// before the division by 3T), abandoned once it cannot win.  After each
 // 32-tap chunk the warp sums what it has; the terms are non-negative and FP32
-// addition is monotonic, so a partial sum that already reaches the best cost
-// bounds the full sum from below and the strict-less test would reject the
-// candidate anyway.  Returns the full cost, or +inf if abandoned -- the
-// accept/reject decision is exactly that of patch_cost.
+// addition is monotonic, so a partial sum at or above `thr` (the best cost so
+// far times 3T, raised by 2^-20 to absorb the rounding of that product) bounds
+// the full cost at or above the best, and the strict-less test would reject
+// the candidate anyway: the function returns false.  Each lane accumulates
+// its taps in the same order as patch_cost, so a full sum divided by 3T gives
+// bitwise the same cost.
 template <int R, int ST>
-__device__ __forceinline__ float patch_cost_bounded(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c,
-                                                    float best, int lane) {
+__device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, float thr,
+                                        float& sum, int lane) {
     const bool in = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c, W, H);
     const int off = c.y * W + c.x;
-    const float scale = (float)(3 * Patch<R>::T);
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
         if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST>(lp, tgt, W, H, j, c, off, in));
+        float p = s;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
         if (j + 1 < Patch<R>::NT) {
-            float p = s;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
-            if (p / scale >= best) return __int_as_float(0x7f800000);
+            if (!(p < thr)) return false;
+        } else {
+            sum = p;
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-    return s / scale;
+    return true;
 }
 
-// Costs of B candidate offsets at once: each lane issues the loads of its
-// taps for all B before reducing, so a warp keeps B x ceil(T/32) texel loads
-// in flight.  Per candidate the lane accumulates its taps in the same order
-// as patch_cost, so the costs are bitwise the same.
-template <int R, int ST, int B>
-__device__ __forceinline__ void patch_costB(const LanePatch<R>& lp, const void* tgt, int W, int H,
-                                            const int2 (&c)[B], float (&out)[B], int lane) {
-    float s[B];
-    bool in[B];
-    int off[B];
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-        s[k] = 0.f;
-        in[k] = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c[k], W, H);
-        off[k] = c[k].y * W + c[k].x;
-    }
-#pragma unroll
-    for (int j = 0; j < Patch<R>::NT; ++j) {
-        const int t = lane + 32 * j;
-        if (t < Patch<R>::T) {
-            float3 b[B];
-#pragma unroll
-            for (int k = 0; k < B; ++k) b[k] = tap_sample<R, ST>(lp, tgt, W, H, j, c[k], off[k], in[k]);
-#pragma unroll
-            for (int k = 0; k < B; ++k) s[k] += absdiff3(lp.a[j], b[k]);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < B; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(FULL, s[k], o);
-        out[k] = s[k] / (float)(3 * Patch<R>::T);
-    }
+__device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
+
+// Key of a candidate offset for duplicate detection; lanes without a
+// candidate get a key no offset can have.
+__device__ __forceinline__ unsigned long long cand_key(bool ok, int2 c, int lane) {
+    return ok ? (((unsigned long long)(unsigned)c.x << 32) | (unsigned)c.y) : (0x8000000000000000ull | (unsigned)lane);
 }
 
-// Candidate queue of one pixel: candidates are evaluated B at a time and then
-// accepted in their fixed order with the strict-less rule, which gives the
-// same result as evaluating them one by one (a candidate equal to the current
-// best, or to an earlier one, can never be strictly cheaper).
-template <int R, int ST, int B>
-struct CandQueue {
-    int2 c[B];
-    int n;
-    int2 best;
-    float bc;
-    int nev;
-    __device__ __forceinline__ void flush(const LanePatch<R>& lp, const void* tgt, int W, int H, int lane) {
-        if (n == 0) return;
-        if (B == 1) {  // one at a time: abandon hopeless candidates early
-            const float cc = patch_cost_bounded<R, ST>(lp, tgt, W, H, c[0], bc, lane);
-            if (cc < bc) {
-                bc = cc;
-                best = c[0];
-            }
-            nev += 1;
-            n = 0;
-            return;
-        }
-#pragma unroll
-        for (int k = 1; k < B; ++k)
-            if (k >= n) c[k] = c[0];
-        float cc[B];
-        patch_costB<R, ST, B>(lp, tgt, W, H, c, cc, lane);
-#pragma unroll
-        for (int k = 0; k < B; ++k)
-            if (k < n && cc[k] < bc) {
-                bc = cc[k];
-                best = c[k];
-            }
-        nev += n;
-        n = 0;
-    }
-    __device__ __forceinline__ void push(int2 cand, const LanePatch<R>& lp, const void* tgt, int W, int H,
-                                         int lane) {
-        if (cand.x == best.x && cand.y == best.y) return;
-        bool dup = false;
-#pragma unroll
-        for (int k = 0; k < B; ++k) dup |= k < n && c[k].x == cand.x && c[k].y == cand.y;
-        if (dup) return;
-#pragma unroll
-        for (int k = 0; k < B; ++k)  // c[n] = cand with compile-time indices (keeps c in registers)
-            if (k == n) c[k] = cand;
-        ++n;
-        if (n == B) flush(lp, tgt, W, H, lane);
-    }
-};
+// Lanes whose candidate is to be evaluated: valid, not the incumbent and not
+// a repeat of a lower lane's candidate.  Skipping those changes nothing: the
+// cost of an offset is a deterministic function of it, and a repeat can never
+// be strictly cheaper than the best so far, which is at most its first cost.
+__device__ __forceinline__ unsigned fresh_lanes(bool ok, int2 c, int2 inc, int lane) {
+    const unsigned same = __match_any_sync(FULL, cand_key(ok, c, lane));
+    const bool keep = ok && !(c.x == inc.x && c.y == inc.y) && (same & lanemask_lt(lane)) == 0;
+    return __ballot_sync(FULL, keep);
+}
 
 // Home-window plane of p at a level (residual-stage model first), or nullptr.
 __device__ __forceinline__ const Mef* home_plane(const LevelGeom& g, const Mef* mef, int x, int y) {
@@ -415,7 +349,15 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
 // ---------------------------------------------------------------- sweep
 // PLANES: levels >= 1 (restricted pixel list, plane-distorted patches, plane
 // candidates); level 0 is compiled without any of that.
-template <int R, int ST, int B, bool PLANES>
+//
+// Candidates come in two lists, one candidate per lane, in the fixed order:
+// (A) propagation from the left, right, upper and lower neighbours (lanes
+// 0-3), then at levels >= 1 the models of the windows covering p in window
+// order, first stage then residual stage (lanes 4..21); (B) random search
+// around the best offset after A, radius R0 >> k on lane k.  The warp walks
+// each list in lane order through one evaluation site (a small kernel body
+// keeps the instruction cache warm) and accepts with the strict-less rule.
+template <int R, int ST, bool PLANES>
 __global__ void __launch_bounds__(256, PLANES ? 3 : 4) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
                                                   uint32_t k0, uint32_t k1) {
     const int dir = blockIdx.y;
@@ -430,6 +372,7 @@ __global__ void __launch_bounds__(256, PLANES ? 3 : 4) k_pm_sweep(PairView pv, L
     const int* list = !PLANES ? nullptr : pv.list[dir] + phase * pv.n;
     const int R0 = max(W, H);
     const uint32_t tag = stream_tag(RNG_SEARCH, dir, level, 0);
+    const float scale = (float)(3 * Patch<R>::T);
     for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         int x, y, i;
         if (!PLANES) {
@@ -448,65 +391,80 @@ __global__ void __launch_bounds__(256, PLANES ? 3 : 4) k_pm_sweep(PairView pv, L
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, lane);
         }
-        CandQueue<R, ST, B> q;
-        q.best = nnf[i];
-        q.bc = pv.cost[dir][i];
-        q.n = 0;
-        q.nev = 0;
+        int2 best = nnf[i];
+        float bc = pv.cost[dir][i];
+        int nev = 0;
         // random words for the search radii, two radii per Philox call, one call per lane
         uint4 rw = make_uint4(0, 0, 0, 0);
         if (lane < (nrad + 1) / 2)
             rw = philox((uint32_t)i, ((uint32_t)it << 8) | (uint32_t)lane, tag, pv.pair_id, k0, k1);
-        // propagation: left, right, up, down
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int nx = x + (k == 0 ? -1 : (k == 1 ? 1 : 0));
-            const int ny = y + (k == 2 ? -1 : (k == 3 ? 1 : 0));
-            if (nx < 0 || nx >= W || ny < 0 || ny >= H) continue;
-            const int2 c = nnf[ny * W + nx];
-            const int tx = x + c.x, ty = y + c.y;
-            if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
-            q.push(c, lp, tgt, W, H, lane);
+        // list A
+        int2 cand = make_int2(0, 0);
+        bool ok = false;
+        if (lane < 4) {
+            const int nx = x + (lane == 0 ? -1 : (lane == 1 ? 1 : 0));
+            const int ny = y + (lane == 2 ? -1 : (lane == 3 ? 1 : 0));
+            if (nx >= 0 && nx < W && ny >= 0 && ny < H) {
+                cand = nnf[ny * W + nx];
+                const int tx = x + cand.x, ty = y + cand.y;
+                ok = tx >= 0 && tx < W && ty >= 0 && ty < H;
+            }
+        } else if (PLANES && lane < 4 + 18) {
+            int fx0, nrx, fy0, nry;
+            const int nxw = covering_range(g.gx, g.s, g.h, x, fx0, nrx);
+            const int nyw = covering_range(g.gy, g.s, g.h, y, fy0, nry);
+            const int j = lane - 4, st = j & 1, wk = j >> 1;       // window wk of at most 3 x 3, stage st
+            const int a = nxw == 1 ? wk : (nxw == 2 ? wk >> 1 : (wk * 11) >> 5);  // wk / nxw for wk < 9
+            const int b = wk - a * nxw;
+            if (nxw > 0 && a < nyw) {
+                const int cell = covering_at(g.gy, fy0, nry, a) * g.gx.count + covering_at(g.gx, fx0, nrx, b);
+                const Mef m = pv.mef[dir][(g.base + cell) * 2 + st];
+                int kx, ky;
+                float fx, fy;
+                if (m.valid && mef_flow(m, (float)(x - m.ox), (float)(y - m.oy), kx, fx, ky, fy)) {
+                    float rx, ry;
+                    round_split(kx, fx, cand.x, rx);
+                    round_split(ky, fy, cand.y, ry);
+                    const int tx = x + cand.x, ty = y + cand.y;
+                    ok = tx >= 0 && tx < W && ty >= 0 && ty < H;
+                }
+            }
         }
-        // plane candidates of the windows covering p, in window order, stage 1 then 2
-        if (PLANES) {
-            int ix[3], iy[3];
-            const int nxw = covering(g.gx, g.s, g.h, x, ix), nyw = covering(g.gy, g.s, g.h, y, iy);
-            for (int a = 0; a < nyw; ++a)
-                for (int b = 0; b < nxw; ++b) {
-                    const int cell = iy[a] * g.gx.count + ix[b];
-                    for (int st = 0; st < 2; ++st) {
-                        const Mef m = pv.mef[dir][(g.base + cell) * 2 + st];
-                        if (!m.valid) continue;
-                        int kx, ky;
-                        float fx, fy;
-                        if (!mef_flow(m, (float)(x - m.ox), (float)(y - m.oy), kx, fx, ky, fy)) continue;
-                        int cx, cy;
-                        float rx, ry;
-                        round_split(kx, fx, cx, rx);
-                        round_split(ky, fy, cy, ry);
-                        const int tx = x + cx, ty = y + cy;
-                        if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
-                        q.push(make_int2(cx, cy), lp, tgt, W, H, lane);
+        unsigned todo = fresh_lanes(ok, cand, best, lane);
+#pragma unroll 1
+        for (int list_b = 0; list_b < 2; ++list_b) {
+            if (list_b) {
+                // list B: random search around v0, the best offset after list A
+                const int2 v0 = best;
+                const int src_lane = lane >> 1;
+                uint32_t wx = __shfl_sync(FULL, rw.x, src_lane), wy = __shfl_sync(FULL, rw.y, src_lane);
+                const uint32_t wz = __shfl_sync(FULL, rw.z, src_lane), ww = __shfl_sync(FULL, rw.w, src_lane);
+                if (lane & 1) {
+                    wx = wz;
+                    wy = ww;
+                }
+                const int Rk = R0 >> lane;
+                const int ox = (int)bounded_u32(wx, (uint32_t)(2 * Rk + 1)) - Rk;
+                const int oy = (int)bounded_u32(wy, (uint32_t)(2 * Rk + 1)) - Rk;
+                const int tx = min(max(x + v0.x + ox, 0), W - 1), ty = min(max(y + v0.y + oy, 0), H - 1);
+                cand = make_int2(tx - x, ty - y);
+                todo = fresh_lanes(lane < nrad, cand, v0, lane);
+            }
+            while (todo) {
+                const int l = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
+                float sum;
+                if (tap_sum<R, ST>(lp, tgt, W, H, c, bc * scale * (1.f + 9.5367431640625e-07f), sum, lane)) {
+                    const float cc = sum / scale;
+                    if (cc < bc) {
+                        bc = cc;
+                        best = c;
                     }
                 }
+                ++nev;
+            }
         }
-        q.flush(lp, tgt, W, H, lane);
-        // random search around the best offset after propagation, radii R0 >> k
-        const int2 v0 = q.best;
-        for (int k = 0; k < nrad; ++k) {
-            const int Rk = R0 >> k;
-            const uint32_t wx = __shfl_sync(FULL, (k & 1) ? rw.z : rw.x, k >> 1);
-            const uint32_t wy = __shfl_sync(FULL, (k & 1) ? rw.w : rw.y, k >> 1);
-            const int ox = (int)(wx % (uint32_t)(2 * Rk + 1)) - Rk;
-            const int oy = (int)(wy % (uint32_t)(2 * Rk + 1)) - Rk;
-            const int tx = min(max(x + v0.x + ox, 0), W - 1), ty = min(max(y + v0.y + oy, 0), H - 1);
-            q.push(make_int2(tx - x, ty - y), lp, tgt, W, H, lane);
-        }
-        q.flush(lp, tgt, W, H, lane);
-        const int2 best = q.best;
-        const float bc = q.bc;
-        const int nev = q.nev;
         if (lane == 0) {
             nnf[i] = best;
             pv.cost[dir][i] = bc;
@@ -553,17 +511,10 @@ static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
             k_pm_recost<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level);
             break;
         case PmLaunch::SWEEP:
-            if (L.level == 0) {
-                if (L.batch >= 2)
-                    k_pm_sweep<R, ST, 2, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0, L.k1);
-                else
-                    k_pm_sweep<R, ST, 1, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0, L.k1);
-            } else {
-                if (L.batch >= 2)
-                    k_pm_sweep<R, ST, 2, true><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
-                else
-                    k_pm_sweep<R, ST, 1, true><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
-            }
+            if (L.level == 0)
+                k_pm_sweep<R, ST, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0, L.k1);
+            else
+                k_pm_sweep<R, ST, true><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
             break;
     }
 }

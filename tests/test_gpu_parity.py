@@ -155,6 +155,15 @@ RANSAC_FIELDS = [O.MI_COUNT, O.MI_NIN, O.MI_BESTK, O.MI_BESTSCORE, O.MI_NRC]
 CUE_FIELDS = [O.MI_VALID, O.MI_NASSIGN, O.MI_NSYM]
 
 
+def _label_report(bad, g, o, d, W, k=8):
+    """(x, y, GPU model, oracle model, GPU L, oracle L, GPU flow, oracle flow) of the first k flagged pixels."""
+    out = []
+    for i in np.flatnonzero(bad.reshape(-1))[:k]:
+        out.append((int(i % W), int(i // W), int(g[0][d][i]), int(o.m[i]), float(g[1][d][i]), float(o.L[i]),
+                    tuple(np.round(g[2][d][i], 6)), (round(float(o.fx[i]), 6), round(float(o.fy[i]), 6))))
+    return out
+
+
 def _ransac_equal(gmh, gmi, omh, omi, ids):
     """Per model: the RANSAC outputs (support, input size, winner, refit/geometry flags, colour overlap) and
     H within 1e-6 after normalisation."""
@@ -243,9 +252,14 @@ def test_fit_planes_level1_lockstep(torch, W, H, r, cells):
         for m in ids[~model_ok]:
             ys, xs = _window_box(P, cells, m // 2, 0)
             expl[ys, xs] = True
+        # a many-to-one loss is decided by the lowest (L, index) claimant of the target, and claimants of one
+        # target lie within the motion bound of each other: a loss may differ near an explained pixel
+        lost = (((gcue[d] | cue[d]) & O.CUE_M2O) > 0).reshape(H, W)
+        expl |= dilate(expl, margin) & lost
         for name, g, o in (("stage-1", gs1, S1[d]), ("level", glv, C[d])):
             diff = (g[0][d] != o.m).reshape(H, W)
-            assert not (diff & ~expl).any(), f"dir {d} {name} labels: {int((diff & ~expl).sum())} unexplained"
+            assert not (diff & ~expl).any(), (f"dir {d} {name} labels: {int((diff & ~expl).sum())} unexplained",
+                                              _label_report(diff & ~expl, g, o, d, W))
             assert diff.mean() < 0.05
             # flows and losses where both sides chose the same, identical model
             same = (~diff.reshape(-1)) & (o.m >= 0)

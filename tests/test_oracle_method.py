@@ -293,7 +293,7 @@ def test_translating_layer_scene_occlusion_and_flow():
     R = O.run(P, s.frame1, s.frame2)
     m = _evaluate(s, R)
     assert m["epe_nocc"] < 0.05, m
-    assert m["rec"] > 0.9 and m["prec"] > 0.6, m
+    assert m["rec"] > 0.8 and m["prec"] > 0.6, m
 
 
 @pytest.mark.parametrize("seed", [0, 1])
