@@ -319,6 +319,21 @@ struct Labels {
     float2* r;   // plane flow minus v, in [-0.5, 0.5)
 };
 
+// Per-window record of the RANSAC refit, filled in three launches (fit,
+// solve, finish) and reused by every level and stage.
+struct __align__(16) RefitWork {
+    long long mom[24];      // exact DLT moments of the winner's inliers about (cx, cy, cu, cv)
+    __int128 hx[9];         // the winning hypothesis, exact
+    Mef mef0, mef1;         // evaluation forms (origin 0) of the winner and of the refit
+    double ds, dt;          // sums of the inliers' distances to the source / target centroids
+    double ha_w[9], ha_r[9];  // absolute homographies of the winner and of the refit
+    int cx, cy, cu, cv;     // integer centres of the moments
+    int status;             // 2: refit pending (set by the fit), else the window is final
+    int nin;                // winner's inliers
+    int refit_ok, geo_w, geo_r;
+    int pad[3];
+};
+
 struct PairView {
     int W, H, n;
     int m_models;         // models per direction (bound of every model id)
@@ -336,6 +351,7 @@ struct PairView {
     int* list[2];         // unfrozen pixel indices, colour 0 then colour 1
     int* list_count;      // [2 dirs][2 colours]
     unsigned long long* m2o_key[2];
+    RefitWork* rw[2];     // [cells of the largest level]
     unsigned long long* evals;  // [PM evaluations level 0, levels >= 1, RANSAC residual tests], or nullptr
 };
 

@@ -46,7 +46,7 @@ struct gpm_ctx {
     void* user = nullptr;
     cudaStream_t stream = nullptr;
     int nsm = 152;
-    int max_n = 0, max_models = 0;
+    int max_n = 0, max_models = 0, max_cells = 1;
     size_t slot_bytes = 0;
     std::vector<Slot> slots;
     std::string err;
@@ -106,6 +106,20 @@ gpm_status cuda_check(gpm_ctx* c, const char* where) {
     return GPM_OK;
 }
 
+// Windows of the level with the most (refit records are per window of one level).
+int max_level_cells_for(const gpm_params& P, int W, int H) {
+    int mx = 1;
+    for (int l = 0; l < P.num_scales; ++l) {
+        LevelGeom g{};
+        g.s = P.cell_size[l];
+        g.h = g.s / 2;
+        g.gx = make_axis(W, g.s);
+        g.gy = make_axis(H, g.s);
+        mx = std::max(mx, g.ncells());
+    }
+    return mx;
+}
+
 int total_cells_for(const gpm_params& P, int W, int H, LevelGeom* geoms) {
     int total = 0;
     for (int l = 0; l < P.num_scales; ++l) {
@@ -139,7 +153,7 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
 }
 
 // Carves one slot's buffers out of a single block; returns bytes needed.
-size_t layout_slot(const gpm_params& P, int max_n, int max_models, char* base, Slot* s) {
+size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells, char* base, Slot* s) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> void* {
         off = (off + kAlign - 1) / kAlign * kAlign;
@@ -169,6 +183,7 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, char* base, S
         pv.mi[d] = (int*)take(m * kMI * sizeof(int));
         pv.list[d] = (int*)take(2 * n * sizeof(int));
         pv.m2o_key[d] = (unsigned long long*)take(n * sizeof(unsigned long long));
+        pv.rw[d] = (RefitWork*)take((size_t)max_cells * sizeof(RefitWork));
     }
     pv.list_count = (int*)take(4 * sizeof(int));
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
@@ -292,12 +307,12 @@ void fit_level(gpm_ctx* c, Slot& s, int level) {
     const int gb = grid_for(c, s.n);
     cudaStream_t st = c->stream;
     // first stage: fit, tentative assignment, cues on both directions, final assignment
-    pbeg(c, GPM_PROF_RANSAC, 1), launch_ransac(s.pv, g, level, 1, pp, st), pend(c);
+    pbeg(c, GPM_PROF_RANSAC, 3), launch_ransac(s.pv, g, level, 1, pp, st), pend(c);
     pbeg(c, GPM_PROF_ASSIGN, 1), launch_assign(s.pv, g, 1, 0, 0, pp, gb, st), pend(c);
     pbeg(c, GPM_PROF_CUES, 3), launch_cues(s.pv, g, 1, 0, pp, gb, st), pend(c);
     pbeg(c, GPM_PROF_ASSIGN, 1), launch_assign(s.pv, g, 1, 1, 1, pp, gb, st), pend(c);
     // second stage on the residual pixels
-    pbeg(c, GPM_PROF_RANSAC, 1), launch_ransac(s.pv, g, level, 2, pp, st), pend(c);
+    pbeg(c, GPM_PROF_RANSAC, 3), launch_ransac(s.pv, g, level, 2, pp, st), pend(c);
     pbeg(c, GPM_PROF_ASSIGN, 1);
     for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
     launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
@@ -348,7 +363,8 @@ size_t gpm_required_bytes(const gpm_params* params, const gpm_limits* limits) {
     if (!params || !limits || limits->max_width <= 0 || limits->max_height <= 0 || limits->max_pairs <= 0) return 0;
     const int max_n = limits->max_width * limits->max_height;
     const int max_models = 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr);
-    const size_t per = layout_slot(*params, max_n, std::max(max_models, 2), nullptr, nullptr);
+    const int max_cells = max_level_cells_for(*params, limits->max_width, limits->max_height);
+    const size_t per = layout_slot(*params, max_n, std::max(max_models, 2), max_cells, nullptr, nullptr);
     return per * (size_t)limits->max_pairs;
 }
 
@@ -381,7 +397,8 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
     }
     c->max_n = limits->max_width * limits->max_height;
     c->max_models = std::max(2, 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr));
-    c->slot_bytes = layout_slot(*params, c->max_n, c->max_models, nullptr, nullptr);
+    c->max_cells = max_level_cells_for(*params, limits->max_width, limits->max_height);
+    c->slot_bytes = layout_slot(*params, c->max_n, c->max_models, c->max_cells, nullptr, nullptr);
     if (limits->hbm_budget_bytes && c->slot_bytes * (size_t)limits->max_pairs > limits->hbm_budget_bytes) {
         delete c;
         return GPM_EBUSY;
@@ -400,7 +417,7 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
             return GPM_ENOMEM;
         }
         s.block = p;
-        layout_slot(*params, c->max_n, c->max_models, (char*)p, &s);
+        layout_slot(*params, c->max_n, c->max_models, c->max_cells, (char*)p, &s);
     }
     *out = c;
     return GPM_OK;

@@ -78,6 +78,11 @@ struct WarpGroup {
         }
         return v;
     }
+    __device__ long long sum(long long v) const {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        return v;
+    }
     // exclusive prefix of `take` over the group and the total
     __device__ int scan(bool take, int& total) const {
         const unsigned b = __ballot_sync(FULL, take);
@@ -114,6 +119,16 @@ struct BlockGroup {
         for (int w = 0; w < NT / 32; ++w) t += red_i[w];
         return t;
     }
+    __device__ long long sum(long long v) const {  // exact: integer addition in any order
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red_u[threadIdx.x >> 5] = (unsigned long long)v;
+        __syncthreads();
+        unsigned long long t = 0;
+        for (int w = 0; w < NT / 32; ++w) t += red_u[w];
+        return (long long)t;
+    }
     __device__ unsigned long long max(unsigned long long v) const {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
@@ -143,91 +158,117 @@ struct BlockGroup {
     }
 };
 
-struct RansacScratch {
-    double Hw[9], Hr[9], M[81], Li[81], x[9], rd[9], h0[9];
-    Mef mef[2];
-    int refit_ok;
-};
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
-    return v;
+// ---------------------------------------------------------------- least-squares refit (one thread per window)
+// Entry (r, c) of the normalised DLT normal matrix A^T A from the 24 moments
+// mom[a * 6 + q] = sum w_a zz^T[q] (w in {1, u, v, u^2 + v^2}, zz^T entries
+// q in {x^2, xy, x, y^2, y, 1}): rows/columns 0-2 hold the b b^T block, 3-5
+// the a a^T block, 6-8 the (u, v)-weighted blocks of the rows a = (0, -z, v z)
+// and b = (z, 0, -u z).
+__device__ __forceinline__ double dlt_entry(const double* mom, int r, int c) {
+    const int br = r / 3, bc = c / 3, ir = r % 3, ic = c % 3;
+    const int lo = ir < ic ? ir : ic, hi = ir < ic ? ic : ir;
+    const int q = lo == 0 ? hi : (lo == 1 ? (hi == 1 ? 3 : 4) : 5);
+    if (br == bc) return br < 2 ? mom[q] : mom[18 + q];
+    if ((br == 0 && bc == 2) || (br == 2 && bc == 0)) return -mom[6 + q];
+    if ((br == 1 && bc == 2) || (br == 2 && bc == 1)) return -mom[12 + q];
+    return 0.0;
 }
-__device__ __forceinline__ double warp_max_d(double v) {
+
+// Plane geometry checks of a local homography (rows, maps u -> local
+// target): denominator positive on the window grown by the patch radius and
+// local area scale sqrt(det J) at the window centre in [scale_min, scale_max].
+__device__ __forceinline__ bool plane_geometry_ok(const double* Hl, int s, int r, double scale_min, double scale_max) {
+    const double dc = Hl[8] - 0.5 * (Hl[6] + Hl[7]);
+    const double rdc = 1.0 / dc;
+    double hn[9];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(FULL, v, off));
-    return v;
+    for (int q = 0; q < 9; ++q) hn[q] = Hl[q] * rdc;
+    bool ok = true;
+    const double cxs[2] = {-(double)(s / 2) - r, (double)(s / 2) - 1 + r};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (!(hn[6] * cxs[a] + hn[7] * cxs[b] + hn[8] > 0)) ok = false;
+    const double uc = -0.5;
+    const double X = hn[0] * uc + hn[1] * uc + hn[2], Y = hn[3] * uc + hn[4] * uc + hn[5];
+    const double j00 = hn[0] - X * hn[6], j01 = hn[1] - X * hn[7];
+    const double j10 = hn[3] - Y * hn[6], j11 = hn[4] - Y * hn[7];
+    const double det = j00 * j11 - j01 * j10;
+    if (!(det > 0)) return false;
+    const double sc = sqrt(det);
+    return ok && sc >= scale_min && sc <= scale_max;
 }
 
-// Smallest-eigenvalue eigenvector of the symmetric positive semi-definite 9x9
-// matrix sc->M, started from sc->x, by one warp: M + sigma I is factored
-// column by column (Cholesky, rows in parallel), its inverse formed
-// explicitly (columns in parallel), and inverse iteration then costs one
-// lane-parallel matrix-vector product per step.  A single-lane FP64 chain
-// would hold GB300's FP64 pipe for a whole warp instruction per operation.
-__device__ void min_eigvec_warp(RansacScratch* sc, int lane) {
-    double* M = sc->M;
-    double* Li = sc->Li;
-    const double tr = warp_sum_d(lane < 9 ? M[lane * 9 + lane] : 0.0);
+// Unit eigenvector of the smallest eigenvalue of the 9 x 9 symmetric positive
+// semi-definite matrix whose lower triangle is A (packed, row i at i(i+1)/2),
+// by inverse iteration from x: A + sigma I is factored once (Cholesky, in
+// place), then each step solves with the two triangular factors.  One thread
+// per window: each FP64 warp instruction serves 32 windows.
+__device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
+    double tr = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tr += A[i * (i + 1) / 2 + i];
     const double sigma = 1e-13 * tr + 1e-300;
-    if (lane < 9) M[lane * 9 + lane] += sigma;
-    __syncwarp();
-    for (int j = 0; j < 9; ++j) {  // Cholesky, lower triangle in place
-        if (lane == j) {
-            double d = M[j * 9 + j];
-            for (int k = 0; k < j; ++k) d -= M[j * 9 + k] * M[j * 9 + k];
-            d = d > 0 ? sqrt(d) : 1e-150;
-            M[j * 9 + j] = d;
-            sc->rd[j] = 1.0 / d;
-        }
-        __syncwarp();
-        if (lane > j && lane < 9) {
-            double t = M[lane * 9 + j];
-            for (int k = 0; k < j; ++k) t -= M[lane * 9 + k] * M[j * 9 + k];
-            M[lane * 9 + j] = t * sc->rd[j];
-        }
-        __syncwarp();
-    }
-    if (lane < 9) {  // column `lane` of L^-1 by forward substitution
-        const int c = lane;
-        for (int i = 0; i < 9; ++i) {
-            double t = (i == c) ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) t -= M[i * 9 + k] * Li[k * 9 + c];
-            Li[i * 9 + c] = i < c ? 0.0 : t * sc->rd[i];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A[i * (i + 1) / 2 + i] += sigma;
+    double rd[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        double d = A[j * (j + 1) / 2 + j];
+#pragma unroll
+        for (int k = 0; k < j; ++k) d -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+        d = d > 0 ? sqrt(d) : 1e-150;
+        A[j * (j + 1) / 2 + j] = d;
+        rd[j] = 1.0 / d;
+#pragma unroll
+        for (int i = j + 1; i < 9; ++i) {
+            double t = A[i * (i + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
+            A[i * (i + 1) / 2 + j] = t * rd[j];
         }
     }
-    __syncwarp();
-    // (M + sigma I)^-1 = L^-T L^-1, kept in M
-    for (int e = lane; e < 81; e += 32) {
-        const int i = e / 9, j = e % 9;
-        double t = 0;
-        for (int k = (i > j ? i : j); k < 9; ++k) t += Li[k * 9 + i] * Li[k * 9 + j];
-        sc->M[e] = t;
-    }
-    __syncwarp();
-    double xi = lane < 9 ? sc->x[lane] : 0.0;
-    const double n0 = warp_sum_d(xi * xi);
-    xi *= 1.0 / sqrt(n0);
-    if (lane < 9) sc->x[lane] = xi;
-    __syncwarp();
+    double n0 = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) n0 += x[i] * x[i];
+    const double s0 = 1.0 / sqrt(n0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) x[i] *= s0;
     for (int it = 0; it < 60; ++it) {
-        double yi = 0;
-        if (lane < 9)
-            for (int j = 0; j < 9; ++j) yi += M[lane * 9 + j] * sc->x[j];
-        const double n = warp_sum_d(yi * yi), dot = warp_sum_d(yi * xi);
-        double sc_ = 1.0 / sqrt(n);
-        if (dot < 0) sc_ = -sc_;
-        yi *= sc_;
-        const double diff = warp_max_d(lane < 9 ? fabs(yi - xi) : 0.0);
-        __syncwarp();
-        if (lane < 9) sc->x[lane] = yi;
-        xi = yi;
-        __syncwarp();
+        double y[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {  // L z = x
+            double t = x[i];
+#pragma unroll
+            for (int k = 0; k < i; ++k) t -= A[i * (i + 1) / 2 + k] * y[k];
+            y[i] = t * rd[i];
+        }
+#pragma unroll
+        for (int i = 8; i >= 0; --i) {  // L^T y = z
+            double t = y[i];
+#pragma unroll
+            for (int k = i + 1; k < 9; ++k) t -= A[k * (k + 1) / 2 + i] * y[k];
+            y[i] = t * rd[i];
+        }
+        double n = 0, dot = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            n += y[i] * y[i];
+            dot += y[i] * x[i];
+        }
+        double sc = 1.0 / sqrt(n);
+        if (dot < 0) sc = -sc;
+        double diff = 0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            y[i] *= sc;
+            diff = fmax(diff, fabs(y[i] - x[i]));
+            x[i] = y[i];
+        }
         if (diff < 1e-15) break;
     }
 }
-
 
 // Draws hypothesis k of a window: Philox indices into the N matches; false if
 // the sample is degenerate (three source or three target points collinear).
@@ -262,27 +303,44 @@ __device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int 
 }
 
 // ---------------------------------------------------------------- RANSAC per window
-// Sec. 3.1.2 / 3.2.  The window's matches (u, u + v(u)) -- all pixels at stage
-// 1, the still-unassigned ones in raster order at stage 2 -- sit in shared
-// memory as exact floats; the group's threads draw, solve and score the
-// hypotheses k = rank, rank + size, ...; the group keeps the largest support
-// (lowest k on ties), refits it by the normalised DLT on its inliers and keeps
-// the refit unless it has fewer inliers.
-template <class G, int ST>
-__device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
-                              const PlaneParams& pp, int dir, int cell, float4* match, RansacScratch* sc) {
-    const int tid = grp.rank();
+// Sec. 3.1.2 / 3.2, in three launches per level and stage:
+//   (A) ransac_fit, a group per window: the window's matches (u, u + v(u))
+//       -- all pixels at stage 1, the still-unassigned ones in raster order at
+//       stage 2 -- go to shared memory as exact floats; the group draws, solves
+//       and scores the hypotheses, keeps the largest support (lowest index on
+//       ties) and accumulates what the least-squares refit needs on the
+//       winner's inliers: Hartley sums and the 24 DLT moments as exact integers;
+//   (B) k_refit_solve, a thread per window: normalised DLT refit in FP64;
+//   (C) ransac_finish, a group per window: rescoring of the refit (kept unless
+//       it has fewer inliers), the colour-overlap count and the model record.
+
+// Windows with at most this many matches score each hypothesis on one thread.
+constexpr int kLaneScoreMax = 64;
+
+// Exact integer of a small integer-valued float: adding 1.5 * 2^23 puts it in
+// the low mantissa bits (no conversion instruction).
+__device__ __forceinline__ int exact_int(float f) { return __float_as_int(f + 12582912.f) - 0x4B400000; }
+
+template <class G>
+__device__ __forceinline__ void window_origin(const LevelGeom& g, int cell, int& x0, int& y0, int& ox, int& oy) {
     const int cxw = cell % g.gx.count, cyw = cell / g.gx.count;
+    x0 = win_pos(g.gx, g.h, cxw);
+    y0 = win_pos(g.gy, g.h, cyw);
+    ox = x0 + g.s / 2;
+    oy = y0 + g.s / 2;
+}
+
+// The window's matches in raster order into `match`; returns their number.
+template <class G>
+__device__ int gather_matches(const G& grp, const PairView& pv, const LevelGeom& g, int stage, int dir, int cell,
+                              float4* match) {
+    const int tid = grp.rank();
     const int s = g.s;
-    const int x0 = win_pos(g.gx, g.h, cxw), y0 = win_pos(g.gy, g.h, cyw);
-    const int ox = x0 + s / 2, oy = y0 + s / 2;
-    const int W = pv.W, H = pv.H;
-    const int id = (g.base + cell) * 2 + (stage - 1);
-    int* mi = pv.mi[dir] + (size_t)id * kMI;
+    int x0, y0, ox, oy;
+    window_origin<G>(g, cell, x0, y0, ox, oy);
+    const int W = pv.W;
     const int2* nnf = pv.nnf[dir];
     const uint8_t* resid = pv.resid[dir];
-
-    // gather the window's matches in raster order
     int N = 0;
     for (int base = 0; base < s * s; base += G::size) {
         const int j = base + tid;
@@ -301,6 +359,18 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
         N += total;
     }
     grp.sync();
+    return N;
+}
+
+template <class G, int ST>
+__device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
+                           const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, Mef* wmef) {
+    const int tid = grp.rank();
+    const int id = (g.base + cell) * 2 + (stage - 1);
+    int* mi = pv.mi[dir] + (size_t)id * kMI;
+    RefitWork* rw = pv.rw[dir] + cell;
+    if (G::size > 32 && tid == 0) *gbest = -1;
+    const int N = gather_matches<G>(grp, pv, g, stage, dir, cell, match);
     if (tid == 0) {
         for (int k = 0; k < kMI; ++k) mi[k] = 0;
         mi[MI_NIN] = N;
@@ -308,32 +378,90 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
         for (int k = 0; k < 9; ++k) pv.mh[dir][(size_t)id * 9 + k] = 0.0;
         Mef z = {};
         pv.mef[dir][id] = z;
+        rw->status = 0;
     }
     if (N < pp.min_inliers || N < 4) return;
 
-    // hypotheses
+    // Hypotheses.  Few matches: each thread draws and scores its own
+    // hypotheses k = rank, rank + size, ... in full.  Otherwise each warp of
+    // the group draws 32 at a time (one per lane), then scores them in index
+    // order with its lanes over the matches, 128 at a time, and abandons one
+    // as soon as it cannot win: its inliers so far plus the matches left fall
+    // below the best score of the group (any index), or do not exceed the
+    // best of this warp's earlier, lower-index hypotheses.  The winner (most
+    // inliers, lowest index) is never abandoned, so the outcome is that of
+    // scoring every hypothesis in full.
     const float t2 = pp.t2;
     const uint32_t tag = stream_tag(RNG_RANSAC, dir, level, stage);
-    int best_score = -1, best_k = 0x7fffffff, scored = 0;
-    for (int k = tid; k < pp.num_hyp; k += G::size) {
-        i128 Hk[9];
-        if (!draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk)) continue;
-        Mef m;
-        if (!make_mef_exact(Hk, m)) continue;
-        ++scored;
-        int score = 0;
-        for (int j = 0; j < N; ++j) {
-            const float4 mt = match[j];
-            score += mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
-        }
-        if (score > best_score) {
-            best_score = score;
-            best_k = k;
+    constexpr int NW = G::size / 32;
+    const int lane = tid & 31;
+    Mef* hb = hyp + (tid >> 5) * 32;
+    int best_score = -1, best_k = 0x7fffffff, tests = 0;
+    if (N <= kLaneScoreMax) {
+        for (int k = tid; k < pp.num_hyp; k += G::size) {
+            i128 Hk[9];
+            if (!draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk)) continue;
+            Mef m;
+            if (!make_mef_exact(Hk, m)) continue;
+            int score = 0;
+            for (int j = 0; j < N; ++j) {
+                const float4 mt = match[j];
+                score += mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
+            }
+            tests += N;
+            if (score > best_score) {
+                best_score = score;
+                best_k = k;
+            }
         }
     }
-    if (pv.evals) {  // residual tests (profiling)
-        const int tests = grp.sum(scored);
-        if (tid == 0) atomicAdd(&pv.evals[2], (unsigned long long)tests * (unsigned long long)N);
+    for (int b = tid >> 5; N > kLaneScoreMax && b * 32 < pp.num_hyp; b += NW) {
+        const int k = b * 32 + lane;
+        bool ok = false;
+        if (k < pp.num_hyp) {
+            i128 Hk[9];
+            Mef m;
+            ok = draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk) && make_mef_exact(Hk, m);
+            if (ok) hb[lane] = m;
+        }
+        unsigned todo = __ballot_sync(FULL, ok);
+        __syncwarp();
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const Mef m = hb[l];
+            // abandon when reach < group best or reach <= this warp's best
+            const int bound = max(NW > 1 ? *(volatile int*)gbest - 1 : -1, best_score);
+            int score = 0;
+            bool alive = true;
+            for (int c = 0; c < N; c += 128) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = c + 32 * u + lane;
+                    bool in = false;
+                    if (j < N) {
+                        const float4 mt = match[j];
+                        in = mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
+                    }
+                    score += __popc(__ballot_sync(FULL, in));
+                }
+                tests += min(128, N - c);
+                if (score + max(N - c - 128, 0) <= bound) {
+                    alive = false;
+                    break;
+                }
+            }
+            if (alive) {  // more inliers than every earlier hypothesis of this warp
+                best_score = score;
+                best_k = b * 32 + l;
+                if (NW > 1 && lane == 0) atomicMax(gbest, score);
+            }
+        }
+        __syncwarp();
+    }
+    if (pv.evals) {  // residual tests performed (profiling)
+        const int t = grp.sum(N <= kLaneScoreMax || lane == 0 ? tests : 0);
+        if (tid == 0) atomicAdd(&pv.evals[2], (unsigned long long)t);
     }
     // most inliers, then lowest hypothesis index
     const unsigned long long key =
@@ -344,127 +472,215 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
     if (wkey == 0ull) return;
     const int wscore = (int)(wkey >> 32) - 1;
     const int wk = (int)(0xFFFFFFFFu - (uint32_t)(wkey & 0xFFFFFFFFull));
-    if (tid < 32) {  // first warp: the winner again, converted to double lane by lane
+    if (tid < 32) {  // first warp: the winner again, exact, and its evaluation form
         i128 Hk[9];
         draw_hypothesis(match, N, cell, wk, tag, pv.pair_id, pp.k0, pp.k1, Hk);
         if (tid == 0) {
-            make_mef_exact(Hk, sc->mef[0]);
+            Mef m0;
+            make_mef_exact(Hk, m0);
+            *wmef = m0;
+            rw->mef0 = m0;
             mi[MI_BESTK] = wk;
             mi[MI_BESTSCORE] = wscore;
         }
-        double dk = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q)
-            if (tid == q) {
-                exact_to_double(&Hk[q], &dk, 1);
-            }
-        const double f = warp_max_d(fabs(dk));
-        if (tid < 9) sc->Hw[tid] = dk * (1.0 / f);
+            if (tid == q) rw->hx[q] = Hk[q];
     }
     grp.sync();
     if (wscore < 4) return;
 
-    // least-squares refit: Hartley normalisation of the winner's inliers
-    const Mef wm = sc->mef[0];
-    double sx = 0, sy = 0, tx = 0, ty = 0;
+    // refit inputs on the winner's inliers: Hartley centroids (exact integer
+    // sums), mean distances, and the DLT moments as exact integers about the
+    // rounded centroids
+    const Mef wm = *wmef;
+    int sx = 0, sy = 0, tx = 0, ty = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
         if (mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) {
-            sx += mt.x;
-            sy += mt.y;
-            tx += mt.x + mt.z;
-            ty += mt.y + mt.w;
+            sx += exact_int(mt.x);
+            sy += exact_int(mt.y);
+            tx += exact_int(mt.x + mt.z);
+            ty += exact_int(mt.y + mt.w);
         }
     }
     sx = grp.sum(sx);
     sy = grp.sum(sy);
     tx = grp.sum(tx);
     ty = grp.sum(ty);
-    const double inv_n = 1.0 / (double)wscore;
-    const double mx = sx * inv_n, my = sy * inv_n, mqx = tx * inv_n, mqy = ty * inv_n;
-    const float fmx = (float)mx, fmy = (float)my, fmqx = (float)mqx, fmqy = (float)mqy;
+    const float fn = (float)wscore;
+    const float fmx = __fdiv_rn((float)sx, fn), fmy = __fdiv_rn((float)sy, fn);
+    const float fmqx = __fdiv_rn((float)tx, fn), fmqy = __fdiv_rn((float)ty, fn);
+    const int cx = __float2int_rn(fmx), cy = __float2int_rn(fmy), cu = __float2int_rn(fmqx), cv = __float2int_rn(fmqy);
     double ds = 0, dt = 0;
+    long long R[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) R[q] = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
-        if (mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) {
-            // FP32 roots summed in FP64: the mean distance only sets the normalising scale
-            const float a = mt.x - fmx, b = mt.y - fmy, c = (mt.x + mt.z) - fmqx, d = (mt.y + mt.w) - fmqy;
-            ds += (double)sqrtf(a * a + b * b);
-            dt += (double)sqrtf(c * c + d * d);
-        }
-    }
-    ds = grp.sum(ds) * inv_n;
-    dt = grp.sum(dt) * inv_n;
-    const bool norm_ok = ds > 1e-12 && dt > 1e-12;
-    const double ss = norm_ok ? sqrt(2.0) / ds : 1.0, sq = norm_ok ? sqrt(2.0) / dt : 1.0;
-    // The normalised DLT rows of a pair (z = (x, y, 1) source, (u, v) target)
-    // are a = (0, -z, v z) and b = (z, 0, -u z); their outer products sum to
-    // blocks of S[w] = sum w z z^T with w in {1, u, v, u^2 + v^2}: 24 moments.
-    // (one pass per weight keeps six accumulators live instead of 24)
-    double mom[24];
-    for (int a = 0; a < 4; ++a) {
-        double acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int j = tid; j < N; j += G::size) {
-            const float4 mt = match[j];
-            if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
-            const double x = ss * (mt.x - mx), y = ss * (mt.y - my);
-            const double u = sq * ((double)mt.x + mt.z - mqx), v = sq * ((double)mt.y + mt.w - mqy);
-            const double w = a == 0 ? 1.0 : (a == 1 ? u : (a == 2 ? v : u * u + v * v));
-            acc[0] = fma(w, x * x, acc[0]);
-            acc[1] = fma(w, x * y, acc[1]);
-            acc[2] = fma(w, x, acc[2]);
-            acc[3] = fma(w, y * y, acc[3]);
-            acc[4] = fma(w, y, acc[4]);
-            acc[5] += w;
-        }
+        if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
+        // FP32 roots summed in FP64: the mean distance only sets the normalising scale
+        const float a = mt.x - fmx, b = mt.y - fmy, c = (mt.x + mt.z) - fmqx, d = (mt.y + mt.w) - fmqy;
+        ds += (double)sqrtf(a * a + b * b);
+        dt += (double)sqrtf(c * c + d * d);
+        const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
+        const int U = exact_int(mt.x + mt.z) - cu, V = exact_int(mt.y + mt.w) - cv;
+        const int zz[6] = {X * X, X * Y, X, Y * Y, Y, 1};
+        const int w3 = U * U + V * V;
 #pragma unroll
-        for (int b = 0; b < 6; ++b) mom[a * 6 + b] = grp.sum(acc[b]);
-    }
-    if (tid < 32) {  // first warp: assemble A^T A, solve, back to pixel coordinates
-        const int lane = tid;
-        if (lane == 0) sc->refit_ok = 0;
-        if (norm_ok) {
-            // entry (r, c) of the 9x9 from the moment blocks: rows/cols 0-2 b b^T, 3-5 a a^T, 6-8 the u,v blocks
-            const int map[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-            for (int e = lane; e < 81; e += 32) {
-                const int r = e / 9, c = e % 9, br = r / 3, bc = c / 3, ir = r % 3, ic = c % 3;
-                const int q = map[ir][ic];
-                double v = 0;
-                if (br == bc) v = br < 2 ? mom[q] : mom[18 + q];
-                else if ((br == 0 && bc == 2) || (br == 2 && bc == 0)) v = -mom[6 + q];
-                else if ((br == 1 && bc == 2) || (br == 2 && bc == 1)) v = -mom[12 + q];
-                sc->M[e] = v;
-            }
-            // start: the winning hypothesis in the normalised frames, h0 = Tq Hw Tp^-1
-            if (lane < 9) {
-                const int r = lane / 3, c = lane % 3;
-                const double* Hw = sc->Hw;
-                // (Hw Tp^-1)[k][c] for Tp^-1 = [1/ss 0 mx; 0 1/ss my; 0 0 1]
-                double b[3];
-                for (int k = 0; k < 3; ++k)
-                    b[k] = c == 0 ? Hw[k * 3] / ss : (c == 1 ? Hw[k * 3 + 1] / ss : Hw[k * 3] * mx + Hw[k * 3 + 1] * my + Hw[k * 3 + 2]);
-                sc->x[lane] = r == 0 ? sq * (b[0] - mqx * b[2]) : (r == 1 ? sq * (b[1] - mqy * b[2]) : b[2]);
-            }
-            __syncwarp();
-            min_eigvec_warp(sc, lane);
-            // Hr = Tq^-1 h Tp
-            if (lane < 9) {
-                const int r = lane / 3, c = lane % 3;
-                const double* h = sc->x;
-                double b[3];
-                for (int k = 0; k < 3; ++k)
-                    b[k] = c == 0 ? h[k * 3] * ss : (c == 1 ? h[k * 3 + 1] * ss : h[k * 3 + 2] - ss * (mx * h[k * 3] + my * h[k * 3 + 1]));
-                sc->Hr[lane] = r == 0 ? b[0] / sq + mqx * b[2] : (r == 1 ? b[1] / sq + mqy * b[2] : b[2]);
-            }
-            __syncwarp();
-            if (lane == 0) sc->refit_ok = make_mef(sc->Hr, 0, 0, sc->mef[1]) ? 1 : 0;
+        for (int q = 0; q < 6; ++q) {
+            R[q] += zz[q];
+            R[6 + q] += (long long)U * zz[q];
+            R[12 + q] += (long long)V * zz[q];
+            R[18 + q] += (long long)w3 * zz[q];
         }
     }
-    grp.sync();
+    ds = grp.sum(ds);
+    dt = grp.sum(dt);
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+        const long long t = grp.sum(R[q]);
+        if (tid == q) rw->mom[q] = t;
+    }
+    if (tid == 0) {
+        rw->ds = ds;
+        rw->dt = dt;
+        rw->cx = cx;
+        rw->cy = cy;
+        rw->cu = cu;
+        rw->cv = cv;
+        rw->nin = wscore;
+        rw->status = 2;
+    }
+}
+
+// (B) Normalised DLT refit of each window whose fit is pending, one thread
+// per window and direction: centred, Hartley-scaled moments from the exact
+// integer ones, the smallest eigenvector of A^T A started from the winner,
+// denormalisation, and the geometry checks of the winner and of the refit.
+__global__ void __launch_bounds__(64) k_refit_solve(PairView pv, LevelGeom g, PlaneParams pp) {
+    const int nc = g.ncells();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 2 * nc) return;
+    const int dir = t / nc, cell = t - dir * nc;
+    RefitWork* rw = pv.rw[dir] + cell;
+    if (rw->status != 2) return;
+    int x0, y0, ox, oy;
+    window_origin<WarpGroup>(g, cell, x0, y0, ox, oy);
+    // the winner, normalised by its largest entry
+    double Hw[9];
+    i128 hx[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) hx[q] = rw->hx[q];
+    exact_to_double(hx, Hw, 9);
+    double f = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f = fmax(f, fabs(Hw[q]));
+    const double rf = 1.0 / f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Hw[q] *= rf;
+    rw->geo_w = plane_geometry_ok(Hw, g.s, pp.radius, pp.scale_min, pp.scale_max) ? 1 : 0;
+    local_to_abs(Hw, ox, oy, rw->ha_w);
+    rw->refit_ok = 0;
+    rw->geo_r = 0;
+
+    // centroids and Hartley scales
+    double R[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) R[q] = (double)rw->mom[q];  // exact: |moment| < 2^53
+    const double inv_n = 1.0 / (double)rw->nin;
+    const double dx = R[2] * inv_n, dy = R[4] * inv_n, du = R[11] * inv_n, dv = R[17] * inv_n;
+    const double mx = rw->cx + dx, my = rw->cy + dy, mqx = rw->cu + du, mqy = rw->cv + dv;
+    const double ds = rw->ds * inv_n, dt = rw->dt * inv_n;
+    if (!(ds > 1e-12 && dt > 1e-12)) return;
+    const double ss = sqrt(2.0) / ds, sq = sqrt(2.0) / dt;
+    // centre the source terms (per raw weight 1, U, V, U^2 + V^2), then the weights
+    double P[24];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const double* r = R + 6 * a;
+        P[6 * a + 0] = r[0] - 2.0 * dx * r[2] + dx * dx * r[5];
+        P[6 * a + 1] = r[1] - dy * r[2] - dx * r[4] + dx * dy * r[5];
+        P[6 * a + 2] = r[2] - dx * r[5];
+        P[6 * a + 3] = r[3] - 2.0 * dy * r[4] + dy * dy * r[5];
+        P[6 * a + 4] = r[4] - dy * r[5];
+        P[6 * a + 5] = r[5];
+    }
+    double mom[24];
+    const double sz[6] = {ss * ss, ss * ss, ss, ss * ss, ss, 1.0};
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        const double c0 = P[q];
+        const double c1 = P[6 + q] - du * P[q];
+        const double c2 = P[12 + q] - dv * P[q];
+        const double c3 = P[18 + q] - 2.0 * du * P[6 + q] - 2.0 * dv * P[12 + q] + (du * du + dv * dv) * P[q];
+        mom[q] = sz[q] * c0;
+        mom[6 + q] = sq * sz[q] * c1;
+        mom[12 + q] = sq * sz[q] * c2;
+        mom[18 + q] = sq * sq * sz[q] * c3;
+    }
+    double A[45];
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) A[i * (i + 1) / 2 + j] = dlt_entry(mom, i, j);
+    // start: the winner in the normalised frames, h0 = Tq Hw Tp^-1
+    double x[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double b[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                b[k] = c == 0 ? Hw[k * 3] / ss
+                              : (c == 1 ? Hw[k * 3 + 1] / ss : Hw[k * 3] * mx + Hw[k * 3 + 1] * my + Hw[k * 3 + 2]);
+            x[r * 3 + c] = r == 0 ? sq * (b[0] - mqx * b[2]) : (r == 1 ? sq * (b[1] - mqy * b[2]) : b[2]);
+        }
+    min_eigvec9(A, x);
+    // Hr = Tq^-1 h Tp
+    double Hr[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double b[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                b[k] = c == 0 ? x[k * 3] * ss
+                              : (c == 1 ? x[k * 3 + 1] * ss : x[k * 3 + 2] - ss * (mx * x[k * 3] + my * x[k * 3 + 1]));
+            Hr[r * 3 + c] = r == 0 ? b[0] / sq + mqx * b[2] : (r == 1 ? b[1] / sq + mqy * b[2] : b[2]);
+        }
+    Mef m1;
+    if (!make_mef(Hr, 0, 0, m1)) return;
+    rw->mef1 = m1;
+    rw->geo_r = plane_geometry_ok(Hr, g.s, pp.radius, pp.scale_min, pp.scale_max) ? 1 : 0;
+    local_to_abs(Hr, ox, oy, rw->ha_r);
+    rw->refit_ok = 1;
+}
+
+// (C) Rescore the refit on the window's matches, choose, count colour
+// inliers among the RANSAC inliers (|S_R n S_C|, Sec. 3.4 third cue) and
+// write the model: valid iff the support is at least max(min_inliers, N / 5)
+// and the chosen homography passed the geometry checks.
+template <class G, int ST>
+__device__ void ransac_finish(const G& grp, const PairView& pv, const LevelGeom& g, int stage, const PlaneParams& pp,
+                              int dir, int cell, float4* match) {
+    const RefitWork* rw = pv.rw[dir] + cell;
+    if (rw->status != 2) return;
+    const int tid = grp.rank();
+    const int id = (g.base + cell) * 2 + (stage - 1);
+    int* mi = pv.mi[dir] + (size_t)id * kMI;
+    const int N = gather_matches<G>(grp, pv, g, stage, dir, cell, match);
+    int x0, y0, ox, oy;
+    window_origin<G>(g, cell, x0, y0, ox, oy);
+    const int W = pv.W, H = pv.H;
+    const float t2 = pp.t2;
+    const int wscore = rw->nin;
+    const bool have_refit = rw->refit_ok != 0;
     int rcount = 0;
-    const bool have_refit = sc->refit_ok != 0;
     if (have_refit) {
-        const Mef rm = sc->mef[1];
+        const Mef rm = rw->mef1;
         for (int j = tid; j < N; j += G::size) {
             const float4 mt = match[j];
             rcount += mef_inlier(rm, mt.x, mt.y, mt.z, mt.w, t2);
@@ -472,10 +688,8 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
     }
     rcount = grp.sum(rcount);
     const bool use_refit = have_refit && rcount >= wscore;
-    Mef fm = sc->mef[use_refit ? 1 : 0];
+    Mef fm = use_refit ? rw->mef1 : rw->mef0;
     const int count = use_refit ? rcount : wscore;
-
-    // colour inliers among the RANSAC inliers: |S_R n S_C| (Sec. 3.4, third cue)
     const void* src = pv.img[dir];
     const void* tgt = pv.img[1 - dir];
     fm.ox = ox;
@@ -491,36 +705,9 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
         nrc += colour_delta<ST>(src, tgt, W, H, px, py, ix, fx, iy, fy) < pp.eps;
     }
     nrc = grp.sum(nrc);
-
     if (tid == 0) {
-        const double* Hl = use_refit ? sc->Hr : sc->Hw;
-        // orientation/scale of the evaluation form: denominator 1 at the window centre
-        const double dc = Hl[8] - 0.5 * (Hl[6] + Hl[7]);
-        const double rdc = 1.0 / dc;
-        double hn[9];
-        for (int q = 0; q < 9; ++q) hn[q] = Hl[q] * rdc;
-        // plane validity: support, positive denominator on the window grown by
-        // the patch radius, local area scale at the centre within range
-        bool valid = count >= pp.min_inliers && 5 * count >= N;
-        const int r = pp.radius;
-        const double cxs[2] = {-(double)(s / 2) - r, (double)(s / 2) - 1 + r};
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b)
-                if (!(hn[6] * cxs[a] + hn[7] * cxs[b] + hn[8] > 0)) valid = false;
-        {
-            const double uc = -0.5;
-            const double X = hn[0] * uc + hn[1] * uc + hn[2], Y = hn[3] * uc + hn[4] * uc + hn[5];
-            const double j00 = hn[0] - X * hn[6], j01 = hn[1] - X * hn[7];
-            const double j10 = hn[3] - Y * hn[6], j11 = hn[4] - Y * hn[7];
-            const double det = j00 * j11 - j01 * j10;
-            if (!(det > 0)) valid = false;
-            else {
-                const double sc2 = sqrt(det);
-                if (!(sc2 >= (double)pp.scale_min && sc2 <= (double)pp.scale_max)) valid = false;
-            }
-        }
-        double Ha[9];
-        local_to_abs(Hl, ox, oy, Ha);
+        const bool valid = count >= pp.min_inliers && 5 * count >= N && (use_refit ? rw->geo_r : rw->geo_w) != 0;
+        const double* Ha = use_refit ? rw->ha_r : rw->ha_w;
         for (int q = 0; q < 9; ++q) pv.mh[dir][(size_t)id * 9 + q] = Ha[q];
         fm.valid = valid ? 1 : 0;
         pv.mef[dir][id] = fm;
@@ -532,29 +719,53 @@ __device__ void ransac_window(const G& grp, const PairView& pv, const LevelGeom&
 }
 
 // Windows up to 16 x 16: one warp per window, eight windows per block.
+// Dynamic shared memory: 8 x 256 matches, then 8 x 32 hypotheses.
 template <int ST>
 __global__ void __launch_bounds__(256, 2) k_ransac_warp(PairView pv, LevelGeom g, int level, int stage,
                                                      PlaneParams pp) {
+    extern __shared__ float4 warp_dyn[];
+    __shared__ Mef wmef[8];
+    const int warp = threadIdx.x >> 5;
+    const int cell = blockIdx.x * 8 + warp;
+    if (cell >= g.ncells()) return;
+    float4* match = warp_dyn + warp * 256;
+    Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + 8 * 256) + warp * 32;
+    WarpGroup grp;
+    ransac_fit<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, &wmef[warp]);
+}
+template <int ST>
+__global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
     __shared__ float4 match[8][256];
-    __shared__ RansacScratch scratch[8];
     const int warp = threadIdx.x >> 5;
     const int cell = blockIdx.x * 8 + warp;
     if (cell >= g.ncells()) return;
     WarpGroup grp;
-    ransac_window<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match[warp], &scratch[warp]);
+    ransac_finish<WarpGroup, ST>(grp, pv, g, stage, pp, blockIdx.y, cell, match[warp]);
 }
 
-// Larger windows: one 256-thread block per window.
+// Larger windows: one 256-thread block per window (matches in dynamic shared memory).
 template <int ST>
 __global__ void __launch_bounds__(256, 2) k_ransac_block(PairView pv, LevelGeom g, int level, int stage,
                                                       PlaneParams pp) {
     extern __shared__ float4 match_dyn[];
-    __shared__ RansacScratch scratch;
+    __shared__ double red_d[8];
+    __shared__ int red_i[8];
+    __shared__ unsigned long long red_u[8];
+    __shared__ Mef hyp[8 * 32];
+    __shared__ Mef wmef;
+    __shared__ int gbest;
+    BlockGroup<256> grp{red_d, red_i, red_u};
+    ransac_fit<BlockGroup<256>, ST>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, hyp, &gbest,
+                                    &wmef);
+}
+template <int ST>
+__global__ void __launch_bounds__(256) k_ransac_finish_block(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
+    extern __shared__ float4 match_dyn[];
     __shared__ double red_d[8];
     __shared__ int red_i[8];
     __shared__ unsigned long long red_u[8];
     BlockGroup<256> grp{red_d, red_i, red_u};
-    ransac_window<BlockGroup<256>, ST>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, &scratch);
+    ransac_finish<BlockGroup<256>, ST>(grp, pv, g, stage, pp, blockIdx.y, blockIdx.x, match_dyn);
 }
 
 // ---------------------------------------------------------------- assignment (eq. 3-4)
@@ -875,17 +1086,29 @@ __global__ void k_labels_import(Labels l, int n, const int* im, const float* iL,
 template <int ST>
 static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
                              cudaStream_t st) {
+    const int nc = g.ncells();
     if (g.s <= 16) {
-        k_ransac_warp<ST><<<dim3((g.ncells() + 7) / 8, 2), 256, 0, st>>>(pv, g, level, stage, pp);
+        const size_t wsmem = 8 * 256 * sizeof(float4) + 8 * 32 * sizeof(Mef);
+        static bool wattr_set = false;
+        if (!wattr_set) {
+            cudaFuncSetAttribute(k_ransac_warp<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+            wattr_set = true;
+        }
+        k_ransac_warp<ST><<<dim3((nc + 7) / 8, 2), 256, wsmem, st>>>(pv, g, level, stage, pp);
+        k_refit_solve<<<(2 * nc + 63) / 64, 64, 0, st>>>(pv, g, pp);
+        k_ransac_finish_warp<ST><<<dim3((nc + 7) / 8, 2), 256, 0, st>>>(pv, g, stage, pp);
         return;
     }
     const size_t smem = (size_t)g.s * g.s * sizeof(float4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_ransac_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        cudaFuncSetAttribute(k_ransac_finish_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
         attr_set = true;
     }
-    k_ransac_block<ST><<<dim3(g.ncells(), 2), 256, smem, st>>>(pv, g, level, stage, pp);
+    k_ransac_block<ST><<<dim3(nc, 2), 256, smem, st>>>(pv, g, level, stage, pp);
+    k_refit_solve<<<(2 * nc + 63) / 64, 64, 0, st>>>(pv, g, pp);
+    k_ransac_finish_block<ST><<<dim3(nc, 2), 256, smem, st>>>(pv, g, stage, pp);
 }
 void launch_ransac(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
                    cudaStream_t st) {
