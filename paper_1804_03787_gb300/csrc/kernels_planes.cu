@@ -195,16 +195,30 @@ __device__ __forceinline__ bool plane_geometry_ok(const double* Hl, int s, int r
     const double j00 = hn[0] - X * hn[6], j01 = hn[1] - X * hn[7];
     const double j10 = hn[3] - Y * hn[6], j11 = hn[4] - Y * hn[7];
     const double det = j00 * j11 - j01 * j10;
-    if (!(det > 0)) return false;
-    const double sc = sqrt(det);
-    return ok && sc >= scale_min && sc <= scale_max;
+    // sqrt(det) in [scale_min, scale_max], compared without the root
+    return ok && det > 0 && det >= scale_min * scale_min && det <= scale_max * scale_max;
+}
+
+// 1 / sqrt(n) for a positive normal double: an FP32 estimate refined by two
+// Newton steps (relative error ~1e-16), far fewer FP64 operations than a
+// correctly rounded square root and division.  Inverse iteration only needs a
+// scale close to the unit norm.
+__device__ __forceinline__ double rsqrt_nr(double n) {
+    if (!(n > 1e-30 && n < 1e30)) return 1.0 / sqrt(n);  // outside the FP32 estimate's range
+    double r = (double)rsqrtf((float)n);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) r = fma(0.5 * r, fma(-n * r, r, 1.0), r);
+    return r;
 }
 
 // Unit eigenvector of the smallest eigenvalue of the 9 x 9 symmetric positive
 // semi-definite matrix whose lower triangle is A (packed, row i at i(i+1)/2),
-// by inverse iteration from x: A + sigma I is factored once (Cholesky, in
-// place), then each step solves with the two triangular factors.  One thread
-// per window: each FP64 warp instruction serves 32 windows.
+// by inverse iteration from x.  A + sigma I is factored once (Cholesky) and
+// its inverse formed explicitly (L^-T L^-1), so each step is one product with
+// it.  Most of the convergence happens in FP32 (an FP32 warp instruction
+// issues in a cycle, an FP64 one holds this GPU's FP64 pipe for about 64),
+// then FP64 steps polish the direction.  One thread per window: each FP64 warp
+// instruction serves 32 windows.
 __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
     double tr = 0;
 #pragma unroll
@@ -229,27 +243,89 @@ __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
             A[i * (i + 1) / 2 + j] = t * rd[j];
         }
     }
-    double n0 = 0;
+    double Li[45];  // L^-1, lower triangular
 #pragma unroll
-    for (int i = 0; i < 9; ++i) n0 += x[i] * x[i];
-    const double s0 = 1.0 / sqrt(n0);
+    for (int j = 0; j < 9; ++j) {
+        Li[j * (j + 1) / 2 + j] = rd[j];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) x[i] *= s0;
+        for (int i = j + 1; i < 9; ++i) {
+            double t = 0;
+#pragma unroll
+            for (int k = j; k < i; ++k) t -= A[i * (i + 1) / 2 + k] * Li[k * (k + 1) / 2 + j];
+            Li[i * (i + 1) / 2 + j] = t * rd[i];
+        }
+    }
+    // (A + sigma I)^-1 = Li^T Li, lower triangle into A
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double t = 0;
+#pragma unroll
+            for (int k = i; k < 9; ++k) t += Li[k * (k + 1) / 2 + i] * Li[k * (k + 1) / 2 + j];
+            A[i * (i + 1) / 2 + j] = t;
+        }
+    auto sym = [](int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; };
+    {  // FP32 steps with the rounded inverse (scaled well inside range) until the direction settles
+        float trs = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) trs += (float)A[i * (i + 1) / 2 + i];
+        const float rs = trs > 0.f ? 1.f / trs : 1.f;
+        float Af[45], xf[9];
+#pragma unroll
+        for (int q = 0; q < 45; ++q) Af[q] = (float)A[q] * rs;
+        float n0 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            xf[i] = (float)x[i];
+            n0 = fmaf(xf[i], xf[i], n0);
+        }
+        const float s0 = rsqrtf(n0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) xf[i] *= s0;
+        for (int it = 0; it < 400; ++it) {
+            float y[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                float t = 0.f;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) t = fmaf(Af[sym(i, j)], xf[j], t);
+                y[i] = t;
+            }
+            float n = 0.f, dot = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                n = fmaf(y[i], y[i], n);
+                dot = fmaf(y[i], xf[i], dot);
+            }
+            if (!(n > 0.f) || !isfinite(n)) break;
+            float sc = rsqrtf(n);
+            if (dot < 0.f) sc = -sc;
+            float diff = 0.f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                y[i] *= sc;
+                diff = fmaxf(diff, fabsf(y[i] - xf[i]));
+                xf[i] = y[i];
+            }
+            if (diff < 4e-7f) break;
+        }
+        bool finite = true;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) finite = finite && isfinite(xf[i]);
+        if (finite) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) x[i] = (double)xf[i];
+        }
+    }
     for (int it = 0; it < 60; ++it) {
         double y[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {  // L z = x
-            double t = x[i];
+        for (int i = 0; i < 9; ++i) {
+            double t = 0;
 #pragma unroll
-            for (int k = 0; k < i; ++k) t -= A[i * (i + 1) / 2 + k] * y[k];
-            y[i] = t * rd[i];
-        }
-#pragma unroll
-        for (int i = 8; i >= 0; --i) {  // L^T y = z
-            double t = y[i];
-#pragma unroll
-            for (int k = i + 1; k < 9; ++k) t -= A[k * (k + 1) / 2 + i] * y[k];
-            y[i] = t * rd[i];
+            for (int j = 0; j < 9; ++j) t += A[sym(i, j)] * x[j];
+            y[i] = t;
         }
         double n = 0, dot = 0;
 #pragma unroll
@@ -257,7 +333,7 @@ __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
             n += y[i] * y[i];
             dot += y[i] * x[i];
         }
-        double sc = 1.0 / sqrt(n);
+        double sc = rsqrt_nr(n);
         if (dot < 0) sc = -sc;
         double diff = 0;
 #pragma unroll
@@ -266,7 +342,10 @@ __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
             diff = fmax(diff, fabs(y[i] - x[i]));
             x[i] = y[i];
         }
-        if (diff < 1e-15) break;
+        // 1e-12 is far below what the rescore (1e-5 near-tie band) and the
+        // model comparison (1e-6) can see, and above the ~1e-15 rounding
+        // noise of the iteration on matrices conditioned near 1e13
+        if (diff < 1e-12) break;
     }
 }
 
@@ -594,6 +673,7 @@ __global__ void __launch_bounds__(64) k_refit_solve(PairView pv, LevelGeom g, Pl
     const double ds = rw->ds * inv_n, dt = rw->dt * inv_n;
     if (!(ds > 1e-12 && dt > 1e-12)) return;
     const double ss = sqrt(2.0) / ds, sq = sqrt(2.0) / dt;
+    const double iss = ds * 0.70710678118654752440, isq = dt * 0.70710678118654752440;  // 1 / ss, 1 / sq
     // centre the source terms (per raw weight 1, U, V, U^2 + V^2), then the weights
     double P[24];
 #pragma unroll
@@ -633,8 +713,8 @@ __global__ void __launch_bounds__(64) k_refit_solve(PairView pv, LevelGeom g, Pl
             double b[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k)
-                b[k] = c == 0 ? Hw[k * 3] / ss
-                              : (c == 1 ? Hw[k * 3 + 1] / ss : Hw[k * 3] * mx + Hw[k * 3 + 1] * my + Hw[k * 3 + 2]);
+                b[k] = c == 0 ? Hw[k * 3] * iss
+                              : (c == 1 ? Hw[k * 3 + 1] * iss : Hw[k * 3] * mx + Hw[k * 3 + 1] * my + Hw[k * 3 + 2]);
             x[r * 3 + c] = r == 0 ? sq * (b[0] - mqx * b[2]) : (r == 1 ? sq * (b[1] - mqy * b[2]) : b[2]);
         }
     min_eigvec9(A, x);
@@ -649,7 +729,7 @@ __global__ void __launch_bounds__(64) k_refit_solve(PairView pv, LevelGeom g, Pl
             for (int k = 0; k < 3; ++k)
                 b[k] = c == 0 ? x[k * 3] * ss
                               : (c == 1 ? x[k * 3 + 1] * ss : x[k * 3 + 2] - ss * (mx * x[k * 3] + my * x[k * 3 + 1]));
-            Hr[r * 3 + c] = r == 0 ? b[0] / sq + mqx * b[2] : (r == 1 ? b[1] / sq + mqy * b[2] : b[2]);
+            Hr[r * 3 + c] = r == 0 ? b[0] * isq + mqx * b[2] : (r == 1 ? b[1] * isq + mqy * b[2] : b[2]);
         }
     Mef m1;
     if (!make_mef(Hr, 0, 0, m1)) return;

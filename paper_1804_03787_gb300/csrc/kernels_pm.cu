@@ -230,17 +230,27 @@ __device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* 
     return s / (float)(3 * Patch<R>::T);
 }
 
+// Integer threshold for the abandon test of tap_sum: with thr the best raw
+// sum so far times 3T (raised by 2^-20 for the rounding of that product),
+// returns ceil(thr * 2^19 * (1 + 2^-21)).  The extra 2^-21 covers the five
+// rounded additions of the warp's final float sum (each loses at most 2^-24).
+__device__ __forceinline__ int abandon_threshold(float thr) {
+    return __float2int_ru(__fmul_ru(thr * 524288.f, 1.f + 4.76837158203125e-07f));
+}
+
 // Raw tap sum of candidate offset c (over taps and channels of |difference|,
 // before the division by 3T), abandoned once it cannot win.  After each
-// 32-tap chunk the warp sums what it has; the terms are non-negative and FP32
-// addition is monotonic, so a partial sum at or above `thr` (the best cost so
-// far times 3T, raised by 2^-20 to absorb the rounding of that product) bounds
-// the full cost at or above the best, and the strict-less test would reject
-// the candidate anyway: the function returns false.  Each lane accumulates
-// its taps in the same order as patch_cost, so a full sum divided by 3T gives
-// bitwise the same cost.
+// 32-tap chunk every lane floors its partial sum to a multiple of 2^-19 and
+// the warp adds those integers exactly (one redux): a lower bound of the
+// exact partial sum.  The terms are non-negative and FP32 addition is
+// monotonic, so the final float sum is at least the exact partial sum less
+// the rounding of five additions; a bound at or above `ithr`
+// (abandon_threshold) therefore means the full cost is at or above the best,
+// and the strict-less test would reject the candidate anyway: the function
+// returns false.  Each lane accumulates its taps in the same order as
+// patch_cost, so a full sum divided by 3T gives bitwise the same cost.
 template <int R, int ST>
-__device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, float thr,
+__device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int lane) {
     const bool in = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c, W, H);
     const int off = c.y * W + c.x;
@@ -249,12 +259,16 @@ __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt,
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
         if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST>(lp, tgt, W, H, j, c, off, in));
-        float p = s;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
         if (j + 1 < Patch<R>::NT) {
-            if (!(p < thr)) return false;
+            // floor(min(s * 2^19, 2^23 - 1)): exact scaling, clamp (keeps a lower bound), truncation in the
+            // mantissa of 2^23
+            const unsigned q =
+                (unsigned)(__float_as_int(__fadd_rz(fminf(s * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
+            if ((int)__reduce_add_sync(FULL, q) >= ithr) return false;
         } else {
+            float p = s;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
             sum = p;
         }
     }
@@ -358,7 +372,7 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
 // each list in lane order through one evaluation site (a small kernel body
 // keeps the instruction cache warm) and accepts with the strict-less rule.
 template <int R, int ST, bool PLANES>
-__global__ void __launch_bounds__(256, PLANES ? 3 : 4) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
+__global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
                                                   uint32_t k0, uint32_t k1) {
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
@@ -455,7 +469,8 @@ __global__ void __launch_bounds__(256, PLANES ? 3 : 4) k_pm_sweep(PairView pv, L
                 todo &= todo - 1;
                 const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
                 float sum;
-                if (tap_sum<R, ST>(lp, tgt, W, H, c, bc * scale * (1.f + 9.5367431640625e-07f), sum, lane)) {
+                if (tap_sum<R, ST>(lp, tgt, W, H, c, abandon_threshold(bc * scale * (1.f + 9.5367431640625e-07f)), sum,
+                                   lane)) {
                     const float cc = sum / scale;
                     if (cc < bc) {
                         bc = cc;
