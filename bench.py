@@ -206,6 +206,100 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched and served forms
+BATCH_PAIRS, BATCH_DISTINCT = 64, 16
+SERVE_RATE_HZ, SERVE_TRACE_S, SERVE_POOL, SERVE_SLOTS = 200.0, 1.0, 8, 16
+
+
+def extras_start(workers: int):
+    """Starts rendering the batched and serving scenes on the host cores (spawned workers) while the GPU runs
+    the headline workload."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from paper_1804_03787_gb300 import batch, serve
+    ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+    fb = [ex.submit(batch.make_scene_from_spec, s) for s in batch.batch_specs(BATCH_DISTINCT, seed=0)]
+    fs = [ex.submit(batch.make_scene_from_spec, s) for s in serve.serving_specs(SERVE_POOL, seed=0)]
+    return ex, fb, fs
+
+
+def batched_block(scenes):
+    """64 pairs of mixed sizes: the plain FP32 form (one stream, eager launches) against the batched form (BF16
+    storage, FP32 accumulation, autotuned streams, CUDA graphs), with EPE against ground truth for both."""
+    import numpy as np
+    import torch
+
+    from paper_1804_03787_gb300 import batch, gpm
+    which = [k % len(scenes) for k in range(BATCH_PAIRS)]
+    frames = [(scenes[w].frame1, scenes[w].frame2) for w in which]
+    gt = [scenes[w].flow for w in which]
+    ids = list(range(BATCH_PAIRS))
+    gp32 = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP)
+    plain = batch.BatchRunner(gp32, frames, ids, streams=1, graph=False)
+    plain.run()
+    t_plain = plain.time(1)
+    r32 = plain.results()
+    plain.close()
+    del plain
+    torch.cuda.empty_cache()
+    gpb = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=gpm.GPM_BF16)
+    best, tune = batch.autotune_streams(gpb, frames, ids, candidates=(2, 4, 8))
+    r = batch.BatchRunner(gpb, frames, ids, streams=best, graph=True)
+    r.run()
+    t = r.time(2)
+    rb = r.results()
+    r.close()
+    del r
+    torch.cuda.empty_cache()
+    # EPE over ground-truth non-occluded pixels: occluded pixels keep their NNF offset (no interpolation)
+    nocc = [scenes[w].occ == 0 for w in which]
+    e32 = float(np.mean([batch.epe(r32[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
+    eb = float(np.mean([batch.epe(rb[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
+    sizes = sorted({(s.frame1.shape[1], s.frame1.shape[0]) for s in scenes})
+    return {"value": BATCH_PAIRS / t, "unit": "pairs/s", "pairs": BATCH_PAIRS,
+            "workload": f"{BATCH_PAIRS} pairs from {len(scenes)} seeded scenes, sizes uniform over "
+                        f"{[f'{w}x{h}' for w, h in batch.BATCH_SIZES]} (drawn: {[f'{w}x{h}' for w, h in sizes]}), "
+                        "3-8 planar layers, motion up to 96 px",
+            "storage": "bf16", "accumulation": "f32", "streams": best, "cuda_graph": True,
+            "autotune_ms_per_pass": {str(k): v * 1e3 for k, v in tune.items()},
+            "plain_f32": {"value": BATCH_PAIRS / t_plain, "unit": "pairs/s", "streams": 1, "cuda_graph": False},
+            "speedup_vs_plain_f32": t_plain / t,
+            "epe_nocc_px": {"plain_f32": e32, "batched_bf16": eb, "abs_diff": abs(eb - e32),
+                            "pixels": "ground-truth non-occluded, mean over the pairs"},
+            "l2": "inputs of one pass (> 1 GB of frames and state) exceed L2"}
+
+
+def serving_block(scenes):
+    """Poisson arrivals of pairs of log-uniform sizes served by continuous batching (BF16 storage)."""
+    from paper_1804_03787_gb300 import gpm, serve
+    gpb = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=gpm.GPM_BF16)
+    pool = [(s.frame1, s.frame2) for s in scenes]
+    mw = max(f.shape[1] for f, _ in pool)
+    mh = max(f.shape[0] for f, _ in pool)
+    per = serve.slot_bytes(gpb, mw, mh) + mw * mh * 33
+    srv = serve.Server(gpb, mw, mh, hbm_budget_bytes=SERVE_SLOTS * per, max_slots=SERVE_SLOTS)
+    warm = [serve.Request(rid=k, arrival=0.0, frame1=f1, frame2=f2, pair_id=100000 + k)
+            for k, (f1, f2) in enumerate(pool)]
+    srv.run(warm, realtime=False)
+    trace = serve.poisson_trace(SERVE_RATE_HZ, SERVE_TRACE_S, pool, seed=0)
+    st = srv.run(trace, realtime=True)
+    # the same pool offered at half the throughput just measured: latency without a standing queue
+    rate = max(1.0, 0.5 * st["pairs_per_s"])
+    dur = max(2.0, 24.0 / rate)
+    st2 = srv.run(serve.poisson_trace(rate, dur, pool, seed=1), realtime=True)
+    srv.close()
+    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "pairs_per_s": st["pairs_per_s"],
+            "requests": st["requests"], "offered_rate_hz": SERVE_RATE_HZ, "trace_s": SERVE_TRACE_S,
+            "note": "the offered rate exceeds the throughput, so these latencies are mostly queueing",
+            "below_capacity": {"offered_rate_hz": rate, "trace_s": dur, "requests": st2["requests"],
+                               "p50_ms": st2["p50_ms"], "p99_ms": st2["p99_ms"], "pairs_per_s": st2["pairs_per_s"]},
+            "slots": st["slots"], "storage": "bf16",
+            "workload": f"Poisson arrivals (seed 0) over a pool of {len(pool)} seeded scenes, sizes log-uniform "
+                        "320x240 to 1920x1080, 4-10 planar layers, motion up to 128 px",
+            "latency": "arrival to flow and occlusion in host memory (host frames copied in per request)"}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -228,6 +322,9 @@ def run_ours(args):
     except Exception:
         pass
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = extras_start(max(1, min(16, (os.cpu_count() or 2) - 2)))
     # inputs: seeded benchmark scenes, resident in HBM before timing
     nscenes = 3
     scenes = [scene.benchmark_scene(100 * rank + k) for k in range(nscenes)]
@@ -310,6 +407,16 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = max_over_ranks(sum(e2e_times), dist, "cuda")
+    # accuracy of the last end-to-end step against the scenes' ground truth
+    import numpy as np
+    acc = []
+    for j in range(P):
+        sc = scenes[((args.steps - 1) * P + j) % nscenes]
+        e = np.sqrt(((pin_flow[j].numpy() - sc.flow) ** 2).sum(-1))
+        nocc = sc.occ == 0
+        o = pin_occ[j].numpy() > 0
+        acc.append((float(e[nocc].mean()), float(np.median(e[nocc])), float((o & (sc.occ > 0)).sum() / max(1, o.sum())),
+                    float((o & (sc.occ > 0)).sum() / max(1, (sc.occ > 0).sum()))))
     h2d = P * 2 * W * H * 3 * 4
     d2h = P * (W * H * 2 * 4 + W * H)
 
@@ -326,14 +433,29 @@ def run_ours(args):
             "roofline": roof,
             "e2e": {"value": job_throughput(args.steps * P, ws, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "clocks": clocks}
+            "gpu_launches": launches, "clocks": clocks,
+            "accuracy": {"epe_nocc_px": float(np.mean([a[0] for a in acc])),
+                         "median_error_nocc_px": float(np.mean([a[1] for a in acc])),
+                         "occlusion_precision": float(np.mean([a[2] for a in acc])),
+                         "occlusion_recall": float(np.mean([a[3] for a in acc])),
+                         "against": "the synthetic scenes' exact flow and occlusion (last end-to-end step)"}}
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    if extras is not None:
+        ex, fb, fs = extras
+        for key, fut, fn in (("batched", fb, batched_block), ("serving", fs, serving_block)):
+            try:
+                line[key] = fn([f.result() for f in fut])
+            except Exception as e:  # reported, never fatal for the headline line
+                line[key] = {"error": f"{type(e).__name__}: {e}"}
+        ex.shutdown()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import build as ob
         ob.build()
         line["cpu_baseline"] = cpu_baseline_block(scenes[0])
     if rank == 0:
         print(json.dumps(line))
-    ctx.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -348,6 +470,7 @@ def main():
     ap.add_argument("--pairs", type=int, default=1, help="frame pairs per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served forms")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -244,7 +244,7 @@ gpm_status set_dims(gpm_ctx* c, Slot& s, int W, int H) {
     s.pv.H = H;
     s.pv.n = s.n;
     s.pv.m_models = s.m;
-    cudaMemcpyAsync(s.d_geoms, s.geoms, sizeof(LevelGeom) * GPM_MAX_SCALES, cudaMemcpyHostToDevice, c->stream);
+    launch_set_geoms(s.geoms, s.d_geoms, c->stream);
     // a defined NNF (zero offsets) before anything reads it
     for (int d = 0; d < 2; ++d) cudaMemsetAsync(s.pv.nnf[d], 0, sizeof(int2) * s.n, c->stream);
     return cuda_check(c, "set_dims");

@@ -12,6 +12,7 @@
 // p + v + G(s) - G(p), s = clamp(p + d).
 #include "common.cuh"
 #include "kernels.h"
+#include "../../include/gpm.h"
 
 namespace gpm {
 
@@ -577,6 +578,18 @@ void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride,
 
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
     k_build_lists<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+}
+
+struct GeomPack {
+    LevelGeom g[GPM_MAX_SCALES];
+};
+__global__ void k_set_geoms(GeomPack p, LevelGeom* dst) {
+    if (threadIdx.x < GPM_MAX_SCALES) dst[threadIdx.x] = p.g[threadIdx.x];
+}
+void launch_set_geoms(const LevelGeom* host_geoms, LevelGeom* dst, cudaStream_t st) {
+    GeomPack p;
+    for (int l = 0; l < GPM_MAX_SCALES; ++l) p.g[l] = host_geoms[l];
+    k_set_geoms<<<1, 32, 0, st>>>(p, dst);
 }
 
 }  // namespace gpm

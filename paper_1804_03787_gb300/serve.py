@@ -50,6 +50,7 @@ class _Slot:
     occ: object
     h_flow: object
     h_occ: object
+    h_in: object                   # pinned staging of the request's two frames
     req: Request | None = None
     done: object = None
 
@@ -82,18 +83,28 @@ class Server:
                 occ = torch.empty(max_width * max_height, dtype=torch.uint8, device="cuda")
             h_flow = torch.empty(max_width * max_height * 2, dtype=torch.float32).pin_memory()
             h_occ = torch.empty(max_width * max_height, dtype=torch.uint8).pin_memory()
-            self.slots.append(_Slot(ctx, st, f1, f2, flow, occ, h_flow, h_occ))
+            h_in = torch.empty(2 * max_width * max_height * 3, dtype=torch.float32).pin_memory()
+            self.slots.append(_Slot(ctx, st, f1, f2, flow, occ, h_flow, h_occ, h_in))
         self.per_slot_bytes = per
         torch.cuda.synchronize()
+
+    def close(self):
+        for s in self.slots:
+            s.ctx.close()
+        self.slots = []
 
     def _launch(self, s: _Slot, r: Request, t0: float):
         torch = self.torch
         H, W, _ = r.frame1.shape
         n = W * H
         r.t_start = time.perf_counter() - t0
+        # host frames -> pinned staging (host copy) -> device, asynchronously on the slot's stream
+        stage = s.h_in.numpy()
+        np.copyto(stage[: 3 * n], r.frame1.reshape(-1))
+        np.copyto(stage[3 * n: 6 * n], r.frame2.reshape(-1))
         with torch.cuda.stream(s.stream):
-            s.f1[: 3 * n].copy_(torch.from_numpy(r.frame1.reshape(-1)), non_blocking=False)
-            s.f2[: 3 * n].copy_(torch.from_numpy(r.frame2.reshape(-1)), non_blocking=False)
+            s.f1[: 3 * n].copy_(s.h_in[: 3 * n], non_blocking=True)
+            s.f2[: 3 * n].copy_(s.h_in[3 * n: 6 * n], non_blocking=True)
             f1 = s.f1[: 3 * n].view(H, W, 3)
             f2 = s.f2[: 3 * n].view(H, W, 3)
             s.ctx.match([(f1, f2)], 0, pair_ids=[r.pair_id])
@@ -163,6 +174,17 @@ def poisson_trace(rate_hz: float, duration_s: float, pool: list, seed: int = 0) 
             break
         f1, f2 = pool[int(rng.integers(len(pool)))]
         out.append(Request(rid=len(out), arrival=t, frame1=f1, frame2=f2, pair_id=len(out)))
+    return out
+
+
+def serving_specs(n: int, seed: int = 0) -> list[dict]:
+    """Scene recipes of the serving workload: log-uniform sizes 320x240 to 1920x1080, 4-10 layers, motion up
+    to 128 px.  Each is a keyword dict for scene.make_scene."""
+    rng = np.random.default_rng(seed + 7)
+    out = []
+    for k, (w, h) in enumerate(log_uniform_sizes(n, seed=seed)):
+        out.append(dict(width=w, height=h, seed=3000 + seed * 100 + k, n_layers=int(rng.integers(4, 11)),
+                        max_disp=128.0, affine=False, area_frac=(0.02, 0.08)))
     return out
 
 
