@@ -146,6 +146,17 @@ def fp32_peak_tops(sm_mhz: float, nsm: int) -> float:
     return nsm * 128 * sm_mhz * 1e6 / 1e12
 
 
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the kernel class, from the
+# captures summarised in profiles/ (null where the kernel changed since, or no capture matches the class).
+TRAFFIC_PER_LAUNCH = {
+    "pm_sweep": (25016832 + 12544, "profiles/pm_sweep_level0_1024x436.md"),
+    "pm_sweep_plane": (17875968 + 284160, "profiles/pm_sweep_plane_level1_1024x436.md"),
+}
+# Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
+# written (8 + 8 B) and one RGBX texel of each frame (16 + 16 B).
+PM_BYTES_PER_VISIT = 48
+
+
 def roofline_block(prof, evals, nsm, clocks, peaks, steps):
     """Roofline of the kernel class with the largest share of device time."""
     total = sum(ms for ms, _ in prof.values()) or 1.0
@@ -175,7 +186,18 @@ def roofline_block(prof, evals, nsm, clocks, peaks, steps):
                       "units": "FP32 lane operations (14 per residual test; hypothesis solves not counted)"})
     else:
         block.update({"bound": "alu", "achieved": None, "peak": peak_ops, "unit": "TFLOP/s", "frac": None})
-    block["traffic"] = None
+    tr = TRAFFIC_PER_LAUNCH.get(top)
+    block["traffic"] = tr[0] if tr else None
+    if tr:
+        block["traffic_source"] = tr[1]
+    if top == "pm_sweep":
+        # HBM view: a half-iteration visits W*H/2 pixels in each of the two directions
+        visits = W * H
+        hbm = peaks.get("hbm_gbs") or 6800.0
+        gbs = visits * PM_BYTES_PER_VISIT / (block["avg_launch_ms"] * 1e-3) / 1e9
+        block["hbm_view"] = {"algorithmic_bytes_per_launch": visits * PM_BYTES_PER_VISIT, "achieved_gbs": gbs,
+                             "peak_gbs": hbm, "frac": gbs / hbm,
+                             "note": "frames stay in L2, so the sweep is bound by gathers and issue, not HBM"}
     return block
 
 
