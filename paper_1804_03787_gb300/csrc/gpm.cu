@@ -590,7 +590,7 @@ gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
             break;
         case GPM_COST:
             for (int k = 0; k < 2; ++k)
-                cudaMemcpyAsync(d + k * n * sizeof(float), s.pv.cost[k], n * sizeof(float), cudaMemcpyDeviceToDevice, st);
+                launch_cost_export(s.pv.cost[k], (float*)(d + k * n * sizeof(float)), (int)n, c->P.patch_radius, st);
             break;
         case GPM_MODELS:
             for (int k = 0; k < 2; ++k)

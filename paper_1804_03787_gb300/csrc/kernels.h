@@ -19,6 +19,8 @@ void launch_pm(const PmLaunch& L, cudaStream_t st);
 void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
                    double* partial, int nblk, double* gain, void* o1, void* o2, cudaStream_t st);
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
+// dst[i] = src[i] / (3 (2 radius + 1)^2): the NNF cost buffer holds raw tap sums, the export means.
+void launch_cost_export(const float* src, float* dst, int n, int radius, cudaStream_t st);
 // Writes the level geometries (host array, copied by value into the launch) to dst: no host copy in the
 // stream, so a pipeline that changes frame size can be captured into a CUDA graph.
 void launch_set_geoms(const LevelGeom* host_geoms, LevelGeom* dst, cudaStream_t st);

@@ -110,9 +110,22 @@ struct LanePatch {
     float4 a[Patch<R>::NT];   // source texels of the lane's taps
     int tx[Patch<R>::NT], ty[Patch<R>::NT], tidx[Patch<R>::NT];
     float fx[Patch<R>::NT], fy[Patch<R>::NT];
-    int xlo, xhi, ylo, yhi;
+    // offsets c with oxlo <= c.x <= oxlo + oxspan and oylo <= c.y <= oylo + oyspan keep every texel of
+    // the patch inside the frame (the unclamped, one-add indexing path)
+    int oxlo, oxspan, oylo, oyspan;
     bool warped;
 };
+
+// The patch touches texels [xlo, xhi] x [ylo, yhi] at offset 0; offsets keep them inside the frame iff
+// -xlo <= c.x <= W-1-xhi (likewise y).  An empty range gets a start no offset reaches.
+template <int R>
+__device__ __forceinline__ void set_interior_box(LanePatch<R>& lp, int xlo, int xhi, int ylo, int yhi, int W, int H) {
+    const int sx = (W - 1 - xhi) + xlo, sy = (H - 1 - yhi) + ylo;
+    lp.oxlo = sx >= 0 ? -xlo : (1 << 30);
+    lp.oxspan = max(sx, 0);
+    lp.oylo = sy >= 0 ? -ylo : (1 << 30);
+    lp.oyspan = max(sy, 0);
+}
 
 template <int R, int ST>
 __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, int W, int H, int px, int py,
@@ -129,10 +142,7 @@ __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, in
         lp.fx[j] = 0.f;
         lp.fy[j] = 0.f;
     }
-    lp.xlo = max(px - R, 0);
-    lp.xhi = min(px + R, W - 1);
-    lp.ylo = max(py - R, 0);
-    lp.yhi = min(py + R, H - 1);
+    set_interior_box(lp, max(px - R, 0), min(px + R, W - 1), max(py - R, 0), min(py + R, H - 1), W, H);
     lp.warped = false;
 }
 
@@ -151,7 +161,7 @@ __device__ __forceinline__ int warp_max(int v) {
 // Jacobian form: with J the derivative of G at p and c = (g0, g1) / den(p),
 // G(p + d) - G(p) = J d / (1 + c . d) exactly.
 template <int R>
-__device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px, int py, int W, int lane) {
+__device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px, int py, int W, int H, int lane) {
     const float ux = (float)(px - m.ox), uy = (float)(py - m.oy);
     const float e = m.e0 + m.g0 * ux + m.g1 * uy;
     const float den = 1.f + e;
@@ -184,10 +194,7 @@ __device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px
             yhi = max(yhi, lp.ty[j] + 1);
         }
     }
-    lp.xlo = warp_min(xlo);
-    lp.xhi = warp_max(xhi);
-    lp.ylo = warp_min(ylo);
-    lp.yhi = warp_max(yhi);
+    set_interior_box(lp, warp_min(xlo), warp_max(xhi), warp_min(ylo), warp_max(yhi), W, H);
     lp.warped = true;
 }
 
@@ -209,15 +216,19 @@ __device__ __forceinline__ float3 tap_sample(const LanePatch<R>& lp, const void*
     return bilinear<ST>(tgt, W, H, lp.tx[j] + c.x, lp.fx[j], lp.ty[j] + c.y, lp.fy[j]);
 }
 
-__device__ __forceinline__ bool interior_of(int xlo, int xhi, int ylo, int yhi, int2 c, int W, int H) {
-    return xlo + c.x >= 0 && xhi + c.x <= W - 1 && ylo + c.y >= 0 && yhi + c.y <= H - 1;
+template <int R>
+__device__ __forceinline__ bool interior_of(const LanePatch<R>& lp, int2 c) {
+    return (unsigned)(c.x - lp.oxlo) <= (unsigned)lp.oxspan && (unsigned)(c.y - lp.oylo) <= (unsigned)lp.oyspan;
 }
 
+// Raw patch cost of offset (vx, vy): the sum over taps and channels of
+// |difference|.  The NNF cost buffer holds these sums (strict-less decisions
+// compare them directly); the exported cost is the sum divided by 3T.
 template <int R, int ST>
-__device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
-                                            int vx, int vy, int lane) {
+__device__ __forceinline__ float patch_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
+                                           int vx, int vy, int lane) {
     const int2 c = make_int2(vx, vy);
-    const bool in = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c, W, H);
+    const bool in = interior_of<R>(lp, c);
     const int off = vy * W + vx;
     float s = 0.f;
 #pragma unroll
@@ -228,13 +239,13 @@ __device__ __forceinline__ float patch_cost(const LanePatch<R>& lp, const void* 
     // butterfly sum: every lane ends with the same bits (IEEE addition commutes)
 #pragma unroll
     for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_xor_sync(FULL, s, off2);
-    return s / (float)(3 * Patch<R>::T);
+    return s;
 }
 
 // Integer threshold for the abandon test of tap_sum: with thr the best raw
-// sum so far times 3T (raised by 2^-20 for the rounding of that product),
-// returns ceil(thr * 2^19 * (1 + 2^-21)).  The extra 2^-21 covers the five
-// rounded additions of the warp's final float sum (each loses at most 2^-24).
+// sum so far, returns ceil(thr * 2^19 * (1 + 2^-21)).  The extra 2^-21 covers
+// the five rounded additions of the warp's final float sum (each loses at
+// most 2^-24).
 __device__ __forceinline__ int abandon_threshold(float thr) {
     return __float2int_ru(__fmul_ru(thr * 524288.f, 1.f + 4.76837158203125e-07f));
 }
@@ -249,11 +260,11 @@ __device__ __forceinline__ int abandon_threshold(float thr) {
 // (abandon_threshold) therefore means the full cost is at or above the best,
 // and the strict-less test would reject the candidate anyway: the function
 // returns false.  Each lane accumulates its taps in the same order as
-// patch_cost, so a full sum divided by 3T gives bitwise the same cost.
+// patch_sum, so a full sum is bitwise the same as patch_sum's.
 template <int R, int ST>
 __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int lane) {
-    const bool in = interior_of(lp.xlo, lp.xhi, lp.ylo, lp.yhi, c, W, H);
+    const bool in = interior_of<R>(lp, c);
     const int off = c.y * W + c.x;
     float s = 0.f;
 #pragma unroll
@@ -320,7 +331,7 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
         const int vx = (int)(w.x % (uint32_t)W) - x, vy = (int)(w.y % (uint32_t)H) - y;
         LanePatch<R> lp;
         load_patch<R, ST>(lp, src, W, H, x, y, lane);
-        const float c = patch_cost<R, ST>(lp, tgt, W, H, x, y, vx, vy, lane);
+        const float c = patch_sum<R, ST>(lp, tgt, W, H, x, y, vx, vy, lane);
         if (lane == 0) {
             pv.nnf[dir][i] = make_int2(vx, vy);
             pv.cost[dir][i] = c;
@@ -349,10 +360,10 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
             load_patch<R, ST>(lp, src, W, H, x, y, lane);
             if (level > 0) {
                 const Mef* G = home_plane(g, pv.mef[dir], x, y);
-                if (G) warp_taps<R>(lp, *G, x, y, W, lane);
+                if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
             }
             const int2 v = pv.nnf[dir][i];
-            const float c = patch_cost<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
+            const float c = patch_sum<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
             if (lane == 0) {
                 pv.cost[dir][i] = c;
                 if (pv.evals) atomicAdd(&pv.evals[level > 0], 1ull);
@@ -387,7 +398,6 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
     const int* list = !PLANES ? nullptr : pv.list[dir] + phase * pv.n;
     const int R0 = max(W, H);
     const uint32_t tag = stream_tag(RNG_SEARCH, dir, level, 0);
-    const float scale = (float)(3 * Patch<R>::T);
     for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
         int x, y, i;
         if (!PLANES) {
@@ -404,10 +414,11 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
         load_patch<R, ST>(lp, src, W, H, x, y, lane);
         if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
-            if (G) warp_taps<R>(lp, *G, x, y, W, lane);
+            if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
         }
         int2 best = nnf[i];
-        float bc = pv.cost[dir][i];
+        float bc = pv.cost[dir][i];  // raw sum of the incumbent
+        int ithr = abandon_threshold(bc);
         int nev = 0;
         // random words for the search radii, two radii per Philox call, one call per lane
         uint4 rw = make_uint4(0, 0, 0, 0);
@@ -470,13 +481,10 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                 todo &= todo - 1;
                 const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
                 float sum;
-                if (tap_sum<R, ST>(lp, tgt, W, H, c, abandon_threshold(bc * scale * (1.f + 9.5367431640625e-07f)), sum,
-                                   lane)) {
-                    const float cc = sum / scale;
-                    if (cc < bc) {
-                        bc = cc;
-                        best = c;
-                    }
+                if (tap_sum<R, ST>(lp, tgt, W, H, c, ithr, sum, lane) && sum < bc) {
+                    bc = sum;
+                    best = c;
+                    ithr = abandon_threshold(bc);
                 }
                 ++nev;
             }
@@ -578,6 +586,16 @@ void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride,
 
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
     k_build_lists<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+}
+
+// Exported patch costs: the raw sums divided by 3T (the same division, so the same bits, as a mean taken
+// at evaluation time).
+__global__ void k_cost_export(const float* src, float* dst, int n, float scale) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] / scale;
+}
+void launch_cost_export(const float* src, float* dst, int n, int radius, cudaStream_t st) {
+    const int d = 2 * radius + 1;
+    k_cost_export<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n, (float)(3 * d * d));
 }
 
 struct GeomPack {
