@@ -398,14 +398,26 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
     const int* list = !PLANES ? nullptr : pv.list[dir] + phase * pv.n;
     const int R0 = max(W, H);
     const uint32_t tag = stream_tag(RNG_SEARCH, dir, level, 0);
-    for (int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < total; w += nw) {
+    // Level 0: a block takes tiles of 8 x 8 pixels of this colour (16 x 8 image pixels), its eight warps one
+    // row of the tile per round, so that successive rounds reuse the target region already in the SM's L1.
+    // Plane levels: the compacted pixel list, grid-strided.
+    const int wid = threadIdx.x >> 5;
+    const int ntx = (hw + 7) >> 3, ntiles = ntx * ((H + 7) >> 3);
+    for (int rnd = 0;; ++rnd) {
         int x, y, i;
         if (!PLANES) {
-            y = w / hw;
-            x = 2 * (w - y * hw) + ((y + phase) & 1);
+            const int tile = blockIdx.x + (rnd >> 3) * gridDim.x;
+            if (tile >= ntiles) break;
+            const int ty = tile / ntx, tx = tile - ty * ntx;
+            y = 8 * ty + (rnd & 7);
+            const int xh = 8 * tx + wid;
+            if (y >= H || xh >= hw) continue;
+            x = 2 * xh + ((y + phase) & 1);
             if (x >= W) continue;
             i = y * W + x;
         } else {
+            const int w = blockIdx.x * (blockDim.x >> 5) + wid + rnd * nw;
+            if (w >= total) break;
             i = list[w];
             y = i / W;
             x = i - y * W;
