@@ -322,6 +322,53 @@ def serving_block(scenes):
             "latency": "arrival to flow and occlusion in host memory (host frames copied in per request)"}
 
 
+def reduced_precision_block(scenes, dev, flows32, flush):
+    """The headline workload with frames stored as FP16 / BF16 (FP32 arithmetic): pairs/s, EPE on non-occluded
+    pixels, and the flow difference from the FP32 form on the same scenes."""
+    import numpy as np
+    import torch
+
+    from paper_1804_03787_gb300 import gpm
+    out = {}
+    for name, st in (("f16", gpm.GPM_F16), ("bf16", gpm.GPM_BF16)):
+        gp = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=st)
+        ctx = gpm.Context(gp, W, H)
+        fl = [torch.empty((H, W, 2), dtype=torch.float32, device="cuda") for _ in scenes]
+        oc = [torch.empty((H, W), dtype=torch.uint8, device="cuda") for _ in scenes]
+
+        def one(k):
+            ctx.match([dev[k]], 0, pair_ids=[k])
+            for lvl in range(1, len(CELLS) + 1):
+                ctx.fit_planes(lvl)
+                ctx.match(None, lvl)
+            ctx.flow_and_occlusion([fl[k]], [oc[k]])
+
+        one(0)
+        ms = 0.0
+        for k in range(len(scenes)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            one(k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        epe, dfl = [], []
+        for k, sc in enumerate(scenes):
+            f = fl[k].cpu().numpy()
+            nocc = sc.occ == 0
+            epe.append(float(np.sqrt(((f - sc.flow) ** 2).sum(-1))[nocc].mean()))
+            dfl.append(float(np.sqrt(((f - flows32[k]) ** 2).sum(-1))[nocc].mean()))
+        ctx.close()
+        out[name] = {"value": len(scenes) / (ms * 1e-3), "unit": "pairs/s", "epe_nocc_px": float(np.mean(epe)),
+                     "mean_flow_diff_from_f32_nocc_px": float(np.mean(dfl))}
+    out["f32_epe_nocc_px"] = float(np.mean([np.sqrt(((flows32[k] - sc.flow) ** 2).sum(-1))[sc.occ == 0].mean()
+                                            for k, sc in enumerate(scenes)]))
+    out["workload"] = "the headline 1024x436 scenes, one pass each, frames stored as FP16 / BF16, FP32 arithmetic"
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -461,6 +508,19 @@ def run_ours(args):
                          "occlusion_precision": float(np.mean([a[2] for a in acc])),
                          "occlusion_recall": float(np.mean([a[3] for a in acc])),
                          "against": "the synthetic scenes' exact flow and occlusion (last end-to-end step)"}}
+    if rank == 0 and not args.no_extras:
+        try:
+            flows32 = []
+            for k in range(nscenes):
+                ctx.match([dev[k]], 0, pair_ids=[k])
+                for lvl in range(1, len(CELLS) + 1):
+                    ctx.fit_planes(lvl)
+                    ctx.match(None, lvl)
+                ctx.flow_and_occlusion(flows[:1], occs[:1])
+                flows32.append(flows[0].cpu().numpy())
+            line["reduced_precision"] = reduced_precision_block(scenes, dev, flows32, flush)
+        except Exception as e:  # reported, never fatal for the headline line
+            line["reduced_precision"] = {"error": f"{type(e).__name__}: {e}"}
     ctx.close()
     del ctx
     torch.cuda.empty_cache()

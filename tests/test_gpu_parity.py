@@ -443,3 +443,36 @@ def test_reduced_precision_storage(torch, kind, storage):
     print(f"{kind}: level-0 NNF agreement with the FP64 oracle on FP32 frames {np.mean(agree):.4f}")
     assert np.mean(agree) > 0.8
     ctx.close()
+
+
+@pytest.mark.parametrize("kind,storage", [("f16", gpm.GPM_F16), ("bf16", gpm.GPM_BF16)])
+def test_reduced_precision_end_to_end(torch, kind, storage):
+    """Tiny config, frames stored as FP16/BF16: the whole method against the oracle on the dequantised frames
+    (the same bars as the FP32 end-to-end test), and the accuracy change against the FP64 oracle on the original
+    frames reported and bounded."""
+    s = scene.tiny_scene(0)
+    gp = gpm.default_params(storage=storage)
+    ctx = _ctx(torch, gp, 128, 96)
+    flows, occs = ctx.run([_dev(torch, s)])
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy()
+    P = oracle_params(gp, 128, 96)
+    _, g = oracle_frames(P, s.frame1, s.frame2)
+    q1 = _quantise(s.frame1, kind).astype(np.float64)
+    q2 = _quantise((s.frame2.astype(np.float64) * g).astype(np.float32), kind).astype(np.float64)
+    Pq = oracle_params(gp, 128, 96)
+    Pq.gain_normalize = 0
+    Rq = O.run(Pq, q1, q2)
+    qflow = Rq.flow[0].reshape(96, 128, 2)
+    vis = s.occ == 0
+    agree = np.mean(np.hypot(*(gflow - qflow).transpose(2, 0, 1)) < 1e-4)
+    epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    epe_q = np.hypot(*(qflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    R = O.run(P, s.frame1, s.frame2)
+    epe_o = np.hypot(*(R.flow[0].reshape(96, 128, 2) - s.flow).transpose(2, 0, 1))[vis].mean()
+    print(f"{kind}: flow agreement with the oracle on dequantised frames {agree:.4f}; EPE nocc gpu {epe_g:.4f}, "
+          f"oracle (dequantised) {epe_q:.4f}, oracle (FP64 frames) {epe_o:.4f}")
+    assert agree > 0.95
+    assert abs(epe_g - epe_q) < 0.01
+    assert abs(epe_g - epe_o) < 0.1
+    ctx.close()
