@@ -211,70 +211,76 @@ __device__ __forceinline__ double rsqrt_nr(double n) {
     return r;
 }
 
-// Unit eigenvector of the smallest eigenvalue of the 9 x 9 symmetric positive
-// semi-definite matrix whose lower triangle is A (packed, row i at i(i+1)/2),
-// by inverse iteration from x.  A + sigma I is factored once (Cholesky) and
-// its inverse formed explicitly (L^-T L^-1), so each step is one product with
-// it.  Most of the convergence happens in FP32 (an FP32 warp instruction
-// issues in a cycle, an FP64 one holds this GPU's FP64 pipe for about 64),
-// then FP64 steps polish the direction.  One thread per window: each FP64 warp
-// instruction serves 32 windows.
-__device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
-    double tr = 0;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) tr += A[i * (i + 1) / 2 + i];
-    const double sigma = 1e-13 * tr + 1e-300;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) A[i * (i + 1) / 2 + i] += sigma;
-    double rd[9];
+// Cholesky factor (lower, packed, in place) of the symmetric matrix in A;
+// rd[j] = 1 / L[j][j].  The diagonal roots come from an FP32 estimate and
+// Newton steps (rsqrt_nr).  Returns false if a pivot is not positive (the
+// matrix is not positive definite).
+__device__ __forceinline__ bool cholesky9(double (&A)[45], double (&rd)[9]) {
+    bool ok = true;
 #pragma unroll
     for (int j = 0; j < 9; ++j) {
         double d = A[j * (j + 1) / 2 + j];
 #pragma unroll
-        for (int k = 0; k < j; ++k) d -= A[j * (j + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
-        d = d > 0 ? sqrt(d) : 1e-150;
-        A[j * (j + 1) / 2 + j] = d;
-        rd[j] = 1.0 / d;
+        for (int k = 0; k < j; ++k) d = fma(-A[j * (j + 1) / 2 + k], A[j * (j + 1) / 2 + k], d);
+        ok = ok && d > 0;
+        const double r = d > 0 ? rsqrt_nr(d) : 1.0;
+        A[j * (j + 1) / 2 + j] = d * r;
+        rd[j] = r;
 #pragma unroll
         for (int i = j + 1; i < 9; ++i) {
             double t = A[i * (i + 1) / 2 + j];
 #pragma unroll
-            for (int k = 0; k < j; ++k) t -= A[i * (i + 1) / 2 + k] * A[j * (j + 1) / 2 + k];
-            A[i * (i + 1) / 2 + j] = t * rd[j];
+            for (int k = 0; k < j; ++k) t = fma(-A[i * (i + 1) / 2 + k], A[j * (j + 1) / 2 + k], t);
+            A[i * (i + 1) / 2 + j] = t * r;
         }
     }
-    double Li[45];  // L^-1, lower triangular
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        Li[j * (j + 1) / 2 + j] = rd[j];
-#pragma unroll
-        for (int i = j + 1; i < 9; ++i) {
-            double t = 0;
-#pragma unroll
-            for (int k = j; k < i; ++k) t -= A[i * (i + 1) / 2 + k] * Li[k * (k + 1) / 2 + j];
-            Li[i * (i + 1) / 2 + j] = t * rd[i];
-        }
-    }
-    // (A + sigma I)^-1 = Li^T Li, lower triangle into A
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            double t = 0;
-#pragma unroll
-            for (int k = i; k < 9; ++k) t += Li[k * (k + 1) / 2 + i] * Li[k * (k + 1) / 2 + j];
-            A[i * (i + 1) / 2 + j] = t;
-        }
+    return ok;
+}
+
+// Unit eigenvector of the smallest eigenvalue of the 9 x 9 symmetric positive
+// semi-definite matrix M (lower triangle packed, row i at i(i+1)/2), from the
+// start x.  The FP64 pipe of this GPU issues a warp instruction in about 64
+// cycles, an FP32 one in 1, so:
+//  1. FP32: inverse iteration with the explicit inverse of M / tr + 1e-6 I
+//     until the direction settles at FP32 resolution;
+//  2. FP64: Rayleigh quotient rho and residual r = M x - rho x of that
+//     direction; M has an eigenvalue within |r| of rho, the smallest one when
+//     x is nearest its eigenvector, so sigma = rho - 2 |r| lies below it;
+//  3. FP64 inverse iteration with the Cholesky factor of M - sigma I: the
+//     shift makes each step shrink the other directions by
+//     (l1 - sigma) / (li - sigma), so a few steps reach 1e-12.  If that matrix
+//     is not positive definite (the bound did not hold), the shift falls back
+//     to -1e-13 tr, plain inverse iteration.
+// One thread per window: each FP64 warp instruction serves 32 windows.
+__device__ __forceinline__ void min_eigvec9(const double (&M)[45], double (&x)[9]) {
     auto sym = [](int i, int j) { return i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i; };
-    {  // FP32 steps with the rounded inverse (scaled well inside range) until the direction settles
-        float trs = 0.f;
+    double tr = 0;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) trs += (float)A[i * (i + 1) / 2 + i];
-        const float rs = trs > 0.f ? 1.f / trs : 1.f;
-        float Af[45], xf[9];
+    for (int i = 0; i < 9; ++i) tr += M[i * (i + 1) / 2 + i];
+    {  // 1. FP32 direction
+        const float rs = tr > 0 ? (float)(1.0 / tr) : 1.f;
+        float L[45], rdf[9];
 #pragma unroll
-        for (int q = 0; q < 45; ++q) Af[q] = (float)A[q] * rs;
-        float n0 = 0.f;
+        for (int q = 0; q < 45; ++q) L[q] = (float)M[q] * rs;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) L[i * (i + 1) / 2 + i] += 1e-6f;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            float d = L[j * (j + 1) / 2 + j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) d = fmaf(-L[j * (j + 1) / 2 + k], L[j * (j + 1) / 2 + k], d);
+            const float r = d > 1e-30f ? rsqrtf(d) : 1e15f;
+            L[j * (j + 1) / 2 + j] = d * r;
+            rdf[j] = r;
+#pragma unroll
+            for (int i = j + 1; i < 9; ++i) {
+                float t = L[i * (i + 1) / 2 + j];
+#pragma unroll
+                for (int k = 0; k < j; ++k) t = fmaf(-L[i * (i + 1) / 2 + k], L[j * (j + 1) / 2 + k], t);
+                L[i * (i + 1) / 2 + j] = t * r;
+            }
+        }
+        float xf[9], n0 = 0.f;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             xf[i] = (float)x[i];
@@ -283,14 +289,21 @@ __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
         const float s0 = rsqrtf(n0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) xf[i] *= s0;
-        for (int it = 0; it < 400; ++it) {
+        for (int it = 0; it < 300; ++it) {
             float y[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                float t = 0.f;
+            for (int i = 0; i < 9; ++i) {  // L z = x
+                float t = xf[i];
 #pragma unroll
-                for (int j = 0; j < 9; ++j) t = fmaf(Af[sym(i, j)], xf[j], t);
-                y[i] = t;
+                for (int k = 0; k < i; ++k) t = fmaf(-L[i * (i + 1) / 2 + k], y[k], t);
+                y[i] = t * rdf[i];
+            }
+#pragma unroll
+            for (int i = 8; i >= 0; --i) {  // L^T y = z
+                float t = y[i];
+#pragma unroll
+                for (int k = i + 1; k < 9; ++k) t = fmaf(-L[k * (k + 1) / 2 + i], y[k], t);
+                y[i] = t * rdf[i];
             }
             float n = 0.f, dot = 0.f;
 #pragma unroll
@@ -318,20 +331,67 @@ __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
             for (int i = 0; i < 9; ++i) x[i] = (double)xf[i];
         }
     }
+    // 2. shift from the Rayleigh quotient and the residual of x
+    double xx = 0, rho = 0, Mx[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        double t = 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) t = fma(M[sym(i, j)], x[j], t);
+        Mx[i] = t;
+        xx = fma(x[i], x[i], xx);
+        rho = fma(x[i], t, rho);
+    }
+    const double ixx = 1.0 / xx;
+    rho *= ixx;
+    double rr = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const double r = fma(-rho, x[i], Mx[i]);
+        rr = fma(r, r, rr);
+    }
+    const double floor_shift = -1e-13 * tr - 1e-300;
+    double sigma = rho - 2.0 * sqrt(rr * ixx);
+    if (!(sigma > floor_shift)) sigma = floor_shift;
+    // 3. shifted inverse iteration in FP64
+    double A[45], rd[9];
+#pragma unroll
+    for (int q = 0; q < 45; ++q) A[q] = M[q];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A[i * (i + 1) / 2 + i] -= sigma;
+    if (!cholesky9(A, rd)) {
+#pragma unroll
+        for (int q = 0; q < 45; ++q) A[q] = M[q];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) A[i * (i + 1) / 2 + i] -= floor_shift;
+        cholesky9(A, rd);
+    }
+    {
+        const double s0 = rsqrt_nr(xx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) x[i] *= s0;
+    }
     for (int it = 0; it < 60; ++it) {
         double y[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            double t = 0;
+        for (int i = 0; i < 9; ++i) {  // L z = x
+            double t = x[i];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) t += A[sym(i, j)] * x[j];
-            y[i] = t;
+            for (int k = 0; k < i; ++k) t = fma(-A[i * (i + 1) / 2 + k], y[k], t);
+            y[i] = t * rd[i];
+        }
+#pragma unroll
+        for (int i = 8; i >= 0; --i) {  // L^T y = z
+            double t = y[i];
+#pragma unroll
+            for (int k = i + 1; k < 9; ++k) t = fma(-A[k * (k + 1) / 2 + i], y[k], t);
+            y[i] = t * rd[i];
         }
         double n = 0, dot = 0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            n += y[i] * y[i];
-            dot += y[i] * x[i];
+            n = fma(y[i], y[i], n);
+            dot = fma(y[i], x[i], dot);
         }
         double sc = rsqrt_nr(n);
         if (dot < 0) sc = -sc;
@@ -343,8 +403,7 @@ __device__ __forceinline__ void min_eigvec9(double (&A)[45], double (&x)[9]) {
             x[i] = y[i];
         }
         // 1e-12 is far below what the rescore (1e-5 near-tie band) and the
-        // model comparison (1e-6) can see, and above the ~1e-15 rounding
-        // noise of the iteration on matrices conditioned near 1e13
+        // model comparison (1e-6) can see
         if (diff < 1e-12) break;
     }
 }
