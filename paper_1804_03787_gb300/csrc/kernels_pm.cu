@@ -198,17 +198,20 @@ __device__ __forceinline__ void warp_taps(LanePatch<R>& lp, const Mef& m, int px
     lp.warped = true;
 }
 
-// Target sample of tap j for candidate offset c (off = c.y * W + c.x).
-template <int R, int ST>
+// Target sample of tap j for candidate offset c (off = c.y * W + c.x).  IN:
+// the offset keeps every texel of the patch inside the frame (one add gives
+// the index); otherwise the coordinates are clamped.  The caller makes this
+// warp-uniform choice once per candidate, outside the tap loop.
+template <int R, int ST, bool IN>
 __device__ __forceinline__ float3 tap_sample(const LanePatch<R>& lp, const void* tgt, int W, int H, int j, int2 c,
-                                             int off, bool interior) {
+                                             int off) {
     if (!lp.warped) {
-        const int idx = interior ? lp.tidx[j] + off
-                                 : min(max(lp.ty[j] + c.y, 0), H - 1) * W + min(max(lp.tx[j] + c.x, 0), W - 1);
+        const int idx = IN ? lp.tidx[j] + off
+                           : min(max(lp.ty[j] + c.y, 0), H - 1) * W + min(max(lp.tx[j] + c.x, 0), W - 1);
         const float4 v = ldpix<ST>(tgt, idx);
         return make_float3(v.x, v.y, v.z);
     }
-    if (interior) {
+    if (IN) {
         const int i0 = lp.tidx[j] + off;
         return blend4(ldpix<ST>(tgt, i0), ldpix<ST>(tgt, i0 + 1), ldpix<ST>(tgt, i0 + W), ldpix<ST>(tgt, i0 + W + 1),
                       lp.fx[j], lp.fy[j]);
@@ -224,22 +227,26 @@ __device__ __forceinline__ bool interior_of(const LanePatch<R>& lp, int2 c) {
 // Raw patch cost of offset (vx, vy): the sum over taps and channels of
 // |difference|.  The NNF cost buffer holds these sums (strict-less decisions
 // compare them directly); the exported cost is the sum divided by 3T.
-template <int R, int ST>
-__device__ __forceinline__ float patch_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
-                                           int vx, int vy, int lane) {
-    const int2 c = make_int2(vx, vy);
-    const bool in = interior_of<R>(lp, c);
-    const int off = vy * W + vx;
+template <int R, int ST, bool IN>
+__device__ __forceinline__ float patch_sum_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int lane) {
+    const int off = c.y * W + c.x;
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
-        if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST>(lp, tgt, W, H, j, c, off, in));
+        if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST, IN>(lp, tgt, W, H, j, c, off));
     }
     // butterfly sum: every lane ends with the same bits (IEEE addition commutes)
 #pragma unroll
     for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_xor_sync(FULL, s, off2);
     return s;
+}
+template <int R, int ST>
+__device__ __forceinline__ float patch_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
+                                           int vx, int vy, int lane) {
+    const int2 c = make_int2(vx, vy);
+    return interior_of<R>(lp, c) ? patch_sum_in<R, ST, true>(lp, tgt, W, H, c, lane)
+                                 : patch_sum_in<R, ST, false>(lp, tgt, W, H, c, lane);
 }
 
 // Integer threshold for the abandon test of tap_sum: with thr the best raw
@@ -261,16 +268,15 @@ __device__ __forceinline__ int abandon_threshold(float thr) {
 // and the strict-less test would reject the candidate anyway: the function
 // returns false.  Each lane accumulates its taps in the same order as
 // patch_sum, so a full sum is bitwise the same as patch_sum's.
-template <int R, int ST>
-__device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
+template <int R, int ST, bool IN>
+__device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int lane) {
-    const bool in = interior_of<R>(lp, c);
     const int off = c.y * W + c.x;
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
-        if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST>(lp, tgt, W, H, j, c, off, in));
+        if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST, IN>(lp, tgt, W, H, j, c, off));
         if (j + 1 < Patch<R>::NT) {
             // floor(min(s * 2^19, 2^23 - 1)): exact scaling, clamp (keeps a lower bound), truncation in the
             // mantissa of 2^23
@@ -285,6 +291,12 @@ __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt,
         }
     }
     return true;
+}
+template <int R, int ST>
+__device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
+                                        float& sum, int lane) {
+    return interior_of<R>(lp, c) ? tap_sum_in<R, ST, true>(lp, tgt, W, H, c, ithr, sum, lane)
+                                 : tap_sum_in<R, ST, false>(lp, tgt, W, H, c, ithr, sum, lane);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
