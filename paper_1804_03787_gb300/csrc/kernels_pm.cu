@@ -258,7 +258,7 @@ __device__ __forceinline__ int abandon_threshold(float thr) {
 }
 
 // Raw tap sum of candidate offset c (over taps and channels of |difference|,
-// before the division by 3T), abandoned once it cannot win.  After each
+// before the division by 3T), abandoned once it cannot win.  After a tested
 // 32-tap chunk every lane floors its partial sum to a multiple of 2^-19 and
 // the warp adds those integers exactly (one redux): a lower bound of the
 // exact partial sum.  The terms are non-negative and FP32 addition is
@@ -268,7 +268,7 @@ __device__ __forceinline__ int abandon_threshold(float thr) {
 // and the strict-less test would reject the candidate anyway: the function
 // returns false.  Each lane accumulates its taps in the same order as
 // patch_sum, so a full sum is bitwise the same as patch_sum's.
-template <int R, int ST, bool IN>
+template <int R, int ST, bool IN, bool EVERY_CHUNK>
 __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int lane) {
     const int off = c.y * W + c.x;
@@ -277,13 +277,14 @@ __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* t
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
         if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST, IN>(lp, tgt, W, H, j, c, off));
-        if (j + 1 < Patch<R>::NT) {
+        if (j + 1 < Patch<R>::NT && (EVERY_CHUNK || j == 0)) {
             // floor(min(s * 2^19, 2^23 - 1)): exact scaling, clamp (keeps a lower bound), truncation in the
             // mantissa of 2^23
             const unsigned q =
                 (unsigned)(__float_as_int(__fadd_rz(fminf(s * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
             if ((int)__reduce_add_sync(FULL, q) >= ithr) return false;
-        } else {
+        }
+        if (j + 1 == Patch<R>::NT) {
             float p = s;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
@@ -292,11 +293,13 @@ __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* t
     }
     return true;
 }
-template <int R, int ST>
+// EVERY_CHUNK: test the bound after every chunk but the last (plane levels, where a chunk costs four gathers per
+// tap); otherwise after the first chunk only (square patches, where a further test costs about what it saves).
+template <int R, int ST, bool EVERY_CHUNK>
 __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int lane) {
-    return interior_of<R>(lp, c) ? tap_sum_in<R, ST, true>(lp, tgt, W, H, c, ithr, sum, lane)
-                                 : tap_sum_in<R, ST, false>(lp, tgt, W, H, c, ithr, sum, lane);
+    return interior_of<R>(lp, c) ? tap_sum_in<R, ST, true, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, lane)
+                                 : tap_sum_in<R, ST, false, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, lane);
 }
 
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
@@ -505,7 +508,7 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                 todo &= todo - 1;
                 const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
                 float sum;
-                if (tap_sum<R, ST>(lp, tgt, W, H, c, ithr, sum, lane) && sum < bc) {
+                if (tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, lane) && sum < bc) {
                     bc = sum;
                     best = c;
                     ithr = abandon_threshold(bc);
