@@ -860,7 +860,7 @@ __device__ void ransac_finish(const G& grp, const PairView& pv, const LevelGeom&
 // Windows up to 16 x 16: one warp per window, eight windows per block.
 // Dynamic shared memory: 8 x 256 matches, then 8 x 32 hypotheses.
 template <int ST>
-__global__ void __launch_bounds__(256, 2) k_ransac_warp(PairView pv, LevelGeom g, int level, int stage,
+__global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g, int level, int stage,
                                                      PlaneParams pp) {
     extern __shared__ float4 warp_dyn[];
     __shared__ Mef wmef[8];
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGe
 
 // Larger windows: one 256-thread block per window (matches in dynamic shared memory).
 template <int ST>
-__global__ void __launch_bounds__(256, 2) k_ransac_block(PairView pv, LevelGeom g, int level, int stage,
+__global__ void __launch_bounds__(256, 3) k_ransac_block(PairView pv, LevelGeom g, int level, int stage,
                                                       PlaneParams pp) {
     extern __shared__ float4 match_dyn[];
     __shared__ double red_d[8];
