@@ -83,6 +83,7 @@ struct WarpGroup {
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
         return v;
     }
+    __device__ bool any(bool p) const { return __any_sync(FULL, p); }
     // exclusive prefix of `take` over the group and the total
     __device__ int scan(bool take, int& total) const {
         const unsigned b = __ballot_sync(FULL, take);
@@ -119,6 +120,7 @@ struct BlockGroup {
         for (int w = 0; w < NT / 32; ++w) t += red_i[w];
         return t;
     }
+    __device__ bool any(bool p) const { return __syncthreads_or(p) != 0; }
     __device__ long long sum(long long v) const {  // exact: integer addition in any order
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
@@ -502,12 +504,16 @@ __device__ int gather_matches(const G& grp, const PairView& pv, const LevelGeom&
 
 template <class G, int ST>
 __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
-                           const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, Mef* wmef) {
+                           const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, int* kfull,
+                           Mef* wmef) {
     const int tid = grp.rank();
     const int id = (g.base + cell) * 2 + (stage - 1);
     int* mi = pv.mi[dir] + (size_t)id * kMI;
     RefitWork* rw = pv.rw[dir] + cell;
-    if (G::size > 32 && tid == 0) *gbest = -1;
+    if (G::size > 32 && tid == 0) {
+        *gbest = -1;
+        *kfull = 0x7fffffff;
+    }
     const int N = gather_matches<G>(grp, pv, g, stage, dir, cell, match);
     if (tid == 0) {
         for (int k = 0; k < kMI; ++k) mi[k] = 0;
@@ -528,7 +534,9 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     // below the best score of the group (any index), or do not exceed the
     // best of this warp's earlier, lower-index hypotheses.  The winner (most
     // inliers, lowest index) is never abandoned, so the outcome is that of
-    // scoring every hypothesis in full.
+    // scoring every hypothesis in full.  Once a hypothesis has all N matches
+    // as inliers, hypotheses of higher index can at most tie and are not
+    // drawn at all.
     const float t2 = pp.t2;
     const uint32_t tag = stream_tag(RNG_RANSAC, dir, level, stage);
     constexpr int NW = G::size / 32;
@@ -536,24 +544,30 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     Mef* hb = hyp + (tid >> 5) * 32;
     int best_score = -1, best_k = 0x7fffffff, tests = 0;
     if (N <= kLaneScoreMax) {
-        for (int k = tid; k < pp.num_hyp; k += G::size) {
+        for (int r = 0; r * G::size < pp.num_hyp; ++r) {
+            const int k = r * G::size + tid;
             i128 Hk[9];
-            if (!draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk)) continue;
             Mef m;
-            if (!make_mef_exact(Hk, m)) continue;
-            int score = 0;
-            for (int j = 0; j < N; ++j) {
-                const float4 mt = match[j];
-                score += mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
+            if (k < pp.num_hyp && draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk) &&
+                make_mef_exact(Hk, m)) {
+                int score = 0;
+                for (int j = 0; j < N; ++j) {
+                    const float4 mt = match[j];
+                    score += mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
+                }
+                tests += N;
+                if (score > best_score) {
+                    best_score = score;
+                    best_k = k;
+                }
             }
-            tests += N;
-            if (score > best_score) {
-                best_score = score;
-                best_k = k;
-            }
+            // all N matches inliers: every later round has higher indices and can at most tie
+            if (grp.any(best_score >= N)) break;
         }
     }
     for (int b = tid >> 5; N > kLaneScoreMax && b * 32 < pp.num_hyp; b += NW) {
+        // a hypothesis with all N matches inliers at a lower index than this batch: nothing here can win
+        if ((NW > 1 ? *(volatile int*)kfull : (best_score >= N ? best_k : 0x7fffffff)) < b * 32) break;
         const int k = b * 32 + lane;
         bool ok = false;
         if (k < pp.num_hyp) {
@@ -592,7 +606,10 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             if (alive) {  // more inliers than every earlier hypothesis of this warp
                 best_score = score;
                 best_k = b * 32 + l;
-                if (NW > 1 && lane == 0) atomicMax(gbest, score);
+                if (NW > 1 && lane == 0) {
+                    atomicMax(gbest, score);
+                    if (score >= N) atomicMin(kfull, best_k);
+                }
             }
         }
         __syncwarp();
@@ -870,7 +887,8 @@ __global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g
     float4* match = warp_dyn + warp * 256;
     Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + 8 * 256) + warp * 32;
     WarpGroup grp;
-    ransac_fit<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, &wmef[warp]);
+    ransac_fit<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, nullptr,
+                              &wmef[warp]);
 }
 template <int ST>
 __global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
@@ -892,10 +910,10 @@ __global__ void __launch_bounds__(256, 3) k_ransac_block(PairView pv, LevelGeom 
     __shared__ unsigned long long red_u[8];
     __shared__ Mef hyp[8 * 32];
     __shared__ Mef wmef;
-    __shared__ int gbest;
+    __shared__ int gbest, kfull;
     BlockGroup<256> grp{red_d, red_i, red_u};
     ransac_fit<BlockGroup<256>, ST>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, hyp, &gbest,
-                                    &wmef);
+                                    &kfull, &wmef);
 }
 template <int ST>
 __global__ void __launch_bounds__(256) k_ransac_finish_block(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
