@@ -28,7 +28,8 @@ class _Params(C.Structure):
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("r", C.c_int32), ("num_scales", C.c_int32),
                 ("cell", C.c_int32 * MAX_SCALES), ("pm_iters", C.c_int32), ("num_hyp", C.c_int32),
                 ("min_inliers", C.c_int32), ("fill_iters", C.c_int32), ("gain_normalize", C.c_int32),
-                ("pm_init", C.c_int32), ("eps", C.c_double), ("ransac_px", C.c_double),
+                ("pm_init", C.c_int32), ("equalize", C.c_int32), ("pad0", C.c_int32),
+                ("eps", C.c_double), ("ransac_px", C.c_double),
                 ("fb_px", C.c_double), ("eta", C.c_double), ("kappa", C.c_double), ("beta", C.c_double),
                 ("occ_thresh", C.c_double), ("scale_min", C.c_double), ("scale_max", C.c_double),
                 ("seed", C.c_uint64), ("pair_id", C.c_uint32), ("pad", C.c_uint32)]
@@ -56,6 +57,7 @@ class Params:
     fill_iters: int = 8
     gain_normalize: int = 1
     pm_init: int = 1
+    equalize: int = 0                # HSV V-channel histogram equalisation of both frames (Sec. 4.2)
     seed: int = 0
     pair_id: int = 0
 
@@ -66,7 +68,7 @@ class Params:
         for i, s in enumerate(self.cells):
             p.cell[i] = s
         p.pm_iters, p.num_hyp, p.min_inliers, p.fill_iters = self.pm_iters, self.num_hyp, self.min_inliers, self.fill_iters
-        p.gain_normalize, p.pm_init = self.gain_normalize, self.pm_init
+        p.gain_normalize, p.pm_init, p.equalize = self.gain_normalize, self.pm_init, self.equalize
         p.eps, p.ransac_px, p.fb_px, p.eta, p.kappa = self.eps, self.ransac_px, self.fb_px, self.eta, self.kappa
         p.beta, p.occ_thresh, p.scale_min, p.scale_max = self.beta, self.occ_thresh, self.scale_min, self.scale_max
         p.seed, p.pair_id = self.seed & 0xFFFFFFFFFFFFFFFF, self.pair_id & 0xFFFFFFFF
@@ -104,6 +106,10 @@ def lib() -> C.CDLL:
             "orc_fill": (None, [pp, d, d, d, i32, u8, i32, d, d, d]),
             "orc_final": (None, [pp, d, d, i32, d, d, i32, i32, u8, P(C.c_float), u8]),
             "orc_gain": (C.c_double, [pp, d, d]),
+            "orc_rgb_to_hsv": (None, [C.c_double, C.c_double, C.c_double, d, d, d]),
+            "orc_hsv_to_rgb": (None, [C.c_double, C.c_double, C.c_double, d, d, d]),
+            "orc_v_lut": (C.c_int, [pp, d, d]),
+            "orc_hsv_equalize": (None, [pp, d, d]),
             "orc_run": (None, [pp, d, d, C.c_void_p, C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -173,6 +179,33 @@ def h_dlt(src, dst):
     H = np.zeros(9)
     ok = lib().orc_h_dlt(n, _p(s.reshape(-1), C.c_double), _p(d.reshape(-1), C.c_double), _p(H, C.c_double))
     return (H.reshape(3, 3) if ok else None)
+
+
+def rgb_to_hsv(r: float, g: float, b: float):
+    h, s, v = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_rgb_to_hsv(r, g, b, C.byref(h), C.byref(s), C.byref(v))
+    return h.value, s.value, v.value
+
+
+def hsv_to_rgb(h: float, s: float, v: float):
+    r, g, b = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_hsv_to_rgb(h, s, v, C.byref(r), C.byref(g), C.byref(b))
+    return r.value, g.value, b.value
+
+
+def v_lut(P: Params, rgb):
+    """(changed?, 256 equalised V values by bin) of one HxWx3 frame (Sec. 4.2)."""
+    lut = np.zeros(256)
+    ok = lib().orc_v_lut(C.byref(P.c()), _p(_f64(rgb), C.c_double), _p(lut, C.c_double))
+    return bool(ok), lut
+
+
+def hsv_equalize(P: Params, rgb):
+    """One frame with its V histogram equalised, H and S kept (Sec. 4.2)."""
+    a = _f64(rgb)
+    out = np.zeros_like(a)
+    lib().orc_hsv_equalize(C.byref(P.c()), _p(a, C.c_double), _p(out, C.c_double))
+    return out
 
 
 def gain(P: Params, f1, f2) -> float:

@@ -9,7 +9,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["oracle_core.c", "oracle_planes.c", "oracle_pipeline.c"]
+SOURCES = ["oracle_core.c", "oracle_planes.c", "oracle_pipeline.c", "oracle_color.c"]
 LIB = os.path.join(HERE, "_build", "liboracle.so")
 
 

@@ -1,0 +1,109 @@
+/*
+ * FP64 oracle: histogram equalisation of the frames in HSV (Sec. 4.2, the
+ * paper's illumination experiment: equalise the image pair in HSV and run the
+ * unchanged method on the result).  Test infrastructure, never the product.
+ *
+ * Reading (the paper gives no detail): each frame separately; the V channel
+ * (V = max(R, G, B), Smith's hexcone model) is equalised over 256 bins of
+ * [0, 1], bin = min(255, floor(256 V)); a pixel in bin b gets
+ * V' = (cdf(b) - cdf_min) / (n - cdf_min), where cdf_min is the count of the
+ * lowest occupied bin; H and S are kept.  A frame whose pixels all share one
+ * bin is left unchanged.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+/* Smith's hexcone RGB -> HSV, h in [0, 1), everything in [0, 1] for inputs in [0, 1]. */
+void orc_rgb_to_hsv(double r, double g, double b, double* h, double* s, double* v) {
+    double mx = r, mn = r;
+    if (g > mx) mx = g;
+    if (b > mx) mx = b;
+    if (g < mn) mn = g;
+    if (b < mn) mn = b;
+    *v = mx;
+    if (mx == mn) {
+        *h = 0.0;
+        *s = 0.0;
+        return;
+    }
+    const double c = mx - mn;
+    *s = c / mx;
+    double hh;
+    if (mx == r)
+        hh = (g - b) / c;          /* between yellow and magenta */
+    else if (mx == g)
+        hh = 2.0 + (b - r) / c;    /* between cyan and yellow */
+    else
+        hh = 4.0 + (r - g) / c;    /* between magenta and cyan */
+    hh /= 6.0;
+    if (hh < 0) hh += 1.0;
+    *h = hh;
+}
+
+/* The inverse: sector i = floor(6 h), fraction f, and the three levels
+   v (1 - s), v (1 - s f), v (1 - s (1 - f)). */
+void orc_hsv_to_rgb(double h, double s, double v, double* r, double* g, double* b) {
+    if (s == 0.0) {
+        *r = *g = *b = v;
+        return;
+    }
+    const double h6 = h * 6.0;
+    int i = (int)floor(h6);
+    const double f = h6 - i;
+    const double p = v * (1.0 - s), q = v * (1.0 - s * f), t = v * (1.0 - s * (1.0 - f));
+    i %= 6;
+    if (i < 0) i += 6;
+    switch (i) {
+        case 0: *r = v; *g = t; *b = p; break;
+        case 1: *r = q; *g = v; *b = p; break;
+        case 2: *r = p; *g = v; *b = t; break;
+        case 3: *r = p; *g = q; *b = v; break;
+        case 4: *r = t; *g = p; *b = v; break;
+        default: *r = v; *g = p; *b = q; break;
+    }
+}
+
+static int v_bin(double v) {
+    double x = floor(256.0 * v);
+    if (!(x >= 0)) x = 0;
+    if (x > 255) x = 255;
+    return (int)x;
+}
+
+/* Equalised V of each bin (lut[256]); returns 0 when the frame is left unchanged. */
+int orc_v_lut(const orc_params* P, const double* rgb, double* lut) {
+    const int n = P->W * P->H;
+    long long cnt[256];
+    memset(cnt, 0, sizeof cnt);
+    for (int i = 0; i < n; ++i) {
+        double h, s, v;
+        orc_rgb_to_hsv(rgb[3 * i], rgb[3 * i + 1], rgb[3 * i + 2], &h, &s, &v);
+        cnt[v_bin(v)]++;
+    }
+    long long cdf = 0, cmin = -1;
+    for (int b = 0; b < 256; ++b) {
+        cdf += cnt[b];
+        if (cmin < 0 && cnt[b] > 0) cmin = cnt[b];
+        lut[b] = (double)cdf; /* cumulative count, mapped below */
+    }
+    if (cmin < 0 || cmin == n) return 0;
+    for (int b = 0; b < 256; ++b) lut[b] = (lut[b] - (double)cmin) / (double)(n - cmin);
+    return 1;
+}
+
+void orc_hsv_equalize(const orc_params* P, const double* in, double* out) {
+    const int n = P->W * P->H;
+    double lut[256];
+    if (!orc_v_lut(P, in, lut)) {
+        memcpy(out, in, sizeof(double) * 3 * (size_t)n);
+        return;
+    }
+    for (int i = 0; i < n; ++i) {
+        double h, s, v;
+        orc_rgb_to_hsv(in[3 * i], in[3 * i + 1], in[3 * i + 2], &h, &s, &v);
+        orc_hsv_to_rgb(h, s, lut[v_bin(v)], &out[3 * i], &out[3 * i + 1], &out[3 * i + 2]);
+    }
+}

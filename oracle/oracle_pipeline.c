@@ -48,9 +48,20 @@ static void pm_run(const orc_params* P, const double* src, const double* tgt, in
         for (int ph = 0; ph < 2; ++ph) orc_pm_sweep(P, src, tgt, dir, level, it, ph, mh, mi, frozen, vx, vy, cost, NULL);
 }
 
-void orc_run(const orc_params* P, const double* f1, const double* f2in, orc_state* S, int stop_after) {
+void orc_run(const orc_params* P, const double* f1in, const double* f2in, orc_state* S, int stop_after) {
     const int W = P->W, H = P->H, n = W * H;
     const size_t nf = (size_t)n * 3;
+    double* f1e = NULL;
+    double* f2e = NULL;
+    const double* f1 = f1in;
+    if (P->equalize) { /* Sec. 4.2: both frames equalised in HSV, then the unchanged method */
+        f1e = (double*)malloc(sizeof(double) * nf);
+        f2e = (double*)malloc(sizeof(double) * nf);
+        orc_hsv_equalize(P, f1in, f1e);
+        orc_hsv_equalize(P, f2in, f2e);
+        f1 = f1e;
+        f2in = f2e;
+    }
     double* f2 = (double*)malloc(sizeof(double) * nf);
     double g = P->gain_normalize ? orc_gain(P, f1, f2in) : 1.0;
     for (size_t i = 0; i < nf; ++i) f2[i] = f2in[i] * g;
@@ -144,4 +155,6 @@ void orc_run(const orc_params* P, const double* f1, const double* f2in, orc_stat
 out:
     for (int d = 0; d < 2; ++d) free(frozen[d]);
     free(f2);
+    free(f1e);
+    free(f2e);
 }

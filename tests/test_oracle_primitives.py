@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from paper_1804_03787_gb300 import scene
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -244,3 +245,74 @@ def test_ransac_recovers_integer_affine_with_outliers():
     assert mi[0, O.MI_COUNT] == 256 - 77 and mi[0, O.MI_NIN] == 256 and mi[0, O.MI_VALID] == 1
     assert mi[0, O.MI_FLAGS] & O.F_REFIT
     np.testing.assert_allclose(_norm(mh[0].reshape(3, 3)), _norm(A_INT), atol=1e-9)
+
+
+# ---------------------------------------------------------------- HSV histogram equalisation (Sec. 4.2)
+def test_hsv_conversion_matches_the_library_routine():
+    """The oracle's hexcone conversion against Python's colorsys, both ways, incl. grays, black and primaries."""
+    import colorsys
+    rng = np.random.default_rng(5)
+    cols = [tuple(c) for c in rng.random((300, 3))] + [(0, 0, 0), (1, 1, 1), (0.3, 0.3, 0.3), (1, 0, 0),
+                                                        (0, 1, 0), (0, 0, 1), (1, 1, 0), (0, 1, 1), (1, 0, 1)]
+    for c in cols:
+        h, s, v = O.rgb_to_hsv(*c)
+        H, S, V = colorsys.rgb_to_hsv(*c)
+        assert abs(h - H) < 1e-12 and abs(s - S) < 1e-12 and abs(v - V) < 1e-12, (c, (h, s, v), (H, S, V))
+        np.testing.assert_allclose(O.hsv_to_rgb(h, s, v), colorsys.hsv_to_rgb(H, S, V), atol=1e-12)
+        np.testing.assert_allclose(O.hsv_to_rgb(h, s, v), c, atol=1e-12)
+
+
+def test_v_lut_closed_form():
+    """Four V levels in distinct bins with counts 10, 20, 30, 40: cumulative 10, 30, 60, 100, so the
+    equalised values are (cdf - 10) / 90 = 0, 2/9, 5/9, 1."""
+    levels = [0.1, 0.3, 0.55, 0.8]
+    counts = [10, 20, 30, 40]
+    px = np.concatenate([np.full((c, 3), v) for v, c in zip(levels, counts)]).reshape(1, 100, 3)
+    P = O.Params(100, 1)
+    ok, lut = O.v_lut(P, px)
+    assert ok
+    bins = [int(np.floor(256 * v)) for v in levels]
+    np.testing.assert_allclose(lut[bins], [0.0, 2 / 9, 5 / 9, 1.0], atol=1e-15)
+    # a frame with one occupied bin is left unchanged
+    flat = np.full((4, 5, 3), 0.42)
+    ok, _ = O.v_lut(O.Params(5, 4), flat)
+    assert not ok
+    np.testing.assert_array_equal(O.hsv_equalize(O.Params(5, 4), flat), flat)
+
+
+def test_hsv_equalize_keeps_hue_and_saturation_and_orders_value():
+    """Per pixel: H and S unchanged (colorsys), V replaced by the LUT value of its bin, monotone in V."""
+    import colorsys
+    rng = np.random.default_rng(8)
+    W, H = 23, 17
+    img = rng.random((H, W, 3)) ** 2
+    img[0, 0] = 0.0
+    P = O.Params(W, H)
+    out = O.hsv_equalize(P, img)
+    ok, lut = O.v_lut(P, img)
+    assert ok
+    vin, vout = [], []
+    for y in range(H):
+        for x in range(W):
+            hi, si, vi = colorsys.rgb_to_hsv(*img[y, x])
+            ho, so, vo = colorsys.rgb_to_hsv(*out[y, x])
+            if vi > 0 and si > 0 and vo > 0:
+                assert abs(hi - ho) < 1e-9 and abs(si - so) < 1e-9
+            assert abs(vo - lut[min(255, int(np.floor(256 * vi)))]) < 1e-12
+            vin.append(vi)
+            vout.append(vo)
+    order = np.argsort(vin, kind="stable")
+    assert np.all(np.diff(np.asarray(vout)[order]) >= -1e-12)
+    # the equalised values fill [0, 1]: lowest occupied bin -> 0, highest -> 1
+    assert min(vout) == 0.0 and abs(max(vout) - 1.0) < 1e-12
+
+
+def test_pipeline_equalises_both_frames_first():
+    """run(equalize=1) on a pair equals run(equalize=0) on the pair equalised beforehand."""
+    s = scene.make_scene(40, 32, seed=3, n_layers=1, max_disp=3.0, affine=True)
+    P1 = O.Params(40, 32, patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=32, equalize=1)
+    P0 = O.Params(40, 32, patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=32, equalize=0)
+    R1 = O.run(P1, s.frame1, s.frame2)
+    R0 = O.run(P0, O.hsv_equalize(P0, s.frame1), O.hsv_equalize(P0, s.frame2))
+    np.testing.assert_array_equal(R1.flow[0], R0.flow[0])
+    np.testing.assert_array_equal(R1.occ[0], R0.occ[0])
