@@ -73,7 +73,7 @@ typedef struct {
     int32_t gain_normalize;               /* 1: scale I2 by mean(I1)/mean(I2) */
     int32_t pm_init;                      /* 1: random initial NNF; 0: keep the current one */
     int32_t storage;                      /* gpm_dtype of the ingested frames */
-    int32_t reserved0;
+    int32_t equalize;                     /* 1: equalise each frame's HSV value histogram first (Sec. 4.2) */
     float eps;                            /* epsilon of eq. 4 (mean |RGB| error, frames in [0,1]) */
     float ransac_px;                      /* RANSAC inlier radius in pixels */
     float fb_px;                          /* forward-backward / many-to-one flow tolerance */

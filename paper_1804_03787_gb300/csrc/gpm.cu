@@ -33,6 +33,8 @@ struct Slot {
     int total_cells = 0, m = 0;
     double* partial = nullptr;
     double* gain = nullptr;
+    int* eq_hist = nullptr;    // 2 x 256 V-histogram counts (HSV equalisation)
+    float* eq_lut = nullptr;   // 2 x 256 equalised V per bin
     unsigned long long* d_evals = nullptr;
 };
 
@@ -147,6 +149,7 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
     if (P.min_inliers < 4) return why = "min_inliers must be >= 4", GPM_EINVAL;
     if (P.fill_iters < 0 || P.fill_iters > 1024) return why = "fill_iters must be 0..1024", GPM_EINVAL;
     if (P.storage < 0 || P.storage > 2) return why = "storage must be GPM_F32, GPM_F16 or GPM_BF16", GPM_EINVAL;
+    if (P.equalize != 0 && P.equalize != 1) return why = "equalize must be 0 or 1", GPM_EINVAL;
     if (!(P.eps > 0) || !(P.ransac_px > 0) || !(P.fb_px > 0)) return why = "eps, ransac_px, fb_px must be > 0", GPM_EINVAL;
     if (!(P.scale_min > 0) || !(P.scale_max >= P.scale_min)) return why = "bad scale range", GPM_EINVAL;
     return GPM_OK;
@@ -189,6 +192,8 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
     double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
     double* gain = (double*)take(sizeof(double));
+    int* eq_hist = (int*)take(2 * 256 * sizeof(int));
+    float* eq_lut = (float*)take(2 * 256 * sizeof(float));
     unsigned long long* evals = (unsigned long long*)take(3 * sizeof(unsigned long long));
     if (s) {
         s->d_evals = evals;
@@ -196,6 +201,8 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells
         s->d_geoms = dg;
         s->partial = partial;
         s->gain = gain;
+        s->eq_hist = eq_hist;
+        s->eq_lut = eq_lut;
     }
     return off;
 }
@@ -468,10 +475,11 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
             if (e) return e;
             s.pair_id = p.pair_id;
             s.pv.pair_id = p.pair_id;
-            pbeg(c, GPM_PROF_INGEST, 4);
+            pbeg(c, GPM_PROF_INGEST, c->P.equalize ? 6 : 4);
             launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
                           s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
-                          const_cast<void*>(s.pv.img[1]), c->stream);
+                          const_cast<void*>(s.pv.img[1]), c->P.equalize ? s.eq_hist : nullptr,
+                          c->P.equalize ? s.eq_lut : nullptr, c->stream);
             reset_models(c, s);
             launch_reset_labels(s.pv, c->P.eps, grid_for(c, s.n), c->stream);
             pend(c);

@@ -16,8 +16,10 @@ struct PmLaunch {
     uint32_t k0, k1;
 };
 void launch_pm(const PmLaunch& L, cudaStream_t st);
+// eq_hist / eq_lut (2 x 256 each, device) non-null: HSV histogram equalisation of both frames first (Sec. 4.2).
 void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
-                   double* partial, int nblk, double* gain, void* o1, void* o2, cudaStream_t st);
+                   double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
+                   cudaStream_t st);
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
 // dst[i] = src[i] / (3 (2 radius + 1)^2): the NNF cost buffer holds raw tap sums, the export means.
 void launch_cost_export(const float* src, float* dst, int n, int radius, cudaStream_t st);

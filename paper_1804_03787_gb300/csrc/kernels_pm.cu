@@ -19,16 +19,93 @@ namespace gpm {
 constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------- ingest
-// Deterministic FP64 sums of both frames: fixed grid, fixed tree.
-__global__ void k_frame_sums(const float* f1, const float* f2, int W, int H, int64_t stride, double* partial) {
+// Optional HSV histogram equalisation (Sec. 4.2): V = max(R, G, B) of each
+// frame is equalised over 256 bins of [0, 1] (bin = min(255, floor(256 V)),
+// V' = (cdf(bin) - cdf_min) / (n - cdf_min), cdf_min the count of the lowest
+// occupied bin) with H and S kept.  At fixed H and S the hexcone RGB is
+// proportional to V, so the equalised pixel is RGB * V' / V (V' grey for
+// black pixels).  A frame with a single occupied bin is left unchanged
+// (its table holds -1).
+__device__ __forceinline__ int v_bin(float v) {
+    float x = floorf(v * 256.f);
+    if (!(x >= 0.f)) x = 0.f;
+    return (int)fminf(x, 255.f);
+}
+
+// V histogram of each frame (blockIdx.y = frame); hist holds 2 x 256 zeroed counts.
+__global__ void k_vhist(const float* f1, const float* f2, int W, int H, int64_t stride, int* hist) {
+    __shared__ int h[256];
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) h[k] = 0;
+    __syncthreads();
+    const float* f = blockIdx.y ? f2 : f1;
+    const int n = W * H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const float* p = f + (int64_t)y * stride + 3 * x;
+        atomicAdd(&h[v_bin(fmaxf(p[0], fmaxf(p[1], p[2])))], 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 256; k += blockDim.x)
+        if (h[k]) atomicAdd(&hist[blockIdx.y * 256 + k], h[k]);
+}
+
+// Equalised V per bin (blockIdx.x = frame, 256 threads): an inclusive scan of the counts.
+__global__ void k_vlut(const int* hist, int n, float* lut) {
+    __shared__ int c[256];
+    __shared__ int cmin;
+    const int t = threadIdx.x;
+    const int* hf = hist + blockIdx.x * 256;
+    c[t] = hf[t];
+    if (t == 0) {
+        cmin = -1;
+        for (int b = 0; b < 256; ++b)
+            if (hf[b] > 0) {
+                cmin = hf[b];
+                break;
+            }
+    }
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        const int v = t >= off ? c[t - off] : 0;
+        __syncthreads();
+        c[t] += v;
+        __syncthreads();
+    }
+    // counts below 2^24 are exact floats, so this is the correctly rounded quotient
+    lut[blockIdx.x * 256 + t] = (cmin < 0 || cmin == n) ? -1.f : (float)(c[t] - cmin) / (float)(n - cmin);
+}
+
+__device__ __forceinline__ float3 equalize_px(float r, float g, float b, const float* lut) {
+    const float v = fmaxf(r, fmaxf(g, b));
+    const float l = lut[v_bin(v)];
+    if (l < 0.f) return make_float3(r, g, b);
+    if (v > 0.f) {
+        const float k = l / v;
+        return make_float3(r * k, g * k, b * k);
+    }
+    return make_float3(l, l, l);
+}
+
+// Deterministic FP64 sums of both frames (after equalisation when lut is set): fixed grid, fixed tree.
+__global__ void k_frame_sums(const float* f1, const float* f2, int W, int H, int64_t stride, const float* lut,
+                             double* partial) {
     __shared__ double sh[2][256];
     double a = 0, b = 0;
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
         const float* r1 = f1 + (int64_t)y * stride;
         const float* r2 = f2 + (int64_t)y * stride;
-        for (int k = threadIdx.x; k < 3 * W; k += blockDim.x) {
-            a += (double)r1[k];
-            b += (double)r2[k];
+        if (lut) {
+            for (int x = threadIdx.x; x < W; x += blockDim.x) {
+                const float3 p = equalize_px(r1[3 * x], r1[3 * x + 1], r1[3 * x + 2], lut);
+                const float3 q = equalize_px(r2[3 * x], r2[3 * x + 1], r2[3 * x + 2], lut + 256);
+                a += (double)p.x + (double)p.y + (double)p.z;
+                b += (double)q.x + (double)q.y + (double)q.z;
+            }
+        } else {
+            for (int k = threadIdx.x; k < 3 * W; k += blockDim.x) {
+                a += (double)r1[k];
+                b += (double)r2[k];
+            }
         }
     }
     sh[0][threadIdx.x] = a;
@@ -77,16 +154,21 @@ __device__ __forceinline__ void store_pix(void* base, int i, float r, float g, f
 }
 
 template <int ST>
-__global__ void k_pack(const float* f1, const float* f2, int W, int H, int64_t stride, const double* gain, void* o1,
-                       void* o2) {
+__global__ void k_pack(const float* f1, const float* f2, int W, int H, int64_t stride, const double* gain,
+                       const float* lut, void* o1, void* o2) {
     const double g = *gain;
     const int n = W * H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
         const float* a = f1 + (int64_t)y * stride + 3 * x;
         const float* b = f2 + (int64_t)y * stride + 3 * x;
-        store_pix<ST>(o1, i, a[0], a[1], a[2]);
-        store_pix<ST>(o2, i, (float)((double)b[0] * g), (float)((double)b[1] * g), (float)((double)b[2] * g));
+        float3 p = make_float3(a[0], a[1], a[2]), q = make_float3(b[0], b[1], b[2]);
+        if (lut) {
+            p = equalize_px(p.x, p.y, p.z, lut);
+            q = equalize_px(q.x, q.y, q.z, lut + 256);
+        }
+        store_pix<ST>(o1, i, p.x, p.y, p.z);
+        store_pix<ST>(o2, i, (float)((double)q.x * g), (float)((double)q.y * g), (float)((double)q.z * g));
     }
 }
 
@@ -590,14 +672,22 @@ void launch_pm(const PmLaunch& L, cudaStream_t st) {
 }
 
 void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
-                   double* partial, int nblk, double* gain, void* o1, void* o2, cudaStream_t st) {
-    k_frame_sums<<<nblk, 256, 0, st>>>(f1, f2, W, H, stride, partial);
-    k_gain<<<1, 32, 0, st>>>(partial, nblk, gain_enable, gain);
+                   double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
+                   cudaStream_t st) {
     const int blocks = 152 * 4;
+    const float* lut = nullptr;
+    if (eq_hist && eq_lut) {
+        cudaMemsetAsync(eq_hist, 0, 2 * 256 * sizeof(int), st);
+        k_vhist<<<dim3(blocks, 2), 256, 0, st>>>(f1, f2, W, H, stride, eq_hist);
+        k_vlut<<<2, 256, 0, st>>>(eq_hist, W * H, eq_lut);
+        lut = eq_lut;
+    }
+    k_frame_sums<<<nblk, 256, 0, st>>>(f1, f2, W, H, stride, lut, partial);
+    k_gain<<<1, 32, 0, st>>>(partial, nblk, gain_enable, gain);
     switch (storage) {
-        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
-        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
-        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, lut, o1, o2); break;
+        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, lut, o1, o2); break;
+        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, lut, o1, o2); break;
     }
 }
 
@@ -605,9 +695,9 @@ void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride,
                  void* o1, void* o2, cudaStream_t st) {
     const int blocks = 152 * 4;
     switch (storage) {
-        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
-        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
-        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, o1, o2); break;
+        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
+        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
+        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
     }
 }
 

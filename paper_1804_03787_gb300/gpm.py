@@ -39,7 +39,7 @@ class Params(C.Structure):
     _fields_ = [("patch_radius", C.c_int32), ("num_scales", C.c_int32), ("cell_size", C.c_int32 * MAX_SCALES),
                 ("pm_iters", C.c_int32), ("num_hyp", C.c_int32), ("min_inliers", C.c_int32),
                 ("fill_iters", C.c_int32), ("gain_normalize", C.c_int32), ("pm_init", C.c_int32),
-                ("storage", C.c_int32), ("reserved0", C.c_int32), ("eps", C.c_float), ("ransac_px", C.c_float),
+                ("storage", C.c_int32), ("equalize", C.c_int32), ("eps", C.c_float), ("ransac_px", C.c_float),
                 ("fb_px", C.c_float), ("eta", C.c_float), ("kappa", C.c_float), ("beta", C.c_float),
                 ("occ_thresh", C.c_float), ("scale_min", C.c_float), ("scale_max", C.c_float),
                 ("seed", C.c_uint64)]

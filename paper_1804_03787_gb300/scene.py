@@ -27,7 +27,8 @@ Recipe (all randomness from ``numpy.random.default_rng(seed)``):
 * ground-truth flow ``f(p) = H_z(p) p - p`` for the topmost layer ``z(p)`` of
   frame 1; ground-truth occlusion: ``p + f(p)`` leaves the frame or another
   layer is on top there in frame 2;
-* photometrics: frame 2 multiplied by a gain ``g ~ U[gain_lo, gain_hi]``,
+* photometrics: frame 2 multiplied by a gain ``g ~ U[gain_lo, gain_hi]`` (and, if
+  ``gamma`` != 1, raised to that power: a non-uniform illumination change),
   Gaussian noise of std ``noise`` on both frames, clamped to [0, 1], stored as
   float32 HxWx3.
 """
@@ -197,7 +198,7 @@ class Scene:
 
 def make_scene(width: int, height: int, seed: int = 0, n_layers: int = 2, max_disp: float = 8.0,
                affine: bool = False, bg_disp: float | None = None, gain: tuple = (0.8, 1.2),
-               noise: float = 2.0 / 255.0, area_frac: tuple = (0.05, 0.25)) -> Scene:
+               noise: float = 2.0 / 255.0, area_frac: tuple = (0.05, 0.25), gamma: float = 1.0) -> Scene:
     """Render one seeded frame pair with exact flow and occlusion ground truth."""
     rng = np.random.default_rng(seed)
     W, H = int(width), int(height)
@@ -267,6 +268,8 @@ def make_scene(width: int, height: int, seed: int = 0, n_layers: int = 2, max_di
 
     g = float(rng.uniform(*gain))
     f2 = f2 * g
+    if gamma != 1.0:  # a non-uniform illumination change of frame 2: I -> I^gamma
+        f2 = np.clip(f2, 0.0, 1.0) ** gamma
     f1 = f1 + rng.normal(0.0, noise, size=f1.shape)
     f2 = f2 + rng.normal(0.0, noise, size=f2.shape)
     f1 = np.clip(f1, 0.0, 1.0).astype(np.float32)

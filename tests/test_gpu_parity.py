@@ -476,3 +476,46 @@ def test_reduced_precision_end_to_end(torch, kind, storage):
     assert abs(epe_g - epe_q) < 0.01
     assert abs(epe_g - epe_o) < 0.1
     ctx.close()
+
+
+# ---------------------------------------------------------------- HSV histogram equalisation (Sec. 4.2)
+def test_equalized_ingest_matches_oracle(torch):
+    """Ingest with equalize=1: both stored frames against the oracle's FP64 equalisation (then gain). The GPU
+    rescales RGB by V'/V in FP32, the oracle goes through HSV and back in FP64: a few float roundings apart."""
+    W, H = 70, 45
+    s = _scene(W, H, seed=31)
+    gp = gpm.default_params(patch_radius=2, cells=(16, 8), pm_iters=0, num_hyp=32, equalize=1)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    fr = ctx.export(gpm.FRAMES)
+    P = oracle_params(gp, W, H)
+    e1 = O.hsv_equalize(P, s.frame1)
+    e2 = O.hsv_equalize(P, s.frame2)
+    g = O.gain(P, e1, e2)
+    np.testing.assert_allclose(fr[0, ..., :3], e1, rtol=1e-6, atol=1e-7)
+    np.testing.assert_allclose(fr[1, ..., :3], e2 * g, rtol=1e-6, atol=1e-7)
+    # equalisation changed the frames (the scenes do not fill [0, 1] evenly)
+    assert np.abs(e1 - s.frame1).max() > 0.05
+    ctx.close()
+
+
+def test_equalized_tiny_end_to_end(torch):
+    """Tiny config with equalize=1 against the oracle with equalize=1: the bars of the plain end-to-end test."""
+    s = scene.tiny_scene(0)
+    gp = gpm.default_params(equalize=1)
+    ctx = _ctx(torch, gp, 128, 96)
+    flows, occs = ctx.run([_dev(torch, s)])
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy()
+    P = oracle_params(gp, 128, 96)
+    assert P.equalize == 1
+    R = O.run(P, s.frame1, s.frame2)
+    oflow = R.flow[0].reshape(96, 128, 2)
+    vis = s.occ == 0
+    agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-4)
+    epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    epe_o = np.hypot(*(oflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    print(f"equalized tiny: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
+    assert agree > 0.95
+    assert abs(epe_g - epe_o) < 0.01
+    ctx.close()
