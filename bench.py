@@ -421,6 +421,38 @@ def equalized_block(scenes, dev, flows32, flush):
                         "plus one scene of the same kind whose frame 2 is also raised to the power 1.3"}
 
 
+LEVEL_STUDY = {"1 level (64)": (4, (64,)), "2 levels (64/32)": (4, (64, 32)), "3 levels (64/32/16)": (4, (64, 32, 16)),
+               "4 levels (64/32/16/8)": (4, (64, 32, 16, 8)), "5 levels (64/32/16/8/4)": (4, (64, 32, 16, 8, 4)),
+               "paper preset (7x7 patches, 2 levels of 80/40 px windows)": (3, (80, 40))}
+
+
+def level_study_block(scenes, dev):
+    """EPE on non-occluded pixels and time per pair against the number of levels (and the paper's own 2-level
+    preset) on the headline scenes: the level-count study of the paper's Sec. 4 and 6."""
+    import numpy as np
+    import torch
+
+    from paper_1804_03787_gb300 import gpm
+    out = {}
+    for name, (r, cells) in LEVEL_STUDY.items():
+        gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=ITERS, num_hyp=HYP)
+        ctx = gpm.Context(gp, W, H)
+        ctx.run([dev[0]], pair_ids=[0])
+        ms, epe = 0.0, []
+        for k, sc in enumerate(scenes):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f, _ = ctx.run([dev[k]], pair_ids=[k])
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            epe.append(float(np.sqrt(((f[0].cpu().numpy() - sc.flow) ** 2).sum(-1))[sc.occ == 0].mean()))
+        ctx.close()
+        out[name] = {"epe_nocc_px": float(np.mean(epe)), "ms_per_pair": ms / len(scenes)}
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
@@ -577,6 +609,10 @@ def run_ours(args):
             line["hsv_equalized"] = equalized_block(scenes, dev, flows32, flush)
         except Exception as e:
             line["hsv_equalized"] = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            line["level_study"] = level_study_block(scenes, dev)
+        except Exception as e:
+            line["level_study"] = {"error": f"{type(e).__name__}: {e}"}
     ctx.close()
     del ctx
     torch.cuda.empty_cache()

@@ -65,7 +65,7 @@ typedef enum { GPM_F32 = 0, GPM_F16 = 1, GPM_BF16 = 2 } gpm_dtype;
 typedef struct {
     int32_t patch_radius;                 /* r: 3 -> 7x7 (Sec. 4), 4 -> 9x9 */
     int32_t num_scales;                   /* levels k of Sec. 3.3 */
-    int32_t cell_size[GPM_MAX_SCALES];    /* window side per level, coarse to fine; even, >= 4 */
+    int32_t cell_size[GPM_MAX_SCALES];    /* window side per level, coarse to fine; even, 4..96 */
     int32_t pm_iters;                     /* PatchMatch red-black iterations per run */
     int32_t num_hyp;                      /* RANSAC hypotheses per window, 1..4096 */
     int32_t min_inliers;                  /* minimum RANSAC support (>= 4) */

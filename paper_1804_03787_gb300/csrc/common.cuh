@@ -10,6 +10,7 @@
 
 namespace gpm {
 
+constexpr int kMaxCell = 96;  // largest window side (its matches fill 144 KiB of shared memory in RANSAC)
 constexpr int kMI = 12;  // integer fields per model (layout of GPM_MODEL_INFO)
 // A warped sample point counts as inside the frame up to this far (px)
 // beyond the border: clamped bilinear sampling is continuous there, and

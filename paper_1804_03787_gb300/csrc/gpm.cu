@@ -142,7 +142,7 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
     if (P.num_scales < 0 || P.num_scales > GPM_MAX_SCALES) return why = "num_scales must be 0..8", GPM_EINVAL;
     for (int l = 0; l < P.num_scales; ++l) {
         const int s = P.cell_size[l];
-        if (s < 4 || s > 64 || (s & 1)) return why = "cell sizes must be even, 4..64", GPM_EINVAL;
+        if (s < 4 || s > kMaxCell || (s & 1)) return why = "cell sizes must be even, 4..96", GPM_EINVAL;
     }
     if (P.pm_iters < 0 || P.pm_iters > 64) return why = "pm_iters must be 0..64", GPM_EINVAL;
     if (P.num_hyp < 1 || P.num_hyp > 4096) return why = "num_hyp must be 1..4096", GPM_EINVAL;

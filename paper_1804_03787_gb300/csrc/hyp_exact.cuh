@@ -4,7 +4,7 @@
 // homography in FP64 was the bottleneck of the per-window fit.  Here the
 // projective-basis solution H ~ B adj(A) (see minimal_h in
 // kernels_planes.cu) is formed exactly in 128-bit integers -- window-local
-// coordinates keep every entry below 2^75 -- and the FP32 evaluation form is
+// coordinates keep every entry below 2^89 -- and the FP32 evaluation form is
 // derived from exact integer numerators with one rounding each; the
 // translation, which needs ~1e-7 px absolute accuracy on flows of hundreds of
 // pixels, is split into hi + lo with an exact integer remainder.
@@ -38,7 +38,7 @@ __host__ __device__ __forceinline__ float u32_to_float(uint32_t v) {
 #endif
 }
 
-// Float near a 128-bit integer below 2^96 in magnitude (ours stay below 2^76):
+// Float near a 128-bit integer below 2^96 in magnitude (ours stay below 2^92):
 // the 32-bit limbs combined by fused multiply-adds, within about 1 ulp -- every
 // caller tolerates that (the translation is corrected by an exact remainder).
 __host__ __device__ __forceinline__ float i128_to_float(i128 x) {
@@ -56,7 +56,7 @@ __host__ __device__ __forceinline__ float i128_to_float(i128 x) {
 
 // 4-point homography, exact: H = B adj(A) with the projective bases of the
 // source points (A) and target points (B); window-local integer coordinates
-// (|source| <= 32, |target| <= 2080).
+// (|source| <= 48, |target| < 2^15).
 __host__ __device__ inline void minimal_h_exact(const int* px, const int* py, const int* qx, const int* qy,
                                                 i128* H) {
     int A[9];
@@ -86,18 +86,20 @@ __host__ __device__ inline void minimal_h_exact(const int* px, const int* py, co
     adj[6] = (int64_t)A[3] * A[7] - (int64_t)A[4] * A[6];
     adj[7] = (int64_t)A[1] * A[6] - (int64_t)A[0] * A[7];
     adj[8] = (int64_t)A[0] * A[4] - (int64_t)A[1] * A[3];
-    // H = Q diag(mu) adj(A) = Q C with C = diag(mu) adj(A): |mu| < 2^25 and
-    // |adj| < 2^37 keep C in 64 bits, and Q holds 12-bit coordinates (last row 1).
-    int64_t Cm[9];
+    // H = Q diag(mu) adj(A) = Q C with C = diag(mu) adj(A).  Bounds for windows
+    // up to 96 px (|source| <= 48) and frames up to 32767 px (|target| < 2^15):
+    // |A| < 2^19.4, |adj| < 2^39.8, |mu| < 2^32.6, so C needs 128 bits
+    // (< 2^72.4) and |H| < 2^89 (Q holds 16-bit coordinates, last row 1).
+    i128 Cm[9];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Cm[k * 3 + c] = mu[k] * adj[k * 3 + c];
+        for (int c = 0; c < 3; ++c) Cm[k * 3 + c] = (i128)mu[k] * adj[k * 3 + c];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        H[0 * 3 + c] = (i128)Cm[c] * qx[0] + (i128)Cm[3 + c] * qx[1] + (i128)Cm[6 + c] * qx[2];
-        H[1 * 3 + c] = (i128)Cm[c] * qy[0] + (i128)Cm[3 + c] * qy[1] + (i128)Cm[6 + c] * qy[2];
-        H[2 * 3 + c] = (i128)Cm[c] + (i128)Cm[3 + c] + (i128)Cm[6 + c];
+        H[0 * 3 + c] = Cm[c] * qx[0] + Cm[3 + c] * qx[1] + Cm[6 + c] * qx[2];
+        H[1 * 3 + c] = Cm[c] * qy[0] + Cm[3 + c] * qy[1] + Cm[6 + c] * qy[2];
+        H[2 * 3 + c] = Cm[c] + Cm[3 + c] + Cm[6 + c];
     }
 }
 

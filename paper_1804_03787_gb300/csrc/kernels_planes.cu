@@ -1259,8 +1259,9 @@ static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, 
     const size_t smem = (size_t)g.s * g.s * sizeof(float4);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_ransac_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
-        cudaFuncSetAttribute(k_ransac_finish_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024 + 1024);
+        const int mx = kMaxCell * kMaxCell * (int)sizeof(float4);  // the largest window's matches
+        cudaFuncSetAttribute(k_ransac_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_ransac_finish_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr_set = true;
     }
     k_ransac_block<ST><<<dim3(nc, 2), 256, smem, st>>>(pv, g, level, stage, pp);

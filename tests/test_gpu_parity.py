@@ -519,3 +519,26 @@ def test_equalized_tiny_end_to_end(torch):
     assert agree > 0.95
     assert abs(epe_g - epe_o) < 0.01
     ctx.close()
+
+
+# ---------------------------------------------------------------- large windows (the paper's preset sizes)
+def test_large_windows_end_to_end(torch):
+    """Windows of 80 and 40 px (the paper's radius-40/20 windows, 2 levels, 7x7 patches) on a 192x112 pair:
+    the whole method against the oracle, with the bars of the tiny end-to-end test."""
+    W, H = 192, 112
+    s = scene.make_scene(W, H, seed=9, n_layers=2, max_disp=6.0, affine=True)
+    gp = gpm.default_params(patch_radius=3, cells=(80, 40), pm_iters=4, num_hyp=128)
+    ctx = _ctx(torch, gp, W, H)
+    flows, _ = ctx.run([_dev(torch, s)])
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy()
+    R = O.run(oracle_params(gp, W, H), s.frame1, s.frame2)
+    oflow = R.flow[0].reshape(H, W, 2)
+    vis = s.occ == 0
+    agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-4)
+    epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    epe_o = np.hypot(*(oflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    print(f"80/40 windows: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
+    assert agree > 0.95
+    assert abs(epe_g - epe_o) < 0.01
+    ctx.close()
