@@ -30,7 +30,9 @@ typedef struct {
     int32_t cell[ORC_MAX_SCALES];    /* window side per level, coarse to fine */
     int32_t pm_iters, num_hyp, min_inliers, fill_iters;
     int32_t gain_normalize, pm_init;
-    int32_t equalize, pad0;          /* equalize: HSV V-channel histogram equalisation of both frames (Sec. 4.2) */
+    int32_t equalize;                /* HSV V-channel histogram equalisation of both frames (Sec. 4.2) */
+    int32_t census;                  /* census data term for the level-0 NNF (Sec. 6); inside the PatchMatch
+                                        routines: the frames given are census code frames */
     double eps, ransac_px, fb_px, eta, kappa, beta, occ_thresh, scale_min, scale_max;
     uint64_t seed;
     uint32_t pair_id, pad;
@@ -144,6 +146,9 @@ void orc_rgb_to_hsv(double r, double g, double b, double* h, double* s, double* 
 void orc_hsv_to_rgb(double h, double s, double v, double* r, double* g, double* b);
 int orc_v_lut(const orc_params* P, const double* rgb, double* lut);      /* 0: frame left unchanged */
 void orc_hsv_equalize(const orc_params* P, const double* in, double* out);
+/* ---- census data term (Sec. 6), oracle_color.c ---- */
+void orc_census(const orc_params* P, const double* rgb, double* codes);   /* code frame: (code, 0, 0) per pixel */
+int orc_popcount32(uint32_t v);
 
 /* ---- whole method (Algorithm 1 for every level, then Sec. 3.4) ---- */
 typedef struct {

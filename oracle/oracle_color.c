@@ -107,3 +107,54 @@ void orc_hsv_equalize(const orc_params* P, const double* in, double* out) {
         orc_hsv_to_rgb(h, s, lut[v_bin(v)], &out[3 * i], &out[3 * i + 1], &out[3 * i + 2]);
     }
 }
+
+/*
+ * Census transform data term (Sec. 6 names census as an illumination-robust
+ * data term for the framework).  Reading: grey = R + G + B (FP64); the code
+ * of a pixel has one bit per neighbour of its 5x5 window in raster order
+ * without the centre (24 bits, neighbour coordinates clamped into the frame),
+ * set iff the neighbour's grey is strictly below the centre's.  Codes come
+ * from the frames as given: census is unchanged by a global gain.  Written as
+ * a "code frame" (code, 0, 0 per pixel) that the PatchMatch routines read
+ * when P->census is set: the patch cost is then the sum over taps of the
+ * Hamming distance of the two codes, over 24 T.
+ */
+#define ORC_CENSUS_R 2
+#define ORC_CENSUS_BITS 24
+
+static double grey(const double* rgb, int W, int x, int y) {
+    const double* p = rgb + ((size_t)y * W + x) * 3;
+    return (p[0] + p[1]) + p[2];
+}
+
+void orc_census(const orc_params* P, const double* rgb, double* codes) {
+    const int W = P->W, H = P->H;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const double c = grey(rgb, W, x, y);
+            uint32_t code = 0;
+            int bit = 0;
+            for (int dy = -ORC_CENSUS_R; dy <= ORC_CENSUS_R; ++dy)
+                for (int dx = -ORC_CENSUS_R; dx <= ORC_CENSUS_R; ++dx) {
+                    if (dx == 0 && dy == 0) continue;
+                    int nx = x + dx, ny = y + dy;
+                    nx = nx < 0 ? 0 : (nx > W - 1 ? W - 1 : nx);
+                    ny = ny < 0 ? 0 : (ny > H - 1 ? H - 1 : ny);
+                    if (grey(rgb, W, nx, ny) < c) code |= 1u << bit;
+                    ++bit;
+                }
+            double* o = codes + ((size_t)y * W + x) * 3;
+            o[0] = (double)code;
+            o[1] = 0.0;
+            o[2] = 0.0;
+        }
+}
+
+int orc_popcount32(uint32_t v) {
+    int n = 0;
+    while (v) {
+        v &= v - 1;
+        ++n;
+    }
+    return n;
+}

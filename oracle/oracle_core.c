@@ -124,6 +124,17 @@ static inline void apply_h(const double* G, double x, double y, double* X, doubl
 double orc_patch_cost(const orc_params* P, const double* src, const double* tgt,
                       int px, int py, int vx, int vy, const double* G) {
     const int W = P->W, H = P->H, r = P->r;
+    if (P->census && !G) { /* census code frames: Hamming distance per tap (Sec. 6) */
+        long long sum = 0;
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx) {
+                int sx = clampi(px + dx, 0, W - 1), sy = clampi(py + dy, 0, H - 1);
+                int tx = clampi(sx + vx, 0, W - 1), ty = clampi(sy + vy, 0, H - 1);
+                uint32_t a = (uint32_t)src[((size_t)sy * W + sx) * 3], b = (uint32_t)tgt[((size_t)ty * W + tx) * 3];
+                sum += orc_popcount32(a ^ b);
+            }
+        return (double)sum / (24.0 * (2 * r + 1) * (2 * r + 1));
+    }
     double gpx = 0, gpy = 0, sum = 0.0, s[3];
     if (G) apply_h(G, px, py, &gpx, &gpy);
     for (int dy = -r; dy <= r; ++dy) {

@@ -48,9 +48,21 @@ static void pm_run(const orc_params* P, const double* src, const double* tgt, in
         for (int ph = 0; ph < 2; ++ph) orc_pm_sweep(P, src, tgt, dir, level, it, ph, mh, mi, frozen, vx, vy, cost, NULL);
 }
 
-void orc_run(const orc_params* P, const double* f1in, const double* f2in, orc_state* S, int stop_after) {
-    const int W = P->W, H = P->H, n = W * H;
+void orc_run(const orc_params* Pin, const double* f1in, const double* f2in, orc_state* S, int stop_after) {
+    const int W = Pin->W, H = Pin->H, n = W * H;
     const size_t nf = (size_t)n * 3;
+    /* census data term (Sec. 6): code frames of the frames as given, read by the level-0 PatchMatch only */
+    const orc_params P0 = *Pin;
+    orc_params Pc = *Pin;
+    Pc.census = 0;
+    const orc_params* P = &Pc;
+    double* code[2] = {NULL, NULL};
+    if (P0.census) {
+        code[0] = (double*)malloc(sizeof(double) * nf);
+        code[1] = (double*)malloc(sizeof(double) * nf);
+        orc_census(&P0, f1in, code[0]);
+        orc_census(&P0, f2in, code[1]);
+    }
     double* f1e = NULL;
     double* f2e = NULL;
     const double* f1 = f1in;
@@ -83,11 +95,13 @@ void orc_run(const orc_params* P, const double* f1in, const double* f2in, orc_st
     }
     /* level 0: plain PatchMatch (Sec. 3.1, 7x7 patches in Sec. 4) */
     for (int d = 0; d < 2; ++d) {
+        const double* s0 = P0.census ? code[d] : src[d];
+        const double* t0 = P0.census ? code[1 - d] : tgt[d];
         if (P->pm_init)
-            orc_pm_init(P, src[d], tgt[d], d, S->vx[d], S->vy[d], S->cost[d]);
+            orc_pm_init(&P0, s0, t0, d, S->vx[d], S->vy[d], S->cost[d]);
         else
-            orc_pm_recost(P, src[d], tgt[d], 0, NULL, NULL, NULL, S->vx[d], S->vy[d], S->cost[d]);
-        pm_run(P, src[d], tgt[d], d, 0, NULL, NULL, NULL, S->vx[d], S->vy[d], S->cost[d]);
+            orc_pm_recost(&P0, s0, t0, 0, NULL, NULL, NULL, S->vx[d], S->vy[d], S->cost[d]);
+        pm_run(&P0, s0, t0, d, 0, NULL, NULL, NULL, S->vx[d], S->vy[d], S->cost[d]);
     }
     if (stop_after == 0) goto out;
     {
@@ -157,4 +171,6 @@ out:
     free(f2);
     free(f1e);
     free(f2e);
+    free(code[0]);
+    free(code[1]);
 }

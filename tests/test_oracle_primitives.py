@@ -316,3 +316,79 @@ def test_pipeline_equalises_both_frames_first():
     R0 = O.run(P0, O.hsv_equalize(P0, s.frame1), O.hsv_equalize(P0, s.frame2))
     np.testing.assert_array_equal(R1.flow[0], R0.flow[0])
     np.testing.assert_array_equal(R1.occ[0], R0.occ[0])
+
+
+# ---------------------------------------------------------------- census data term (Sec. 6)
+def _census_bit(dx, dy):
+    """Bit index of the neighbour at (dx, dy) in the 5x5 window, raster order without the centre."""
+    k = (dy + 2) * 5 + (dx + 2)
+    return k if k < 12 else k - 1
+
+
+def test_census_closed_forms():
+    """Constant frame: every code 0.  One dark pixel in a flat bright frame: its code is 0 and each pixel within
+    2 of it has exactly the bit pointing at it.  One bright pixel: its code has all 24 bits, the rest are 0."""
+    W, H = 11, 9
+    P = O.Params(W, H)
+    flat = np.full((H, W, 3), 0.6)
+    assert not O.census(P, flat)[..., 0].any()
+    dark = flat.copy()
+    dark[4, 5] = 0.1
+    c = O.census(P, dark)[..., 0].astype(np.int64)
+    for y in range(H):
+        for x in range(W):
+            a, b = 5 - x, 4 - y  # the dark pixel relative to (x, y)
+            want = (1 << _census_bit(a, b)) if (max(abs(a), abs(b)) <= 2 and (a, b) != (0, 0)) else 0
+            assert c[y, x] == want, (x, y, c[y, x], want)
+    bright = flat.copy()
+    bright[4, 5] = 0.9
+    c = O.census(P, bright)[..., 0].astype(np.int64)
+    assert c[4, 5] == (1 << 24) - 1 and np.count_nonzero(c) == 1
+
+
+def test_census_invariant_under_monotone_grey_changes():
+    """Codes compare greys only: a strictly increasing map of a grey frame, or a gain of 2 (exact), keeps them."""
+    rng = np.random.default_rng(4)
+    W, H = 19, 13
+    P = O.Params(W, H)
+    t = rng.random((H, W))
+    grey = np.repeat(t[..., None], 3, axis=2)
+    c0 = O.census(P, grey)
+    np.testing.assert_array_equal(O.census(P, grey ** 2), c0)
+    np.testing.assert_array_equal(O.census(P, np.sqrt(grey) + 0.25), c0)
+    colour = rng.random((H, W, 3))
+    np.testing.assert_array_equal(O.census(P, 2.0 * colour), O.census(P, colour))
+
+
+def test_census_cost_finds_an_integer_shift_exhaustively():
+    """Hamming patch cost on code frames: zero at offset 0 against itself, and on a frame against its copy shifted
+    by (3, -2) the exhaustive argmin over offsets is that shift at interior pixels."""
+    rng = np.random.default_rng(11)
+    W, H = 28, 22
+    P = O.Params(W, H, patch_radius=2, census=1)
+    f1 = rng.random((H, W, 3))
+    f2 = np.roll(f1, shift=(-2, 3), axis=(0, 1))  # f2(x + 3, y - 2) = f1(x, y)
+    c1, c2 = O.census(P, f1), O.census(P, f2)
+    assert O.patch_cost(P, c1, c1, 10, 10, 0, 0) == 0.0
+    for (x, y) in [(9, 8), (12, 11), (15, 9)]:
+        best = min(((O.patch_cost(P, c1, c2, x, y, vx, vy), (vx, vy))
+                    for vy in range(-5, 6) for vx in range(-5, 6)))
+        assert best[1] == (3, -2) and best[0] == 0.0
+
+
+def test_pipeline_census_level0_uses_code_frames():
+    """run(census=1) stopped after level 0 equals PatchMatch run directly on the census code frames."""
+    s = scene.make_scene(36, 28, seed=6, n_layers=1, max_disp=3.0, affine=True)
+    P = O.Params(36, 28, patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=32, census=1)
+    R = O.run(P, s.frame1, s.frame2, stop_after=0)
+    c1, c2 = O.census(P, s.frame1), O.census(P, s.frame2)
+    n = 36 * 28
+    frozen = np.zeros(n, np.uint8)
+    for d, (src, tgt) in enumerate([(c1, c2), (c2, c1)]):
+        vx, vy, cost = O.pm_init(P, src, tgt, d)
+        for it in range(P.pm_iters):
+            for ph in range(2):
+                O.pm_sweep(P, src, tgt, d, 0, it, ph, None, None, frozen, vx, vy, cost)
+        np.testing.assert_array_equal(R.vx[d], vx)
+        np.testing.assert_array_equal(R.vy[d], vy)
+        np.testing.assert_array_equal(R.cost[d], cost)
