@@ -82,6 +82,7 @@ typedef struct {
     float beta;                           /* coarse-level priority margin in the merge */
     float occ_thresh;                     /* final warp-error occlusion threshold */
     float scale_min, scale_max;           /* plane validity: local area scale range */
+    int32_t census;                       /* 1: level-0 PatchMatch on 5x5 census codes, Hamming cost (Sec. 6) */
     uint64_t seed;                        /* Philox4x32-10 key */
 } gpm_params;
 

@@ -353,6 +353,7 @@ struct PairView {
     int* list_count;      // [2 dirs][2 colours]
     unsigned long long* m2o_key[2];
     RefitWork* rw[2];     // [cells of the largest level]
+    uint32_t* code[2];    // census codes of each frame (census data term)
     unsigned long long* evals;  // [PM evaluations level 0, levels >= 1, RANSAC residual tests], or nullptr
 };
 

@@ -33,6 +33,7 @@ struct Slot {
     int total_cells = 0, m = 0;
     double* partial = nullptr;
     double* gain = nullptr;
+    bool census_costs = false;  // the NNF costs are census Hamming sums (level 0 with the census data term)
     int* eq_hist = nullptr;    // 2 x 256 V-histogram counts (HSV equalisation)
     float* eq_lut = nullptr;   // 2 x 256 equalised V per bin
     unsigned long long* d_evals = nullptr;
@@ -150,6 +151,8 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
     if (P.fill_iters < 0 || P.fill_iters > 1024) return why = "fill_iters must be 0..1024", GPM_EINVAL;
     if (P.storage < 0 || P.storage > 2) return why = "storage must be GPM_F32, GPM_F16 or GPM_BF16", GPM_EINVAL;
     if (P.equalize != 0 && P.equalize != 1) return why = "equalize must be 0 or 1", GPM_EINVAL;
+    if (P.census != 0 && P.census != 1) return why = "census must be 0 or 1", GPM_EINVAL;
+    if (P.census && !P.pm_init) return why = "census needs pm_init = 1 (a random initial NNF)", GPM_EINVAL;
     if (!(P.eps > 0) || !(P.ransac_px > 0) || !(P.fb_px > 0)) return why = "eps, ransac_px, fb_px must be > 0", GPM_EINVAL;
     if (!(P.scale_min > 0) || !(P.scale_max >= P.scale_min)) return why = "bad scale range", GPM_EINVAL;
     return GPM_OK;
@@ -187,6 +190,7 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells
         pv.list[d] = (int*)take(2 * n * sizeof(int));
         pv.m2o_key[d] = (unsigned long long*)take(n * sizeof(unsigned long long));
         pv.rw[d] = (RefitWork*)take((size_t)max_cells * sizeof(RefitWork));
+        pv.code[d] = (uint32_t*)take(n * sizeof(uint32_t));
     }
     pv.list_count = (int*)take(4 * sizeof(int));
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
@@ -283,6 +287,8 @@ void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
     L.grid_blocks = c->nsm * 8;
     L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
     L.k1 = (uint32_t)(c->P.seed >> 32);
+    L.census = level == 0 ? c->P.census : 0;
+    s.census_costs = L.census != 0;
     if (level > 0 || !c->P.pm_init) {
         L.op = PmLaunch::RECOST;
         pbeg(c, GPM_PROF_PM_RECOST, 1);
@@ -475,6 +481,13 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
             if (e) return e;
             s.pair_id = p.pair_id;
             s.pv.pair_id = p.pair_id;
+            if (c->P.census) {  // codes of the frames as given (census ignores a global gain)
+                pbeg(c, GPM_PROF_INGEST, 2);
+                launch_census(p.frame1, p.frame2, p.width, p.height, p.row_stride,
+                              reinterpret_cast<long long*>(s.pv.m2o_key[0]), reinterpret_cast<long long*>(s.pv.m2o_key[1]),
+                              s.pv.code[0], s.pv.code[1], c->stream);
+                pend(c);
+            }
             pbeg(c, GPM_PROF_INGEST, c->P.equalize ? 6 : 4);
             launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
                           s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
@@ -492,6 +505,7 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
                 L.grid_blocks = c->nsm * 8;
                 L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
                 L.k1 = (uint32_t)(c->P.seed >> 32);
+                L.census = c->P.census;
                 pbeg(c, GPM_PROF_PM_INIT, 1);
                 launch_pm(L, c->stream);
                 pend(c);
@@ -598,7 +612,8 @@ gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
             break;
         case GPM_COST:
             for (int k = 0; k < 2; ++k)
-                launch_cost_export(s.pv.cost[k], (float*)(d + k * n * sizeof(float)), (int)n, c->P.patch_radius, st);
+                launch_cost_export(s.pv.cost[k], (float*)(d + k * n * sizeof(float)), (int)n, c->P.patch_radius,
+                                   s.census_costs ? 1 : 0, st);
             break;
         case GPM_MODELS:
             for (int k = 0; k < 2; ++k)

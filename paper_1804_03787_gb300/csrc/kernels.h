@@ -13,6 +13,7 @@ struct PmLaunch {
     const PairView* pv;
     LevelGeom geom;
     int radius, storage, level, it, phase, nrad, grid_blocks;
+    int census;  // level 0: census data term (codes in pv.code)
     uint32_t k0, k1;
 };
 void launch_pm(const PmLaunch& L, cudaStream_t st);
@@ -21,8 +22,12 @@ void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t strid
                    double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
                    cudaStream_t st);
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
-// dst[i] = src[i] / (3 (2 radius + 1)^2): the NNF cost buffer holds raw tap sums, the export means.
-void launch_cost_export(const float* src, float* dst, int n, int radius, cudaStream_t st);
+// Census codes of both input frames (k1, k2: n int64 of scratch each).
+void launch_census(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1, long long* k2,
+                   uint32_t* c1, uint32_t* c2, cudaStream_t st);
+// dst[i] = src[i] / (3 (2 radius + 1)^2), or / 24 (2 radius + 1)^2 for census costs: the NNF cost buffer holds
+// raw tap sums, the export means.
+void launch_cost_export(const float* src, float* dst, int n, int radius, int census, cudaStream_t st);
 // Writes the level geometries (host array, copied by value into the launch) to dst: no host copy in the
 // stream, so a pipeline that changes frame size can be captured into a CUDA graph.
 void launch_set_geoms(const LevelGeom* host_geoms, LevelGeom* dst, cudaStream_t st);

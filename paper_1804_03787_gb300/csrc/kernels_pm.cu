@@ -86,6 +86,57 @@ __device__ __forceinline__ float3 equalize_px(float r, float g, float b, const f
     return make_float3(l, l, l);
 }
 
+// ---------------------------------------------------------------- census codes (Sec. 6)
+// Grey = R + G + B in FP64 (the same additions as the FP64 oracle, so the
+// same values), stored as an orderable integer key: the bits of a
+// non-negative double increase with it, negative ones are mirrored; + 0.0
+// turns -0 into +0.  The 24 comparisons per pixel then run on the integer
+// pipe with exactly the outcomes of comparing the doubles.
+__global__ void k_grey_keys(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1,
+                            long long* k2) {
+    const int n = W * H;
+    const float* f = blockIdx.y ? f2 : f1;
+    long long* k = blockIdx.y ? k2 : k1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const float* p = f + (int64_t)y * stride + 3 * x;
+        const double g = (((double)p[0] + (double)p[1]) + (double)p[2]) + 0.0;
+        const long long b = __double_as_longlong(g);
+        k[i] = b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b) - 1;
+    }
+}
+
+// 5x5 census code per pixel: bit k (raster order without the centre, neighbours clamped into the frame) set iff
+// the neighbour's grey is below the centre's.
+__global__ void k_census(const long long* k1, const long long* k2, int W, int H, uint32_t* c1, uint32_t* c2) {
+    const int n = W * H;
+    const long long* k = blockIdx.y ? k2 : k1;
+    uint32_t* c = blockIdx.y ? c2 : c1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const long long kc = k[i];
+        uint32_t code = 0;
+        int bit = 0;
+#pragma unroll
+        for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+            for (int dx = -2; dx <= 2; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                const int nx = min(max(x + dx, 0), W - 1), ny = min(max(y + dy, 0), H - 1);
+                code |= (k[ny * W + nx] < kc ? 1u : 0u) << bit;
+                ++bit;
+            }
+        c[i] = code;
+    }
+}
+
+void launch_census(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1, long long* k2,
+                   uint32_t* c1, uint32_t* c2, cudaStream_t st) {
+    const dim3 grid(152 * 4, 2);
+    k_grey_keys<<<grid, 256, 0, st>>>(f1, f2, W, H, stride, k1, k2);
+    k_census<<<grid, 256, 0, st>>>(k1, k2, W, H, c1, c2);
+}
+
 // Deterministic FP64 sums of both frames (after equalisation when lut is set): fixed grid, fixed tree.
 __global__ void k_frame_sums(const float* f1, const float* f2, int W, int H, int64_t stride, const float* lut,
                              double* partial) {
@@ -190,6 +241,7 @@ struct Patch {
 template <int R>
 struct LanePatch {
     float4 a[Patch<R>::NT];   // source texels of the lane's taps
+    uint32_t code[Patch<R>::NT];  // census data term: source codes of the lane's taps
     int tx[Patch<R>::NT], ty[Patch<R>::NT], tidx[Patch<R>::NT];
     float fx[Patch<R>::NT], fy[Patch<R>::NT];
     // offsets c with oxlo <= c.x <= oxlo + oxspan and oylo <= c.y <= oylo + oyspan keep every texel of
@@ -209,7 +261,8 @@ __device__ __forceinline__ void set_interior_box(LanePatch<R>& lp, int xlo, int 
     lp.oyspan = max(sy, 0);
 }
 
-template <int R, int ST>
+// CENSUS: src holds the frame's census codes (uint32 per pixel) instead of texels.
+template <int R, int ST, bool CENSUS = false>
 __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, int W, int H, int px, int py,
                                            int lane) {
 #pragma unroll
@@ -220,7 +273,10 @@ __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, in
         lp.tx[j] = min(max(px + dx, 0), W - 1);
         lp.ty[j] = min(max(py + dy, 0), H - 1);
         lp.tidx[j] = lp.ty[j] * W + lp.tx[j];
-        lp.a[j] = ldpix<ST>(src, lp.tidx[j]);
+        if (CENSUS)
+            lp.code[j] = __ldg(reinterpret_cast<const uint32_t*>(src) + lp.tidx[j]);
+        else
+            lp.a[j] = ldpix<ST>(src, lp.tidx[j]);
         lp.fx[j] = 0.f;
         lp.fy[j] = 0.f;
     }
@@ -331,6 +387,42 @@ __device__ __forceinline__ float patch_sum(const LanePatch<R>& lp, const void* t
                                  : patch_sum_in<R, ST, false>(lp, tgt, W, H, c, lane);
 }
 
+// ---------------------------------------------------------------- census data term (Sec. 6)
+// Square patches only (level 0).  The cost is the sum over taps of the
+// Hamming distance of the source and target census codes: an exact integer,
+// summed across the warp by one redux, so decisions are exact and the
+// abandon test needs no margin (a partial sum at or above the best cannot
+// become strictly lower).  Returns false when abandoned; best < 0 never
+// abandons.
+template <int R, bool IN>
+__device__ __forceinline__ bool census_sum_in(const LanePatch<R>& lp, const uint32_t* tgt, int W, int H, int2 c,
+                                              int best, int& sum, int lane) {
+    const int off = c.y * W + c.x;
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        if (t < Patch<R>::T) {
+            const int idx = IN ? lp.tidx[j] + off
+                               : min(max(lp.ty[j] + c.y, 0), H - 1) * W + min(max(lp.tx[j] + c.x, 0), W - 1);
+            s += __popc(lp.code[j] ^ __ldg(tgt + idx));
+        }
+        const int tot = (int)__reduce_add_sync(FULL, (unsigned)s);
+        if (j + 1 < Patch<R>::NT) {
+            if (best >= 0 && tot >= best) return false;
+        } else {
+            sum = tot;
+        }
+    }
+    return true;
+}
+template <int R>
+__device__ __forceinline__ bool census_sum(const LanePatch<R>& lp, const uint32_t* tgt, int W, int H, int2 c,
+                                           int best, int& sum, int lane) {
+    return interior_of<R>(lp, c) ? census_sum_in<R, true>(lp, tgt, W, H, c, best, sum, lane)
+                                 : census_sum_in<R, false>(lp, tgt, W, H, c, best, sum, lane);
+}
+
 // Integer threshold for the abandon test of tap_sum: with thr the best raw
 // sum so far, returns ceil(thr * 2^19 * (1 + 2^-21)).  The extra 2^-21 covers
 // the five rounded additions of the warp's final float sum (each loses at
@@ -414,21 +506,28 @@ __device__ __forceinline__ const Mef* home_plane(const LevelGeom& g, const Mef* 
 }
 
 // ---------------------------------------------------------------- init
-template <int R, int ST>
+template <int R, int ST, bool CENSUS>
 __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint32_t k1) {
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int W = pv.W, H = pv.H, n = pv.n;
-    const void* src = pv.img[dir];
-    const void* tgt = pv.img[1 - dir];
+    const void* src = CENSUS ? (const void*)pv.code[dir] : pv.img[dir];
+    const void* tgt = CENSUS ? (const void*)pv.code[1 - dir] : pv.img[1 - dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
         const int y = i / W, x = i - y * W;
         const uint4 w = philox((uint32_t)i, 0u, stream_tag(RNG_INIT, dir, 0, 0), pv.pair_id, k0, k1);
         const int vx = (int)(w.x % (uint32_t)W) - x, vy = (int)(w.y % (uint32_t)H) - y;
         LanePatch<R> lp;
-        load_patch<R, ST>(lp, src, W, H, x, y, lane);
-        const float c = patch_sum<R, ST>(lp, tgt, W, H, x, y, vx, vy, lane);
+        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
+        float c;
+        if constexpr (CENSUS) {
+            int sum = 0;
+            census_sum<R>(lp, reinterpret_cast<const uint32_t*>(tgt), W, H, make_int2(vx, vy), -1, sum, lane);
+            c = (float)sum;
+        } else {
+            c = patch_sum<R, ST>(lp, tgt, W, H, x, y, vx, vy, lane);
+        }
         if (lane == 0) {
             pv.nnf[dir][i] = make_int2(vx, vy);
             pv.cost[dir][i] = c;
@@ -480,14 +579,16 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
 // around the best offset after A, radius R0 >> k on lane k.  The warp walks
 // each list in lane order through one evaluation site (a small kernel body
 // keeps the instruction cache warm) and accepts with the strict-less rule.
-template <int R, int ST, bool PLANES>
+// CENSUS (level 0 only): the census data term on the frames' code images.
+template <int R, int ST, bool PLANES, bool CENSUS>
 __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
                                                   uint32_t k0, uint32_t k1) {
+    static_assert(!(PLANES && CENSUS), "the census data term is for square patches");
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int W = pv.W, H = pv.H;
-    const void* src = pv.img[dir];
-    const void* tgt = pv.img[1 - dir];
+    const void* src = CENSUS ? (const void*)pv.code[dir] : pv.img[dir];
+    const void* tgt = CENSUS ? (const void*)pv.code[1 - dir] : pv.img[1 - dir];
     int2* __restrict__ nnf = pv.nnf[dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int hw = (W + 1) >> 1;
@@ -520,14 +621,14 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
             x = i - y * W;
         }
         LanePatch<R> lp;
-        load_patch<R, ST>(lp, src, W, H, x, y, lane);
+        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
         if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
         }
         int2 best = nnf[i];
         float bc = pv.cost[dir][i];  // raw sum of the incumbent
-        int ithr = abandon_threshold(bc);
+        int ithr = CENSUS ? 0 : abandon_threshold(bc);
         int nev = 0;
         // random words for the search radii, two radii per Philox call, one call per lane
         uint4 rw = make_uint4(0, 0, 0, 0);
@@ -589,11 +690,20 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                 const int l = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
-                float sum;
-                if (tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, lane) && sum < bc) {
-                    bc = sum;
-                    best = c;
-                    ithr = abandon_threshold(bc);
+                if constexpr (CENSUS) {
+                    int sum;  // exact integer costs: the incumbent's sum is an integer held in a float
+                    if (census_sum<R>(lp, reinterpret_cast<const uint32_t*>(tgt), W, H, c, (int)bc, sum, lane) &&
+                        sum < (int)bc) {
+                        bc = (float)sum;
+                        best = c;
+                    }
+                } else {
+                    float sum;
+                    if (tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, lane) && sum < bc) {
+                        bc = sum;
+                        best = c;
+                        ithr = abandon_threshold(bc);
+                    }
                 }
                 ++nev;
             }
@@ -637,17 +747,25 @@ template <int R, int ST>
 static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
     const dim3 grid(L.grid_blocks, 2), block(256);
     switch (L.op) {
-        case PmLaunch::INIT:
-            k_pm_init<R, ST><<<grid, block, 0, st>>>(*L.pv, L.k0, L.k1);
+        case PmLaunch::INIT:  // census codes do not depend on the texel storage: one instance serves all
+            if (L.census)
+                k_pm_init<R, 0, true><<<grid, block, 0, st>>>(*L.pv, L.k0, L.k1);
+            else
+                k_pm_init<R, ST, false><<<grid, block, 0, st>>>(*L.pv, L.k0, L.k1);
             break;
         case PmLaunch::RECOST:
             k_pm_recost<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level);
             break;
         case PmLaunch::SWEEP:
-            if (L.level == 0)
-                k_pm_sweep<R, ST, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0, L.k1);
+            if (L.level == 0 && L.census)
+                k_pm_sweep<R, 0, false, true><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0,
+                                                                     L.k1);
+            else if (L.level == 0)
+                k_pm_sweep<R, ST, false, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0,
+                                                                       L.k1);
             else
-                k_pm_sweep<R, ST, true><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad, L.k0, L.k1);
+                k_pm_sweep<R, ST, true, false><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad,
+                                                                      L.k0, L.k1);
             break;
     }
 }
@@ -710,9 +828,9 @@ void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
 __global__ void k_cost_export(const float* src, float* dst, int n, float scale) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] / scale;
 }
-void launch_cost_export(const float* src, float* dst, int n, int radius, cudaStream_t st) {
+void launch_cost_export(const float* src, float* dst, int n, int radius, int census, cudaStream_t st) {
     const int d = 2 * radius + 1;
-    k_cost_export<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n, (float)(3 * d * d));
+    k_cost_export<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n, (float)((census ? 24 : 3) * d * d));
 }
 
 struct GeomPack {

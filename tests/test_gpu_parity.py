@@ -542,3 +542,41 @@ def test_large_windows_end_to_end(torch):
     assert agree > 0.95
     assert abs(epe_g - epe_o) < 0.01
     ctx.close()
+
+
+# ---------------------------------------------------------------- census data term (Sec. 6)
+@pytest.mark.parametrize("W,H,r", [(64, 48, 2), (70, 45, 3)])
+def test_census_level0_equals_oracle_exactly(torch, W, H, r):
+    """Level-0 PatchMatch with the census data term: integer Hamming costs leave no near ties, so the NNF must
+    equal the oracle's exactly (both directions) and the costs agree to the division."""
+    s = _scene(W, H, seed=W + 5)
+    gp = gpm.default_params(patch_radius=r, cells=(16, 8), pm_iters=3, num_hyp=32, census=1)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)], pair_ids=[3])
+    nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
+    R = O.run(oracle_params(gp, W, H, pair_id=3), s.frame1, s.frame2, stop_after=0)
+    for d in range(2):
+        np.testing.assert_array_equal(nnf[d, :, 0], R.vx[d])
+        np.testing.assert_array_equal(nnf[d, :, 1], R.vy[d])
+        np.testing.assert_allclose(cost[d], R.cost[d], rtol=1e-6, atol=0)
+    ctx.close()
+
+
+def test_census_tiny_end_to_end(torch):
+    """Tiny config with the census data term against the oracle with it: the bars of the plain end-to-end test."""
+    s = scene.tiny_scene(0)
+    gp = gpm.default_params(census=1)
+    ctx = _ctx(torch, gp, 128, 96)
+    flows, _ = ctx.run([_dev(torch, s)])
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy()
+    R = O.run(oracle_params(gp, 128, 96), s.frame1, s.frame2)
+    oflow = R.flow[0].reshape(96, 128, 2)
+    vis = s.occ == 0
+    agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-4)
+    epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    epe_o = np.hypot(*(oflow - s.flow).transpose(2, 0, 1))[vis].mean()
+    print(f"census tiny: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
+    assert agree > 0.95
+    assert abs(epe_g - epe_o) < 0.01
+    ctx.close()
