@@ -28,7 +28,7 @@ class _Params(C.Structure):
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("r", C.c_int32), ("num_scales", C.c_int32),
                 ("cell", C.c_int32 * MAX_SCALES), ("pm_iters", C.c_int32), ("num_hyp", C.c_int32),
                 ("min_inliers", C.c_int32), ("fill_iters", C.c_int32), ("gain_normalize", C.c_int32),
-                ("pm_init", C.c_int32), ("equalize", C.c_int32), ("census", C.c_int32),
+                ("pm_init", C.c_int32), ("equalize", C.c_int32), ("census", C.c_int32), ("interp", C.c_int32), ("pad1", C.c_int32),
                 ("eps", C.c_double), ("ransac_px", C.c_double),
                 ("fb_px", C.c_double), ("eta", C.c_double), ("kappa", C.c_double), ("beta", C.c_double),
                 ("occ_thresh", C.c_double), ("scale_min", C.c_double), ("scale_max", C.c_double),
@@ -59,6 +59,7 @@ class Params:
     pm_init: int = 1
     equalize: int = 0                # HSV V-channel histogram equalisation of both frames (Sec. 4.2)
     census: int = 0                  # census data term for the level-0 NNF (Sec. 6)
+    interp: int = 0                  # edge-aware fill of the pixels left without a plane
     seed: int = 0
     pair_id: int = 0
 
@@ -70,7 +71,7 @@ class Params:
             p.cell[i] = s
         p.pm_iters, p.num_hyp, p.min_inliers, p.fill_iters = self.pm_iters, self.num_hyp, self.min_inliers, self.fill_iters
         p.gain_normalize, p.pm_init, p.equalize = self.gain_normalize, self.pm_init, self.equalize
-        p.census = self.census
+        p.census, p.interp = self.census, self.interp
         p.eps, p.ransac_px, p.fb_px, p.eta, p.kappa = self.eps, self.ransac_px, self.fb_px, self.eta, self.kappa
         p.beta, p.occ_thresh, p.scale_min, p.scale_max = self.beta, self.occ_thresh, self.scale_min, self.scale_max
         p.seed, p.pair_id = self.seed & 0xFFFFFFFFFFFFFFFF, self.pair_id & 0xFFFFFFFF
@@ -113,6 +114,8 @@ def lib() -> C.CDLL:
             "orc_v_lut": (C.c_int, [pp, d, d]),
             "orc_hsv_equalize": (None, [pp, d, d]),
             "orc_census": (None, [pp, d, d]),
+            "orc_grey_q": (None, [pp, d, i32]),
+            "orc_interp_seeds": (None, [pp, i32, i32, i32]),
             "orc_run": (None, [pp, d, d, C.c_void_p, C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -217,6 +220,17 @@ def census(P: Params, rgb):
     out = np.zeros_like(a)
     lib().orc_census(C.byref(P.c()), _p(a, C.c_double), _p(out, C.c_double))
     return out
+
+
+def interp_seeds(P: Params, rgb, am):
+    """Seed (nearest assigned pixel in geodesic distance, -1 if none) of every pixel, for the edge-aware fill."""
+    n = P.width * P.height
+    q = np.zeros(n, np.int32)
+    lib().orc_grey_q(C.byref(P.c()), _p(_f64(rgb), C.c_double), _p(q, C.c_int32))
+    seed = np.zeros(n, np.int32)
+    lib().orc_interp_seeds(C.byref(P.c()), _p(q, C.c_int32), _p(np.ascontiguousarray(am, np.int32), C.c_int32),
+                           _p(seed, C.c_int32))
+    return seed
 
 
 def gain(P: Params, f1, f2) -> float:

@@ -33,6 +33,7 @@ typedef struct {
     int32_t equalize;                /* HSV V-channel histogram equalisation of both frames (Sec. 4.2) */
     int32_t census;                  /* census data term for the level-0 NNF (Sec. 6); inside the PatchMatch
                                         routines: the frames given are census code frames */
+    int32_t interp, pad1;            /* interp: edge-aware fill of the pixels left without a plane */
     double eps, ransac_px, fb_px, eta, kappa, beta, occ_thresh, scale_min, scale_max;
     uint64_t seed;
     uint32_t pair_id, pad;
@@ -149,6 +150,11 @@ void orc_hsv_equalize(const orc_params* P, const double* in, double* out);
 /* ---- census data term (Sec. 6), oracle_color.c ---- */
 void orc_census(const orc_params* P, const double* rgb, double* codes);   /* code frame: (code, 0, 0) per pixel */
 int orc_popcount32(uint32_t v);
+/* ---- edge-aware fill of unassigned pixels, oracle_color.c ---- */
+void orc_grey_q(const orc_params* P, const double* rgb, int32_t* q);              /* floor(1024 (R+G+B)) */
+void orc_interp_seeds(const orc_params* P, const int32_t* q, const int32_t* am, int32_t* seed);
+void orc_interp_flow(const orc_params* P, const double* mh, const int32_t* am, const double* afx, const double* afy,
+                     const int32_t* seed, float* flow);
 
 /* ---- whole method (Algorithm 1 for every level, then Sec. 3.4) ---- */
 typedef struct {

@@ -158,3 +158,50 @@ int orc_popcount32(uint32_t v) {
     }
     return n;
 }
+
+/*
+ * Edge-aware fill of the pixels left without a plane (stands in for the
+ * EpicFlow interpolation the paper applies after MSGPM, Sec. 3.4.1 / 4).
+ * Reading: each such pixel takes the plane of the assigned pixel nearest to
+ * it in geodesic distance, where a step between 4-neighbours costs
+ * 256 + |q_i - q_j| with q = floor(1024 (R + G + B)) of the frame as given
+ * (FP64).  Distances are integers, computed by fast sweeping: ORC_INTERP_ROUNDS
+ * rounds of four in-place scans (rows left to right, rows right to left,
+ * columns top to bottom, columns bottom to top); a neighbour's offer replaces
+ * the current one if its distance is lower, or equal with a lower seed index.
+ */
+#define ORC_INTERP_ROUNDS 4
+
+void orc_grey_q(const orc_params* P, const double* rgb, int32_t* q) {
+    const int n = P->W * P->H;
+    for (int i = 0; i < n; ++i) q[i] = (int32_t)floor(1024.0 * ((rgb[3 * i] + rgb[3 * i + 1]) + rgb[3 * i + 2]));
+}
+
+static void relax(const int32_t* q, long long* dist, int32_t* seed, int j, int i) {
+    if (seed[j] < 0) return;
+    const long long c = dist[j] + 256 + llabs((long long)q[i] - q[j]);
+    if (c < dist[i] || (c == dist[i] && seed[j] < seed[i])) {
+        dist[i] = c;
+        seed[i] = seed[j];
+    }
+}
+
+void orc_interp_seeds(const orc_params* P, const int32_t* q, const int32_t* am, int32_t* seed) {
+    const int W = P->W, H = P->H, n = W * H;
+    long long* dist = (long long*)malloc(sizeof(long long) * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        dist[i] = am[i] >= 0 ? 0 : (long long)1 << 62;
+        seed[i] = am[i] >= 0 ? i : -1;
+    }
+    for (int r = 0; r < ORC_INTERP_ROUNDS; ++r) {
+        for (int y = 0; y < H; ++y)
+            for (int x = 1; x < W; ++x) relax(q, dist, seed, y * W + x - 1, y * W + x);
+        for (int y = 0; y < H; ++y)
+            for (int x = W - 2; x >= 0; --x) relax(q, dist, seed, y * W + x + 1, y * W + x);
+        for (int x = 0; x < W; ++x)
+            for (int y = 1; y < H; ++y) relax(q, dist, seed, (y - 1) * W + x, y * W + x);
+        for (int x = 0; x < W; ++x)
+            for (int y = H - 2; y >= 0; --y) relax(q, dist, seed, (y + 1) * W + x, y * W + x);
+    }
+    free(dist);
+}

@@ -52,6 +52,7 @@ void orc_run(const orc_params* Pin, const double* f1in, const double* f2in, orc_
     const int W = Pin->W, H = Pin->H, n = W * H;
     const size_t nf = (size_t)n * 3;
     /* census data term (Sec. 6): code frames of the frames as given, read by the level-0 PatchMatch only */
+    const double* raw[2] = {f1in, f2in};  /* the frames as given (census codes, fill greys) */
     const orc_params P0 = *Pin;
     orc_params Pc = *Pin;
     Pc.census = 0;
@@ -165,6 +166,15 @@ void orc_run(const orc_params* Pin, const double* f1in, const double* f2in, orc_
     for (int d = 0; d < 2; ++d) {
         orc_fill(P, src[d], tgt[d], S->mh[d], S->mi[d], S->cue[d], S->am[d], S->aL[d], S->afx[d], S->afy[d]);
         orc_final(P, src[d], tgt[d], S->am[d], S->afx[d], S->afy[d], S->vx[d], S->vy[d], S->cue[d], S->flow[d], S->occ[d]);
+        if (P->interp) { /* edge-aware fill of the pixels left without a plane */
+            int32_t* q = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+            int32_t* seed = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+            orc_grey_q(P, raw[d], q);
+            orc_interp_seeds(P, q, S->am[d], seed);
+            orc_interp_flow(P, S->mh[d], S->am[d], S->afx[d], S->afy[d], seed, S->flow[d]);
+            free(q);
+            free(seed);
+        }
     }
 out:
     for (int d = 0; d < 2; ++d) free(frozen[d]);

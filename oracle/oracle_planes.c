@@ -809,3 +809,25 @@ double orc_gain(const orc_params* P, const double* f1, const double* f2) {
     }
     return s2 > 0 ? s1 / s2 : 1.0;
 }
+
+/* Edge-aware fill (reading in oracle_color.c): a pixel without a plane and
+   with a seed takes the seed's plane at its own position (H p - p), or the
+   seed's flow where that plane's denominator is not positive there. */
+void orc_interp_flow(const orc_params* P, const double* mh, const int32_t* am, const double* afx, const double* afy,
+                     const int32_t* seed, float* flow) {
+    const int W = P->W, H = P->H;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int i = y * W + x;
+            if (am[i] >= 0 || seed[i] < 0) continue;
+            const int s = seed[i];
+            double X, Y;
+            if (map_h(mh + (size_t)am[s] * 9, x, y, &X, &Y)) {
+                flow[2 * i] = (float)(X - x);
+                flow[2 * i + 1] = (float)(Y - y);
+            } else {
+                flow[2 * i] = (float)afx[s];
+                flow[2 * i + 1] = (float)afy[s];
+            }
+        }
+}

@@ -392,3 +392,77 @@ def test_pipeline_census_level0_uses_code_frames():
         np.testing.assert_array_equal(R.vx[d], vx)
         np.testing.assert_array_equal(R.vy[d], vy)
         np.testing.assert_array_equal(R.cost[d], cost)
+
+
+# ---------------------------------------------------------------- edge-aware fill of unassigned pixels
+def _nearest_seeds_dijkstra(q, seeds, W, H):
+    """Reference seeds: exact geodesic distance (step 256 + |q_i - q_j| between 4-neighbours) from each seed by
+    Dijkstra, the lowest distance winning, then the lowest seed index."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import dijkstra
+    n = W * H
+    rows, cols, wts = [], [], []
+    for y in range(H):
+        for x in range(W):
+            i = y * W + x
+            for (nx, ny) in ((x + 1, y), (x, y + 1)):
+                if nx < W and ny < H:
+                    j = ny * W + nx
+                    w = 256 + abs(int(q[i]) - int(q[j]))
+                    rows += [i, j]
+                    cols += [j, i]
+                    wts += [w, w]
+    G = coo_matrix((wts, (rows, cols)), shape=(n, n)).tocsr()
+    D = dijkstra(G, indices=sorted(seeds))
+    best = np.full(n, -1)
+    bd = np.full(n, np.inf)
+    for k, s in enumerate(sorted(seeds)):  # ascending index: a tie keeps the earlier (lower) seed
+        better = D[k] < bd
+        best[better] = s
+        bd[better] = D[k][better]
+    return best
+
+
+def test_fill_seeds_flat_frame_are_manhattan_nearest():
+    rng = np.random.default_rng(2)
+    W, H = 17, 11
+    P = O.Params(W, H)
+    am = np.full(W * H, -1, np.int32)
+    seeds = rng.choice(W * H, 6, replace=False)
+    am[seeds] = 0
+    got = O.interp_seeds(P, np.full((H, W, 3), 0.3), am)
+    ys, xs = np.divmod(np.arange(W * H), W)
+    for i in range(W * H):
+        d = [(abs(xs[i] - xs[s]) + abs(ys[i] - ys[s]), s) for s in seeds]
+        assert got[i] == min(d)[1], (i, got[i], min(d))
+
+
+def test_fill_seeds_respect_an_edge():
+    """Two regions split by a vertical edge (grey steps of 2000 across it): pixels take the seed on their own
+    side even when the other one is closer, exactly as the geodesic reference says."""
+    W, H = 20, 9
+    P = O.Params(W, H)
+    img = np.zeros((H, W, 3))
+    img[:, 10:] = 0.7  # q jumps by floor(1024 * 2.1) = 2150
+    q = np.floor(1024.0 * img.sum(-1)).astype(np.int64).reshape(-1)
+    am = np.full(W * H, -1, np.int32)
+    left, right = 4 * W + 0, 4 * W + 11
+    am[[left, right]] = 0
+    got = O.interp_seeds(P, img, am)
+    want = _nearest_seeds_dijkstra(q, [left, right], W, H)
+    np.testing.assert_array_equal(got, want)
+    assert got[4 * W + 9] == left  # 2 px from the right seed across the edge, 9 px from the left one
+
+
+def test_pipeline_fill_changes_only_unassigned_flows():
+    s = scene.make_scene(48, 36, seed=12, n_layers=2, max_disp=4.0, affine=True)
+    kw = dict(patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=32)
+    R0 = O.run(O.Params(48, 36, **kw), s.frame1, s.frame2)
+    R1 = O.run(O.Params(48, 36, interp=1, **kw), s.frame1, s.frame2)
+    for d in range(2):
+        assigned = R0.acc[d].m >= 0
+        f0, f1 = R0.flow[d].reshape(-1, 2), R1.flow[d].reshape(-1, 2)
+        np.testing.assert_array_equal(R0.occ[d], R1.occ[d])
+        same = np.all(f0 == f1, axis=1)
+        assert same.mean() > 0.5 and not same.all()
+        assert same[assigned].all()
