@@ -84,6 +84,8 @@ typedef struct {
     float scale_min, scale_max;           /* plane validity: local area scale range */
     int32_t census;                       /* 1: level-0 PatchMatch on 5x5 census codes, Hamming cost (Sec. 6) */
     uint64_t seed;                        /* Philox4x32-10 key */
+    int32_t interp;                       /* 1: pixels left without a plane take the geodesically nearest
+                                             assigned pixel's plane (edge-aware fill; EpicFlow stand-in) */
 } gpm_params;
 
 /* Capacity of a context, fixed at creation. */

@@ -116,6 +116,7 @@ def lib() -> C.CDLL:
             "orc_census": (None, [pp, d, d]),
             "orc_grey_q": (None, [pp, d, i32]),
             "orc_interp_seeds": (None, [pp, i32, i32, i32]),
+            "orc_interp_flow": (None, [pp, d, i32, d, d, i32, P(C.c_float)]),
             "orc_run": (None, [pp, d, d, C.c_void_p, C.c_int]),
         }
         for name, (res, args) in sig.items():
@@ -231,6 +232,14 @@ def interp_seeds(P: Params, rgb, am):
     lib().orc_interp_seeds(C.byref(P.c()), _p(q, C.c_int32), _p(np.ascontiguousarray(am, np.int32), C.c_int32),
                            _p(seed, C.c_int32))
     return seed
+
+
+def interp_flow(P: Params, mh, acc: "Labels", seed, flow):
+    """Edge-aware fill: flows (n x 2 float32, updated in place) of the pixels without a plane from their seeds."""
+    lib().orc_interp_flow(C.byref(P.c()), _p(_f64(mh), C.c_double), _p(acc.m, C.c_int32), _p(acc.fx, C.c_double),
+                          _p(acc.fy, C.c_double), _p(np.ascontiguousarray(seed, np.int32), C.c_int32),
+                          _p(flow, C.c_float))
+    return flow
 
 
 def gain(P: Params, f1, f2) -> float:

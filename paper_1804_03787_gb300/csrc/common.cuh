@@ -354,6 +354,7 @@ struct PairView {
     unsigned long long* m2o_key[2];
     RefitWork* rw[2];     // [cells of the largest level]
     uint32_t* code[2];    // census codes of each frame (census data term)
+    int* gq;              // floor(1024 (R + G + B)) of frame 1 as given (edge-aware fill)
     unsigned long long* evals;  // [PM evaluations level 0, levels >= 1, RANSAC residual tests], or nullptr
 };
 

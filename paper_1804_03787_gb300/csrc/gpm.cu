@@ -109,6 +109,8 @@ gpm_status cuda_check(gpm_ctx* c, const char* where) {
     return GPM_OK;
 }
 
+constexpr int kFillRounds = 4;  // fast-sweeping rounds of the edge-aware fill
+
 // Windows of the level with the most (refit records are per window of one level).
 int max_level_cells_for(const gpm_params& P, int W, int H) {
     int mx = 1;
@@ -153,6 +155,7 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
     if (P.equalize != 0 && P.equalize != 1) return why = "equalize must be 0 or 1", GPM_EINVAL;
     if (P.census != 0 && P.census != 1) return why = "census must be 0 or 1", GPM_EINVAL;
     if (P.census && !P.pm_init) return why = "census needs pm_init = 1 (a random initial NNF)", GPM_EINVAL;
+    if (P.interp != 0 && P.interp != 1) return why = "interp must be 0 or 1", GPM_EINVAL;
     if (!(P.eps > 0) || !(P.ransac_px > 0) || !(P.fb_px > 0)) return why = "eps, ransac_px, fb_px must be > 0", GPM_EINVAL;
     if (!(P.scale_min > 0) || !(P.scale_max >= P.scale_min)) return why = "bad scale range", GPM_EINVAL;
     return GPM_OK;
@@ -193,6 +196,7 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells
         pv.code[d] = (uint32_t*)take(n * sizeof(uint32_t));
     }
     pv.list_count = (int*)take(4 * sizeof(int));
+    pv.gq = (int*)take(n * sizeof(int));
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
     double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
     double* gain = (double*)take(sizeof(double));
@@ -488,6 +492,11 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
                               s.pv.code[0], s.pv.code[1], c->stream);
                 pend(c);
             }
+            if (c->P.interp) {  // greys of frame 1 as given, for the edge-aware fill at the end
+                pbeg(c, GPM_PROF_INGEST, 1);
+                launch_grey_q(p.frame1, p.width, p.height, p.row_stride, s.pv.gq, c->stream);
+                pend(c);
+            }
             pbeg(c, GPM_PROF_INGEST, c->P.equalize ? 6 : 4);
             launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
                           s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
@@ -558,8 +567,16 @@ gpm_status gpm_flow_and_occlusion(gpm_ctx* c, int32_t n_pairs, float* const* flo
         pbeg(c, GPM_PROF_FILL, c->P.fill_iters);
         launch_fill(s.pv, pp, c->P.fill_iters, gb, Labels{}, c->stream);
         pend(c);
+        const int* seed = nullptr;
+        if (c->P.interp) {  // scratch: the many-to-one keys and the pixel lists are idle by now
+            pbeg(c, GPM_PROF_FILL, 1 + 2 * kFillRounds);
+            launch_fill_seeds(s.pv, s.pv.gq, reinterpret_cast<long long*>(s.pv.m2o_key[0]), s.pv.list[0], kFillRounds,
+                              gb, c->stream);
+            pend(c);
+            seed = s.pv.list[0];
+        }
         pbeg(c, GPM_PROF_FINAL, 1);
-        launch_final(s.pv, pp, flow_out[i], occ_out[i], gb, c->stream);
+        launch_final(s.pv, pp, seed, flow_out[i], occ_out[i], gb, c->stream);
         pend(c);
     }
     return cuda_check(c, "gpm_flow_and_occlusion");

@@ -55,8 +55,14 @@ void launch_fill(const PairView& pv, const PlaneParams& pp, int iters, int grid_
 void launch_reset_labels(const PairView& pv, float eps, int grid_blocks, cudaStream_t st);
 void launch_frozen_from_labels(const PairView& pv, int grid_blocks, cudaStream_t st);
 void launch_frames_export(const PairView& pv, int storage, float* dst, cudaStream_t st);
-void launch_final(const PairView& pv, const PlaneParams& pp, float* flow, uint8_t* occ, int grid_blocks,
-                  cudaStream_t st);
+// seed: nearest assigned pixel of each pixel (edge-aware fill), or nullptr for the plain rule (NNF offset)
+void launch_final(const PairView& pv, const PlaneParams& pp, const int* seed, float* flow, uint8_t* occ,
+                  int grid_blocks, cudaStream_t st);
+// q = floor(1024 (R + G + B)) of a frame as given, for the geodesic steps of the fill
+void launch_grey_q(const float* f, int W, int H, int64_t stride, int* q, cudaStream_t st);
+// Seeds of the edge-aware fill (direction 0): dist (n int64) and seed (n int) are scratch / output
+void launch_fill_seeds(const PairView& pv, const int* q, long long* dist, int* seed, int rounds, int grid_blocks,
+                       cudaStream_t st);
 // geoms: DEVICE array of nlev level geometries
 void launch_import_models(const PairView& pv, const LevelGeom* geoms, int nlev, int m, cudaStream_t st);
 void launch_labels_export(const Labels& l, int n, int* om, float* oL, double* of, cudaStream_t st);

@@ -1159,10 +1159,100 @@ __global__ void k_fill(PairView pv, Labels cur0, Labels cur1, Labels nxt0, Label
     }
 }
 
-// Final flow (plane flow, else the NNF offset) and occlusion: no plane, a
-// cue flag, or colour error after warping by the final flow >= occ_thresh.
+// ---------------------------------------------------------------- edge-aware fill of unassigned pixels
+// Each pixel left without a plane takes the plane of the assigned pixel
+// nearest in geodesic distance (steps 256 + |q_i - q_j| between
+// 4-neighbours, q = floor(1024 (R + G + B)) of frame 1 as given).  Integer
+// distances by fast sweeping: rounds of four in-place scans in the order rows
+// left to right, rows right to left, columns top to bottom, columns bottom to
+// top; an offer wins with a lower distance, or an equal one from a lower seed
+// index.
+__global__ void k_grey_q(const float* f, int W, int H, int64_t stride, int* q) {
+    const int n = W * H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const float* p = f + (int64_t)y * stride + 3 * x;
+        q[i] = (int)floor(1024.0 * (((double)p[0] + (double)p[1]) + (double)p[2]));
+    }
+}
+__global__ void k_seed_init(const int* am, int n, long long* dist, int* seed) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        dist[i] = am[i] >= 0 ? 0 : (1ll << 62);
+        seed[i] = am[i] >= 0 ? i : -1;
+    }
+}
+// One walk along a line (a row or a column): relax each pixel from the one
+// before it.  The previous pixel's (distance, seed, grey) stays in registers,
+// so the loop-carried chain is integer arithmetic only; the next chunk of U
+// pixels is loaded before the current chunk is stored (disjoint pixels), so
+// the loads run ahead of the chain.  Every register of a chunk is defined,
+// also past the end of the line (those slots are never used).
+template <int U>
+__device__ __forceinline__ void seed_walk(const int* q, long long* dist, int* seed, int64_t i0, int64_t step, int len) {
+    long long dp = dist[i0];
+    int sp = seed[i0], qp = q[i0];
+    long long dn[U];
+    int sn[U], qn[U];
+    int cnt = min(U, len - 1);
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        dn[j] = 0, sn[j] = -1, qn[j] = 0;
+        if (j < cnt) {
+            const int64_t i = i0 + (int64_t)(1 + j) * step;
+            dn[j] = dist[i], sn[j] = seed[i], qn[j] = q[i];
+        }
+    }
+    for (int m = 1; m < len; m += U) {
+        long long dc[U];
+        int sc[U], qc[U];
+        const int cur = cnt;
+        cnt = min(U, len - (m + U));  // pixels in the next chunk (<= 0 past the end)
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            dc[j] = dn[j], sc[j] = sn[j], qc[j] = qn[j];
+            if (j < cnt) {
+                const int64_t i = i0 + (int64_t)(m + U + j) * step;
+                dn[j] = dist[i], sn[j] = seed[i], qn[j] = q[i];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (j < cur) {
+                if (sp >= 0) {
+                    const long long c = dp + 256 + (long long)abs(qc[j] - qp);
+                    if (c < dc[j] || (c == dc[j] && sp < sc[j])) {
+                        const int64_t i = i0 + (int64_t)(m + j) * step;
+                        dc[j] = c, sc[j] = sp;
+                        dist[i] = c, seed[i] = sp;
+                    }
+                }
+                dp = dc[j], sp = sc[j], qp = qc[j];
+            }
+        }
+    }
+}
+// cols = 0: one thread per row, left to right then right to left; cols = 1:
+// one thread per column, top to bottom then bottom to top (a warp's loads of
+// one step are then coalesced).  Lines are disjoint, so fusing a line's two
+// scans keeps the order of four whole-frame scans.
+__global__ void k_seed_lines(const int* q, long long* dist, int* seed, int W, int H, int cols) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!cols) {
+        if (t >= H) return;
+        seed_walk<8>(q, dist, seed, (int64_t)t * W, 1, W);
+        seed_walk<8>(q, dist, seed, (int64_t)t * W + W - 1, -1, W);
+    } else {
+        if (t >= W) return;
+        seed_walk<8>(q, dist, seed, t, W, H);
+        seed_walk<8>(q, dist, seed, (int64_t)(H - 1) * W + t, -(int64_t)W, H);
+    }
+}
+
+// Final flow (plane flow, else the NNF offset, else with a seed the seed's
+// plane at this pixel) and occlusion: no plane, a cue flag, or colour error
+// after warping by the final flow >= occ_thresh.
 template <int ST>
-__global__ void k_final(PairView pv, int dir, PlaneParams pp, float* flow, uint8_t* occ) {
+__global__ void k_final(PairView pv, int dir, PlaneParams pp, const int* seed, float* flow, uint8_t* occ) {
     const int W = pv.W, H = pv.H, n = pv.n;
     const Labels acc = pv.acc[dir];
     const void* src = pv.img[dir];
@@ -1188,6 +1278,21 @@ __global__ void k_final(PairView pv, int dir, PlaneParams pp, float* flow, uint8
             bx = x + v.x;
             by = y + v.y;
             fx = fy = 0.f;
+            const int sd = seed ? seed[i] : -1;
+            if (sd >= 0) {  // edge-aware fill: the seed's plane here, or the seed's flow
+                const Mef m = pv.mef[dir][acc.m[sd]];
+                int kx, ky;
+                float gx, gy;
+                if (mef_flow(m, (float)(x - m.ox), (float)(y - m.oy), kx, gx, ky, gy)) {
+                    flow[2 * i] = (float)kx + gx;
+                    flow[2 * i + 1] = (float)ky + gy;
+                } else {
+                    const int2 vs = acc.v[sd];
+                    const float2 rs = acc.r[sd];
+                    flow[2 * i] = (float)vs.x + rs.x;
+                    flow[2 * i + 1] = (float)vs.y + rs.y;
+                }
+            }
         }
         bool o = !as || (pv.cue[dir][i] & CUE_M2O);
         if (!in_frame_tol(bx, fx, W) || !in_frame_tol(by, fy, H))
@@ -1334,12 +1439,25 @@ void launch_fill(const PairView& pv, const PlaneParams& pp, int iters, int grid_
     }
 }
 
-void launch_final(const PairView& pv, const PlaneParams& pp, float* flow, uint8_t* occ, int grid_blocks,
-                  cudaStream_t st) {
+void launch_grey_q(const float* f, int W, int H, int64_t stride, int* q, cudaStream_t st) {
+    k_grey_q<<<152 * 4, 256, 0, st>>>(f, W, H, stride, q);
+}
+
+void launch_fill_seeds(const PairView& pv, const int* q, long long* dist, int* seed, int rounds, int grid_blocks,
+                       cudaStream_t st) {
+    k_seed_init<<<grid_blocks, 256, 0, st>>>(pv.acc[0].m, pv.n, dist, seed);
+    for (int r = 0; r < rounds; ++r) {
+        k_seed_lines<<<(pv.H + 31) / 32, 32, 0, st>>>(q, dist, seed, pv.W, pv.H, 0);
+        k_seed_lines<<<(pv.W + 31) / 32, 32, 0, st>>>(q, dist, seed, pv.W, pv.H, 1);
+    }
+}
+
+void launch_final(const PairView& pv, const PlaneParams& pp, const int* seed, float* flow, uint8_t* occ,
+                  int grid_blocks, cudaStream_t st) {
     switch (pp.storage) {
-        case 0: k_final<0><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, flow, occ); break;
-        case 1: k_final<1><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, flow, occ); break;
-        case 2: k_final<2><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, flow, occ); break;
+        case 0: k_final<0><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, seed, flow, occ); break;
+        case 1: k_final<1><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, seed, flow, occ); break;
+        case 2: k_final<2><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, seed, flow, occ); break;
     }
 }
 

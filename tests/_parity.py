@@ -25,7 +25,7 @@ def oracle_params(gp, W, H, pair_id=0) -> O.Params:
                     kappa=f32(gp.kappa), beta=f32(gp.beta), occ_thresh=f32(gp.occ_thresh),
                     scale_min=f32(gp.scale_min), scale_max=f32(gp.scale_max), min_inliers=gp.min_inliers,
                     fill_iters=gp.fill_iters, gain_normalize=gp.gain_normalize, pm_init=gp.pm_init, seed=gp.seed,
-                    pair_id=pair_id, equalize=gp.equalize, census=gp.census)
+                    pair_id=pair_id, equalize=gp.equalize, census=gp.census, interp=gp.interp)
 
 
 def oracle_frames(P: O.Params, f1, f2):

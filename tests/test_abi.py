@@ -37,7 +37,9 @@ def test_binding_lists_the_same_symbols():
 def test_struct_layouts_match_header(lib):
     """Sizes of the ctypes mirrors agree with the C structs (x86-64 and aarch64 LP64)."""
     from paper_1804_03787_gb300 import gpm
-    assert ctypes.sizeof(gpm.Params) == 4 * (2 + 8 + 8) + 4 * 9 + 4 + 8  # padded to 8-byte seed
+    # 18 ints, 9 floats, census, the 8-byte seed, interp and tail padding to the seed's alignment
+    assert ctypes.sizeof(gpm.Params) == 4 * (2 + 8 + 8) + 4 * 9 + 4 + 8 + 4 + 4
+    assert gpm.Params.seed.offset == 112 and gpm.Params.interp.offset == 120
     assert ctypes.sizeof(gpm.Limits) == 24
     assert ctypes.sizeof(gpm.Pair) == 40
 

@@ -580,3 +580,64 @@ def test_census_tiny_end_to_end(torch):
     assert agree > 0.95
     assert abs(epe_g - epe_o) < 0.01
     ctx.close()
+
+
+# ---------------------------------------------------------------- edge-aware fill of unassigned pixels
+@pytest.mark.parametrize("W,H,r,cells", CASES)
+def test_interp_fill_lockstep(torch, W, H, r, cells):
+    """The oracle's state before the final stage imported, interp=1: pixels without a plane take the geodesically
+    nearest assigned pixel's plane.  Seeds are integer geodesics (the same on both sides for the same labels), so
+    the filled flows agree up to the FP32 evaluation of the seed plane."""
+    s = _scene(W, H, seed=W + 3)
+    gp = gpm.default_params(patch_radius=r, cells=cells, pm_iters=2, num_hyp=64, fill_iters=5, interp=1)
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    L = len(cells)
+    R = O.run(P, s.frame1, s.frame2, stop_after=L)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    n = W * H
+    ctx.import_state(gpm.NNF, np.stack([np.stack([R.vx[d], R.vy[d]], 1) for d in range(2)]).astype(np.int32), L)
+    ctx.import_state(gpm.MODELS, np.stack(R.mh), L)
+    ctx.import_state(gpm.MODEL_INFO, np.stack(R.mi), L)
+    ctx.import_state(gpm.LABELS, (np.stack([R.acc[d].m for d in range(2)]),
+                                  np.stack([R.acc[d].L for d in range(2)]).astype(np.float32),
+                                  np.stack([np.stack([R.acc[d].fx, R.acc[d].fy], 1) for d in range(2)])), L)
+    ctx.import_state(gpm.CUES, np.stack(R.cue), L)
+    flows, occs = ctx.flow_and_occlusion()
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy().reshape(n, 2)
+    acc = R.acc[0].copy()
+    O.fill(P, frames[0][0], frames[0][1], R.mh[0], R.mi[0], R.cue[0], acc)
+    oflow, _ = O.final(P, frames[0][0], frames[0][1], acc, R.vx[0], R.vy[0], R.cue[0])
+    seed = O.interp_seeds(P, s.frame1, acc.m)
+    O.interp_flow(P, R.mh[0], acc, seed, oflow)
+    filled = (acc.m < 0) & (seed >= 0)
+    assert filled.any()
+    fd = np.hypot(*(gflow - oflow).T)
+    assert np.mean(fd > 1e-5) < 0.005, np.mean(fd > 1e-5)
+    assert np.mean(fd[filled] > 1e-3) < 0.02, np.mean(fd[filled] > 1e-3)
+    ctx.close()
+
+
+def test_interp_tiny_end_to_end(torch):
+    """Tiny config with interp=1 against the oracle with it: the plain end-to-end bars, and the EPE over all
+    pixels (occluded ones included) much lower than without the fill."""
+    s = scene.tiny_scene(0)
+    gp = gpm.default_params(interp=1)
+    ctx = _ctx(torch, gp, 128, 96)
+    flows, _ = ctx.run([_dev(torch, s)])
+    torch.cuda.synchronize()
+    gflow = flows[0].cpu().numpy()
+    R = O.run(oracle_params(gp, 128, 96), s.frame1, s.frame2)
+    oflow = R.flow[0].reshape(96, 128, 2)
+    agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-3)
+    epe_all = np.hypot(*(gflow - s.flow).transpose(2, 0, 1)).mean()
+    ctx0 = _ctx(torch, gpm.default_params(), 128, 96)
+    f0, _ = ctx0.run([_dev(torch, s)])
+    epe0 = np.hypot(*(f0[0].cpu().numpy() - s.flow).transpose(2, 0, 1)).mean()
+    print(f"fill tiny: flow agreement {agree:.4f}, EPE all with fill {epe_all:.3f}, without {epe0:.3f}")
+    assert agree > 0.95
+    assert epe_all < epe0
+    ctx.close()
+    ctx0.close()
