@@ -476,6 +476,61 @@ __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt,
                                  : tap_sum_in<R, ST, false, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, lane);
 }
 
+// Two candidates at once: each one's taps are accumulated per lane in the
+// same order as tap_sum_in, so a full sum is bitwise the same, but the two
+// candidates' gathers are issued together and share the latency of each
+// chunk.  Both are tested against the same threshold, the best before the
+// pair: a bound at or above it means that candidate cannot win against that
+// best nor against a lower one, so the caller's in-order strict-less updates
+// give the result of evaluating the two one after the other.
+template <int R, int ST, bool IN, bool EVERY_CHUNK>
+__device__ __forceinline__ void tap_sum2_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c1, int2 c2,
+                                            int ithr, float& sum1, float& sum2, bool& ok1, bool& ok2, int lane) {
+    const int off1 = c1.y * W + c1.x, off2 = c2.y * W + c2.x;
+    float s1 = 0.f, s2 = 0.f;
+    ok1 = ok2 = true;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        if (t < Patch<R>::T) {
+            float3 v1 = make_float3(0.f, 0.f, 0.f), v2 = v1;
+            if (ok1) v1 = tap_sample<R, ST, IN>(lp, tgt, W, H, j, c1, off1);
+            if (ok2) v2 = tap_sample<R, ST, IN>(lp, tgt, W, H, j, c2, off2);
+            if (ok1) s1 += absdiff3(lp.a[j], v1);
+            if (ok2) s2 += absdiff3(lp.a[j], v2);
+        }
+        if (j + 1 < Patch<R>::NT && (EVERY_CHUNK || j == 0)) {
+            const unsigned q1 =
+                (unsigned)(__float_as_int(__fadd_rz(fminf(s1 * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
+            const unsigned q2 =
+                (unsigned)(__float_as_int(__fadd_rz(fminf(s2 * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
+            if (ok1) ok1 = (int)__reduce_add_sync(FULL, q1) < ithr;
+            if (ok2) ok2 = (int)__reduce_add_sync(FULL, q2) < ithr;
+            if (!ok1 && !ok2) return;
+        }
+    }
+    if (ok1) {
+        float p = s1;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
+        sum1 = p;
+    }
+    if (ok2) {
+        float p = s2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
+        sum2 = p;
+    }
+}
+template <int R, int ST, bool EVERY_CHUNK>
+__device__ __forceinline__ void tap_sum2(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c1, int2 c2,
+                                         int ithr, float& sum1, float& sum2, bool& ok1, bool& ok2, int lane) {
+    if (interior_of<R>(lp, c1) && interior_of<R>(lp, c2))
+        tap_sum2_in<R, ST, true, EVERY_CHUNK>(lp, tgt, W, H, c1, c2, ithr, sum1, sum2, ok1, ok2, lane);
+    else
+        tap_sum2_in<R, ST, false, EVERY_CHUNK>(lp, tgt, W, H, c1, c2, ithr, sum1, sum2, ok1, ok2, lane);
+}
+
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
 // Key of a candidate offset for duplicate detection; lanes without a
@@ -690,6 +745,29 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                 const int l = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
+                if constexpr (!CENSUS && !PLANES) {
+                    // a second candidate: the two share their gathers' latency (square patches only: for plane
+                    // levels the pair's registers spill, and the sweep was slower)
+                    if (todo) {
+                        const int l2 = __ffs(todo) - 1;
+                        todo &= todo - 1;
+                        const int2 c2 = make_int2(__shfl_sync(FULL, cand.x, l2), __shfl_sync(FULL, cand.y, l2));
+                        float s1 = 0.f, s2 = 0.f;
+                        bool ok1, ok2;
+                        tap_sum2<R, ST, false>(lp, tgt, W, H, c, c2, ithr, s1, s2, ok1, ok2, lane);
+                        if (ok1 && s1 < bc) {
+                            bc = s1;
+                            best = c;
+                        }
+                        if (ok2 && s2 < bc) {
+                            bc = s2;
+                            best = c2;
+                        }
+                        ithr = abandon_threshold(bc);
+                        nev += 2;
+                        continue;
+                    }
+                }
                 if constexpr (CENSUS) {
                     int sum;  // exact integer costs: the incumbent's sum is an integer held in a float
                     if (census_sum<R>(lp, reinterpret_cast<const uint32_t*>(tgt), W, H, c, (int)bc, sum, lane) &&
