@@ -685,10 +685,6 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
         float bc = pv.cost[dir][i];  // raw sum of the incumbent
         int ithr = CENSUS ? 0 : abandon_threshold(bc);
         int nev = 0;
-        // random words for the search radii, two radii per Philox call, one call per lane
-        uint4 rw = make_uint4(0, 0, 0, 0);
-        if (lane < (nrad + 1) / 2)
-            rw = philox((uint32_t)i, ((uint32_t)it << 8) | (uint32_t)lane, tag, pv.pair_id, k0, k1);
         // list A
         int2 cand = make_int2(0, 0);
         bool ok = false;
@@ -727,6 +723,10 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
             if (list_b) {
                 // list B: random search around v0, the best offset after list A
                 const int2 v0 = best;
+                // random words for the search radii, two radii per Philox call, one call per lane
+                uint4 rw = make_uint4(0, 0, 0, 0);
+                if (lane < (nrad + 1) / 2)
+                    rw = philox((uint32_t)i, ((uint32_t)it << 8) | (uint32_t)lane, tag, pv.pair_id, k0, k1);
                 const int src_lane = lane >> 1;
                 uint32_t wx = __shfl_sync(FULL, rw.x, src_lane), wy = __shfl_sync(FULL, rw.y, src_lane);
                 const uint32_t wz = __shfl_sync(FULL, rw.z, src_lane), ww = __shfl_sync(FULL, rw.w, src_lane);
