@@ -168,7 +168,11 @@ gpm_status gpm_sync(gpm_ctx* ctx);
                                        positive denominator at the window centre)
      GPM_MODEL_INFO int32  [2][m][12]  valid, inliers, RANSAC input size,
                                        winning hypothesis, its inliers, flags,
-                                       |S_R n S_C|, assigned, symmetric, 3 x 0
+                                       |S_R n S_C|, assigned, symmetric, 3 x 0;
+                                       fewer than max(4, min_inliers) matches:
+                                       winner -1, its inliers 0; enough matches
+                                       but every sample degenerate: winner -1,
+                                       its inliers -1
      GPM_LABELS     int32  [2][n] model id (-1 none), then float [2][n] L,
                     then double [2][n][2] plane flow (8-byte aligned: the
                     float block is padded to a multiple of 8 bytes)

@@ -19,7 +19,7 @@ from . import build as _build
 
 MAX_SCALES = 8
 MI = 12
-MI_VALID, MI_COUNT, MI_NIN, MI_BESTK, MI_BESTSCORE, MI_FLAGS, MI_NRC, MI_NASSIGN, MI_NSYM, MI_AMB = range(10)
+MI_VALID, MI_COUNT, MI_NIN, MI_BESTK, MI_BESTSCORE, MI_FLAGS, MI_NRC, MI_NASSIGN, MI_NSYM, MI_AMB, MI_GAP10 = range(11)
 F_FITTED, F_REFIT, F_AMBIG, F_BAD_FB, F_BAD_KAPPA, F_BAD_GEOM = 1, 2, 4, 8, 16, 32
 CUE_M2O = 1
 
@@ -100,6 +100,8 @@ def lib() -> C.CDLL:
             "orc_h_minimal": (C.c_int, [d, d, d]),
             "orc_h_dlt": (C.c_int, [C.c_int, d, d, d]),
             "orc_fit_level": (None, [pp, d, d, C.c_int, C.c_int, C.c_int, i32, i32, u8, d, i32]),
+            "orc_den_zero_at_centre": (C.c_int, [i32, i32, i32, i32, C.c_int, C.c_int, C.c_int]),
+            "orc_fit_cells": (None, [pp, d, d, C.c_int, C.c_int, C.c_int, i32, i32, u8, i32, C.c_int, d, i32]),
             "orc_assign": (None, [pp, d, d, C.c_int, C.c_int, d, i32, u8, i32, d, d, d, u8]),
             "orc_cue_counts": (None, [pp, C.c_int, C.c_int, i32, d, d, i32, d, d, i32, u8]),
             "orc_cue_invalidate": (None, [pp, C.c_int, C.c_int, i32]),
@@ -296,6 +298,25 @@ def fit_level(P: Params, src, tgt, direction, level, stage, vx, vy, resid, mh, m
     lib().orc_fit_level(C.byref(P.c()), _p(_f64(src), C.c_double), _p(_f64(tgt), C.c_double), direction, level, stage,
                         _p(vx, C.c_int32), _p(vy, C.c_int32), _p(resid, C.c_uint8), _p(mh, C.c_double),
                         _p(mi, C.c_int32))
+
+
+def den_zero_at_centre(src, dst, x0: int, y0: int, s: int) -> bool:
+    """Exact test: the homography of 4 integer point pairs (4 x 2 each) has a zero denominator at the centre of
+    the window of side s at (x0, y0)."""
+    a = np.ascontiguousarray(src, np.int32).reshape(4, 2)
+    b = np.ascontiguousarray(dst, np.int32).reshape(4, 2)
+    sx, sy, tx, ty = (np.ascontiguousarray(v) for v in (a[:, 0], a[:, 1], b[:, 0], b[:, 1]))
+    return bool(lib().orc_den_zero_at_centre(_p(sx, C.c_int32), _p(sy, C.c_int32), _p(tx, C.c_int32),
+                                             _p(ty, C.c_int32), x0, y0, s))
+
+
+def fit_cells(P: Params, src, tgt, direction, level, stage, vx, vy, resid, cells, mh, mi):
+    """fit_level restricted to the listed windows of the level (their model slots of mh / mi are written)."""
+    cells = np.ascontiguousarray(cells, np.int32)
+    lib().orc_fit_cells(C.byref(P.c()), _p(_f64(src), C.c_double), _p(_f64(tgt), C.c_double), direction, level,
+                        stage, _p(np.ascontiguousarray(vx, np.int32), C.c_int32),
+                        _p(np.ascontiguousarray(vy, np.int32), C.c_int32), _p(resid, C.c_uint8),
+                        _p(cells, C.c_int32), len(cells), _p(mh, C.c_double), _p(mi, C.c_int32))
 
 
 def assign(P: Params, src, tgt, level, stage, mh, mi, mask, lab: Labels, amb=None):

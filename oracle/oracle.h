@@ -51,7 +51,7 @@ enum {
     ORC_MI_NASSIGN,     /* pixels assigned to the model (tentative labels) */
     ORC_MI_NSYM,        /* of those, forward-backward symmetric */
     ORC_MI_AMB,         /* ambiguous residual comparisons of the winner */
-    ORC_MI_RESERVED0,
+    ORC_MI_GAP10,       /* refit: floor(-log10) of the relative eigen-gap of its normal matrix (0: none) */
     ORC_MI_RESERVED1,
     ORC_MI
 };
@@ -110,6 +110,14 @@ int orc_h_dlt(int n, const double* src /*nx2*/, const double* dst /*nx2*/, doubl
 /* ---- robust plane fit per window (Sec. 3.1.2, 3.2) ---- */
 void orc_fit_level(const orc_params* P, const double* src, const double* tgt, int dir, int level,
                    int stage, const int32_t* vx, const int32_t* vy, const uint8_t* resid,
+                   double* mh, int32_t* mi);
+
+/* exact: the 4-point homography of sample (s -> t) has a zero denominator at the centre of the window of
+   side s at (x0, y0); such a hypothesis cannot be oriented and is rejected */
+int orc_den_zero_at_centre(const int32_t* sx, const int32_t* sy, const int32_t* tx, const int32_t* ty, int x0, int y0,
+                           int s);
+void orc_fit_cells(const orc_params* P, const double* src, const double* tgt, int dir, int level, int stage,
+                   const int32_t* vx, const int32_t* vy, const uint8_t* resid, const int32_t* cells, int ncells,
                    double* mh, int32_t* mi);
 
 /* ---- plane distortion compensation and assignment (eq. 3-4) ---- */

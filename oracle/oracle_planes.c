@@ -158,7 +158,13 @@ int orc_h_minimal(const double* src, const double* dst, double H[9]) {
 
 /* Smallest-eigenvalue eigenvector of a symmetric 9x9 matrix by the cyclic
    Jacobi method. */
-static void jacobi_min_vector(double A[9][9], double v[9]) {
+static void jacobi_min_vector_gap(double A[9][9], double v[9], double* gap);
+static void jacobi_min_vector(double A[9][9], double v[9]) { jacobi_min_vector_gap(A, v, NULL); }
+
+/* eigenvector of the smallest eigenvalue of the symmetric A (destroyed); with
+   gap != NULL also (lambda_2 - lambda_1) / lambda_max, the relative gap that
+   bounds how far the eigenvector moves under a perturbation of A */
+static void jacobi_min_vector_gap(double A[9][9], double v[9], double* gap) {
     double V[9][9];
     for (int i = 0; i < 9; ++i)
         for (int j = 0; j < 9; ++j) V[i][j] = (i == j);
@@ -196,11 +202,22 @@ static void jacobi_min_vector(double A[9][9], double v[9]) {
     for (int i = 1; i < 9; ++i)
         if (A[i][i] < A[m][m]) m = i;
     for (int i = 0; i < 9; ++i) v[i] = V[i][m];
+    if (gap) {
+        double l1 = DBL_MAX, lmax = 0;
+        for (int i = 0; i < 9; ++i) {
+            lmax = fmax(lmax, fabs(A[i][i]));
+            if (i != m) l1 = fmin(l1, A[i][i]);
+        }
+        *gap = lmax > 0 ? (l1 - A[m][m]) / lmax : 0.0;
+    }
 }
 
+static int h_dlt_gap(int n, const double* src, const double* dst, double H[9], double* gap);
 /* Least-squares refit over n >= 4 pairs: normalised DLT, h = eigenvector of
    A^T A with the smallest eigenvalue. */
-int orc_h_dlt(int n, const double* src, const double* dst, double H[9]) {
+int orc_h_dlt(int n, const double* src, const double* dst, double H[9]) { return h_dlt_gap(n, src, dst, H, NULL); }
+
+static int h_dlt_gap(int n, const double* src, const double* dst, double H[9], double* gap) {
     if (n < 4) return 0;
     double Ts[9], Td[9];
     double* ps = (double*)malloc(sizeof(double) * 4 * n);
@@ -217,7 +234,7 @@ int orc_h_dlt(int n, const double* src, const double* dst, double H[9]) {
                     for (int q = 0; q < 9; ++q) M[p][q] += a[r][p] * a[r][q];
         }
         double h[9];
-        jacobi_min_vector(M, h);
+        jacobi_min_vector_gap(M, h, gap);
         denormalise(h, Ts, Td, H);
     }
     free(ps);
@@ -291,7 +308,177 @@ typedef struct {
     double* p; /* n x 2 source points */
     double* q; /* n x 2 target points */
     int32_t* pix;
+    double cx, cy; /* window centre */
 } matches_t;
+
+/* ---- near-tie bands for decisions that FP32 evaluation of a homography
+   takes.  Not part of the method: these only widen the logs of comparisons
+   the oracle calls ambiguous.
+
+   A homography is evaluated in FP32 in a frame local to its window: source
+   u = p - c about the window centre c, H scaled to denominator 1 at c,
+   displacement at c held to ~1e-7 px.  With e = g . u the denominator's
+   change (den = 1 + e), B = A - I the local linear part, t the displacement
+   at c and v a match's offset q - p, the residual numerator is
+       n = (t - v) + B u - (u + v) e,   and the inlier test n.n < t2 den^2.
+   Every term of n is stored or formed with relative error of a few units of
+   2^-24, so |dn| <= K 2^-24 S with S the sum of the terms' magnitudes, and
+   |d den| <= K 2^-24 (1 + |g0 ux| + |g1 uy|).  A strongly projective H
+   (denominator small somewhere in the window) or a far match makes S large
+   against n: the FP32 test can then decide differently from FP64 well
+   outside a fixed relative band. */
+#define ORC_FP32_K 8.0
+#define ORC_REFIT_GAP 1e-8
+#define ORC_U32 5.9604644775390625e-08 /* 2^-24 */
+typedef struct {
+    double b00, b01, b10, b11, tx, ty, g0, g1; /* local form about the window centre */
+} hloc_t;
+
+static int h_local(const double* H, double cx, double cy, hloc_t* L) {
+    const double z0 = H[6] * cx + H[7] * cy + H[8];
+    if (!(z0 != 0)) return 0;
+    const double X0 = (H[0] * cx + H[1] * cy + H[2]) / z0, Y0 = (H[3] * cx + H[4] * cy + H[5]) / z0;
+    L->g0 = H[6] / z0;
+    L->g1 = H[7] / z0;
+    L->b00 = (H[0] - X0 * H[6]) / z0 - 1.0;
+    L->b01 = (H[1] - X0 * H[7]) / z0;
+    L->b10 = (H[3] - Y0 * H[6]) / z0;
+    L->b11 = (H[4] - Y0 * H[7]) / z0 - 1.0;
+    L->tx = X0 - cx;
+    L->ty = Y0 - cy;
+    return 1;
+}
+
+/* FP32 error bound of the inlier test f = n.n - t2 den^2 of source p with
+   offset v, expressed on r2 - t2 (f / den^2); 0 if the local form fails */
+static double fp32_band_r2(const hloc_t* L, double px, double py, double vx, double vy, double cx, double cy,
+                           double t2) {
+    const double ux = px - cx, uy = py - cy;
+    const double ea = fabs(L->g0 * ux) + fabs(L->g1 * uy);
+    const double e = L->g0 * ux + L->g1 * uy, den = 1.0 + e;
+    const double nx = (L->tx - vx) + L->b00 * ux + L->b01 * uy - (ux + vx) * e;
+    const double ny = (L->ty - vy) + L->b10 * ux + L->b11 * uy - (uy + vy) * e;
+    const double Sx = fabs(L->tx - vx) + fabs(L->b00 * ux) + fabs(L->b01 * uy) + (fabs(ux) + fabs(vx)) * ea;
+    const double Sy = fabs(L->ty - vy) + fabs(L->b10 * ux) + fabs(L->b11 * uy) + (fabs(uy) + fabs(vy)) * ea;
+    const double k = ORC_FP32_K * ORC_U32;
+    const double df = 2.0 * (fabs(nx) * k * Sx + fabs(ny) * k * Sy) + 2.0 * t2 * fabs(den) * k * (1.0 + ea);
+    return den != 0 ? df / (den * den) : HUGE_VAL;
+}
+
+/* FP32 error bound of the mapped position of source p (sum of |dX| and |dY|) */
+static double fp32_band_pos(const hloc_t* L, double px, double py, double cx, double cy) {
+    const double ux = px - cx, uy = py - cy;
+    const double ea = fabs(L->g0 * ux) + fabs(L->g1 * uy);
+    const double e = L->g0 * ux + L->g1 * uy, den = 1.0 + e;
+    if (!(den != 0)) return HUGE_VAL;
+    const double Dx = (L->tx + L->b00 * ux + L->b01 * uy - ux * e) / den;
+    const double Dy = (L->ty + L->b10 * ux + L->b11 * uy - uy * e) / den;
+    const double Sx = fabs(Dx * den) + fabs(L->b00 * ux) + fabs(L->b01 * uy) + fabs(ux) * ea;
+    const double Sy = fabs(Dy * den) + fabs(L->b10 * ux) + fabs(L->b11 * uy) + fabs(uy) * ea;
+    const double k = ORC_FP32_K * ORC_U32;
+    return k * (Sx + Sy + (fabs(Dx) + fabs(Dy)) * (1.0 + ea)) / fabs(den);
+}
+
+/* largest change of a channel of the bilinear sample of img around (X, Y)
+   per unit of position: the largest texel difference of its 2 x 2 cell */
+static double bilinear_slope(const double* img, int W, int H, double X, double Y) {
+    int x0 = (int)floor(X), y0 = (int)floor(Y);
+    if (x0 < 0) x0 = 0;
+    if (y0 < 0) y0 = 0;
+    if (x0 > W - 1) x0 = W - 1;
+    if (y0 > H - 1) y0 = H - 1;
+    const int x1 = x0 + 1 < W ? x0 + 1 : W - 1, y1 = y0 + 1 < H ? y0 + 1 : H - 1;
+    double m = 0;
+    for (int c = 0; c < 3; ++c) {
+        const double a = img[((size_t)y0 * W + x0) * 3 + c], b = img[((size_t)y0 * W + x1) * 3 + c];
+        const double d = img[((size_t)y1 * W + x0) * 3 + c], e = img[((size_t)y1 * W + x1) * 3 + c];
+        m = fmax(m, fmax(fmax(fabs(b - a), fabs(e - d)), fmax(fabs(d - a), fabs(e - b))));
+    }
+    return m;
+}
+
+/* Exact test that the 4-point homography of a sample has a zero
+   denominator at the window centre.  With the projective bases
+   P_s = [s1 s2 s3] diag(adj([s1 s2 s3]) s4) of the source points and weights
+   mu = adj([t1 t2 t3]) t4 of the target points (homogeneous, z = 1), H is
+   proportional to P_t adj(P_s), and P_t's third row is mu; so the
+   denominator at p is proportional to mu^T adj(P_s) (p, 1).  Source points
+   relative to an integer origin o near the centre (|coordinates| <= 48 for
+   windows up to 96 px) and the centre doubled keep every product below
+   2^110.  Such a hypothesis cannot be oriented (positive denominator at the
+   centre) and is rejected like a degenerate sample. */
+static int den_zero_at_centre(const int* sx, const int* sy, const int* tx, const int* ty, int ox, int oy,
+                              int cx2, int cy2) {
+    typedef __int128 i128;
+    long long u[4], v[4];
+    for (int j = 0; j < 4; ++j) {
+        u[j] = sx[j] - ox;
+        v[j] = sy[j] - oy;
+    }
+    /* M = [s1 s2 s3] (columns), lambda = adj(M) s4 */
+    const long long M[9] = {u[0], u[1], u[2], v[0], v[1], v[2], 1, 1, 1};
+    long long aM[9];
+    aM[0] = M[4] * M[8] - M[5] * M[7];
+    aM[1] = M[2] * M[7] - M[1] * M[8];
+    aM[2] = M[1] * M[5] - M[2] * M[4];
+    aM[3] = M[5] * M[6] - M[3] * M[8];
+    aM[4] = M[0] * M[8] - M[2] * M[6];
+    aM[5] = M[2] * M[3] - M[0] * M[5];
+    aM[6] = M[3] * M[7] - M[4] * M[6];
+    aM[7] = M[1] * M[6] - M[0] * M[7];
+    aM[8] = M[0] * M[4] - M[1] * M[3];
+    const long long s4[3] = {u[3], v[3], 1};
+    long long lam[3];
+    for (int r = 0; r < 3; ++r) lam[r] = aM[3 * r] * s4[0] + aM[3 * r + 1] * s4[1] + aM[3 * r + 2] * s4[2];
+    i128 Ps[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) Ps[3 * r + c] = (i128)M[3 * r + c] * lam[c];
+    i128 aP[9];
+    aP[0] = Ps[4] * Ps[8] - Ps[5] * Ps[7];
+    aP[1] = Ps[2] * Ps[7] - Ps[1] * Ps[8];
+    aP[2] = Ps[1] * Ps[5] - Ps[2] * Ps[4];
+    aP[3] = Ps[5] * Ps[6] - Ps[3] * Ps[8];
+    aP[4] = Ps[0] * Ps[8] - Ps[2] * Ps[6];
+    aP[5] = Ps[2] * Ps[3] - Ps[0] * Ps[5];
+    aP[6] = Ps[3] * Ps[7] - Ps[4] * Ps[6];
+    aP[7] = Ps[1] * Ps[6] - Ps[0] * Ps[7];
+    aP[8] = Ps[0] * Ps[4] - Ps[1] * Ps[3];
+    /* mu = adj(T) t4, T = [t1 t2 t3] (columns) */
+    const long long T[9] = {tx[0], tx[1], tx[2], ty[0], ty[1], ty[2], 1, 1, 1};
+    long long aT[9];
+    aT[0] = T[4] * T[8] - T[5] * T[7];
+    aT[1] = T[2] * T[7] - T[1] * T[8];
+    aT[2] = T[1] * T[5] - T[2] * T[4];
+    aT[3] = T[5] * T[6] - T[3] * T[8];
+    aT[4] = T[0] * T[8] - T[2] * T[6];
+    aT[5] = T[2] * T[3] - T[0] * T[5];
+    aT[6] = T[3] * T[7] - T[4] * T[6];
+    aT[7] = T[1] * T[6] - T[0] * T[7];
+    aT[8] = T[0] * T[4] - T[1] * T[3];
+    const long long t4[3] = {tx[3], ty[3], 1};
+    long long mu[3];
+    for (int r = 0; r < 3; ++r) mu[r] = aT[3 * r] * t4[0] + aT[3 * r + 1] * t4[1] + aT[3 * r + 2] * t4[2];
+    /* (2c - 2o, 2) doubled centre */
+    const long long p2[3] = {cx2 - 2LL * ox, cy2 - 2LL * oy, 2};
+    i128 den = 0;
+    for (int c = 0; c < 3; ++c) {
+        const i128 row = (i128)mu[0] * aP[c] + (i128)mu[1] * aP[3 + c] + (i128)mu[2] * aP[6 + c];
+        den += row * p2[c];
+    }
+    return den == 0;
+}
+
+int orc_den_zero_at_centre(const int32_t* sx, const int32_t* sy, const int32_t* tx, const int32_t* ty, int x0, int y0,
+                           int s) {
+    int a[4], b[4], c[4], d[4];
+    for (int j = 0; j < 4; ++j) {
+        a[j] = sx[j];
+        b[j] = sy[j];
+        c[j] = tx[j];
+        d[j] = ty[j];
+    }
+    return den_zero_at_centre(a, b, c, d, x0 + s / 2, y0 + s / 2, 2 * x0 + s - 1, 2 * y0 + s - 1);
+}
 
 static int collinear_int(const int* x, const int* y, int a, int b, int c) {
     long long cr = (long long)(x[b] - x[a]) * (y[c] - y[a]) - (long long)(y[b] - y[a]) * (x[c] - x[a]);
@@ -301,14 +488,25 @@ static int collinear_int(const int* x, const int* y, int a, int b, int c) {
 /* counts inliers ||H p - q||^2 < t^2 and the comparisons inside the near-tie band */
 static int score_h(const double* H, const matches_t* M, double t2, int* amb, uint8_t* flags) {
     int cnt = 0, a = 0;
+    hloc_t L;
+    const int loc = amb ? h_local(H, M->cx, M->cy, &L) : 0;
     for (int j = 0; j < M->n; ++j) {
         double X, Y;
         int in = 0;
-        if (map_h(H, M->p[2 * j], M->p[2 * j + 1], &X, &Y)) {
+        const double px = M->p[2 * j], py = M->p[2 * j + 1];
+        if (map_h(H, px, py, &X, &Y)) {
             double dx = X - M->q[2 * j], dy = Y - M->q[2 * j + 1];
             double r2 = dx * dx + dy * dy;
             in = r2 < t2;
             if (rel_gap(r2, t2) < ORC_TIE_REL) ++a;
+            else if (loc && fabs(r2 - t2) <= fp32_band_r2(&L, px, py, M->q[2 * j] - px, M->q[2 * j + 1] - py,
+                                                          M->cx, M->cy, t2))
+                ++a;
+        } else if (amb && loc) {
+            /* denominator at or below zero: ambiguous if FP32 could see it positive */
+            const double ux = px - M->cx, uy = py - M->cy;
+            const double den = 1.0 + L.g0 * ux + L.g1 * uy;
+            if (fabs(den) <= ORC_FP32_K * ORC_U32 * (1.0 + fabs(L.g0 * ux) + fabs(L.g1 * uy))) ++a;
         }
         cnt += in;
         if (flags) flags[j] = (uint8_t)in;
@@ -357,6 +555,8 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
         }
     const int N = M.n;
     const double cxw = x0 + 0.5 * (s - 1), cyw = y0 + 0.5 * (s - 1);
+    M.cx = cxw;
+    M.cy = cyw;
     mi[ORC_MI_NIN] = N;
     for (int k = 0; k < 9; ++k) Hout[k] = 0;
     if (N < P->min_inliers || N < 4) goto done;
@@ -384,6 +584,7 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
                 degen = collinear_int(sx, sy, TRI[t][0], TRI[t][1], TRI[t][2]) ||
                         collinear_int(tx, ty, TRI[t][0], TRI[t][1], TRI[t][2]);
             if (degen) continue;
+            if (den_zero_at_centre(sx, sy, tx, ty, x0 + s / 2, y0 + s / 2, 2 * x0 + s - 1, 2 * y0 + s - 1)) continue;
             double ps[8], pd[8], Hk[9];
             for (int j = 0; j < 4; ++j) {
                 ps[2 * j] = sx[j]; ps[2 * j + 1] = sy[j];
@@ -401,7 +602,8 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
                 memcpy(Hb, Hk, sizeof Hb);
             }
         }
-        int ambig = 0;
+        /* the winner's own inlier decisions fix its recorded score and the refit's input set */
+        int ambig = bamb > 0;
         for (int k = 0; k < K && best >= 0; ++k) {
             if (k == best || scores[k] < 0) continue;
             if (k < best && scores[k] + ambs[k] >= bscore - bamb) ambig = 1;
@@ -425,7 +627,12 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
             }
         double Hr[9];
         int famb = bamb, count = bscore;
-        if (orc_h_dlt(n, ip, iq, Hr)) {
+        double gap = 0;
+        if (h_dlt_gap(n, ip, iq, Hr, &gap)) {
+            mi[ORC_MI_GAP10] = gap > 0 ? (int)floor(-log10(gap)) : 99;
+            /* the eigenvector moves by about 1e-16 / gap under rounding of the normal matrix: below
+               ORC_REFIT_GAP the refit is not determined to the 1e-6 a model is compared at */
+            if (!(gap >= ORC_REFIT_GAP)) ambig = 1;
             normalise_sign(Hr, cxw, cyw);
             int ramb;
             int rscore = score_h(Hr, &M, t2, &ramb, NULL);
@@ -471,15 +678,22 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
         /* S_R intersect S_C: RANSAC inliers of the final H that are also colour inliers */
         score_h(Hb, &M, t2, NULL, fl);
         int nrc = 0;
+        hloc_t Lb;
+        const int locb = h_local(Hb, cxw, cyw, &Lb);
         for (int j = 0; j < N; ++j) {
             if (!fl[j]) continue;
             double X, Y;
             if (!map_h(Hb, M.p[2 * j], M.p[2 * j + 1], &X, &Y)) continue;
+            /* FP32 position error of the mapped point, and what it can move in the frame test and the colour */
+            const double dp = locb ? fp32_band_pos(&Lb, M.p[2 * j], M.p[2 * j + 1], cxw, cyw) : 0.0;
             if (near_frame_edge(P, X, Y)) ambig = 1;
+            if (fabs(X + ORC_FRAME_TOL) <= dp || fabs(X - (P->W - 1 + ORC_FRAME_TOL)) <= dp ||
+                fabs(Y + ORC_FRAME_TOL) <= dp || fabs(Y - (P->H - 1 + ORC_FRAME_TOL)) <= dp)
+                ambig = 1;
             if (!in_frame(P, X, Y)) continue;
             double d = delta_at(P, src, tgt, ix[j], iy[j], X, Y);
             if (d < P->eps) ++nrc;
-            if (near_colour(d, P->eps)) ambig = 1;
+            if (near_colour(d, P->eps) || fabs(d - P->eps) <= bilinear_slope(tgt, P->W, P->H, X, Y) * dp) ambig = 1;
         }
         mi[ORC_MI_NRC] = nrc;
         if (ambig) mi[ORC_MI_FLAGS] |= ORC_F_AMBIG;
@@ -497,6 +711,26 @@ void orc_fit_level(const orc_params* P, const double* src, const double* tgt, in
     int ncell = g->ncx * g->ncy;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int c = 0; c < ncell; ++c) {
+        int cx = c % g->ncx, cy = c / g->ncx;
+        int id = (g->base + c) * 2 + (stage - 1);
+        fit_cell(P, src, tgt, dir, level, stage, c, g->xs[cx], g->ys[cy], g->s, vx, vy, resid,
+                 mh + (size_t)id * 9, mi + (size_t)id * ORC_MI);
+    }
+    free(g);
+}
+
+/* The same fit for a listed subset of the level's windows (spot checks of
+   single windows at full frame sizes); indices outside the level are skipped. */
+void orc_fit_cells(const orc_params* P, const double* src, const double* tgt, int dir, int level, int stage,
+                   const int32_t* vx, const int32_t* vy, const uint8_t* resid, const int32_t* cells, int ncells,
+                   double* mh, int32_t* mi) {
+    grid_t* g = (grid_t*)malloc(sizeof(grid_t));
+    make_grid(P, level, g);
+    const int ncell = g->ncx * g->ncy;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < ncells; ++k) {
+        const int c = cells[k];
+        if (c < 0 || c >= ncell) continue;
         int cx = c % g->ncx, cy = c / g->ncx;
         int id = (g->base + c) * 2 + (stage - 1);
         fit_cell(P, src, tgt, dir, level, stage, c, g->xs[cx], g->ys[cy], g->s, vx, vy, resid,

@@ -502,6 +502,17 @@ __device__ int gather_matches(const G& grp, const PairView& pv, const LevelGeom&
     return N;
 }
 
+// |(a, b)| for exact integers: in FP32 from exact inputs when both are below
+// 2^24 (one rounding of the sum of squares and one of the root), else in FP64.
+__device__ __forceinline__ double scaled_dist(long long a, long long b) {
+    if (a > -16777216ll && a < 16777216ll && b > -16777216ll && b < 16777216ll) {
+        const float fa = (float)(int)a, fb = (float)(int)b;
+        return (double)sqrtf(fmaf(fa, fa, fb * fb));
+    }
+    const double da = (double)a, db = (double)b;
+    return sqrt(da * da + db * db);
+}
+
 template <class G, int ST>
 __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
                            const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, int* kfull,
@@ -624,7 +635,10 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
                        : (((unsigned long long)(best_score + 1)) << 32) |
                              (unsigned long long)(0xFFFFFFFFu - (uint32_t)best_k);
     const unsigned long long wkey = grp.max(key);
-    if (wkey == 0ull) return;
+    if (wkey == 0ull) {  // every sample degenerate: no winner, best score -1
+        if (tid == 0) mi[MI_BESTSCORE] = -1;
+        return;
+    }
     const int wscore = (int)(wkey >> 32) - 1;
     const int wk = (int)(0xFFFFFFFFu - (uint32_t)(wkey & 0xFFFFFFFFull));
     if (tid < 32) {  // first warp: the winner again, exact, and its evaluation form
@@ -667,6 +681,10 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     const float fmx = __fdiv_rn((float)sx, fn), fmy = __fdiv_rn((float)sy, fn);
     const float fmqx = __fdiv_rn((float)tx, fn), fmqy = __fdiv_rn((float)ty, fn);
     const int cx = __float2int_rn(fmx), cy = __float2int_rn(fmy), cu = __float2int_rn(fmqx), cv = __float2int_rn(fmqy);
+    // Hartley scales: distances to the exact centroids, as n |p - mean| = |n p - sum| from exact integers
+    // (the least-squares refit of a noisy support moves with its normalisation, so the scale must carry no
+    // more than float rounding)
+    const long long nw = wscore;
     double ds = 0, dt = 0;
     long long R[24];
 #pragma unroll
@@ -674,10 +692,8 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
         if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
-        // FP32 roots summed in FP64: the mean distance only sets the normalising scale
-        const float a = mt.x - fmx, b = mt.y - fmy, c = (mt.x + mt.z) - fmqx, d = (mt.y + mt.w) - fmqy;
-        ds += (double)sqrtf(a * a + b * b);
-        dt += (double)sqrtf(c * c + d * d);
+        ds += scaled_dist(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
+        dt += scaled_dist(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
         const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
         const int U = exact_int(mt.x + mt.z) - cu, V = exact_int(mt.y + mt.w) - cv;
         const int zz[6] = {X * X, X * Y, X, Y * Y, Y, 1};
@@ -690,8 +706,8 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             R[18 + q] += (long long)w3 * zz[q];
         }
     }
-    ds = grp.sum(ds);
-    dt = grp.sum(dt);
+    ds = grp.sum(ds) / (double)nw;  // sums of |p - mean|
+    dt = grp.sum(dt) / (double)nw;
 #pragma unroll
     for (int q = 0; q < 24; ++q) {
         const long long t = grp.sum(R[q]);

@@ -65,3 +65,21 @@ def rel_close(a, b, rel=1e-5, floor=1e-7, atol=0.0):
 # channels of values in [0, 1]; in FP32 each sample carries a few ulp(1)
 # (~6e-8 each) of rounding, so its bound is absolute: 1e-6.
 COLOUR_ATOL = 1e-6
+
+
+# RANSAC outputs of a model that depend only on its window's matches (and, for the colour overlap, the frames)
+RANSAC_FIELDS = [O.MI_COUNT, O.MI_NIN, O.MI_BESTK, O.MI_BESTSCORE, O.MI_NRC]
+
+
+def ransac_equal(gmh, gmi, omh, omi, ids):
+    """Per model: the RANSAC outputs (support, input size, winner, refit/geometry flags, colour overlap) and
+    H within 1e-6 after normalisation."""
+    ok = np.ones(len(ids), bool)
+    geo = O.F_FITTED | O.F_REFIT | O.F_BAD_GEOM
+    for k, m in enumerate(ids):
+        a, b = gmi[m], omi[m]
+        if any(a[f] != b[f] for f in RANSAC_FIELDS) or (a[O.MI_FLAGS] & geo) != (b[O.MI_FLAGS] & geo):
+            ok[k] = False
+        elif b[O.MI_FLAGS] & O.F_FITTED and np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() > 1e-6:
+            ok[k] = False
+    return ok

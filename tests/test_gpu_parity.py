@@ -15,6 +15,7 @@ import oracle as O
 from paper_1804_03787_gb300 import gpm, scene
 
 from _parity import COLOUR_ATOL, TIE, dilate, norm_h, oracle_frames, oracle_params, rel_close
+from _parity import ransac_equal as _ransac_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -151,7 +152,6 @@ def _oracle_level(P, frames, l, vx, vy, mh, mi, acc, cue):
     return S1, C, frozen, amb
 
 
-RANSAC_FIELDS = [O.MI_COUNT, O.MI_NIN, O.MI_BESTK, O.MI_BESTSCORE, O.MI_NRC]
 CUE_FIELDS = [O.MI_VALID, O.MI_NASSIGN, O.MI_NSYM]
 
 
@@ -162,20 +162,6 @@ def _label_report(bad, g, o, d, W, k=8):
         out.append((int(i % W), int(i // W), int(g[0][d][i]), int(o.m[i]), float(g[1][d][i]), float(o.L[i]),
                     tuple(np.round(g[2][d][i], 6)), (round(float(o.fx[i]), 6), round(float(o.fy[i]), 6))))
     return out
-
-
-def _ransac_equal(gmh, gmi, omh, omi, ids):
-    """Per model: the RANSAC outputs (support, input size, winner, refit/geometry flags, colour overlap) and
-    H within 1e-6 after normalisation."""
-    ok = np.ones(len(ids), bool)
-    geo = O.F_FITTED | O.F_REFIT | O.F_BAD_GEOM
-    for k, m in enumerate(ids):
-        a, b = gmi[m], omi[m]
-        if any(a[f] != b[f] for f in RANSAC_FIELDS) or (a[O.MI_FLAGS] & geo) != (b[O.MI_FLAGS] & geo):
-            ok[k] = False
-        elif b[O.MI_FLAGS] & O.F_FITTED and np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() > 1e-6:
-            ok[k] = False
-    return ok
 
 
 def _cues_equal(gmi, omi, ids):

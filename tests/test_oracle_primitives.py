@@ -172,6 +172,57 @@ def test_minimal_solver_rejects_collinear_sample():
     assert O.h_minimal(p, p + 1) is None
 
 
+def test_exact_centre_denominator_test_against_fp64_solver():
+    """The exact test that a sample's homography has a zero denominator at the window centre, against the
+    FP64 minimal solver (pinned above): samples built from an integer H whose third row vanishes at the centre
+    are caught; a 1 px change of one target and random samples are not, and for those the solver's
+    denominator at the centre is far from zero."""
+    rng = np.random.default_rng(11)
+    for s in (8, 16, 64, 96):
+        for _ in range(40):
+            x0, y0 = int(rng.integers(0, 900)), int(rng.integers(0, 300))
+            cx2, cy2 = 2 * x0 + s - 1, 2 * y0 + s - 1          # twice the centre
+            # third row (2, 0, -cx2) or (0, 2, -cy2): the denominator is 2x - cx2 (odd, +-1 next to the centre)
+            use_x = bool(rng.integers(0, 2))
+            row3 = np.array([2, 0, -cx2]) if use_x else np.array([0, 2, -cy2])
+            Hi = np.vstack([rng.integers(-3, 4, size=(2, 3)), row3]).astype(float)
+            # two source points on each line next to the centre: denominator -1 or +1, integer targets
+            a, b = (cx2 - 1) // 2, (cx2 + 1) // 2
+            c, e = (cy2 - 1) // 2, (cy2 + 1) // 2
+            ys = rng.choice(np.arange(y0, y0 + s), 2, replace=False)
+            xs = rng.choice(np.arange(x0, x0 + s), 2, replace=False)
+            src = (np.array([[a, ys[0]], [a, ys[1]], [b, ys[0]], [b, ys[1]]]) if use_x
+                   else np.array([[xs[0], c], [xs[1], c], [xs[0], e], [xs[1], e]]))
+            dst = np.rint(_apply(Hi, src.astype(float))).astype(int)
+            np.testing.assert_allclose(_apply(Hi, src.astype(float)), dst, atol=1e-9)
+            Hm = O.h_minimal(src.astype(float), dst.astype(float))
+            if Hm is None:  # three target points on a line: not a hypothesis at all
+                continue
+            Hm = np.asarray(Hm, float).reshape(3, 3)
+            den_c = (Hm[2, 0] * cx2 + Hm[2, 1] * cy2 + 2 * Hm[2, 2]) / 2
+            assert abs(den_c) < 1e-9 * np.abs(Hm[2]).sum() * (abs(cx2) + abs(cy2) + 2)
+            assert O.den_zero_at_centre(src, dst, x0, y0, s)
+            d2 = dst.copy()
+            d2[3, 0] += 1
+            H2 = O.h_minimal(src.astype(float), d2.astype(float))
+            if H2 is not None:
+                H2 = np.asarray(H2, float).reshape(3, 3)
+                if abs(H2[2, 0] * cx2 + H2[2, 1] * cy2 + 2 * H2[2, 2]) > 1e-6 * np.abs(H2[2]).sum():
+                    assert not O.den_zero_at_centre(src, d2, x0, y0, s)
+    for _ in range(300):
+        s = 64
+        x0, y0 = int(rng.integers(0, 900)), int(rng.integers(0, 300))
+        src = np.stack([rng.integers(x0, x0 + s, 4), rng.integers(y0, y0 + s, 4)], 1)
+        dst = src + rng.integers(-60, 61, size=(4, 2))
+        Hm = O.h_minimal(src.astype(float), dst.astype(float))
+        if Hm is None:
+            continue
+        Hm = np.asarray(Hm, float).reshape(3, 3)
+        den_c = Hm[2, 0] * (x0 + (s - 1) / 2) + Hm[2, 1] * (y0 + (s - 1) / 2) + Hm[2, 2]
+        if abs(den_c) > 1e-9 * np.abs(Hm[2]).sum() * 1000:
+            assert not O.den_zero_at_centre(src, dst, x0, y0, s)
+
+
 def test_dlt_is_least_squares_optimal_under_noise():
     """With noise, the refit has smaller algebraic residual than the generating H
     (it minimises ||A h|| over unit h in normalised coordinates)."""
