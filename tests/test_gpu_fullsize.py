@@ -6,8 +6,9 @@ At this size the oracle cannot run the whole method within a test, so the checks
     the last PatchMatch iteration of the whole frame, re-run by the oracle from the GPU's state before it;
   - every window: the stage-1 and stage-2 RANSAC + refit of every window at every level, re-run by the oracle on
     the GPU's own inputs (its NNF and its residual mask), equal up to the oracle's logged near ties;
-  - properties that hold at any size: patch costs of sampled pixels, plane flows equal to their model's
-    mapping, pixels without a plane keeping their NNF offset, and the occlusion rule of the final map (Sec. 3.4.1).
+  - properties that hold at any size: patch costs of sampled pixels and the fixed point of the last half-step
+    (level 0 and every plane level, with plane-distorted patches), plane flows equal to their model's mapping,
+    pixels without a plane keeping their NNF offset, and the occlusion rule of the final map (Sec. 3.4.1).
 """
 import numpy as np
 import pytest
@@ -125,6 +126,82 @@ def test_fullsize_level0_costs_and_fixed_point(torch, pair):
                     continue
                 cn = O.patch_cost(P, src, tgt, x, y, ux, uy)
                 assert cost[d][i] <= cn * (1 + TIE) + 1e-7, (d, x, y, cost[d][i], cn)
+
+
+def _home_plane(x, y, xs, ys, s, base, mh, mi):
+    """The distorting plane of pixel (x, y) at a level (window side s at positions xs, ys): the home window's --
+    the one whose central half holds the pixel -- residual-stage model if valid, else its first-stage model if
+    valid, else none."""
+    h = s // 2
+    cx = min(max(int(np.floor((x - s // 4) / h)), 0), len(xs) - 1)
+    cy = min(max(int(np.floor((y - s // 4) / h)), 0), len(ys) - 1)
+    cell = cy * len(xs) + cx
+    for st in (1, 0):
+        m = (base + cell) * 2 + st
+        if mi[m, O.MI_VALID]:
+            return mh[m].reshape(3, 3)
+    return None
+
+
+def test_fullsize_plane_sweep_fixed_point(torch, pair):
+    """At every plane level, sampled unassigned pixels of the colour swept last: the stored cost is the
+    oracle's cost of the stored offset with the pixel's plane-distorted patch, and no candidate its last
+    half-step proposed is better -- the 4-neighbours' offsets (unchanged after it) and the offsets induced by
+    every valid model of the windows covering the pixel."""
+    gp = _params()
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, pair.frame1, pair.frame2)
+    cb = O.cell_base(P)
+    ctx = gpm.Context(gp, W, H)
+    ctx.match([_dev(torch, pair)])
+    rng = np.random.default_rng(3)
+    n_checked = 0
+    for L in range(1, len(CELLS) + 1):
+        ctx.fit_planes(L)
+        ctx.match(None, L)
+        nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
+        gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+        am = ctx.export(gpm.LABELS)[0]
+        s = CELLS[L - 1]
+        xs, ys = O.grid_axis(W, s), O.grid_axis(H, s)
+        base = int(cb[L - 1])
+        for d in range(2):
+            src, tgt = frames[d]
+            pix = np.flatnonzero((am[d] < 0) & (((np.arange(W * H) % W) + (np.arange(W * H) // W)) % 2 == 1))
+            for i in rng.choice(pix, min(150, len(pix)), replace=False):
+                x, y = int(i % W), int(i // W)
+                G = _home_plane(x, y, xs, ys, s, base, gmh[d], gmi[d])
+                vx, vy = int(nnf[d, i, 0]), int(nnf[d, i, 1])
+                c = O.patch_cost(P, src, tgt, x, y, vx, vy, G)
+                assert rel_close(cost[d][i], c, rel=2e-5, atol=1e-6), (L, d, x, y, cost[d][i], c)
+                cands = []
+                for nx, ny in ((x - 1, y), (x + 1, y), (x, y - 1), (x, y + 1)):
+                    if 0 <= nx < W and 0 <= ny < H:
+                        cands.append(tuple(int(v) for v in nnf[d, ny * W + nx]))
+                for a_ in [k for k in range(len(ys)) if ys[k] <= y < ys[k] + s]:
+                    for b_ in [k for k in range(len(xs)) if xs[k] <= x < xs[k] + s]:
+                        for st in (0, 1):
+                            m = (base + a_ * len(xs) + b_) * 2 + st
+                            if not gmi[d][m, O.MI_VALID]:
+                                continue
+                            h = gmh[d][m]
+                            w = h[6] * x + h[7] * y + h[8]
+                            if not w > 0:
+                                continue
+                            fx, fy = (h[0] * x + h[1] * y + h[2]) / w - x, (h[3] * x + h[4] * y + h[5]) / w - y
+                            # within a near tie of a rounding boundary (relative 1e-5, as the oracle logs them)
+                            if any(min(t - np.floor(t), np.ceil(t) - t) < 1e-5 * max(1.0, abs(t))
+                                   for t in (fx + 0.5, fy + 0.5)):
+                                continue
+                            cands.append((int(np.floor(fx + 0.5)), int(np.floor(fy + 0.5))))
+                for cx, cy in cands:
+                    if not (0 <= x + cx < W and 0 <= y + cy < H) or (cx, cy) == (vx, vy):
+                        continue
+                    cc = O.patch_cost(P, src, tgt, x, y, cx, cy, G)
+                    assert cost[d][i] <= cc * (1 + 2e-5) + 1e-6, (L, d, x, y, (vx, vy), cost[d][i], (cx, cy), cc)
+                n_checked += 1
+    ctx.close()
+    assert n_checked > 800, n_checked
 
 
 def test_fullsize_ransac_every_window_every_level(torch, pair):
