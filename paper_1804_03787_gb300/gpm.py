@@ -157,6 +157,7 @@ class Context:
             raise GpmError(st, f"gpm_create failed: {self.lib.gpm_status_string(st).decode()}")
         self.h = h
         self._pairs = None
+        self._n = 0
 
     # ------------------------------------------------------------ stages
     def _check(self, st: int, what: str):

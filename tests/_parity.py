@@ -83,3 +83,48 @@ def ransac_equal(gmh, gmi, omh, omi, ids):
         elif b[O.MI_FLAGS] & O.F_FITTED and np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() > 1e-6:
             ok[k] = False
     return ok
+
+
+def final_map_check(ctx, P, frames, flow_t, occ_t, samples, seed):
+    """Properties of a final flow and occlusion map (Sec. 3.4.1) on sampled pixels of direction 0: a pixel with a
+    plane carries that model's mapping of it (to 1e-3 px) and is occluded iff its many-to-one cue is set, its
+    target leaves the frame, or its colour error at the target reaches the threshold; a pixel without a plane keeps
+    its NNF offset and is occluded.  Samples within 1e-5 of the threshold or 1e-3 px of the border are skipped.
+    Returns (pixels with a plane, pixels whose occlusion bit was checked)."""
+    W, H = P.width, P.height
+    flow = flow_t.cpu().numpy().reshape(-1, 2)
+    occ = occ_t.cpu().numpy().reshape(-1)
+    from paper_1804_03787_gb300 import gpm
+    m = ctx.export(gpm.LABELS)[0][0]
+    mh = ctx.export(gpm.MODELS)[0]
+    cue = ctx.export(gpm.CUES)[0]
+    nnf = ctx.export(gpm.NNF)[0]
+    src, tgt = frames[0]
+    thr = P.occ_thresh
+    rng = np.random.default_rng(seed)
+    n_plane = n_checked = 0
+    for i in rng.choice(W * H, min(samples, W * H), replace=False):
+        x, y = int(i % W), int(i // W)
+        if m[i] < 0:
+            assert flow[i, 0] == nnf[i, 0] and flow[i, 1] == nnf[i, 1] and occ[i] == 1, (x, y)
+            continue
+        n_plane += 1
+        h = mh[m[i]]
+        w = h[6] * x + h[7] * y + h[8]
+        X, Y = (h[0] * x + h[1] * y + h[2]) / w, (h[3] * x + h[4] * y + h[5]) / w
+        assert abs(flow[i, 0] - (X - x)) < 1e-3 and abs(flow[i, 1] - (Y - y)) < 1e-3, (x, y, flow[i], X - x, Y - y)
+        if cue[i] & O.CUE_M2O:
+            assert occ[i] == 1
+            continue
+        Xg, Yg = x + float(flow[i, 0]), y + float(flow[i, 1])
+        if min(abs(Xg), abs(Xg - (W - 1)), abs(Yg), abs(Yg - (H - 1))) < 1e-3:
+            continue
+        if not (0 <= Xg <= W - 1 and 0 <= Yg <= H - 1):
+            assert occ[i] == 1, (x, y)
+            continue
+        delta = float(np.abs(src[y, x] - O.sample_bilinear(tgt, Xg, Yg)).mean())
+        if abs(delta - thr) < 1e-5:
+            continue
+        assert occ[i] == (1 if delta >= thr else 0), (x, y, delta, thr, occ[i])
+        n_checked += 1
+    return n_plane, n_checked

@@ -1,0 +1,122 @@
+"""GPU edge cases: degenerate inputs, the smallest and a large frame, and calls the library must refuse.
+
+Constant frames make every patch cost exactly zero, so every decision is exact on both sides: the GPU result
+must equal the oracle's bit for bit (PatchMatch keeps the random initial field on ties, no window finds a
+plane, every pixel is occluded).  Identical frames are the zero-motion case.  A frame of exactly the largest
+window's size has one window per axis at that level; a ragged size just above it gets a border-flush window.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1804_03787_gb300 import gpm, scene
+
+from _parity import final_map_check, oracle_frames, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    assert t.cuda.is_available(), "GPU tests need a CUDA device"
+    gpm.load()
+    return t
+
+
+def _dev(torch, f1, f2):
+    return torch.from_numpy(np.ascontiguousarray(f1, np.float32)).cuda(), \
+        torch.from_numpy(np.ascontiguousarray(f2, np.float32)).cuda()
+
+
+def _both(torch, gp, f1, f2):
+    H, W = f1.shape[:2]
+    ctx = gpm.Context(gp, W, H)
+    flows, occs = ctx.run([_dev(torch, f1, f2)])
+    torch.cuda.synchronize()
+    g = (flows[0].cpu().numpy(), occs[0].cpu().numpy())
+    R = O.run(oracle_params(gp, W, H), f1, f2)
+    o = (R.flow[0].reshape(H, W, 2), R.occ[0].reshape(H, W))
+    return ctx, g, o
+
+
+def test_constant_frames_exactly_equal_oracle(torch):
+    f = np.full((48, 64, 3), 0.4, np.float32)
+    gp = gpm.default_params(patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=64)
+    ctx, (gf, go), (of, oo) = _both(torch, gp, f, f.copy())
+    np.testing.assert_array_equal(gf, of)
+    np.testing.assert_array_equal(go, oo)
+    assert (go == 1).all()  # no plane anywhere: every pixel keeps its (random) NNF offset, occluded
+    P = oracle_params(gp, 64, 48)
+    frames, _ = oracle_frames(P, f, f)
+    vx, vy, _ = O.pm_init(P, frames[0][0], frames[0][1], 0)
+    np.testing.assert_array_equal(gf[..., 0].reshape(-1), vx)
+    np.testing.assert_array_equal(gf[..., 1].reshape(-1), vy)
+    ctx.close()
+
+
+def test_identical_frames_zero_motion(torch):
+    s = scene.tiny_scene(4)
+    gp = gpm.default_params()
+    ctx, (gf, go), (of, oo) = _both(torch, gp, s.frame1, s.frame1.copy())
+    agree = np.mean(np.hypot(*(gf - of).transpose(2, 0, 1)) < 1e-4)
+    assert agree > 0.95, agree
+    # the zero field is the answer: nearly every pixel gets a plane within 0.05 px of it (the least-squares refit
+    # also takes NNF offsets within the RANSAC threshold, so a plane need not be the exact identity), and nearly
+    # none is occluded
+    assert np.mean(np.hypot(*gf.transpose(2, 0, 1)) < 0.05) > 0.97
+    assert go.mean() < 0.03
+    ctx.close()
+
+
+@pytest.mark.parametrize("W,H", [(32, 32), (33, 35)])
+def test_smallest_frames_end_to_end(torch, W, H):
+    """Frames of the largest window's size (one window per axis at level 1) and a ragged size just above."""
+    s = scene.make_scene(W, H, seed=W + H, n_layers=1, max_disp=3.0, affine=True)
+    gp = gpm.default_params()
+    ctx, (gf, go), (of, oo) = _both(torch, gp, s.frame1, s.frame2)
+    agree = np.mean(np.hypot(*(gf - of).transpose(2, 0, 1)) < 1e-4)
+    assert agree > 0.95, agree
+    assert np.mean(go == oo) > 0.95
+    ctx.close()
+
+
+def test_full_hd_frame_final_map(torch):
+    """A 1920x1080 pair (the largest serving size) in the benchmark configuration: the final map's properties on
+    sampled pixels."""
+    s = scene.make_scene(1920, 1080, seed=7, n_layers=6, max_disp=64.0, affine=False, area_frac=(0.02, 0.08))
+    gp = gpm.default_params(patch_radius=4, cells=(64, 32, 16, 8), pm_iters=8, num_hyp=512)
+    P = oracle_params(gp, 1920, 1080)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    ctx = gpm.Context(gp, 1920, 1080)
+    flows, occs = ctx.run([_dev(torch, s.frame1, s.frame2)])
+    torch.cuda.synchronize()
+    n_plane, n_checked = final_map_check(ctx, P, frames, flows[0], occs[0], samples=3000, seed=5)
+    assert n_plane > 2000 and n_checked > 1500, (n_plane, n_checked)
+    e = np.hypot(*(flows[0].cpu().numpy() - s.flow).transpose(2, 0, 1))
+    assert e[s.occ == 0].mean() < 3.0
+    ctx.close()
+
+
+def test_invalid_calls_are_refused(torch):
+    gp = gpm.default_params()
+    ctx = gpm.Context(gp, 64, 48)
+    # stage order: planes before any matching, matching a level before fitting it
+    with pytest.raises(gpm.GpmError):
+        ctx.fit_planes(1)
+    s = scene.make_scene(64, 48, seed=1, n_layers=1, max_disp=3.0, affine=True)
+    ctx.match([_dev(torch, s.frame1, s.frame2)])
+    with pytest.raises(gpm.GpmError):
+        ctx.match(None, 1)
+    with pytest.raises(gpm.GpmError):
+        ctx.fit_planes(2)
+    # frames smaller than the largest window, or larger than the context's limits
+    with pytest.raises(gpm.GpmError):
+        ctx.match([_dev(torch, np.zeros((20, 64, 3)), np.zeros((20, 64, 3)))])
+    with pytest.raises(gpm.GpmError):
+        ctx.match([_dev(torch, np.zeros((48, 80, 3)), np.zeros((48, 80, 3)))])
+    # the context stays usable after refused calls
+    flows, occs = ctx.run([_dev(torch, s.frame1, s.frame2)])
+    torch.cuda.synchronize()
+    assert np.isfinite(flows[0].cpu().numpy()).all()
+    ctx.close()

@@ -16,7 +16,7 @@ import pytest
 import oracle as O
 from paper_1804_03787_gb300 import gpm, scene
 
-from _parity import TIE, dilate, oracle_frames, oracle_params, ransac_equal, rel_close
+from _parity import TIE, dilate, final_map_check, oracle_frames, oracle_params, ransac_equal, rel_close
 
 pytestmark = pytest.mark.gpu
 
@@ -245,50 +245,13 @@ def test_fullsize_ransac_every_window_every_level(torch, pair):
 
 
 def test_fullsize_final_map_properties(torch, pair):
-    """The final flow and occlusion map of the whole method, on sampled pixels: a pixel with a plane carries
-    that model's mapping of it (to 1e-3 px) and is occluded iff its many-to-one cue is set, its target leaves
-    the frame, or its colour error at the target reaches the threshold; a pixel without a plane keeps its NNF
-    offset and is occluded.  Samples within 1e-5 of the threshold or 1e-3 px of the border are skipped."""
+    """The final flow and occlusion map of the whole method, on sampled pixels (final_map_check)."""
     gp = _params()
     P = oracle_params(gp, W, H)
     frames, _ = oracle_frames(P, pair.frame1, pair.frame2)
     ctx = gpm.Context(gp, W, H)
     flows, occs = ctx.run([_dev(torch, pair)])
     torch.cuda.synchronize()
-    flow = flows[0].cpu().numpy().reshape(-1, 2)
-    occ = occs[0].cpu().numpy().reshape(-1)
-    m = ctx.export(gpm.LABELS)[0][0]
-    mh = ctx.export(gpm.MODELS)[0]
-    cue = ctx.export(gpm.CUES)[0]
-    nnf = ctx.export(gpm.NNF)[0]
+    n_plane, n_checked = final_map_check(ctx, P, frames, flows[0], occs[0], samples=4000, seed=2)
     ctx.close()
-    src, tgt = frames[0]
-    thr = P.occ_thresh
-    rng = np.random.default_rng(2)
-    n_plane = n_checked = 0
-    for i in rng.choice(W * H, 4000, replace=False):
-        x, y = int(i % W), int(i // W)
-        if m[i] < 0:
-            assert flow[i, 0] == nnf[i, 0] and flow[i, 1] == nnf[i, 1] and occ[i] == 1, (x, y)
-            continue
-        n_plane += 1
-        h = mh[m[i]]
-        w = h[6] * x + h[7] * y + h[8]
-        X, Y = (h[0] * x + h[1] * y + h[2]) / w, (h[3] * x + h[4] * y + h[5]) / w
-        assert abs(flow[i, 0] - (X - x)) < 1e-3 and abs(flow[i, 1] - (Y - y)) < 1e-3, (x, y, flow[i], X - x, Y - y)
-        if cue[i] & O.CUE_M2O:
-            assert occ[i] == 1
-            continue
-        Xg, Yg = x + float(flow[i, 0]), y + float(flow[i, 1])
-        edge = min(abs(Xg), abs(Xg - (W - 1)), abs(Yg), abs(Yg - (H - 1)))
-        if edge < 1e-3:
-            continue
-        if not (0 <= Xg <= W - 1 and 0 <= Yg <= H - 1):
-            assert occ[i] == 1, (x, y)
-            continue
-        delta = float(np.abs(src[y, x] - O.sample_bilinear(tgt, Xg, Yg)).mean())
-        if abs(delta - thr) < 1e-5:
-            continue
-        assert occ[i] == (1 if delta >= thr else 0), (x, y, delta, thr, occ[i])
-        n_checked += 1
     assert n_plane > 3000 and n_checked > 2500, (n_plane, n_checked)
