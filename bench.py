@@ -149,8 +149,8 @@ def fp32_peak_tops(sm_mhz: float, nsm: int) -> float:
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the kernel class, from the
 # captures summarised in profiles/ (null where the kernel changed since, or no capture matches the class).
 TRAFFIC_PER_LAUNCH = {
-    "pm_sweep": (25016320 + 45568, "profiles/pm_sweep_level0_1024x436.md"),
-    "pm_sweep_plane": (17856768 + 284928, "profiles/pm_sweep_plane_level1_1024x436.md"),
+    "pm_sweep": (25024256 + 49152, "profiles/pm_sweep_level0_1024x436.md"),
+    "pm_sweep_plane": (17855744 + 8960, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
 # written (8 + 8 B) and one RGBX texel of each frame (16 + 16 B).
@@ -247,8 +247,9 @@ def extras_start(workers: int):
 
 
 def batched_block(scenes):
-    """64 pairs of mixed sizes: the plain FP32 form (one stream, eager launches) against the batched form (BF16
-    storage, FP32 accumulation, autotuned streams, CUDA graphs), with EPE against ground truth for both."""
+    """64 pairs of mixed sizes: the plain FP32 form (one stream, eager launches) against the batched forms
+    (autotuned streams, CUDA graphs) with FP32 storage and with BF16 storage (FP32 accumulation), with EPE
+    against ground truth for each."""
     import numpy as np
     import torch
 
@@ -265,6 +266,15 @@ def batched_block(scenes):
     plain.close()
     del plain
     torch.cuda.empty_cache()
+    # batched with FP32 storage: the plain form's arithmetic, so its accuracy is the plain form's
+    best32, tune32 = batch.autotune_streams(gp32, frames, ids, candidates=(2, 4, 8))
+    rf = batch.BatchRunner(gp32, frames, ids, streams=best32, graph=True)
+    rf.run()
+    t32b = rf.time(2)
+    rf32 = rf.results()
+    rf.close()
+    del rf
+    torch.cuda.empty_cache()
     gpb = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=gpm.GPM_BF16)
     best, tune = batch.autotune_streams(gpb, frames, ids, candidates=(2, 4, 8))
     r = batch.BatchRunner(gpb, frames, ids, streams=best, graph=True)
@@ -278,6 +288,9 @@ def batched_block(scenes):
     nocc = [scenes[w].occ == 0 for w in which]
     e32 = float(np.mean([batch.epe(r32[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
     eb = float(np.mean([batch.epe(rb[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
+    ef = float(np.mean([batch.epe(rf32[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
+    same = all(np.array_equal(rf32[i][0], r32[i][0]) and np.array_equal(rf32[i][1], r32[i][1])
+               for i in range(BATCH_PAIRS))
     sizes = sorted({(s.frame1.shape[1], s.frame1.shape[0]) for s in scenes})
     return {"value": BATCH_PAIRS / t, "unit": "pairs/s", "pairs": BATCH_PAIRS,
             "workload": f"{BATCH_PAIRS} pairs from {len(scenes)} seeded scenes, sizes uniform over "
@@ -287,6 +300,10 @@ def batched_block(scenes):
             "autotune_ms_per_pass": {str(k): v * 1e3 for k, v in tune.items()},
             "plain_f32": {"value": BATCH_PAIRS / t_plain, "unit": "pairs/s", "streams": 1, "cuda_graph": False},
             "speedup_vs_plain_f32": t_plain / t,
+            "batched_f32": {"value": BATCH_PAIRS / t32b, "unit": "pairs/s", "streams": best32, "cuda_graph": True,
+                            "speedup_vs_plain_f32": t_plain / t32b, "epe_nocc_px": ef, "abs_diff": abs(ef - e32),
+                            "bitwise_equal_to_plain": same,
+                            "autotune_ms_per_pass": {str(k): v * 1e3 for k, v in tune32.items()}},
             "epe_nocc_px": {"plain_f32": e32, "batched_bf16": eb, "abs_diff": abs(eb - e32),
                             "pixels": "ground-truth non-occluded, mean over the pairs"},
             "l2": "inputs of one pass (> 1 GB of frames and state) exceed L2"}
