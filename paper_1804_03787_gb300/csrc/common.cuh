@@ -245,6 +245,45 @@ __device__ __forceinline__ bool mef_inlier(const Mef& m, float ux, float uy, flo
     return den > 0.f && nx * nx + ny * ny < t2 * den * den;
 }
 
+// mef_inlier for two matches at once on the packed FP32x2 pipe: each
+// coefficient of the evaluation form in both halves of a float2, and the
+// same operations as mef_inlier in each half (one rounding each, as there).
+struct Mef2 {
+    float2 b0, h1, h2h, h2l, h3, b4, h5h, h5l, g0, g1, e0;
+};
+__device__ __forceinline__ Mef2 mef2_of(const Mef& m) {
+    Mef2 r;
+    r.b0 = make_float2(m.b0, m.b0);
+    r.h1 = make_float2(m.h1, m.h1);
+    r.h2h = make_float2(m.h2h, m.h2h);
+    r.h2l = make_float2(m.h2l, m.h2l);
+    r.h3 = make_float2(m.h3, m.h3);
+    r.b4 = make_float2(m.b4, m.b4);
+    r.h5h = make_float2(m.h5h, m.h5h);
+    r.h5l = make_float2(m.h5l, m.h5l);
+    r.g0 = make_float2(m.g0, m.g0);
+    r.g1 = make_float2(m.g1, m.g1);
+    r.e0 = make_float2(m.e0, m.e0);
+    return r;
+}
+__device__ __forceinline__ void mef_inlier2(const Mef2& m, const float4& a, const float4& b, float t2, bool& ia,
+                                            bool& ib) {
+    const float2 ux = make_float2(a.x, b.x), uy = make_float2(a.y, b.y);
+    const float2 vx = make_float2(a.z, b.z), vy = make_float2(a.w, b.w);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 e = __ffma2_rn(m.g1, uy, __ffma2_rn(m.g0, ux, m.e0));
+    const float2 den = __fadd2_rn(make_float2(1.f, 1.f), e);
+    const float2 ne = __fmul2_rn(e, m1);
+    const float2 sx = __ffma2_rn(ux, ne, __ffma2_rn(m.h1, uy, __fmul2_rn(m.b0, ux)));
+    const float2 sy = __ffma2_rn(uy, ne, __ffma2_rn(m.b4, uy, __fmul2_rn(m.h3, ux)));
+    const float2 nx = __ffma2_rn(vx, ne, __fadd2_rn(__fadd2_rn(__ffma2_rn(vx, m1, m.h2h), m.h2l), sx));
+    const float2 ny = __ffma2_rn(vy, ne, __fadd2_rn(__fadd2_rn(__ffma2_rn(vy, m1, m.h5h), m.h5l), sy));
+    const float2 n2 = __ffma2_rn(nx, nx, __fmul2_rn(ny, ny));
+    const float2 rhs = __fmul2_rn(__fmul2_rn(make_float2(t2, t2), den), den);
+    ia = den.x > 0.f && n2.x < rhs.x;
+    ib = den.y > 0.f && n2.y < rhs.y;
+}
+
 // Local homography (double, rows, maps u -> local target) to the evaluation
 // form.  Orientation and scale: denominator +1 at the window centre
 // (-0.5, -0.5).  Returns false if that denominator is zero.

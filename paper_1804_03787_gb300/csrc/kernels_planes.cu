@@ -502,16 +502,27 @@ __device__ int gather_matches(const G& grp, const PairView& pv, const LevelGeom&
     return N;
 }
 
-// |(a, b)| for exact integers: in FP32 from exact inputs when both are below
-// 2^24 (one rounding of the sum of squares and one of the root), else in FP64.
-__device__ __forceinline__ double scaled_dist(long long a, long long b) {
-    if (a > -16777216ll && a < 16777216ll && b > -16777216ll && b < 16777216ll) {
-        const float fa = (float)(int)a, fb = (float)(int)b;
-        return (double)sqrtf(fmaf(fa, fa, fb * fb));
+// Sum of |(a, b)| over a lane's points, for exact integers a, b: FP32 roots
+// of exact inputs (|a|, |b| < 2^24; one rounding of the sum of squares and
+// one of the root) added with Kahan compensation (a couple of units of
+// rounding in total, whatever the count), larger inputs in FP64.
+struct DistSum {
+    float s = 0.f, c = 0.f;
+    double big = 0.0;
+    __device__ __forceinline__ void add(int a, int b) {
+        if (a > -16777216 && a < 16777216 && b > -16777216 && b < 16777216) {
+            const float fa = (float)a, fb = (float)b;
+            const float y = sqrtf(fmaf(fa, fa, fb * fb)) - c;
+            const float t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            const double da = (double)a, db = (double)b;
+            big += sqrt(da * da + db * db);
+        }
     }
-    const double da = (double)a, db = (double)b;
-    return sqrt(da * da + db * db);
-}
+    __device__ __forceinline__ double total() const { return ((double)s - (double)c) + big; }
+};
 
 template <class G, int ST>
 __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
@@ -592,21 +603,20 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
         while (todo) {
             const int l = __ffs(todo) - 1;
             todo &= todo - 1;
-            const Mef m = hb[l];
+            const Mef2 m2 = mef2_of(hb[l]);
             // abandon when reach < group best or reach <= this warp's best
             const int bound = max(NW > 1 ? *(volatile int*)gbest - 1 : -1, best_score);
             int score = 0;
             bool alive = true;
             for (int c = 0; c < N; c += 128) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 4; u += 2) {  // matches j and j + 32 of this lane, tested as a pair
                     const int j = c + 32 * u + lane;
-                    bool in = false;
-                    if (j < N) {
-                        const float4 mt = match[j];
-                        in = mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
-                    }
-                    score += __popc(__ballot_sync(FULL, in));
+                    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 ma = j < N ? match[j] : z, mb = j + 32 < N ? match[j + 32] : z;
+                    bool ia, ib;
+                    mef_inlier2(m2, ma, mb, t2, ia, ib);
+                    score += __popc(__ballot_sync(FULL, ia && j < N)) + __popc(__ballot_sync(FULL, ib && j + 32 < N));
                 }
                 tests += min(128, N - c);
                 if (score + max(N - c - 128, 0) <= bound) {
@@ -684,16 +694,16 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     // Hartley scales: distances to the exact centroids, as n |p - mean| = |n p - sum| from exact integers
     // (the least-squares refit of a noisy support moves with its normalisation, so the scale must carry no
     // more than float rounding)
-    const long long nw = wscore;
-    double ds = 0, dt = 0;
+    const int nw = wscore;  // n |coordinate| < 2^31 for frames up to 32767 px and windows up to 96 px
+    DistSum dsum, dtsum;
     long long R[24];
 #pragma unroll
     for (int q = 0; q < 24; ++q) R[q] = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
         if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
-        ds += scaled_dist(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
-        dt += scaled_dist(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
+        dsum.add(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
+        dtsum.add(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
         const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
         const int U = exact_int(mt.x + mt.z) - cu, V = exact_int(mt.y + mt.w) - cv;
         const int zz[6] = {X * X, X * Y, X, Y * Y, Y, 1};
@@ -706,8 +716,8 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             R[18 + q] += (long long)w3 * zz[q];
         }
     }
-    ds = grp.sum(ds) / (double)nw;  // sums of |p - mean|
-    dt = grp.sum(dt) / (double)nw;
+    const double ds = grp.sum(dsum.total()) / (double)nw;  // sums of |p - mean|
+    const double dt = grp.sum(dtsum.total()) / (double)nw;
 #pragma unroll
     for (int q = 0; q < 24; ++q) {
         const long long t = grp.sum(R[q]);
