@@ -5,8 +5,9 @@
 // before the launch (its four neighbours all have the other colour).  One
 // warp evaluates one pixel: each lane owns ceil(T/32) taps of the (2r+1)^2
 // patch, keeps their source texels in registers for all candidates, and the
-// per-candidate cost is a butterfly shuffle sum, identical on every lane, so
-// the accept/reject decision is warp-uniform.  At levels >= 1 the patch is
+// per-candidate cost is one integer reduction of the lanes' sums (rounded to
+// 2^-24), identical on every lane, so the accept/reject decision is
+// warp-uniform.  At levels >= 1 the patch is
 // distorted by the pixel's home-window plane (Sec. 3.3.2 with the plane
 // distortion compensation of Sec. 3.1.3): tap d samples the target frame at
 // p + v + G(s) - G(p), s = clamp(p + d).
@@ -365,6 +366,18 @@ __device__ __forceinline__ bool interior_of(const LanePatch<R>& lp, int2 c) {
 // Raw patch cost of offset (vx, vy): the sum over taps and channels of
 // |difference|.  The NNF cost buffer holds these sums (strict-less decisions
 // compare them directly); the exported cost is the sum divided by 3T.
+// The warp's total of the lanes' tap sums: each lane's sum rounded to a
+// multiple of 2^-24 and the integers added exactly by one redux, so every
+// lane gets the same bits.  A lane's sum is below 9 (three taps of three
+// channels in [0, 1]), so the total stays below 2^32; it is within
+// 32 * 2^-25 of the exact total of the lane sums, about the rounding of a
+// float butterfly, and costs one reduction instead of five dependent
+// shuffles and additions.
+__device__ __forceinline__ float warp_sum_q24(float s) {
+    const unsigned q = __float2uint_rn(s * 16777216.f);
+    return (float)__reduce_add_sync(FULL, q) * 5.9604644775390625e-08f;
+}
+
 template <int R, int ST, bool IN>
 __device__ __forceinline__ float patch_sum_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int lane) {
     const int off = c.y * W + c.x;
@@ -374,10 +387,7 @@ __device__ __forceinline__ float patch_sum_in(const LanePatch<R>& lp, const void
         const int t = lane + 32 * j;
         if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST, IN>(lp, tgt, W, H, j, c, off));
     }
-    // butterfly sum: every lane ends with the same bits (IEEE addition commutes)
-#pragma unroll
-    for (int off2 = 16; off2 > 0; off2 >>= 1) s += __shfl_xor_sync(FULL, s, off2);
-    return s;
+    return warp_sum_q24(s);
 }
 template <int R, int ST>
 __device__ __forceinline__ float patch_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
@@ -424,11 +434,12 @@ __device__ __forceinline__ bool census_sum(const LanePatch<R>& lp, const uint32_
 }
 
 // Integer threshold for the abandon test of tap_sum: with thr the best raw
-// sum so far, returns ceil(thr * 2^19 * (1 + 2^-21)).  The extra 2^-21 covers
-// the five rounded additions of the warp's final float sum (each loses at
-// most 2^-24).
+// sum so far, returns ceil(thr * 2^19 * (1 + 2^-21)) + 1.  A partial bound at
+// or above it means the exact total of the lane sums is at least
+// thr (1 + 2^-21) + 2^-19; the final sum (warp_sum_q24) is within 2^-20 of
+// that total and then rounded to a float, so it stays above thr.
 __device__ __forceinline__ int abandon_threshold(float thr) {
-    return __float2int_ru(__fmul_ru(thr * 524288.f, 1.f + 4.76837158203125e-07f));
+    return __float2int_ru(__fmul_ru(thr * 524288.f, 1.f + 4.76837158203125e-07f)) + 1;
 }
 
 // Raw tap sum of candidate offset c (over taps and channels of |difference|,
@@ -436,12 +447,12 @@ __device__ __forceinline__ int abandon_threshold(float thr) {
 // 32-tap chunk every lane floors its partial sum to a multiple of 2^-19 and
 // the warp adds those integers exactly (one redux): a lower bound of the
 // exact partial sum.  The terms are non-negative and FP32 addition is
-// monotonic, so the final float sum is at least the exact partial sum less
-// the rounding of five additions; a bound at or above `ithr`
-// (abandon_threshold) therefore means the full cost is at or above the best,
-// and the strict-less test would reject the candidate anyway: the function
-// returns false.  Each lane accumulates its taps in the same order as
-// patch_sum, so a full sum is bitwise the same as patch_sum's.
+// monotonic, so a lane's final sum is at least its partial sum; a bound at
+// or above `ithr` (abandon_threshold) therefore means the full cost is above
+// the best, and the strict-less test would reject the candidate anyway: the
+// function returns false.  Each lane accumulates its taps in the same order
+// as patch_sum and the total is warp_sum_q24's, so a full sum is bitwise the
+// same as patch_sum's.
 template <int R, int ST, bool IN, bool EVERY_CHUNK>
 __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int lane) {
@@ -458,12 +469,7 @@ __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* t
                 (unsigned)(__float_as_int(__fadd_rz(fminf(s * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
             if ((int)__reduce_add_sync(FULL, q) >= ithr) return false;
         }
-        if (j + 1 == Patch<R>::NT) {
-            float p = s;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
-            sum = p;
-        }
+        if (j + 1 == Patch<R>::NT) sum = warp_sum_q24(s);
     }
     return true;
 }
@@ -509,18 +515,8 @@ __device__ __forceinline__ void tap_sum2_in(const LanePatch<R>& lp, const void* 
             if (!ok1 && !ok2) return;
         }
     }
-    if (ok1) {
-        float p = s1;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
-        sum1 = p;
-    }
-    if (ok2) {
-        float p = s2;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(FULL, p, o);
-        sum2 = p;
-    }
+    if (ok1) sum1 = warp_sum_q24(s1);
+    if (ok2) sum2 = warp_sum_q24(s2);
 }
 template <int R, int ST, bool EVERY_CHUNK>
 __device__ __forceinline__ void tap_sum2(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c1, int2 c2,
