@@ -158,15 +158,22 @@ TRAFFIC_PER_LAUNCH = {
 PM_BYTES_PER_VISIT = 48
 
 
-def roofline_block(prof, evals, nsm, clocks, peaks, steps):
-    """Roofline of the kernel class with the largest share of device time."""
+def roofline_block(prof, evals, nsm, clocks, peaks, steps, timed=None):
+    """Roofline of the kernel class with the largest share of device time (shares and evaluation counts from the
+    profiled replay `prof`, `evals`; the kernel's launch times from the timed region, `timed`, when measured)."""
     total = sum(ms for ms, _ in prof.values()) or 1.0
     top = max(prof, key=lambda k: prof[k][0])
-    ms, launches = prof[top]
+    ms, launches = (timed or {}).get(top, (0.0, 0))
+    src = "CUDA events on the context's stream around each launch, over the timed region"
+    if not launches:
+        ms, launches = prof[top]
+        src = "CUDA events on the context's stream around each launch, over a profiled replay of the timed steps"
+    share = prof[top][0] / total
     T = (2 * RADIUS + 1) ** 2
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak_ops = fp32_peak_tops(mhz, nsm)
-    block = {"kernel": top, "share": ms / total, "launches": launches, "avg_launch_ms": ms / max(launches, 1)}
+    block = {"kernel": top, "share": share, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
+             "avg_launch_source": src}
     if top in ("pm_sweep", "pm_init", "pm_recost"):
         # square-patch evaluation: per tap 3 channels x (subtract, |.| accumulate) = 6 FP32 operations
         ops = evals[0] * T * 6
@@ -586,7 +593,9 @@ def run_ours(args):
     gpu_id = getattr(props, "uuid", None)
     gpu_id = f"GPU-{gpu_id}" if gpu_id is not None and not str(gpu_id).startswith("GPU-") else str(gpu_id or local)
     clk = Clocks(gpu_id)
-    ctx.profile_enable(True)
+    # the timed steps bracket only the level-0 sweeps with events (the roofline's kernel) and count nothing;
+    # the per-class breakdown and the evaluation counts come from an untimed replay of the same steps
+    ctx.profile_select(["pm_sweep"], count_evals=False)
     ctx.profile_read()
     launches0 = ctx.launch_count()
     clk.start()
@@ -604,6 +613,11 @@ def run_ours(args):
         times.append(e0.elapsed_time(e1))
     clocks = clk.stop()
     launches = ctx.launch_count() - launches0
+    prof_timed, _ = ctx.profile_read()
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    for k in range(args.steps):
+        step(args.warmup + k)
     prof, evals = ctx.profile_read()
     ctx.profile_enable(False)
     total_ms = max_over_ranks(sum(times), dist, "cuda")
@@ -661,7 +675,7 @@ def run_ours(args):
     h2d = P * 2 * W * H * 3 * 4
     d2h = P * (W * H * 2 * 4 + W * H)
 
-    roof = roofline_block(prof, evals, nsm, clocks, peaks, args.steps)
+    roof = roofline_block(prof, evals, nsm, clocks, peaks, args.steps, timed=prof_timed)
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -671,6 +685,7 @@ def run_ours(args):
             "evals_per_step": (evals[0] + evals[1]) / args.steps,
             "ransac_tests_per_step": evals[2] / args.steps,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "kernel_ms_source": "every launch bracketed by CUDA events in an untimed replay of the timed steps",
             "roofline": roof,
             "e2e": {"value": job_throughput(args.steps * P, ws, e2e_ms), "unit": "pairs/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

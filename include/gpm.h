@@ -231,6 +231,12 @@ enum {
     GPM_PROF_CLASSES = 13
 };
 gpm_status gpm_profile_enable(gpm_ctx* ctx, int32_t enable);
+/* Finer control: bracket only the launches of the kernel classes whose bit
+   (1 << GPM_PROF_*) is set in class_mask, and count evaluations only if
+   count_evals != 0 (the counters add atomics and reductions to the kernels).
+   gpm_profile_enable(ctx, e) is gpm_profile_select(ctx, e ? all : 0, e).
+   GPM_EINVAL for a bit beyond the last class. */
+gpm_status gpm_profile_select(gpm_ctx* ctx, uint32_t class_mask, int32_t count_evals);
 gpm_status gpm_profile_read(gpm_ctx* ctx, double* ms, uint64_t* launches, uint64_t* evals);
 
 /* ---- ingest without allocation ----

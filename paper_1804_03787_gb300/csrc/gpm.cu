@@ -59,7 +59,8 @@ struct gpm_ctx {
         int cls;
         cudaEvent_t a, b;
     };
-    bool prof = false;
+    uint32_t prof_mask = 0;  // kernel classes whose launches are bracketed by events
+    bool prof_open = false;  // the last pbeg opened a bracket
     std::vector<ProfRec> recs;
     std::vector<cudaEvent_t> pool;
     uint64_t prof_launches[GPM_PROF_CLASSES] = {};
@@ -80,19 +81,21 @@ cudaEvent_t take_event(gpm_ctx* c) {
     return e;
 }
 
-// Counts `n` kernel launches of class `cls` and, with profiling on, opens an
-// event bracket on the context's stream (closed by pend).
+// Counts `n` kernel launches of class `cls` and, with profiling on for that
+// class, opens an event bracket on the context's stream (closed by pend).
 void pbeg(gpm_ctx* c, int cls, int n) {
     c->launches += n;
-    if (!c->prof) return;
+    c->prof_open = (c->prof_mask >> cls) & 1u;
+    if (!c->prof_open) return;
     c->prof_launches[cls] += n;
     gpm_ctx::ProfRec r{cls, take_event(c), take_event(c)};
     cudaEventRecord(r.a, c->stream);
     c->recs.push_back(r);
 }
 void pend(gpm_ctx* c) {
-    if (!c->prof) return;
+    if (!c->prof_open) return;
     cudaEventRecord(c->recs.back().b, c->stream);
+    c->prof_open = false;
 }
 
 gpm_status fail(gpm_ctx* c, gpm_status s, const std::string& msg) {
@@ -723,14 +726,19 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
     return cuda_check(c, "gpm_import");
 }
 
-gpm_status gpm_profile_enable(gpm_ctx* c, int32_t enable) {
+gpm_status gpm_profile_select(gpm_ctx* c, uint32_t class_mask, int32_t count_evals) {
     if (!c) return GPM_EINVAL;
-    c->prof = enable != 0;
+    if (class_mask >> GPM_PROF_CLASSES) return fail(c, GPM_EINVAL, "class_mask names no kernel class");
+    c->prof_mask = class_mask;
     for (auto& s : c->slots) {
-        s.pv.evals = c->prof ? s.d_evals : nullptr;
-        if (c->prof) cudaMemsetAsync(s.d_evals, 0, 3 * sizeof(unsigned long long), c->stream);
+        s.pv.evals = count_evals ? s.d_evals : nullptr;
+        if (count_evals) cudaMemsetAsync(s.d_evals, 0, 3 * sizeof(unsigned long long), c->stream);
     }
-    return cuda_check(c, "gpm_profile_enable");
+    return cuda_check(c, "gpm_profile_select");
+}
+
+gpm_status gpm_profile_enable(gpm_ctx* c, int32_t enable) {
+    return gpm_profile_select(c, enable ? (1u << GPM_PROF_CLASSES) - 1u : 0u, enable);
 }
 
 gpm_status gpm_profile_read(gpm_ctx* c, double* ms, uint64_t* launches, uint64_t* evals) {

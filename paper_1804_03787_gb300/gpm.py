@@ -24,7 +24,7 @@ GPM_F32, GPM_F16, GPM_BF16 = 0, 1, 2
 EXPORTED = ["gpm_default_params", "gpm_create", "gpm_destroy", "gpm_required_bytes", "gpm_match",
             "gpm_fit_planes", "gpm_flow_and_occlusion", "gpm_sync", "gpm_state_bytes", "gpm_export",
             "gpm_import", "gpm_status_string", "gpm_last_error", "gpm_launch_count", "gpm_profile_enable",
-            "gpm_profile_read", "gpm_ingest_noalloc"]
+            "gpm_profile_select", "gpm_profile_read", "gpm_ingest_noalloc"]
 PROF_CLASSES = ["ingest", "pm_init", "pm_sweep", "pm_sweep_plane", "pm_recost", "ransac", "assign", "cues",
                 "many_to_one", "merge", "lists", "fill", "final"]
 
@@ -94,6 +94,7 @@ def load(build: bool = True) -> C.CDLL:
         "gpm_last_error": (C.c_char_p, [C.c_void_p]),
         "gpm_launch_count": (C.c_uint64, [C.c_void_p]),
         "gpm_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+        "gpm_profile_select": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int32]),
         "gpm_profile_read": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_uint64), P(C.c_uint64)]),
         "gpm_ingest_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32,
                                          C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -213,6 +214,13 @@ class Context:
 
     def profile_enable(self, on: bool = True):
         self._check(self.lib.gpm_profile_enable(self.h, 1 if on else 0), "gpm_profile_enable")
+
+    def profile_select(self, classes, count_evals: bool = False):
+        """Brackets only the launches of the named kernel classes (names of PROF_CLASSES) with events."""
+        mask = 0
+        for name in classes:
+            mask |= 1 << PROF_CLASSES.index(name)
+        self._check(self.lib.gpm_profile_select(self.h, mask, 1 if count_evals else 0), "gpm_profile_select")
 
     def profile_read(self):
         """{class: (ms, launches)}, (PM evals at level 0, at levels >= 1, RANSAC residual tests); clears them."""

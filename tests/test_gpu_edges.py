@@ -120,3 +120,26 @@ def test_invalid_calls_are_refused(torch):
     torch.cuda.synchronize()
     assert np.isfinite(flows[0].cpu().numpy()).all()
     ctx.close()
+
+
+def test_profile_select_brackets_only_the_chosen_classes(torch):
+    """gpm_profile_select: only the chosen kernel classes are timed, evaluations are counted only on request, and
+    a bit beyond the last class is refused."""
+    s = scene.tiny_scene(1)
+    ctx = gpm.Context(gpm.default_params(), 128, 96)
+    ctx.profile_select(["pm_sweep"], count_evals=False)
+    ctx.profile_read()
+    ctx.run([_dev(torch, s.frame1, s.frame2)])
+    prof, evals = ctx.profile_read()
+    assert prof["pm_sweep"][0] > 0 and prof["pm_sweep"][1] > 0
+    assert all(ms == 0 and n == 0 for k, (ms, n) in prof.items() if k != "pm_sweep")
+    assert evals == (0, 0, 0)
+    ctx.profile_enable(True)
+    ctx.profile_read()
+    ctx.run([_dev(torch, s.frame1, s.frame2)])
+    prof, evals = ctx.profile_read()
+    assert all(prof[k][1] > 0 for k in ("pm_sweep", "pm_sweep_plane", "ransac", "assign", "final"))
+    assert evals[0] > 0 and evals[1] > 0 and evals[2] > 0
+    with pytest.raises(gpm.GpmError):
+        ctx._check(ctx.lib.gpm_profile_select(ctx.h, 1 << len(gpm.PROF_CLASSES), 0), "gpm_profile_select")
+    ctx.close()
