@@ -11,6 +11,11 @@
 namespace gpm {
 
 constexpr int kMaxCell = 96;  // largest window side (its matches fill 144 KiB of shared memory in RANSAC)
+// Border of the padded frame copies read by the level-0 PatchMatch: the
+// largest patch radius.  Every tap of a candidate whose target pixel is in
+// the frame then lies inside the padded copy, whose border replicates the
+// edge texels, so a tap reads what clamping its coordinates would read.
+constexpr int kPad = 4;
 constexpr int kMI = 12;  // integer fields per model (layout of GPM_MODEL_INFO)
 // A warped sample point counts as inside the frame up to this far (px)
 // beyond the border: clamped bilinear sampling is continuous there, and
@@ -379,6 +384,8 @@ struct PairView {
     int m_models;         // models per direction (bound of every model id)
     uint32_t pair_id;
     const void* img[2];   // ingested I1, I2 (RGBX in storage type)
+    const void* imgp[2];  // the same, (W + 2 kPad) x (H + 2 kPad) with replicated borders (level-0 PatchMatch)
+    int Wp;               // row length of imgp
     int2* nnf[2];
     float* cost[2];
     uint8_t* frozen[2];

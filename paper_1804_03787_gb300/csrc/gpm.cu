@@ -50,6 +50,7 @@ struct gpm_ctx {
     cudaStream_t stream = nullptr;
     int nsm = 152;
     int max_n = 0, max_models = 0, max_cells = 1;
+    int max_np = 0;  // texels of a padded frame copy at the largest frame size
     size_t slot_bytes = 0;
     std::vector<Slot> slots;
     std::string err;
@@ -165,7 +166,7 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
 }
 
 // Carves one slot's buffers out of a single block; returns bytes needed.
-size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells, char* base, Slot* s) {
+size_t layout_slot(const gpm_params& P, int max_n, int max_np, int max_models, int max_cells, char* base, Slot* s) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> void* {
         off = (off + kAlign - 1) / kAlign * kAlign;
@@ -177,6 +178,7 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_models, int max_cells
     const size_t texel = P.storage == 0 ? 16 : 8;
     PairView pv{};
     for (int d = 0; d < 2; ++d) pv.img[d] = take(n * texel);
+    for (int d = 0; d < 2; ++d) pv.imgp[d] = take((size_t)max_np * texel);
     for (int d = 0; d < 2; ++d) {
         pv.nnf[d] = (int2*)take(n * sizeof(int2));
         pv.cost[d] = (float*)take(n * sizeof(float));
@@ -261,6 +263,7 @@ gpm_status set_dims(gpm_ctx* c, Slot& s, int W, int H) {
     s.pv.W = W;
     s.pv.H = H;
     s.pv.n = s.n;
+    s.pv.Wp = W + 2 * kPad;
     s.pv.m_models = s.m;
     launch_set_geoms(s.geoms, s.d_geoms, c->stream);
     // a defined NNF (zero offsets) before anything reads it
@@ -384,7 +387,8 @@ size_t gpm_required_bytes(const gpm_params* params, const gpm_limits* limits) {
     const int max_n = limits->max_width * limits->max_height;
     const int max_models = 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr);
     const int max_cells = max_level_cells_for(*params, limits->max_width, limits->max_height);
-    const size_t per = layout_slot(*params, max_n, std::max(max_models, 2), max_cells, nullptr, nullptr);
+    const int max_np = (limits->max_width + 2 * kPad) * (limits->max_height + 2 * kPad);
+    const size_t per = layout_slot(*params, max_n, max_np, std::max(max_models, 2), max_cells, nullptr, nullptr);
     return per * (size_t)limits->max_pairs;
 }
 
@@ -418,7 +422,8 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
     c->max_n = limits->max_width * limits->max_height;
     c->max_models = std::max(2, 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr));
     c->max_cells = max_level_cells_for(*params, limits->max_width, limits->max_height);
-    c->slot_bytes = layout_slot(*params, c->max_n, c->max_models, c->max_cells, nullptr, nullptr);
+    c->max_np = (limits->max_width + 2 * kPad) * (limits->max_height + 2 * kPad);
+    c->slot_bytes = layout_slot(*params, c->max_n, c->max_np, c->max_models, c->max_cells, nullptr, nullptr);
     if (limits->hbm_budget_bytes && c->slot_bytes * (size_t)limits->max_pairs > limits->hbm_budget_bytes) {
         delete c;
         return GPM_EBUSY;
@@ -437,7 +442,7 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
             return GPM_ENOMEM;
         }
         s.block = p;
-        layout_slot(*params, c->max_n, c->max_models, c->max_cells, (char*)p, &s);
+        layout_slot(*params, c->max_n, c->max_np, c->max_models, c->max_cells, (char*)p, &s);
     }
     *out = c;
     return GPM_OK;
@@ -500,11 +505,12 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
                 launch_grey_q(p.frame1, p.width, p.height, p.row_stride, s.pv.gq, c->stream);
                 pend(c);
             }
-            pbeg(c, GPM_PROF_INGEST, c->P.equalize ? 6 : 4);
+            pbeg(c, GPM_PROF_INGEST, c->P.equalize ? 7 : 5);
             launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
                           s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
                           const_cast<void*>(s.pv.img[1]), c->P.equalize ? s.eq_hist : nullptr,
                           c->P.equalize ? s.eq_lut : nullptr, c->stream);
+            launch_pad_frames(s.pv, c->P.storage, grid_for(c, s.pv.Wp * (s.H + 2 * kPad)), c->stream);
             reset_models(c, s);
             launch_reset_labels(s.pv, c->P.eps, grid_for(c, s.n), c->stream);
             pend(c);

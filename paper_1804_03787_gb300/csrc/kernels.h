@@ -21,6 +21,8 @@ void launch_pm(const PmLaunch& L, cudaStream_t st);
 void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
                    double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
                    cudaStream_t st);
+// Padded copies of both ingested frames (imgp), borders replicating the edges.
+void launch_pad_frames(const PairView& pv, int storage, int grid_blocks, cudaStream_t st);
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
 // Census codes of both input frames (k1, k2: n int64 of scratch each).
 void launch_census(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1, long long* k2,

@@ -263,9 +263,12 @@ __device__ __forceinline__ void set_interior_box(LanePatch<R>& lp, int xlo, int 
 }
 
 // CENSUS: src holds the frame's census codes (uint32 per pixel) instead of texels.
+// Wp > 0: the target is read from a padded copy (row length Wp, border
+// kPad): tidx then indexes the clamped tap there, and a candidate whose target
+// pixel is in the frame needs no clamping for any tap.
 template <int R, int ST, bool CENSUS = false>
 __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, int W, int H, int px, int py,
-                                           int lane) {
+                                           int lane, int Wp = 0) {
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
@@ -273,11 +276,12 @@ __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, in
         const int dy = tt / Patch<R>::D - R, dx = tt % Patch<R>::D - R;
         lp.tx[j] = min(max(px + dx, 0), W - 1);
         lp.ty[j] = min(max(py + dy, 0), H - 1);
-        lp.tidx[j] = lp.ty[j] * W + lp.tx[j];
+        const int si = lp.ty[j] * W + lp.tx[j];
+        lp.tidx[j] = Wp > 0 ? (lp.ty[j] + kPad) * Wp + lp.tx[j] + kPad : si;
         if (CENSUS)
-            lp.code[j] = __ldg(reinterpret_cast<const uint32_t*>(src) + lp.tidx[j]);
+            lp.code[j] = __ldg(reinterpret_cast<const uint32_t*>(src) + si);
         else
-            lp.a[j] = ldpix<ST>(src, lp.tidx[j]);
+            lp.a[j] = ldpix<ST>(src, si);
         lp.fx[j] = 0.f;
         lp.fy[j] = 0.f;
     }
@@ -570,14 +574,15 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
         const uint4 w = philox((uint32_t)i, 0u, stream_tag(RNG_INIT, dir, 0, 0), pv.pair_id, k0, k1);
         const int vx = (int)(w.x % (uint32_t)W) - x, vy = (int)(w.y % (uint32_t)H) - y;
         LanePatch<R> lp;
-        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
         float c;
         if constexpr (CENSUS) {
+            load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
             int sum = 0;
             census_sum<R>(lp, reinterpret_cast<const uint32_t*>(tgt), W, H, make_int2(vx, vy), -1, sum, lane);
             c = (float)sum;
         } else {
-            c = patch_sum<R, ST>(lp, tgt, W, H, x, y, vx, vy, lane);
+            load_patch<R, ST>(lp, src, W, H, x, y, lane, pv.Wp);
+            c = patch_sum_in<R, ST, true>(lp, pv.imgp[1 - dir], pv.Wp, H, make_int2(vx, vy), lane);
         }
         if (lane == 0) {
             pv.nnf[dir][i] = make_int2(vx, vy);
@@ -604,13 +609,21 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
             const int i = list[w];
             const int y = i / W, x = i - y * W;
             LanePatch<R> lp;
-            load_patch<R, ST>(lp, src, W, H, x, y, lane);
-            if (level > 0) {
-                const Mef* G = home_plane(g, pv.mef[dir], x, y);
-                if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
-            }
             const int2 v = pv.nnf[dir][i];
-            const float c = patch_sum<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
+            float c;
+            // the padded copy serves square patches whose target pixel is in the frame (an imported offset
+            // need not be)
+            if (level > 0 || (unsigned)(x + v.x) >= (unsigned)W || (unsigned)(y + v.y) >= (unsigned)H) {
+                load_patch<R, ST>(lp, src, W, H, x, y, lane);
+                if (level > 0) {
+                    const Mef* G = home_plane(g, pv.mef[dir], x, y);
+                    if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
+                }
+                c = patch_sum<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
+            } else {
+                load_patch<R, ST>(lp, src, W, H, x, y, lane, pv.Wp);
+                c = patch_sum_in<R, ST, true>(lp, pv.imgp[1 - dir], pv.Wp, H, v, lane);
+            }
             if (lane == 0) {
                 pv.cost[dir][i] = c;
                 if (pv.evals) atomicAdd(&pv.evals[level > 0], 1ull);
@@ -640,6 +653,10 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
     const int W = pv.W, H = pv.H;
     const void* src = CENSUS ? (const void*)pv.code[dir] : pv.img[dir];
     const void* tgt = CENSUS ? (const void*)pv.code[1 - dir] : pv.img[1 - dir];
+    // square colour patches read the target from its padded copy: no clamping and no interior test per candidate
+    constexpr bool PADDED = !PLANES && !CENSUS;
+    const void* tgtp = PADDED ? pv.imgp[1 - dir] : tgt;
+    const int Wt = PADDED ? pv.Wp : pv.W;
     int2* __restrict__ nnf = pv.nnf[dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int hw = (W + 1) >> 1;
@@ -672,7 +689,7 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
             x = i - y * W;
         }
         LanePatch<R> lp;
-        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
+        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane, PADDED ? Wt : 0);
         if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
@@ -750,7 +767,7 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                         const int2 c2 = make_int2(__shfl_sync(FULL, cand.x, l2), __shfl_sync(FULL, cand.y, l2));
                         float s1 = 0.f, s2 = 0.f;
                         bool ok1, ok2;
-                        tap_sum2<R, ST, false>(lp, tgt, W, H, c, c2, ithr, s1, s2, ok1, ok2, lane);
+                        tap_sum2_in<R, ST, true, false>(lp, tgtp, Wt, H, c, c2, ithr, s1, s2, ok1, ok2, lane);
                         if (ok1 && s1 < bc) {
                             bc = s1;
                             best = c;
@@ -773,7 +790,9 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                     }
                 } else {
                     float sum;
-                    if (tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, lane) && sum < bc) {
+                    const bool done = PADDED ? tap_sum_in<R, ST, true, false>(lp, tgtp, Wt, H, c, ithr, sum, lane)
+                                             : tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, lane);
+                    if (done && sum < bc) {
                         bc = sum;
                         best = c;
                         ithr = abandon_threshold(bc);
@@ -891,6 +910,28 @@ void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride,
         case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
         case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
     }
+}
+
+// Padded copy of each ingested frame: texel (x, y) of the copy, for x in
+// [-kPad, W + kPad) and y in [-kPad, H + kPad), is the frame's texel at the
+// clamped coordinates (T: one texel, 16 or 8 bytes).
+template <typename T>
+__global__ void k_pad_frames(PairView pv) {
+    const int dir = blockIdx.y;
+    const T* src = reinterpret_cast<const T*>(pv.img[dir]);
+    T* dst = reinterpret_cast<T*>(const_cast<void*>(pv.imgp[dir]));
+    const int W = pv.W, H = pv.H, Wp = pv.Wp, np = Wp * (H + 2 * kPad);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const int yp = i / Wp, xp = i - yp * Wp;
+        const int x = min(max(xp - kPad, 0), W - 1), y = min(max(yp - kPad, 0), H - 1);
+        dst[i] = src[y * W + x];
+    }
+}
+void launch_pad_frames(const PairView& pv, int storage, int grid_blocks, cudaStream_t st) {
+    if (storage == 0)
+        k_pad_frames<uint4><<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+    else
+        k_pad_frames<uint2><<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
 }
 
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
