@@ -522,15 +522,6 @@ __device__ __forceinline__ void tap_sum2_in(const LanePatch<R>& lp, const void* 
     if (ok1) sum1 = warp_sum_q24(s1);
     if (ok2) sum2 = warp_sum_q24(s2);
 }
-template <int R, int ST, bool EVERY_CHUNK>
-__device__ __forceinline__ void tap_sum2(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c1, int2 c2,
-                                         int ithr, float& sum1, float& sum2, bool& ok1, bool& ok2, int lane) {
-    if (interior_of<R>(lp, c1) && interior_of<R>(lp, c2))
-        tap_sum2_in<R, ST, true, EVERY_CHUNK>(lp, tgt, W, H, c1, c2, ithr, sum1, sum2, ok1, ok2, lane);
-    else
-        tap_sum2_in<R, ST, false, EVERY_CHUNK>(lp, tgt, W, H, c1, c2, ithr, sum1, sum2, ok1, ok2, lane);
-}
-
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
 // Key of a candidate offset for duplicate detection; lanes without a
