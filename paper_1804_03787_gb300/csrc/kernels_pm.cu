@@ -263,9 +263,10 @@ __device__ __forceinline__ void set_interior_box(LanePatch<R>& lp, int xlo, int 
 }
 
 // CENSUS: src holds the frame's census codes (uint32 per pixel) instead of texels.
-// Wp > 0: the target is read from a padded copy (row length Wp, border
-// kPad): tidx then indexes the clamped tap there, and a candidate whose target
-// pixel is in the frame needs no clamping for any tap.
+// Wp > 0: src is a padded copy (row length Wp, border kPad) and the target
+// is read from the other frame's copy: tidx then indexes the clamped tap
+// there, and a candidate whose target pixel is in the frame needs no clamping
+// for any tap.
 template <int R, int ST, bool CENSUS = false>
 __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, int W, int H, int px, int py,
                                            int lane, int Wp = 0) {
@@ -281,7 +282,7 @@ __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, in
         if (CENSUS)
             lp.code[j] = __ldg(reinterpret_cast<const uint32_t*>(src) + si);
         else
-            lp.a[j] = ldpix<ST>(src, si);
+            lp.a[j] = ldpix<ST>(src, Wp > 0 ? lp.tidx[j] : si);
         lp.fx[j] = 0.f;
         lp.fy[j] = 0.f;
     }
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
             census_sum<R>(lp, reinterpret_cast<const uint32_t*>(tgt), W, H, make_int2(vx, vy), -1, sum, lane);
             c = (float)sum;
         } else {
-            load_patch<R, ST>(lp, src, W, H, x, y, lane, pv.Wp);
+            load_patch<R, ST>(lp, pv.imgp[dir], W, H, x, y, lane, pv.Wp);
             c = patch_sum_in<R, ST, true>(lp, pv.imgp[1 - dir], pv.Wp, H, make_int2(vx, vy), lane);
         }
         if (lane == 0) {
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
                 }
                 c = patch_sum<R, ST>(lp, tgt, W, H, x, y, v.x, v.y, lane);
             } else {
-                load_patch<R, ST>(lp, src, W, H, x, y, lane, pv.Wp);
+                load_patch<R, ST>(lp, pv.imgp[dir], W, H, x, y, lane, pv.Wp);
                 c = patch_sum_in<R, ST, true>(lp, pv.imgp[1 - dir], pv.Wp, H, v, lane);
             }
             if (lane == 0) {
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
             x = i - y * W;
         }
         LanePatch<R> lp;
-        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane, PADDED ? Wt : 0);
+        load_patch<R, ST, CENSUS>(lp, PADDED ? pv.imgp[dir] : src, W, H, x, y, lane, PADDED ? Wt : 0);
         if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
