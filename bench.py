@@ -18,6 +18,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -99,8 +100,7 @@ class Clocks:
               "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_id: str):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        self.path = os.path.join(tempfile.gettempdir(), f"gpm_clocks_{os.getpid()}.csv")
         self.proc = None
         self.gpu_id = gpu_id
 
@@ -150,7 +150,7 @@ def fp32_peak_tops(sm_mhz: float, nsm: int) -> float:
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the kernel class, from the
 # captures summarised in profiles/ (null where the kernel changed since, or no capture matches the class).
 TRAFFIC_PER_LAUNCH = {
-    "pm_sweep": (25442816 + 1536, "profiles/pm_sweep_level0_1024x436.md"),
+    "pm_sweep": (25392896 + 10752, "profiles/pm_sweep_level0_1024x436.md"),
     "pm_sweep_plane": (17855744 + 8960, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
