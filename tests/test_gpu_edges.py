@@ -81,14 +81,15 @@ def test_smallest_frames_end_to_end(torch, W, H):
     ctx.close()
 
 
-def test_full_hd_frame_final_map(torch):
-    """A 1920x1080 pair (the largest serving size) in the benchmark configuration: the final map's properties on
-    sampled pixels."""
-    s = scene.make_scene(1920, 1080, seed=7, n_layers=6, max_disp=64.0, affine=False, area_frac=(0.02, 0.08))
+@pytest.mark.parametrize("W,H", [(1920, 1080), (3840, 2160)])
+def test_large_frame_final_map(torch, W, H):
+    """1920x1080 (the largest serving size) and 3840x2160 pairs in the benchmark configuration: the final map's
+    properties on sampled pixels."""
+    s = scene.make_scene(W, H, seed=7, n_layers=6, max_disp=64.0, affine=False, area_frac=(0.02, 0.08))
     gp = gpm.default_params(patch_radius=4, cells=(64, 32, 16, 8), pm_iters=8, num_hyp=512)
-    P = oracle_params(gp, 1920, 1080)
+    P = oracle_params(gp, W, H)
     frames, _ = oracle_frames(P, s.frame1, s.frame2)
-    ctx = gpm.Context(gp, 1920, 1080)
+    ctx = gpm.Context(gp, W, H)
     flows, occs = ctx.run([_dev(torch, s.frame1, s.frame2)])
     torch.cuda.synchronize()
     n_plane, n_checked = final_map_check(ctx, P, frames, flows[0], occs[0], samples=3000, seed=5)
