@@ -266,7 +266,7 @@ __device__ __forceinline__ void set_interior_box(LanePatch<R>& lp, int xlo, int 
 // Wp > 0: src is a padded copy (row length Wp, border kPad) and the target
 // is read from the other frame's copy: tidx then indexes the clamped tap
 // there, and a candidate whose target pixel is in the frame needs no clamping
-// for any tap.
+// for any tap (the interior box, in unpadded terms, is then not consulted).
 template <int R, int ST, bool CENSUS = false>
 __device__ __forceinline__ void load_patch(LanePatch<R>& lp, const void* src, int W, int H, int px, int py,
                                            int lane, int Wp = 0) {
