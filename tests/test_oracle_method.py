@@ -320,3 +320,29 @@ def test_run_is_deterministic():
     for d in range(2):
         np.testing.assert_array_equal(a.flow[d], b.flow[d])
         np.testing.assert_array_equal(a.mi[d], b.mi[d])
+
+
+def test_fit_cells_equals_fit_level_on_its_windows():
+    """The per-window fit used by the full-size GPU checks is the whole-level fit restricted to the listed
+    windows, for both stages (stage 2 on a residual mask), and leaves every other model slot untouched."""
+    s = scene.make_scene(64, 48, seed=5, n_layers=2, max_disp=5.0, affine=True)
+    P = O.Params(64, 48, patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=64)
+    R = O.run(P, s.frame1, s.frame2, stop_after=0)
+    a = np.asarray(s.frame1, np.float64)
+    b = np.asarray(s.frame2, np.float64) * O.gain(P, a, s.frame2)
+    rng = np.random.default_rng(0)
+    resid = (rng.random(64 * 48) < 0.4).astype(np.uint8)
+    cb = O.cell_base(P)
+    for level in (1, 2):
+        count = int(cb[level] - cb[level - 1])
+        cells = sorted(rng.choice(count, 5, replace=False).tolist())
+        for stage, mask in ((1, None), (2, resid)):
+            mh, mi = O.empty_models(P)
+            O.fit_level(P, a, b, 0, level, stage, R.vx[0], R.vy[0], mask, mh, mi)
+            mh2, mi2 = O.empty_models(P)
+            O.fit_cells(P, a, b, 0, level, stage, R.vx[0], R.vy[0], mask, cells, mh2, mi2)
+            ids = (int(cb[level - 1]) + np.asarray(cells)) * 2 + stage - 1
+            np.testing.assert_array_equal(mh2[ids], mh[ids])
+            np.testing.assert_array_equal(mi2[ids], mi[ids])
+            others = np.setdiff1d(np.arange(len(mi2)), ids)
+            assert not mi2[others].any() and not mh2[others].any()
