@@ -553,6 +553,28 @@ __device__ __forceinline__ const Mef* home_plane(const LevelGeom& g, const Mef* 
 }
 
 // ---------------------------------------------------------------- init
+// The costs of two pixels' candidates at once (patches l1, l2, interior offsets
+// c1, c2 into the padded target copy of row length Wp): the same arithmetic per
+// pixel as patch_sum_in, with the two pixels' gathers in flight together.
+template <int R, int ST>
+__device__ __forceinline__ void patch_sum_pair_in(const LanePatch<R>& l1, const LanePatch<R>& l2, const void* tgt,
+                                                  int Wp, int H, int2 c1, int2 c2, float& sum1, float& sum2) {
+    const int o1 = c1.y * Wp + c1.x, o2 = c2.y * Wp + c2.x;
+    float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = (int)(threadIdx.x & 31) + 32 * j;
+        if (t < Patch<R>::T) {
+            const float3 v1 = tap_sample<R, ST, true>(l1, tgt, Wp, H, j, c1, o1);
+            const float3 v2 = tap_sample<R, ST, true>(l2, tgt, Wp, H, j, c2, o2);
+            s1 += absdiff3(l1.a[j], v1);
+            s2 += absdiff3(l2.a[j], v2);
+        }
+    }
+    sum1 = warp_sum_q24(s1);
+    sum2 = warp_sum_q24(s2);
+}
+
 template <int R, int ST, bool CENSUS>
 __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint32_t k1) {
     const int dir = blockIdx.y;
@@ -561,7 +583,33 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
     const void* src = CENSUS ? (const void*)pv.code[dir] : pv.img[dir];
     const void* tgt = CENSUS ? (const void*)pv.code[1 - dir] : pv.img[1 - dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+    const int first = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if constexpr (!CENSUS) {
+        // two pixels per warp and round (i and i + nw): their gathers share the latency
+        for (int i = first; i < n; i += 2 * nw) {
+            const int i2 = i + nw < n ? i + nw : i;  // warp-uniform; the last odd pixel is computed twice
+            const int y1 = i / W, x1 = i - y1 * W, y2 = i2 / W, x2 = i2 - y2 * W;
+            const uint32_t tag = stream_tag(RNG_INIT, dir, 0, 0);
+            const uint4 w1 = philox((uint32_t)i, 0u, tag, pv.pair_id, k0, k1);
+            const uint4 w2 = philox((uint32_t)i2, 0u, tag, pv.pair_id, k0, k1);
+            const int2 c1 = make_int2((int)(w1.x % (uint32_t)W) - x1, (int)(w1.y % (uint32_t)H) - y1);
+            const int2 c2 = make_int2((int)(w2.x % (uint32_t)W) - x2, (int)(w2.y % (uint32_t)H) - y2);
+            LanePatch<R> l1, l2;
+            load_patch<R, ST>(l1, pv.imgp[dir], W, H, x1, y1, lane, pv.Wp);
+            load_patch<R, ST>(l2, pv.imgp[dir], W, H, x2, y2, lane, pv.Wp);
+            float s1, s2;
+            patch_sum_pair_in<R, ST>(l1, l2, pv.imgp[1 - dir], pv.Wp, H, c1, c2, s1, s2);
+            if (lane == 0) {
+                pv.nnf[dir][i] = c1;
+                pv.cost[dir][i] = s1;
+                pv.nnf[dir][i2] = c2;
+                pv.cost[dir][i2] = s2;
+                if (pv.evals) atomicAdd(&pv.evals[0], i2 != i ? 2ull : 1ull);
+            }
+        }
+        return;
+    }
+    for (int i = first; i < n; i += nw) {
         const int y = i / W, x = i - y * W;
         const uint4 w = philox((uint32_t)i, 0u, stream_tag(RNG_INIT, dir, 0, 0), pv.pair_id, k0, k1);
         const int vx = (int)(w.x % (uint32_t)W) - x, vy = (int)(w.y % (uint32_t)H) - y;
