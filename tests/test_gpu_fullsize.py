@@ -6,6 +6,7 @@ At this size the oracle cannot run the whole method within a test, so the checks
     the last PatchMatch iteration of the whole frame, re-run by the oracle from the GPU's state before it;
   - every window: the stage-1 and stage-2 RANSAC + refit of every window at every level, re-run by the oracle on
     the GPU's own inputs (its NNF and its residual mask), equal up to the oracle's logged near ties;
+  - every pixel: the first-stage plane assignment at every level, re-run by the oracle on the GPU's own models;
   - properties that hold at any size: patch costs of sampled pixels and the fixed point of the last half-step
     (level 0 and every plane level, with plane-distorted patches), plane flows equal to their model's mapping,
     pixels without a plane keeping their NNF offset, and the occlusion rule of the final map (Sec. 3.4.1).
@@ -16,7 +17,7 @@ import pytest
 import oracle as O
 from paper_1804_03787_gb300 import gpm, scene
 
-from _parity import TIE, dilate, final_map_check, oracle_frames, oracle_params, ransac_equal, rel_close
+from _parity import COLOUR_ATOL, TIE, dilate, final_map_check, oracle_frames, oracle_params, ransac_equal, rel_close
 
 pytestmark = pytest.mark.gpu
 
@@ -202,6 +203,47 @@ def test_fullsize_plane_sweep_fixed_point(torch, pair):
                 n_checked += 1
     ctx.close()
     assert n_checked > 800, n_checked
+
+
+def test_fullsize_stage1_assignment_every_pixel(torch, pair):
+    """At every level and in both directions, the first-stage plane assignment of every pixel (eq. 3-4: colour
+    inlier test against eps, smallest robust loss, lowest window on ties) recomputed by the oracle from the GPU's
+    own exported models and validity bits equals the GPU's labels, except at the oracle's logged near ties; where
+    both chose the same plane, flows agree within 1e-5 px plus FP32 rounding of the flow's length and losses within
+    the colour tolerance."""
+    gp = _params()
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, pair.frame1, pair.frame2)
+    ctx = gpm.Context(gp, W, H)
+    ctx.match([_dev(torch, pair)])
+    n = W * H
+    n_assigned = n_diff = 0
+    for L in range(1, len(CELLS) + 1):
+        ctx.fit_planes(L)
+        gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+        gm, gL, gf = ctx.export(gpm.STAGE1_LABELS)
+        for d in range(2):
+            lab = O.Labels.empty(n, P.eps)
+            amb = np.zeros(n, np.uint8)
+            O.assign(P, frames[d][0], frames[d][1], L, 1, np.ascontiguousarray(gmh[d]), np.ascontiguousarray(gmi[d]),
+                     None, lab, amb)
+            diff = gm[d] != lab.m
+            bad = diff & (amb == 0)
+            assert not bad.any(), (L, d, int(bad.sum()), np.flatnonzero(bad)[:8].tolist())
+            same = ~diff & (lab.m >= 0)
+            flo = np.stack([lab.fx, lab.fy], 1)
+            # the FP32 evaluation form rounds terms of the flow's size: a few units of 2^-24 of |flow| on top of
+            # 1e-5 px (measured: median ~3e-8 px, worst 1.4e-7 |flow|, on a 158 px flow)
+            tol = 1e-5 + 4 * 2.0 ** -24 * np.hypot(flo[same, 0], flo[same, 1])
+            assert (np.abs(gf[d][same] - flo[same]).max(1) <= tol).all()
+            assert rel_close(gL[d][same], lab.L[same], atol=COLOUR_ATOL).all()
+            n_assigned += int((lab.m >= 0).sum())
+            n_diff += int(diff.sum())
+        ctx.match(None, L)
+    ctx.close()
+    # most pixels get a plane; labels differ (always at a logged near tie) on very few
+    assert n_assigned > 0.5 * 2 * n * len(CELLS) * 0.5, n_assigned
+    assert n_diff < 0.005 * 2 * n * len(CELLS), n_diff
 
 
 def test_fullsize_ransac_every_window_every_level(torch, pair):
