@@ -6,7 +6,8 @@ At this size the oracle cannot run the whole method within a test, so the checks
     the last PatchMatch iteration of the whole frame, re-run by the oracle from the GPU's state before it;
   - every window: the stage-1 and stage-2 RANSAC + refit of every window at every level, re-run by the oracle on
     the GPU's own inputs (its NNF and its residual mask), equal up to the oracle's logged near ties;
-  - every pixel: the first-stage plane assignment at every level, re-run by the oracle on the GPU's own models;
+  - every pixel: the first-stage plane assignment at every level, re-run by the oracle on the GPU's own models,
+    and the cross-level merge and NNF update, re-run on the GPU's labels;
   - properties that hold at any size: patch costs of sampled pixels and the fixed point of the last half-step
     (level 0 and every plane level, with plane-distorted patches), plane flows equal to their model's mapping,
     pixels without a plane keeping their NNF offset, and the occlusion rule of the final map (Sec. 3.4.1).
@@ -244,6 +245,50 @@ def test_fullsize_stage1_assignment_every_pixel(torch, pair):
     # most pixels get a plane; labels differ (always at a logged near tie) on very few
     assert n_assigned > 0.5 * 2 * n * len(CELLS) * 0.5, n_assigned
     assert n_diff < 0.005 * 2 * n * len(CELLS), n_diff
+
+
+def _labels(m, L, f):
+    return O.Labels(np.ascontiguousarray(m, np.int32), np.ascontiguousarray(L, np.float64),
+                    np.ascontiguousarray(f[:, 0], np.float64), np.ascontiguousarray(f[:, 1], np.float64))
+
+
+def test_fullsize_merge_and_nnf_update_every_level(torch, pair):
+    """At every level and in both directions, the cross-level merge (Sec. 3.3: a finer plane replaces the
+    accumulated one only if its loss is lower by more than beta) and the NNF update (Sec. 3.3.1: assigned pixels
+    take their rounded plane flow and are frozen), recomputed by the oracle from the GPU's accumulated labels
+    before the level and its level labels, equal the GPU's accumulated labels and NNF after the level, except at
+    the oracle's logged near ties."""
+    gp = _params()
+    P = oracle_params(gp, W, H)
+    ctx = gpm.Context(gp, W, H)
+    ctx.match([_dev(torch, pair)])
+    n = W * H
+    n_diff = 0
+    for L in range(1, len(CELLS) + 1):
+        am0, aL0, af0 = ctx.export(gpm.LABELS)
+        nnf0 = ctx.export(gpm.NNF)
+        ctx.fit_planes(L)
+        cm, cL, cf = ctx.export(gpm.LEVEL_LABELS)
+        am1, aL1, af1 = ctx.export(gpm.LABELS)
+        nnf1 = ctx.export(gpm.NNF)
+        for d in range(2):
+            acc = _labels(am0[d], aL0[d], af0[d])
+            amb = np.zeros(n, np.uint8)
+            O.merge(P, _labels(cm[d], cL[d], cf[d]), acc, amb)
+            vx, vy = nnf0[d, :, 0].copy(), nnf0[d, :, 1].copy()
+            frozen = np.zeros(n, np.uint8)
+            O.nnf_update(P, acc, vx, vy, frozen)
+            diff = am1[d] != acc.m
+            assert not (diff & (amb == 0)).any(), (L, d, int((diff & (amb == 0)).sum()))
+            same = ~diff
+            np.testing.assert_array_equal(nnf1[d, same, 0], vx[same])
+            np.testing.assert_array_equal(nnf1[d, same, 1], vy[same])
+            assert np.abs(af1[d][same & (acc.m >= 0)] - np.stack([acc.fx, acc.fy], 1)[same & (acc.m >= 0)]).max(
+                initial=0) < 1e-9
+            n_diff += int(diff.sum())
+        ctx.match(None, L)
+    ctx.close()
+    assert n_diff < 0.001 * 2 * n * len(CELLS), n_diff
 
 
 def test_fullsize_ransac_every_window_every_level(torch, pair):
