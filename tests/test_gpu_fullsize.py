@@ -7,7 +7,8 @@ At this size the oracle cannot run the whole method within a test, so the checks
   - every window: the stage-1 and stage-2 RANSAC + refit of every window at every level, re-run by the oracle on
     the GPU's own inputs (its NNF and its residual mask), equal up to the oracle's logged near ties;
   - every pixel: the first-stage plane assignment at every level, re-run by the oracle on the GPU's own models,
-    and the cross-level merge and NNF update, re-run on the GPU's labels;
+    the cross-level merge and NNF update, re-run on the GPU's labels, and the fill and final map, re-run on the
+    GPU's state before them;
   - properties that hold at any size: patch costs of sampled pixels and the fixed point of the last half-step
     (level 0 and every plane level, with plane-distorted patches), plane flows equal to their model's mapping,
     pixels without a plane keeping their NNF offset, and the occlusion rule of the final map (Sec. 3.4.1).
@@ -289,6 +290,42 @@ def test_fullsize_merge_and_nnf_update_every_level(torch, pair):
         ctx.match(None, L)
     ctx.close()
     assert n_diff < 0.001 * 2 * n * len(CELLS), n_diff
+
+
+def test_fullsize_fill_and_final_map(torch, pair):
+    """The model-propagation fill and the final flow and occlusion map (Sec. 3.4.1), recomputed by the oracle from
+    the GPU's state just before them (accumulated labels, models, cue bits, NNF): labels after the fill, flows and
+    occlusion bits equal the GPU's on all but a tiny fraction of pixels (the oracle logs no near ties here, so
+    the bound is on the fraction: decisions within rounding of the loss ties or of the occlusion threshold)."""
+    gp = _params()
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, pair.frame1, pair.frame2)
+    ctx = gpm.Context(gp, W, H)
+    ctx.match([_dev(torch, pair)])
+    for L in range(1, len(CELLS) + 1):
+        ctx.fit_planes(L)
+        ctx.match(None, L)
+    am0, aL0, af0 = ctx.export(gpm.LABELS)
+    gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+    cue, nnf = ctx.export(gpm.CUES), ctx.export(gpm.NNF)
+    flows, occs = ctx.flow_and_occlusion()
+    torch.cuda.synchronize()
+    am1 = ctx.export(gpm.LABELS)[0]
+    gflow = flows[0].cpu().numpy().reshape(-1, 2)
+    gocc = occs[0].cpu().numpy().reshape(-1)
+    ctx.close()
+    d = 0
+    acc = _labels(am0[d], aL0[d], af0[d])
+    O.fill(P, frames[d][0], frames[d][1], np.ascontiguousarray(gmh[d]), np.ascontiguousarray(gmi[d]),
+           np.ascontiguousarray(cue[d]), acc)
+    diff = am1[d] != acc.m
+    assert diff.mean() < 1e-4, int(diff.sum())
+    oflow, oocc = O.final(P, frames[d][0], frames[d][1], acc, nnf[d, :, 0].copy(), nnf[d, :, 1].copy(),
+                          np.ascontiguousarray(cue[d]))
+    fd = np.hypot(*(gflow - oflow).T)
+    tol = 1e-5 + 4 * 2.0 ** -24 * np.hypot(oflow[:, 0], oflow[:, 1])
+    assert np.mean(fd[~diff] > tol[~diff]) < 1e-4
+    assert np.mean(gocc != oocc) < 1e-3, int((gocc != oocc).sum())
 
 
 def test_fullsize_ransac_every_window_every_level(torch, pair):
