@@ -153,6 +153,12 @@ TRAFFIC_PER_LAUNCH = {
     "pm_sweep": (25392896 + 10752, "profiles/pm_sweep_level0_1024x436.md"),
     "pm_sweep_plane": (17855744 + 8960, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
+# Issue-slot utilisation of the kernel (ncu smsp__issue_active, one launch of the same workload): the sweeps are
+# bound by gather latency and issue, which the ALU fraction alone does not show.
+ISSUE_PER_LAUNCH = {
+    "pm_sweep": (0.5785, "profiles/pm_sweep_level0_1024x436.md"),
+    "pm_sweep_plane": (0.5836, "profiles/pm_sweep_plane_level1_1024x436.md"),
+}
 # Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
 # written (8 + 8 B) and one RGBX texel of each frame (16 + 16 B).
 PM_BYTES_PER_VISIT = 48
@@ -194,6 +200,10 @@ def roofline_block(prof, evals, nsm, clocks, peaks, steps, timed=None):
                       "units": "FP32 lane operations (14 per residual test; hypothesis solves not counted)"})
     else:
         block.update({"bound": "alu", "achieved": None, "peak": peak_ops, "unit": "TFLOP/s", "frac": None})
+    iss = ISSUE_PER_LAUNCH.get(top)
+    if iss:
+        block["issue_view"] = {"issue_slots_busy": iss[0], "source": iss[1],
+                               "note": "share of issue cycles used; the rest are stalls, mostly on L2 gathers"}
     tr = TRAFFIC_PER_LAUNCH.get(top)
     block["traffic"] = tr[0] if tr else None
     if tr:
