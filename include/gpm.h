@@ -181,6 +181,9 @@ gpm_status gpm_sync(gpm_ctx* ctx);
      GPM_STAGE1_LABELS same layout: this level's first-stage labels
      GPM_CUES       uint8  [2][n]      bit 0 = many-to-one occlusion cue
      GPM_FRAMES     float  [2][n][4]   ingested frames as FP32 RGBX (export only)
+     GPM_TENT_LABELS same layout as GPM_LABELS: this level's first-stage
+                    tentative labels, before the cues dropped any plane (the
+                    labels the symmetry cue counts; export only)
    Import accepts GPM_NNF, GPM_MODELS (+ valid bits from GPM_MODEL_INFO when
    imported right after), GPM_LABELS (also sets the frozen pixels: those with
    a plane) and GPM_CUES; it sets the stage order so that the next call may
@@ -194,7 +197,8 @@ enum {
     GPM_LEVEL_LABELS = 5,
     GPM_STAGE1_LABELS = 6,
     GPM_CUES = 7,
-    GPM_FRAMES = 8
+    GPM_FRAMES = 8,
+    GPM_TENT_LABELS = 9
 };
 /* Bytes of one export of `what` for pair `pair` (0 if unknown). */
 size_t gpm_state_bytes(const gpm_ctx* ctx, int32_t pair, int32_t what);

@@ -607,7 +607,8 @@ static size_t state_bytes(const Slot& s, int what) {
         case GPM_MODEL_INFO: return 2 * m * kMI * sizeof(int32_t);
         case GPM_LABELS:
         case GPM_LEVEL_LABELS:
-        case GPM_STAGE1_LABELS: {
+        case GPM_STAGE1_LABELS:
+        case GPM_TENT_LABELS: {
             size_t a = 2 * n * (sizeof(int32_t) + sizeof(float));
             a = (a + 7) / 8 * 8;
             return a + 2 * n * 2 * sizeof(double);
@@ -653,14 +654,18 @@ gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
             break;
         case GPM_LABELS:
         case GPM_LEVEL_LABELS:
-        case GPM_STAGE1_LABELS: {
+        case GPM_STAGE1_LABELS:
+        case GPM_TENT_LABELS: {
             int* om = (int*)d;
             float* oL = (float*)(d + 2 * n * sizeof(int));
             size_t a = 2 * n * (sizeof(int32_t) + sizeof(float));
             a = (a + 7) / 8 * 8;
             double* of = (double*)(d + a);
             for (int k = 0; k < 2; ++k) {
-                const Labels& l = what == GPM_LABELS ? s.pv.acc[k] : (what == GPM_LEVEL_LABELS ? s.pv.lvl[k] : s.pv.st1[k]);
+                const Labels& l = what == GPM_LABELS         ? s.pv.acc[k]
+                                  : what == GPM_LEVEL_LABELS   ? s.pv.lvl[k]
+                                  : what == GPM_STAGE1_LABELS ? s.pv.st1[k]
+                                                               : s.pv.tent[k];
                 launch_labels_export(l, s.n, om + k * n, oL + k * n, of + k * n * 2, st);
             }
             break;

@@ -18,7 +18,7 @@ MAX_SCALES = 8
 MI = 12
 (GPM_OK, GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT, GPM_EBUSY, GPM_EINTERNAL) = range(7)
 GPM_F32, GPM_F16, GPM_BF16 = 0, 1, 2
-(NNF, COST, MODELS, MODEL_INFO, LABELS, LEVEL_LABELS, STAGE1_LABELS, CUES, FRAMES) = range(9)
+(NNF, COST, MODELS, MODEL_INFO, LABELS, LEVEL_LABELS, STAGE1_LABELS, CUES, FRAMES, TENT_LABELS) = range(10)
 
 # every symbol the header declares (checked by the CPU test suite)
 EXPORTED = ["gpm_default_params", "gpm_create", "gpm_destroy", "gpm_required_bytes", "gpm_match",
@@ -252,7 +252,7 @@ class Context:
             return raw.view(np.float64).reshape(2, -1, 9)
         if what == MODEL_INFO:
             return raw.view(np.int32).reshape(2, -1, MI)
-        if what in (LABELS, LEVEL_LABELS, STAGE1_LABELS):
+        if what in (LABELS, LEVEL_LABELS, STAGE1_LABELS, TENT_LABELS):
             m = raw[: 2 * n * 4].view(np.int32).reshape(2, n)
             L = raw[2 * n * 4: 2 * n * 8].view(np.float32).reshape(2, n)
             a = (2 * n * 8 + 7) // 8 * 8

@@ -7,8 +7,9 @@ At this size the oracle cannot run the whole method within a test, so the checks
   - every window: the stage-1 and stage-2 RANSAC + refit of every window at every level, re-run by the oracle on
     the GPU's own inputs (its NNF and its residual mask), equal up to the oracle's logged near ties;
   - every pixel: the first-stage plane assignment at every level, re-run by the oracle on the GPU's own models,
-    the cross-level merge and NNF update, re-run on the GPU's labels, and the fill and final map, re-run on the
-    GPU's state before them;
+    the first-stage cue counts and invalidation of every model, re-run on the GPU's tentative labels, the
+    cross-level merge and NNF update, re-run on the GPU's labels, and the fill and final map, re-run on the GPU's
+    state before them;
   - properties that hold at any size: patch costs of sampled pixels and the fixed point of the last half-step
     (level 0 and every plane level, with plane-distorted patches), plane flows equal to their model's mapping,
     pixels without a plane keeping their NNF offset, and the occlusion rule of the final map (Sec. 3.4.1).
@@ -326,6 +327,50 @@ def test_fullsize_fill_and_final_map(torch, pair):
     tol = 1e-5 + 4 * 2.0 ** -24 * np.hypot(oflow[:, 0], oflow[:, 1])
     assert np.mean(fd[~diff] > tol[~diff]) < 1e-4
     assert np.mean(gocc != oocc) < 1e-3, int((gocc != oocc).sum())
+
+
+def test_fullsize_stage1_cues_every_model(torch, pair):
+    """At every level and in both directions, the first-stage occlusion cues (Sec. 3.4: symmetry counts of every
+    model from the tentative labels of both directions, then the eta and kappa invalidation), recomputed by the
+    oracle from the GPU's tentative labels and model records, equal the GPU's: counts exactly, except for models
+    holding a pixel with a logged near tie, and the validity and cue flags that follow from them."""
+    gp = _params()
+    P = oracle_params(gp, W, H)
+    cb = O.cell_base(P)
+    cue_flags = O.F_BAD_FB | O.F_BAD_KAPPA
+    ctx = gpm.Context(gp, W, H)
+    ctx.match([_dev(torch, pair)])
+    n = W * H
+    checked = excused = 0
+    for L in range(1, len(CELLS) + 1):
+        ctx.fit_planes(L)
+        tm, tL, tf = ctx.export(gpm.TENT_LABELS)
+        gmi = ctx.export(gpm.MODEL_INFO)
+        base, count = int(cb[L - 1]), int(cb[L] - cb[L - 1])
+        ids = (base + np.arange(count)) * 2  # stage-1 models of this level
+        for d in range(2):
+            mi = np.ascontiguousarray(gmi[d]).copy()
+            amb = np.zeros(n, np.uint8)
+            O.cue_counts(P, L, 1, _labels(tm[d], tL[d], tf[d]), _labels(tm[1 - d], tL[1 - d], tf[1 - d]), mi, amb)
+            near = np.zeros(len(mi), bool)
+            hit = tm[d][(amb > 0) & (tm[d] >= 0)]
+            near[hit] = True
+            same = (mi[ids, O.MI_NASSIGN] == gmi[d][ids, O.MI_NASSIGN]) & (mi[ids, O.MI_NSYM] == gmi[d][ids, O.MI_NSYM])
+            bad = ids[~same & ~near[ids]]
+            assert len(bad) == 0, (L, d, (bad[:8] // 2 - base).tolist())
+            # the invalidation, from each model's validity before the cues (valid, or dropped by a cue)
+            pre = mi.copy()
+            pre[ids, O.MI_VALID] = ((gmi[d][ids, O.MI_VALID] != 0) | ((gmi[d][ids, O.MI_FLAGS] & cue_flags) != 0))
+            pre[ids, O.MI_FLAGS] = gmi[d][ids, O.MI_FLAGS] & ~cue_flags
+            O.cue_invalidate(P, L, 1, pre)
+            k = ids[same]
+            np.testing.assert_array_equal(pre[k, O.MI_VALID], gmi[d][k, O.MI_VALID])
+            np.testing.assert_array_equal(pre[k, O.MI_FLAGS], gmi[d][k, O.MI_FLAGS])
+            checked += len(ids)
+            excused += int((~same).sum())
+        ctx.match(None, L)
+    ctx.close()
+    assert excused < 0.01 * checked, (excused, checked)
 
 
 def test_fullsize_ransac_every_window_every_level(torch, pair):
