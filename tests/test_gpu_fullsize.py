@@ -8,6 +8,7 @@ At this size the oracle cannot run the whole method within a test, so the checks
     the GPU's own inputs (its NNF and its residual mask), equal up to the oracle's logged near ties;
   - every pixel: the first-stage plane assignment at every level, re-run by the oracle on the GPU's own models,
     the first-stage cue counts and invalidation of every model, re-run on the GPU's tentative labels, the
+    second-stage assignment and the many-to-one cue, re-run on the GPU's first-stage labels, the
     cross-level merge and NNF update, re-run on the GPU's labels, and the fill and final map, re-run on the GPU's
     state before them;
   - properties that hold at any size: patch costs of sampled pixels and the fixed point of the last half-step
@@ -371,6 +372,50 @@ def test_fullsize_stage1_cues_every_model(torch, pair):
         ctx.match(None, L)
     ctx.close()
     assert excused < 0.01 * checked, (excused, checked)
+
+
+def test_fullsize_stage2_assignment_and_many_to_one(torch, pair):
+    """At every level and in both directions, the second-stage assignment of the residual pixels (starting from the
+    first-stage labels) and the many-to-one cue (Sec. 3.4: the lowest loss keeps a target pixel; a loser with a
+    clearly different flow is occluded and loses its plane), recomputed by the oracle from the GPU's first-stage
+    labels, residual mask, models and cue bits, equal the GPU's level labels and cue bits except at logged near
+    ties."""
+    gp = _params()
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, pair.frame1, pair.frame2)
+    ctx = gpm.Context(gp, W, H)
+    ctx.match([_dev(torch, pair)])
+    n = W * H
+    n_diff = 0
+    for L in range(1, len(CELLS) + 1):
+        cue0 = ctx.export(gpm.CUES)
+        ctx.fit_planes(L)
+        gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+        sm, sL, sf = ctx.export(gpm.STAGE1_LABELS)
+        lm, lL, lf = ctx.export(gpm.LEVEL_LABELS)
+        cue1 = ctx.export(gpm.CUES)
+        for d in range(2):
+            c = _labels(sm[d], sL[d], sf[d])
+            resid = np.ascontiguousarray(sm[d] < 0, np.uint8)
+            amb = np.zeros(n, np.uint8)
+            O.assign(P, frames[d][0], frames[d][1], L, 2, np.ascontiguousarray(gmh[d]), np.ascontiguousarray(gmi[d]),
+                     resid, c, amb)
+            # the target pixel each assigned pixel claims, before the many-to-one decision
+            pm = c.m.copy()
+            xs, ys = np.arange(n) % W, np.arange(n) // W
+            tq = np.where(pm >= 0, np.floor(ys + c.fy + 0.5) * W + np.floor(xs + c.fx + 0.5), -1).astype(np.int64)
+            cue = np.ascontiguousarray(cue0[d]).copy()
+            O.many_to_one(P, c, cue, amb)
+            # a many-to-one decision reads every claimant of a target: a near tie at one claimant may move the
+            # decision for all of them
+            tied = np.unique(tq[(amb > 0) & (tq >= 0)])
+            expl = (amb > 0) | np.isin(tq, tied)
+            diff = (lm[d] != c.m) | (cue1[d] != cue)
+            assert not (diff & ~expl).any(), (L, d, int((diff & ~expl).sum()))
+            n_diff += int(diff.sum())
+        ctx.match(None, L)
+    ctx.close()
+    assert n_diff < 0.002 * 2 * n * len(CELLS), n_diff
 
 
 def test_fullsize_ransac_every_window_every_level(torch, pair):
