@@ -221,7 +221,7 @@ def test_fullsize_stage1_assignment_every_pixel(torch, pair):
     ctx = gpm.Context(gp, W, H)
     ctx.match([_dev(torch, pair)])
     n = W * H
-    n_assigned = n_diff = 0
+    n_assigned = n_diff = n_amb = 0
     for L in range(1, len(CELLS) + 1):
         ctx.fit_planes(L)
         gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
@@ -243,11 +243,14 @@ def test_fullsize_stage1_assignment_every_pixel(torch, pair):
             assert rel_close(gL[d][same], lab.L[same], atol=COLOUR_ATOL).all()
             n_assigned += int((lab.m >= 0).sum())
             n_diff += int(diff.sum())
+            n_amb += int((amb > 0).sum())
         ctx.match(None, L)
     ctx.close()
-    # most pixels get a plane; labels differ (always at a logged near tie) on very few
+    # most pixels get a plane; labels differ (always at a logged near tie) on very few; the logged share is bounded
+    # (measured: 9 %, mostly ties between planes of one surface from overlapping windows)
     assert n_assigned > 0.5 * 2 * n * len(CELLS) * 0.5, n_assigned
     assert n_diff < 0.005 * 2 * n * len(CELLS), n_diff
+    assert n_amb < 0.15 * 2 * n * len(CELLS), n_amb
 
 
 def _labels(m, L, f):
@@ -454,8 +457,10 @@ def test_fullsize_ransac_every_window_every_level(torch, pair):
         ctx.match(None, L)
     ctx.close()
     print(f"windows checked {checked}, fits flagged as near ties {flagged}, differing (all flagged) {differ}")
-    # near ties explain few differences
+    # near ties explain few differences; the flagged share is bounded too, so that a band grown too wide cannot
+    # excuse the comparison wholesale (measured: 10 % of fits flagged, 0.2 % differing)
     assert differ <= checked // 100, (differ, checked)
+    assert flagged <= 0.15 * checked, (flagged, checked)
 
 
 def test_fullsize_final_map_properties(torch, pair):
