@@ -346,3 +346,62 @@ def test_fit_cells_equals_fit_level_on_its_windows():
             np.testing.assert_array_equal(mi2[ids], mi[ids])
             others = np.setdiff1d(np.arange(len(mi2)), ids)
             assert not mi2[others].any() and not mh2[others].any()
+
+
+def test_final_map_flow_source_and_occlusion_rule_on_hand_built_state():
+    """Sec. 3.4.1 and readings R20/R23: the flow is the plane's where a pixel has one, else its NNF offset; a pixel
+    is occluded without a plane, under the many-to-one cue, outside the frame (beyond 1e-3 px) or where the warp
+    error is not below the threshold. Dyadic colours make every warp error exact, so the threshold is hit exactly."""
+    W, H = 8, 2
+    P = O.Params(W, H, cells=(2,), occ_thresh=0.25)
+    rng = np.random.default_rng(3)
+    src = rng.integers(0, 5, (H, W, 3)) / 8.0
+    tgt = rng.integers(0, 5, (H, W, 3)) / 8.0
+    tgt[0, 2:] = src[0, :W - 2]                     # row 0 of the target: row 0 of the source moved 2 px right
+    tgt[0, 5] = src[0, 3] + 0.125                   # warp error of x=3 below the threshold
+    tgt[0, 6] = src[0, 4] + 0.25                    # warp error of x=4 exactly at it
+    src[0, 7] = (tgt[0, 6] + tgt[0, 7]) / 2         # x=7 lands half-way between target pixels 6 and 7
+    src[1, 0], src[1, 1] = tgt[0, 0], tgt[0, 1]     # row 1 pixels 0 and 1 map one row up
+    n = W * H
+    acc = O.Labels.empty(n, P.eps)
+    vx, vy = np.full(n, 2, np.int32), np.full(n, -3, np.int32)
+    cue = np.zeros(n, np.uint8)
+    for x, fx in ((0, 2.0), (2, 2.0), (3, 2.0), (4, 2.0), (5, 2.0), (6, 2.0), (7, -0.5)):
+        acc.m[x], acc.fx[x] = 3, fx
+    cue[2] = O.CUE_M2O
+    for x, fy in ((0, -1.0), (1, -1.0005), (2, -1.002)):
+        acc.m[W + x], acc.fy[W + x] = 5, fy
+    flow, occ = O.final(P, src, tgt, acc, vx, vy, cue)
+    exp_occ = [0, 1, 1, 0, 1, 0, 1, 0,             # row 0: no plane at 1, cue at 2, at threshold 4, outside 6
+               0, 0, 1, 1, 1, 1, 1, 1]             # row 1: 1 px beyond the top is inside the tolerance, 2e-3 is not
+    assert list(occ) == exp_occ
+    exp_fx = [2, 2, 2, 2, 2, 2, 2, -0.5] + [0, 0, 0, 2, 2, 2, 2, 2]
+    exp_fy = [0, -3, 0, 0, 0, 0, 0, 0] + [-1.0, -1.0005, -1.002, -3, -3, -3, -3, -3]
+    np.testing.assert_array_equal(flow[:, 0], np.float32(exp_fx))
+    np.testing.assert_array_equal(flow[:, 1], np.float32(exp_fy))
+
+
+def test_edge_aware_fill_evaluates_the_seed_plane_at_the_pixel():
+    """Reading R28: a pixel without a plane takes its seed's plane evaluated at its own position, or the seed's
+    flow where that plane's denominator is not positive; pixels with a plane or without a seed keep their flow.
+    The projective plane w = 1 - x/4 maps (x, y) to (x, y) / w, so its flows are known in closed form."""
+    W, H = 6, 2
+    P = O.Params(W, H, cells=(2,))
+    mh, _ = O.empty_models(P)
+    mh[0] = 3.0 * np.array([1, 0, 2, 0, 1, -1, 0, 0, 1.0])      # translation by (2, -1), homogeneous scale 3
+    mh[1] = np.array([1, 0, 0, 0, 1, 0, -0.25, 0, 1.0])
+    n = W * H
+    acc = O.Labels.empty(n, P.eps)
+    acc.m[0], acc.fx[0] = 0, 7.0
+    acc.m[W + 5], acc.fx[W + 5], acc.fy[W + 5] = 1, 9.5, -3.25
+    seed = np.full(n, -1, np.int32)
+    seed[1:5] = 0
+    seed[W:W + 5] = W + 5
+    flow = (100 + np.arange(2 * n, dtype=np.float32)).reshape(n, 2)
+    before = flow.copy()
+    O.interp_flow(P, mh, acc, seed, flow)
+    np.testing.assert_array_equal(flow[1:5], np.float32([[2, -1]] * 4))
+    for i in (0, 5, W + 5):                                      # a plane of its own, or no seed
+        np.testing.assert_array_equal(flow[i], before[i])
+    exp = np.float32([[0, 0], [1 / 3, 1 / 3], [2, 1], [9, 3], [9.5, -3.25]])   # x = 0..4 of row 1; w = 0 at x = 4
+    np.testing.assert_allclose(flow[W:W + 5], exp, rtol=0, atol=1e-7)
