@@ -405,3 +405,58 @@ def test_edge_aware_fill_evaluates_the_seed_plane_at_the_pixel():
         np.testing.assert_array_equal(flow[i], before[i])
     exp = np.float32([[0, 0], [1 / 3, 1 / 3], [2, 1], [9, 3], [9.5, -3.25]])   # x = 0..4 of row 1; w = 0 at x = 4
     np.testing.assert_allclose(flow[W:W + 5], exp, rtol=0, atol=1e-7)
+
+
+def test_assignment_rules_on_hand_built_windows():
+    """Eq. 3-4 with readings R23/R24 on three 4 px windows (x = 0-3, 2-5, 4-7) over an 8x4 frame pair: the source
+    is black and the target grey, so a translation's colour error at p is the target's grey level at the mapped
+    pixel, exact in dyadic values. A pixel takes, over its covering windows in order, the valid plane that maps
+    it into the frame with a positive denominator and an error below eps; a later window displaces the current
+    one only if its error is lower by more than 1e-6. The residual stage uses the second model slot of each
+    window and only the masked pixels."""
+    W, H, eps = 8, 4, 0.5
+    P = O.Params(W, H, cells=(4,), eps=eps)
+    assert list(O.grid_axis(W, 4)) == [0, 2, 4] and list(O.grid_axis(H, 4)) == [0]
+    t = np.full((H, W), 0.75)
+    t[0] = [0.25, 0.5, 0.25, 0.25, 0.25 - 2**-21, 0.125, 0.125 - 2**-19, 0.0625]
+    t[1, 1] = 0.0
+    t[2] = [0.125, 0.25, 0.125, 0.25, 0.0, 0.25, 0.25, 0.25]
+    src = np.zeros((H, W, 3))
+    tgt = np.repeat(t[:, :, None], 3, axis=2)
+
+    def tr(a):
+        return np.array([1, 0, a, 0, 1, 0, 0, 0, 1.0])
+
+    mh, mi = O.empty_models(P)
+    mh[0], mh[2], mh[4] = 2 * tr(0), tr(1), tr(2)                  # stage 1 of windows 0, 1, 2 (model ids 0, 2, 4)
+    mh[1], mh[3] = tr(1), tr(0)                                    # stage 2 of windows 0, 1
+    mh[5] = np.array([0, 0, -1, 0, 0, -1, 0, 0, -1.0])             # maps every pixel to (1, 1), but w = -1
+    mi[[0, 1, 2, 4, 5], O.MI_VALID] = 1                            # model 3 (window 1, stage 2) is invalid
+    n = W * H
+    lab = O.Labels.empty(n, eps)
+    amb = np.zeros(n, np.uint8)
+    O.assign(P, src, tgt, 1, 1, mh, mi, None, lab, amb)
+    r0 = slice(0, W)
+    # x = 0: only window 0; 1: error equals eps; 2: equal errors, the first window keeps it; 3: lower by 2^-21
+    # only; 4: lower by 2^-19; 5: much lower; 6, 7: the +2 translation leaves the frame
+    assert list(lab.m[r0]) == [0, -1, 0, 0, 4, 4, -1, -1]
+    np.testing.assert_array_equal(lab.L[r0], [0.25, eps, 0.25, 0.25, 0.125 - 2**-19, 0.0625, eps, eps])
+    np.testing.assert_array_equal(lab.fx[r0], [0, 0, 0, 0, 2, 2, 0, 0])
+    assert not lab.fy.any()
+    assert list(amb[r0]) == [0, 1, 1, 1, 1, 0, 0, 0]                 # the ties and the eps boundary are logged
+    assert list(lab.m[W:2 * W]) == [-1, 0, -1, -1, -1, -1, -1, -1]     # row 1: only the black target pixel (1, 1)
+    assert list(lab.m[2 * W:3 * W]) == [0, 0, 0, 2, 2, 2, -1, -1]      # row 2: x = 3 lower later, x = 4 a tie
+    assert (lab.m[3 * W:] == -1).all()
+    # residual stage on row 2 only; the other rows keep what they held
+    lab2 = O.Labels(np.full(n, 77, np.int32), np.full(n, 9.0), np.full(n, 5.0), np.full(n, 6.0))
+    mask = np.zeros(n, np.uint8)
+    mask[2 * W:3 * W] = 1
+    O.assign(P, src, tgt, 1, 2, mh, mi, mask, lab2)
+    r2 = slice(2 * W, 3 * W)
+    # x = 2 would prefer the invalid identity of window 1; x = 4..7 would map to the black pixel (1, 1) if the
+    # negative denominator were ignored
+    assert list(lab2.m[r2]) == [1, 1, 1, 1, -1, -1, -1, -1]
+    np.testing.assert_array_equal(lab2.L[r2], [0.25, 0.125, 0.25, 0.0, eps, eps, eps, eps])
+    np.testing.assert_array_equal(lab2.fx[r2], [1, 1, 1, 1, 0, 0, 0, 0])
+    keep = mask == 0
+    assert (lab2.m[keep] == 77).all() and (lab2.L[keep] == 9).all() and (lab2.fx[keep] == 5).all()
