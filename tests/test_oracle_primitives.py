@@ -517,3 +517,58 @@ def test_pipeline_fill_changes_only_unassigned_flows():
         same = np.all(f0 == f1, axis=1)
         assert same.mean() > 0.5 and not same.all()
         assert same[assigned].all()
+
+
+def _fit_one_window(s, vx, vy, **kw):
+    P = O.Params(s, s, cells=(s,), num_hyp=4000, **{"patch_radius": 1, **kw})
+    mh, mi = O.empty_models(P)
+    frame = np.zeros((s, s, 3))
+    O.fit_level(P, frame, frame, 0, 1, 1, vx, vy, None, mh, mi)
+    return mh[0].reshape(3, 3), mi[0]
+
+
+def test_plane_validity_support_orientation_and_scale():
+    """Readings R12 and R14 on one 8x8 window (64 matches): a plane is valid iff its consensus has at least
+    min_inliers and at least a fifth of the matches (13 of 64 is enough, 12 is not), it keeps orientation
+    (det J > 0 at the centre) and its scale sqrt(det J) lies in [scale_min, scale_max]; a fitted but invalid
+    plane carries the bad-geometry flag, and a scale at a bound is logged as a near tie."""
+    s = 8
+    xs, ys, vx0, vy0 = _affine_nnf(s, s, A_INT)                     # orientation kept, scale exactly 1
+    rng = np.random.default_rng(11)
+    for n_in, min_in, valid in ((13, 8, 1), (12, 8, 0), (20, 20, 1), (20, 21, 0)):
+        vx, vy = vx0.copy(), vy0.copy()
+        out = rng.permutation(s * s)[n_in:]
+        vx[out] += (rng.integers(4, 9, size=out.size) * rng.choice([-1, 1], size=out.size)).astype(np.int32)
+        vy[out] += (rng.integers(4, 9, size=out.size) * rng.choice([-1, 1], size=out.size)).astype(np.int32)
+        _, mi = _fit_one_window(s, vx, vy, min_inliers=min_in)
+        assert mi[O.MI_NIN] == 64 and mi[O.MI_COUNT] == n_in, (n_in, mi)
+        assert mi[O.MI_VALID] == valid and bool(mi[O.MI_FLAGS] & O.F_BAD_GEOM) == (not valid), (n_in, min_in, mi)
+    for smin, smax, valid in ((0.999, 1.001, 1), (1.001, 2.0, 0), (0.5, 0.999, 0)):
+        _, mi = _fit_one_window(s, vx0, vy0, scale_min=smin, scale_max=smax)
+        assert mi[O.MI_COUNT] == 64 and mi[O.MI_VALID] == valid, (smin, smax, mi)
+    # a mirror image: all 64 matches agree, but the orientation flips
+    _, _, vx, vy = _affine_nnf(s, s, np.array([[-1, 0, 7], [0, 1, 0], [0, 0, 1]], float))
+    _, mi = _fit_one_window(s, vx, vy)
+    assert mi[O.MI_COUNT] == 64 and mi[O.MI_FLAGS] & O.F_FITTED and not mi[O.MI_VALID]
+    # scale exactly 2 = scale_max: valid or not by rounding, so the fit is logged as a near tie
+    _, _, vx, vy = _affine_nnf(s, s, np.array([[2, 0, 0], [0, 2, 0], [0, 0, 1]], float))
+    _, mi = _fit_one_window(s, vx, vy)
+    assert mi[O.MI_COUNT] == 64 and mi[O.MI_FLAGS] & O.F_AMBIG
+
+
+def test_plane_validity_denominator_on_the_grown_window():
+    """Reading R14: the denominator of a projective plane must stay positive over the window grown by the patch
+    radius r. With w = 1 - x/12 (zero at x = 12) and targets rounded to pixels, the fitted plane of an 8x8 window
+    is valid for r = 3 (grown corners at x = 10) and invalid for r = 6 (x = 13), its scale at the centre, about
+    1.7, inside [0.5, 2] either way."""
+    s = 8
+    ys, xs = np.divmod(np.arange(s * s), s)
+    w = 1 - xs / 12.0
+    vx = (np.round(xs / w) - xs).astype(np.int32)
+    vy = (np.round(ys / w) - ys).astype(np.int32)
+    for r, valid in ((3, 1), (6, 0)):
+        Hf, mi = _fit_one_window(s, vx, vy, patch_radius=r)
+        assert mi[O.MI_COUNT] >= 60 and mi[O.MI_FLAGS] & O.F_FITTED, (r, mi)
+        Hn = Hf / Hf[2, 2]
+        assert abs(Hn[2, 0] + 1 / 12) < 5e-3 and abs(Hn[2, 1]) < 5e-3, Hn   # the fit is the generating plane
+        assert mi[O.MI_VALID] == valid, (r, mi)
