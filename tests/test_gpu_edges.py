@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 from paper_1804_03787_gb300 import gpm, scene
 
-from _parity import final_map_check, oracle_frames, oracle_params
+from _parity import final_map_check, oracle_frames, oracle_params, ransac_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -144,3 +144,88 @@ def test_profile_select_brackets_only_the_chosen_classes(torch):
     with pytest.raises(gpm.GpmError):
         ctx._check(ctx.lib.gpm_profile_select(ctx.h, 1 << len(gpm.PROF_CLASSES), 0), "gpm_profile_select")
     ctx.close()
+
+
+# ---------------------------------------------------------------- plane validity on hand-built matches
+def _validity_nnf(S, scenarios, seed):
+    """NNF of an SxS frame whose disjoint 8x8 windows at (x0, y0) carry the given match sets (zero offsets
+    elsewhere). Kinds: ('shear', n_in): x' = x + (y - y0) - 4, y' = y - 2 (orientation kept, scale 1), with the
+    other 64 - n_in matches moved to random targets at least 4 px from it; 'mirror': x' = 2 x0 + 7 - x;
+    'scale2': twice the distance from (x0 + 2, y0 + 2); 'proj': (p - o) / w + o - 8 with w = 1 - (x - x0) / 10.5,
+    rounded. Every target stays inside the frame."""
+    rng = np.random.default_rng(seed)
+    vx = np.zeros((S, S), np.int32)
+    vy = np.zeros((S, S), np.int32)
+    for (x0, y0), kind in scenarios.items():
+        ys, xs = np.mgrid[y0:y0 + 8, x0:x0 + 8]
+        if kind == "mirror":
+            tx, ty = 2 * x0 + 7 - xs, ys
+        elif kind == "scale2":
+            tx, ty = 2 * (xs - x0) + x0 - 4, 2 * (ys - y0) + y0 - 4
+        elif kind == "proj":
+            w = 1 - (xs - x0) / 10.5
+            tx, ty = np.round((xs - x0) / w) + x0 - 8, np.round((ys - y0) / w) + y0 - 8
+        else:
+            tx, ty = xs + (ys - y0) - 4, ys - 2
+            out = rng.permutation(64)[kind[1]:]
+            for k in out:
+                r, c = divmod(k, 8)
+                while True:
+                    qx, qy = rng.integers(x0 - 8, x0 + 16), rng.integers(y0 - 8, y0 + 16)
+                    if max(abs(qx - tx[r, c]), abs(qy - ty[r, c])) >= 4:
+                        break
+                tx[r, c], ty[r, c] = qx, qy
+        assert tx.min() >= 0 and ty.min() >= 0 and tx.max() < S and ty.max() < S
+        vx[y0:y0 + 8, x0:x0 + 8] = tx - xs
+        vy[y0:y0 + 8, x0:x0 + 8] = ty - ys
+    return vx.reshape(-1), vy.reshape(-1)
+
+
+@pytest.mark.parametrize("r,min_in,scenarios", [
+    (2, 8, {(8, 8): ("shear", 13), (16, 8): ("shear", 12), (24, 8): "mirror", (32, 8): "scale2",
+            (8, 16): "proj", (16, 16): ("shear", 64), (24, 16): ("shear", 20)}),
+    (4, 20, {(8, 8): ("shear", 20), (16, 8): ("shear", 19), (8, 16): "proj"}),
+])
+def test_plane_validity_rules_on_hand_built_matches(torch, r, min_in, scenarios):
+    """Readings R12/R14 through the C ABI: a 48x48 frame pair whose disjoint interior 8x8 windows carry match
+    sets built to sit on either side of a validity rule (support of at least max(min_inliers, N/5), orientation,
+    scale range, denominator over the window grown by r). The GPU's stage-1 fit of every window equals the
+    oracle's (support, winner, refit and geometry flags, H to 1e-6) except where the oracle logged a near tie,
+    and each built window is valid or not as the rule says."""
+    S = 48
+    f = np.full((S, S, 3), 0.5, np.float32)
+    gp = gpm.default_params(patch_radius=r, cells=(8,), pm_iters=1, num_hyp=4000, min_inliers=min_in)
+    P = oracle_params(gp, S, S)
+    vx, vy = _validity_nnf(S, scenarios, seed=r)
+    ctx = gpm.Context(gp, S, S)
+    ctx.match([_dev(torch, f, f)])
+    nnf = np.stack([np.stack([vx, vy], 1)] * 2).astype(np.int32)
+    ctx.import_state(gpm.NNF, nnf, level=0)
+    ctx.fit_planes(1)
+    gmh, gmi = ctx.export(gpm.MODELS), ctx.export(gpm.MODEL_INFO)
+    ctx.close()
+    nx = len(O.grid_axis(S, 8))
+    ids = np.arange(0, 2 * int(O.cell_base(P)[1]), 2)
+    frame = np.asarray(f, np.float64)
+    for d in range(2):
+        mh, mi = O.empty_models(P)
+        O.fit_level(P, frame, frame, d, 1, 1, vx, vy, None, mh, mi)
+        ok = ransac_equal(gmh[d], gmi[d], mh, mi, ids)
+        tie = (mi[ids, O.MI_FLAGS] & O.F_AMBIG) > 0
+        assert not (~ok & ~tie).any(), f"dir {d}: windows {ids[~ok & ~tie] // 2} differ"
+        for (x0, y0), kind in scenarios.items():
+            m = ((y0 // 4) * nx + x0 // 4) * 2
+            if kind == "scale2":                       # scale 2 = scale_max: decided by rounding, logged as a tie
+                assert mi[m, O.MI_FLAGS] & O.F_AMBIG and gmi[d][m, O.MI_COUNT] == 64
+                continue
+            if kind == "mirror":
+                want = False
+            elif kind == "proj":
+                want = r + 7 < 10.5                    # denominator positive at the grown window's far corners
+            else:
+                want = kind[1] >= min_in and 5 * kind[1] >= 64
+                assert mi[m, O.MI_COUNT] == kind[1], (kind, mi[m])
+            # the rule on the oracle; on the GPU wherever the oracle logged no near tie (then both sides agree)
+            sides = (mi[m],) if tie[m // 2] else (mi[m], gmi[d][m])
+            for side in sides:
+                assert bool(side[O.MI_FLAGS] & O.F_BAD_GEOM) == (not want), ((x0, y0), kind, d, side)
