@@ -1,0 +1,72 @@
+"""Host logic of bench.py on CPU: the roofline block's arithmetic and source selection, and the parser of the
+clock samples taken during the timed region (the rejection rules read its reasons)."""
+import os
+
+import pytest
+
+import bench
+
+
+def test_roofline_block_takes_the_top_class_and_divides_by_its_launch_time():
+    # 1e9 square-patch evaluations of 81 taps at 6 FP32 operations each, over 160 launches taking 100 ms in all
+    prof = {"pm_sweep": (100.0, 160), "ransac": (50.0, 40), "pm_sweep_plane": (30.0, 64)}
+    evals = [1e9, 0, 0]
+    blk = bench.roofline_block(prof, evals, 152, {"sm_mhz": 2000.0}, {"hbm_gbs": 6783.0}, steps=10)
+    assert blk["kernel"] == "pm_sweep" and blk["bound"] == "alu"
+    assert blk["share"] == pytest.approx(100 / 180)
+    assert blk["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)                  # 38.9 TFLOP/s
+    assert blk["achieved"] == pytest.approx(1e9 * 81 * 6 / 0.100 / 1e12)             # 4.86 TFLOP/s
+    assert blk["frac"] == pytest.approx(blk["achieved"] / blk["peak"])
+    assert blk["avg_launch_ms"] == pytest.approx(100 / 160)
+    assert "profiled replay" in blk["avg_launch_source"]
+    hv = blk["hbm_view"]                                                            # 48 B per visit, W*H visits
+    assert hv["algorithmic_bytes_per_launch"] == 1024 * 436 * 48
+    assert hv["achieved_gbs"] == pytest.approx(1024 * 436 * 48 / (100 / 160 * 1e-3) / 1e9)
+    assert hv["frac"] == pytest.approx(hv["achieved_gbs"] / 6783.0)
+    assert blk["traffic"] == bench.TRAFFIC_PER_LAUNCH["pm_sweep"][0]
+
+
+def test_roofline_block_prefers_the_timed_region_and_reports_no_fraction_it_cannot_model():
+    prof = {"pm_sweep": (100.0, 160)}
+    blk = bench.roofline_block(prof, [1e9, 0, 0], 152, {"sm_mhz": None}, {"sm_max_mhz": 2070.0}, steps=10,
+                               timed={"pm_sweep": (80.0, 160)})
+    assert blk["avg_launch_ms"] == pytest.approx(0.5) and "timed region" in blk["avg_launch_source"]
+    assert blk["achieved"] == pytest.approx(1e9 * 81 * 6 / 0.080 / 1e12)
+    assert blk["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)                  # the maximum clock, unsampled
+    other = bench.roofline_block({"fill": (5.0, 8)}, [0, 0, 0], 152, {"sm_mhz": 2000.0}, {}, steps=1)
+    assert other["achieved"] is None and other["frac"] is None and other["traffic"] is None
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_samples_median_and_throttle_reasons(tmp_path):
+    c = bench.Clocks("0")
+    c.path = str(tmp_path / "clocks.csv")
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",     # unreadable: skipped
+            "garbage"]
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    c.proc, c.f = _FakeProc(), open(os.devnull, "w")
+    got = c.stop()
+    assert got["sm_mhz"] == 2055 and got["sm_max_mhz"] == 2070 and got["samples"] == 3
+    assert got["reasons"] == ["sw_power_cap"]
+    rows[0] = "0, 1500, 2070, 900.1, 0x0, Active, Not Active, Not Active, Not Active"
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    c.f = open(os.devnull, "w")
+    assert c.stop()["reasons"] == ["hw_slowdown", "sw_power_cap"]
+
+
+def test_clock_sampler_without_nvidia_smi_says_so():
+    c = bench.Clocks("0")
+    c.proc = None
+    assert c.stop()["reasons"] == ["nvidia-smi unavailable"]
