@@ -85,6 +85,31 @@ def test_patchmatch_converges_toward_exhaustive_nnf():
     assert np.all(c >= best - 1e-12)
 
 
+def test_propagation_takes_offsets_from_each_of_the_four_neighbours():
+    """Sec. 3.1 (PatchMatch propagation): the target frame is the source moved by (3, 2), so that offset costs
+    exactly zero inside the frame, and every pixel holds the offset (0, 0) except one neighbour of each test pixel
+    (left, right, upper or lower in turn), which holds (3, 2). One half-step of the red-black sweep gives every
+    test pixel (3, 2): from whichever side it is offered (random search alone would rarely hit that exact offset)."""
+    W, H, r = 48, 40, 1
+    rng = np.random.default_rng(21)
+    src = rng.random((H, W, 3))
+    tgt = np.roll(src, (2, 3), axis=(0, 1))
+    P = O.Params(W, H, patch_radius=r)
+    vx, vy = np.zeros(W * H, np.int32), np.zeros(W * H, np.int32)
+    tests = [(x, y) for y in range(4, H - 5, 4) for x in range(4, W - 6, 4)]
+    for j, (x, y) in enumerate(tests):
+        dx, dy = ((-1, 0), (1, 0), (0, -1), (0, 1))[j % 4]
+        vx[(y + dy) * W + x + dx], vy[(y + dy) * W + x + dx] = 3, 2
+    cost = np.zeros(W * H)
+    O.pm_recost(P, src, tgt, 0, None, None, None, vx, vy, cost)
+    O.pm_sweep(P, src, tgt, 0, 0, 0, 0, None, None, None, vx, vy, cost)
+    ids = np.array([y * W + x for x, y in tests])
+    got = np.stack([vx[ids], vy[ids]], 1)
+    for k in range(4):
+        np.testing.assert_array_equal(got[k::4], np.tile([3, 2], (len(ids[k::4]), 1)), err_msg=f"neighbour {k}")
+    assert (cost[ids] == 0).all()
+
+
 def test_pm_init_targets_inside_frame_and_deterministic():
     P = O.Params(40, 30, patch_radius=1, seed=77)
     f = np.random.default_rng(0).random((30, 40, 3))

@@ -1,0 +1,154 @@
+"""The oracle's pins are sharp: each entry below plants one plausible mistake (a dropped term, a wrong sign,
+index, bound or operand) in a copy of the oracle's C source, rebuilds the copy, and runs the pins meant to
+catch it, which must fail.  The unchanged copy passes the same pins first, so a failure is the mistake's.
+
+CPU only; the copies build and run in parallel, one OpenMP thread each.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PRIM = "tests/test_oracle_primitives.py::"
+METH = "tests/test_oracle_method.py::"
+
+# (file, original text, planted text, pins that must catch it)
+MUTANTS = [
+    # bilinear sampling (exact on affine ramps; clamped at the border)
+    ("oracle_core.c", "out[c] = (1.0 - fy) * ((1.0 - fx) * a + fx * b) + fy * ((1.0 - fx) * d + fx * e);",
+     "out[c] = (1.0 - fx) * ((1.0 - fy) * a + fy * b) + fx * ((1.0 - fy) * d + fy * e);",
+     [PRIM + "test_bilinear_reproduces_affine_ramp"]),
+    ("oracle_core.c", "    if (X > W - 1) X = W - 1;\n", "",
+     [PRIM + "test_bilinear_integer_points_and_clamping"]),
+    # warped patch cost (eq. 3 over a patch): a dropped channel, the plane's offset taken from p instead of G(p)
+    ("oracle_core.c", "            sum += fabs(a[0] - s[0]) + fabs(a[1] - s[1]) + fabs(a[2] - s[2]);\n        }\n    }",
+     "            sum += fabs(a[0] - s[0]) + fabs(a[1] - s[1]);\n        }\n    }",
+     [PRIM + "test_identity_and_translation_planes_reduce_to_square_patch",
+      PRIM + "test_warped_cost_closed_form_on_projective_ramp"]),
+    ("oracle_core.c", "X = px + vx + (gx - gpx);", "X = px + vx + (gx - px);",
+     [PRIM + "test_warped_cost_closed_form_on_projective_ramp"]),
+    # PatchMatch: random initial targets inside the frame; propagation from all four neighbours
+    ("oracle_core.c", "ty = (int)(w[1] % (uint32_t)H);", "ty = (int)(w[1] % (uint32_t)W);",
+     [METH + "test_pm_init_targets_inside_frame_and_deterministic"]),
+    ("oracle_core.c", "NY[4] = {0, 0, -1, 1};\n            for (int k = 0; k < 4; ++k) {\n                int nx",
+     "NY[4] = {0, 0, -1, -1};\n            for (int k = 0; k < 4; ++k) {\n                int nx",
+     [METH + "test_propagation_takes_offsets_from_each_of_the_four_neighbours"]),
+    # homography solvers: a wrong index in a DLT row
+    ("oracle_planes.c", "double r1[9] = {x, y, 1, 0, 0, 0, -u * x, -u * y, -u};",
+     "double r1[9] = {x, y, 1, 0, 0, 0, -u * x, -v * y, -u};",
+     [PRIM + "test_minimal_and_refit_recover_generating_homography"]),
+    # plane validity (R12, R14)
+    ("oracle_planes.c", "int valid = count >= P->min_inliers && 5 * count >= N;",
+     "int valid = count >= P->min_inliers && count >= N / 5;", [PRIM + "test_plane_validity_support_orientation_and_scale"]),
+    ("oracle_planes.c", "int valid = count >= P->min_inliers && 5 * count >= N;",
+     "int valid = count > P->min_inliers && 5 * count >= N;", [PRIM + "test_plane_validity_support_orientation_and_scale"]),
+    ("oracle_planes.c", "double cxs[4] = {x0 - r, x0 + s - 1 + r, x0 - r, x0 + s - 1 + r};",
+     "double cxs[4] = {x0, x0 + s - 1, x0, x0 + s - 1};", [PRIM + "test_plane_validity_denominator_on_the_grown_window"]),
+    ("oracle_planes.c", "if (!(sc >= P->scale_min && sc <= P->scale_max)) valid = 0;",
+     "if (!(sc >= P->scale_min)) valid = 0;", [PRIM + "test_plane_validity_support_orientation_and_scale"]),
+    ("oracle_planes.c", "double sc = sqrt(det);", "double sc = det;",
+     [PRIM + "test_plane_validity_support_orientation_and_scale", PRIM + "test_plane_validity_denominator_on_the_grown_window"]),
+    ("oracle_planes.c", "if (!valid) mi[ORC_MI_FLAGS] |= ORC_F_BAD_GEOM;", ";",
+     [PRIM + "test_plane_validity_support_orientation_and_scale"]),
+    # assignment (eq. 3-4, R23, R24)
+    ("oracle_planes.c", "if (!(d < P->eps)) continue;\n                    if (bm >= 0 && near_colour",
+     "if (!(d <= P->eps)) continue;\n                    if (bm >= 0 && near_colour", [METH + "test_assignment_rules_on_hand_built_windows"]),
+    ("oracle_planes.c", "if (d < bL - ORC_L_TIE) {\n                        bL = d;\n                        bm = id;",
+     "if (d < bL) {\n                        bL = d;\n                        bm = id;", [METH + "test_assignment_rules_on_hand_built_windows"]),
+    ("oracle_planes.c", "if (!in_frame(P, X, Y)) continue;\n                    double d = delta_at(P, src, tgt, x, y, X, Y);\n                    if (near_colour(d, P->eps)) a = 1;",
+     "double d = delta_at(P, src, tgt, x, y, X, Y);\n                    if (near_colour(d, P->eps)) a = 1;",
+     [METH + "test_assignment_rules_on_hand_built_windows"]),
+    ("oracle_planes.c", "if (!mi[id * ORC_MI + ORC_MI_VALID]) continue;\n                    const double* Hm = mh + (size_t)id * 9;\n                    double X, Y;",
+     "const double* Hm = mh + (size_t)id * 9;\n                    double X, Y;", [METH + "test_assignment_rules_on_hand_built_windows"]),
+    ("oracle_planes.c", "int id = (g->base + cell) * 2 + (stage - 1);", "int id = (g->base + cell) * 2;",
+     [METH + "test_assignment_rules_on_hand_built_windows"]),
+    ("oracle_planes.c", "    if (!(w > 0)) return 0;\n    *X", "    if (w == 0) return 0;\n    *X",
+     [METH + "test_assignment_rules_on_hand_built_windows", METH + "test_edge_aware_fill_evaluates_the_seed_plane_at_the_pixel"]),
+    ("oracle_planes.c", "return (fabs(a[0] - s[0]) + fabs(a[1] - s[1]) + fabs(a[2] - s[2])) / 3.0;",
+     "return (fabs(a[0] - s[0]) + fabs(a[1] - s[1]) + fabs(a[2] - s[2])) / 2.0;",
+     [METH + "test_assignment_rules_on_hand_built_windows"]),
+    # occlusion cues (Sec. 3.4)
+    ("oracle_planes.c", "f[ORC_MI_NSYM] < P->eta * f[ORC_MI_NASSIGN]", "f[ORC_MI_NSYM] > P->eta * f[ORC_MI_NASSIGN]",
+     [METH + "test_symmetry_cue_discards_asymmetric_plane", METH + "test_single_plane_scene_is_recovered_and_assigned"]),
+    ("oracle_planes.c", "if (f[ORC_MI_NRC] < P->kappa * f[ORC_MI_COUNT]) {", "if (0) {",
+     [METH + "test_overlap_cue_discards_colour_inconsistent_plane"]),
+    ("oracle_planes.c", "if (!(e2 < t2)) lose[i] = 1;", "if (e2 < t2) lose[i] = 1;",
+     [METH + "test_many_to_one_flags_the_worse_of_two_motions"]),
+    ("oracle_planes.c", "double ex = lfx[i] - lfx[w]", "double ex = lfx[i] + lfx[w]",
+     [METH + "test_many_to_one_flags_the_worse_of_two_motions"]),
+    # merge and NNF update (Sec. 3.3, 3.3.1)
+    ("oracle_planes.c", "lL[i] < aL[i] - P->beta) {", "lL[i] < aL[i] + P->beta) {",
+     [METH + "test_merge_keeps_coarse_unless_clearly_better_and_nnf_update_rounds_half_up"]),
+    ("oracle_planes.c", "vx[i] = (int)floor(afx[i] + 0.5);", "vx[i] = (int)afx[i];",
+     [METH + "test_merge_keeps_coarse_unless_clearly_better_and_nnf_update_rounds_half_up"]),
+    # model-propagation fill (Sec. 3.4.1): neighbours, and the colour bound
+    ("oracle_planes.c", "NY[4] = {0, 0, -1, 1};\n                int bm = -1;", "NY[4] = {0, 0, -1, -1};\n                int bm = -1;",
+     [METH + "test_fill_front_advances_one_pixel_per_jacobi_iteration"]),
+    # final map (Sec. 3.4.1, R20, R23) and the edge-aware fill (R28)
+    ("oracle_planes.c", "int o = am[i] < 0 || (cue[i] & ORC_CUE_M2O);", "int o = am[i] < 0;",
+     [METH + "test_final_map_flow_source_and_occlusion_rule_on_hand_built_state"]),
+    ("oracle_planes.c", "else if (!(delta_at(P, src, tgt, x, y, X, Y) < P->occ_thresh)) o = 1;",
+     "else if (delta_at(P, src, tgt, x, y, X, Y) > P->occ_thresh) o = 1;",
+     [METH + "test_final_map_flow_source_and_occlusion_rule_on_hand_built_state"]),
+    ("oracle_planes.c", "flow[2 * i] = (float)afx[s];", "flow[2 * i] = (float)afx[i];",
+     [METH + "test_edge_aware_fill_evaluates_the_seed_plane_at_the_pixel"]),
+    # census codes (Sec. 6), HSV equalisation (Sec. 4.2), geodesic fill seeds (R28)
+    ("oracle_color.c", "if (grey(rgb, W, nx, ny) < c) code |= 1u << bit;", "if (grey(rgb, W, nx, ny) <= c) code |= 1u << bit;",
+     [PRIM + "test_census_closed_forms"]),
+    ("oracle_color.c", "lut[b] = (lut[b] - (double)cmin) / (double)(n - cmin);", "lut[b] = lut[b] / (double)n;",
+     [PRIM + "test_v_lut_closed_form"]),
+    ("oracle_color.c", "const long long c = dist[j] + 256 + llabs((long long)q[i] - q[j]);",
+     "const long long c = dist[j] + 256;", [PRIM + "test_fill_seeds_respect_an_edge"]),
+]
+
+
+def _copy_tree(dst):
+    """The oracle sources, the tests and the input generator (no built library, no GPU code)."""
+    os.makedirs(os.path.join(dst, "oracle"))
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".c", ".h", ".py")):
+            shutil.copy(os.path.join(ROOT, "oracle", f), os.path.join(dst, "oracle", f))
+    shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(dst, "tests"),
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(os.path.join(dst, "paper_1804_03787_gb300"))
+    for f in ("__init__.py", "scene.py"):
+        shutil.copy(os.path.join(ROOT, "paper_1804_03787_gb300", f), os.path.join(dst, "paper_1804_03787_gb300", f))
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), dst)
+
+
+def _run_pins(dst, pins):
+    env = dict(os.environ, OMP_NUM_THREADS="1", PYTHONPATH=dst, PYTHONDONTWRITEBYTECODE="1")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-m", "not gpu", *pins], cwd=dst, env=env,
+                       stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+def _mutant(base, k):
+    fname, old, new, pins = MUTANTS[k]
+    dst = os.path.join(base, f"m{k:02d}")
+    _copy_tree(dst)
+    path = os.path.join(dst, "oracle", fname)
+    src = open(path).read()
+    assert src.count(old) == 1, f"mutant {k}: the original text is not found exactly once in {fname}"
+    open(path, "w").write(src.replace(old, new))
+    return _run_pins(dst, pins)
+
+
+def test_every_planted_mistake_fails_its_pins(tmp_path):
+    base = str(tmp_path)
+    pins = sorted({p for m in MUTANTS for p in m[3]})
+    clean = os.path.join(base, "clean")
+    _copy_tree(clean)
+    rc, out = _run_pins(clean, pins)
+    assert rc == 0, "the unchanged oracle copy must pass its pins:\n" + out
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        results = list(ex.map(lambda k: _mutant(base, k), range(len(MUTANTS))))
+    survivors = [(k, MUTANTS[k][0], MUTANTS[k][2]) for k, (rc, _) in enumerate(results) if rc == 0]
+    assert not survivors, f"planted mistakes no pin caught: {survivors}"
+    # a pin that fails must fail by an assertion, not by a broken copy
+    for k, (rc, out) in enumerate(results):
+        assert rc == 1, f"mutant {k}: pytest exited {rc}:\n{out}"
