@@ -110,6 +110,39 @@ def test_propagation_takes_offsets_from_each_of_the_four_neighbours():
     assert (cost[ids] == 0).all()
 
 
+def test_distortion_plane_is_the_home_window_model():
+    """Reading R9: at a level >= 1 a pixel's patch is distorted by the plane of its home window, the window whose
+    central half [x0 + s/4, x0 + 3s/4) holds it (the first or last window beyond the grid's ends): its
+    residual-stage plane if valid, else its first-stage plane, else none. Windows of 8 px at stride 4 over a
+    24 px row start at 0, 4, 8, 12, 16, so pixels 0-5 are homed in window 0, 6-9 in 1, 10-13 in 2, 14-17 in
+    3 and 18-23 in 4. Each window carries a different zoom, so a wrong home changes the cost."""
+    W, H, r = 24, 8, 1
+    P = O.Params(W, H, patch_radius=r, cells=(8,))
+    assert list(O.grid_axis(W, 8)) == [0, 4, 8, 12, 16] and list(O.grid_axis(H, 8)) == [0]
+    rng = np.random.default_rng(8)
+    src, tgt = rng.random((H, W, 3)), rng.random((H, W, 3))
+
+    def zoom(z):
+        return np.diag([z, z, 1.0])
+
+    mh, mi = O.empty_models(P)
+    for c in range(5):
+        mh[2 * c] = zoom(1.0 + 0.1 * c).reshape(9)                 # first stage of window c
+    mh[2 * 2 + 1] = zoom(0.7).reshape(9)                           # residual stage of window 2
+    mi[[0, 2, 4, 5, 8], O.MI_VALID] = 1                            # window 3: no valid plane
+    home = [0] * 6 + [1] * 4 + [2] * 4 + [3] * 4 + [4] * 6
+    plane = {0: zoom(1.0), 1: zoom(1.1), 2: zoom(0.7), 3: None, 4: zoom(1.4)}
+    vx = rng.integers(-2, 3, W * H).astype(np.int32)
+    vy = rng.integers(-2, 3, W * H).astype(np.int32)
+    cost = np.zeros(W * H)
+    O.pm_recost(P, src, tgt, 1, mh, mi, np.zeros(W * H, np.uint8), vx, vy, cost)
+    for y in (0, 3, 7):
+        for x in range(W):
+            i = y * W + x
+            want = O.patch_cost(P, src, tgt, x, y, int(vx[i]), int(vy[i]), plane[home[x]])
+            assert cost[i] == want, (x, y, home[x])
+
+
 def test_pm_init_targets_inside_frame_and_deterministic():
     P = O.Params(40, 30, patch_radius=1, seed=77)
     f = np.random.default_rng(0).random((30, 40, 3))

@@ -41,6 +41,18 @@ MUTANTS = [
     ("oracle_planes.c", "double r1[9] = {x, y, 1, 0, 0, 0, -u * x, -u * y, -u};",
      "double r1[9] = {x, y, 1, 0, 0, 0, -u * x, -v * y, -u};",
      [PRIM + "test_minimal_and_refit_recover_generating_homography"]),
+    # Philox-4x32-10 (known answers), the window grid, RANSAC ties and refit acceptance
+    ("oracle_core.c", "uint64_t p0 = (uint64_t)0xD2511F53u * c0;", "uint64_t p0 = (uint64_t)0xD2511F53u * c1;",
+     [PRIM + "test_philox_known_answers"]),
+    ("oracle_core.c", "if (mi[id2 * ORC_MI + ORC_MI_VALID]) return mh + (size_t)id2 * 9;\n    if (mi[id1",
+     "if (mi[id1 * ORC_MI + ORC_MI_VALID]) return mh + (size_t)id1 * 9;\n    if (mi[id1",
+     [METH + "test_distortion_plane_is_the_home_window_model"]),
+    ("oracle_core.c", "if (last + s < n) {", "if (last + s <= n) {",
+     [PRIM + "test_grid_counts_and_overlap", PRIM + "test_cell_totals_of_the_two_workloads"]),
+    ("oracle_planes.c", "if (scores[k] > bscore) {", "if (scores[k] >= bscore) {",
+     [PRIM + "test_ransac_ties_keep_the_lowest_hypothesis"]),
+    ("oracle_planes.c", "if (rscore >= bscore) {", "if (rscore > bscore) {",
+     [PRIM + "test_ransac_recovers_integer_affine_with_outliers"]),
     # plane validity (R12, R14)
     ("oracle_planes.c", "int valid = count >= P->min_inliers && 5 * count >= N;",
      "int valid = count >= P->min_inliers && count >= N / 5;", [PRIM + "test_plane_validity_support_orientation_and_scale"]),
@@ -76,6 +88,8 @@ MUTANTS = [
      [METH + "test_symmetry_cue_discards_asymmetric_plane", METH + "test_single_plane_scene_is_recovered_and_assigned"]),
     ("oracle_planes.c", "if (f[ORC_MI_NRC] < P->kappa * f[ORC_MI_COUNT]) {", "if (0) {",
      [METH + "test_overlap_cue_discards_colour_inconsistent_plane"]),
+    ("oracle_planes.c", "double ex = lfx[i] + ofx[j]", "double ex = lfx[i] - ofx[j]",
+     [METH + "test_symmetry_cue_discards_asymmetric_plane", METH + "test_single_plane_scene_is_recovered_and_assigned"]),
     ("oracle_planes.c", "if (!(e2 < t2)) lose[i] = 1;", "if (e2 < t2) lose[i] = 1;",
      [METH + "test_many_to_one_flags_the_worse_of_two_motions"]),
     ("oracle_planes.c", "double ex = lfx[i] - lfx[w]", "double ex = lfx[i] + lfx[w]",
@@ -101,6 +115,12 @@ MUTANTS = [
      [PRIM + "test_census_closed_forms"]),
     ("oracle_color.c", "lut[b] = (lut[b] - (double)cmin) / (double)(n - cmin);", "lut[b] = lut[b] / (double)n;",
      [PRIM + "test_v_lut_closed_form"]),
+    ("oracle_color.c", "hh = 2.0 + (b - r) / c;", "hh = 2.0 + (r - b) / c;",
+     [PRIM + "test_hsv_conversion_matches_the_library_routine"]),
+    ("oracle_color.c", "(c == dist[i] && seed[j] < seed[i])", "(c == dist[i] && seed[j] > seed[i])",
+     [PRIM + "test_fill_seeds_flat_frame_are_manhattan_nearest"]),
+    ("oracle_core.c", "int i = (int)floor((double)(x - s / 4) / h);", "int i = (int)floor((double)x / h);",
+     [METH + "test_distortion_plane_is_the_home_window_model"]),
     ("oracle_color.c", "const long long c = dist[j] + 256 + llabs((long long)q[i] - q[j]);",
      "const long long c = dist[j] + 256;", [PRIM + "test_fill_seeds_respect_an_edge"]),
 ]

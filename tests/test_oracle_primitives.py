@@ -280,6 +280,21 @@ def test_exhaustive_consensus_matches_brute_force():
     assert mi[0, O.MI_BESTSCORE] == best and mi[0, O.MI_NIN] == 16
 
 
+def test_ransac_ties_keep_the_lowest_hypothesis():
+    """Reading R21: with every match an exact inlier of one integer map, every non-degenerate hypothesis scores
+    all 64 matches. Hypothesis k draws the same sample whatever the count K (its counter is k), so the fit with
+    K = 1 shows hypothesis 0 is such a one; with K = 512 the tie must still go to hypothesis 0."""
+    s = 8
+    P1 = O.Params(s, s, patch_radius=1, cells=(s,), num_hyp=1)
+    Pk = O.Params(s, s, patch_radius=1, cells=(s,), num_hyp=512)
+    _, _, vx, vy = _affine_nnf(s, s, A_INT)
+    frame = np.zeros((s, s, 3))
+    for P, n_hyp in ((P1, 1), (Pk, 512)):
+        mh, mi = O.empty_models(P)
+        O.fit_level(P, frame, frame, 0, 1, 1, vx, vy, None, mh, mi)
+        assert mi[0, O.MI_BESTK] == 0 and mi[0, O.MI_BESTSCORE] == 64, (n_hyp, mi[0])
+
+
 def test_ransac_recovers_integer_affine_with_outliers():
     """30 % gross outliers: the refit on the consensus set is the generating map to 1e-9."""
     rng = np.random.default_rng(6)
