@@ -406,6 +406,28 @@ def test_fit_cells_equals_fit_level_on_its_windows():
             assert not mi2[others].any() and not mh2[others].any()
 
 
+def test_fill_takes_the_lowest_model_id_among_equal_neighbours():
+    """Sec. 3.4.1 with reading R24: a pixel without a plane takes, from its 4-neighbours, the plane with the lowest
+    colour error below eps, the lowest model id among errors within 1e-6. On identical constant frames every
+    identity plane has error 0: the hole between models 5 (left) and 3 (right) takes 3; a neighbour whose plane
+    maps the pixel outside the frame offers nothing, though its id (1) is lower and the clamped sample matches."""
+    W, H = 5, 1
+    P = O.Params(W, H, cells=(2,), fill_iters=1, eps=0.05)
+    f = np.full((H, W, 3), 0.5)
+    n = W
+    mh = np.zeros((8, 9))
+    for m in (3, 5):
+        mh[m] = np.eye(3).reshape(9)
+    mh[1] = np.array([1, 0, 9.0, 0, 1, 0, 0, 0, 1])               # moves every pixel 9 px right, out of the frame
+    mi = np.zeros((8, O.MI), np.int32)
+    acc = O.Labels.empty(n, P.eps)
+    acc.m[:] = [5, -1, 3, -1, 1]
+    cue = np.zeros(n, np.uint8)
+    O.fill(P, f, f, mh, mi, cue, acc)
+    assert list(acc.m) == [5, 3, 3, 3, 1]                            # pixel 3: model 3 from the left, not 1
+    assert acc.L[1] == 0 and acc.L[3] == 0
+
+
 def test_final_map_flow_source_and_occlusion_rule_on_hand_built_state():
     """Sec. 3.4.1 and readings R20/R23: the flow is the plane's where a pixel has one, else its NNF offset; a pixel
     is occluded without a plane, under the many-to-one cue, outside the frame (beyond 1e-3 px) or where the warp

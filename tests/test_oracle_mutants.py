@@ -53,6 +53,8 @@ MUTANTS = [
      [PRIM + "test_ransac_ties_keep_the_lowest_hypothesis"]),
     ("oracle_planes.c", "if (rscore >= bscore) {", "if (rscore > bscore) {",
      [PRIM + "test_ransac_recovers_integer_affine_with_outliers"]),
+    ("oracle_planes.c", "if (stage == 2 && !resid[i]) continue;", ";",
+     [PRIM + "test_residual_stage_fits_only_the_masked_matches"]),
     # plane validity (R12, R14)
     ("oracle_planes.c", "int valid = count >= P->min_inliers && 5 * count >= N;",
      "int valid = count >= P->min_inliers && count >= N / 5;", [PRIM + "test_plane_validity_support_orientation_and_scale"]),
@@ -102,6 +104,11 @@ MUTANTS = [
     # model-propagation fill (Sec. 3.4.1): neighbours, and the colour bound
     ("oracle_planes.c", "NY[4] = {0, 0, -1, 1};\n                int bm = -1;", "NY[4] = {0, 0, -1, -1};\n                int bm = -1;",
      [METH + "test_fill_front_advances_one_pixel_per_jacobi_iteration"]),
+    ("oracle_planes.c", "(fabs(d - bL) <= ORC_L_TIE && m < bm)", "(fabs(d - bL) <= ORC_L_TIE && m > bm)",
+     [METH + "test_fill_takes_the_lowest_model_id_among_equal_neighbours"]),
+    ("oracle_planes.c", "if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y) || !in_frame(P, X, Y)) continue;",
+     "if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y)) continue;",
+     [METH + "test_fill_takes_the_lowest_model_id_among_equal_neighbours"]),
     # final map (Sec. 3.4.1, R20, R23) and the edge-aware fill (R28)
     ("oracle_planes.c", "int o = am[i] < 0 || (cue[i] & ORC_CUE_M2O);", "int o = am[i] < 0;",
      [METH + "test_final_map_flow_source_and_occlusion_rule_on_hand_built_state"]),

@@ -295,6 +295,27 @@ def test_ransac_ties_keep_the_lowest_hypothesis():
         assert mi[0, O.MI_BESTK] == 0 and mi[0, O.MI_BESTSCORE] == 64, (n_hyp, mi[0])
 
 
+def test_residual_stage_fits_only_the_masked_matches():
+    """Sec. 3.2: the second stage fits a window's unassigned pixels only. Here the masked pixels (about 40 %)
+    follow an integer shear and the others a plain shift; stage 1 finds the majority's shift, stage 2 the
+    shear, on exactly the masked matches."""
+    s = 8
+    rng = np.random.default_rng(13)
+    xs, ys, vx, vy = _affine_nnf(s, s, A_INT)
+    mask = (rng.random(s * s) < 0.4).astype(np.uint8)
+    vx[mask == 0], vy[mask == 0] = -4, 3       # at least 4 px from the shear's offset (y + 2, -1) everywhere
+    P = O.Params(s, s, patch_radius=1, cells=(s,), num_hyp=512)
+    frame = np.zeros((s, s, 3))
+    mh, mi = O.empty_models(P)
+    O.fit_level(P, frame, frame, 0, 1, 1, vx, vy, None, mh, mi)
+    O.fit_level(P, frame, frame, 0, 1, 2, vx, vy, mask, mh, mi)
+    shift = np.array([[1, 0, -4], [0, 1, 3], [0, 0, 1.0]])
+    assert mi[0, O.MI_NIN] == 64 and mi[0, O.MI_COUNT] == 64 - int(mask.sum())
+    np.testing.assert_allclose(_norm(mh[0].reshape(3, 3)), _norm(shift), atol=1e-9)
+    assert mi[1, O.MI_NIN] == int(mask.sum()) and mi[1, O.MI_COUNT] == int(mask.sum())
+    np.testing.assert_allclose(_norm(mh[1].reshape(3, 3)), _norm(A_INT), atol=1e-9)
+
+
 def test_ransac_recovers_integer_affine_with_outliers():
     """30 % gross outliers: the refit on the consensus set is the generating map to 1e-9."""
     rng = np.random.default_rng(6)
