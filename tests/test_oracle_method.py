@@ -370,6 +370,43 @@ def test_tiny_config_accuracy_against_ground_truth(seed):
         assert m["rec"] > 0.5, m
 
 
+def test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours():
+    """Algorithm 1 as run end to end: after each level a pixel with a plane holds the rounded plane flow in its
+    NNF (Sec. 3.3.1) and keeps it through that level's restricted PatchMatch (Sec. 3.3.2); the final
+    model-propagation fill (Sec. 3.4.1) keeps every plane assigned before it, gives new planes only to pixels
+    within fill_iters 4-neighbour steps of one, each one of the planes held before the fill, and does fill some."""
+    s = scene.make_scene(96, 72, seed=6, n_layers=3, max_disp=6.0, affine=True)
+    P = O.Params(96, 72, patch_radius=2, cells=(32, 16), pm_iters=3, num_hyp=128, fill_iters=3)
+    W, H, n = 96, 72, 96 * 72
+    for stop in (1, 2):
+        R = O.run(P, s.frame1, s.frame2, stop_after=stop)
+        for d in range(2):
+            a = R.acc[d]
+            on = a.m >= 0
+            assert on.mean() > 0.3
+            np.testing.assert_array_equal(R.vx[d][on], np.floor(a.fx[on] + 0.5).astype(np.int32))
+            np.testing.assert_array_equal(R.vy[d][on], np.floor(a.fy[on] + 0.5).astype(np.int32))
+    pre = O.run(P, s.frame1, s.frame2, stop_after=2)
+    post = O.run(P, s.frame1, s.frame2)
+    filled_any = False
+    for d in range(2):
+        before, after = pre.acc[d].m, post.acc[d].m
+        np.testing.assert_array_equal(after[before >= 0], before[before >= 0])
+        new = (before < 0) & (after >= 0)
+        filled_any |= bool(new.any())
+        near = (before >= 0).reshape(H, W)
+        for _ in range(P.fill_iters):
+            g = near.copy()
+            g[1:] |= near[:-1]
+            g[:-1] |= near[1:]
+            g[:, 1:] |= near[:, :-1]
+            g[:, :-1] |= near[:, 1:]
+            near = g
+        assert not (new & ~near.reshape(-1)).any()
+        assert np.isin(after[new], before[before >= 0]).all()
+    assert filled_any
+
+
 def test_run_is_deterministic():
     s = scene.make_scene(64, 48, seed=4, n_layers=2, max_disp=5.0)
     P = O.Params(64, 48, patch_radius=2, cells=(16, 8), num_hyp=64, pm_iters=2)

@@ -117,6 +117,27 @@ MUTANTS = [
      [METH + "test_final_map_flow_source_and_occlusion_rule_on_hand_built_state"]),
     ("oracle_planes.c", "flow[2 * i] = (float)afx[s];", "flow[2 * i] = (float)afx[i];",
      [METH + "test_edge_aware_fill_evaluates_the_seed_plane_at_the_pixel"]),
+    # the pipeline (Algorithm 1): gain, cue directions and order, residual mask, freezing, fill
+    ("oracle_pipeline.c", "for (size_t i = 0; i < nf; ++i) f2[i] = f2in[i] * g;", "for (size_t i = 0; i < nf; ++i) f2[i] = f2in[i] / g;",
+     [METH + "test_tiny_config_accuracy_against_ground_truth"]),
+    ("oracle_pipeline.c", "orc_cue_counts(P, l, 1, T[d].m, T[d].fx, T[d].fy, T[1 - d].m, T[1 - d].fx, T[1 - d].fy, S->mi[d], NULL);",
+     "orc_cue_counts(P, l, 1, T[d].m, T[d].fx, T[d].fy, T[d].m, T[d].fx, T[d].fy, S->mi[d], NULL);",
+     [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
+    ("oracle_pipeline.c", "            for (int d = 0; d < 2; ++d) orc_cue_invalidate(P, l, 1, S->mi[d]);\n", "",
+     [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
+    ("oracle_pipeline.c", "for (int i = 0; i < n; ++i) resid[d][i] = S1[d].m[i] < 0;",
+     "for (int i = 0; i < n; ++i) resid[d][i] = S1[d].m[i] >= 0;",
+     [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
+    ("oracle_pipeline.c", "                orc_many_to_one(P, C[d].m, C[d].L, C[d].fx, C[d].fy, S->cue[d], NULL);\n", "",
+     [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
+    ("oracle_pipeline.c", "                orc_nnf_update(P, S->am[d], S->afx[d], S->afy[d], S->vx[d], S->vy[d], frozen[d]);\n", "",
+     [METH + "test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours"]),
+    ("oracle_pipeline.c", "pm_run(P, src[d], tgt[d], d, l, S->mh[d], S->mi[d], frozen[d], S->vx[d], S->vy[d], S->cost[d]);",
+     "pm_run(P, src[d], tgt[d], d, l, S->mh[d], S->mi[d], NULL, S->vx[d], S->vy[d], S->cost[d]);",
+     [METH + "test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours"]),
+    ("oracle_pipeline.c",
+     "        orc_fill(P, src[d], tgt[d], S->mh[d], S->mi[d], S->cue[d], S->am[d], S->aL[d], S->afx[d], S->afy[d]);\n", "",
+     [METH + "test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours"]),
     # census codes (Sec. 6), HSV equalisation (Sec. 4.2), geodesic fill seeds (R28)
     ("oracle_color.c", "if (grey(rgb, W, nx, ny) < c) code |= 1u << bit;", "if (grey(rgb, W, nx, ny) <= c) code |= 1u << bit;",
      [PRIM + "test_census_closed_forms"]),
