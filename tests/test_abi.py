@@ -66,3 +66,48 @@ def test_host_only_calls_without_gpu(lib):
     p.cell_size[0] = 7
     assert L.gpm_create(ctypes.byref(p), ctypes.byref(lim), gpm.ALLOC_FN(0), gpm.FREE_FN(0), None, None,
                         ctypes.byref(h)) == gpm.GPM_EINVAL
+
+
+def test_product_path_and_oracle_are_separate():
+    """The package (binding, batching, serving, CUDA sources) neither imports nor includes the oracle, and the
+    oracle includes nothing of the CUDA path: the two share only the seeded input generator."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_1804_03787_gb300")
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            tree = ast.parse(open(os.path.join(pkg, f)).read())
+            for node in ast.walk(tree):
+                names = []
+                if isinstance(node, ast.Import):
+                    names = [a.name for a in node.names]
+                elif isinstance(node, ast.ImportFrom):
+                    names = [node.module or ""]
+                assert not any(n.split(".")[0] == "oracle" for n in names), (f, names)
+    inc = re.compile(r'^\s*#\s*include\s*[<"]([^">]+)[">]', re.M)
+    csrc = os.path.join(pkg, "csrc")
+    for f in os.listdir(csrc):
+        for h in inc.findall(open(os.path.join(csrc, f)).read()):
+            assert "oracle" not in h, (f, h)
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".c", ".h")):
+            for h in inc.findall(open(os.path.join(ROOT, "oracle", f)).read()):
+                assert "gpm" not in h and "csrc" not in h and not h.endswith(".cuh"), (f, h)
+
+
+def test_product_path_fails_loudly_without_a_gpu():
+    """Importing the binding, batching and serving modules loads no oracle; without a CUDA device a context
+    cannot be made (there is no CPU fallback)."""
+    import subprocess
+    import sys
+    code = ("import sys, torch\n"
+            "import paper_1804_03787_gb300.gpm as g, paper_1804_03787_gb300.batch, paper_1804_03787_gb300.serve\n"
+            "assert 'oracle' not in sys.modules, 'oracle imported by the product path'\n"
+            "if not torch.cuda.is_available():\n"
+            "    try:\n"
+            "        g.Context(g.default_params(), 64, 48)\n"
+            "    except RuntimeError as e:\n"
+            "        print('refused:', e)\n"
+            "    else:\n"
+            "        raise SystemExit('a context was made without a GPU')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
