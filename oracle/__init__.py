@@ -6,7 +6,9 @@ tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg use
 it; the CUDA library never does, and the two share no code.
 
 Parity pins: every public function here is pinned by ``tests/test_oracle_*``
-against closed forms, brute force or invariants (see each test's docstring).
+against closed forms, brute force, hand-built cases or invariants (see each
+test's docstring); ``tests/test_oracle_mutants.py`` plants plausible mistakes
+in copies of the C source and checks that the pins catch every one.
 """
 from __future__ import annotations
 
