@@ -137,13 +137,16 @@ size_t gpm_required_bytes(const gpm_params* params, const gpm_limits* limits);
    plane after gpm_fit_planes(l), patches distorted by the pixel's home
    window plane (Sec. 3.3.2).  pairs is a HOST array of n_pairs descriptors;
    at level >= 1 it may be NULL (the pairs of the last level-0 call are
-   used). */
+   used).  n_pairs outside 1..max_pairs (an empty batch included), frames
+   smaller than the largest window or beyond the limits, and a level out of
+   the stage order return GPM_EINVAL before anything is enqueued. */
 gpm_status gpm_match(gpm_ctx* ctx, const gpm_pair* pairs, int32_t n_pairs, int32_t level);
 
 /* Algorithm 1 for level l (1 <= l <= num_scales) on every pair of the last
    gpm_match(0): both RANSAC stages per window, assignment by eq. 3-4, the
    symmetry, overlap and many-to-one cues of Sec. 3.4, the coarse-priority
-   merge of Sec. 3.3 and the NNF update of Sec. 3.3.1. */
+   merge of Sec. 3.3 and the NNF update of Sec. 3.3.1.  GPM_EINVAL for n_pairs
+   outside 1..max_pairs or a level out of the stage order. */
 gpm_status gpm_fit_planes(gpm_ctx* ctx, int32_t n_pairs, int32_t level);
 
 /* Model propagation fill, final flow and occlusion map (Sec. 3.4.1) for the

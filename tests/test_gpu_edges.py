@@ -116,6 +116,9 @@ def test_invalid_calls_are_refused(torch):
         ctx.match([_dev(torch, np.zeros((20, 64, 3)), np.zeros((20, 64, 3)))])
     with pytest.raises(gpm.GpmError):
         ctx.match([_dev(torch, np.zeros((48, 80, 3)), np.zeros((48, 80, 3)))])
+    # an empty batch
+    with pytest.raises(gpm.GpmError):
+        ctx.match([])
     # the context stays usable after refused calls
     flows, occs = ctx.run([_dev(torch, s.frame1, s.frame2)])
     torch.cuda.synchronize()
