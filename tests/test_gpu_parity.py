@@ -508,12 +508,14 @@ def test_equalized_tiny_end_to_end(torch):
 
 
 # ---------------------------------------------------------------- large windows (the paper's preset sizes)
-def test_large_windows_end_to_end(torch):
-    """Windows of 80 and 40 px (the paper's radius-40/20 windows, 2 levels, 7x7 patches) on a 192x112 pair:
-    the whole method against the oracle, with the bars of the tiny end-to-end test."""
-    W, H = 192, 112
+@pytest.mark.parametrize("W,H,cells", [(192, 112, (80, 40)), (288, 192, (96, 48))])
+def test_large_windows_end_to_end(torch, W, H, cells):
+    """Windows of 80 and 40 px (the paper's radius-40/20 windows, 2 levels, 7x7 patches) on a 192x112 pair, and
+    the largest windows the library takes (96 px: 9,216 matches, 144 KiB of shared memory in RANSAC, the widest
+    128-bit hypothesis bounds) on a 288x192 pair: the whole method against the oracle, with the bars of the tiny
+    end-to-end test."""
     s = scene.make_scene(W, H, seed=9, n_layers=2, max_disp=6.0, affine=True)
-    gp = gpm.default_params(patch_radius=3, cells=(80, 40), pm_iters=4, num_hyp=128)
+    gp = gpm.default_params(patch_radius=3, cells=cells, pm_iters=4, num_hyp=128)
     ctx = _ctx(torch, gp, W, H)
     flows, _ = ctx.run([_dev(torch, s)])
     torch.cuda.synchronize()
@@ -524,7 +526,7 @@ def test_large_windows_end_to_end(torch):
     agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-4)
     epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))[vis].mean()
     epe_o = np.hypot(*(oflow - s.flow).transpose(2, 0, 1))[vis].mean()
-    print(f"80/40 windows: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
+    print(f"{cells} windows: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
     assert agree > 0.95
     assert abs(epe_g - epe_o) < 0.01
     ctx.close()
