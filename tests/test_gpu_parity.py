@@ -40,7 +40,7 @@ def _dev(torch, s):
     return torch.from_numpy(s.frame1).cuda(), torch.from_numpy(s.frame2).cuda()
 
 
-CASES = [(64, 48, 2, (16, 8)), (70, 45, 3, (16, 8))]
+CASES = [(64, 48, 2, (16, 8)), (70, 45, 3, (16, 8)), (66, 50, 1, (16, 8))]   # r = 1: a single 32-tap chunk
 
 
 # ---------------------------------------------------------------- ingest and init
