@@ -232,3 +232,21 @@ def test_plane_validity_rules_on_hand_built_matches(torch, r, min_in, scenarios)
             sides = (mi[m],) if tie[m // 2] else (mi[m], gmi[d][m])
             for side in sides:
                 assert bool(side[O.MI_FLAGS] & O.F_BAD_GEOM) == (not want), ((x0, y0), kind, d, side)
+
+
+@pytest.mark.parametrize("kw", [dict(num_hyp=1), dict(num_hyp=4096, min_inliers=4), dict(fill_iters=0, pm_iters=1)])
+def test_parameter_extremes_end_to_end(torch, kw):
+    """The tiny configuration at the ends of the parameter ranges the library accepts (one RANSAC hypothesis per
+    window; the most hypotheses with the smallest support; no fill and a single PatchMatch iteration): the whole
+    method against the oracle, with the bars of the tiny end-to-end test."""
+    s = scene.tiny_scene(2)
+    gp = gpm.default_params(**kw)
+    ctx, (gf, _), (of, _) = _both(torch, gp, s.frame1, s.frame2)
+    ctx.close()
+    vis = s.occ == 0
+    agree = np.mean(np.hypot(*(gf - of).transpose(2, 0, 1)) < 1e-4)
+    epe_g = np.hypot(*(gf - s.flow).transpose(2, 0, 1))[vis].mean()
+    epe_o = np.hypot(*(of - s.flow).transpose(2, 0, 1))[vis].mean()
+    print(f"{kw}: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
+    assert agree > 0.95
+    assert abs(epe_g - epe_o) < 0.01
