@@ -55,6 +55,12 @@ MUTANTS = [
      [PRIM + "test_ransac_recovers_integer_affine_with_outliers"]),
     ("oracle_planes.c", "if (stage == 2 && !resid[i]) continue;", ";",
      [PRIM + "test_residual_stage_fits_only_the_masked_matches"]),
+    # Hartley normalisation of the DLT: no centring; a scale that is not rotation invariant
+    ("oracle_planes.c", "    mx /= n;\n    my /= n;\n    for (int i = 0; i < n; ++i) d += hypot",
+     "    mx = 0;\n    my = 0;\n    for (int i = 0; i < n; ++i) d += hypot",
+     [PRIM + "test_normalised_dlt_is_similarity_covariant"]),
+    ("oracle_planes.c", "d += hypot(p[2 * i] - mx, p[2 * i + 1] - my);", "d += fabs(p[2 * i] - mx);",
+     [PRIM + "test_normalised_dlt_is_similarity_covariant"]),
     # plane validity (R12, R14)
     ("oracle_planes.c", "int valid = count >= P->min_inliers && 5 * count >= N;",
      "int valid = count >= P->min_inliers && count >= N / 5;", [PRIM + "test_plane_validity_support_orientation_and_scale"]),

@@ -237,6 +237,26 @@ def test_dlt_is_least_squares_optimal_under_noise():
     assert np.abs(_apply(Hd, p) - _apply(Hg, p)).max() < 0.3
 
 
+def test_normalised_dlt_is_similarity_covariant():
+    """Hartley & Zisserman's argument for normalising (Sec. 3.1.2 fits planes by the normalised DLT): with both
+    point sets centred and scaled to a fixed mean distance, the least-squares homography of noisy matches moves
+    with the data under similarities: fitting S p -> S' q gives S' H S^-1 for the H that p -> q gives (up to
+    scale). An unnormalised or uncentred DLT does not have this property."""
+    rng = np.random.default_rng(12)
+    Hg = _rand_h(rng)
+    p = rng.uniform(0, 40, size=(60, 2))
+    q = _apply(Hg, p) + rng.normal(0, 0.5, size=(60, 2))
+
+    def sim(theta, scale, tx, ty):
+        c, s_ = np.cos(theta) * scale, np.sin(theta) * scale
+        return np.array([[c, -s_, tx], [s_, c, ty], [0, 0, 1.0]])
+
+    S, Sq = sim(0.5, 3.0, 100.0, -50.0), sim(-1.1, 0.4, -7.0, 220.0)
+    H1 = O.h_dlt(p, q)
+    H2 = O.h_dlt(_apply(S, p), _apply(Sq, q))
+    np.testing.assert_allclose(_norm(H2), _norm(Sq @ H1 @ np.linalg.inv(S)), atol=1e-9)
+
+
 def _affine_nnf(W, H, A):
     ys, xs = np.divmod(np.arange(W * H), W)
     q = _apply(A, np.stack([xs, ys], 1).astype(float))
