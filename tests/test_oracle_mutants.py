@@ -155,6 +155,17 @@ MUTANTS = [
      [PRIM + "test_fill_seeds_flat_frame_are_manhattan_nearest"]),
     ("oracle_core.c", "int i = (int)floor((double)(x - s / 4) / h);", "int i = (int)floor((double)x / h);",
      [METH + "test_distortion_plane_is_the_home_window_model"]),
+    ("oracle_color.c", "case 0: *r = v; *g = t; *b = p; break;", "case 0: *r = v; *g = p; *b = t; break;",
+     [PRIM + "test_hsv_conversion_matches_the_library_routine"]),
+    ("oracle_core.c", "sum += orc_popcount32(a ^ b);", "sum += orc_popcount32(a & b);",
+     [PRIM + "test_census_cost_finds_an_integer_shift_exhaustively"]),
+    ("oracle_color.c", "q[i] = (int32_t)floor(1024.0 * ((rgb[3 * i] + rgb[3 * i + 1]) + rgb[3 * i + 2]));",
+     "q[i] = (int32_t)floor(1023.0 * ((rgb[3 * i] + rgb[3 * i + 1]) + rgb[3 * i + 2]));",
+     [PRIM + "test_fill_seeds_grey_quantisation_decides_a_close_call"]),
+    ("oracle_color.c", "for (int x = W - 2; x >= 0; --x) relax(q, dist, seed, y * W + x + 1, y * W + x);", ";",
+     [PRIM + "test_fill_seeds_flat_frame_are_manhattan_nearest"]),
+    ("oracle_planes.c", "return s2 > 0 ? s1 / s2 : 1.0;", "return s2 > 0 ? s2 / s1 : 1.0;",
+     [METH + "test_tiny_config_accuracy_against_ground_truth"]),
     ("oracle_color.c", "const long long c = dist[j] + 256 + llabs((long long)q[i] - q[j]);",
      "const long long c = dist[j] + 256;", [PRIM + "test_fill_seeds_respect_an_edge"]),
 ]

@@ -561,6 +561,19 @@ def test_fill_seeds_respect_an_edge():
     assert got[4 * W + 9] == left  # 2 px from the right seed across the edge, 9 px from the left one
 
 
+def test_fill_seeds_grey_quantisation_decides_a_close_call():
+    """Reading R28's grey levels q = floor(1024 (R + G + B)) decide a close call: on a 7-pixel row with seeds at
+    both ends, pixel 3 is three steps from each; the left path crosses q 0 -> 512 (a grey sum of 0.5), the right
+    one q 512 -> 1 (a grey sum of 0.000977, so q = 1). The right path is cheaper by one, so pixel 3 takes the
+    right seed; with equal costs the lower seed index (the left) would win."""
+    P = O.Params(7, 1)
+    img = np.zeros((1, 7, 3))
+    img[0, 2:5, 0] = 0.5
+    img[0, 5:, 0] = 0.000977
+    am = np.array([0, -1, -1, -1, -1, -1, 0], np.int32)
+    assert list(O.interp_seeds(P, img, am)) == [0, 0, 0, 6, 6, 6, 6]
+
+
 def test_pipeline_fill_changes_only_unassigned_flows():
     s = scene.make_scene(48, 36, seed=12, n_layers=2, max_disp=4.0, affine=True)
     kw = dict(patch_radius=2, cells=(16, 8), pm_iters=2, num_hyp=32)
