@@ -278,6 +278,19 @@ def test_many_to_one_flags_the_worse_of_two_motions():
     assert lab.m[1] == -1 and lab.m[4] == -1 and lab.m[7] == 4 and lab.m[6] == 4 and lab.m[8] == 8
 
 
+def test_many_to_one_targets_round_half_up():
+    """Reading R17's target q = round(p + f), rounding halves up: p = 2 with flow 2.5 lands on q = 5, as does
+    p = 7 with flow -2; their flows differ by 4.5 >= t_fb, so the one with the higher L (p = 2) is occluded.
+    Truncating instead would send p = 2 to 4, with no conflict."""
+    P = O.Params(10, 1, patch_radius=1, cells=(2,))
+    lab = O.Labels.empty(10, P.eps)
+    for p, f, L, m in [(2, 2.5, 0.03, 2), (7, -2.0, 0.01, 4)]:
+        lab.m[p], lab.fx[p], lab.L[p] = m, f, L
+    cue = np.zeros(10, np.uint8)
+    O.many_to_one(P, lab, cue)
+    assert list(np.flatnonzero(cue)) == [2] and lab.m[2] == -1 and lab.m[7] == 4
+
+
 def test_merge_keeps_coarse_unless_clearly_better_and_nnf_update_rounds_half_up():
     P = O.Params(4, 1, cells=(2,), beta=0.015)
     acc = O.Labels(np.array([-1, 5, 5, 5], np.int32), np.array([0.06, 0.03, 0.03, 0.03]),

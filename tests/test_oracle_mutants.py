@@ -100,6 +100,10 @@ MUTANTS = [
      [METH + "test_symmetry_cue_discards_asymmetric_plane", METH + "test_single_plane_scene_is_recovered_and_assigned"]),
     ("oracle_planes.c", "if (!(e2 < t2)) lose[i] = 1;", "if (e2 < t2) lose[i] = 1;",
      [METH + "test_many_to_one_flags_the_worse_of_two_motions"]),
+    ("oracle_planes.c",
+     "        if (lm[i] < 0) continue;\n        int x = i % W, y = i / W;\n        double tx = x + lfx[i] + 0.5, ty = y + lfy[i] + 0.5;",
+     "        if (lm[i] < 0) continue;\n        int x = i % W, y = i / W;\n        double tx = x + lfx[i], ty = y + lfy[i];",
+     [METH + "test_many_to_one_targets_round_half_up"]),
     ("oracle_planes.c", "double ex = lfx[i] - lfx[w]", "double ex = lfx[i] + lfx[w]",
      [METH + "test_many_to_one_flags_the_worse_of_two_motions"]),
     # merge and NNF update (Sec. 3.3, 3.3.1)
