@@ -291,6 +291,22 @@ def test_many_to_one_targets_round_half_up():
     assert list(np.flatnonzero(cue)) == [2] and lab.m[2] == -1 and lab.m[7] == 4
 
 
+def test_symmetry_count_reads_the_target_rounded_half_up():
+    """Sec. 3.4 cue (1) with reading R17's rounding: p = 2 with flow 2.5 looks up the other direction at
+    q = round(4.5) = 5, where the flow is -2.5 (symmetric); at 4, where truncation would look, the flow is +9.
+    Pixel 6 with flow 1 meets -1 at 7 (symmetric). Both count as assigned and symmetric."""
+    P = O.Params(10, 2, patch_radius=1, cells=(2,), fb_px=1.0)
+    n = 20
+    lab, other = O.Labels.empty(n, P.eps), O.Labels.empty(n, P.eps)
+    for p, f in [(2, 2.5), (6, 1.0)]:
+        lab.m[p], lab.fx[p] = 4, f
+    for q, f in [(5, -2.5), (4, 9.0), (7, -1.0)]:
+        other.m[q], other.fx[q] = 0, f
+    _, mi = O.empty_models(P)
+    O.cue_counts(P, 1, 1, lab, other, mi)
+    assert mi[4, O.MI_NASSIGN] == 2 and mi[4, O.MI_NSYM] == 2
+
+
 def test_merge_keeps_coarse_unless_clearly_better_and_nnf_update_rounds_half_up():
     P = O.Params(4, 1, cells=(2,), beta=0.015)
     acc = O.Labels(np.array([-1, 5, 5, 5], np.int32), np.array([0.06, 0.03, 0.03, 0.03]),

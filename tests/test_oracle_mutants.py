@@ -98,6 +98,10 @@ MUTANTS = [
      [METH + "test_overlap_cue_discards_colour_inconsistent_plane"]),
     ("oracle_planes.c", "double ex = lfx[i] + ofx[j]", "double ex = lfx[i] - ofx[j]",
      [METH + "test_symmetry_cue_discards_asymmetric_plane", METH + "test_single_plane_scene_is_recovered_and_assigned"]),
+    ("oracle_planes.c",
+     "            mi[m * ORC_MI + ORC_MI_NASSIGN]++;\n            double tx = x + lfx[i] + 0.5, ty = y + lfy[i] + 0.5;",
+     "            mi[m * ORC_MI + ORC_MI_NASSIGN]++;\n            double tx = x + lfx[i], ty = y + lfy[i];",
+     [METH + "test_symmetry_count_reads_the_target_rounded_half_up"]),
     ("oracle_planes.c", "if (!(e2 < t2)) lose[i] = 1;", "if (e2 < t2) lose[i] = 1;",
      [METH + "test_many_to_one_flags_the_worse_of_two_motions"]),
     ("oracle_planes.c",
