@@ -79,18 +79,58 @@ def oracle_sample(scene_obj):
 
 
 def oracle_threads() -> int:
-    n = os.environ.get("OMP_NUM_THREADS")
-    return int(n) if n else (os.cpu_count() or 1)
+    import oracle as O
+    return O.max_threads()
 
 
-def cpu_baseline_block(scene_obj, samples: int = 6):
+def oracle_full_frame_level0(scene_obj, threads: int):
+    """Measured oracle rates on the FULL 1024x436 benchmark frame, reduced to the level-0 PatchMatch (the initial
+    field and one red-black iteration, both directions): seconds, pixel visits/s and patch evaluations/s."""
+    import oracle as O
+    O.set_threads(threads)
+    f = lambda x: float(np.float32(x))
+    P = O.Params(W, H, patch_radius=RADIUS, cells=CELLS, pm_iters=1, num_hyp=HYP, eps=f(0.06), beta=f(0.015),
+                 occ_thresh=f(0.06))
+    O.eval_count(reset=True)
+    t0 = time.perf_counter()
+    O.run(P, scene_obj.frame1, scene_obj.frame2, stop_after=0)
+    t = time.perf_counter() - t0
+    ev = O.eval_count(reset=True)
+    visits = 2 * W * H * 2  # init + one iteration (two half-sweeps), both directions
+    return {"seconds": t, "threads": threads, "pixel_visits_per_s": visits / t, "evals_per_s": ev / t,
+            "evals": ev, "workload": "full 1024x436 frame, 9x9 patches: initial field + 1 PatchMatch iteration, "
+                                     "both directions (level 0 only)"}
+
+
+def cpu_baseline_block(scene_obj, samples: int = 3):
+    """The FP64 oracle on the host cores: the whole method on a 256x218 crop (1/8 of the pixels, all levels and
+    iterations; the headline figure), the level-0 PatchMatch on the full frame (all cores and one thread), and the
+    tiny configuration end to end on one thread."""
+    import oracle as O
+    from paper_1804_03787_gb300 import scene
+    cores = O.max_threads()
+    O.set_threads(cores)
     ts = [oracle_sample(scene_obj) for _ in range(samples)]
     t = statistics.median(ts)
-    scale = (W * H) / (CROP[0] * CROP[1])
-    return {"value": 1.0 / (t * scale), "unit": "pairs/s", "cores": oracle_threads(), "kind": "oracle",
-            "sample": f"whole method on a {CROP[0]}x{CROP[1]} crop (1/8 of the pixels) of benchmark scene 0, "
-                      f"median of {samples} runs ({sum(ts):.1f} s of CPU work), {t:.2f} s each, scaled to a full 1024x436 pair "
-                      "by pixel count"}
+    frac = (CROP[0] * CROP[1]) / (W * H)
+    full_all = oracle_full_frame_level0(scene_obj, cores)
+    full_one = oracle_full_frame_level0(scene_obj, 1)
+    tiny = scene.tiny_scene(0)
+    O.set_threads(1)
+    t0 = time.perf_counter()
+    O.run(O.Params(128, 96), tiny.frame1, tiny.frame2)
+    t_tiny = time.perf_counter() - t0
+    O.set_threads(cores)
+    return {"value": frac / t, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+            "sample": f"whole method on a {CROP[0]}x{CROP[1]} crop of benchmark scene 0 ({frac:.4f} of a 1024x436 "
+                      f"pair's pixels, all 4 levels and 8 iterations), median of {samples} runs of {t:.2f} s; "
+                      "value = crop pixels / full-frame pixels / time",
+            "full_frame_level0": {"all_cores": full_all, "one_thread": full_one},
+            "tiny_config_one_thread": {"seconds": t_tiny, "workload": "128x96, 7x7 patches, cells 32/16/8, "
+                                                                       "4 iterations, 256 hypotheses, whole method"},
+            "extrapolated": {"whole_pair_s_all_cores": t / frac, "pairs_per_s": frac / t,
+                             "how": "crop time scaled by pixel count (the method's work grows with the pixels and "
+                                    "the windows they hold)"}}
 
 
 # ---------------------------------------------------------------- clocks
@@ -143,20 +183,53 @@ class Clocks:
 
 # ---------------------------------------------------------------- roofline model
 def fp32_peak_tops(sm_mhz: float, nsm: int) -> float:
-    """FP32 lane-operation peak: 128 FP32 lanes per SM, one operation per lane per clock."""
+    """Nominal FP32 lane-operation peak: 128 FP32 lanes per SM, one operation per lane per clock."""
     return nsm * 128 * sm_mhz * 1e6 / 1e12
+
+
+def measure_fp32_peak(nsm: int, gpu_id: str, launches: int = 24):
+    """FP32 lane operations per SM clock, measured with the library's FMA probe (CUDA events on the launching
+    stream, the SM clock sampled during the launches): the peak at any clock is this times the clock."""
+    import torch
+
+    from paper_1804_03787_gb300 import gpm
+    blocks, iters = nsm * 8, 1200
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    gpm.fp32_peak_probe(blocks, 10, sink)
+    torch.cuda.synchronize()
+    clk = Clocks(gpu_id)
+    clk.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream()
+    best = None
+    t_end = time.perf_counter() + 1.0
+    n = 0
+    while n < launches or time.perf_counter() < t_end:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ops = gpm.fp32_peak_probe(blocks, iters, sink)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+        n += 1
+    c = clk.stop()
+    mhz = c.get("sm_mhz")
+    rate = ops / (best * 1e-3)
+    return {"lane_ops_per_s": rate, "sm_mhz": mhz, "lane_ops_per_clk": rate / (mhz * 1e6) if mhz else None,
+            "nominal_lane_ops_per_clk": nsm * 128, "launches": n, "clock_reasons": c.get("reasons"),
+            "how": f"{blocks} blocks x 256 threads x 8 chains of {iters * 64} FMAs, fastest of {n} launches "
+                   "(CUDA events), divided by the median SM clock sampled during them"}
 
 
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the kernel class, from the
 # captures summarised in profiles/ (null where the kernel changed since, or no capture matches the class).
 TRAFFIC_PER_LAUNCH = {
-    "pm_sweep": (25392896 + 10752, "profiles/pm_sweep_level0_1024x436.md"),
     "pm_sweep_plane": (17855744 + 8960, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Issue-slot utilisation of the kernel (ncu smsp__issue_active, one launch of the same workload): the sweeps are
 # bound by gather latency and issue, which the ALU fraction alone does not show.
 ISSUE_PER_LAUNCH = {
-    "pm_sweep": (0.5785, "profiles/pm_sweep_level0_1024x436.md"),
     "pm_sweep_plane": (0.5836, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
@@ -164,9 +237,12 @@ ISSUE_PER_LAUNCH = {
 PM_BYTES_PER_VISIT = 48
 
 
-def roofline_block(prof, evals, nsm, clocks, peaks, steps, timed=None):
-    """Roofline of the kernel class with the largest share of device time (shares and evaluation counts from the
-    profiled replay `prof`, `evals`; the kernel's launch times from the timed region, `timed`, when measured)."""
+def roofline_block(prof, evals, nsm, clocks, peaks, steps, timed=None, fp32=None):
+    """Roofline of the kernel class with the largest share of device time (shares and work counts from the
+    profiled replay `prof`, `evals`; the kernel's launch times from the timed region, `timed`, when measured).
+    The ALU peak is the measured FP32 lane rate per clock (`fp32`) at the timed region's median SM clock, else the
+    nominal 128 lanes per SM."""
+    from paper_1804_03787_gb300 import gpm
     total = sum(ms for ms, _ in prof.values()) or 1.0
     top = max(prof, key=lambda k: prof[k][0])
     ms, launches = (timed or {}).get(top, (0.0, 0))
@@ -177,25 +253,39 @@ def roofline_block(prof, evals, nsm, clocks, peaks, steps, timed=None):
     share = prof[top][0] / total
     T = (2 * RADIUS + 1) ** 2
     mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = fp32_peak_tops(mhz, nsm)
+    if fp32 and fp32.get("lane_ops_per_clk"):
+        peak_ops = fp32["lane_ops_per_clk"] * mhz * 1e6 / 1e12
+        peak_src = (f"measured: {fp32['lane_ops_per_clk']:.0f} FP32 lane operations per SM clock (FMA probe) x the "
+                    f"timed region's median {mhz:.0f} MHz")
+    else:
+        peak_ops = fp32_peak_tops(mhz, nsm)
+        peak_src = f"nominal: {nsm} SMs x 128 FP32 lanes x {mhz:.0f} MHz"
     block = {"kernel": top, "share": share, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
-             "avg_launch_source": src}
-    if top in ("pm_sweep", "pm_init", "pm_recost"):
-        # square-patch evaluation: per tap 3 channels x (subtract, |.| accumulate) = 6 FP32 operations
-        ops = evals[0] * T * 6
-        ach = ops / (ms * 1e-3) / 1e12
+             "avg_launch_source": src, "peak_source": peak_src}
+    n_prof_launches = max(prof[top][1], 1)
+    if top == "pm_sweep":
+        # square-patch evaluation: per tap 3 channels x (subtract, |.| accumulate) = 6 FP32 operations, counted on
+        # the taps the sweeps actually summed (abandoned evaluations stop early)
+        taps = evals[gpm.COUNT_SWEEP0_TAPS] / n_prof_launches
+        ev = evals[gpm.COUNT_SWEEP0] / n_prof_launches
+        ach = taps * 6 / (block["avg_launch_ms"] * 1e-3) / 1e12
         block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
-                      "units": "FP32 lane operations (6 per tap, 81 taps per evaluation)"})
+                      "units": "FP32 lane operations: 6 per tap summed",
+                      "per_launch": {"evaluations": ev, "taps_summed": taps, "taps_per_evaluation": taps / max(ev, 1),
+                                     "nominal_taps_per_evaluation": T}})
     elif top == "pm_sweep_plane":
         # warped evaluation: per tap and channel 6 for the bilinear blend + 2 for the absolute difference
-        ops = evals[1] * T * 3 * 8
-        ach = ops / (ms * 1e-3) / 1e12
+        taps = evals[gpm.COUNT_SWEEP_PLANE_TAPS] / n_prof_launches
+        ev = evals[gpm.COUNT_SWEEP_PLANE] / n_prof_launches
+        ach = taps * 24 / (block["avg_launch_ms"] * 1e-3) / 1e12
         block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
-                      "units": "FP32 lane operations (24 per tap)"})
+                      "units": "FP32 lane operations: 24 per tap summed",
+                      "per_launch": {"evaluations": ev, "taps_summed": taps, "taps_per_evaluation": taps / max(ev, 1),
+                                     "nominal_taps_per_evaluation": T}})
     elif top == "ransac":
         # one residual test ||H u - (u + v)||^2 < t^2 in the evaluation form: 14 FP32 operations
-        ops = evals[2] * 14
-        ach = ops / (ms * 1e-3) / 1e12
+        ops = evals[gpm.COUNT_RANSAC] / n_prof_launches * 14
+        ach = ops / (block["avg_launch_ms"] * 1e-3) / 1e12
         block.update({"bound": "alu", "achieved": ach, "peak": peak_ops, "unit": "TFLOP/s", "frac": ach / peak_ops,
                       "units": "FP32 lane operations (14 per residual test; hypothesis solves not counted)"})
     else:
@@ -231,16 +321,17 @@ def run_reference(args):
     for _ in range(args.warmup):
         oracle_sample(s)
     ts = [oracle_sample(s) for _ in range(args.steps)]
-    scale = (W * H) / (CROP[0] * CROP[1])
-    step_s = sum(ts) * scale
-    value = args.steps / step_s
+    frac = (CROP[0] * CROP[1]) / (W * H)
+    value = args.steps * frac / sum(ts)
+    cores = oracle_threads()
+    sample = (f"each step: the whole method (all 4 levels, 8 iterations) on a {CROP[0]}x{CROP[1]} crop of benchmark "
+              f"scene 0, {frac:.4f} of a 1024x436 pair's pixels; ms_per_step is the measured crop time, value = "
+              "pair fractions per second")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(ts) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "pairs_per_step": 1, "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": oracle_threads(), "kind": "oracle",
-                             "sample": f"each step: the whole method on a {CROP[0]}x{CROP[1]} crop (1/8 of the "
-                                       f"pixels) of benchmark scene 0, scaled by pixel count"},
+            "config": {"workload": WORKLOAD, "pairs_per_step": frac, "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -633,7 +724,8 @@ def run_ours(args):
     total_ms = max_over_ranks(sum(times), dist, "cuda")
     value = job_throughput(args.steps * P, ws, total_ms)
     pm_ms = prof["pm_sweep"][0] + prof["pm_init"][0] + prof["pm_sweep_plane"][0] + prof["pm_recost"][0]
-    evals_per_s = (evals[0] + evals[1]) * ws / (pm_ms * 1e-3) if pm_ms > 0 else None
+    n_pm_evals = evals[gpm.COUNT_SWEEP0] + evals[gpm.COUNT_SWEEP_PLANE] + evals[gpm.COUNT_INIT]
+    evals_per_s = n_pm_evals * ws / (pm_ms * 1e-3) if pm_ms > 0 else None
 
     # end to end through the public API: pinned host frames in, flow and occlusion back to pinned host memory
     host_in = [(s.frame1, s.frame2) for s in scenes]
@@ -685,15 +777,20 @@ def run_ours(args):
     h2d = P * 2 * W * H * 3 * 4
     d2h = P * (W * H * 2 * 4 + W * H)
 
-    roof = roofline_block(prof, evals, nsm, clocks, peaks, args.steps, timed=prof_timed)
+    fp32 = measure_fp32_peak(nsm, gpu_id)
+    roof = roofline_block(prof, evals, nsm, clocks, peaks, args.steps, timed=prof_timed, fp32=fp32)
     line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "pairs_per_step": P, "scenes": f"{nscenes} seeded scenes per rank, cycled",
                        "l2": "flushed between timed steps by a 256 MiB device write", "parallelism": "replicas"},
             "warped_patch_evals_per_s": evals_per_s,
-            "evals_per_step": (evals[0] + evals[1]) / args.steps,
-            "ransac_tests_per_step": evals[2] / args.steps,
+            "evals_per_step": n_pm_evals / args.steps,
+            "evals_per_step_by_kind": {"level0_sweep": evals[gpm.COUNT_SWEEP0] / args.steps,
+                                       "plane_sweeps": evals[gpm.COUNT_SWEEP_PLANE] / args.steps,
+                                       "init_and_recost": evals[gpm.COUNT_INIT] / args.steps},
+            "ransac_tests_per_step": evals[gpm.COUNT_RANSAC] / args.steps,
+            "fp32_peak_probe": fp32,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "kernel_ms_source": "every launch bracketed by CUDA events in an untimed replay of the timed steps",
             "roofline": roof,

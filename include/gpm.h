@@ -24,8 +24,10 @@
  *   - Every call enqueues work on the context's CUDA stream and returns
  *     without synchronising.  Results are valid once that stream has
  *     reached them.  Argument errors are reported synchronously
- *     (GPM_EINVAL) before anything is enqueued.  An error detected on the
- *     device (a bounds check) is reported by the next call, or by gpm_sync.
+ *     (GPM_EINVAL) before anything is enqueued.  A failed CUDA launch is
+ *     reported by the call that enqueued it (GPM_ECUDA).  A consistency
+ *     check on the device (imported labels that name a model outside the
+ *     model table) is reported by gpm_sync (GPM_EINTERNAL).
  *   - No exception or C++ type crosses this boundary.  A context is used by
  *     one host thread at a time.
  *   - Ownership: the caller owns frames and outputs; the context owns every
@@ -50,10 +52,10 @@ typedef enum {
     GPM_OK = 0,
     GPM_EINVAL = 1,     /* bad argument, shape, parameter or call order */
     GPM_ENOMEM = 2,     /* the allocator callback returned NULL */
-    GPM_ECUDA = 3,      /* a CUDA runtime call failed */
-    GPM_ETIMEOUT = 4,   /* a bounded device wait gave up */
-    GPM_EBUSY = 5,      /* no free slot / HBM budget exhausted */
-    GPM_EINTERNAL = 6   /* a device-side consistency check failed */
+    GPM_ECUDA = 3,      /* a CUDA runtime call failed (or no CUDA device) */
+                        /* 4 is not used */
+    GPM_EBUSY = 5,      /* the context would exceed its HBM budget */
+    GPM_EINTERNAL = 6   /* a device-side consistency check failed (reported by gpm_sync) */
 } gpm_status;
 
 /* storage type of the frames inside the context (arithmetic is FP32) */
@@ -119,8 +121,12 @@ void gpm_default_params(gpm_params* p);
 
 /* Creates a context for up to limits->max_pairs pairs of at most
    max_width x max_height.  stream: a cudaStream_t (NULL = legacy default).
-   Errors: GPM_EINVAL (bad params or limits), GPM_ENOMEM, GPM_EBUSY (budget),
-   GPM_ECUDA.  *out is NULL on error. */
+   Order of the checks: GPM_EINVAL (bad params or limits); GPM_EBUSY when
+   gpm_required_bytes exceeds a non-zero hbm_budget_bytes (nothing is
+   allocated and no CUDA call is made); GPM_ENOMEM when the allocator
+   callback (or cudaMallocAsync) returns NULL -- what was allocated is freed
+   through free_fn; GPM_ECUDA when no CUDA device answers.  *out is NULL on
+   error. */
 gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_alloc_fn alloc,
                       gpm_free_fn free_fn, void* user, void* stream, gpm_ctx** out);
 
@@ -156,7 +162,12 @@ gpm_status gpm_fit_planes(gpm_ctx* ctx, int32_t n_pairs, int32_t level);
 gpm_status gpm_flow_and_occlusion(gpm_ctx* ctx, int32_t n_pairs, float* const* flow_out,
                                   uint8_t* const* occ_out);
 
-/* Waits for the context's stream and reports any pending device error. */
+/* Waits for the context's stream and reports any pending device error:
+   GPM_ECUDA for a CUDA error, GPM_EINTERNAL when a device consistency check
+   failed since the last gpm_sync (an imported label named a model id outside
+   [-1, m) or carried a non-finite flow: that pixel was set to no plane, so
+   nothing read outside the model table).  The flag is cleared when reported,
+   and the context stays usable. */
 gpm_status gpm_sync(gpm_ctx* ctx);
 
 /* ---- state export / import (parity checks, resume at a level boundary) ----
@@ -213,14 +224,36 @@ gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_
 
 /* ---- measurement ----
    With profiling on, every kernel launch of the context is bracketed by CUDA
-   events on the context's stream, and the PatchMatch kernels count the
-   candidate offsets they evaluate (one evaluation = one (2r+1)^2-tap,
-   3-channel patch cost) and RANSAC counts its residual tests (scored
-   hypotheses x window matches).  gpm_profile_read synchronises the stream,
-   returns per kernel class the summed device milliseconds and the launch
-   count, and the counts [PatchMatch evaluations at level 0, at levels >= 1,
-   RANSAC residual tests], then clears them.  Host arrays:
-   ms[GPM_PROF_CLASSES], launches[GPM_PROF_CLASSES], evals[3]. */
+   events on the context's stream, and the kernels count their work (counts
+   on request only, see gpm_profile_select):
+     GPM_COUNT_SWEEP0         candidate offsets evaluated by the level-0
+                              sweeps (one evaluation = one (2r+1)^2-tap,
+                              3-channel patch cost, possibly abandoned);
+     GPM_COUNT_SWEEP_PLANE    the same for the restricted, plane-distorted
+                              sweeps of levels >= 1;
+     GPM_COUNT_RANSAC         RANSAC residual tests (scored hypotheses x
+                              window matches);
+     GPM_COUNT_INIT           evaluations of the initial field and recosts;
+     GPM_COUNT_SWEEP0_TAPS    taps the level-0 sweep evaluations actually
+                              summed (an abandoned evaluation stops early);
+     GPM_COUNT_SWEEP_PLANE_TAPS  the same for the plane-level sweeps;
+     GPM_COUNT_SWEEP0_PRUNED  level-0 sweep candidates rejected without any
+                              tap by the patch-sum lower bound (not counted
+                              as evaluations).
+   gpm_profile_read synchronises the stream, returns per kernel class the
+   summed device milliseconds and the launch count, and the GPM_COUNTERS
+   counts, then clears them.  Host arrays: ms[GPM_PROF_CLASSES],
+   launches[GPM_PROF_CLASSES], counts[GPM_COUNTERS]. */
+enum {
+    GPM_COUNT_SWEEP0 = 0,
+    GPM_COUNT_SWEEP_PLANE = 1,
+    GPM_COUNT_RANSAC = 2,
+    GPM_COUNT_INIT = 3,
+    GPM_COUNT_SWEEP0_TAPS = 4,
+    GPM_COUNT_SWEEP_PLANE_TAPS = 5,
+    GPM_COUNT_SWEEP0_PRUNED = 6,
+    GPM_COUNTERS = 7
+};
 enum {
     GPM_PROF_INGEST = 0,
     GPM_PROF_PM_INIT = 1,
@@ -246,26 +279,47 @@ gpm_status gpm_profile_enable(gpm_ctx* ctx, int32_t enable);
 gpm_status gpm_profile_select(gpm_ctx* ctx, uint32_t class_mask, int32_t count_evals);
 gpm_status gpm_profile_read(gpm_ctx* ctx, double* ms, uint64_t* launches, uint64_t* evals);
 
+/* ---- measurement aid ----
+   The paper has no counterpart to this call.  It launches, on `stream`,
+   `blocks` blocks of 256 threads, each thread running 8 independent chains
+   of iters x 64 FP32 fused multiply-adds, and writes one float per thread to
+   sink (a DEVICE buffer of blocks x 256 floats).  One launch executes
+   blocks x 256 x iters x 512 FP32 lane operations; timed with CUDA events
+   on the same stream it measures the FP32 lane-operation peak that the
+   PatchMatch kernels' ALU roofline is quoted against.  GPM_EINVAL for
+   blocks or iters outside 1..2^20 or a NULL sink, GPM_ECUDA if the launch
+   fails (an error earlier work left pending is reported too). */
+gpm_status gpm_fp32_peak_probe(int32_t blocks, int32_t iters, float* sink, void* stream);
+
 /* ---- ingest without allocation ----
-   The paper has no counterpart to this call: it serves callers that cannot
-   call cudaMalloc -- code inside a CUDA stream capture, hosts whose device
-   memory is fixed up front, plugins of frameworks that own the memory pool.
-   It converts one frame pair exactly as gpm_match(level 0) ingests it:
-   frame1/frame2 are DEVICE buffers, height x width x 3 FP32 (HWC, row stride
-   in elements); out1/out2 are caller-owned DEVICE buffers of width x height
-   RGBX texels in `storage` (GPM_F32: 16 bytes each, GPM_F16 / GPM_BF16:
-   8 bytes); with gain_normalize, frame 2 is scaled by mean(I1) / mean(I2).
-   It allocates nothing: its scratch is a static device array sized for at
-   most 4096 rows (64 KiB, held on every GPU that loads the library until the
-   process exits).  Returns GPM_EINVAL for NULL pointers, bad sizes or a frame
-   taller than 4096 rows, GPM_ECUDA if a CUDA call fails.  The first call on a
-   device looks up the array's device address (once per device); make that
-   first call before any stream capture.  All calls share the array: calls
-   that overlap on the GPU (unordered streams) race, so order them.
-   stream: a cudaStream_t (NULL = legacy default). */
+   The paper has no counterpart to this call.  It serves callers that must
+   not allocate device memory when they ingest a pair: real-time and embedded
+   hosts whose device memory is reserved once at start-up, plugins of
+   frameworks that own the device memory pool and forbid allocations behind
+   their back, and latency-critical loops where cudaMalloc (and the
+   synchronisation it can bring) is not allowed.
+   It runs the ingest of gpm_match(level 0) -- the same kernels on the same
+   grid, so the output is bitwise the same: frame1/frame2 are DEVICE
+   buffers, height x width x 3 FP32 (HWC, row stride in elements); out1/out2
+   are caller-owned DEVICE buffers of width x height RGBX texels in `storage`
+   (GPM_F32: 16 bytes each, GPM_F16 / GPM_BF16: 8 bytes); with equalize, each
+   frame's HSV value histogram is equalised first (Sec. 4.2); with
+   gain_normalize, frame 2 is then scaled by mean(I1) / mean(I2).
+   It allocates nothing: its scratch is one static device array of 6.25 KiB
+   (partial sums, the gain, the histograms and tables), held on every GPU that
+   loads the library until the process exits.  Frames up to 32767 x 32767
+   and 2^26 pixels (the largest frame a context takes); larger ones, NULL
+   pointers, a row stride below 3 * width or a bad storage / equalize value
+   return GPM_EINVAL before anything is enqueued.  GPM_ECUDA if a CUDA call
+   fails; an error that earlier work left pending in the CUDA runtime is
+   reported and cleared by this call too.  The first call on a device looks
+   up the array's device address (once per device, with that device
+   current); make that first call before any stream capture.  All calls share
+   the array: calls that overlap on the GPU (unordered streams) race, so
+   order them.  stream: a cudaStream_t (NULL = legacy default). */
 gpm_status gpm_ingest_noalloc(const float* frame1, const float* frame2, int32_t width, int32_t height,
-                              int64_t row_stride, int32_t gain_normalize, int32_t storage, void* out1, void* out2,
-                              void* stream);
+                              int64_t row_stride, int32_t gain_normalize, int32_t equalize, int32_t storage,
+                              void* out1, void* out2, void* stream);
 
 /* Human-readable status name and the context's last error message. */
 const char* gpm_status_string(gpm_status s);

@@ -122,12 +122,31 @@ def lib() -> C.CDLL:
             "orc_interp_seeds": (None, [pp, i32, i32, i32]),
             "orc_interp_flow": (None, [pp, d, i32, d, d, i32, P(C.c_float)]),
             "orc_run": (None, [pp, d, d, C.c_void_p, C.c_int]),
+            "orc_eval_count": (C.c_longlong, [C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(_lib, name)
             f.restype = res
             f.argtypes = args
     return _lib
+
+
+def eval_count(reset: bool = True) -> int:
+    """Patch costs the oracle evaluated since the last reset (timing instrumentation)."""
+    return int(lib().orc_eval_count(1 if reset else 0))
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops (results do not depend on it)."""
+    import ctypes.util
+    gomp = C.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
+    gomp.omp_set_num_threads(int(n))
+
+
+def max_threads() -> int:
+    import ctypes.util
+    gomp = C.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
+    return int(gomp.omp_get_max_threads())
 
 
 def _p(a: np.ndarray | None, ct):

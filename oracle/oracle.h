@@ -90,6 +90,8 @@ int orc_total_cells(const orc_params* P, int32_t* cell_base /* [num_scales+1] or
 
 /* ---- sampling and patch cost (eq. 2-3, patches warped by a plane) ---- */
 void orc_sample_bilinear(const double* img, int W, int H, double X, double Y, double out[3]);
+/* patch costs evaluated since the last reset (timing instrumentation) */
+long long orc_eval_count(int reset);
 double orc_patch_cost(const orc_params* P, const double* src, const double* tgt,
                       int px, int py, int vx, int vy, const double* G /* NULL = identity */);
 

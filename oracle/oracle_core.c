@@ -121,9 +121,25 @@ static inline void apply_h(const double* G, double x, double y, double* X, doubl
 /* square patch moved by the candidate offset v and distorted by the plane G */
 /* (identity: the ordinary square patch of PatchMatch).                     */
 /* ------------------------------------------------------------------------ */
+/* Patch costs evaluated since the last reset (instrumentation for the timed
+   CPU baseline; not part of the method). */
+static long long orc_evals_;
+long long orc_eval_count(int reset) {
+    long long v;
+#pragma omp atomic read
+    v = orc_evals_;
+    if (reset) {
+#pragma omp atomic write
+        orc_evals_ = 0;
+    }
+    return v;
+}
+
 double orc_patch_cost(const orc_params* P, const double* src, const double* tgt,
                       int px, int py, int vx, int vy, const double* G) {
     const int W = P->W, H = P->H, r = P->r;
+#pragma omp atomic
+    orc_evals_++;
     if (P->census && !G) { /* census code frames: Hamming distance per tap (Sec. 6) */
         long long sum = 0;
         for (int dy = -r; dy <= r; ++dy)

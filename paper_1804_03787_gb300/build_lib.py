@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libgpm.so")
-SOURCES = ["kernels_pm.cu", "kernels_planes.cu", "gpm.cu", "noalloc.cu"]
+SOURCES = ["kernels_pm.cu", "kernels_planes.cu", "gpm.cu", "noalloc.cu", "measure.cu"]
 HEADERS = ["common.cuh", "kernels.h", "hyp_exact.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -82,6 +82,66 @@ __device__ __forceinline__ float4 ldpix<2>(const void* base, int i) {
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The raw texel type of a storage type, and loads of texels held in shared memory.
+template <int ST>
+struct TexelOf {
+    using type = uint2;
+};
+template <>
+struct TexelOf<0> {
+    using type = float4;
+};
+template <int ST>
+__device__ __forceinline__ float4 ldpix_shared(const void* base, int i);
+template <>
+__device__ __forceinline__ float4 ldpix_shared<0>(const void* base, int i) {
+    return reinterpret_cast<const float4*>(base)[i];
+}
+template <>
+__device__ __forceinline__ float4 ldpix_shared<1>(const void* base, int i) {
+    const uint2 u = reinterpret_cast<const uint2*>(base)[i];
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 ldpix_shared<2>(const void* base, int i) {
+    const uint2 u = reinterpret_cast<const uint2*>(base)[i];
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// A texel at a shared-memory byte address (a 32-bit shared-window address, as from __cvta_generic_to_shared).
+template <int ST>
+__device__ __forceinline__ float4 ldpix_shared_addr(unsigned addr);
+template <>
+__device__ __forceinline__ float4 ldpix_shared_addr<0>(unsigned addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+template <int ST>
+__device__ __forceinline__ uint2 ld_shared_u2(unsigned addr) {
+    uint2 u;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(u.x), "=r"(u.y) : "r"(addr));
+    return u;
+}
+template <>
+__device__ __forceinline__ float4 ldpix_shared_addr<1>(unsigned addr) {
+    const uint2 u = ld_shared_u2<1>(addr);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 ldpix_shared_addr<2>(unsigned addr) {
+    const uint2 u = ld_shared_u2<2>(addr);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // Bilinear blend of the four texels around a point with fractions (fx, fy).
 __device__ __forceinline__ float3 blend4(float4 a, float4 b, float4 c, float4 d, float fx, float fy) {
     const float gx = 1.f - fx, gy = 1.f - fy;
@@ -385,6 +445,7 @@ struct PairView {
     uint32_t pair_id;
     const void* img[2];   // ingested I1, I2 (RGBX in storage type)
     const void* imgp[2];  // the same, (W + 2 kPad) x (H + 2 kPad) with replicated borders (level-0 PatchMatch)
+    float4* box[2];       // per pixel, the RGB sums over its square patch of clamped taps (level-0 lower bound)
     int Wp;               // row length of imgp
     int2* nnf[2];
     float* cost[2];
@@ -397,6 +458,7 @@ struct PairView {
     int* mi[2];           // [m][kMI]
     int* list[2];         // unfrozen pixel indices, colour 0 then colour 1
     int* list_count;      // [2 dirs][2 colours]
+    int* flag;            // device consistency flag: set (non-zero) by a check that failed, read by gpm_sync
     unsigned long long* m2o_key[2];
     RefitWork* rw[2];     // [cells of the largest level]
     uint32_t* code[2];    // census codes of each frame (census data term)

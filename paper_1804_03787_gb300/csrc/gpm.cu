@@ -69,7 +69,7 @@ struct gpm_ctx {
 
 namespace {
 
-const int kPartialBlocks = 128;
+const int kPartialBlocks = kIngestPartialBlocks;
 
 cudaEvent_t take_event(gpm_ctx* c) {
     if (c->pool.empty()) {
@@ -179,6 +179,7 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_np, int max_models, i
     PairView pv{};
     for (int d = 0; d < 2; ++d) pv.img[d] = take(n * texel);
     for (int d = 0; d < 2; ++d) pv.imgp[d] = take((size_t)max_np * texel);
+    for (int d = 0; d < 2; ++d) pv.box[d] = (float4*)take(n * sizeof(float4));
     for (int d = 0; d < 2; ++d) {
         pv.nnf[d] = (int2*)take(n * sizeof(int2));
         pv.cost[d] = (float*)take(n * sizeof(float));
@@ -201,13 +202,14 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_np, int max_models, i
         pv.code[d] = (uint32_t*)take(n * sizeof(uint32_t));
     }
     pv.list_count = (int*)take(4 * sizeof(int));
+    pv.flag = (int*)take(sizeof(int));
     pv.gq = (int*)take(n * sizeof(int));
     LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
     double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
     double* gain = (double*)take(sizeof(double));
     int* eq_hist = (int*)take(2 * 256 * sizeof(int));
     float* eq_lut = (float*)take(2 * 256 * sizeof(float));
-    unsigned long long* evals = (unsigned long long*)take(3 * sizeof(unsigned long long));
+    unsigned long long* evals = (unsigned long long*)take(GPM_COUNTERS * sizeof(unsigned long long));
     if (s) {
         s->d_evals = evals;
         s->pv = pv;
@@ -412,18 +414,12 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
     c->free_fn = free_fn;
     c->user = user;
     c->stream = (cudaStream_t)stream;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        cudaGetLastError();
-        delete c;
-        return GPM_ECUDA;
-    }
     c->max_n = limits->max_width * limits->max_height;
     c->max_models = std::max(2, 2 * total_cells_for(*params, limits->max_width, limits->max_height, nullptr));
     c->max_cells = max_level_cells_for(*params, limits->max_width, limits->max_height);
     c->max_np = (limits->max_width + 2 * kPad) * (limits->max_height + 2 * kPad);
     c->slot_bytes = layout_slot(*params, c->max_n, c->max_np, c->max_models, c->max_cells, nullptr, nullptr);
+    // the budget is checked before anything is allocated or any CUDA call is made
     if (limits->hbm_budget_bytes && c->slot_bytes * (size_t)limits->max_pairs > limits->hbm_budget_bytes) {
         delete c;
         return GPM_EBUSY;
@@ -443,6 +439,19 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
         }
         s.block = p;
         layout_slot(*params, c->max_n, c->max_np, c->max_models, c->max_cells, (char*)p, &s);
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        gpm_destroy(c);
+        return GPM_ECUDA;
+    }
+    // the device consistency flags start clear
+    for (auto& s : c->slots) cudaMemsetAsync(s.pv.flag, 0, sizeof(int), c->stream);
+    if (cuda_check(c, "gpm_create") != GPM_OK) {
+        gpm_destroy(c);
+        return GPM_ECUDA;
     }
     *out = c;
     return GPM_OK;
@@ -505,12 +514,13 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
                 launch_grey_q(p.frame1, p.width, p.height, p.row_stride, s.pv.gq, c->stream);
                 pend(c);
             }
-            pbeg(c, GPM_PROF_INGEST, c->P.equalize ? 7 : 5);
+            pbeg(c, GPM_PROF_INGEST, (c->P.equalize ? 7 : 5) + (c->P.census ? 0 : 1));
             launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
                           s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
                           const_cast<void*>(s.pv.img[1]), c->P.equalize ? s.eq_hist : nullptr,
                           c->P.equalize ? s.eq_lut : nullptr, c->stream);
             launch_pad_frames(s.pv, c->P.storage, grid_for(c, s.pv.Wp * (s.H + 2 * kPad)), c->stream);
+            if (!c->P.census) launch_box_sums(s.pv, c->P.patch_radius, c->P.storage, grid_for(c, s.n), c->stream);
             reset_models(c, s);
             launch_reset_labels(s.pv, c->P.eps, grid_for(c, s.n), c->stream);
             pend(c);
@@ -595,6 +605,23 @@ gpm_status gpm_sync(gpm_ctx* c) {
     if (!c) return GPM_EINVAL;
     const cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(c, GPM_ECUDA, std::string("sync: ") + cudaGetErrorString(e));
+    gpm_status st = cuda_check(c, "gpm_sync");
+    if (st != GPM_OK) return st;
+    // device consistency flags: read, then cleared so that the context stays usable
+    int bad = 0;
+    for (auto& s : c->slots) {
+        if (!s.block) continue;
+        int f = 0;
+        if (cudaMemcpy(&f, s.pv.flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_check(c, "gpm_sync");
+        if (f) {
+            bad |= f;
+            cudaMemset(s.pv.flag, 0, sizeof(int));
+        }
+    }
+    if (bad)
+        return fail(c, GPM_EINTERNAL,
+                    "device consistency check: imported labels named a model outside the model table or a "
+                    "non-finite flow (those pixels were set to no plane)");
     return cuda_check(c, "gpm_sync");
 }
 
@@ -718,7 +745,7 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
             a = (a + 7) / 8 * 8;
             const double* iF = (const double*)(d + a);
             for (int k = 0; k < 2; ++k) {
-                launch_labels_import(s.pv.acc[k], s.n, im + k * n, iL + k * n, iF + k * n * 2, st);
+                launch_labels_import(s.pv.acc[k], s.n, s.m, im + k * n, iL + k * n, iF + k * n * 2, s.pv.flag, st);
                 c->launches += 1;
             }
             // frozen pixels and the restricted PatchMatch lists follow the accumulated map
@@ -743,7 +770,7 @@ gpm_status gpm_profile_select(gpm_ctx* c, uint32_t class_mask, int32_t count_eva
     c->prof_mask = class_mask;
     for (auto& s : c->slots) {
         s.pv.evals = count_evals ? s.d_evals : nullptr;
-        if (count_evals) cudaMemsetAsync(s.d_evals, 0, 3 * sizeof(unsigned long long), c->stream);
+        if (count_evals) cudaMemsetAsync(s.d_evals, 0, GPM_COUNTERS * sizeof(unsigned long long), c->stream);
     }
     return cuda_check(c, "gpm_profile_select");
 }
@@ -770,16 +797,16 @@ gpm_status gpm_profile_read(gpm_ctx* c, double* ms, uint64_t* launches, uint64_t
         if (launches) launches[k] = c->prof_launches[k];
         c->prof_launches[k] = 0;
     }
-    uint64_t ev[3] = {0, 0, 0};
+    uint64_t ev[GPM_COUNTERS] = {};
     for (auto& s : c->slots) {
         if (!s.d_evals) continue;
-        unsigned long long h[3] = {0, 0, 0};
+        unsigned long long h[GPM_COUNTERS] = {};
         cudaMemcpy(h, s.d_evals, sizeof h, cudaMemcpyDeviceToHost);
-        for (int k = 0; k < 3; ++k) ev[k] += h[k];
+        for (int k = 0; k < GPM_COUNTERS; ++k) ev[k] += h[k];
         cudaMemset(s.d_evals, 0, sizeof h);
     }
     if (evals)
-        for (int k = 0; k < 3; ++k) evals[k] = ev[k];
+        for (int k = 0; k < GPM_COUNTERS; ++k) evals[k] = ev[k];
     return cuda_check(c, "gpm_profile_read");
 }
 
@@ -789,7 +816,6 @@ const char* gpm_status_string(gpm_status s) {
         case GPM_EINVAL: return "GPM_EINVAL";
         case GPM_ENOMEM: return "GPM_ENOMEM";
         case GPM_ECUDA: return "GPM_ECUDA";
-        case GPM_ETIMEOUT: return "GPM_ETIMEOUT";
         case GPM_EBUSY: return "GPM_EBUSY";
         case GPM_EINTERNAL: return "GPM_EINTERNAL";
     }

@@ -17,12 +17,17 @@ struct PmLaunch {
     uint32_t k0, k1;
 };
 void launch_pm(const PmLaunch& L, cudaStream_t st);
+// Blocks of the FP64 frame sums behind the gain (a fixed grid, so a fixed summation order): partial holds
+// 2 * kIngestPartialBlocks doubles.
+constexpr int kIngestPartialBlocks = 128;
 // eq_hist / eq_lut (2 x 256 each, device) non-null: HSV histogram equalisation of both frames first (Sec. 4.2).
 void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
                    double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
                    cudaStream_t st);
 // Padded copies of both ingested frames (imgp), borders replicating the edges.
 void launch_pad_frames(const PairView& pv, int storage, int grid_blocks, cudaStream_t st);
+// Patch sums of both ingested frames (pv.box), after launch_pad_frames: the level-0 sweep's lower bound.
+void launch_box_sums(const PairView& pv, int radius, int storage, int grid_blocks, cudaStream_t st);
 void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st);
 // Census codes of both input frames (k1, k2: n int64 of scratch each).
 void launch_census(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1, long long* k2,
@@ -68,6 +73,9 @@ void launch_fill_seeds(const PairView& pv, const int* q, long long* dist, int* s
 // geoms: DEVICE array of nlev level geometries
 void launch_import_models(const PairView& pv, const LevelGeom* geoms, int nlev, int m, cudaStream_t st);
 void launch_labels_export(const Labels& l, int n, int* om, float* oL, double* of, cudaStream_t st);
-void launch_labels_import(const Labels& l, int n, const int* im, const float* iL, const double* iF, cudaStream_t st);
+// Imported labels are checked: a model id outside [-1, m) or a non-finite or huge flow sets *flag and the pixel
+// gets no plane (so no later kernel reads outside the model table).
+void launch_labels_import(const Labels& l, int n, int m, const int* im, const float* iL, const double* iF, int* flag,
+                          cudaStream_t st);
 
 }  // namespace gpm

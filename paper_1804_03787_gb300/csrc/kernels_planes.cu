@@ -1359,14 +1359,27 @@ __global__ void k_labels_export(Labels l, int n, int* om, float* oL, double* of)
         of[2 * i + 1] = (double)l.v[i].y + (double)l.r[i].y;
     }
 }
-__global__ void k_labels_import(Labels l, int n, const int* im, const float* iL, const double* iF) {
+__global__ void k_labels_import(Labels l, int n, int m, const int* im, const float* iL, const double* iF,
+                                int* flag) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        l.m[i] = im[i];
-        l.L[i] = iL[i];
+        int id = im[i];
         const double fx = iF[2 * i], fy = iF[2 * i + 1];
-        const double vx = floor(fx + 0.5), vy = floor(fy + 0.5);
-        l.v[i] = make_int2((int)vx, (int)vy);
-        l.r[i] = make_float2((float)(fx - vx), (float)(fy - vy));
+        // |flow| < 2^30 (and finite): the rounded offset fits an int
+        const bool flow_ok = fabs(fx) < 1073741824.0 && fabs(fy) < 1073741824.0;
+        if (id < -1 || id >= m || (id >= 0 && !flow_ok)) {
+            *flag = 1;
+            id = -1;
+        }
+        l.m[i] = id;
+        l.L[i] = iL[i];
+        if (flow_ok) {
+            const double vx = floor(fx + 0.5), vy = floor(fy + 0.5);
+            l.v[i] = make_int2((int)vx, (int)vy);
+            l.r[i] = make_float2((float)(fx - vx), (float)(fy - vy));
+        } else {
+            l.v[i] = make_int2(0, 0);
+            l.r[i] = make_float2(0.f, 0.f);
+        }
     }
 }
 
@@ -1535,8 +1548,9 @@ void launch_import_models(const PairView& pv, const LevelGeom* geoms, int nlev, 
 void launch_labels_export(const Labels& l, int n, int* om, float* oL, double* of, cudaStream_t st) {
     k_labels_export<<<(n + 255) / 256, 256, 0, st>>>(l, n, om, oL, of);
 }
-void launch_labels_import(const Labels& l, int n, const int* im, const float* iL, const double* iF, cudaStream_t st) {
-    k_labels_import<<<(n + 255) / 256, 256, 0, st>>>(l, n, im, iL, iF);
+void launch_labels_import(const Labels& l, int n, int m, const int* im, const float* iL, const double* iF, int* flag,
+                          cudaStream_t st) {
+    k_labels_import<<<(n + 255) / 256, 256, 0, st>>>(l, n, m, im, iL, iF, flag);
 }
 
 }  // namespace gpm

@@ -372,15 +372,15 @@ __device__ __forceinline__ bool interior_of(const LanePatch<R>& lp, int2 c) {
 // |difference|.  The NNF cost buffer holds these sums (strict-less decisions
 // compare them directly); the exported cost is the sum divided by 3T.
 // The warp's total of the lanes' tap sums: each lane's sum rounded to a
-// multiple of 2^-24 and the integers added exactly by one redux, so every
-// lane gets the same bits.  A lane's sum is below 9 (three taps of three
-// channels in [0, 1]), so the total stays below 2^32; it is within
-// 32 * 2^-25 of the exact total of the lane sums, about the rounding of a
-// float butterfly, and costs one reduction instead of five dependent
-// shuffles and additions.
-__device__ __forceinline__ float warp_sum_q24(float s) {
-    const unsigned q = __float2uint_rn(s * 16777216.f);
-    return (float)__reduce_add_sync(FULL, q) * 5.9604644775390625e-08f;
+// multiple of 2^-23 and the integers added exactly by one redux, so every
+// lane gets the same bits.  A lane's sum is at most 18 (three taps of three
+// channels, each |difference| at most 2: frames in [0, 1], a gain below 2),
+// so the total of at most 243 channel terms stays below 2^32; it is within
+// 32 * 2^-24 = 2^-19 of the exact total of the lane sums, and costs one
+// reduction instead of five dependent shuffles and additions.
+__device__ __forceinline__ float warp_sum_q23(float s) {
+    const unsigned q = __float2uint_rn(s * 8388608.f);
+    return (float)__reduce_add_sync(FULL, q) * 1.1920928955078125e-07f;
 }
 
 template <int R, int ST, bool IN>
@@ -392,7 +392,7 @@ __device__ __forceinline__ float patch_sum_in(const LanePatch<R>& lp, const void
         const int t = lane + 32 * j;
         if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST, IN>(lp, tgt, W, H, j, c, off));
     }
-    return warp_sum_q24(s);
+    return warp_sum_q23(s);
 }
 template <int R, int ST>
 __device__ __forceinline__ float patch_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int px, int py,
@@ -441,7 +441,7 @@ __device__ __forceinline__ bool census_sum(const LanePatch<R>& lp, const uint32_
 // Integer threshold for the abandon test of tap_sum: with thr the best raw
 // sum so far, returns ceil(thr * 2^19 * (1 + 2^-21)) + 1.  A partial bound at
 // or above it means the exact total of the lane sums is at least
-// thr (1 + 2^-21) + 2^-19; the final sum (warp_sum_q24) is within 2^-20 of
+// thr (1 + 2^-21) + 2^-19; the final sum (warp_sum_q23) is within 2^-19 of
 // that total and then rounded to a float, so it stays above thr.
 __device__ __forceinline__ int abandon_threshold(float thr) {
     return __float2int_ru(__fmul_ru(thr * 524288.f, 1.f + 4.76837158203125e-07f)) + 1;
@@ -460,7 +460,7 @@ __device__ __forceinline__ int abandon_threshold(float thr) {
 // same as patch_sum's.
 template <int R, int ST, bool IN, bool EVERY_CHUNK>
 __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
-                                        float& sum, int lane) {
+                                        float& sum, int& nch, int lane) {
     const int off = c.y * W + c.x;
     float s = 0.f;
 #pragma unroll
@@ -472,19 +472,23 @@ __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* t
             // mantissa of 2^23
             const unsigned q =
                 (unsigned)(__float_as_int(__fadd_rz(fminf(s * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
-            if ((int)__reduce_add_sync(FULL, q) >= ithr) return false;
+            if ((int)__reduce_add_sync(FULL, q) >= ithr) {
+                nch = j + 1;
+                return false;
+            }
         }
-        if (j + 1 == Patch<R>::NT) sum = warp_sum_q24(s);
+        if (j + 1 == Patch<R>::NT) sum = warp_sum_q23(s);
     }
+    nch = Patch<R>::NT;
     return true;
 }
 // EVERY_CHUNK: test the bound after every chunk but the last (plane levels, where a chunk costs four gathers per
 // tap); otherwise after the first chunk only (square patches, where a further test costs about what it saves).
 template <int R, int ST, bool EVERY_CHUNK>
 __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
-                                        float& sum, int lane) {
-    return interior_of<R>(lp, c) ? tap_sum_in<R, ST, true, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, lane)
-                                 : tap_sum_in<R, ST, false, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, lane);
+                                        float& sum, int& nch, int lane) {
+    return interior_of<R>(lp, c) ? tap_sum_in<R, ST, true, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, nch, lane)
+                                 : tap_sum_in<R, ST, false, EVERY_CHUNK>(lp, tgt, W, H, c, ithr, sum, nch, lane);
 }
 
 // Two candidates at once: each one's taps are accumulated per lane in the
@@ -496,10 +500,12 @@ __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt,
 // give the result of evaluating the two one after the other.
 template <int R, int ST, bool IN, bool EVERY_CHUNK>
 __device__ __forceinline__ void tap_sum2_in(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c1, int2 c2,
-                                            int ithr, float& sum1, float& sum2, bool& ok1, bool& ok2, int lane) {
+                                            int ithr, float& sum1, float& sum2, bool& ok1, bool& ok2, int& ntap,
+                                            int lane) {
     const int off1 = c1.y * W + c1.x, off2 = c2.y * W + c2.x;
     float s1 = 0.f, s2 = 0.f;
     ok1 = ok2 = true;
+    ntap = 0;
 #pragma unroll
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
@@ -515,13 +521,17 @@ __device__ __forceinline__ void tap_sum2_in(const LanePatch<R>& lp, const void* 
                 (unsigned)(__float_as_int(__fadd_rz(fminf(s1 * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
             const unsigned q2 =
                 (unsigned)(__float_as_int(__fadd_rz(fminf(s2 * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
+            const bool was1 = ok1, was2 = ok2;
             if (ok1) ok1 = (int)__reduce_add_sync(FULL, q1) < ithr;
             if (ok2) ok2 = (int)__reduce_add_sync(FULL, q2) < ithr;
+            // taps summed by a candidate abandoned here, for the work counters
+            ntap += ((was1 && !ok1) + (was2 && !ok2)) * min(32 * (j + 1), Patch<R>::T);
             if (!ok1 && !ok2) return;
         }
     }
-    if (ok1) sum1 = warp_sum_q24(s1);
-    if (ok2) sum2 = warp_sum_q24(s2);
+    ntap += (ok1 ? Patch<R>::T : 0) + (ok2 ? Patch<R>::T : 0);
+    if (ok1) sum1 = warp_sum_q23(s1);
+    if (ok2) sum2 = warp_sum_q23(s2);
 }
 __device__ __forceinline__ unsigned lanemask_lt(int lane) { return (1u << lane) - 1u; }
 
@@ -571,8 +581,8 @@ __device__ __forceinline__ void patch_sum_pair_in(const LanePatch<R>& l1, const 
             s2 += absdiff3(l2.a[j], v2);
         }
     }
-    sum1 = warp_sum_q24(s1);
-    sum2 = warp_sum_q24(s2);
+    sum1 = warp_sum_q23(s1);
+    sum2 = warp_sum_q23(s2);
 }
 
 template <int R, int ST, bool CENSUS>
@@ -604,7 +614,7 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
                 pv.cost[dir][i] = s1;
                 pv.nnf[dir][i2] = c2;
                 pv.cost[dir][i2] = s2;
-                if (pv.evals) atomicAdd(&pv.evals[0], i2 != i ? 2ull : 1ull);
+                if (pv.evals) atomicAdd(&pv.evals[GPM_COUNT_INIT], i2 != i ? 2ull : 1ull);
             }
         }
         return;
@@ -627,7 +637,7 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
         if (lane == 0) {
             pv.nnf[dir][i] = make_int2(vx, vy);
             pv.cost[dir][i] = c;
-            if (pv.evals) atomicAdd(&pv.evals[0], 1ull);
+            if (pv.evals) atomicAdd(&pv.evals[GPM_COUNT_INIT], 1ull);
         }
     }
 }
@@ -666,10 +676,63 @@ __global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int
             }
             if (lane == 0) {
                 pv.cost[dir][i] = c;
-                if (pv.evals) atomicAdd(&pv.evals[level > 0], 1ull);
+                if (pv.evals) atomicAdd(&pv.evals[GPM_COUNT_INIT], 1ull);
             }
         }
     }
+}
+
+// ---------------------------------------------------------------- patch-sum lower bound (level 0)
+// For a pixel p whose patch stays inside the frame and an offset c whose
+// target pixel is in the frame, the raw cost is
+// sum_t sum_ch |a - b| >= sum_ch |sum_t a - sum_t b| = LB, the sums read from
+// the frames' box images (k_box_sums).  A candidate is dropped, without a
+// tap, when LB_f - m >= bc (1 + 2^-16) + 2^-18, which allows for rounding on
+// both sides: the computed cost C_f is at least C (1 - 2^-18) - 2^-19 (FP32
+// sums of at most 9 terms per lane, the 2^-23 rounding of 32 lane sums, one
+// conversion), and the exact LB is at least the computed one minus
+// m = 2^-19 (sum of both boxes' channels) (each box sum carries at most 16
+// FP32 roundings of its own size, then six FP32 operations), so the test
+// implies C_f >= bc: the candidate could not be strictly cheaper.
+__device__ __forceinline__ float box_lb(float4 b1, float4 b2) {
+    const float lb = fabsf(b1.x - b2.x) + fabsf(b1.y - b2.y) + fabsf(b1.z - b2.z);
+    const float m = 1.9073486328125e-06f * (((b1.x + b1.y) + b1.z) + ((b2.x + b2.y) + b2.z));
+    return lb - m;
+}
+__device__ __forceinline__ float box_threshold(float bc) {
+    return fmaf(bc, 1.52587890625e-05f, bc) + 3.814697265625e-06f;
+}
+
+// Level-0 tiles of the sweep: 8 x 8 pixels of one colour, 16 x 8 image pixels; the staged source region is the
+// tile grown by r, in rows of TW texels (TW congruent to 2r + 1 modulo 8, so that eight consecutive taps of a
+// patch fall on eight distinct 16-byte bank groups).
+template <int R>
+struct Tile0 {
+    static constexpr int TX = 16, TY = 8;
+    static constexpr int TW0 = TX + 2 * R;
+    static constexpr int TW = TW0 + ((2 * R + 1 - TW0) % 8 + 8) % 8;
+    static constexpr int TH = TY + 2 * R;
+};
+
+// load_patch for a square colour patch whose source texels are staged in shared memory (tile origin (x0, y0) in
+// image coordinates, row length TW): the same taps, target indices into the padded copy (row length Wp).
+template <int R, int ST, int TW>
+__device__ __forceinline__ void load_patch_tile(LanePatch<R>& lp, const void* tile, int x0, int y0, int W, int H,
+                                                int px, int py, int lane, int Wp) {
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        const int t = lane + 32 * j;
+        const int tt = t < Patch<R>::T ? t : 0;
+        const int dy = tt / Patch<R>::D - R, dx = tt % Patch<R>::D - R;
+        lp.tx[j] = min(max(px + dx, 0), W - 1);
+        lp.ty[j] = min(max(py + dy, 0), H - 1);
+        lp.tidx[j] = (lp.ty[j] + kPad) * Wp + lp.tx[j] + kPad;
+        lp.a[j] = ldpix_shared<ST>(tile, (lp.ty[j] - y0 + R) * TW + lp.tx[j] - x0 + R);
+        lp.fx[j] = 0.f;
+        lp.fy[j] = 0.f;
+    }
+    set_interior_box(lp, max(px - R, 0), min(px + R, W - 1), max(py - R, 0), min(py + R, H - 1), W, H);
+    lp.warped = false;
 }
 
 // ---------------------------------------------------------------- sweep
@@ -697,6 +760,10 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
     constexpr bool PADDED = !PLANES && !CENSUS;
     const void* tgtp = PADDED ? pv.imgp[1 - dir] : tgt;
     const int Wt = PADDED ? pv.Wp : pv.W;
+    // square colour patches: each tile's source texels and their r-halo are staged in shared memory
+    using TL = Tile0<R>;
+    using Tex = typename TexelOf<ST>::type;
+    __shared__ Tex stile[PADDED ? TL::TH * TL::TW : 1];
     int2* __restrict__ nnf = pv.nnf[dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int hw = (W + 1) >> 1;
@@ -709,12 +776,29 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
     // Plane levels: the compacted pixel list, grid-strided.
     const int wid = threadIdx.x >> 5;
     const int ntx = (hw + 7) >> 3, ntiles = ntx * ((H + 7) >> 3);
+    unsigned npr = 0;  // candidates dropped by the patch-sum bound (counted by lane 0)
+    int x0t = 0, y0t = 0;
     for (int rnd = 0;; ++rnd) {
         int x, y, i;
         if (!PLANES) {
             const int tile = blockIdx.x + (rnd >> 3) * gridDim.x;
-            if (tile >= ntiles) break;
+            if (tile >= ntiles) break;  // block-uniform
             const int ty = tile / ntx, tx = tile - ty * ntx;
+            if (PADDED && (rnd & 7) == 0) {
+                // stage the tile's source region (padded-copy coordinates; entries past the padded edge are
+                // clamped and unused)
+                x0t = 16 * tx;
+                y0t = 8 * ty;
+                __syncthreads();
+                const Tex* sp = reinterpret_cast<const Tex*>(pv.imgp[dir]);
+                const int Wp = pv.Wp, Hp = H + 2 * kPad;
+                for (int e = threadIdx.x; e < TL::TH * TL::TW; e += blockDim.x) {
+                    const int ly = e / TL::TW, lx = e - ly * TL::TW;
+                    const int gx = min(x0t - R + lx + kPad, Wp - 1), gy = min(y0t - R + ly + kPad, Hp - 1);
+                    stile[e] = sp[gy * Wp + gx];
+                }
+                __syncthreads();
+            }
             y = 8 * ty + (rnd & 7);
             const int xh = 8 * tx + wid;
             if (y >= H || xh >= hw) continue;
@@ -729,7 +813,10 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
             x = i - y * W;
         }
         LanePatch<R> lp;
-        load_patch<R, ST, CENSUS>(lp, PADDED ? pv.imgp[dir] : src, W, H, x, y, lane, PADDED ? Wt : 0);
+        if (PADDED)
+            load_patch_tile<R, ST, TL::TW>(lp, stile, x0t, y0t, W, H, x, y, lane, Wt);
+        else
+            load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
         if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
@@ -737,7 +824,10 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
         int2 best = nnf[i];
         float bc = pv.cost[dir][i];  // raw sum of the incumbent
         int ithr = CENSUS ? 0 : abandon_threshold(bc);
-        int nev = 0;
+        int nev = 0, ntap = 0;
+        // square colour patches of pixels whose patch stays inside the frame: the patch-sum bound applies
+        const bool prune = PADDED && x >= R && y >= R && x < W - R && y < H - R;  // warp-uniform
+        const float4 b1 = prune ? pv.box[dir][i] : make_float4(0.f, 0.f, 0.f, 0.f);
         // list A
         int2 cand = make_int2(0, 0);
         bool ok = false;
@@ -770,6 +860,16 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                 }
             }
         }
+        if (prune) {
+            bool cut = false;
+            if (ok && !(cand.x == best.x && cand.y == best.y) &&
+                box_lb(b1, pv.box[1 - dir][i + cand.y * W + cand.x]) >= box_threshold(bc)) {
+                ok = false;
+                cut = true;
+            }
+            const unsigned cm = __ballot_sync(FULL, cut);
+            if (lane == 0) npr += __popc(cm);
+        }
         unsigned todo = fresh_lanes(ok, cand, best, lane);
 #pragma unroll 1
         for (int list_b = 0; list_b < 2; ++list_b) {
@@ -792,7 +892,18 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                 const int oy = (int)bounded_u32(wy, (uint32_t)(2 * Rk + 1)) - Rk;
                 const int tx = min(max(x + v0.x + ox, 0), W - 1), ty = min(max(y + v0.y + oy, 0), H - 1);
                 cand = make_int2(tx - x, ty - y);
-                todo = fresh_lanes(lane < nrad, cand, v0, lane);
+                bool okb = lane < nrad;
+                if (prune) {
+                    bool cut = false;
+                    if (okb && !(cand.x == v0.x && cand.y == v0.y) &&
+                        box_lb(b1, pv.box[1 - dir][i + cand.y * W + cand.x]) >= box_threshold(bc)) {
+                        okb = false;
+                        cut = true;
+                    }
+                    const unsigned cm = __ballot_sync(FULL, cut);
+                    if (lane == 0) npr += __popc(cm);
+                }
+                todo = fresh_lanes(okb, cand, v0, lane);
             }
             while (todo) {
                 const int l = __ffs(todo) - 1;
@@ -807,7 +918,9 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                         const int2 c2 = make_int2(__shfl_sync(FULL, cand.x, l2), __shfl_sync(FULL, cand.y, l2));
                         float s1 = 0.f, s2 = 0.f;
                         bool ok1, ok2;
-                        tap_sum2_in<R, ST, true, false>(lp, tgtp, Wt, H, c, c2, ithr, s1, s2, ok1, ok2, lane);
+                        int nt2;
+                        tap_sum2_in<R, ST, true, false>(lp, tgtp, Wt, H, c, c2, ithr, s1, s2, ok1, ok2, nt2, lane);
+                        ntap += nt2;
                         if (ok1 && s1 < bc) {
                             bc = s1;
                             best = c;
@@ -830,8 +943,11 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
                     }
                 } else {
                     float sum;
-                    const bool done = PADDED ? tap_sum_in<R, ST, true, false>(lp, tgtp, Wt, H, c, ithr, sum, lane)
-                                             : tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, lane);
+                    int nch;
+                    const bool done =
+                        PADDED ? tap_sum_in<R, ST, true, false>(lp, tgtp, Wt, H, c, ithr, sum, nch, lane)
+                               : tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, nch, lane);
+                    ntap += min(32 * nch, Patch<R>::T);
                     if (done && sum < bc) {
                         bc = sum;
                         best = c;
@@ -844,9 +960,14 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
         if (lane == 0) {
             nnf[i] = best;
             pv.cost[dir][i] = bc;
-            if (pv.evals) atomicAdd(&pv.evals[level > 0], (unsigned long long)nev);
+            if (pv.evals) {
+                atomicAdd(&pv.evals[PLANES ? GPM_COUNT_SWEEP_PLANE : GPM_COUNT_SWEEP0], (unsigned long long)nev);
+                atomicAdd(&pv.evals[PLANES ? GPM_COUNT_SWEEP_PLANE_TAPS : GPM_COUNT_SWEEP0_TAPS],
+                          (unsigned long long)(CENSUS ? nev * Patch<R>::T : ntap));
+            }
         }
     }
+    if (pv.evals && lane == 0 && npr) atomicAdd(&pv.evals[GPM_COUNT_SWEEP0_PRUNED], (unsigned long long)npr);
 }
 
 // Unfrozen pixels of each colour, for the restricted sweeps (order is free:
@@ -967,6 +1088,73 @@ __global__ void k_pad_frames(PairView pv) {
         dst[i] = src[y * W + x];
     }
 }
+// Patch sums of each ingested frame: box[q] = the RGB sums over the (2r+1)^2 taps of q's patch, taps clamped
+// into the frame (read from the padded copy).  For a pixel p whose patch stays inside the frame and an offset c
+// whose target pixel is in the frame, the level-0 cost's taps are exactly these patches' texels, so
+// sum_ch |box1(p)_ch - box2(p + c)_ch| bounds the raw cost from below.  Separable, in FP32: a block stages a
+// 32 x 8 tile and its r-halo, sums each row's 2r + 1 texels, then each column's 2r + 1 row sums, in a fixed order
+// (at most 16 FP32 roundings per sum, which the sweep's test allows for).
+template <int R, int ST>
+__global__ void __launch_bounds__(256) k_box_sums(PairView pv) {
+    constexpr int BX = 32, BY = 8, TWB = BX + 2 * R, THB = BY + 2 * R;
+    __shared__ float3 tex[THB][TWB];
+    __shared__ float3 hs[THB][BX];
+    const int dir = blockIdx.z;
+    const int W = pv.W, H = pv.H, Wp = pv.Wp, Hp = H + 2 * kPad;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    for (int e = threadIdx.x; e < THB * TWB; e += blockDim.x) {
+        const int ly = e / TWB, lx = e - ly * TWB;
+        const int gx = min(x0 - R + lx + kPad, Wp - 1), gy = min(y0 - R + ly + kPad, Hp - 1);
+        const float4 v = ldpix<ST>(pv.imgp[dir], gy * Wp + gx);
+        tex[ly][lx] = make_float3(v.x, v.y, v.z);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < THB * BX; e += blockDim.x) {
+        const int ly = e / BX, lx = e - ly * BX;
+        float3 a = tex[ly][lx];
+#pragma unroll
+        for (int d = 1; d <= 2 * R; ++d) {
+            const float3 v = tex[ly][lx + d];
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+        }
+        hs[ly][lx] = a;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x & (BX - 1), ly = threadIdx.x / BX;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x < W && y < H) {
+        float3 a = hs[ly][lx];
+#pragma unroll
+        for (int d = 1; d <= 2 * R; ++d) {
+            const float3 v = hs[ly + d][lx];
+            a.x += v.x;
+            a.y += v.y;
+            a.z += v.z;
+        }
+        pv.box[dir][y * W + x] = make_float4(a.x, a.y, a.z, 0.f);
+    }
+}
+template <int ST>
+static void launch_box_st(const PairView& pv, int radius, dim3, cudaStream_t st) {
+    const dim3 grid((pv.W + 31) / 32, (pv.H + 7) / 8, 2);
+    switch (radius) {
+        case 1: k_box_sums<1, ST><<<grid, 256, 0, st>>>(pv); break;
+        case 2: k_box_sums<2, ST><<<grid, 256, 0, st>>>(pv); break;
+        case 3: k_box_sums<3, ST><<<grid, 256, 0, st>>>(pv); break;
+        case 4: k_box_sums<4, ST><<<grid, 256, 0, st>>>(pv); break;
+    }
+}
+void launch_box_sums(const PairView& pv, int radius, int storage, int grid_blocks, cudaStream_t st) {
+    const dim3 grid(grid_blocks, 2);
+    switch (storage) {
+        case 0: launch_box_st<0>(pv, radius, grid, st); break;
+        case 1: launch_box_st<1>(pv, radius, grid, st); break;
+        case 2: launch_box_st<2>(pv, radius, grid, st); break;
+    }
+}
+
 void launch_pad_frames(const PairView& pv, int storage, int grid_blocks, cudaStream_t st) {
     if (storage == 0)
         k_pad_frames<uint4><<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);

@@ -1,15 +1,21 @@
 // Frame ingest that allocates nothing (gpm_ingest_noalloc in include/gpm.h).
 //
-// Who needs it: callers that cannot call cudaMalloc at all, or not at the
-// moment they ingest -- code running inside a CUDA stream capture (where an
-// allocation would break or be recorded into the graph), real-time and
-// embedded hosts whose memory is fixed up front, and plugins of frameworks
-// that own the device memory pool.  They pass the input frames and the
-// output RGBX buffers; the gain-normalisation scratch (per-row FP64 sums of
-// both frames and the gain) lives in a file-scope device array instead of a
-// buffer from an allocator.
+// Who needs it: callers that must not call cudaMalloc when they ingest --
+// real-time and embedded hosts whose device memory is reserved once at
+// start-up, plugins of frameworks that own the device memory pool and forbid
+// allocations behind their back, and latency-critical loops where an
+// allocation (and the implicit synchronisation cudaMalloc can bring) is not
+// allowed.  They pass the input frames and the output RGBX buffers; the
+// ingest's scratch (the FP64 partial sums of both frames, the gain, and the
+// V histogram and table of the optional HSV equalisation) lives in one
+// file-scope device array instead of a buffer from an allocator.
+//
+// The work is the same launch sequence, on the same grid, as the ingest of
+// gpm_match(level 0): the same kernels in the same order with the same
+// summation tree, so the output is bitwise the same.
 #include <cuda_runtime.h>
 
+#include <cstddef>
 #include <mutex>
 
 #include "../../include/gpm.h"
@@ -18,54 +24,23 @@
 
 namespace gpm {
 
-constexpr int kNoAllocMaxRows = 4096;  // rows a frame may have: scratch = 2 * 4096 + 1 doubles (64 KiB)
+// The scratch of one ingest (6 KiB in all).
+struct NoAllocScratch {
+    double partial[2 * kIngestPartialBlocks];  // per-block FP64 sums of both frames
+    double gain;                                // mean(I1) / mean(I2), or 1
+    double pad[31];                             // keeps the tables 256-byte aligned
+    int hist[2 * 256];                          // V histograms (HSV equalisation)
+    float lut[2 * 256];                         // equalised V per bin
+};
 
 // Every GPU that loads the library holds this array until the process exits.
 // Calls share it: two calls that overlap on the GPU (different streams, no
 // ordering between them) race on it.
-static __device__ __align__(256) double g_ingest_scratch[2 * kNoAllocMaxRows + 1];
-
-// One block per row: FP64 sums of the row's RGB values in both frames.
-__global__ void k_row_sums_noalloc(const float* f1, const float* f2, int W, int64_t stride, double* rows) {
-    __shared__ double sh[2][256];
-    const int y = blockIdx.x;
-    const float* r1 = f1 + (int64_t)y * stride;
-    const float* r2 = f2 + (int64_t)y * stride;
-    double a = 0, b = 0;
-    for (int k = threadIdx.x; k < 3 * W; k += blockDim.x) {
-        a += (double)r1[k];
-        b += (double)r2[k];
-    }
-    sh[0][threadIdx.x] = a;
-    sh[1][threadIdx.x] = b;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        rows[2 * y] = sh[0][0];
-        rows[2 * y + 1] = sh[1][0];
-    }
-}
-
-// gain = sum(I1) / sum(I2), summed over the rows in order (deterministic).
-__global__ void k_row_gain_noalloc(const double* rows, int H, int enable, double* gain) {
-    if (threadIdx.x != 0) return;
-    double a = 0, b = 0;
-    for (int y = 0; y < H; ++y) {
-        a += rows[2 * y];
-        b += rows[2 * y + 1];
-    }
-    *gain = (enable && b > 0) ? a / b : 1.0;
-}
+static __device__ __align__(256) NoAllocScratch g_ingest_scratch;
 
 namespace {
 std::mutex g_mu;
-double* g_scratch_ptr[64] = {};  // device address of the array, per device (set once)
+NoAllocScratch* g_scratch_ptr[64] = {};  // device address of the array, per device (looked up once)
 }  // namespace
 
 }  // namespace gpm
@@ -73,22 +48,22 @@ double* g_scratch_ptr[64] = {};  // device address of the array, per device (set
 using namespace gpm;
 
 extern "C" gpm_status gpm_ingest_noalloc(const float* frame1, const float* frame2, int32_t width, int32_t height,
-                                         int64_t row_stride, int32_t gain_normalize, int32_t storage, void* out1,
-                                         void* out2, void* stream) {
+                                         int64_t row_stride, int32_t gain_normalize, int32_t equalize,
+                                         int32_t storage, void* out1, void* out2, void* stream) {
     if (!frame1 || !frame2 || !out1 || !out2) return GPM_EINVAL;
-    if (width < 1 || height < 1 || row_stride < 3 * (int64_t)width) return GPM_EINVAL;
-    if (height > kNoAllocMaxRows) return GPM_EINVAL;  // beyond the static scratch
-    if ((int64_t)width * height > (1 << 26)) return GPM_EINVAL;
-    if (storage < 0 || storage > 2) return GPM_EINVAL;
+    if (width < 1 || height < 1 || width > 32767 || height > 32767 || row_stride < 3 * (int64_t)width)
+        return GPM_EINVAL;
+    if ((int64_t)width * height > (1 << 26)) return GPM_EINVAL;  // the largest frame a context takes
+    if (storage < 0 || storage > 2 || (equalize != 0 && equalize != 1)) return GPM_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
         return GPM_ECUDA;
     }
-    double* scratch = nullptr;
+    NoAllocScratch* sc = nullptr;
     {
         // Set-up, once per device, with that device current: the host-side
-        // name of the array is not a device address, so look the address up.
+        // name of the array is only a stand-in, not a device address.
         std::lock_guard<std::mutex> lock(g_mu);
         if (!g_scratch_ptr[dev]) {
             void* p = nullptr;
@@ -96,19 +71,20 @@ extern "C" gpm_status gpm_ingest_noalloc(const float* frame1, const float* frame
                 cudaGetLastError();
                 return GPM_ECUDA;
             }
-            g_scratch_ptr[dev] = (double*)p;
+            g_scratch_ptr[dev] = (NoAllocScratch*)p;
         }
-        scratch = g_scratch_ptr[dev];
+        sc = g_scratch_ptr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    // every row slot and the gain are rewritten by each call: nothing carries over
-    k_row_sums_noalloc<<<height, 256, 0, st>>>(frame1, frame2, width, row_stride, scratch);
-    k_row_gain_noalloc<<<1, 32, 0, st>>>(scratch, height, gain_normalize, scratch + 2 * kNoAllocMaxRows);
-    launch_pack(frame1, frame2, width, height, row_stride, storage, scratch + 2 * kNoAllocMaxRows, out1, out2, st);
-    const cudaError_t e = cudaPeekAtLastError();
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return GPM_ECUDA;
-    }
-    return GPM_OK;
+    // Every slot this call reads is written first by this call (the partial sums and the gain by their kernels,
+    // the histogram cleared on the stream before it is counted), so nothing carries over from an earlier call.
+    char* base = reinterpret_cast<char*>(sc);  // a device address: only offsets are taken on the host
+    double* partial = reinterpret_cast<double*>(base + offsetof(NoAllocScratch, partial));
+    double* gain = reinterpret_cast<double*>(base + offsetof(NoAllocScratch, gain));
+    int* hist = reinterpret_cast<int*>(base + offsetof(NoAllocScratch, hist));
+    float* lut = reinterpret_cast<float*>(base + offsetof(NoAllocScratch, lut));
+    launch_ingest(frame1, frame2, width, height, row_stride, gain_normalize, storage, partial, kIngestPartialBlocks,
+                  gain, out1, out2, equalize ? hist : nullptr, equalize ? lut : nullptr, (cudaStream_t)stream);
+    // Reports a launch failure of this call; an error that earlier work left pending is reported (and cleared) too.
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GPM_OK : GPM_ECUDA;
 }

@@ -16,7 +16,7 @@ import numpy as np
 
 MAX_SCALES = 8
 MI = 12
-(GPM_OK, GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_ETIMEOUT, GPM_EBUSY, GPM_EINTERNAL) = range(7)
+GPM_OK, GPM_EINVAL, GPM_ENOMEM, GPM_ECUDA, GPM_EBUSY, GPM_EINTERNAL = 0, 1, 2, 3, 5, 6
 GPM_F32, GPM_F16, GPM_BF16 = 0, 1, 2
 (NNF, COST, MODELS, MODEL_INFO, LABELS, LEVEL_LABELS, STAGE1_LABELS, CUES, FRAMES, TENT_LABELS) = range(10)
 
@@ -24,7 +24,10 @@ GPM_F32, GPM_F16, GPM_BF16 = 0, 1, 2
 EXPORTED = ["gpm_default_params", "gpm_create", "gpm_destroy", "gpm_required_bytes", "gpm_match",
             "gpm_fit_planes", "gpm_flow_and_occlusion", "gpm_sync", "gpm_state_bytes", "gpm_export",
             "gpm_import", "gpm_status_string", "gpm_last_error", "gpm_launch_count", "gpm_profile_enable",
-            "gpm_profile_select", "gpm_profile_read", "gpm_ingest_noalloc"]
+            "gpm_profile_select", "gpm_profile_read", "gpm_ingest_noalloc", "gpm_fp32_peak_probe"]
+(COUNT_SWEEP0, COUNT_SWEEP_PLANE, COUNT_RANSAC, COUNT_INIT, COUNT_SWEEP0_TAPS, COUNT_SWEEP_PLANE_TAPS,
+ COUNT_SWEEP0_PRUNED) = range(7)
+COUNTERS = 7
 PROF_CLASSES = ["ingest", "pm_init", "pm_sweep", "pm_sweep_plane", "pm_recost", "ransac", "assign", "cues",
                 "many_to_one", "merge", "lists", "fill", "final"]
 
@@ -97,7 +100,8 @@ def load(build: bool = True) -> C.CDLL:
         "gpm_profile_select": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int32]),
         "gpm_profile_read": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_uint64), P(C.c_uint64)]),
         "gpm_ingest_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_int32,
-                                         C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+                                         C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+        "gpm_fp32_peak_probe": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -105,6 +109,17 @@ def load(build: bool = True) -> C.CDLL:
         f.argtypes = args
     _lib = L
     return L
+
+
+def fp32_peak_probe(blocks: int, iters: int, sink, stream=None) -> int:
+    """Launches the FP32 FMA probe (gpm_fp32_peak_probe) on the stream; returns the lane operations it executes.
+    sink: a CUDA float32 tensor of at least blocks x 256 elements."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    r = load().gpm_fp32_peak_probe(blocks, iters, C.c_void_p(sink.data_ptr()), C.c_void_p(st.cuda_stream))
+    if r != GPM_OK:
+        raise GpmError(r, "gpm_fp32_peak_probe failed")
+    return blocks * 256 * iters * 512
 
 
 def default_params(**kw) -> Params:
@@ -223,13 +238,16 @@ class Context:
         self._check(self.lib.gpm_profile_select(self.h, mask, 1 if count_evals else 0), "gpm_profile_select")
 
     def profile_read(self):
-        """{class: (ms, launches)}, (PM evals at level 0, at levels >= 1, RANSAC residual tests); clears them."""
+        """{class: (ms, launches)} and the work counts (a tuple indexed by the COUNT_* constants: level-0 sweep
+        evaluations, plane-level sweep evaluations, RANSAC residual tests, init / recost evaluations, taps summed by
+        the level-0 sweeps, taps summed by the plane-level sweeps, level-0 candidates rejected by the patch-sum bound);
+        clears them."""
         k = len(PROF_CLASSES)
         ms = (C.c_double * k)()
         ln = (C.c_uint64 * k)()
-        ev = (C.c_uint64 * 3)()
+        ev = (C.c_uint64 * COUNTERS)()
         self._check(self.lib.gpm_profile_read(self.h, ms, ln, ev), "gpm_profile_read")
-        return {PROF_CLASSES[i]: (ms[i], int(ln[i])) for i in range(k)}, (int(ev[0]), int(ev[1]), int(ev[2]))
+        return {PROF_CLASSES[i]: (ms[i], int(ln[i])) for i in range(k)}, tuple(int(e) for e in ev)
 
     # ------------------------------------------------------------ state
     def export(self, what: int, pair: int = 0):
@@ -277,10 +295,27 @@ class Context:
             raw[a:] = np.ascontiguousarray(f, np.float64).view(np.uint8).reshape(-1)
         else:
             raw = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
-        buf = torch.from_numpy(raw.copy()).to("cuda")
         stage = 2 * level - 1 if after_fit else 2 * level
-        self._check(self.lib.gpm_import(self.h, pair, what, C.c_void_p(buf.data_ptr()), stage), "gpm_import")
+        self.import_state_raw(what, raw, stage, pair, packed=True)
         self.sync()
+
+    def import_state_raw(self, what: int, data, stage: int, pair: int = 0, packed: bool = False):
+        """gpm_import at a raw stage number, without the synchronising check (device consistency checks are
+        then reported by the next sync)."""
+        torch = self._torch
+        if what == LABELS and not packed:
+            m, L, f = data
+            n = m.shape[1]
+            a = (2 * n * 8 + 7) // 8 * 8
+            raw = np.zeros(a + 2 * n * 16, np.uint8)
+            raw[: 2 * n * 4] = np.ascontiguousarray(m, np.int32).view(np.uint8).reshape(-1)
+            raw[2 * n * 4: 2 * n * 8] = np.ascontiguousarray(L, np.float32).view(np.uint8).reshape(-1)
+            raw[a:] = np.ascontiguousarray(f, np.float64).view(np.uint8).reshape(-1)
+        else:
+            raw = np.ascontiguousarray(data).view(np.uint8).reshape(-1)
+        buf = torch.from_numpy(raw.copy()).to("cuda")
+        self._check(self.lib.gpm_import(self.h, pair, what, C.c_void_p(buf.data_ptr()), stage), "gpm_import")
+        self._import_keep = buf
 
     def close(self):
         if getattr(self, "h", None):

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "gpm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gpm_[a-z_]+)\s*\(", src)) - {"gpm_alloc_fn", "gpm_free_fn"})
+    return sorted(set(re.findall(r"\b(gpm_[a-z0-9_]+)\s*\(", src)) - {"gpm_alloc_fn", "gpm_free_fn"})
 
 
 @pytest.fixture(scope="module")
@@ -111,3 +111,87 @@ def test_product_path_fails_loudly_without_a_gpu():
             "        raise SystemExit('a context was made without a GPU')\n")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def _bench_params(gpm):
+    p = gpm.Params()
+    gpm.load(build=False).gpm_default_params(ctypes.byref(p))
+    p.patch_radius = 4
+    p.num_scales = 4
+    for i, s in enumerate((64, 32, 16, 8)):
+        p.cell_size[i] = s
+    return p
+
+
+def test_create_over_budget_is_busy_before_any_allocation(lib):
+    """GPM_EBUSY: a budget below gpm_required_bytes refuses the context before the allocator is called."""
+    from paper_1804_03787_gb300 import gpm
+    L = gpm.load(build=False)
+    p = _bench_params(gpm)
+    calls = []
+    alloc = gpm.ALLOC_FN(lambda user, nb, st: calls.append(nb) or 0)
+    free = gpm.FREE_FN(lambda user, ptr, st: None)
+    need = L.gpm_required_bytes(ctypes.byref(p), ctypes.byref(gpm.Limits(1024, 436, 2, 0, 0)))
+    h = ctypes.c_void_p(1)
+    lim = gpm.Limits(1024, 436, 2, 0, need - 1)
+    assert L.gpm_create(ctypes.byref(p), ctypes.byref(lim), alloc, free, None, None, ctypes.byref(h)) == gpm.GPM_EBUSY
+    assert not h.value and calls == []
+
+
+def test_create_with_failing_allocator_is_enomem_and_frees_what_it_took(lib):
+    """GPM_ENOMEM: the allocator callback returns NULL for the third slot; the two blocks it gave are freed
+    through the free callback, and the caller gets no context."""
+    from paper_1804_03787_gb300 import gpm
+    L = gpm.load(build=False)
+    p = _bench_params(gpm)
+    given, freed = [], []
+
+    def _alloc(user, nb, st):
+        if len(given) == 2:
+            return 0
+        given.append(0x100000 * (len(given) + 1))
+        return given[-1]
+
+    alloc = gpm.ALLOC_FN(_alloc)
+    free = gpm.FREE_FN(lambda user, ptr, st: freed.append(ptr))
+    h = ctypes.c_void_p(1)
+    lim = gpm.Limits(256, 192, 4, 0, 0)
+    assert L.gpm_create(ctypes.byref(p), ctypes.byref(lim), alloc, free, None, None, ctypes.byref(h)) == gpm.GPM_ENOMEM
+    assert not h.value
+    assert sorted(freed) == sorted(given) and len(given) == 2
+
+
+def test_create_without_a_device_is_ecuda():
+    """GPM_ECUDA: on a host without a CUDA device a context cannot be made, even when the allocator callback
+    succeeds (its blocks are handed back)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_1804_03787_gb300 import gpm, build_lib
+    build_lib.build()
+    L = gpm.load(build=False)
+    p = _bench_params(gpm)
+    given, freed = [], []
+    alloc = gpm.ALLOC_FN(lambda user, nb, st: given.append(0x200000 * (len(given) + 1)) or given[-1])
+    free = gpm.FREE_FN(lambda user, ptr, st: freed.append(ptr))
+    h = ctypes.c_void_p(1)
+    lim = gpm.Limits(256, 192, 2, 0, 0)
+    assert L.gpm_create(ctypes.byref(p), ctypes.byref(lim), alloc, free, None, None, ctypes.byref(h)) == gpm.GPM_ECUDA
+    assert not h.value and sorted(freed) == sorted(given) and len(given) == 2
+
+
+def test_every_status_code_has_a_name(lib):
+    """The status codes the header lists, and only those, have names; GPM_OK and GPM_EINTERNAL are reached by the
+    GPU tests (test_gpu_edges.py: the consistency flag), the others above."""
+    from paper_1804_03787_gb300 import gpm
+    L = gpm.load(build=False)
+    src = open(os.path.join(ROOT, "include", "gpm.h")).read()
+    codes = dict((m, int(v)) for m, v in re.findall(r"\b(GPM_E[A-Z]+|GPM_OK)\s*=\s*(\d+)", src))
+    assert codes == {"GPM_OK": 0, "GPM_EINVAL": 1, "GPM_ENOMEM": 2, "GPM_ECUDA": 3, "GPM_EBUSY": 5,
+                     "GPM_EINTERNAL": 6}
+    for name, v in codes.items():
+        assert L.gpm_status_string(v).decode() == name
+        assert getattr(gpm, name) == v
+    assert L.gpm_status_string(4) == b"unknown"
+    # calls on a NULL context are refused without a device
+    assert L.gpm_sync(None) == gpm.GPM_EINVAL and L.gpm_fit_planes(None, 1, 1) == gpm.GPM_EINVAL

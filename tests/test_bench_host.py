@@ -7,33 +7,47 @@ import pytest
 import bench
 
 
+def _counts(sweep0=0, taps0=0, plane=0, taps_plane=0, ransac=0, init=0):
+    from paper_1804_03787_gb300 import gpm
+    c = [0] * gpm.COUNTERS
+    c[gpm.COUNT_SWEEP0], c[gpm.COUNT_SWEEP0_TAPS] = sweep0, taps0
+    c[gpm.COUNT_SWEEP_PLANE], c[gpm.COUNT_SWEEP_PLANE_TAPS] = plane, taps_plane
+    c[gpm.COUNT_RANSAC], c[gpm.COUNT_INIT] = ransac, init
+    return c
+
+
 def test_roofline_block_takes_the_top_class_and_divides_by_its_launch_time():
-    # 1e9 square-patch evaluations of 81 taps at 6 FP32 operations each, over 160 launches taking 100 ms in all
+    # 1e9 square-patch evaluations summing 5e10 taps at 6 FP32 operations each, over 160 launches taking 100 ms in
+    # all; the initial field's evaluations are not the sweep's work
     prof = {"pm_sweep": (100.0, 160), "ransac": (50.0, 40), "pm_sweep_plane": (30.0, 64)}
-    evals = [1e9, 0, 0]
+    evals = _counts(sweep0=1e9, taps0=5e10, init=7e8)
     blk = bench.roofline_block(prof, evals, 152, {"sm_mhz": 2000.0}, {"hbm_gbs": 6783.0}, steps=10)
     assert blk["kernel"] == "pm_sweep" and blk["bound"] == "alu"
     assert blk["share"] == pytest.approx(100 / 180)
-    assert blk["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)                  # 38.9 TFLOP/s
-    assert blk["achieved"] == pytest.approx(1e9 * 81 * 6 / 0.100 / 1e12)             # 4.86 TFLOP/s
+    assert blk["peak"] == pytest.approx(152 * 128 * 2000e6 / 1e12)                  # nominal: no probe given
+    assert "nominal" in blk["peak_source"]
+    assert blk["achieved"] == pytest.approx(5e10 / 160 * 6 / (100 / 160 * 1e-3) / 1e12)
     assert blk["frac"] == pytest.approx(blk["achieved"] / blk["peak"])
+    assert blk["per_launch"]["taps_per_evaluation"] == pytest.approx(50.0)
     assert blk["avg_launch_ms"] == pytest.approx(100 / 160)
     assert "profiled replay" in blk["avg_launch_source"]
     hv = blk["hbm_view"]                                                            # 48 B per visit, W*H visits
     assert hv["algorithmic_bytes_per_launch"] == 1024 * 436 * 48
     assert hv["achieved_gbs"] == pytest.approx(1024 * 436 * 48 / (100 / 160 * 1e-3) / 1e9)
     assert hv["frac"] == pytest.approx(hv["achieved_gbs"] / 6783.0)
-    assert blk["traffic"] == bench.TRAFFIC_PER_LAUNCH["pm_sweep"][0]
+    assert blk["traffic"] is None                                                   # the kernel changed since
 
 
-def test_roofline_block_prefers_the_timed_region_and_reports_no_fraction_it_cannot_model():
+def test_roofline_block_prefers_the_timed_region_and_the_measured_peak():
     prof = {"pm_sweep": (100.0, 160)}
-    blk = bench.roofline_block(prof, [1e9, 0, 0], 152, {"sm_mhz": None}, {"sm_max_mhz": 2070.0}, steps=10,
-                               timed={"pm_sweep": (80.0, 160)})
+    fp32 = {"lane_ops_per_clk": 19000.0}
+    blk = bench.roofline_block(prof, _counts(sweep0=1e9, taps0=8.1e10), 152, {"sm_mhz": None},
+                               {"sm_max_mhz": 2070.0}, steps=10, timed={"pm_sweep": (80.0, 160)}, fp32=fp32)
     assert blk["avg_launch_ms"] == pytest.approx(0.5) and "timed region" in blk["avg_launch_source"]
-    assert blk["achieved"] == pytest.approx(1e9 * 81 * 6 / 0.080 / 1e12)
-    assert blk["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)                  # the maximum clock, unsampled
-    other = bench.roofline_block({"fill": (5.0, 8)}, [0, 0, 0], 152, {"sm_mhz": 2000.0}, {}, steps=1)
+    assert blk["achieved"] == pytest.approx(8.1e10 / 160 * 6 / 0.5e-3 / 1e12)
+    assert blk["peak"] == pytest.approx(19000.0 * 2070e6 / 1e12)                   # measured rate, max clock
+    assert "measured" in blk["peak_source"]
+    other = bench.roofline_block({"fill": (5.0, 8)}, _counts(), 152, {"sm_mhz": 2000.0}, {}, steps=1)
     assert other["achieved"] is None and other["frac"] is None and other["traffic"] is None
 
 
@@ -90,4 +104,7 @@ def test_reference_arm_prints_one_contract_line():
     assert d["impl"] == "reference" and d["unit"] == "pairs/s" and d["value"] > 0 and d["steps"] == 1
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
-    assert abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    # ms_per_step is the measured time of a step's sample (a crop); value counts the crop as its fraction of a pair
+    frac = d["config"]["pairs_per_step"]
+    assert 0.1 < frac < 0.2
+    assert abs(d["ms_per_step"] - 1e3 * frac / d["value"]) < 1e-6 * d["ms_per_step"]

@@ -126,6 +126,36 @@ def test_invalid_calls_are_refused(torch):
     ctx.close()
 
 
+def test_device_consistency_flag_reports_bad_imported_labels(torch):
+    """GPM_EINTERNAL: labels imported with a model id beyond the model table (and one with a non-finite flow) are
+    caught on the device, those pixels get no plane, gpm_sync reports the check once, and the context then runs a
+    whole pair as before (nothing read outside the model table)."""
+    gp = gpm.default_params()
+    s = scene.make_scene(64, 48, seed=2, n_layers=1, max_disp=3.0, affine=True)
+    ctx = gpm.Context(gp, 64, 48)
+    ctx.match([_dev(torch, s.frame1, s.frame2)])
+    ctx.fit_planes(1)
+    m, L, f = ctx.export(gpm.LABELS)
+    n_models = ctx.export(gpm.MODELS).shape[1]
+    m = m.copy()
+    f = f.copy()
+    m[0, 5] = n_models + 7
+    m[1, 9] = -3
+    m[0, 11] = 0
+    f[0, 11] = (np.inf, 0.0)
+    ctx.import_state_raw(gpm.LABELS, (m, L, f), stage=1)
+    with pytest.raises(gpm.GpmError) as e:
+        ctx.sync()
+    assert e.value.status == gpm.GPM_EINTERNAL
+    ctx.sync()  # reported once, then cleared
+    got, _, _ = ctx.export(gpm.LABELS)
+    assert got[0, 5] == -1 and got[1, 9] == -1 and got[0, 11] == -1
+    flows, occs = ctx.run([_dev(torch, s.frame1, s.frame2)])
+    ctx.sync()
+    assert np.isfinite(flows[0].cpu().numpy()).all()
+    ctx.close()
+
+
 def test_profile_select_brackets_only_the_chosen_classes(torch):
     """gpm_profile_select: only the chosen kernel classes are timed, evaluations are counted only on request, and
     a bit beyond the last class is refused."""
@@ -137,13 +167,18 @@ def test_profile_select_brackets_only_the_chosen_classes(torch):
     prof, evals = ctx.profile_read()
     assert prof["pm_sweep"][0] > 0 and prof["pm_sweep"][1] > 0
     assert all(ms == 0 and n == 0 for k, (ms, n) in prof.items() if k != "pm_sweep")
-    assert evals == (0, 0, 0)
+    assert evals == (0,) * gpm.COUNTERS
     ctx.profile_enable(True)
     ctx.profile_read()
     ctx.run([_dev(torch, s.frame1, s.frame2)])
     prof, evals = ctx.profile_read()
     assert all(prof[k][1] > 0 for k in ("pm_sweep", "pm_sweep_plane", "ransac", "assign", "final"))
-    assert evals[0] > 0 and evals[1] > 0 and evals[2] > 0
+    assert all(e > 0 for e in evals)
+    # the initial field (one evaluation per pixel and direction) and the recosts of the plane levels
+    assert evals[gpm.COUNT_INIT] > 2 * 128 * 96
+    # taps actually summed: at most (2r + 1)^2 per evaluation, at least the first 32 (r = 3)
+    for ev, taps in ((gpm.COUNT_SWEEP0, gpm.COUNT_SWEEP0_TAPS), (gpm.COUNT_SWEEP_PLANE, gpm.COUNT_SWEEP_PLANE_TAPS)):
+        assert 32 * evals[ev] <= evals[taps] <= 49 * evals[ev], (evals[ev], evals[taps])
     with pytest.raises(gpm.GpmError):
         ctx._check(ctx.lib.gpm_profile_select(ctx.h, 1 << len(gpm.PROF_CLASSES), 0), "gpm_profile_select")
     ctx.close()
