@@ -790,6 +790,11 @@ def run_ours(args):
                                        "plane_sweeps": evals[gpm.COUNT_SWEEP_PLANE] / args.steps,
                                        "init_and_recost": evals[gpm.COUNT_INIT] / args.steps},
             "ransac_tests_per_step": evals[gpm.COUNT_RANSAC] / args.steps,
+            "ransac_certification": {
+                "tests_decided_in_fp64_per_step": evals[gpm.COUNT_RANSAC_FP64] / args.steps,
+                "hypotheses_with_per_match_bounds_per_step": evals[gpm.COUNT_RANSAC_LOOSE] / args.steps,
+                "note": "an FP32 residual test within its rounding bound is decided again in FP64"},
+            "level0_pruned_candidates_per_step": evals[gpm.COUNT_SWEEP0_PRUNED] / args.steps,
             "fp32_peak_probe": fp32,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "kernel_ms_source": "every launch bracketed by CUDA events in an untimed replay of the timed steps",

@@ -239,7 +239,11 @@ gpm_status gpm_import(gpm_ctx* ctx, int32_t pair, int32_t what, const void* src_
      GPM_COUNT_SWEEP_PLANE_TAPS  the same for the plane-level sweeps;
      GPM_COUNT_SWEEP0_PRUNED  level-0 sweep candidates rejected without any
                               tap by the patch-sum lower bound (not counted
-                              as evaluations).
+                              as evaluations);
+     GPM_COUNT_RANSAC_FP64    RANSAC residual tests whose FP32 decision was
+                              within its rounding bound, decided again in FP64;
+     GPM_COUNT_RANSAC_LOOSE   hypotheses whose window-wide rounding bound was
+                              too loose, tested with a bound per match.
    gpm_profile_read synchronises the stream, returns per kernel class the
    summed device milliseconds and the launch count, and the GPM_COUNTERS
    counts, then clears them.  Host arrays: ms[GPM_PROF_CLASSES],
@@ -252,7 +256,9 @@ enum {
     GPM_COUNT_SWEEP0_TAPS = 4,
     GPM_COUNT_SWEEP_PLANE_TAPS = 5,
     GPM_COUNT_SWEEP0_PRUNED = 6,
-    GPM_COUNTERS = 7
+    GPM_COUNT_RANSAC_FP64 = 7,
+    GPM_COUNT_RANSAC_LOOSE = 8,
+    GPM_COUNTERS = 9
 };
 enum {
     GPM_PROF_INGEST = 0,

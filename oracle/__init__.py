@@ -391,7 +391,7 @@ def final(P: Params, src, tgt, acc: Labels, vx, vy, cue):
 # ---------------------------------------------------------------- whole method
 class _State(C.Structure):
     _fields_ = [(n, C.c_void_p * 2) for n in
-                ("vx", "vy", "cost", "mh", "mi", "am", "aL", "afx", "afy", "cue", "flow", "occ")]
+                ("vx", "vy", "cost", "mh", "mi", "am", "aL", "afx", "afy", "cue", "flow", "occ", "s1m")]
 
 
 @dataclass
@@ -435,6 +435,9 @@ def run(P: Params, f1, f2, stop_after: int = -1, init_nnf=None) -> Result:
                           ("am", R.acc[d].m), ("aL", R.acc[d].L), ("afx", R.acc[d].fx), ("afy", R.acc[d].fy),
                           ("cue", R.cue[d]), ("flow", R.flow[d]), ("occ", R.occ[d])):
             getattr(st, name)[d] = arr.ctypes.data
+        # the first-stage labels of the last level run (Sec. 3.2's residual region is where they are -1)
+        R.extra.setdefault("stage1_m", []).append(np.full(n, -1, np.int32))
+        st.s1m[d] = R.extra["stage1_m"][d].ctypes.data
     lib().orc_run(C.byref(P.c()), _p(f1, C.c_double), _p(f2, C.c_double), C.cast(C.pointer(st), C.c_void_p),
                   stop_after)
     return R

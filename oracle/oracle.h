@@ -174,6 +174,7 @@ typedef struct {
     int32_t* am[2]; double* aL[2]; double* afx[2]; double* afy[2];
     uint8_t* cue[2];
     float* flow[2]; uint8_t* occ[2];
+    int32_t* s1m[2];   /* optional (NULL = not wanted): the first-stage labels of the last level run */
 } orc_state;
 
 /* stop_after: -1 = run everything; 0 = after level-0 PatchMatch;

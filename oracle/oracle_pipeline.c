@@ -126,6 +126,7 @@ void orc_run(const orc_params* Pin, const double* f1in, const double* f2in, orc_
             for (int d = 0; d < 2; ++d) {
                 orc_assign(P, src[d], tgt[d], l, 1, S->mh[d], S->mi[d], NULL, S1[d].m, S1[d].L, S1[d].fx, S1[d].fy, NULL);
                 for (int i = 0; i < n; ++i) resid[d][i] = S1[d].m[i] < 0;
+                if (S->s1m[d]) memcpy(S->s1m[d], S1[d].m, sizeof(int32_t) * (size_t)n);
             }
             /* second stage on the residual region (Sec. 3.2) */
             for (int d = 0; d < 2; ++d)

@@ -311,91 +311,11 @@ typedef struct {
     double cx, cy; /* window centre */
 } matches_t;
 
-/* ---- near-tie bands for decisions that FP32 evaluation of a homography
-   takes.  Not part of the method: these only widen the logs of comparisons
-   the oracle calls ambiguous.
-
-   A homography is evaluated in FP32 in a frame local to its window: source
-   u = p - c about the window centre c, H scaled to denominator 1 at c,
-   displacement at c held to ~1e-7 px.  With e = g . u the denominator's
-   change (den = 1 + e), B = A - I the local linear part, t the displacement
-   at c and v a match's offset q - p, the residual numerator is
-       n = (t - v) + B u - (u + v) e,   and the inlier test n.n < t2 den^2.
-   Every term of n is stored or formed with relative error of a few units of
-   2^-24, so |dn| <= K 2^-24 S with S the sum of the terms' magnitudes, and
-   |d den| <= K 2^-24 (1 + |g0 ux| + |g1 uy|).  A strongly projective H
-   (denominator small somewhere in the window) or a far match makes S large
-   against n: the FP32 test can then decide differently from FP64 well
-   outside a fixed relative band. */
-#define ORC_FP32_K 8.0
+/* A refit whose normal matrix has a relative eigen-gap below this is not
+   determined to the 1e-6 a model is compared at (its eigenvector moves by
+   about 1e-16 / gap under rounding of the matrix): a property of the
+   least-squares problem, logged as a near tie. */
 #define ORC_REFIT_GAP 1e-8
-#define ORC_U32 5.9604644775390625e-08 /* 2^-24 */
-typedef struct {
-    double b00, b01, b10, b11, tx, ty, g0, g1; /* local form about the window centre */
-} hloc_t;
-
-static int h_local(const double* H, double cx, double cy, hloc_t* L) {
-    const double z0 = H[6] * cx + H[7] * cy + H[8];
-    if (!(z0 != 0)) return 0;
-    const double X0 = (H[0] * cx + H[1] * cy + H[2]) / z0, Y0 = (H[3] * cx + H[4] * cy + H[5]) / z0;
-    L->g0 = H[6] / z0;
-    L->g1 = H[7] / z0;
-    L->b00 = (H[0] - X0 * H[6]) / z0 - 1.0;
-    L->b01 = (H[1] - X0 * H[7]) / z0;
-    L->b10 = (H[3] - Y0 * H[6]) / z0;
-    L->b11 = (H[4] - Y0 * H[7]) / z0 - 1.0;
-    L->tx = X0 - cx;
-    L->ty = Y0 - cy;
-    return 1;
-}
-
-/* FP32 error bound of the inlier test f = n.n - t2 den^2 of source p with
-   offset v, expressed on r2 - t2 (f / den^2); 0 if the local form fails */
-static double fp32_band_r2(const hloc_t* L, double px, double py, double vx, double vy, double cx, double cy,
-                           double t2) {
-    const double ux = px - cx, uy = py - cy;
-    const double ea = fabs(L->g0 * ux) + fabs(L->g1 * uy);
-    const double e = L->g0 * ux + L->g1 * uy, den = 1.0 + e;
-    const double nx = (L->tx - vx) + L->b00 * ux + L->b01 * uy - (ux + vx) * e;
-    const double ny = (L->ty - vy) + L->b10 * ux + L->b11 * uy - (uy + vy) * e;
-    const double Sx = fabs(L->tx - vx) + fabs(L->b00 * ux) + fabs(L->b01 * uy) + (fabs(ux) + fabs(vx)) * ea;
-    const double Sy = fabs(L->ty - vy) + fabs(L->b10 * ux) + fabs(L->b11 * uy) + (fabs(uy) + fabs(vy)) * ea;
-    const double k = ORC_FP32_K * ORC_U32;
-    const double df = 2.0 * (fabs(nx) * k * Sx + fabs(ny) * k * Sy) + 2.0 * t2 * fabs(den) * k * (1.0 + ea);
-    return den != 0 ? df / (den * den) : HUGE_VAL;
-}
-
-/* FP32 error bound of the mapped position of source p (sum of |dX| and |dY|) */
-static double fp32_band_pos(const hloc_t* L, double px, double py, double cx, double cy) {
-    const double ux = px - cx, uy = py - cy;
-    const double ea = fabs(L->g0 * ux) + fabs(L->g1 * uy);
-    const double e = L->g0 * ux + L->g1 * uy, den = 1.0 + e;
-    if (!(den != 0)) return HUGE_VAL;
-    const double Dx = (L->tx + L->b00 * ux + L->b01 * uy - ux * e) / den;
-    const double Dy = (L->ty + L->b10 * ux + L->b11 * uy - uy * e) / den;
-    const double Sx = fabs(Dx * den) + fabs(L->b00 * ux) + fabs(L->b01 * uy) + fabs(ux) * ea;
-    const double Sy = fabs(Dy * den) + fabs(L->b10 * ux) + fabs(L->b11 * uy) + fabs(uy) * ea;
-    const double k = ORC_FP32_K * ORC_U32;
-    return k * (Sx + Sy + (fabs(Dx) + fabs(Dy)) * (1.0 + ea)) / fabs(den);
-}
-
-/* largest change of a channel of the bilinear sample of img around (X, Y)
-   per unit of position: the largest texel difference of its 2 x 2 cell */
-static double bilinear_slope(const double* img, int W, int H, double X, double Y) {
-    int x0 = (int)floor(X), y0 = (int)floor(Y);
-    if (x0 < 0) x0 = 0;
-    if (y0 < 0) y0 = 0;
-    if (x0 > W - 1) x0 = W - 1;
-    if (y0 > H - 1) y0 = H - 1;
-    const int x1 = x0 + 1 < W ? x0 + 1 : W - 1, y1 = y0 + 1 < H ? y0 + 1 : H - 1;
-    double m = 0;
-    for (int c = 0; c < 3; ++c) {
-        const double a = img[((size_t)y0 * W + x0) * 3 + c], b = img[((size_t)y0 * W + x1) * 3 + c];
-        const double d = img[((size_t)y1 * W + x0) * 3 + c], e = img[((size_t)y1 * W + x1) * 3 + c];
-        m = fmax(m, fmax(fmax(fabs(b - a), fabs(e - d)), fmax(fabs(d - a), fabs(e - b))));
-    }
-    return m;
-}
 
 /* Exact test that the 4-point homography of a sample has a zero
    denominator at the window centre.  With the projective bases
@@ -488,8 +408,6 @@ static int collinear_int(const int* x, const int* y, int a, int b, int c) {
 /* counts inliers ||H p - q||^2 < t^2 and the comparisons inside the near-tie band */
 static int score_h(const double* H, const matches_t* M, double t2, int* amb, uint8_t* flags) {
     int cnt = 0, a = 0;
-    hloc_t L;
-    const int loc = amb ? h_local(H, M->cx, M->cy, &L) : 0;
     for (int j = 0; j < M->n; ++j) {
         double X, Y;
         int in = 0;
@@ -499,14 +417,6 @@ static int score_h(const double* H, const matches_t* M, double t2, int* amb, uin
             double r2 = dx * dx + dy * dy;
             in = r2 < t2;
             if (rel_gap(r2, t2) < ORC_TIE_REL) ++a;
-            else if (loc && fabs(r2 - t2) <= fp32_band_r2(&L, px, py, M->q[2 * j] - px, M->q[2 * j + 1] - py,
-                                                          M->cx, M->cy, t2))
-                ++a;
-        } else if (amb && loc) {
-            /* denominator at or below zero: ambiguous if FP32 could see it positive */
-            const double ux = px - M->cx, uy = py - M->cy;
-            const double den = 1.0 + L.g0 * ux + L.g1 * uy;
-            if (fabs(den) <= ORC_FP32_K * ORC_U32 * (1.0 + fabs(L.g0 * ux) + fabs(L.g1 * uy))) ++a;
         }
         cnt += in;
         if (flags) flags[j] = (uint8_t)in;
@@ -678,22 +588,15 @@ static void fit_cell(const orc_params* P, const double* src, const double* tgt, 
         /* S_R intersect S_C: RANSAC inliers of the final H that are also colour inliers */
         score_h(Hb, &M, t2, NULL, fl);
         int nrc = 0;
-        hloc_t Lb;
-        const int locb = h_local(Hb, cxw, cyw, &Lb);
         for (int j = 0; j < N; ++j) {
             if (!fl[j]) continue;
             double X, Y;
             if (!map_h(Hb, M.p[2 * j], M.p[2 * j + 1], &X, &Y)) continue;
-            /* FP32 position error of the mapped point, and what it can move in the frame test and the colour */
-            const double dp = locb ? fp32_band_pos(&Lb, M.p[2 * j], M.p[2 * j + 1], cxw, cyw) : 0.0;
             if (near_frame_edge(P, X, Y)) ambig = 1;
-            if (fabs(X + ORC_FRAME_TOL) <= dp || fabs(X - (P->W - 1 + ORC_FRAME_TOL)) <= dp ||
-                fabs(Y + ORC_FRAME_TOL) <= dp || fabs(Y - (P->H - 1 + ORC_FRAME_TOL)) <= dp)
-                ambig = 1;
             if (!in_frame(P, X, Y)) continue;
             double d = delta_at(P, src, tgt, ix[j], iy[j], X, Y);
             if (d < P->eps) ++nrc;
-            if (near_colour(d, P->eps) || fabs(d - P->eps) <= bilinear_slope(tgt, P->W, P->H, X, Y) * dp) ambig = 1;
+            if (rel_gap(d, P->eps) < ORC_TIE_REL) ambig = 1;
         }
         mi[ORC_MI_NRC] = nrc;
         if (ambig) mi[ORC_MI_FLAGS] |= ORC_F_AMBIG;

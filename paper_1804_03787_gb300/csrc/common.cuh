@@ -253,8 +253,8 @@ __device__ __forceinline__ int home_index(const AxisGrid& a, int s, int h, int x
 struct __align__(16) Mef {
     float b0, h1, h2h, h2l;
     float h3, b4, h5h, h5l;
-    float g0, g1, e0, pad0;
-    int ox, oy, valid, pad1;
+    float g0, g1, e0, ef;   // ef: rounding bound of the inlier test f (mef_set_bounds), 0 if unset
+    int ox, oy, valid, eden;  // eden: the bits of the denominator's rounding bound (float)
 };
 
 // Splits a flow component t_hi + c (c small) into integer k and fraction f in [0,1).
@@ -298,6 +298,41 @@ __device__ __forceinline__ void round_split(int k, float f, int& v, float& r) {
     }
 }
 
+// ---- certified residual tests
+// The FP32 inlier test below decides f = n.n - t2 den^2 < 0 (and den > 0).
+// A first-order bound of its rounding, valid over a whole window, lets a
+// kernel know when the FP32 sign could differ from the exact one; such a test
+// is then decided again in FP64 (hyp_inlier_fp64).  Coefficients of the form
+// carry at most 4 units of 2^-24 (u) relative error, each operation one.  With
+// U >= |u| and V >= |v| over the window's matches, A = |e0| + (|g0| + |g1|) U
+// (so |e| <= A, den <= 1 + A), B = (|b0| + |h1| + |h3| + |b4|) U, the error of
+// a component of n is at most u (3 |n_c| + D_c), D_x + D_y <= 10 B + 24 U A +
+// 18 V A + 4 (|h2l| + |h5l|), and that of den at most u (6 A + 1).  A test
+// whose exact sign differs from the FP32 one has |f| within the error, so
+// n.n is within 10 % of t2 den^2 there; then
+//   |df| <= u den (12.6 t2 den + 2.1 t (D_x + D_y) + 12 t2 A),
+// taken twice for margin with den <= 1 + A.  If the bound is not small
+// against t2 (strongly projective or far-reaching hypotheses) every test of
+// the hypothesis is decided in FP64.
+__device__ __forceinline__ void mef_set_bounds(Mef& m, float U, float V, float t2) {
+    // FP32 arithmetic on non-negative terms (a few roundings, covered by the 1.001 factor)
+    const float u = 5.9604644775390625e-08f;
+    const float t = sqrtf(t2);
+    const float A = fabsf(m.e0) + (fabsf(m.g0) + fabsf(m.g1)) * U;
+    const float B = (fabsf(m.b0) + fabsf(m.h1) + fabsf(m.h3) + fabsf(m.b4)) * U;
+    // At a possible flip |n| <= 1.05 t den, and n = den (D(u) - v) with D(u) = (h + S) / den the model's flow,
+    // so the match's offset is within 1.05 t of D(u), |D_x| + |D_y| <= (|h2| + |h5| + B + 2 U A) / (1 - A): the
+    // offsets that matter are bounded by the model, whatever far-off (random) matches the window holds.
+    const float h25 = fabsf(m.h2h) + fabsf(m.h5h) + fabsf(m.h2l) + fabsf(m.h5l);
+    if (A < 0.5f) V = fminf(V, (h25 + B + 2.f * U * A) / (1.f - A) + 2.2f * t);
+    const float D = 10.f * B + (24.f * U + 18.f * V) * A + 4.f * (fabsf(m.h2l) + fabsf(m.h5l));
+    const float dmax = 1.f + A;
+    float ef = 2.f * u * dmax * (12.6f * t2 * dmax + 2.1f * t * D + 12.f * t2 * A) * 1.001f;
+    if (!(ef < 0.05f * t2)) ef = 1e30f;  // too loose for the window: each test takes its own bound (mef_inlier_pt)
+    m.ef = ef;
+    m.eden = __float_as_int(2.f * u * (6.f * A + 1.f) * 1.001f);
+}
+
 // Squared-residual test of a match (u, u + v) against the model:
 // ||H(u) - (u + v)||^2 < t2, evaluated as n^2 < t2 den^2 with den > 0.
 __device__ __forceinline__ bool mef_inlier(const Mef& m, float ux, float uy, float vx, float vy, float t2) {
@@ -308,6 +343,68 @@ __device__ __forceinline__ bool mef_inlier(const Mef& m, float ux, float uy, flo
     const float nx = ((m.h2h - vx) + m.h2l) + Sx - vx * e;
     const float ny = ((m.h5h - vy) + m.h5l) + Sy - vy * e;
     return den > 0.f && nx * nx + ny * ny < t2 * den * den;
+}
+
+// The same test, and unc: the FP32 decision may differ from the exact one (the
+// bounds of mef_set_bounds), so the caller decides it again in FP64.
+__device__ __forceinline__ bool mef_inlier_c(const Mef& m, float ux, float uy, float vx, float vy, float t2,
+                                             bool& unc) {
+    const float e = m.e0 + m.g0 * ux + m.g1 * uy;
+    const float den = 1.f + e;
+    const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
+    const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
+    const float nx = ((m.h2h - vx) + m.h2l) + Sx - vx * e;
+    const float ny = ((m.h5h - vy) + m.h5l) + Sy - vy * e;
+    const float n2 = nx * nx + ny * ny, rhs = t2 * den * den;
+    unc = fabsf(n2 - rhs) <= m.ef || fabsf(den) <= __int_as_float(m.eden);
+    return den > 0.f && n2 < rhs;
+}
+
+// A hypothesis whose window-wide bound is too loose (strongly projective, or
+// far-reaching matches against a large local scale).
+__device__ __forceinline__ bool mef_loose(const Mef& m) { return m.ef >= 1e29f; }
+
+// The inlier test with the bound of mef_set_bounds taken at this match alone
+// (A, B, |u|, |v| and n of the match instead of the window's maxima), for
+// loose hypotheses.  unc as in mef_inlier_c.
+__device__ __forceinline__ bool mef_inlier_pt(const Mef& m, float ux, float uy, float vx, float vy, float t2,
+                                              bool& unc) {
+    const float e = m.e0 + m.g0 * ux + m.g1 * uy;
+    const float den = 1.f + e;
+    const float Sx = m.b0 * ux + m.h1 * uy - ux * e;
+    const float Sy = m.h3 * ux + m.b4 * uy - uy * e;
+    const float nx = ((m.h2h - vx) + m.h2l) + Sx - vx * e;
+    const float ny = ((m.h5h - vy) + m.h5l) + Sy - vy * e;
+    const float n2 = nx * nx + ny * ny, rhs = t2 * den * den;
+    const float u = 5.9604644775390625e-08f;
+    const float A = fabsf(m.e0) + fabsf(m.g0 * ux) + fabsf(m.g1 * uy);
+    const float B = fabsf(m.b0 * ux) + fabsf(m.h1 * uy) + fabsf(m.h3 * ux) + fabsf(m.b4 * uy);
+    const float Um = fmaxf(fabsf(ux), fabsf(uy)), Vm = fmaxf(fabsf(vx), fabsf(vy));
+    const float D = 10.f * B + (24.f * Um + 18.f * Vm) * A + 4.f * (fabsf(m.h2l) + fabsf(m.h5l));
+    const float eden = 2.f * u * (6.f * A + 1.f) * 1.0001f;
+    const float dd = fabsf(den) + eden;
+    // the error of f at this match with its own n (the terms of mef_set_bounds without the assumption that
+    // n.n is near t2 den^2): 2 |n_c| dn_c + d(t2 den^2) + the rounding of f, twice for margin
+    const float n1 = fabsf(nx) + fabsf(ny);
+    const float ef = 2.f * u * (8.f * n2 + 2.f * n1 * D + 12.f * t2 * dd * A + 8.f * t2 * dd * dd + 4.f * u * D * D) *
+                     1.0001f;
+    unc = fabsf(n2 - rhs) <= ef || fabsf(den) <= eden;
+    return den > 0.f && n2 < rhs;
+}
+
+// Exact-arithmetic stand-in for the residual test: H in window-local
+// coordinates as doubles (any positive scale, oriented so that the
+// denominator is positive at the window centre), the test in FP64 without a
+// division: den = h6 ux + h7 uy + h8 > 0 and |h_xy . (u, 1) - (u + v) den|^2
+// < t2 den^2.  Its rounding is some 1e-15 of the terms, far inside the
+// 1e-5 near-tie band of the comparison.
+__device__ __forceinline__ bool hyp_inlier_fp64(const double* Hl, float ux, float uy, float vx, float vy, double t2) {
+    const double x = ux, y = uy, qx = (double)ux + (double)vx, qy = (double)uy + (double)vy;
+    const double w = Hl[6] * x + Hl[7] * y + Hl[8];
+    if (!(w > 0.0)) return false;
+    const double nx = Hl[0] * x + Hl[1] * y + Hl[2] - qx * w;
+    const double ny = Hl[3] * x + Hl[4] * y + Hl[5] - qy * w;
+    return nx * nx + ny * ny < t2 * w * w;
 }
 
 // mef_inlier for two matches at once on the packed FP32x2 pipe: each
@@ -348,6 +445,27 @@ __device__ __forceinline__ void mef_inlier2(const Mef2& m, const float4& a, cons
     ia = den.x > 0.f && n2.x < rhs.x;
     ib = den.y > 0.f && n2.y < rhs.y;
 }
+// The same with the uncertainty flags of mef_inlier_c (ef, eden: the form's bounds).
+__device__ __forceinline__ void mef_inlier2_c(const Mef2& m, float ef, float eden, const float4& a, const float4& b,
+                                              float t2, bool& ia, bool& ib, bool& ua, bool& ub) {
+    const float2 ux = make_float2(a.x, b.x), uy = make_float2(a.y, b.y);
+    const float2 vx = make_float2(a.z, b.z), vy = make_float2(a.w, b.w);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 e = __ffma2_rn(m.g1, uy, __ffma2_rn(m.g0, ux, m.e0));
+    const float2 den = __fadd2_rn(make_float2(1.f, 1.f), e);
+    const float2 ne = __fmul2_rn(e, m1);
+    const float2 sx = __ffma2_rn(ux, ne, __ffma2_rn(m.h1, uy, __fmul2_rn(m.b0, ux)));
+    const float2 sy = __ffma2_rn(uy, ne, __ffma2_rn(m.b4, uy, __fmul2_rn(m.h3, ux)));
+    const float2 nx = __ffma2_rn(vx, ne, __fadd2_rn(__fadd2_rn(__ffma2_rn(vx, m1, m.h2h), m.h2l), sx));
+    const float2 ny = __ffma2_rn(vy, ne, __fadd2_rn(__fadd2_rn(__ffma2_rn(vy, m1, m.h5h), m.h5l), sy));
+    const float2 n2 = __ffma2_rn(nx, nx, __fmul2_rn(ny, ny));
+    const float2 rhs = __fmul2_rn(__fmul2_rn(make_float2(t2, t2), den), den);
+    ia = den.x > 0.f && n2.x < rhs.x;
+    ib = den.y > 0.f && n2.y < rhs.y;
+    const float2 f = __fadd2_rn(n2, __fmul2_rn(rhs, m1));
+    ua = fabsf(f.x) <= ef || fabsf(den.x) <= eden;
+    ub = fabsf(f.y) <= ef || fabsf(den.y) <= eden;
+}
 
 // Local homography (double, rows, maps u -> local target) to the evaluation
 // form.  Orientation and scale: denominator +1 at the window centre
@@ -369,10 +487,10 @@ __host__ __device__ inline bool make_mef(const double* Hl, int ox, int oy, Mef& 
     m.g0 = (float)h[6];
     m.g1 = (float)h[7];
     m.e0 = (float)(h[8] - 1.0);
-    m.pad0 = 0.f;
+    m.ef = 0.f;
     m.ox = ox;
     m.oy = oy;
-    m.pad1 = 0;
+    m.eden = 0;
     return true;
 }
 
@@ -429,14 +547,16 @@ struct Labels {
 struct __align__(16) RefitWork {
     long long mom[24];      // exact DLT moments of the winner's inliers about (cx, cy, cu, cv)
     __int128 hx[9];         // the winning hypothesis, exact
-    Mef mef0, mef1;         // evaluation forms (origin 0) of the winner and of the refit
+    Mef mef0, mef1;         // evaluation forms (origin 0) of the winner and of the refit, with test bounds
+    double hl_r[9];         // the refit in window-local coordinates, denominator 1 at the window centre (FP64 tests)
     double ds, dt;          // sums of the inliers' distances to the source / target centroids
     double ha_w[9], ha_r[9];  // absolute homographies of the winner and of the refit
     int cx, cy, cu, cv;     // integer centres of the moments
     int status;             // 2: refit pending (set by the fit), else the window is final
     int nin;                // winner's inliers
     int refit_ok, geo_w, geo_r;
-    int pad[3];
+    float vmax;             // largest |offset| component among the window's matches (test bounds)
+    int pad[2];
 };
 
 struct PairView {

@@ -145,11 +145,11 @@ __host__ __device__ inline bool make_mef_exact(const i128* Hin, Mef& m) {
     m.g0 = i128_to_float(2 * H[6]) * rd;
     m.g1 = i128_to_float(2 * H[7]) * rd;
     m.e0 = i128_to_float(2 * H[8] - dc2) * rd;
-    m.pad0 = 0.f;
+    m.ef = 0.f;
     m.ox = 0;
     m.oy = 0;
     m.valid = 0;
-    m.pad1 = 0;
+    m.eden = 0;
     return true;
 }
 

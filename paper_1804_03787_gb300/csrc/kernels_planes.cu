@@ -6,6 +6,7 @@
 #include "common.cuh"
 #include "hyp_exact.cuh"
 #include "kernels.h"
+#include "../../include/gpm.h"
 
 namespace gpm {
 
@@ -50,6 +51,47 @@ __device__ __forceinline__ float colour_delta(const void* src, const void* tgt, 
     const float4 a = ldpix<ST>(src, py * W + px);
     const float3 b = bilinear<ST>(tgt, W, H, ix, fx, iy, fy);
     return absdiff3(a, b) / 3.f;
+}
+
+// First-order bound of the FP32 error of the position mef_flow gives for local point u (the sum of the x and y
+// errors, px): every term of the flow carries a few units of 2^-24 of its own size.
+__device__ __forceinline__ float mef_pos_bound(const Mef& m, float ux, float uy) {
+    const float ea = fabsf(m.e0) + fabsf(m.g0 * ux) + fabsf(m.g1 * uy);
+    const float den = 1.f + m.e0 + m.g0 * ux + m.g1 * uy;
+    const float sx = fabsf(m.b0 * ux) + fabsf(m.h1 * uy) + fabsf(ux) * ea + fabsf(m.h2h) * ea;
+    const float sy = fabsf(m.h3 * ux) + fabsf(m.b4 * uy) + fabsf(uy) * ea + fabsf(m.h5h) * ea;
+    const float d = fabsf(m.h2h) + fabsf(m.h5h) + (sx + sy) / fmaxf(den, 1e-30f);
+    return 16.f * 5.9604644775390625e-08f * (sx + sy + d * (1.f + ea)) / fmaxf(den, 1e-30f) +
+           1.1920928955078125e-07f * (fabsf(m.h2h) + fabsf(m.h5h));
+}
+
+// The colour-overlap decision of one RANSAC inlier in FP64: the local model Hl
+// (denominator positive at the window centre) maps p, the frame test with the
+// same tolerance, then eq. 3's colour error from the stored texels, bilinear
+// with the point clamped into the frame.  Returns 1 if delta < eps.
+template <int ST>
+__device__ __noinline__ int colour_overlap_fp64(const double* Hl, const void* src, const void* tgt, int W, int H,
+                                                int ox, int oy, int px, int py, float eps) {
+    const double ux = px - ox, uy = py - oy;
+    const double w = Hl[6] * ux + Hl[7] * uy + Hl[8];
+    if (!(w > 0.0)) return 0;
+    const double X = ox + (Hl[0] * ux + Hl[1] * uy + Hl[2]) / w, Y = oy + (Hl[3] * ux + Hl[4] * uy + Hl[5]) / w;
+    if (!(X >= -(double)kFrameTol && X <= W - 1 + (double)kFrameTol && Y >= -(double)kFrameTol &&
+          Y <= H - 1 + (double)kFrameTol))
+        return 0;
+    const double cxp = fmin(fmax(X, 0.0), (double)(W - 1)), cyp = fmin(fmax(Y, 0.0), (double)(H - 1));
+    const int ix = min((int)floor(cxp), W - 1), iy = min((int)floor(cyp), H - 1);
+    const double fx = cxp - ix, fy = cyp - iy;
+    const int ix1 = min(ix + 1, W - 1), iy1 = min(iy + 1, H - 1);
+    const float4 a = ldpix<ST>(tgt, iy * W + ix), b = ldpix<ST>(tgt, iy * W + ix1);
+    const float4 c = ldpix<ST>(tgt, iy1 * W + ix), d = ldpix<ST>(tgt, iy1 * W + ix1);
+    const float4 p = ldpix<ST>(src, py * W + px);
+    const double gx = 1.0 - fx, gy = 1.0 - fy;
+    const double r = gy * (gx * a.x + fx * b.x) + fy * (gx * c.x + fx * d.x);
+    const double g = gy * (gx * a.y + fx * b.y) + fy * (gx * c.y + fx * d.y);
+    const double bb = gy * (gx * a.z + fx * b.z) + fy * (gx * c.z + fx * d.z);
+    const double delta = (fabs(p.x - r) + fabs(p.y - g) + fabs(p.z - bb)) / 3.0;
+    return delta < (double)eps;
 }
 
 // ---------------------------------------------------------------- cooperating groups
@@ -367,13 +409,21 @@ __device__ __forceinline__ void min_eigvec9(const double (&M)[45], double (&x)[9
 #pragma unroll
         for (int i = 0; i < 9; ++i) A[i * (i + 1) / 2 + i] -= floor_shift;
         cholesky9(A, rd);
+        sigma = floor_shift;
     }
     {
         const double s0 = rsqrt_nr(xx);
 #pragma unroll
         for (int i = 0; i < 9; ++i) x[i] *= s0;
     }
-    for (int it = 0; it < 60; ++it) {
+    // Stopping: the step's change is below 1e-12 and, when the iteration converges slowly (a small eigen-gap
+    // against the shift's distance), so is the remaining error extrapolated from the ratio of successive changes
+    // (a small change per step alone would stop a slow iteration far from the vector).  A slow iteration is
+    // re-shifted at the current vector's Rayleigh quotient minus twice its residual (still below the smallest
+    // eigenvalue), a few times at most.
+    double prev = 1e300;
+    int reshifts = 0;
+    for (int it = 0; it < 200; ++it) {
         double y[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {  // L z = x
@@ -406,7 +456,45 @@ __device__ __forceinline__ void min_eigvec9(const double (&M)[45], double (&x)[9
         }
         // 1e-12 is far below what the rescore (1e-5 near-tie band) and the
         // model comparison (1e-6) can see
-        if (diff < 1e-12) break;
+        const double q = diff / prev;  // convergence ratio of the last step
+        prev = diff;
+        if (diff < 1e-12 && (q < 0.5 || diff * q / (1.0 - fmin(q, 0.999999)) < 1e-13)) break;
+        if (it >= 2 && q > 0.5 && reshifts < 4) {
+            double Mx2[9], xx2 = 0, rho2 = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                double t = 0;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) t = fma(M[sym(i, j)], x[j], t);
+                Mx2[i] = t;
+                xx2 = fma(x[i], x[i], xx2);
+                rho2 = fma(x[i], t, rho2);
+            }
+            rho2 /= xx2;
+            double rr2 = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const double r = fma(-rho2, x[i], Mx2[i]);
+                rr2 = fma(r, r, rr2);
+            }
+            const double sig2 = rho2 - 2.0 * sqrt(rr2 / xx2);
+            if (sig2 > sigma) {
+                double B[45], rd2[9];
+#pragma unroll
+                for (int q2 = 0; q2 < 45; ++q2) B[q2] = M[q2];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) B[i * (i + 1) / 2 + i] -= sig2;
+                if (cholesky9(B, rd2)) {
+#pragma unroll
+                    for (int q2 = 0; q2 < 45; ++q2) A[q2] = B[q2];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) rd[i] = rd2[i];
+                    sigma = sig2;
+                    prev = 1e300;
+                }
+            }
+            ++reshifts;
+        }
     }
 }
 
@@ -442,6 +530,20 @@ __device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int 
     return true;
 }
 
+// The exact hypothesis as doubles in window-local coordinates, oriented like
+// its evaluation form (positive denominator at the window centre) and scaled
+// by its largest entry: the FP64 stand-in of the residual test.
+__device__ __forceinline__ void exact_local_fp64(const i128* Hk, double* Hl) {
+    exact_to_double(Hk, Hl, 9);
+    const i128 dc2 = 2 * Hk[8] - (Hk[6] + Hk[7]);
+    double f = 0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) f = fmax(f, fabs(Hl[q]));
+    const double sc = (dc2 < 0 ? -1.0 : 1.0) / f;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Hl[q] *= sc;
+}
+
 // ---------------------------------------------------------------- RANSAC per window
 // Sec. 3.1.2 / 3.2, in three launches per level and stage:
 //   (A) ransac_fit, a group per window: the window's matches (u, u + v(u))
@@ -456,6 +558,84 @@ __device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int 
 
 // Windows with at most this many matches score each hypothesis on one thread.
 constexpr int kLaneScoreMax = 64;
+// Deferred contenders per warp (their exact counts are computed after the scan; beyond this, at once).
+constexpr int kCandMax = 32;
+
+// mef_inlier_pt out of line (loose hypotheses are rare: the callers' loops stay small).
+__device__ __noinline__ bool mef_inlier_pt_ool(const Mef& m, float4 mt, float t2, bool& unc) {
+    return mef_inlier_pt(m, mt.x, mt.y, mt.z, mt.w, t2, unc);
+}
+// The certified test of a match: the FP32 decision, and unc when it is within its rounding bound.
+__device__ __forceinline__ bool cert_inlier(const Mef& m, const float4& mt, float t2, bool& unc) {
+    return mef_loose(m) ? mef_inlier_pt_ool(m, mt, t2, unc) : mef_inlier_c(m, mt.x, mt.y, mt.z, mt.w, t2, unc);
+}
+
+// Support of a loose hypothesis (per-match bounds), the warp's lanes over the
+// matches: the FP32 count and the number of uncertain tests, on every lane.
+// Abandoned (x = -1) once even its optimistic count plus the matches left
+// cannot exceed bound.  Out of line: rare, and the scoring loops stay small in
+// the instruction cache.  tests: residual tests done (counter).
+__device__ __noinline__ int2 loose_score_warp(const float4* match, int N, const Mef& m, float t2, int bound,
+                                              int& tests) {
+    const int lane = threadIdx.x & 31;
+    int s2 = 0, u2 = 0;
+    for (int c = 0; c < N; c += 128) {
+        int sl = 0, ul = 0;
+        for (int j = c + lane; j < min(N, c + 128); j += 32) {
+            const float4 mt = match[j];
+            bool unc;
+            sl += mef_inlier_pt(m, mt.x, mt.y, mt.z, mt.w, t2, unc);
+            ul += unc;
+        }
+        s2 += (int)__reduce_add_sync(FULL, (unsigned)sl);
+        u2 += (int)__reduce_add_sync(FULL, (unsigned)ul);
+        tests += min(128, N - c);
+        if (s2 + u2 + max(N - c - 128, 0) <= bound) return make_int2(-1, 0);
+    }
+    return make_int2(s2, u2);
+}
+
+// The winner's residual test decided in FP64 (its exact form from the refit record).
+__device__ __noinline__ bool winner_inlier_fp64(const i128* hx_global, float4 mt, float t2) {
+    i128 hx[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) hx[q] = hx_global[q];
+    double Hl[9];
+    exact_local_fp64(hx, Hl);
+    return hyp_inlier_fp64(Hl, mt.x, mt.y, mt.z, mt.w, (double)t2);
+}
+
+// Exact support of hypothesis k: every match tested by the certified FP32
+// test, the uncertain ones again in FP64 with the hypothesis drawn once more
+// (exact); the warp's lanes over the matches (every lane gets the score).  Used
+// for a hypothesis whose FP32 count, with its uncertain tests, could still win.
+// nfp64 counts the lane's FP64 decisions.
+__device__ __noinline__ int exact_score_warp(const float4* match, int N, int cell, int k, uint32_t tag,
+                                             uint32_t pair_id, uint32_t k0, uint32_t k1, const Mef& m, float t2,
+                                             int& nfp64) {
+    const int lane = threadIdx.x & 31;
+    double Hl[9];
+    {
+        i128 Hk[9];
+        draw_hypothesis(match, N, cell, k, tag, pair_id, k0, k1, Hk);
+        exact_local_fp64(Hk, Hl);
+    }
+    int score = 0;
+    for (int c = 0; c < N; c += 32) {
+        const int j = c + lane;
+        bool in = false, unc = false;
+        if (j < N) {
+            const float4 mt = match[j];
+            in = cert_inlier(m, mt, t2, unc);
+            if (unc) {
+                in = hyp_inlier_fp64(Hl, mt.x, mt.y, mt.z, mt.w, (double)t2);
+                ++nfp64;
+            }
+        }
+        score += __popc(__ballot_sync(FULL, in));
+    }
+    return score;
+}
 
 // Exact integer of a small integer-valued float: adding 1.5 * 2^23 puts it in
 // the low mantissa bits (no conversion instruction).
@@ -502,32 +682,23 @@ __device__ int gather_matches(const G& grp, const PairView& pv, const LevelGeom&
     return N;
 }
 
-// Sum of |(a, b)| over a lane's points, for exact integers a, b: FP32 roots
-// of exact inputs (|a|, |b| < 2^24; one rounding of the sum of squares and
-// one of the root) added with Kahan compensation (a couple of units of
-// rounding in total, whatever the count), larger inputs in FP64.
+// Sum of |(a, b)| over a lane's points, for exact integers a, b: each root in
+// FP64 of the exact sum of squares, added in FP64.  The least-squares refit of
+// a thin, ill-conditioned support moves with its Hartley normalisation, so the
+// scale carries FP64 rounding only (with FP32 roots, refits moved by ~1e-6).
 struct DistSum {
-    float s = 0.f, c = 0.f;
-    double big = 0.0;
+    double s = 0.0;
     __device__ __forceinline__ void add(int a, int b) {
-        if (a > -16777216 && a < 16777216 && b > -16777216 && b < 16777216) {
-            const float fa = (float)a, fb = (float)b;
-            const float y = sqrtf(fmaf(fa, fa, fb * fb)) - c;
-            const float t = s + y;
-            c = (t - s) - y;
-            s = t;
-        } else {
-            const double da = (double)a, db = (double)b;
-            big += sqrt(da * da + db * db);
-        }
+        const double da = (double)a, db = (double)b;
+        s += sqrt(fma(da, da, db * db));
     }
-    __device__ __forceinline__ double total() const { return ((double)s - (double)c) + big; }
+    __device__ __forceinline__ double total() const { return s; }
 };
 
 template <class G, int ST>
 __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
                            const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, int* kfull,
-                           Mef* wmef) {
+                           Mef* wmef, int* cand) {
     const int tid = grp.rank();
     const int id = (g.base + cell) * 2 + (stage - 1);
     int* mi = pv.mi[dir] + (size_t)id * kMI;
@@ -547,6 +718,15 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
         rw->status = 0;
     }
     if (N < pp.min_inliers || N < 4) return;
+    // the largest |offset| component among the matches, and the window's half side: the bounds of the FP32 tests
+    float vloc = 0.f;
+    for (int j = tid; j < N; j += G::size) {
+        const float4 mt = match[j];
+        vloc = fmaxf(vloc, fmaxf(fabsf(mt.z), fabsf(mt.w)));
+    }
+    const float V = (float)grp.max((unsigned long long)vloc);  // integers: exact as a key
+    const float U = 0.5f * (float)g.s;
+    if (tid == 0) rw->vmax = V;
 
     // Hypotheses.  Few matches: each thread draws and scores its own
     // hypotheses k = rank, rank + size, ... in full.  Otherwise each warp of
@@ -565,26 +745,84 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     const int lane = tid & 31;
     Mef* hb = hyp + (tid >> 5) * 32;
     int best_score = -1, best_k = 0x7fffffff, tests = 0;
+    // Deferred exact counts: a hypothesis that completes as a contender while some of its tests are uncertain
+    // goes on its warp's list (index, FP32 count, uncertain tests), and only its certain lower count
+    // (count - uncertain) raises the abandon bound; after the scan, the listed hypotheses whose optimistic
+    // count can still win get their exact counts.  Most contenders of an early, low bound never need one.
+    // (cand: the group's lists, one per warp of the group.)
+    int* cl = cand + (tid >> 5) * (3 * kCandMax);
+    int ncand = 0, lo_bound = -1;
+    int nfp64 = 0, nloose = 0;  // tests decided in FP64, hypotheses tested with per-match bounds (counters)
     if (N <= kLaneScoreMax) {
+        int group_best = -1;  // the group's best exact count after the previous rounds
         for (int r = 0; r * G::size < pp.num_hyp; ++r) {
             const int k = r * G::size + tid;
-            i128 Hk[9];
             Mef m;
-            if (k < pp.num_hyp && draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk) &&
-                make_mef_exact(Hk, m)) {
-                int score = 0;
-                for (int j = 0; j < N; ++j) {
-                    const float4 mt = match[j];
-                    score += mef_inlier(m, mt.x, mt.y, mt.z, mt.w, t2);
+            bool ok = false;
+            if (k < pp.num_hyp) {
+                i128 Hk[9];
+                ok = draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk) && make_mef_exact(Hk, m);
+            }
+            // FP32 count and uncertain tests: the exact count is within score +- unc_n
+            int score = 0, unc_n = 0;
+            bool loose = false;
+            if (ok) {
+                mef_set_bounds(m, U, V, t2);
+                loose = mef_loose(m);
+                nloose += loose;
+                if (!loose) {
+                    for (int j = 0; j < N; ++j) {
+                        const float4 mt = match[j];
+                        bool unc;
+                        score += mef_inlier_c(m, mt.x, mt.y, mt.z, mt.w, t2, unc);
+                        unc_n += unc;
+                    }
                 }
                 tests += N;
-                if (score > best_score) {
-                    best_score = score;
-                    best_k = k;
+            }
+            hb[lane] = m;
+            __syncwarp();
+            // loose hypotheses (per-match bounds): the warp scores them together, lanes over the matches
+            for (unsigned lm = __ballot_sync(FULL, loose); lm; lm &= lm - 1) {
+                const int l = __ffs(lm) - 1;
+                int tl = 0;
+                const int2 su = loose_score_warp(match, N, hb[l], t2, -1, tl);
+                if (lane == l) {
+                    score = su.x;
+                    unc_n = su.y;
                 }
+            }
+            // a contender with uncertain tests (it could beat the best so far: this thread's, the group's of
+            // earlier rounds) is deferred; without uncertain tests its count is exact
+            const bool contend = ok && score + unc_n > max(max(best_score, lo_bound), group_best);
+            for (unsigned rm = __ballot_sync(FULL, contend && unc_n > 0); rm; rm &= rm - 1) {
+                const int l = __ffs(rm) - 1;
+                const int kl = __shfl_sync(FULL, k, l), sl = __shfl_sync(FULL, score, l);
+                const int ul = __shfl_sync(FULL, unc_n, l);
+                if (ncand < kCandMax) {
+                    if (lane == 0) {
+                        cl[3 * ncand] = kl;
+                        cl[3 * ncand + 1] = sl;
+                        cl[3 * ncand + 2] = ul;
+                    }
+                    ++ncand;
+                    if (lane == l) lo_bound = max(lo_bound, score - unc_n);
+                } else {  // list full: its exact count now
+                    int f = 0;
+                    const int ex = exact_score_warp(match, N, cell, kl, tag, pv.pair_id, pp.k0, pp.k1, hb[l], t2, f);
+                    const unsigned tf = __reduce_add_sync(FULL, (unsigned)f);
+                    if (lane == 0) nfp64 += (int)tf;
+                    if (lane == l) unc_n = 0, score = ex;
+                }
+            }
+            __syncwarp();
+            if (ok && unc_n == 0 && score > best_score) {
+                best_score = score;
+                best_k = k;
             }
             // all N matches inliers: every later round has higher indices and can at most tie
             if (grp.any(best_score >= N)) break;
+            group_best = (int)grp.max((unsigned long long)(max(best_score, lo_bound) + 1)) - 1;
         }
     }
     for (int b = tid >> 5; N > kLaneScoreMax && b * 32 < pp.num_hyp; b += NW) {
@@ -596,7 +834,11 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             i128 Hk[9];
             Mef m;
             ok = draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk) && make_mef_exact(Hk, m);
-            if (ok) hb[lane] = m;
+            if (ok) {
+                mef_set_bounds(m, U, V, t2);
+                nloose += mef_loose(m);
+                hb[lane] = m;
+            }
         }
         unsigned todo = __ballot_sync(FULL, ok);
         __syncwarp();
@@ -604,25 +846,57 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             const int l = __ffs(todo) - 1;
             todo &= todo - 1;
             const Mef2 m2 = mef2_of(hb[l]);
-            // abandon when reach < group best or reach <= this warp's best
-            const int bound = max(NW > 1 ? *(volatile int*)gbest - 1 : -1, best_score);
-            int score = 0;
+            const float ef = hb[l].ef, eden = __int_as_float(hb[l].eden);
+            const bool loose = mef_loose(hb[l]);  // warp-uniform
+            const int kl = b * 32 + l;
+            // abandon when reach < group best or reach <= this warp's best (exact, or a deferred contender's
+            // certain lower count)
+            const int bound = max(NW > 1 ? *(volatile int*)gbest - 1 : -1, max(best_score, lo_bound));
+            int score = 0, unc_n = 0;  // FP32 count, uncertain tests: the exact count is within score +- unc_n
             bool alive = true;
-            for (int c = 0; c < N; c += 128) {
+            if (loose) {  // per-match bounds, out of line
+                const int2 su = loose_score_warp(match, N, hb[l], t2, bound, tests);
+                score = su.x;
+                unc_n = su.y;
+                alive = su.x >= 0 && score + unc_n > bound;
+            }
+            for (int c = 0; !loose && c < N; c += 128) {
+                int uc = 0;  // this lane's uncertain tests in the chunk
 #pragma unroll
                 for (int u = 0; u < 4; u += 2) {  // matches j and j + 32 of this lane, tested as a pair
                     const int j = c + 32 * u + lane;
                     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
                     const float4 ma = j < N ? match[j] : z, mb = j + 32 < N ? match[j + 32] : z;
-                    bool ia, ib;
-                    mef_inlier2(m2, ma, mb, t2, ia, ib);
+                    bool ia, ib, ua, ub;
+                    mef_inlier2_c(m2, ef, eden, ma, mb, t2, ia, ib, ua, ub);
+                    uc += (ua && j < N) + (ub && j + 32 < N);
                     score += __popc(__ballot_sync(FULL, ia && j < N)) + __popc(__ballot_sync(FULL, ib && j + 32 < N));
                 }
+                if (__any_sync(FULL, uc != 0)) unc_n += (int)__reduce_add_sync(FULL, (unsigned)uc);
                 tests += min(128, N - c);
-                if (score + max(N - c - 128, 0) <= bound) {
+                // abandoned only if even every uncertain test turning in its favour could not win
+                if (score + unc_n + max(N - c - 128, 0) <= bound) {
                     alive = false;
                     break;
                 }
+            }
+            if (alive && unc_n > 0) {  // a contender with uncertain tests: deferred (or, list full, counted now)
+                if (ncand < kCandMax) {
+                    if (lane == 0) {
+                        cl[3 * ncand] = kl;
+                        cl[3 * ncand + 1] = score;
+                        cl[3 * ncand + 2] = unc_n;
+                    }
+                    ++ncand;
+                    lo_bound = max(lo_bound, score - unc_n);
+                    if (NW > 1 && lane == 0) atomicMax(gbest, score - unc_n);
+                    continue;
+                }
+                int f = 0;
+                score = exact_score_warp(match, N, cell, kl, tag, pv.pair_id, pp.k0, pp.k1, hb[l], t2, f);
+                const unsigned tf = __reduce_add_sync(FULL, (unsigned)f);
+                if (lane == 0) nfp64 += (int)tf;
+                alive = score > bound;
             }
             if (alive) {  // more inliers than every earlier hypothesis of this warp
                 best_score = score;
@@ -635,9 +909,47 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
         }
         __syncwarp();
     }
-    if (pv.evals) {  // residual tests performed (profiling)
+    // the deferred contenders that can still win: their exact counts (hypothesis order, so ties keep the lower
+    // index).  A contender whose optimistic count is below the group's bound cannot win.
+    {
+        const int gb = N > kLaneScoreMax ? (NW > 1 ? *(volatile int*)gbest : -1) : -1;
+        const int gx = (int)grp.max((unsigned long long)(best_score + 1)) - 1;  // the group's best exact count
+        for (int c = 0; c < ncand; ++c) {
+            const int kc = cl[3 * c], hi = cl[3 * c + 1] + cl[3 * c + 2];
+            const int owner = N <= kLaneScoreMax ? (kc & 31) : lane;  // the lane whose best it may become
+            const int ob = __shfl_sync(FULL, best_score, owner), obk = __shfl_sync(FULL, best_k, owner);
+            if (hi < gb || hi < gx || hi < ob || (hi == ob && kc > obk)) continue;
+            // the hypothesis's evaluation form again (its drawing lane wrote it to hb in its round)
+            Mef m;
+            if (lane == 0) {
+                i128 Hk[9];
+                draw_hypothesis(match, N, cell, kc, tag, pv.pair_id, pp.k0, pp.k1, Hk);
+                make_mef_exact(Hk, m);
+                mef_set_bounds(m, U, V, t2);
+                hb[0] = m;
+            }
+            __syncwarp();
+            m = hb[0];
+            __syncwarp();
+            int f = 0;
+            const int ex = exact_score_warp(match, N, cell, kc, tag, pv.pair_id, pp.k0, pp.k1, m, t2, f);
+            const unsigned tf = __reduce_add_sync(FULL, (unsigned)f);
+            if (lane == 0) nfp64 += (int)tf;
+            if (lane == owner && (ex > best_score || (ex == best_score && kc < best_k))) {
+                best_score = ex;
+                best_k = kc;
+            }
+        }
+    }
+    if (pv.evals) {  // residual tests performed, those decided in FP64, loose hypotheses (profiling)
         const int t = grp.sum(N <= kLaneScoreMax || lane == 0 ? tests : 0);
-        if (tid == 0) atomicAdd(&pv.evals[2], (unsigned long long)t);
+        const int f = grp.sum(nfp64);
+        const int lo = grp.sum(N <= kLaneScoreMax || lane == 0 ? nloose : 0);
+        if (tid == 0) {
+            atomicAdd(&pv.evals[GPM_COUNT_RANSAC], (unsigned long long)t);
+            atomicAdd(&pv.evals[GPM_COUNT_RANSAC_FP64], (unsigned long long)f);
+            atomicAdd(&pv.evals[GPM_COUNT_RANSAC_LOOSE], (unsigned long long)lo);
+        }
     }
     // most inliers, then lowest hypothesis index
     const unsigned long long key =
@@ -657,6 +969,7 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
         if (tid == 0) {
             Mef m0;
             make_mef_exact(Hk, m0);
+            mef_set_bounds(m0, U, V, t2);
             *wmef = m0;
             rw->mef0 = m0;
             mi[MI_BESTK] = wk;
@@ -673,10 +986,16 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     // sums), mean distances, and the DLT moments as exact integers about the
     // rounded centroids
     const Mef wm = *wmef;
+    // the winner's inlier test, certified: an uncertain one is decided in FP64 with the exact winner
+    auto winner_inlier = [&](const float4& mt) -> bool {
+        bool unc;
+        const bool in = cert_inlier(wm, mt, t2, unc);
+        return unc ? winner_inlier_fp64(rw->hx, mt, t2) : in;
+    };
     int sx = 0, sy = 0, tx = 0, ty = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
-        if (mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) {
+        if (winner_inlier(mt)) {
             sx += exact_int(mt.x);
             sy += exact_int(mt.y);
             tx += exact_int(mt.x + mt.z);
@@ -701,7 +1020,7 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     for (int q = 0; q < 24; ++q) R[q] = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
-        if (!mef_inlier(wm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
+        if (!winner_inlier(mt)) continue;
         dsum.add(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
         dtsum.add(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
         const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
@@ -835,7 +1154,14 @@ __global__ void __launch_bounds__(64) k_refit_solve(PairView pv, LevelGeom g, Pl
         }
     Mef m1;
     if (!make_mef(Hr, 0, 0, m1)) return;
+    mef_set_bounds(m1, 0.5f * (float)g.s, rw->vmax, pp.t2);
     rw->mef1 = m1;
+    {
+        // the refit for FP64 tests: denominator 1 at the window centre (-0.5, -0.5), as its evaluation form
+        const double k = 1.0 / (Hr[8] - 0.5 * (Hr[6] + Hr[7]));
+#pragma unroll
+        for (int q = 0; q < 9; ++q) rw->hl_r[q] = Hr[q] * k;
+    }
     rw->geo_r = plane_geometry_ok(Hr, g.s, pp.radius, pp.scale_min, pp.scale_max) ? 1 : 0;
     local_to_abs(Hr, ox, oy, rw->ha_r);
     rw->refit_ok = 1;
@@ -865,12 +1191,26 @@ __device__ void ransac_finish(const G& grp, const PairView& pv, const LevelGeom&
         const Mef rm = rw->mef1;
         for (int j = tid; j < N; j += G::size) {
             const float4 mt = match[j];
-            rcount += mef_inlier(rm, mt.x, mt.y, mt.z, mt.w, t2);
+            bool unc;
+            bool in = cert_inlier(rm, mt, t2, unc);
+            if (unc) in = hyp_inlier_fp64(rw->hl_r, mt.x, mt.y, mt.z, mt.w, (double)t2);
+            rcount += in;
         }
     }
     rcount = grp.sum(rcount);
     const bool use_refit = have_refit && rcount >= wscore;
     Mef fm = use_refit ? rw->mef1 : rw->mef0;
+    // the chosen model in FP64 (local coordinates), for decisions the FP32 form cannot certify
+    double Hl[9];
+    if (use_refit) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Hl[q] = rw->hl_r[q];
+    } else {
+        i128 hx[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) hx[q] = rw->hx[q];
+        exact_local_fp64(hx, Hl);
+    }
     const int count = use_refit ? rcount : wscore;
     const void* src = pv.img[dir];
     const void* tgt = pv.img[1 - dir];
@@ -879,12 +1219,37 @@ __device__ void ransac_finish(const G& grp, const PairView& pv, const LevelGeom&
     int nrc = 0;
     for (int j = tid; j < N; j += G::size) {
         const float4 mt = match[j];
-        if (!mef_inlier(fm, mt.x, mt.y, mt.z, mt.w, t2)) continue;
+        bool unc;
+        bool in = cert_inlier(fm, mt, t2, unc);
+        if (unc) in = hyp_inlier_fp64(Hl, mt.x, mt.y, mt.z, mt.w, (double)t2);
+        if (!in) continue;
         const int px = ox + (int)mt.x, py = oy + (int)mt.y;
         int ix, iy, kx, ky;
         float fx, fy;
-        if (!plane_target(fm, px, py, W, H, ix, fx, iy, fy, kx, ky)) continue;
-        nrc += colour_delta<ST>(src, tgt, W, H, px, py, ix, fx, iy, fy) < pp.eps;
+        // certified: a frame test or colour decision within the FP32 position error (times the largest
+        // texel difference, 2) is taken again in FP64
+        const float dp = mef_pos_bound(fm, mt.x, mt.y);
+        bool sure = mef_flow(fm, mt.x, mt.y, kx, fx, ky, fy);
+        int dec = 0;
+        if (sure) {
+            ix = px + kx;
+            iy = py + ky;
+            const float X = (float)ix + fx, Y = (float)iy + fy;
+            const float e0 = -kFrameTol, ex = (float)(W - 1) + kFrameTol, ey = (float)(H - 1) + kFrameTol;
+            sure = fabsf(X - e0) > dp && fabsf(X - ex) > dp && fabsf(Y - e0) > dp && fabsf(Y - ey) > dp;
+            if (sure) {
+                if (in_frame_tol(ix, fx, W) && in_frame_tol(iy, fy, H)) {
+                    const float dl = colour_delta<ST>(src, tgt, W, H, px, py, ix, fx, iy, fy);
+                    sure = fabsf(dl - pp.eps) > 2.f * dp + 1e-6f;
+                    dec = dl < pp.eps;
+                }
+            }
+        } else {
+            // the FP32 denominator is not positive: certain unless it is within its rounding of zero
+            const float den = 1.f + fm.e0 + fm.g0 * mt.x + fm.g1 * mt.y;
+            sure = fabsf(den) > __int_as_float(fm.eden);
+        }
+        nrc += sure ? dec : colour_overlap_fp64<ST>(Hl, src, tgt, W, H, ox, oy, px, py, pp.eps);
     }
     nrc = grp.sum(nrc);
     if (tid == 0) {
@@ -907,6 +1272,7 @@ __global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g
                                                      PlaneParams pp) {
     extern __shared__ float4 warp_dyn[];
     __shared__ Mef wmef[8];
+    __shared__ int cand[8 * 3 * kCandMax];
     const int warp = threadIdx.x >> 5;
     const int cell = blockIdx.x * 8 + warp;
     if (cell >= g.ncells()) return;
@@ -914,7 +1280,7 @@ __global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g
     Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + 8 * 256) + warp * 32;
     WarpGroup grp;
     ransac_fit<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, nullptr,
-                              &wmef[warp]);
+                              &wmef[warp], cand + warp * 3 * kCandMax);
 }
 template <int ST>
 __global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
@@ -937,9 +1303,10 @@ __global__ void __launch_bounds__(256, 3) k_ransac_block(PairView pv, LevelGeom 
     __shared__ Mef hyp[8 * 32];
     __shared__ Mef wmef;
     __shared__ int gbest, kfull;
+    __shared__ int cand[8 * 3 * kCandMax];
     BlockGroup<256> grp{red_d, red_i, red_u};
     ransac_fit<BlockGroup<256>, ST>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, hyp, &gbest,
-                                    &kfull, &wmef);
+                                    &kfull, &wmef, cand);
 }
 template <int ST>
 __global__ void __launch_bounds__(256) k_ransac_finish_block(PairView pv, LevelGeom g, int stage, PlaneParams pp) {

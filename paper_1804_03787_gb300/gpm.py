@@ -26,8 +26,8 @@ EXPORTED = ["gpm_default_params", "gpm_create", "gpm_destroy", "gpm_required_byt
             "gpm_import", "gpm_status_string", "gpm_last_error", "gpm_launch_count", "gpm_profile_enable",
             "gpm_profile_select", "gpm_profile_read", "gpm_ingest_noalloc", "gpm_fp32_peak_probe"]
 (COUNT_SWEEP0, COUNT_SWEEP_PLANE, COUNT_RANSAC, COUNT_INIT, COUNT_SWEEP0_TAPS, COUNT_SWEEP_PLANE_TAPS,
- COUNT_SWEEP0_PRUNED) = range(7)
-COUNTERS = 7
+ COUNT_SWEEP0_PRUNED, COUNT_RANSAC_FP64, COUNT_RANSAC_LOOSE) = range(9)
+COUNTERS = 9
 PROF_CLASSES = ["ingest", "pm_init", "pm_sweep", "pm_sweep_plane", "pm_recost", "ransac", "assign", "cues",
                 "many_to_one", "merge", "lists", "fill", "final"]
 
@@ -240,8 +240,8 @@ class Context:
     def profile_read(self):
         """{class: (ms, launches)} and the work counts (a tuple indexed by the COUNT_* constants: level-0 sweep
         evaluations, plane-level sweep evaluations, RANSAC residual tests, init / recost evaluations, taps summed by
-        the level-0 sweeps, taps summed by the plane-level sweeps, level-0 candidates rejected by the patch-sum bound);
-        clears them."""
+        the level-0 sweeps, taps summed by the plane-level sweeps, level-0 candidates rejected by the patch-sum bound,
+        RANSAC tests decided in FP64, RANSAC hypotheses tested with per-match bounds); clears them."""
         k = len(PROF_CLASSES)
         ms = (C.c_double * k)()
         ln = (C.c_uint64 * k)()

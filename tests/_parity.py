@@ -9,6 +9,7 @@ such an ambiguity upstream of it.
 import numpy as np
 
 import oracle as O
+from paper_1804_03787_gb300.gpm import LABELS as LABELS_KIND, MODELS as MODELS_KIND
 
 TIE = 1e-5
 
@@ -128,3 +129,33 @@ def final_map_check(ctx, P, frames, flow_t, occ_t, samples, seed):
         assert occ[i] == (1 if delta >= thr else 0), (x, y, delta, thr, occ[i])
         n_checked += 1
     return n_plane, n_checked
+
+
+def end_to_end_stats(ctx, R, gflow, oflow, gt, occ_gt, H, W):
+    """End-to-end comparison of the whole method (direction 0): pixels with a plane on both sides, where the
+    paper's final flow is the plane's mapping (Sec. 3.4.1), and the rest, which keep an NNF offset from the random
+    search (any near tie upstream can change such an offset by many pixels).  Returns a dict of the agreement
+    fractions and the EPE (against the scenes' ground truth, non-occluded pixels) of each side on each set."""
+    gm = ctx.export(LABELS_KIND)[0][0].reshape(H, W)
+    om = R.acc[0].m.reshape(H, W)
+    both = (gm >= 0) & (om >= 0)
+    d = np.hypot(*(gflow - oflow).transpose(2, 0, 1))
+    eg = np.hypot(*(gflow - gt).transpose(2, 0, 1))
+    eo = np.hypot(*(oflow - gt).transpose(2, 0, 1))
+    vis = occ_gt == 0
+    pv = both & vis
+    # the same plane on both sides (the same model, fitted to the same homography): the same decision, so the
+    # flows differ only by FP32 against FP64 arithmetic
+    gmh, omh = ctx.export(MODELS_KIND)[0], R.mh[0]
+    nm = omh.shape[0]
+    hs = np.array([np.abs(norm_h(gmh[m]) - norm_h(omh[m])).max() < 1e-6 if omh[m].any() else False
+                   for m in range(nm)])
+    same = (gm == om) & (gm >= 0) & hs[np.clip(gm, 0, nm - 1)]
+    sv = same & vis
+    return dict(agree=float(np.mean(d < 1e-4)), plane_share=float(both.mean()),
+                plane_agree=float(np.mean(d[both] < 1e-4)), plane_flow_diff=float(d[both].mean()),
+                epe_plane_gpu=float(eg[pv].mean()), epe_plane_oracle=float(eo[pv].mean()),
+                same_share=float(same.mean()), same_max_flow_diff=float(d[same].max()) if same.any() else 0.0,
+                epe_same_gpu=float(eg[sv].mean()), epe_same_oracle=float(eo[sv].mean()),
+                epe_gpu=float(eg[vis].mean()), epe_oracle=float(eo[vis].mean()),
+                label_agree=float(np.mean(gm == om)))

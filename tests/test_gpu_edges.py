@@ -11,7 +11,7 @@ import pytest
 import oracle as O
 from paper_1804_03787_gb300 import gpm, scene
 
-from _parity import final_map_check, oracle_frames, oracle_params, ransac_equal
+from _parity import end_to_end_stats, final_map_check, oracle_frames, oracle_params, ransac_equal
 
 pytestmark = pytest.mark.gpu
 
@@ -273,15 +273,19 @@ def test_plane_validity_rules_on_hand_built_matches(torch, r, min_in, scenarios)
 def test_parameter_extremes_end_to_end(torch, kw):
     """The tiny configuration at the ends of the parameter ranges the library accepts (one RANSAC hypothesis per
     window; the most hypotheses with the smallest support; no fill and a single PatchMatch iteration): the whole
-    method against the oracle, with the bars of the tiny end-to-end test."""
+    method against the oracle, with the bars of the tiny end-to-end test (plane pixels: EPE within 1e-3 px)."""
     s = scene.tiny_scene(2)
     gp = gpm.default_params(**kw)
-    ctx, (gf, _), (of, _) = _both(torch, gp, s.frame1, s.frame2)
+    ctx = gpm.Context(gp, 128, 96)
+    flows, _ = ctx.run([_dev(torch, s.frame1, s.frame2)])
+    torch.cuda.synchronize()
+    R = O.run(oracle_params(gp, 128, 96), s.frame1, s.frame2)
+    st = end_to_end_stats(ctx, R, flows[0].cpu().numpy(), R.flow[0].reshape(96, 128, 2), s.flow, s.occ, 96, 128)
     ctx.close()
-    vis = s.occ == 0
-    agree = np.mean(np.hypot(*(gf - of).transpose(2, 0, 1)) < 1e-4)
-    epe_g = np.hypot(*(gf - s.flow).transpose(2, 0, 1))[vis].mean()
-    epe_o = np.hypot(*(of - s.flow).transpose(2, 0, 1))[vis].mean()
-    print(f"{kw}: flow agreement {agree:.4f}, EPE nocc gpu {epe_g:.4f} oracle {epe_o:.4f}")
-    assert agree > 0.95
-    assert abs(epe_g - epe_o) < 0.01
+    print(kw, {k: round(v, 5) for k, v in st.items()})
+    # the same plane decision: the flows agree within the FP32 mapping's error, the EPE within 1e-3 px
+    assert st["same_share"] > 0.6 and st["same_max_flow_diff"] < 1e-3, st
+    assert abs(st["epe_same_gpu"] - st["epe_same_oracle"]) <= 1e-3, st
+    # different plane decisions (near ties between overlapping windows' fits of one surface) are few
+    assert st["label_agree"] > 0.98 and st["plane_agree"] > 0.97, st
+    assert st["agree"] > 0.95 and abs(st["epe_gpu"] - st["epe_oracle"]) < 0.05, st

@@ -458,9 +458,10 @@ def test_fullsize_ransac_every_window_every_level(torch, pair):
     ctx.close()
     print(f"windows checked {checked}, fits flagged as near ties {flagged}, differing (all flagged) {differ}")
     # near ties explain few differences; the flagged share is bounded too, so that a band grown too wide cannot
-    # excuse the comparison wholesale (measured: 10 % of fits flagged, 0.2 % differing)
-    assert differ <= checked // 100, (differ, checked)
-    assert flagged <= 0.15 * checked, (flagged, checked)
+    # excuse the comparison wholesale.  The oracle flags only comparisons within 1e-5 relative in FP64 (and
+    # refits whose normal matrix is nearly singular): measured 4.4 % of fits flagged, 0.15 % differing
+    assert differ <= checked // 200, (differ, checked)
+    assert flagged <= 0.06 * checked, (flagged, checked)
 
 
 def test_fullsize_final_map_properties(torch, pair):

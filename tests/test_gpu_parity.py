@@ -14,7 +14,7 @@ import pytest
 import oracle as O
 from paper_1804_03787_gb300 import gpm, scene
 
-from _parity import COLOUR_ATOL, TIE, dilate, norm_h, oracle_frames, oracle_params, rel_close
+from _parity import end_to_end_stats, COLOUR_ATOL, TIE, dilate, norm_h, oracle_frames, oracle_params, rel_close
 from _parity import ransac_equal as _ransac_equal
 
 pytestmark = pytest.mark.gpu
@@ -350,7 +350,12 @@ def test_fill_and_final_lockstep(torch, W, H, r, cells):
 
 # ---------------------------------------------------------------- whole method
 def test_tiny_config_end_to_end(torch):
-    """128x96, 2 layers, r=3, cells 32/16/8, 4 iterations, 256 hypotheses."""
+    """128x96, 2 layers, r=3, cells 32/16/8, 4 iterations, 256 hypotheses: the whole method against the oracle.
+    Where both sides give a pixel the same plane, its final flow is that plane's mapping (Sec. 3.4.1): the flows
+    agree within the FP32 mapping's error and their EPE against the ground truth within 1e-3 px.  Different plane
+    choices come from near ties between overlapping windows' fits of one surface and are few.  Pixels without a
+    plane keep their NNF offsets from the random search, where a near tie upstream changes an offset by many
+    pixels: the whole frame's agreement and EPE are bounded more loosely."""
     s = scene.tiny_scene(0)
     gp = gpm.default_params()
     ctx = _ctx(torch, gp, 128, 96)
@@ -358,19 +363,17 @@ def test_tiny_config_end_to_end(torch):
     flows, occs = ctx.run([(f1, f2)])
     torch.cuda.synchronize()
     gflow = flows[0].cpu().numpy()
-    gocc = occs[0].cpu().numpy()
     P = oracle_params(gp, 128, 96)
     R = O.run(P, s.frame1, s.frame2)
     oflow = R.flow[0].reshape(96, 128, 2)
-    oocc = R.occ[0].reshape(96, 128)
-    epe_g = np.hypot(*(gflow - s.flow).transpose(2, 0, 1))
-    epe_o = np.hypot(*(oflow - s.flow).transpose(2, 0, 1))
-    vis = s.occ == 0
-    agree = np.mean(np.hypot(*(gflow - oflow).transpose(2, 0, 1)) < 1e-4)
-    print(f"tiny: flow agreement {agree:.4f}, occ agreement {np.mean(gocc == oocc):.4f}, "
-          f"EPE nocc gpu {epe_g[vis].mean():.4f} oracle {epe_o[vis].mean():.4f}")
-    assert agree > 0.95
-    assert abs(epe_g[vis].mean() - epe_o[vis].mean()) < 0.01
+    st = end_to_end_stats(ctx, R, gflow, oflow, s.flow, s.occ, 96, 128)
+    print("tiny:", {k: round(v, 5) for k, v in st.items()})
+    # the same plane decision: the flows agree within the FP32 mapping's error, the EPE within 1e-3 px
+    assert st["same_share"] > 0.8 and st["same_max_flow_diff"] < 1e-3, st
+    assert abs(st["epe_same_gpu"] - st["epe_same_oracle"]) <= 1e-3, st
+    # different plane decisions (near ties between overlapping windows' fits of one surface) are few
+    assert st["label_agree"] > 0.98 and st["plane_agree"] > 0.97, st
+    assert st["agree"] > 0.95 and abs(st["epe_gpu"] - st["epe_oracle"]) < 0.01, st
     ctx.close()
 
 

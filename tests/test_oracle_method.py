@@ -376,11 +376,16 @@ def test_translating_layer_scene_occlusion_and_flow():
     occ_gt = (~rect(xs, ys)) & rect(xs - t, ys)   # background covered in frame 2
     s = scene.Scene(frame1=f1.astype(np.float32), frame2=f2.astype(np.float32), flow=gt.astype(np.float32),
                     occ=occ_gt.astype(np.uint8), layer_id=rect(xs, ys).astype(np.int16))
-    P = O.Params(W, H, patch_radius=3, cells=(32, 16, 8), gain_normalize=0)
-    R = O.run(P, s.frame1, s.frame2)
-    m = _evaluate(s, R)
-    assert m["epe_nocc"] < 0.05, m
-    assert m["rec"] > 0.8 and m["prec"] > 0.6, m
+    # accuracy of the method, not of one random stream: eight Philox keys, bounds on the mean (measured: EPE
+    # 0.035 px, recall 0.97, precision 0.93) and a floor for each stream (the worst: recall 0.86)
+    ms = []
+    for seed in range(8):
+        P = O.Params(W, H, patch_radius=3, cells=(32, 16, 8), gain_normalize=0, seed=seed)
+        ms.append(_evaluate(s, O.run(P, s.frame1, s.frame2)))
+    mean = {k: float(np.mean([m[k] for m in ms])) for k in ms[0]}
+    assert mean["epe_nocc"] < 0.05 and all(m["epe_nocc"] < 0.1 for m in ms), ms
+    assert mean["rec"] > 0.9 and all(m["rec"] > 0.8 for m in ms), ms
+    assert mean["prec"] > 0.8 and all(m["prec"] > 0.6 for m in ms), ms
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -397,6 +402,57 @@ def test_tiny_config_accuracy_against_ground_truth(seed):
     assert m["epe_nocc"] < 0.6, m
     if s.occ.mean() > 0.05:
         assert m["rec"] > 0.5, m
+
+
+def _pipeline_level1(seed=0):
+    """The tiny configuration run through level 1 of Algorithm 1 (the level's restricted PatchMatch included)."""
+    s = scene.tiny_scene(seed)
+    P = O.Params(128, 96, seed=seed)
+    return P, O.run(P, s.frame1, s.frame2, stop_after=1)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pipeline_discards_every_stage_one_plane_that_fails_a_cue(seed):
+    """Sec. 3.4 in the pipeline: after level 1, no first-stage model whose symmetric fraction is below eta or
+    whose RANSAC / colour overlap is below kappa is still valid, and some models were judged (the scene has
+    occlusions, so the rule is exercised)."""
+    P, R = _pipeline_level1(seed)
+    cb = O.cell_base(P)
+    judged = failed = 0
+    for d in range(2):
+        for c in range(int(cb[0]), int(cb[1])):
+            f = R.mi[d][2 * c]
+            if not (f[O.MI_FLAGS] & O.F_FITTED):
+                continue
+            fails = (f[O.MI_NASSIGN] > 0 and f[O.MI_NSYM] < P.eta * f[O.MI_NASSIGN]) or \
+                f[O.MI_NRC] < P.kappa * f[O.MI_COUNT]
+            judged += 1
+            failed += bool(fails)
+            if fails:
+                assert f[O.MI_VALID] == 0, (d, c, f.tolist())
+    assert judged > 20 and failed > 0, (judged, failed)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_pipeline_residual_stage_fits_the_pixels_stage_one_left(seed):
+    """Sec. 3.2 in the pipeline: at level 1 each window's second-stage fit takes exactly the window's pixels
+    that the first stage left without a plane (its RANSAC input size), in both directions."""
+    P, R = _pipeline_level1(seed)
+    W, H = P.width, P.height
+    s = P.cells[0]
+    xs, ys = O.grid_axis(W, s), O.grid_axis(H, s)
+    cb = O.cell_base(P)
+    some = 0
+    for d in range(2):
+        left = (R.extra["stage1_m"][d] < 0).reshape(H, W)
+        assert 0 < left.sum() < W * H
+        for cy, y0 in enumerate(ys):
+            for cx, x0 in enumerate(xs):
+                c = int(cb[0]) + cy * len(xs) + cx
+                want = int(left[y0:y0 + s, x0:x0 + s].sum())
+                assert R.mi[d][2 * c + 1][O.MI_NIN] == want, (d, cx, cy, want, R.mi[d][2 * c + 1].tolist())
+                some += 0 < want < s * s
+    assert some > 0
 
 
 def test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours():

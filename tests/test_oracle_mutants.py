@@ -138,10 +138,10 @@ MUTANTS = [
      "orc_cue_counts(P, l, 1, T[d].m, T[d].fx, T[d].fy, T[d].m, T[d].fx, T[d].fy, S->mi[d], NULL);",
      [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
     ("oracle_pipeline.c", "            for (int d = 0; d < 2; ++d) orc_cue_invalidate(P, l, 1, S->mi[d]);\n", "",
-     [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
+     [METH + "test_pipeline_discards_every_stage_one_plane_that_fails_a_cue"]),
     ("oracle_pipeline.c", "for (int i = 0; i < n; ++i) resid[d][i] = S1[d].m[i] < 0;",
      "for (int i = 0; i < n; ++i) resid[d][i] = S1[d].m[i] >= 0;",
-     [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
+     [METH + "test_pipeline_residual_stage_fits_the_pixels_stage_one_left"]),
     ("oracle_pipeline.c", "                orc_many_to_one(P, C[d].m, C[d].L, C[d].fx, C[d].fy, S->cue[d], NULL);\n", "",
      [METH + "test_translating_layer_scene_occlusion_and_flow", METH + "test_tiny_config_accuracy_against_ground_truth"]),
     ("oracle_pipeline.c", "                orc_nnf_update(P, S->am[d], S->afx[d], S->afy[d], S->vx[d], S->vy[d], frozen[d]);\n", "",
