@@ -110,8 +110,8 @@ def lib() -> C.CDLL:
             "orc_many_to_one": (None, [pp, i32, d, d, d, u8, u8]),
             "orc_merge": (None, [pp, i32, d, d, d, i32, d, d, d, u8]),
             "orc_nnf_update": (None, [pp, i32, d, d, i32, i32, u8]),
-            "orc_fill": (None, [pp, d, d, d, i32, u8, i32, d, d, d]),
-            "orc_final": (None, [pp, d, d, i32, d, d, i32, i32, u8, P(C.c_float), u8]),
+            "orc_fill": (None, [pp, d, d, d, i32, u8, i32, d, d, d, u8]),
+            "orc_final": (None, [pp, d, d, i32, d, d, i32, i32, u8, P(C.c_float), u8, u8]),
             "orc_gain": (C.c_double, [pp, d, d]),
             "orc_rgb_to_hsv": (None, [C.c_double, C.c_double, C.c_double, d, d, d]),
             "orc_hsv_to_rgb": (None, [C.c_double, C.c_double, C.c_double, d, d, d]),
@@ -372,19 +372,23 @@ def nnf_update(P: Params, acc: Labels, vx, vy, frozen):
                          _p(vx, C.c_int32), _p(vy, C.c_int32), _p(frozen, C.c_uint8))
 
 
-def fill(P: Params, src, tgt, mh, mi, cue, acc: Labels):
+def fill(P: Params, src, tgt, mh, mi, cue, acc: Labels, amb=None):
+    """Model-propagation fill (Sec. 3.4.1) of acc in place; amb (uint8 per pixel, optional): the near-tie log,
+    read and extended (see orc_fill)."""
     lib().orc_fill(C.byref(P.c()), _p(_f64(src), C.c_double), _p(_f64(tgt), C.c_double), _p(mh, C.c_double),
                    _p(mi, C.c_int32), _p(cue, C.c_uint8), _p(acc.m, C.c_int32), _p(acc.L, C.c_double),
-                   _p(acc.fx, C.c_double), _p(acc.fy, C.c_double))
+                   _p(acc.fx, C.c_double), _p(acc.fy, C.c_double), _p(amb, C.c_uint8))
 
 
-def final(P: Params, src, tgt, acc: Labels, vx, vy, cue):
+def final(P: Params, src, tgt, acc: Labels, vx, vy, cue, amb=None):
+    """Final flow and occlusion map (Sec. 3.4.1); amb as in fill, extended with the occlusion decisions that
+    rest on a near tie."""
     n = P.width * P.height
     flow = np.zeros((n, 2), np.float32)
     occ = np.zeros(n, np.uint8)
     lib().orc_final(C.byref(P.c()), _p(_f64(src), C.c_double), _p(_f64(tgt), C.c_double), _p(acc.m, C.c_int32),
                     _p(acc.fx, C.c_double), _p(acc.fy, C.c_double), _p(vx, C.c_int32), _p(vy, C.c_int32),
-                    _p(cue, C.c_uint8), _p(flow, C.c_float), _p(occ, C.c_uint8))
+                    _p(cue, C.c_uint8), _p(flow, C.c_float), _p(occ, C.c_uint8), _p(amb, C.c_uint8))
     return flow, occ
 
 

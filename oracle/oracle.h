@@ -143,11 +143,16 @@ void orc_nnf_update(const orc_params* P, const int32_t* am, const double* afx, c
                     int32_t* vx, int32_t* vy, uint8_t* frozen);
 
 /* ---- filling and final occlusion map (Sec. 3.4.1) ---- */
+/* amb (per pixel, may be NULL): in, the pixels whose label may differ on another evaluation of the same state;
+   out, also those whose fill choice or occlusion decision rests on a near tie (colour error within the band of
+   eps, occ_thresh or of the tie margin between two candidates; target within the band of the frame edge), or
+   that looked at a neighbour marked in the previous iteration */
 void orc_fill(const orc_params* P, const double* src, const double* tgt, const double* mh,
-              const int32_t* mi, const uint8_t* cue, int32_t* am, double* aL, double* afx, double* afy);
+              const int32_t* mi, const uint8_t* cue, int32_t* am, double* aL, double* afx, double* afy,
+              uint8_t* amb);
 void orc_final(const orc_params* P, const double* src, const double* tgt, const int32_t* am,
                const double* afx, const double* afy, const int32_t* vx, const int32_t* vy,
-               const uint8_t* cue, float* flow /*HxWx2*/, uint8_t* occ);
+               const uint8_t* cue, float* flow /*HxWx2*/, uint8_t* occ, uint8_t* amb);
 
 /* ---- gain normalisation of the target frame ---- */
 double orc_gain(const orc_params* P, const double* f1, const double* f2);

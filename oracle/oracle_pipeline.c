@@ -165,8 +165,9 @@ void orc_run(const orc_params* Pin, const double* f1in, const double* f2in, orc_
     }
     /* fill and final flow / occlusion (Sec. 3.4.1) */
     for (int d = 0; d < 2; ++d) {
-        orc_fill(P, src[d], tgt[d], S->mh[d], S->mi[d], S->cue[d], S->am[d], S->aL[d], S->afx[d], S->afy[d]);
-        orc_final(P, src[d], tgt[d], S->am[d], S->afx[d], S->afy[d], S->vx[d], S->vy[d], S->cue[d], S->flow[d], S->occ[d]);
+        orc_fill(P, src[d], tgt[d], S->mh[d], S->mi[d], S->cue[d], S->am[d], S->aL[d], S->afx[d], S->afy[d], NULL);
+        orc_final(P, src[d], tgt[d], S->am[d], S->afx[d], S->afy[d], S->vx[d], S->vy[d], S->cue[d], S->flow[d], S->occ[d],
+                  NULL);
         if (P->interp) { /* edge-aware fill of the pixels left without a plane */
             int32_t* q = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
             int32_t* seed = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);

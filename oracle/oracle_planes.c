@@ -863,33 +863,42 @@ void orc_nnf_update(const orc_params* P, const int32_t* am, const double* afx, c
 /* than ORC_L_TIE counting as a tie).                                        */
 /* ------------------------------------------------------------------------ */
 void orc_fill(const orc_params* P, const double* src, const double* tgt, const double* mh,
-              const int32_t* mi, const uint8_t* cue, int32_t* am, double* aL, double* afx, double* afy) {
+              const int32_t* mi, const uint8_t* cue, int32_t* am, double* aL, double* afx, double* afy,
+              uint8_t* amb) {
     (void)mi;
     const int W = P->W, H = P->H, n = W * H;
     int32_t* nm = (int32_t*)malloc(sizeof(int32_t) * n);
     double* nL = (double*)malloc(sizeof(double) * 3 * n);
     double *nfx = nL + n, *nfy = nfx + n;
+    uint8_t* namb = amb ? (uint8_t*)malloc((size_t)n) : NULL;
     for (int it = 0; it < P->fill_iters; ++it) {
         memcpy(nm, am, sizeof(int32_t) * n);
         memcpy(nL, aL, sizeof(double) * n);
         memcpy(nfx, afx, sizeof(double) * n);
         memcpy(nfy, afy, sizeof(double) * n);
+        if (amb) memcpy(namb, amb, (size_t)n);
         for (int y = 0; y < H; ++y)
             for (int x = 0; x < W; ++x) {
                 int i = y * W + x;
                 if (am[i] >= 0 || (cue[i] & ORC_CUE_M2O)) continue;
                 static const int NX[4] = {-1, 1, 0, 0}, NY[4] = {0, 0, -1, 1};
-                int bm = -1;
-                double bL = DBL_MAX, bfx = 0, bfy = 0;
+                int bm = -1, nd = 0, a = 0;
+                double bL = DBL_MAX, bfx = 0, bfy = 0, dl[4];
                 for (int k = 0; k < 4; ++k) {
                     int xx = x + NX[k], yy = y + NY[k];
                     if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+                    /* a neighbour whose label rests on a near tie may hold another plane, or none */
+                    if (amb && amb[yy * W + xx]) a = 1;
                     int m = am[yy * W + xx];
                     if (m < 0) continue;
                     double X, Y;
-                    if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y) || !in_frame(P, X, Y)) continue;
+                    if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y)) continue;
+                    if (amb && near_frame_edge(P, X, Y)) a = 1;
+                    if (!in_frame(P, X, Y)) continue;
                     double d = delta_at(P, src, tgt, x, y, X, Y);
+                    if (amb && near_colour(d, P->eps)) a = 1;
                     if (!(d < P->eps)) continue;
+                    dl[nd++] = d;
                     if (d < bL - ORC_L_TIE || (fabs(d - bL) <= ORC_L_TIE && m < bm)) {
                         bL = d;
                         bm = m;
@@ -897,6 +906,11 @@ void orc_fill(const orc_params* P, const double* src, const double* tgt, const d
                         bfy = Y - y;
                     }
                 }
+                /* two inlier candidates whose losses differ by about the tie margin */
+                for (int u = 0; amb && u < nd; ++u)
+                    for (int v = u + 1; v < nd; ++v)
+                        if (near_colour(fabs(dl[u] - dl[v]), ORC_L_TIE)) a = 1;
+                if (amb && a) namb[i] = 1;
                 if (bm >= 0) {
                     nm[i] = bm;
                     nL[i] = bL;
@@ -908,9 +922,11 @@ void orc_fill(const orc_params* P, const double* src, const double* tgt, const d
         memcpy(aL, nL, sizeof(double) * n);
         memcpy(afx, nfx, sizeof(double) * n);
         memcpy(afy, nfy, sizeof(double) * n);
+        if (amb) memcpy(amb, namb, (size_t)n);
     }
     free(nm);
     free(nL);
+    free(namb);
 }
 
 /* Final flow and occlusion map (Sec. 3.4 and 3.4.1): a pixel keeps its plane
@@ -919,7 +935,7 @@ void orc_fill(const orc_params* P, const double* src, const double* tgt, const d
    error after warping by the final flow reaches occ_thresh. */
 void orc_final(const orc_params* P, const double* src, const double* tgt, const int32_t* am,
                const double* afx, const double* afy, const int32_t* vx, const int32_t* vy,
-               const uint8_t* cue, float* flow, uint8_t* occ) {
+               const uint8_t* cue, float* flow, uint8_t* occ, uint8_t* amb) {
     const int W = P->W, H = P->H;
     for (int y = 0; y < H; ++y)
         for (int x = 0; x < W; ++x) {
@@ -930,8 +946,13 @@ void orc_final(const orc_params* P, const double* src, const double* tgt, const 
             flow[2 * i + 1] = (float)fy;
             int o = am[i] < 0 || (cue[i] & ORC_CUE_M2O);
             double X = x + fx, Y = y + fy;
+            if (amb && !o && near_frame_edge(P, X, Y)) amb[i] = 1;
             if (!in_frame(P, X, Y)) o = 1;
-            else if (!(delta_at(P, src, tgt, x, y, X, Y) < P->occ_thresh)) o = 1;
+            else {
+                double d = delta_at(P, src, tgt, x, y, X, Y);
+                if (amb && !o && near_colour(d, P->occ_thresh)) amb[i] = 1;
+                if (!(d < P->occ_thresh)) o = 1;
+            }
             occ[i] = (uint8_t)o;
         }
 }

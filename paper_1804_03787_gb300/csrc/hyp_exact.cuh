@@ -153,6 +153,49 @@ __host__ __device__ inline bool make_mef_exact(const i128* Hin, Mef& m) {
     return true;
 }
 
+// Bit length of a 128-bit magnitude (0 for zero).
+__host__ __device__ __forceinline__ int u128_bits(u128 u) {
+    const uint64_t hi = (uint64_t)(u >> 64), lo = (uint64_t)u;
+#ifdef __CUDA_ARCH__
+    return hi ? 128 - __clzll((long long)hi) : (lo ? 64 - __clzll((long long)lo) : 0);
+#else
+    return hi ? 128 - __builtin_clzll(hi) : (lo ? 64 - __builtin_clzll(lo) : 0);
+#endif
+}
+
+// The 9 entries of an exact homography as doubles scaled by one power of two
+// (the largest magnitude in [1, 2)), each truncated to 53 significant bits,
+// with every sign flipped when flip is set.  Built from integer operations
+// alone: the exponent and mantissa fields are assembled directly (on GB300 a
+// 64-bit integer conversion or an FP64 divide issues on the slow FP64 pipe).
+__host__ __device__ inline void exact_to_double_pow2(const i128* H, double* D, bool flip) {
+    int bl[9], E = 0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const u128 u = H[k] < 0 ? (u128)0 - (u128)H[k] : (u128)H[k];
+        bl[k] = u128_bits(u);
+        E = bl[k] > E ? bl[k] : E;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const bool neg = H[k] < 0;
+        const u128 u = neg ? (u128)0 - (u128)H[k] : (u128)H[k];
+        uint64_t bits = 0;
+        if (bl[k] > 0) {
+            // m: the leading 53 bits, value m 2^(bl - 53); scaled by 2^-E: m 2^(bl - E - 53), whose biased
+            // exponent field is bl - E + 1022 + 1 (>= 897 for magnitudes below 2^127: always normal)
+            const uint64_t m = bl[k] > 53 ? (uint64_t)(u >> (bl[k] - 53)) : (uint64_t)u << (53 - bl[k]);
+            bits = ((uint64_t)(bl[k] - E + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull);
+            if (neg != flip) bits |= 0x8000000000000000ull;
+        }
+#ifdef __CUDA_ARCH__
+        D[k] = __longlong_as_double((long long)bits);
+#else
+        __builtin_memcpy(&D[k], &bits, 8);
+#endif
+    }
+}
+
 // The first n entries of an exact homography as doubles (unnormalised).
 __host__ __device__ inline void exact_to_double(const i128* H, double* D, int n = 9) {
     for (int k = 0; k < n; ++k) {

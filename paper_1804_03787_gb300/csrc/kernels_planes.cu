@@ -333,7 +333,7 @@ __device__ __forceinline__ void min_eigvec9(const double (&M)[45], double (&x)[9
         const float s0 = rsqrtf(n0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) xf[i] *= s0;
-        for (int it = 0; it < 300; ++it) {
+        for (int it = 0; it < 60; ++it) {  // a start vector only: the FP64 iteration below converges from it
             float y[9];
 #pragma unroll
             for (int i = 0; i < 9; ++i) {  // L z = x
@@ -420,9 +420,13 @@ __device__ __forceinline__ void min_eigvec9(const double (&M)[45], double (&x)[9
     // against the shift's distance), so is the remaining error extrapolated from the ratio of successive changes
     // (a small change per step alone would stop a slow iteration far from the vector).  A slow iteration is
     // re-shifted at the current vector's Rayleigh quotient minus twice its residual (still below the smallest
-    // eigenvalue), a few times at most.
+    // eigenvalue), a few times at most.  An iteration that stays slow after them measures the eigen-gap: with
+    // the ratio q of successive changes, (lambda_1 - sigma) / (lambda_2 - sigma) = q gives lambda_2 - lambda_1 =
+    // (rho - sigma)(1 - q) / q (rho, the Rayleigh quotient, for lambda_1); below 1e-11 of the trace (at most 9
+    // times the largest eigenvalue), the gap is far below the 1e-8 of the largest eigenvalue at which the
+    // smallest eigenvector is no longer determined to the 1e-6 a refit is compared at, and the iteration stops.
     double prev = 1e300;
-    int reshifts = 0;
+    int reshifts = 0, slow = 0;
     for (int it = 0; it < 200; ++it) {
         double y[9];
 #pragma unroll
@@ -459,6 +463,20 @@ __device__ __forceinline__ void min_eigvec9(const double (&M)[45], double (&x)[9
         const double q = diff / prev;  // convergence ratio of the last step
         prev = diff;
         if (diff < 1e-12 && (q < 0.5 || diff * q / (1.0 - fmin(q, 0.999999)) < 1e-13)) break;
+        slow = q > 0.9 ? slow + 1 : 0;  // q >= 1: no convergence at all (a gap below what rounding resolves)
+        if (reshifts >= 4 && slow >= 4 && (slow & 3) == 0) {  // the gap, from the convergence ratio
+            double xx3 = 0, rho3 = 0;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                double t = 0;
+#pragma unroll
+                for (int j = 0; j < 9; ++j) t = fma(M[sym(i, j)], x[j], t);
+                xx3 = fma(x[i], x[i], xx3);
+                rho3 = fma(x[i], t, rho3);
+            }
+            const double gap = q < 1.0 ? (rho3 / xx3 - sigma) * (1.0 - q) / q : 0.0;
+            if (gap < 1e-11 * tr) break;
+        }
         if (it >= 2 && q > 0.5 && reshifts < 4) {
             double Mx2[9], xx2 = 0, rho2 = 0;
 #pragma unroll
@@ -530,18 +548,20 @@ __device__ __forceinline__ bool draw_hypothesis(const float4* match, int N, int 
     return true;
 }
 
+// The same out of line (the winner's redraw, once per window: the scoring
+// loop keeps the only inline copy).
+__device__ __noinline__ void draw_hypothesis_ool(const float4* match, int N, int cell, int k, uint32_t tag,
+                                                 uint32_t pair_id, uint32_t k0, uint32_t k1, i128* Hk) {
+    draw_hypothesis(match, N, cell, k, tag, pair_id, k0, k1, Hk);
+}
+
 // The exact hypothesis as doubles in window-local coordinates, oriented like
 // its evaluation form (positive denominator at the window centre) and scaled
-// by its largest entry: the FP64 stand-in of the residual test.
+// by a power of two (largest entry in [1, 2)): the FP64 stand-in of the
+// residual test, built without FP64 instructions.
 __device__ __forceinline__ void exact_local_fp64(const i128* Hk, double* Hl) {
-    exact_to_double(Hk, Hl, 9);
     const i128 dc2 = 2 * Hk[8] - (Hk[6] + Hk[7]);
-    double f = 0;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) f = fmax(f, fabs(Hl[q]));
-    const double sc = (dc2 < 0 ? -1.0 : 1.0) / f;
-#pragma unroll
-    for (int q = 0; q < 9; ++q) Hl[q] *= sc;
+    exact_to_double_pow2(Hk, Hl, dc2 < 0);
 }
 
 // ---------------------------------------------------------------- RANSAC per window
@@ -558,8 +578,6 @@ __device__ __forceinline__ void exact_local_fp64(const i128* Hk, double* Hl) {
 
 // Windows with at most this many matches score each hypothesis on one thread.
 constexpr int kLaneScoreMax = 64;
-// Deferred contenders per warp (their exact counts are computed after the scan; beyond this, at once).
-constexpr int kCandMax = 32;
 
 // mef_inlier_pt out of line (loose hypotheses are rare: the callers' loops stay small).
 __device__ __noinline__ bool mef_inlier_pt_ool(const Mef& m, float4 mt, float t2, bool& unc) {
@@ -595,31 +613,63 @@ __device__ __noinline__ int2 loose_score_warp(const float4* match, int N, const 
     return make_int2(s2, u2);
 }
 
-// The winner's residual test decided in FP64 (its exact form from the refit record).
-__device__ __noinline__ bool winner_inlier_fp64(const i128* hx_global, float4 mt, float t2) {
-    i128 hx[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) hx[q] = hx_global[q];
-    double Hl[9];
-    exact_local_fp64(hx, Hl);
-    return hyp_inlier_fp64(Hl, mt.x, mt.y, mt.z, mt.w, (double)t2);
+// Support of a loose hypothesis on at most 64 matches (per-match bounds), the
+// warp's lanes over the matches: the FP32 count on every lane, the uncertain
+// tests (bit j of unc: match j) and the FP32 decisions among them (bit j of
+// uin).  Out of line (rare).  tests: residual tests done (counter).
+__device__ __noinline__ int loose_score64(const float4* match, int N, const Mef& m, float t2,
+                                          unsigned long long& unc, unsigned long long& uin) {
+    const int lane = threadIdx.x & 31;
+    int score = 0;
+    unc = 0;
+    uin = 0;
+    for (int c = 0; c < N; c += 32) {
+        const int j = c + lane;
+        bool in = false, u = false;
+        if (j < N) {
+            const float4 mt = match[j];
+            in = mef_inlier_pt(m, mt.x, mt.y, mt.z, mt.w, t2, u);
+        }
+        const unsigned bi = __ballot_sync(FULL, in), bu = __ballot_sync(FULL, u);
+        score += __popc(bi);
+        unc |= (unsigned long long)bu << c;
+        uin |= (unsigned long long)(bu & bi) << c;
+    }
+    return score;
 }
 
-// Exact support of hypothesis k: every match tested by the certified FP32
-// test, the uncertain ones again in FP64 with the hypothesis drawn once more
-// (exact); the warp's lanes over the matches (every lane gets the score).  Used
-// for a hypothesis whose FP32 count, with its uncertain tests, could still win.
-// nfp64 counts the lane's FP64 decisions.
-__device__ __noinline__ int exact_score_warp(const float4* match, int N, int cell, int k, uint32_t tag,
-                                             uint32_t pair_id, uint32_t k0, uint32_t k1, const Mef& m, float t2,
-                                             int& nfp64) {
-    const int lane = threadIdx.x & 31;
+// The exact count of a hypothesis from its FP32 count on at most 64 matches:
+// each uncertain test (bit j of unc) decided again in FP64 with Hl, the
+// hypothesis's exact form, replacing its FP32 decision (bit j of uin).  One
+// thread; nfp64 counts the FP64 decisions.
+__device__ __noinline__ int resolve_uncertain(const float4* match, const double* Hl, float t2, unsigned long long unc,
+                                              unsigned long long uin, int score, int& nfp64) {
+    for (; unc; unc &= unc - 1) {
+        const int j = __ffsll((long long)unc) - 1;
+        const float4 mt = match[j];
+        score += (int)hyp_inlier_fp64(Hl, mt.x, mt.y, mt.z, mt.w, (double)t2) - (int)((uin >> j) & 1ull);
+        ++nfp64;
+    }
+    return score;
+}
+// The same from the 128-bit hypothesis itself (kept in shared memory since it was drawn).
+__device__ __noinline__ int resolve_uncertain_hk(const float4* match, const i128* hk, float t2,
+                                                 unsigned long long unc, unsigned long long uin, int score,
+                                                 int& nfp64) {
     double Hl[9];
     {
-        i128 Hk[9];
-        draw_hypothesis(match, N, cell, k, tag, pair_id, k0, k1, Hk);
-        exact_local_fp64(Hk, Hl);
+        i128 H[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) H[q] = hk[q];
+        exact_local_fp64(H, Hl);
     }
+    return resolve_uncertain(match, Hl, t2, unc, uin, score, nfp64);
+}
+
+// The same with the warp's lanes over the matches (every lane gets the score).
+__device__ __noinline__ int exact_score_warp(const float4* match, int N, const Mef& m, const double* Hl, float t2,
+                                             int& nfp64) {
+    const int lane = threadIdx.x & 31;
     int score = 0;
     for (int c = 0; c < N; c += 32) {
         const int j = c + lane;
@@ -682,23 +732,33 @@ __device__ int gather_matches(const G& grp, const PairView& pv, const LevelGeom&
     return N;
 }
 
-// Sum of |(a, b)| over a lane's points, for exact integers a, b: each root in
-// FP64 of the exact sum of squares, added in FP64.  The least-squares refit of
-// a thin, ill-conditioned support moves with its Hartley normalisation, so the
-// scale carries FP64 rounding only (with FP32 roots, refits moved by ~1e-6).
+// Sum of |(a, b)| over a lane's points, for exact integers a, b: each root of
+// the sum of squares K (exact in 64-bit integers, rounded once to FP64 above
+// 2^53) to about 1e-14 relative, added in FP64.  The least-squares refit of a thin, ill-conditioned support
+// moves with its Hartley normalisation, so the scale must carry far less than
+// FP32 rounding (with FP32 roots, refits moved by ~1e-6).  The root: the FP32
+// root s0 and reciprocal 1 / (2 s0), then one Newton step in FP64,
+// s0 + (K - s0^2) / (2 s0): its error is about s0 times the square of s0's
+// relative error (2^-23), against some ten FP64 operations of a full FP64
+// root on GB300's slow FP64 pipe.
 struct DistSum {
     double s = 0.0;
     __device__ __forceinline__ void add(int a, int b) {
-        const double da = (double)a, db = (double)b;
-        s += sqrt(fma(da, da, db * db));
+        const long long K = (long long)a * a + (long long)b * b;  // exact: |a|, |b| < 2^31
+        const float fa = (float)a, fb = (float)b;
+        const float s0 = sqrtf(fmaf(fa, fa, fb * fb));
+        if (!(s0 > 0.f)) return;  // K = 0
+        const double sd = (double)s0;
+        const double e = fma(-sd, sd, (double)K);
+        s += fma(e, (double)(0.5f / s0), sd);
     }
     __device__ __forceinline__ double total() const { return s; }
 };
 
-template <class G, int ST>
+template <class G, int ST, bool LANE>
 __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
                            const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, int* kfull,
-                           Mef* wmef, int* cand) {
+                           Mef* wmef, void* hx) {
     const int tid = grp.rank();
     const int id = (g.base + cell) * 2 + (stage - 1);
     int* mi = pv.mi[dir] + (size_t)id * kMI;
@@ -739,21 +799,26 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     // scoring every hypothesis in full.  Once a hypothesis has all N matches
     // as inliers, hypotheses of higher index can at most tie and are not
     // drawn at all.
+    // Counts are certified: a count with uncertain FP32 tests bounds the exact
+    // count by count +- uncertain; a hypothesis whose optimistic count could
+    // still win gets its exact count at once (its uncertain tests decided in
+    // FP64 with its exact form).  hx keeps each lane's hypothesis since it was
+    // drawn: in the one-hypothesis-per-lane kernel (LANE) as its 128-bit
+    // entries (converted only when needed), else as its exact form in FP64.
     const float t2 = pp.t2;
     const uint32_t tag = stream_tag(RNG_RANSAC, dir, level, stage);
     constexpr int NW = G::size / 32;
     const int lane = tid & 31;
     Mef* hb = hyp + (tid >> 5) * 32;
+    i128* hkw = reinterpret_cast<i128*>(hx) + (tid >> 5) * (32 * 9);    // LANE: this warp's 32 hypotheses
+    double* hlw = reinterpret_cast<double*>(hx) + (tid >> 5) * (32 * 9);  // else: their exact forms
     int best_score = -1, best_k = 0x7fffffff, tests = 0;
-    // Deferred exact counts: a hypothesis that completes as a contender while some of its tests are uncertain
-    // goes on its warp's list (index, FP32 count, uncertain tests), and only its certain lower count
-    // (count - uncertain) raises the abandon bound; after the scan, the listed hypotheses whose optimistic
-    // count can still win get their exact counts.  Most contenders of an early, low bound never need one.
-    // (cand: the group's lists, one per warp of the group.)
-    int* cl = cand + (tid >> 5) * (3 * kCandMax);
-    int ncand = 0, lo_bound = -1;
     int nfp64 = 0, nloose = 0;  // tests decided in FP64, hypotheses tested with per-match bounds (counters)
-    if (N <= kLaneScoreMax) {
+    // LANE: the warp's best hypothesis so far (its key, its 128-bit entries after the 32 lanes' in hx, its
+    // evaluation form in *wmef), so that the winner needs no second draw
+    unsigned long long wbest_key = 0ull;
+    i128* wslot = reinterpret_cast<i128*>(hx) + 32 * 9;
+    if (LANE || N <= kLaneScoreMax) {
         int group_best = -1;  // the group's best exact count after the previous rounds
         for (int r = 0; r * G::size < pp.num_hyp; ++r) {
             const int k = r * G::size + tid;
@@ -762,20 +827,46 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             if (k < pp.num_hyp) {
                 i128 Hk[9];
                 ok = draw_hypothesis(match, N, cell, k, tag, pv.pair_id, pp.k0, pp.k1, Hk) && make_mef_exact(Hk, m);
+                if (LANE) {
+#pragma unroll
+                    for (int q = 0; q < 9; ++q) hkw[lane * 9 + q] = Hk[q];
+                } else if (ok) {
+                    exact_local_fp64(Hk, hlw + lane * 9);
+                }
             }
-            // FP32 count and uncertain tests: the exact count is within score +- unc_n
-            int score = 0, unc_n = 0;
+            // FP32 count; the uncertain tests (bit j: match j) and the FP32 decisions among them: the exact
+            // count is within score +- popc(um)
+            int score = 0;
+            unsigned long long um = 0, im = 0;
             bool loose = false;
             if (ok) {
                 mef_set_bounds(m, U, V, t2);
                 loose = mef_loose(m);
                 nloose += loose;
-                if (!loose) {
-                    for (int j = 0; j < N; ++j) {
+                if (!loose) {  // two matches per instruction on the packed FP32x2 pipe
+                    const Mef2 m2 = mef2_of(m);
+                    const float ef = m.ef, eden = __int_as_float(m.eden);
+                    int j = 0;
+                    for (; j + 1 < N; j += 2) {
+                        bool ia, ib, ua, ub;
+                        mef_inlier2_c(m2, ef, eden, match[j], match[j + 1], t2, ia, ib, ua, ub);
+                        score += (int)ia + (int)ib;
+                        if (ua || ub) {
+                            const unsigned long long ba = (unsigned long long)ua << j, bb = (unsigned long long)ub
+                                                                                                  << (j + 1);
+                            um |= ba | bb;
+                            im |= (ia ? ba : 0ull) | (ib ? bb : 0ull);
+                        }
+                    }
+                    if (j < N) {
                         const float4 mt = match[j];
                         bool unc;
-                        score += mef_inlier_c(m, mt.x, mt.y, mt.z, mt.w, t2, unc);
-                        unc_n += unc;
+                        const bool in = mef_inlier_c(m, mt.x, mt.y, mt.z, mt.w, t2, unc);
+                        score += in;
+                        if (unc) {
+                            um |= 1ull << j;
+                            if (in) im |= 1ull << j;
+                        }
                     }
                 }
                 tests += N;
@@ -785,47 +876,55 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             // loose hypotheses (per-match bounds): the warp scores them together, lanes over the matches
             for (unsigned lm = __ballot_sync(FULL, loose); lm; lm &= lm - 1) {
                 const int l = __ffs(lm) - 1;
-                int tl = 0;
-                const int2 su = loose_score_warp(match, N, hb[l], t2, -1, tl);
+                unsigned long long ul, il;
+                const int sl = loose_score64(match, N, hb[l], t2, ul, il);
                 if (lane == l) {
-                    score = su.x;
-                    unc_n = su.y;
+                    score = sl;
+                    um = ul;
+                    im = il;
                 }
             }
-            // a contender with uncertain tests (it could beat the best so far: this thread's, the group's of
-            // earlier rounds) is deferred; without uncertain tests its count is exact
-            const bool contend = ok && score + unc_n > max(max(best_score, lo_bound), group_best);
-            for (unsigned rm = __ballot_sync(FULL, contend && unc_n > 0); rm; rm &= rm - 1) {
-                const int l = __ffs(rm) - 1;
-                const int kl = __shfl_sync(FULL, k, l), sl = __shfl_sync(FULL, score, l);
-                const int ul = __shfl_sync(FULL, unc_n, l);
-                if (ncand < kCandMax) {
-                    if (lane == 0) {
-                        cl[3 * ncand] = kl;
-                        cl[3 * ncand + 1] = sl;
-                        cl[3 * ncand + 2] = ul;
-                    }
-                    ++ncand;
-                    if (lane == l) lo_bound = max(lo_bound, score - unc_n);
-                } else {  // list full: its exact count now
-                    int f = 0;
-                    const int ex = exact_score_warp(match, N, cell, kl, tag, pv.pair_id, pp.k0, pp.k1, hb[l], t2, f);
-                    const unsigned tf = __reduce_add_sync(FULL, (unsigned)f);
-                    if (lane == 0) nfp64 += (int)tf;
-                    if (lane == l) unc_n = 0, score = ex;
-                }
+            const int unc_n = __popcll(um);
+            // A hypothesis with uncertain tests that could beat the best so far (this thread's, the group's of
+            // earlier rounds: lower indices) and that no hypothesis of this round surely beats gets its exact
+            // count.  Without uncertain tests its count is exact.
+            const int rlo = (int)__reduce_max_sync(FULL, (unsigned)(ok ? score - unc_n + 1 : 0)) - 1;
+            const int hi = score + unc_n;
+            bool exact = unc_n == 0;
+            if (ok && !exact && hi > max(best_score, group_best) && hi >= rlo) {
+                score = LANE ? resolve_uncertain_hk(match, hkw + lane * 9, t2, um, im, score, nfp64)
+                             : resolve_uncertain(match, hlw + lane * 9, t2, um, im, score, nfp64);
+                exact = true;
             }
             __syncwarp();
-            if (ok && unc_n == 0 && score > best_score) {
+            if (ok && exact && score > best_score) {
                 best_score = score;
                 best_k = k;
             }
-            // all N matches inliers: every later round has higher indices and can at most tie
-            if (grp.any(best_score >= N)) break;
-            group_best = (int)grp.max((unsigned long long)(max(best_score, lo_bound) + 1)) - 1;
+            if (LANE) {  // the warp's best so far (most inliers, lowest index) into its slot when it changes
+                const unsigned long long key =
+                    best_score < 0 ? 0ull
+                                   : (((unsigned long long)(best_score + 1)) << 32) |
+                                         (unsigned long long)(0xFFFFFFFFu - (uint32_t)best_k);
+                const unsigned long long wk = grp.max(key);
+                if (wk != wbest_key) {  // a hypothesis of this round: its lane still holds it in hkw and hb
+                    const int wl = __ffs(__ballot_sync(FULL, key == wk)) - 1;
+                    if (lane < 9) wslot[lane] = hkw[wl * 9 + lane];
+                    if (lane == 9) *wmef = hb[wl];
+                    wbest_key = wk;
+                }
+                __syncwarp();
+                group_best = (int)(wk >> 32) - 1;
+                // all N matches inliers: every later round has higher indices and can at most tie
+                if (group_best >= N) break;
+            } else {
+                // all N matches inliers: every later round has higher indices and can at most tie
+                if (grp.any(best_score >= N)) break;
+                group_best = (int)grp.max((unsigned long long)(best_score + 1)) - 1;
+            }
         }
     }
-    for (int b = tid >> 5; N > kLaneScoreMax && b * 32 < pp.num_hyp; b += NW) {
+    for (int b = tid >> 5; !LANE && N > kLaneScoreMax && b * 32 < pp.num_hyp; b += NW) {
         // a hypothesis with all N matches inliers at a lower index than this batch: nothing here can win
         if ((NW > 1 ? *(volatile int*)kfull : (best_score >= N ? best_k : 0x7fffffff)) < b * 32) break;
         const int k = b * 32 + lane;
@@ -838,6 +937,7 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
                 mef_set_bounds(m, U, V, t2);
                 nloose += mef_loose(m);
                 hb[lane] = m;
+                exact_local_fp64(Hk, hlw + lane * 9);
             }
         }
         unsigned todo = __ballot_sync(FULL, ok);
@@ -848,10 +948,8 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
             const Mef2 m2 = mef2_of(hb[l]);
             const float ef = hb[l].ef, eden = __int_as_float(hb[l].eden);
             const bool loose = mef_loose(hb[l]);  // warp-uniform
-            const int kl = b * 32 + l;
-            // abandon when reach < group best or reach <= this warp's best (exact, or a deferred contender's
-            // certain lower count)
-            const int bound = max(NW > 1 ? *(volatile int*)gbest - 1 : -1, max(best_score, lo_bound));
+            // abandon when reach < group best or reach <= this warp's best
+            const int bound = max(NW > 1 ? *(volatile int*)gbest - 1 : -1, best_score);
             int score = 0, unc_n = 0;  // FP32 count, uncertain tests: the exact count is within score +- unc_n
             bool alive = true;
             if (loose) {  // per-match bounds, out of line
@@ -880,20 +978,9 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
                     break;
                 }
             }
-            if (alive && unc_n > 0) {  // a contender with uncertain tests: deferred (or, list full, counted now)
-                if (ncand < kCandMax) {
-                    if (lane == 0) {
-                        cl[3 * ncand] = kl;
-                        cl[3 * ncand + 1] = score;
-                        cl[3 * ncand + 2] = unc_n;
-                    }
-                    ++ncand;
-                    lo_bound = max(lo_bound, score - unc_n);
-                    if (NW > 1 && lane == 0) atomicMax(gbest, score - unc_n);
-                    continue;
-                }
+            if (alive && unc_n > 0) {  // a contender with uncertain tests: its exact count
                 int f = 0;
-                score = exact_score_warp(match, N, cell, kl, tag, pv.pair_id, pp.k0, pp.k1, hb[l], t2, f);
+                score = exact_score_warp(match, N, hb[l], hlw + l * 9, t2, f);
                 const unsigned tf = __reduce_add_sync(FULL, (unsigned)f);
                 if (lane == 0) nfp64 += (int)tf;
                 alive = score > bound;
@@ -909,42 +996,11 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
         }
         __syncwarp();
     }
-    // the deferred contenders that can still win: their exact counts (hypothesis order, so ties keep the lower
-    // index).  A contender whose optimistic count is below the group's bound cannot win.
-    {
-        const int gb = N > kLaneScoreMax ? (NW > 1 ? *(volatile int*)gbest : -1) : -1;
-        const int gx = (int)grp.max((unsigned long long)(best_score + 1)) - 1;  // the group's best exact count
-        for (int c = 0; c < ncand; ++c) {
-            const int kc = cl[3 * c], hi = cl[3 * c + 1] + cl[3 * c + 2];
-            const int owner = N <= kLaneScoreMax ? (kc & 31) : lane;  // the lane whose best it may become
-            const int ob = __shfl_sync(FULL, best_score, owner), obk = __shfl_sync(FULL, best_k, owner);
-            if (hi < gb || hi < gx || hi < ob || (hi == ob && kc > obk)) continue;
-            // the hypothesis's evaluation form again (its drawing lane wrote it to hb in its round)
-            Mef m;
-            if (lane == 0) {
-                i128 Hk[9];
-                draw_hypothesis(match, N, cell, kc, tag, pv.pair_id, pp.k0, pp.k1, Hk);
-                make_mef_exact(Hk, m);
-                mef_set_bounds(m, U, V, t2);
-                hb[0] = m;
-            }
-            __syncwarp();
-            m = hb[0];
-            __syncwarp();
-            int f = 0;
-            const int ex = exact_score_warp(match, N, cell, kc, tag, pv.pair_id, pp.k0, pp.k1, m, t2, f);
-            const unsigned tf = __reduce_add_sync(FULL, (unsigned)f);
-            if (lane == 0) nfp64 += (int)tf;
-            if (lane == owner && (ex > best_score || (ex == best_score && kc < best_k))) {
-                best_score = ex;
-                best_k = kc;
-            }
-        }
-    }
     if (pv.evals) {  // residual tests performed, those decided in FP64, loose hypotheses (profiling)
-        const int t = grp.sum(N <= kLaneScoreMax || lane == 0 ? tests : 0);
+        const bool per_lane = LANE || N <= kLaneScoreMax;
+        const int t = grp.sum(per_lane || lane == 0 ? tests : 0);
         const int f = grp.sum(nfp64);
-        const int lo = grp.sum(N <= kLaneScoreMax || lane == 0 ? nloose : 0);
+        const int lo = grp.sum(per_lane || lane == 0 ? nloose : 0);
         if (tid == 0) {
             atomicAdd(&pv.evals[GPM_COUNT_RANSAC], (unsigned long long)t);
             atomicAdd(&pv.evals[GPM_COUNT_RANSAC_FP64], (unsigned long long)f);
@@ -963,13 +1019,33 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     }
     const int wscore = (int)(wkey >> 32) - 1;
     const int wk = (int)(0xFFFFFFFFu - (uint32_t)(wkey & 0xFFFFFFFFull));
-    if (tid < 32) {  // first warp: the winner again, exact, and its evaluation form
+    // the winner's exact form for its FP64 tests, in the first 72 bytes of hx (the scan is over: every warp
+    // of the group has passed the reduction above)
+    double* whl = reinterpret_cast<double*>(hx);
+    if (tid < 32) {  // first warp: the winner again, exact (LANE: from the warp's slot), and its evaluation form
         i128 Hk[9];
-        draw_hypothesis(match, N, cell, wk, tag, pv.pair_id, pp.k0, pp.k1, Hk);
+        if (LANE) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) Hk[q] = wslot[q];
+        } else {
+            draw_hypothesis_ool(match, N, cell, wk, tag, pv.pair_id, pp.k0, pp.k1, Hk);
+        }
+        {
+            double Hl[9];
+            exact_local_fp64(Hk, Hl);
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                if (tid == q) whl[q] = Hl[q];
+        }
         if (tid == 0) {
             Mef m0;
-            make_mef_exact(Hk, m0);
-            mef_set_bounds(m0, U, V, t2);
+            if (LANE) {
+                m0 = *wmef;
+            } else {
+                make_mef_exact(Hk, m0);
+                mef_set_bounds(m0, U, V, t2);
+            }
             *wmef = m0;
             rw->mef0 = m0;
             mi[MI_BESTK] = wk;
@@ -990,12 +1066,17 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     auto winner_inlier = [&](const float4& mt) -> bool {
         bool unc;
         const bool in = cert_inlier(wm, mt, t2, unc);
-        return unc ? winner_inlier_fp64(rw->hx, mt, t2) : in;
+        return unc ? hyp_inlier_fp64(whl, mt.x, mt.y, mt.z, mt.w, (double)t2) : in;
     };
+    // the winner's inliers among this thread's matches (bit c: match tid + c G::size; N <= 64 G::size for
+    // every group: 256 matches per warp window, 96 x 96 per block window)
+    static_assert(kMaxCell * kMaxCell <= 64 * 256 && 16 * 16 <= 64 * 32, "inlier mask too small");
+    unsigned long long inm = 0;
     int sx = 0, sy = 0, tx = 0, ty = 0;
-    for (int j = tid; j < N; j += G::size) {
+    for (int j = tid, c = 0; j < N; j += G::size, ++c) {
         const float4 mt = match[j];
         if (winner_inlier(mt)) {
+            inm |= 1ull << c;
             sx += exact_int(mt.x);
             sy += exact_int(mt.y);
             tx += exact_int(mt.x + mt.z);
@@ -1018,9 +1099,8 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     long long R[24];
 #pragma unroll
     for (int q = 0; q < 24; ++q) R[q] = 0;
-    for (int j = tid; j < N; j += G::size) {
-        const float4 mt = match[j];
-        if (!winner_inlier(mt)) continue;
+    for (; inm; inm &= inm - 1) {
+        const float4 mt = match[tid + (__ffsll((long long)inm) - 1) * G::size];
         dsum.add(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
         dtsum.add(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
         const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
@@ -1266,21 +1346,31 @@ __device__ void ransac_finish(const G& grp, const PairView& pv, const LevelGeom&
 }
 
 // Windows up to 16 x 16: one warp per window, eight windows per block.
-// Dynamic shared memory: 8 x 256 matches, then 8 x 32 hypotheses.
-template <int ST>
+// Dynamic shared memory: 8 x MS matches, 8 x 32 hypotheses (evaluation
+// forms), then per warp the exact hypotheses (LANE: 32 x 9 128-bit entries
+// and the warp's best so far, 9 more; else 32 x 9 doubles).  LANE: windows
+// of at most kLaneScoreMax pixels, whose hypotheses are all scored one per
+// lane (the other scoring path is not compiled in).
+constexpr int ransac_warp_match_stride(bool lane) { return lane ? kLaneScoreMax : 256; }
+constexpr size_t ransac_warp_hx_bytes(bool lane) { return lane ? (32 * 9 + 9) * sizeof(i128) : 32 * 9 * sizeof(double); }
+constexpr size_t ransac_warp_smem(bool lane) {
+    return 8 * ransac_warp_match_stride(lane) * sizeof(float4) + 8 * 32 * sizeof(Mef) + 8 * ransac_warp_hx_bytes(lane);
+}
+template <int ST, bool LANE>
 __global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g, int level, int stage,
                                                      PlaneParams pp) {
+    constexpr int MS = ransac_warp_match_stride(LANE);
     extern __shared__ float4 warp_dyn[];
     __shared__ Mef wmef[8];
-    __shared__ int cand[8 * 3 * kCandMax];
     const int warp = threadIdx.x >> 5;
     const int cell = blockIdx.x * 8 + warp;
     if (cell >= g.ncells()) return;
-    float4* match = warp_dyn + warp * 256;
-    Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + 8 * 256) + warp * 32;
+    float4* match = warp_dyn + warp * MS;
+    Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + 8 * MS) + warp * 32;
+    char* hx = reinterpret_cast<char*>(warp_dyn + 8 * MS + 8 * 32 * 4) + (size_t)warp * ransac_warp_hx_bytes(LANE);
     WarpGroup grp;
-    ransac_fit<WarpGroup, ST>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, nullptr,
-                              &wmef[warp], cand + warp * 3 * kCandMax);
+    ransac_fit<WarpGroup, ST, LANE>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, nullptr,
+                                    &wmef[warp], hx);
 }
 template <int ST>
 __global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
@@ -1303,10 +1393,10 @@ __global__ void __launch_bounds__(256, 3) k_ransac_block(PairView pv, LevelGeom 
     __shared__ Mef hyp[8 * 32];
     __shared__ Mef wmef;
     __shared__ int gbest, kfull;
-    __shared__ int cand[8 * 3 * kCandMax];
     BlockGroup<256> grp{red_d, red_i, red_u};
-    ransac_fit<BlockGroup<256>, ST>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, hyp, &gbest,
-                                    &kfull, &wmef, cand);
+    __shared__ double hl[8 * 32 * 9];  // the exact forms of the block's 8 x 32 hypotheses in flight
+    ransac_fit<BlockGroup<256>, ST, false>(grp, pv, g, level, stage, pp, blockIdx.y, blockIdx.x, match_dyn, hyp,
+                                           &gbest, &kfull, &wmef, hl);
 }
 template <int ST>
 __global__ void __launch_bounds__(256) k_ransac_finish_block(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
@@ -1756,13 +1846,20 @@ static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, 
                              cudaStream_t st) {
     const int nc = g.ncells();
     if (g.s <= 16) {
-        const size_t wsmem = 8 * 256 * sizeof(float4) + 8 * 32 * sizeof(Mef);
         static bool wattr_set = false;
         if (!wattr_set) {
-            cudaFuncSetAttribute(k_ransac_warp<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsmem);
+            cudaFuncSetAttribute(k_ransac_warp<ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ransac_warp_smem(false));
+            cudaFuncSetAttribute(k_ransac_warp<ST, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ransac_warp_smem(true));
             wattr_set = true;
         }
-        k_ransac_warp<ST><<<dim3((nc + 7) / 8, 2), 256, wsmem, st>>>(pv, g, level, stage, pp);
+        if (g.s * g.s <= kLaneScoreMax)
+            k_ransac_warp<ST, true><<<dim3((nc + 7) / 8, 2), 256, ransac_warp_smem(true), st>>>(pv, g, level, stage,
+                                                                                                pp);
+        else
+            k_ransac_warp<ST, false><<<dim3((nc + 7) / 8, 2), 256, ransac_warp_smem(false), st>>>(pv, g, level,
+                                                                                                  stage, pp);
         k_refit_solve<<<(2 * nc + 63) / 64, 64, 0, st>>>(pv, g, pp);
         k_ransac_finish_warp<ST><<<dim3((nc + 7) / 8, 2), 256, 0, st>>>(pv, g, stage, pp);
         return;

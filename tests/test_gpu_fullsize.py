@@ -299,9 +299,11 @@ def test_fullsize_merge_and_nnf_update_every_level(torch, pair):
 
 def test_fullsize_fill_and_final_map(torch, pair):
     """The model-propagation fill and the final flow and occlusion map (Sec. 3.4.1), recomputed by the oracle from
-    the GPU's state just before them (accumulated labels, models, cue bits, NNF): labels after the fill, flows and
-    occlusion bits equal the GPU's on all but a tiny fraction of pixels (the oracle logs no near ties here, so
-    the bound is on the fraction: decisions within rounding of the loss ties or of the occlusion threshold)."""
+    the GPU's state just before them (accumulated labels, models, cue bits, NNF): labels after the fill and
+    occlusion bits equal the GPU's except at the near ties the oracle logs (a colour error within the band of eps
+    or occ_thresh, two candidates' errors within the band of the tie margin, a target within the band of the
+    frame edge, or a marked neighbour), and flows agree within the FP32 mapping's error wherever the labels
+    agree."""
     gp = _params()
     P = oracle_params(gp, W, H)
     frames, _ = oracle_frames(P, pair.frame1, pair.frame2)
@@ -321,16 +323,22 @@ def test_fullsize_fill_and_final_map(torch, pair):
     ctx.close()
     d = 0
     acc = _labels(am0[d], aL0[d], af0[d])
+    amb = np.zeros(W * H, np.uint8)
     O.fill(P, frames[d][0], frames[d][1], np.ascontiguousarray(gmh[d]), np.ascontiguousarray(gmi[d]),
-           np.ascontiguousarray(cue[d]), acc)
+           np.ascontiguousarray(cue[d]), acc, amb)
     diff = am1[d] != acc.m
-    assert diff.mean() < 1e-4, int(diff.sum())
+    filled = (am0[d] < 0) & (acc.m >= 0)
+    print(f"fill: {int(filled.sum())} pixels filled, {int((amb != 0).sum())} logged near ties, "
+          f"{int(diff.sum())} labels differ")
+    assert not (diff & (amb == 0)).any(), int((diff & (amb == 0)).sum())
     oflow, oocc = O.final(P, frames[d][0], frames[d][1], acc, nnf[d, :, 0].copy(), nnf[d, :, 1].copy(),
-                          np.ascontiguousarray(cue[d]))
+                          np.ascontiguousarray(cue[d]), amb)
     fd = np.hypot(*(gflow - oflow).T)
     tol = 1e-5 + 4 * 2.0 ** -24 * np.hypot(oflow[:, 0], oflow[:, 1])
-    assert np.mean(fd[~diff] > tol[~diff]) < 1e-4
-    assert np.mean(gocc != oocc) < 1e-3, int((gocc != oocc).sum())
+    assert not ((fd > tol) & ~diff).any(), int(((fd > tol) & ~diff).sum())
+    docc = gocc != oocc
+    print(f"final: {int(docc.sum())} occlusion bits differ, {int((amb != 0).sum())} pixels logged")
+    assert not (docc & (amb == 0)).any(), int((docc & (amb == 0)).sum())
 
 
 def test_fullsize_stage1_cues_every_model(torch, pair):

@@ -330,21 +330,16 @@ def test_fill_and_final_lockstep(torch, W, H, r, cells):
     torch.cuda.synchronize()
     gflow, gocc = flows[0].cpu().numpy().reshape(n, 2), occs[0].cpu().numpy().reshape(n)
     acc = R.acc[0].copy()
-    O.fill(P, frames[0][0], frames[0][1], R.mh[0], R.mi[0], R.cue[0], acc)
-    oflow, oocc = O.final(P, frames[0][0], frames[0][1], acc, R.vx[0], R.vy[0], R.cue[0])
-    # near ties: final colour error within 1e-5 of the threshold, or fill choices within 1e-5
-    d_occ = np.flatnonzero(gocc != oocc)
-    for i in d_occ:
-        y, x = divmod(int(i), W)
-        X, Y = x + oflow[i, 0], y + oflow[i, 1]
-        if 0 <= X <= W - 1 and 0 <= Y <= H - 1:
-            smp = O.sample_bilinear(frames[0][1], X, Y)
-            dl = np.abs(frames[0][0][y, x] - smp).mean()
-            assert abs(dl - P.occ_thresh) < TIE * P.occ_thresh, (x, y, dl)
-        else:
-            pytest.fail(f"occlusion differs at out-of-frame target ({x}, {y})")
+    amb = np.zeros(n, np.uint8)
+    O.fill(P, frames[0][0], frames[0][1], R.mh[0], R.mi[0], R.cue[0], acc, amb)
+    oflow, oocc = O.final(P, frames[0][0], frames[0][1], acc, R.vx[0], R.vy[0], R.cue[0], amb)
+    # Sec. 3.4.1: occlusion bits and flows equal except at the near ties the oracle logs (fill choices and
+    # occlusion decisions within the bands of their thresholds, or next to such a choice); flows within the FP32
+    # mapping's error
+    assert not ((gocc != oocc) & (amb == 0)).any(), int(((gocc != oocc) & (amb == 0)).sum())
     fd = np.hypot(*(gflow - oflow).T)
-    assert np.mean(fd > 1e-5) < 0.005, np.mean(fd > 1e-5)
+    tol = 1e-5 + 4 * 2.0 ** -24 * np.hypot(oflow[:, 0], oflow[:, 1])
+    assert not ((fd > tol) & (amb == 0)).any(), int(((fd > tol) & (amb == 0)).sum())
     ctx.close()
 
 
@@ -355,7 +350,9 @@ def test_tiny_config_end_to_end(torch):
     agree within the FP32 mapping's error and their EPE against the ground truth within 1e-3 px.  Different plane
     choices come from near ties between overlapping windows' fits of one surface and are few.  Pixels without a
     plane keep their NNF offsets from the random search, where a near tie upstream changes an offset by many
-    pixels: the whole frame's agreement and EPE are bounded more loosely."""
+    pixels; over the whole frame the EPE still agrees within 1e-3 px (the final-flow bar) and under 1 % of the
+    flows differ.  Each stage on its own is checked against the oracle given the same state, with every
+    difference at a logged near tie, by the lock-step tests above and the full-size tests."""
     s = scene.tiny_scene(0)
     gp = gpm.default_params()
     ctx = _ctx(torch, gp, 128, 96)
@@ -371,9 +368,10 @@ def test_tiny_config_end_to_end(torch):
     # the same plane decision: the flows agree within the FP32 mapping's error, the EPE within 1e-3 px
     assert st["same_share"] > 0.8 and st["same_max_flow_diff"] < 1e-3, st
     assert abs(st["epe_same_gpu"] - st["epe_same_oracle"]) <= 1e-3, st
-    # different plane decisions (near ties between overlapping windows' fits of one surface) are few
-    assert st["label_agree"] > 0.98 and st["plane_agree"] > 0.97, st
-    assert st["agree"] > 0.95 and abs(st["epe_gpu"] - st["epe_oracle"]) < 0.01, st
+    # different plane decisions (near ties between overlapping windows' fits of one surface) are few, and the
+    # whole frame's EPE agrees within the final-flow bar, 1e-3 px
+    assert st["label_agree"] > 0.99 and st["plane_agree"] > 0.99, st
+    assert st["agree"] > 0.99 and abs(st["epe_gpu"] - st["epe_oracle"]) <= 1e-3, st
     ctx.close()
 
 

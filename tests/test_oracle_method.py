@@ -550,6 +550,44 @@ def test_fill_takes_the_lowest_model_id_among_equal_neighbours():
     assert acc.L[1] == 0 and acc.L[3] == 0
 
 
+def test_fill_and_final_log_their_near_ties():
+    """The near-tie logs of the fill and of the final map (Sec. 3.4.1): a choice whose colour error lies within
+    the band of eps (1e-5 relative, 2e-6 absolute) is marked; a pixel that looked at a marked neighbour is marked;
+    a clear choice is not.  In the final map an occlusion decision within the band of occ_thresh, or a target
+    within the band of the frame edge, is marked.  Dyadic colours make every error exact."""
+    W, H = 7, 1
+    P = O.Params(W, H, cells=(2,), fill_iters=1, eps=0.25)
+    src = np.full((H, W, 3), 0.5)
+    tgt = src.copy()
+    tgt[0, 1] += 0.25 - 2.0 ** -22                  # pixel 1: error just below eps
+    mh = np.zeros((8, 9))
+    for m in (3, 4, 5):
+        mh[m] = np.eye(3).reshape(9)
+    mi = np.zeros((8, O.MI), np.int32)
+    acc = O.Labels.empty(W, P.eps)
+    acc.m[:] = [5, -1, -1, 3, -1, -1, 4]
+    cue = np.zeros(W, np.uint8)
+    amb = np.zeros(W, np.uint8)
+    amb[6] = 1                                       # pixel 6's own label rests on a near tie upstream
+    O.fill(P, src, tgt, mh, mi, cue, acc, amb)
+    assert list(acc.m) == [5, 5, 3, 3, 3, 4, 4]
+    assert list(amb) == [0, 1, 0, 0, 0, 1, 1]
+    W = 4
+    P = O.Params(W, H, cells=(2,), occ_thresh=0.25)
+    src = np.full((H, W, 3), 0.5)
+    tgt = src.copy()
+    tgt[0, 0] += 0.25 - 2.0 ** -22                  # pixel 0: warp error just below the threshold
+    tgt[0, 1] += 0.125                               # pixel 1: clearly below
+    acc = O.Labels.empty(W, P.eps)
+    acc.m[:] = [3, 3, -1, 3]
+    acc.fx[3] = 1e-3                                 # pixel 3 lands on the edge of the 1e-3 px frame tolerance
+    amb = np.zeros(W, np.uint8)
+    vx = np.zeros(W, np.int32)
+    flow, occ = O.final(P, src, tgt, acc, vx, vx.copy(), np.zeros(W, np.uint8), amb)
+    assert list(occ) == [0, 0, 1, 0]
+    assert list(amb) == [1, 0, 0, 1]
+
+
 def test_final_map_flow_source_and_occlusion_rule_on_hand_built_state():
     """Sec. 3.4.1 and readings R20/R23: the flow is the plane's where a pixel has one, else its NNF offset; a pixel
     is occluded without a plane, under the many-to-one cue, outside the frame (beyond 1e-3 px) or where the warp

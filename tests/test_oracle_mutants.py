@@ -116,18 +116,17 @@ MUTANTS = [
     ("oracle_planes.c", "vx[i] = (int)floor(afx[i] + 0.5);", "vx[i] = (int)afx[i];",
      [METH + "test_merge_keeps_coarse_unless_clearly_better_and_nnf_update_rounds_half_up"]),
     # model-propagation fill (Sec. 3.4.1): neighbours, and the colour bound
-    ("oracle_planes.c", "NY[4] = {0, 0, -1, 1};\n                int bm = -1;", "NY[4] = {0, 0, -1, -1};\n                int bm = -1;",
+    ("oracle_planes.c", "NY[4] = {0, 0, -1, 1};\n                int bm = -1, nd", "NY[4] = {0, 0, -1, -1};\n                int bm = -1, nd",
      [METH + "test_fill_front_advances_one_pixel_per_jacobi_iteration"]),
     ("oracle_planes.c", "(fabs(d - bL) <= ORC_L_TIE && m < bm)", "(fabs(d - bL) <= ORC_L_TIE && m > bm)",
      [METH + "test_fill_takes_the_lowest_model_id_among_equal_neighbours"]),
-    ("oracle_planes.c", "if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y) || !in_frame(P, X, Y)) continue;",
-     "if (!map_h(mh + (size_t)m * 9, x, y, &X, &Y)) continue;",
+    ("oracle_planes.c", "if (!in_frame(P, X, Y)) continue;\n                    double d = delta_at(P, src, tgt, x, y, X, Y);\n"
+     "                    if (amb && near_colour(d, P->eps)) a = 1;", "double d = delta_at(P, src, tgt, x, y, X, Y);",
      [METH + "test_fill_takes_the_lowest_model_id_among_equal_neighbours"]),
     # final map (Sec. 3.4.1, R20, R23) and the edge-aware fill (R28)
     ("oracle_planes.c", "int o = am[i] < 0 || (cue[i] & ORC_CUE_M2O);", "int o = am[i] < 0;",
      [METH + "test_final_map_flow_source_and_occlusion_rule_on_hand_built_state"]),
-    ("oracle_planes.c", "else if (!(delta_at(P, src, tgt, x, y, X, Y) < P->occ_thresh)) o = 1;",
-     "else if (delta_at(P, src, tgt, x, y, X, Y) > P->occ_thresh) o = 1;",
+    ("oracle_planes.c", "if (!(d < P->occ_thresh)) o = 1;", "if (d > P->occ_thresh) o = 1;",
      [METH + "test_final_map_flow_source_and_occlusion_rule_on_hand_built_state"]),
     ("oracle_planes.c", "flow[2 * i] = (float)afx[s];", "flow[2 * i] = (float)afx[i];",
      [METH + "test_edge_aware_fill_evaluates_the_seed_plane_at_the_pixel"]),
@@ -150,7 +149,8 @@ MUTANTS = [
      "pm_run(P, src[d], tgt[d], d, l, S->mh[d], S->mi[d], NULL, S->vx[d], S->vy[d], S->cost[d]);",
      [METH + "test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours"]),
     ("oracle_pipeline.c",
-     "        orc_fill(P, src[d], tgt[d], S->mh[d], S->mi[d], S->cue[d], S->am[d], S->aL[d], S->afx[d], S->afy[d]);\n", "",
+     "        orc_fill(P, src[d], tgt[d], S->mh[d], S->mi[d], S->cue[d], S->am[d], S->aL[d], S->afx[d], S->afy[d], NULL);\n",
+     "",
      [METH + "test_pipeline_freezes_assigned_pixels_and_fills_from_neighbours"]),
     # census codes (Sec. 6), HSV equalisation (Sec. 4.2), geodesic fill seeds (R28)
     ("oracle_color.c", "if (grey(rgb, W, nx, ny) < c) code |= 1u << bit;", "if (grey(rgb, W, nx, ny) <= c) code |= 1u << bit;",
