@@ -416,7 +416,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- batched and served forms
-BATCH_PAIRS, BATCH_DISTINCT = 64, 16
+BATCH_PAIRS, BATCH_DISTINCT = 64, 64
 SERVE_POOL, SERVE_BUDGET_GB, SERVE_ACTIVE, SERVE_TRACE_REQ = 32, 24, 16, 48
 SERVE_LOADS = (0.5, 0.9, 2.0)  # offered rate / measured capacity
 
@@ -435,9 +435,10 @@ def extras_start(workers: int):
 
 
 def batched_block(scenes):
-    """64 pairs of mixed sizes: the plain FP32 form (one stream, eager launches) against the batched forms
-    (autotuned streams, CUDA graphs) with FP32 storage and with BF16 storage (FP32 accumulation), with EPE
-    against ground truth for each."""
+    """64 distinct pairs of mixed sizes: the plain FP32 form (each pair alone, one after the other, eager launches)
+    against the batched form (every stage one launch over a context's pairs, autotuned stream count and
+    PatchMatch launch shape, CUDA graphs) with FP32, FP16 and BF16 storage (FP32 arithmetic), with EPE against
+    ground truth for each."""
     import numpy as np
     import torch
 
@@ -445,55 +446,79 @@ def batched_block(scenes):
     which = [k % len(scenes) for k in range(BATCH_PAIRS)]
     frames = [(scenes[w].frame1, scenes[w].frame2) for w in which]
     gt = [scenes[w].flow for w in which]
+    nocc = [scenes[w].occ == 0 for w in which]
     ids = list(range(BATCH_PAIRS))
     gp32 = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP)
-    plain = batch.BatchRunner(gp32, frames, ids, streams=1, graph=False)
-    plain.run()
-    t_plain = plain.time(1)
-    r32 = plain.results()
-    plain.close()
-    del plain
+    # plain: one pair at a time through its own context
+    dev = [(torch.from_numpy(np.ascontiguousarray(f1)).cuda(), torch.from_numpy(np.ascontiguousarray(f2)).cuda())
+           for f1, f2 in frames]
+    ctxs = [gpm.Context(gp32, f1.shape[1], f1.shape[0]) for f1, _ in frames]
+    outs = [(torch.empty((f1.shape[0], f1.shape[1], 2), dtype=torch.float32, device="cuda"),
+             torch.empty((f1.shape[0], f1.shape[1]), dtype=torch.uint8, device="cuda")) for f1, _ in frames]
+
+    def plain_pass():
+        for k in range(BATCH_PAIRS):
+            c = ctxs[k]
+            c.match([dev[k]], 0, pair_ids=[ids[k]])
+            for lvl in range(1, len(CELLS) + 1):
+                c.fit_planes(lvl)
+                c.match(None, lvl)
+            c.flow_and_occlusion([outs[k][0]], [outs[k][1]])
+
+    plain_pass()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plain_pass()
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) * 1e-3
+    r32 = [(f.cpu().numpy(), o.cpu().numpy()) for f, o in outs]
+    for c in ctxs:
+        c.close()
+    del ctxs, outs, dev
     torch.cuda.empty_cache()
-    # batched with FP32 storage: the plain form's arithmetic, so its accuracy is the plain form's
-    best32, tune32 = batch.autotune_streams(gp32, frames, ids, candidates=(2, 4, 8))
-    rf = batch.BatchRunner(gp32, frames, ids, streams=best32, graph=True)
-    rf.run()
-    t32b = rf.time(2)
-    rf32 = rf.results()
-    rf.close()
-    del rf
-    torch.cuda.empty_cache()
-    gpb = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=gpm.GPM_BF16)
-    best, tune = batch.autotune_streams(gpb, frames, ids, candidates=(2, 4, 8))
-    r = batch.BatchRunner(gpb, frames, ids, streams=best, graph=True)
-    r.run()
-    t = r.time(2)
-    rb = r.results()
-    r.close()
-    del r
-    torch.cuda.empty_cache()
-    # EPE over ground-truth non-occluded pixels: occluded pixels keep their NNF offset (no interpolation)
-    nocc = [scenes[w].occ == 0 for w in which]
     e32 = float(np.mean([batch.epe(r32[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
-    eb = float(np.mean([batch.epe(rb[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
-    ef = float(np.mean([batch.epe(rf32[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
+
+    def batched(gp, tune):
+        (ns, bps), times = tune
+        r = batch.BatchRunner(batch.with_launch_shape(gp, bps), frames, ids, streams=ns, graph=True)
+        r.run()
+        t = r.time(2)
+        res = r.results()
+        r.close()
+        del r
+        torch.cuda.empty_cache()
+        return t, res, ns, bps, times
+
+    tune32 = batch.autotune(gp32, frames, ids)
+    t32b, rf32, ns, bps, times32 = batched(gp32, tune32)
     same = all(np.array_equal(rf32[i][0], r32[i][0]) and np.array_equal(rf32[i][1], r32[i][1])
                for i in range(BATCH_PAIRS))
-    sizes = sorted({(s.frame1.shape[1], s.frame1.shape[0]) for s in scenes})
-    return {"value": BATCH_PAIRS / t, "unit": "pairs/s", "pairs": BATCH_PAIRS,
-            "workload": f"{BATCH_PAIRS} pairs from {len(scenes)} seeded scenes, sizes uniform over "
-                        f"{[f'{w}x{h}' for w, h in batch.BATCH_SIZES]} (drawn: {[f'{w}x{h}' for w, h in sizes]}), "
+    forms = {}
+    for name, stg in (("f16", gpm.GPM_F16), ("bf16", gpm.GPM_BF16)):
+        gp = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=stg)
+        t, res, ns2, bps2, _ = batched(gp, tune32)  # the FP32 choice of streams and launch shape
+        e = float(np.mean([batch.epe(res[i][0], gt[i], nocc[i]) for i in range(BATCH_PAIRS)]))
+        forms[name] = {"value": BATCH_PAIRS / t, "unit": "pairs/s", "speedup_vs_plain_f32": t_plain / t,
+                       "epe_nocc_px": e, "epe_diff_vs_plain_f32_px": e - e32,
+                       "equal_accuracy_within_0.01_px": abs(e - e32) <= 0.01}
+    sizes = sorted({(sc.frame1.shape[1], sc.frame1.shape[0]) for sc in scenes})
+    best_rp = min(forms, key=lambda k: abs(forms[k]["epe_diff_vs_plain_f32_px"]))
+    return {"value": BATCH_PAIRS / t32b, "unit": "pairs/s", "pairs": BATCH_PAIRS, "storage": "f32",
+            "speedup_vs_plain_f32": t_plain / t32b, "bitwise_equal_to_plain": same,
+            "workload": f"{BATCH_PAIRS} distinct seeded scenes, sizes uniform over "
+                        f"{[f'{w}x{h}' for w, h in batch.BATCH_SIZES]} (drawn: {len(sizes)} distinct sizes), "
                         "3-8 planar layers, motion up to 96 px",
-            "storage": "bf16", "accumulation": "f32", "streams": best, "cuda_graph": True,
-            "autotune_ms_per_pass": {str(k): v * 1e3 for k, v in tune.items()},
-            "plain_f32": {"value": BATCH_PAIRS / t_plain, "unit": "pairs/s", "streams": 1, "cuda_graph": False},
-            "speedup_vs_plain_f32": t_plain / t,
-            "batched_f32": {"value": BATCH_PAIRS / t32b, "unit": "pairs/s", "streams": best32, "cuda_graph": True,
-                            "speedup_vs_plain_f32": t_plain / t32b, "epe_nocc_px": ef, "abs_diff": abs(ef - e32),
-                            "bitwise_equal_to_plain": same,
-                            "autotune_ms_per_pass": {str(k): v * 1e3 for k, v in tune32.items()}},
-            "epe_nocc_px": {"plain_f32": e32, "batched_bf16": eb, "abs_diff": abs(eb - e32),
-                            "pixels": "ground-truth non-occluded, mean over the pairs"},
+            "form": "every stage one launch over each context's pairs (pair index on the device), CUDA graph per "
+                    "stream",
+            "autotune": {"streams": ns, "sweep_blocks_per_sm": bps,
+                         "ms_per_pass": {f"{k[0]} streams, {k[1]} blocks/SM": v * 1e3 for k, v in times32.items()},
+                         "cache_key": "frame sizes, patch radius, storage"},
+            "plain_f32": {"value": BATCH_PAIRS / t_plain, "unit": "pairs/s", "epe_nocc_px": e32,
+                          "how": "each pair alone through its own context, eager launches, one stream"},
+            "reduced_precision": forms,
+            "closest_reduced_precision_form": best_rp,
             "l2": "inputs of one pass (> 1 GB of frames and state) exceed L2"}
 
 

@@ -88,6 +88,8 @@ typedef struct {
     uint64_t seed;                        /* Philox4x32-10 key */
     int32_t interp;                       /* 1: pixels left without a plane take the geodesically nearest
                                              assigned pixel's plane (edge-aware fill; EpicFlow stand-in) */
+    int32_t sweep_blocks_per_sm;          /* launch shape of the PatchMatch launches: blocks per SM of the grid
+                                             (0 = 8; 1..32); results do not depend on it */
 } gpm_params;
 
 /* Capacity of a context, fixed at creation. */
@@ -135,6 +137,13 @@ gpm_status gpm_destroy(gpm_ctx* ctx);
 
 /* Bytes of device memory a context with these parameters and limits holds. */
 size_t gpm_required_bytes(const gpm_params* params, const gpm_limits* limits);
+
+/* Batches: each stage of gpm_match / gpm_fit_planes / gpm_flow_and_occlusion
+   is one kernel launch per 8 pairs of the call, whatever their sizes: the
+   pairs' views and level geometries travel in the launch's parameters and
+   the pair index is on the device (blockIdx.z).  Each pair's result is
+   bitwise what it gets alone.  No call copies from the host in the stream,
+   so a whole multi-pair pipeline can be captured in a CUDA graph. */
 
 /* level 0: ingest the pairs' frames (RGB -> RGBX storage, gain
    normalisation), initial NNF for both directions (random offsets from

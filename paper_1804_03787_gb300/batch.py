@@ -1,13 +1,14 @@
 """Batched form: many frame pairs of mixed sizes per step.
 
-The pairs are spread over several CUDA streams, one gpm context per stream,
-balanced by pixel count, so that the small and latency-bound launches of one
-pair (per-window refit solves, the coarse RANSAC levels, the streaming label
-kernels) overlap with the work of the others.  Each stream's whole pipeline
-(every scale, both directions, flow and occlusion) is captured once into a
-CUDA graph and replayed as a single launch per step, which removes the host
-launch cost of the ~180 kernels per pair.  The number of streams is picked by
-a small autotuner that times replays of each candidate.
+The pairs go to one or more gpm contexts, one CUDA stream each, balanced by
+pixel count.  Inside a context the pair index is on the device: every stage
+is one launch per eight of the context's pairs (blockIdx.z = pair), so a
+context of eight pairs makes the same ~190 launches as one of a single pair.  Each stream's whole pipeline (every scale, both directions,
+flow and occlusion) is captured once into a CUDA graph and replayed as a
+single launch per step.  The number of streams and the PatchMatch launch
+shape (blocks per SM) are picked by a small autotuner that times replays of
+each candidate, its choice cached by the batch's frame sizes, patch radius
+and storage type.
 
 Every pair's result depends only on its frames, its pair id and the
 parameters, so the grouping changes nothing but the speed.
@@ -120,18 +121,38 @@ class BatchRunner:
         self.groups = []
 
 
-def autotune_streams(params: gpm.Params, frames, pair_ids, candidates=(2, 4, 8), reps: int = 1):
-    """Times a captured runner for each stream count; returns (best count, {count: seconds per pass})."""
+# Autotuner choices, keyed by (frame sizes, patch radius, storage type).
+_TUNE_CACHE: dict = {}
+
+
+def with_launch_shape(params: gpm.Params, blocks_per_sm: int) -> gpm.Params:
+    """A copy of params with the PatchMatch launch shape set (results do not depend on it)."""
+    p = type(params).from_buffer_copy(params)
+    p.sweep_blocks_per_sm = blocks_per_sm
+    return p
+
+
+def autotune(params: gpm.Params, frames, pair_ids, streams=(1, 2, 4), blocks_per_sm=(4, 8), reps: int = 1,
+             cache: dict | None = None):
+    """Times a captured runner for each (stream count, PatchMatch blocks per SM); returns the fastest pair and
+    {candidate: seconds per pass}.  The choice is cached by the batch's frame sizes, patch radius and storage."""
     import torch
+    cache = _TUNE_CACHE if cache is None else cache
+    key = (tuple(sorted((int(f1.shape[1]), int(f1.shape[0])) for f1, _ in frames)), int(params.patch_radius),
+           int(params.storage))
+    if key in cache:
+        return cache[key]
     times = {}
-    for s in candidates:
-        r = BatchRunner(params, frames, pair_ids, streams=s, graph=True)
-        r.run()
-        times[s] = r.time(reps)
-        r.close()
-        del r
-        torch.cuda.empty_cache()
-    best = min(times, key=lambda s: (times[s], s))
+    for s in streams:
+        for b in blocks_per_sm:
+            r = BatchRunner(with_launch_shape(params, b), frames, pair_ids, streams=s, graph=True)
+            r.run()
+            times[(s, b)] = r.time(reps)
+            r.close()
+            del r
+            torch.cuda.empty_cache()
+    best = min(times, key=lambda k: (times[k], k))
+    cache[key] = (best, times)
     return best, times
 
 

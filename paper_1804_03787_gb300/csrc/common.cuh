@@ -586,4 +586,27 @@ struct PairView {
     unsigned long long* evals;  // [PM evaluations level 0, levels >= 1, RANSAC residual tests], or nullptr
 };
 
+// The pairs of a launch, passed by value as a __grid_constant__ kernel
+// parameter: one launch of a stage covers up to kBatch pairs (blockIdx.z
+// selects the pair), each with its views and level geometries.  Reading them
+// from the constant bank keeps them out of registers and free of aliasing
+// with the kernels' stores (a table in global memory cost the 1024x436 step
+// ~1.5 ms of reloads), and no host copy enters the stream, so a whole
+// multi-pair pipeline can be captured in one CUDA graph.
+constexpr int kMaxScales = 8;  // GPM_MAX_SCALES
+constexpr int kBatch = 8;
+struct Batch {
+    PairView pv[kBatch];
+    LevelGeom geo[kBatch][kMaxScales];  // level l at index l - 1
+    __host__ __device__ __forceinline__ const PairView& view(int z) const { return pv[z]; }
+    __host__ __device__ __forceinline__ LevelGeom geom(int z, int level) const {
+        return level > 0 ? geo[z][level - 1] : LevelGeom{};
+    }
+};
+// The caller's flow and occlusion buffers of the pairs of one final-map launch (kernel parameters).
+struct FinalOut {
+    float* flow[kBatch];
+    uint8_t* occ[kBatch];
+};
+
 }  // namespace gpm

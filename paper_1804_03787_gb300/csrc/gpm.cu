@@ -27,9 +27,8 @@ struct Slot {
     uint32_t pair_id = 0;
     int stage = -1;  // -1 nothing; 2l = after match(l); 2l-1 = after fit_planes(l)
     void* block = nullptr;
-    PairView pv{};
+    PairView pv{};  // the pair's views (passed to the kernels by value)
     LevelGeom geoms[GPM_MAX_SCALES];
-    LevelGeom* d_geoms = nullptr;
     int total_cells = 0, m = 0;
     double* partial = nullptr;
     double* gain = nullptr;
@@ -160,6 +159,8 @@ gpm_status validate_params(const gpm_params& P, std::string& why) {
     if (P.census != 0 && P.census != 1) return why = "census must be 0 or 1", GPM_EINVAL;
     if (P.census && !P.pm_init) return why = "census needs pm_init = 1 (a random initial NNF)", GPM_EINVAL;
     if (P.interp != 0 && P.interp != 1) return why = "interp must be 0 or 1", GPM_EINVAL;
+    if (P.sweep_blocks_per_sm < 0 || P.sweep_blocks_per_sm > 32)
+        return why = "sweep_blocks_per_sm must be 0..32", GPM_EINVAL;
     if (!(P.eps > 0) || !(P.ransac_px > 0) || !(P.fb_px > 0)) return why = "eps, ransac_px, fb_px must be > 0", GPM_EINVAL;
     if (!(P.scale_min > 0) || !(P.scale_max >= P.scale_min)) return why = "bad scale range", GPM_EINVAL;
     return GPM_OK;
@@ -204,7 +205,6 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_np, int max_models, i
     pv.list_count = (int*)take(4 * sizeof(int));
     pv.flag = (int*)take(sizeof(int));
     pv.gq = (int*)take(n * sizeof(int));
-    LevelGeom* dg = (LevelGeom*)take(sizeof(LevelGeom) * GPM_MAX_SCALES);
     double* partial = (double*)take(sizeof(double) * 2 * kPartialBlocks);
     double* gain = (double*)take(sizeof(double));
     int* eq_hist = (int*)take(2 * 256 * sizeof(int));
@@ -213,7 +213,6 @@ size_t layout_slot(const gpm_params& P, int max_n, int max_np, int max_models, i
     if (s) {
         s->d_evals = evals;
         s->pv = pv;
-        s->d_geoms = dg;
         s->partial = partial;
         s->gain = gain;
         s->eq_hist = eq_hist;
@@ -242,19 +241,56 @@ PlaneParams plane_params(const gpm_params& P) {
     return pp;
 }
 
+// Grid of the PatchMatch launches (init, recost, sweeps): the launch shape chosen by the parameters.
+int pm_grid(const gpm_ctx* c) { return c->nsm * (c->P.sweep_blocks_per_sm > 0 ? c->P.sweep_blocks_per_sm : 8); }
+
 int grid_for(const gpm_ctx* c, int n) {
     const int want = (n + 255) / 256;
     return std::max(1, std::min(want, c->nsm * 8));
 }
 
-int num_radii(int W, int H) {
-    const int R0 = std::max(W, H);
-    int k = 0;
-    while ((R0 >> k) >= 1) ++k;
-    return k;
+// The kernel-parameter table of pairs [first, first + nb), nb <= kBatch (blockIdx.z = pair - first).
+Batch batch(const gpm_ctx* c, int first, int nb) {
+    static_assert(kMaxScales == GPM_MAX_SCALES, "level tables");
+    Batch b;
+    std::memset(&b, 0, sizeof b);
+    for (int k = 0; k < nb; ++k) {
+        const Slot& s = c->slots[first + k];
+        b.pv[k] = s.pv;
+        for (int l = 0; l < kMaxScales; ++l) b.geo[k][l] = s.geoms[l];
+    }
+    return b;
+}
+// Calls f(batch, nb) for pairs [first, first + np) in launches of up to kBatch pairs.
+template <class F>
+void each_batch(const gpm_ctx* c, int first, int np, F&& f) {
+    for (int i0 = 0; i0 < np; i0 += kBatch) {
+        const int nb = std::min(kBatch, np - i0);
+        f(batch(c, first + i0, nb), nb);
+    }
+}
+int batches(int np) { return (np + kBatch - 1) / kBatch; }
+
+// Host-side sizes of the pairs 0..np-1 of a call: grids are sized for the largest.
+struct Dims {
+    int np = 0, max_n = 0, max_w = 0, max_h = 0, max_m = 0;
+    int max_cells[GPM_MAX_SCALES] = {};
+};
+Dims dims_of(const gpm_ctx* c, int np) {
+    Dims d;
+    d.np = np;
+    for (int i = 0; i < np; ++i) {
+        const Slot& s = c->slots[i];
+        d.max_n = std::max(d.max_n, s.n);
+        d.max_w = std::max(d.max_w, s.W);
+        d.max_h = std::max(d.max_h, s.H);
+        d.max_m = std::max(d.max_m, s.m);
+        for (int l = 0; l < c->P.num_scales; ++l) d.max_cells[l] = std::max(d.max_cells[l], s.geoms[l].ncells());
+    }
+    return d;
 }
 
-// Sets the slot's frame size and level geometry (uploaded to the device).
+// Sets the slot's frame size and level geometry (its table entry is written by the caller).
 gpm_status set_dims(gpm_ctx* c, Slot& s, int W, int H) {
     if (s.W == W && s.H == H) return GPM_OK;
     s.W = W;
@@ -267,44 +303,42 @@ gpm_status set_dims(gpm_ctx* c, Slot& s, int W, int H) {
     s.pv.n = s.n;
     s.pv.Wp = W + 2 * kPad;
     s.pv.m_models = s.m;
-    launch_set_geoms(s.geoms, s.d_geoms, c->stream);
     // a defined NNF (zero offsets) before anything reads it
     for (int d = 0; d < 2; ++d) cudaMemsetAsync(s.pv.nnf[d], 0, sizeof(int2) * s.n, c->stream);
     return cuda_check(c, "set_dims");
 }
 
-void reset_models(gpm_ctx* c, Slot& s) {
-    for (int d = 0; d < 2; ++d) {
-        cudaMemsetAsync(s.pv.mh[d], 0, sizeof(double) * 9 * s.m, c->stream);
-        cudaMemsetAsync(s.pv.mef[d], 0, sizeof(Mef) * s.m, c->stream);
-        cudaMemsetAsync(s.pv.mi[d], 0, sizeof(int) * kMI * s.m, c->stream);
-    }
-}
-
-void build_lists(gpm_ctx* c, Slot& s) {
-    pbeg(c, GPM_PROF_LISTS, 1);
-    cudaMemsetAsync(s.pv.list_count, 0, 4 * sizeof(int), c->stream);
-    launch_build_lists(s.pv, grid_for(c, s.n), c->stream);
+// Restricted-sweep lists of pairs [first, first + np).
+void build_lists(gpm_ctx* c, int first, int np, int max_n) {
+    pbeg(c, GPM_PROF_LISTS, 2 * batches(np));
+    each_batch(c, first, np, [&](const Batch& b, int nb) { launch_build_lists(b, nb, grid_for(c, max_n), c->stream); });
     pend(c);
 }
 
-void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
+// One PatchMatch launch per batch of pairs.
+void launch_pm_all(gpm_ctx* c, PmLaunch& L, int np) {
+    each_batch(c, 0, np, [&](const Batch& b, int nb) {
+        L.bt = b;
+        L.np = nb;
+        launch_pm(L, c->stream);
+    });
+}
+
+void pm_sweeps(gpm_ctx* c, const Dims& D, int level) {
     PmLaunch L{};
-    L.pv = &s.pv;
-    L.geom = level > 0 ? s.geoms[level - 1] : LevelGeom{};
     L.radius = c->P.patch_radius;
     L.storage = c->P.storage;
     L.level = level;
-    L.nrad = num_radii(s.W, s.H);
-    L.grid_blocks = c->nsm * 8;
+    L.grid_blocks = pm_grid(c);
     L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
     L.k1 = (uint32_t)(c->P.seed >> 32);
     L.census = level == 0 ? c->P.census : 0;
-    s.census_costs = L.census != 0;
+    for (int i = 0; i < D.np; ++i) c->slots[i].census_costs = L.census != 0;
+    const int nb = batches(D.np);
     if (level > 0 || !c->P.pm_init) {
         L.op = PmLaunch::RECOST;
-        pbeg(c, GPM_PROF_PM_RECOST, 1);
-        launch_pm(L, c->stream);
+        pbeg(c, GPM_PROF_PM_RECOST, nb);
+        launch_pm_all(c, L, D.np);
         pend(c);
     }
     L.op = PmLaunch::SWEEP;
@@ -312,45 +346,57 @@ void pm_sweeps(gpm_ctx* c, Slot& s, int level) {
         for (int ph = 0; ph < 2; ++ph) {
             L.it = it;
             L.phase = ph;
-            pbeg(c, level == 0 ? GPM_PROF_PM_SWEEP : GPM_PROF_PM_SWEEP_PLANE, 1);
-            launch_pm(L, c->stream);
+            pbeg(c, level == 0 ? GPM_PROF_PM_SWEEP : GPM_PROF_PM_SWEEP_PLANE, nb);
+            launch_pm_all(c, L, D.np);
             pend(c);
         }
 }
 
-void copy_labels(gpm_ctx* c, const Labels& dst, const Labels& src, int n) {
-    cudaMemcpyAsync(dst.m, src.m, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(dst.L, src.L, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(dst.v, src.v, sizeof(int2) * n, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(dst.r, src.r, sizeof(float2) * n, cudaMemcpyDeviceToDevice, c->stream);
-}
-
-// Algorithm 1 for one level on one pair (both directions in every launch).
-void fit_level(gpm_ctx* c, Slot& s, int level) {
-    const LevelGeom& g = s.geoms[level - 1];
+// Algorithm 1 for one level on pairs 0..np-1 (both directions and every pair in each launch).
+void fit_level(gpm_ctx* c, const Dims& D, int level) {
+    const int s = c->P.cell_size[level - 1], mc = D.max_cells[level - 1], np = D.np, nb = batches(np);
     const PlaneParams pp = plane_params(c->P);
-    const int gb = grid_for(c, s.n);
+    const int gb = grid_for(c, D.max_n);
     cudaStream_t st = c->stream;
+    auto each = [&](auto&& f) { each_batch(c, 0, np, f); };
     // first stage: fit, tentative assignment, cues on both directions, final assignment
-    pbeg(c, GPM_PROF_RANSAC, 3), launch_ransac(s.pv, g, level, 1, pp, st), pend(c);
-    pbeg(c, GPM_PROF_ASSIGN, 1), launch_assign(s.pv, g, 1, 0, 0, pp, gb, st), pend(c);
-    pbeg(c, GPM_PROF_CUES, 3), launch_cues(s.pv, g, 1, 0, pp, gb, st), pend(c);
-    pbeg(c, GPM_PROF_ASSIGN, 1), launch_assign(s.pv, g, 1, 1, 1, pp, gb, st), pend(c);
+    pbeg(c, GPM_PROF_RANSAC, 3 * nb);
+    each([&](const Batch& b, int n) { launch_ransac(b, n, level, s, mc, 1, pp, st); });
+    pend(c);
+    pbeg(c, GPM_PROF_ASSIGN, nb);
+    each([&](const Batch& b, int n) { launch_assign(b, n, level, 1, 0, 0, pp, gb, st); });
+    pend(c);
+    pbeg(c, GPM_PROF_CUES, 3 * nb);
+    each([&](const Batch& b, int n) { launch_cues(b, n, level, mc, 1, 0, pp, gb, st); });
+    pend(c);
+    pbeg(c, GPM_PROF_ASSIGN, nb);
+    each([&](const Batch& b, int n) { launch_assign(b, n, level, 1, 1, 1, pp, gb, st); });
+    pend(c);
     // second stage on the residual pixels
-    pbeg(c, GPM_PROF_RANSAC, 3), launch_ransac(s.pv, g, level, 2, pp, st), pend(c);
-    pbeg(c, GPM_PROF_ASSIGN, 1);
-    for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
-    launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
+    pbeg(c, GPM_PROF_RANSAC, 3 * nb);
+    each([&](const Batch& b, int n) { launch_ransac(b, n, level, s, mc, 2, pp, st); });
     pend(c);
-    pbeg(c, GPM_PROF_CUES, 3), launch_cues(s.pv, g, 2, 2, pp, gb, st), pend(c);
-    pbeg(c, GPM_PROF_ASSIGN, 1);
-    for (int d = 0; d < 2; ++d) copy_labels(c, s.pv.lvl[d], s.pv.st1[d], s.n);
-    launch_assign(s.pv, g, 2, 2, 0, pp, gb, st);
-    pend(c);
+    for (int pass = 0; pass < 2; ++pass) {  // assignment, cues, then the assignment after the cues
+        pbeg(c, GPM_PROF_ASSIGN, 2 * nb);
+        each([&](const Batch& b, int n) {
+            launch_copy_labels(b, n, 2, 3, gb, st);
+            launch_assign(b, n, level, 2, 2, 0, pp, gb, st);
+        });
+        pend(c);
+        if (pass == 0) {
+            pbeg(c, GPM_PROF_CUES, 3 * nb);
+            each([&](const Batch& b, int n) { launch_cues(b, n, level, mc, 2, 2, pp, gb, st); });
+            pend(c);
+        }
+    }
     // many-to-one, merge, NNF update, lists for the restricted sweeps
-    pbeg(c, GPM_PROF_MANY_TO_ONE, 2), launch_many_to_one(s.pv, pp, gb, st), pend(c);
-    pbeg(c, GPM_PROF_MERGE, 1), launch_merge_update(s.pv, pp, gb, st), pend(c);
-    build_lists(c, s);
+    pbeg(c, GPM_PROF_MANY_TO_ONE, 3 * nb);
+    each([&](const Batch& b, int n) { launch_many_to_one(b, n, pp, gb, st); });
+    pend(c);
+    pbeg(c, GPM_PROF_MERGE, nb);
+    each([&](const Batch& b, int n) { launch_merge_update(b, n, pp, gb, st); });
+    pend(c);
+    build_lists(c, 0, np, D.max_n);
 }
 
 }  // namespace
@@ -440,6 +486,7 @@ gpm_status gpm_create(const gpm_params* params, const gpm_limits* limits, gpm_al
         s.block = p;
         layout_slot(*params, c->max_n, c->max_np, c->max_models, c->max_cells, (char*)p, &s);
     }
+
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -473,6 +520,7 @@ gpm_status gpm_destroy(gpm_ctx* c) {
             cudaFreeAsync(s.block, c->stream);
         s.block = nullptr;
     }
+
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
     delete c;
@@ -502,55 +550,75 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
             if (e) return e;
             s.pair_id = p.pair_id;
             s.pv.pair_id = p.pair_id;
-            if (c->P.census) {  // codes of the frames as given (census ignores a global gain)
-                pbeg(c, GPM_PROF_INGEST, 2);
-                launch_census(p.frame1, p.frame2, p.width, p.height, p.row_stride,
-                              reinterpret_cast<long long*>(s.pv.m2o_key[0]), reinterpret_cast<long long*>(s.pv.m2o_key[1]),
-                              s.pv.code[0], s.pv.code[1], c->stream);
-                pend(c);
-            }
-            if (c->P.interp) {  // greys of frame 1 as given, for the edge-aware fill at the end
-                pbeg(c, GPM_PROF_INGEST, 1);
-                launch_grey_q(p.frame1, p.width, p.height, p.row_stride, s.pv.gq, c->stream);
-                pend(c);
-            }
-            pbeg(c, GPM_PROF_INGEST, (c->P.equalize ? 7 : 5) + (c->P.census ? 0 : 1));
-            launch_ingest(p.frame1, p.frame2, p.width, p.height, p.row_stride, c->P.gain_normalize, c->P.storage,
-                          s.partial, kPartialBlocks, s.gain, const_cast<void*>(s.pv.img[0]),
-                          const_cast<void*>(s.pv.img[1]), c->P.equalize ? s.eq_hist : nullptr,
-                          c->P.equalize ? s.eq_lut : nullptr, c->stream);
-            launch_pad_frames(s.pv, c->P.storage, grid_for(c, s.pv.Wp * (s.H + 2 * kPad)), c->stream);
-            if (!c->P.census) launch_box_sums(s.pv, c->P.patch_radius, c->P.storage, grid_for(c, s.n), c->stream);
-            reset_models(c, s);
-            launch_reset_labels(s.pv, c->P.eps, grid_for(c, s.n), c->stream);
-            pend(c);
-            if (c->P.pm_init) {
-                PmLaunch L{};
-                L.op = PmLaunch::INIT;
-                L.pv = &s.pv;
-                L.radius = c->P.patch_radius;
-                L.storage = c->P.storage;
-                L.grid_blocks = c->nsm * 8;
-                L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
-                L.k1 = (uint32_t)(c->P.seed >> 32);
-                L.census = c->P.census;
-                pbeg(c, GPM_PROF_PM_INIT, 1);
-                launch_pm(L, c->stream);
-                pend(c);
-            } else {
-                build_lists(c, s);  // every pixel (nothing frozen) for the recost
-            }
-            pm_sweeps(c, s, 0);
-            s.stage = 0;
         }
+        const Dims D = dims_of(c, n_pairs);
+        // ingest of every pair, in launches of up to kBatch pairs (census codes of the frames as given:
+        // census ignores a global gain; greys of frame 1 for the edge-aware fill)
+        for (int i0 = 0; i0 < n_pairs; i0 += kBatch) {
+            const int nj = std::min(kBatch, n_pairs - i0);
+            IngestJobs J{};
+            int mn = 0, mh = 0;
+            for (int k = 0; k < nj; ++k) {
+                const gpm_pair& p = pairs[i0 + k];
+                Slot& s = c->slots[i0 + k];
+                IngestJob& j = J.j[k];
+                j.f1 = p.frame1;
+                j.f2 = p.frame2;
+                j.W = p.width;
+                j.H = p.height;
+                j.stride = p.row_stride;
+                j.partial = s.partial;
+                j.gain = s.gain;
+                j.o1 = const_cast<void*>(s.pv.img[0]);
+                j.o2 = const_cast<void*>(s.pv.img[1]);
+                j.hist = c->P.equalize ? s.eq_hist : nullptr;
+                j.lut = c->P.equalize ? s.eq_lut : nullptr;
+                if (c->P.census) {
+                    j.k1 = reinterpret_cast<long long*>(s.pv.m2o_key[0]);
+                    j.k2 = reinterpret_cast<long long*>(s.pv.m2o_key[1]);
+                    j.c1 = s.pv.code[0];
+                    j.c2 = s.pv.code[1];
+                }
+                if (c->P.interp) j.gq = s.pv.gq;
+                mn = std::max(mn, s.n);
+                mh = std::max(mh, s.H);
+            }
+            pbeg(c, GPM_PROF_INGEST, (c->P.equalize ? 6 : 3) + (c->P.census ? 2 : 0) + (c->P.interp ? 1 : 0));
+            launch_ingest_jobs(J, nj, mn, mh, c->P.gain_normalize, c->P.storage, c->stream);
+            pend(c);
+        }
+        const int gb = grid_for(c, D.max_n);
+        pbeg(c, GPM_PROF_INGEST, (4 + (c->P.census ? 0 : 1)) * batches(n_pairs));
+        each_batch(c, 0, n_pairs, [&](const Batch& b, int nb) {
+            launch_pad_frames(b, nb, c->P.storage, grid_for(c, (D.max_w + 2 * kPad) * (D.max_h + 2 * kPad)),
+                              c->stream);
+            if (!c->P.census) launch_box_sums(b, nb, D.max_w, D.max_h, c->P.patch_radius, c->P.storage, c->stream);
+            launch_reset_models(b, nb, D.max_m, c->stream);
+            launch_reset_labels(b, nb, c->P.eps, gb, c->stream);
+        });
+        pend(c);
+        if (c->P.pm_init) {
+            PmLaunch L{};
+            L.op = PmLaunch::INIT;
+            L.radius = c->P.patch_radius;
+            L.storage = c->P.storage;
+            L.grid_blocks = pm_grid(c);
+            L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
+            L.k1 = (uint32_t)(c->P.seed >> 32);
+            L.census = c->P.census;
+            pbeg(c, GPM_PROF_PM_INIT, batches(n_pairs));
+            launch_pm_all(c, L, n_pairs);
+            pend(c);
+        } else {
+            build_lists(c, 0, n_pairs, D.max_n);  // every pixel (nothing frozen) for the recost
+        }
+        pm_sweeps(c, D, 0);
+        for (int i = 0; i < n_pairs; ++i) c->slots[i].stage = 0;
     } else {
         for (int i = 0; i < n_pairs; ++i)
             if (c->slots[i].stage != 2 * level - 1) return fail(c, GPM_EINVAL, "gpm_match(l) must follow gpm_fit_planes(l)");
-        for (int i = 0; i < n_pairs; ++i) {
-            Slot& s = c->slots[i];
-            pm_sweeps(c, s, level);
-            s.stage = 2 * level;
-        }
+        pm_sweeps(c, dims_of(c, n_pairs), level);
+        for (int i = 0; i < n_pairs; ++i) c->slots[i].stage = 2 * level;
     }
     return cuda_check(c, "gpm_match");
 }
@@ -562,11 +630,8 @@ gpm_status gpm_fit_planes(gpm_ctx* c, int32_t n_pairs, int32_t level) {
     for (int i = 0; i < n_pairs; ++i)
         if (c->slots[i].stage != 2 * (level - 1))
             return fail(c, GPM_EINVAL, "gpm_fit_planes(l) must follow gpm_match(l-1)");
-    for (int i = 0; i < n_pairs; ++i) {
-        Slot& s = c->slots[i];
-        fit_level(c, s, level);
-        s.stage = 2 * level - 1;
-    }
+    fit_level(c, dims_of(c, n_pairs), level);
+    for (int i = 0; i < n_pairs; ++i) c->slots[i].stage = 2 * level - 1;
     return cuda_check(c, "gpm_fit_planes");
 }
 
@@ -580,24 +645,30 @@ gpm_status gpm_flow_and_occlusion(gpm_ctx* c, int32_t n_pairs, float* const* flo
             return fail(c, GPM_EINVAL, "gpm_flow_and_occlusion must follow a gpm_match call");
     }
     const PlaneParams pp = plane_params(c->P);
-    for (int i = 0; i < n_pairs; ++i) {
-        Slot& s = c->slots[i];
-        const int gb = grid_for(c, s.n);
-        pbeg(c, GPM_PROF_FILL, c->P.fill_iters);
-        launch_fill(s.pv, pp, c->P.fill_iters, gb, Labels{}, c->stream);
-        pend(c);
-        const int* seed = nullptr;
-        if (c->P.interp) {  // scratch: the many-to-one keys and the pixel lists are idle by now
-            pbeg(c, GPM_PROF_FILL, 1 + 2 * kFillRounds);
-            launch_fill_seeds(s.pv, s.pv.gq, reinterpret_cast<long long*>(s.pv.m2o_key[0]), s.pv.list[0], kFillRounds,
-                              gb, c->stream);
-            pend(c);
-            seed = s.pv.list[0];
-        }
-        pbeg(c, GPM_PROF_FINAL, 1);
-        launch_final(s.pv, pp, seed, flow_out[i], occ_out[i], gb, c->stream);
+    const Dims D = dims_of(c, n_pairs);
+    const int gb = grid_for(c, D.max_n);
+    const int nb = batches(n_pairs);
+    pbeg(c, GPM_PROF_FILL, (c->P.fill_iters + (c->P.fill_iters & 1)) * nb);
+    each_batch(c, 0, n_pairs, [&](const Batch& b, int n) { launch_fill(b, n, pp, c->P.fill_iters, gb, c->stream); });
+    pend(c);
+    if (c->P.interp) {  // seeds into scratch: the many-to-one keys and the pixel lists are idle by now
+        pbeg(c, GPM_PROF_FILL, (1 + 2 * kFillRounds) * nb);
+        each_batch(c, 0, n_pairs, [&](const Batch& b, int n) {
+            launch_fill_seeds(b, n, D.max_w, D.max_h, kFillRounds, gb, c->stream);
+        });
         pend(c);
     }
+    pbeg(c, GPM_PROF_FINAL, nb);
+    for (int i0 = 0; i0 < n_pairs; i0 += kBatch) {  // the caller's buffers travel as kernel parameters too
+        const int nf = std::min(kBatch, n_pairs - i0);
+        FinalOut out{};
+        for (int k = 0; k < nf; ++k) {
+            out.flow[k] = flow_out[i0 + k];
+            out.occ[k] = occ_out[i0 + k];
+        }
+        launch_final(batch(c, i0, nf), nf, pp, c->P.interp, out, gb, c->stream);
+    }
+    pend(c);
     return cuda_check(c, "gpm_flow_and_occlusion");
 }
 
@@ -701,7 +772,7 @@ gpm_status gpm_export(gpm_ctx* c, int32_t pair, int32_t what, void* dst) {
             for (int k = 0; k < 2; ++k) cudaMemcpyAsync(d + k * n, s.pv.cue[k], n, cudaMemcpyDeviceToDevice, st);
             break;
         case GPM_FRAMES:
-            launch_frames_export(s.pv, c->P.storage, (float*)d, st);
+            launch_frames_export(batch(c, pair, 1), s.n, c->P.storage, (float*)d, st);
             c->launches += 1;
             break;
         default:
@@ -728,14 +799,14 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
             for (int k = 0; k < 2; ++k)
                 cudaMemcpyAsync(s.pv.mh[k], d + k * m * 9 * sizeof(double), m * 9 * sizeof(double),
                                 cudaMemcpyDeviceToDevice, st);
-            launch_import_models(s.pv, s.d_geoms, c->P.num_scales, s.m, st);
+            launch_import_models(batch(c, pair, 1), c->P.num_scales, s.m, st);
             c->launches += 1;
             break;
         case GPM_MODEL_INFO:
             for (int k = 0; k < 2; ++k)
                 cudaMemcpyAsync(s.pv.mi[k], d + k * m * kMI * sizeof(int), m * kMI * sizeof(int),
                                 cudaMemcpyDeviceToDevice, st);
-            launch_import_models(s.pv, s.d_geoms, c->P.num_scales, s.m, st);
+            launch_import_models(batch(c, pair, 1), c->P.num_scales, s.m, st);
             c->launches += 1;
             break;
         case GPM_LABELS: {
@@ -749,9 +820,9 @@ gpm_status gpm_import(gpm_ctx* c, int32_t pair, int32_t what, const void* src, i
                 c->launches += 1;
             }
             // frozen pixels and the restricted PatchMatch lists follow the accumulated map
-            launch_frozen_from_labels(s.pv, grid_for(c, s.n), st);
+            launch_frozen_from_labels(batch(c, pair, 1), 1, grid_for(c, s.n), st);
             c->launches += 1;
-            build_lists(c, s);
+            build_lists(c, pair, 1, s.n);
             break;
         }
         case GPM_CUES:
@@ -768,7 +839,8 @@ gpm_status gpm_profile_select(gpm_ctx* c, uint32_t class_mask, int32_t count_eva
     if (!c) return GPM_EINVAL;
     if (class_mask >> GPM_PROF_CLASSES) return fail(c, GPM_EINVAL, "class_mask names no kernel class");
     c->prof_mask = class_mask;
-    for (auto& s : c->slots) {
+    for (int i = 0; i < (int)c->slots.size(); ++i) {
+        Slot& s = c->slots[i];
         s.pv.evals = count_evals ? s.d_evals : nullptr;
         if (count_evals) cudaMemsetAsync(s.d_evals, 0, GPM_COUNTERS * sizeof(unsigned long long), c->stream);
     }

@@ -1138,7 +1138,9 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
 // per window and direction: centred, Hartley-scaled moments from the exact
 // integer ones, the smallest eigenvector of A^T A started from the winner,
 // denormalisation, and the geometry checks of the winner and of the refit.
-__global__ void __launch_bounds__(64) k_refit_solve(PairView pv, LevelGeom g, PlaneParams pp) {
+__global__ void __launch_bounds__(64) k_refit_solve(const __grid_constant__ Batch bt, int level, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int nc = g.ncells();
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * nc) return;
@@ -1357,8 +1359,9 @@ constexpr size_t ransac_warp_smem(bool lane) {
     return 8 * ransac_warp_match_stride(lane) * sizeof(float4) + 8 * 32 * sizeof(Mef) + 8 * ransac_warp_hx_bytes(lane);
 }
 template <int ST, bool LANE>
-__global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g, int level, int stage,
-                                                     PlaneParams pp) {
+__global__ void __launch_bounds__(256, 3) k_ransac_warp(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     constexpr int MS = ransac_warp_match_stride(LANE);
     extern __shared__ float4 warp_dyn[];
     __shared__ Mef wmef[8];
@@ -1373,7 +1376,9 @@ __global__ void __launch_bounds__(256, 3) k_ransac_warp(PairView pv, LevelGeom g
                                     &wmef[warp], hx);
 }
 template <int ST>
-__global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
+__global__ void __launch_bounds__(256) k_ransac_finish_warp(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     __shared__ float4 match[8][256];
     const int warp = threadIdx.x >> 5;
     const int cell = blockIdx.x * 8 + warp;
@@ -1384,8 +1389,10 @@ __global__ void __launch_bounds__(256) k_ransac_finish_warp(PairView pv, LevelGe
 
 // Larger windows: one 256-thread block per window (matches in dynamic shared memory).
 template <int ST>
-__global__ void __launch_bounds__(256, 3) k_ransac_block(PairView pv, LevelGeom g, int level, int stage,
-                                                      PlaneParams pp) {
+__global__ void __launch_bounds__(256, 3) k_ransac_block(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
+    if ((int)blockIdx.x >= g.ncells()) return;  // past this pair's windows (block-uniform)
     extern __shared__ float4 match_dyn[];
     __shared__ double red_d[8];
     __shared__ int red_i[8];
@@ -1399,7 +1406,10 @@ __global__ void __launch_bounds__(256, 3) k_ransac_block(PairView pv, LevelGeom 
                                            &gbest, &kfull, &wmef, hl);
 }
 template <int ST>
-__global__ void __launch_bounds__(256) k_ransac_finish_block(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
+__global__ void __launch_bounds__(256) k_ransac_finish_block(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
+    if ((int)blockIdx.x >= g.ncells()) return;  // past this pair's windows (block-uniform)
     extern __shared__ float4 match_dyn[];
     __shared__ double red_d[8];
     __shared__ int red_i[8];
@@ -1415,7 +1425,9 @@ __global__ void __launch_bounds__(256) k_ransac_finish_block(PairView pv, LevelG
 // pixel is an inlier iff delta < eps, and takes the inlier plane with the
 // smallest L = delta (first window on ties), with flow H p - p.
 template <int ST>
-__global__ void k_assign(PairView pv, LevelGeom g, int stage, int which, int write_resid, PlaneParams pp) {
+__global__ void k_assign(const __grid_constant__ Batch bt, int level, int stage, int which, int write_resid, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     const int W = pv.W, H = pv.H, n = pv.n;
     Labels out = which == 0 ? pv.tent[dir] : (which == 1 ? pv.st1[dir] : pv.lvl[dir]);
@@ -1465,7 +1477,9 @@ __global__ void k_assign(PairView pv, LevelGeom g, int stage, int which, int wri
 }
 
 // ---------------------------------------------------------------- occlusion cues (Sec. 3.4)
-__global__ void k_cue_zero(PairView pv, LevelGeom g, int stage) {
+__global__ void k_cue_zero(const __grid_constant__ Batch bt, int level, int stage) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncells(); c += gridDim.x * blockDim.x) {
         int* f = pv.mi[dir] + (size_t)((g.base + c) * 2 + stage - 1) * kMI;
@@ -1477,7 +1491,9 @@ __global__ void k_cue_zero(PairView pv, LevelGeom g, int stage) {
 // Forward-backward plane projection symmetry: a pixel assigned to a plane of
 // this level and stage with flow f is symmetric iff q = round(p + f) holds an
 // assigned pixel of the other direction with flow g, |f + g| < t_fb.
-__global__ void k_cue_counts(PairView pv, LevelGeom g, int stage, int which, PlaneParams pp) {
+__global__ void k_cue_counts(const __grid_constant__ Batch bt, int level, int stage, int which, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     const int W = pv.W, H = pv.H, n = pv.n;
     const Labels lab = which == 0 ? pv.tent[dir] : pv.lvl[dir];
@@ -1503,7 +1519,9 @@ __global__ void k_cue_counts(PairView pv, LevelGeom g, int stage, int which, Pla
 }
 
 // Discard planes failing the symmetry cue (eta) or the RANSAC/colour overlap cue (kappa).
-__global__ void k_cue_invalidate(PairView pv, LevelGeom g, int stage, PlaneParams pp) {
+__global__ void k_cue_invalidate(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < g.ncells(); c += gridDim.x * blockDim.x) {
         const int id = (g.base + c) * 2 + stage - 1;
@@ -1527,7 +1545,14 @@ __global__ void k_cue_invalidate(PairView pv, LevelGeom g, int stage, PlaneParam
 
 // Many-to-one: per target q = round(p + f), the lowest (L, index) keeps it;
 // a loser whose flow differs from the winner's by t_fb or more is occluded.
-__global__ void k_m2o_claim(PairView pv) {
+__global__ void k_m2o_init(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const int dir = blockIdx.y;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x)
+        pv.m2o_key[dir][i] = ~0ull;
+}
+__global__ void k_m2o_claim(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const int W = pv.W, n = pv.n;
     const Labels lab = pv.lvl[dir];
@@ -1541,7 +1566,8 @@ __global__ void k_m2o_claim(PairView pv) {
         atomicMin(&pv.m2o_key[dir][q], key);
     }
 }
-__global__ void k_m2o_resolve(PairView pv, PlaneParams pp) {
+__global__ void k_m2o_resolve(const __grid_constant__ Batch bt, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const int W = pv.W, n = pv.n;
     const Labels lab = pv.lvl[dir];
@@ -1565,7 +1591,8 @@ __global__ void k_m2o_resolve(PairView pv, PlaneParams pp) {
 }
 
 // Sec. 3.3 merge with coarse priority, then the NNF update of Sec. 3.3.1.
-__global__ void k_merge_update(PairView pv, PlaneParams pp) {
+__global__ void k_merge_update(const __grid_constant__ Batch bt, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const int n = pv.n;
     const Labels lab = pv.lvl[dir], acc = pv.acc[dir];
@@ -1585,11 +1612,13 @@ __global__ void k_merge_update(PairView pv, PlaneParams pp) {
 }
 
 // ---------------------------------------------------------------- fill and final map (Sec. 3.4.1)
+// One Jacobi iteration: labels from acc into tent (flip = 0) or from tent into acc (flip = 1).
 template <int ST>
-__global__ void k_fill(PairView pv, Labels cur0, Labels cur1, Labels nxt0, Labels nxt1, PlaneParams pp) {
+__global__ void k_fill(const __grid_constant__ Batch bt, int flip, PlaneParams pp) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const int W = pv.W, H = pv.H, n = pv.n;
-    const Labels cur = dir ? cur1 : cur0, nxt = dir ? nxt1 : nxt0;
+    const Labels cur = flip ? pv.tent[dir] : pv.acc[dir], nxt = flip ? pv.acc[dir] : pv.tent[dir];
     const void* src = pv.img[dir];
     const void* tgt = pv.img[1 - dir];
     const Mef* mef = pv.mef[dir];
@@ -1650,15 +1679,15 @@ __global__ void k_fill(PairView pv, Labels cur0, Labels cur1, Labels nxt0, Label
 // left to right, rows right to left, columns top to bottom, columns bottom to
 // top; an offer wins with a lower distance, or an equal one from a lower seed
 // index.
-__global__ void k_grey_q(const float* f, int W, int H, int64_t stride, int* q) {
-    const int n = W * H;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int y = i / W, x = i - y * W;
-        const float* p = f + (int64_t)y * stride + 3 * x;
-        q[i] = (int)floor(1024.0 * (((double)p[0] + (double)p[1]) + (double)p[2]));
-    }
-}
-__global__ void k_seed_init(const int* am, int n, long long* dist, int* seed) {
+// Scratch of the edge-aware fill (the many-to-one keys and the pixel lists are idle by then): distances and seeds.
+__device__ __forceinline__ long long* seed_dist(const PairView& pv) { return reinterpret_cast<long long*>(pv.m2o_key[0]); }
+__device__ __forceinline__ int* seed_of(const PairView& pv) { return pv.list[0]; }
+__global__ void k_seed_init(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const int* am = pv.acc[0].m;
+    const int n = pv.n;
+    long long* dist = seed_dist(pv);
+    int* seed = seed_of(pv);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         dist[i] = am[i] >= 0 ? 0 : (1ll << 62);
         seed[i] = am[i] >= 0 ? i : -1;
@@ -1718,7 +1747,12 @@ __device__ __forceinline__ void seed_walk(const int* q, long long* dist, int* se
 // one thread per column, top to bottom then bottom to top (a warp's loads of
 // one step are then coalesced).  Lines are disjoint, so fusing a line's two
 // scans keeps the order of four whole-frame scans.
-__global__ void k_seed_lines(const int* q, long long* dist, int* seed, int W, int H, int cols) {
+__global__ void k_seed_lines(const __grid_constant__ Batch bt, int cols) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const int* q = pv.gq;
+    long long* dist = seed_dist(pv);
+    int* seed = seed_of(pv);
+    const int W = pv.W, H = pv.H;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (!cols) {
         if (t >= H) return;
@@ -1735,7 +1769,12 @@ __global__ void k_seed_lines(const int* q, long long* dist, int* seed, int W, in
 // plane at this pixel) and occlusion: no plane, a cue flag, or colour error
 // after warping by the final flow >= occ_thresh.
 template <int ST>
-__global__ void k_final(PairView pv, int dir, PlaneParams pp, const int* seed, float* flow, uint8_t* occ) {
+__global__ void k_final(const __grid_constant__ Batch bt, PlaneParams pp, int interp, const __grid_constant__ FinalOut out) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const int dir = 0;
+    const int* seed = interp ? seed_of(pv) : nullptr;
+    float* flow = out.flow[blockIdx.z];
+    uint8_t* occ = out.occ[blockIdx.z];
     const int W = pv.W, H = pv.H, n = pv.n;
     const Labels acc = pv.acc[dir];
     const void* src = pv.img[dir];
@@ -1788,7 +1827,9 @@ __global__ void k_final(PairView pv, int dir, PlaneParams pp, const int* seed, f
 
 // ---------------------------------------------------------------- state import / export helpers
 // Evaluation forms of imported absolute homographies.
-__global__ void k_import_models(PairView pv, LevelGeom* geoms, int nlev, int m) {
+__global__ void k_import_models(const __grid_constant__ Batch bt, int nlev, int m) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom* geoms = bt.geo[blockIdx.z];
     const int dir = blockIdx.y;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < m; id += gridDim.x * blockDim.x) {
         const int cell_all = id >> 1;
@@ -1841,11 +1882,13 @@ __global__ void k_labels_import(Labels l, int n, int m, const int* im, const flo
 }
 
 // ---------------------------------------------------------------- launchers
+// Every launch covers np pairs (blockIdx.z); grids are sized for the largest pair, and each block past its own
+// pair's pixels or windows does nothing.
 template <int ST>
-static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
-                             cudaStream_t st) {
-    const int nc = g.ncells();
-    if (g.s <= 16) {
+static void launch_ransac_st(const Batch& bt, int np, int level, int s, int max_cells, int stage,
+                             const PlaneParams& pp, cudaStream_t st) {
+    const int nc = max_cells;
+    if (s <= 16) {
         static bool wattr_set = false;
         if (!wattr_set) {
             cudaFuncSetAttribute(k_ransac_warp<ST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1854,17 +1897,16 @@ static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, 
                                  (int)ransac_warp_smem(true));
             wattr_set = true;
         }
-        if (g.s * g.s <= kLaneScoreMax)
-            k_ransac_warp<ST, true><<<dim3((nc + 7) / 8, 2), 256, ransac_warp_smem(true), st>>>(pv, g, level, stage,
-                                                                                                pp);
+        const dim3 grid((nc + 7) / 8, 2, np);
+        if (s * s <= kLaneScoreMax)
+            k_ransac_warp<ST, true><<<grid, 256, ransac_warp_smem(true), st>>>(bt, level, stage, pp);
         else
-            k_ransac_warp<ST, false><<<dim3((nc + 7) / 8, 2), 256, ransac_warp_smem(false), st>>>(pv, g, level,
-                                                                                                  stage, pp);
-        k_refit_solve<<<(2 * nc + 63) / 64, 64, 0, st>>>(pv, g, pp);
-        k_ransac_finish_warp<ST><<<dim3((nc + 7) / 8, 2), 256, 0, st>>>(pv, g, stage, pp);
+            k_ransac_warp<ST, false><<<grid, 256, ransac_warp_smem(false), st>>>(bt, level, stage, pp);
+        k_refit_solve<<<dim3((2 * nc + 63) / 64, 1, np), 64, 0, st>>>(bt, level, pp);
+        k_ransac_finish_warp<ST><<<grid, 256, 0, st>>>(bt, level, stage, pp);
         return;
     }
-    const size_t smem = (size_t)g.s * g.s * sizeof(float4);
+    const size_t smem = (size_t)s * s * sizeof(float4);
     static bool attr_set = false;
     if (!attr_set) {
         const int mx = kMaxCell * kMaxCell * (int)sizeof(float4);  // the largest window's matches
@@ -1872,99 +1914,115 @@ static void launch_ransac_st(const PairView& pv, const LevelGeom& g, int level, 
         cudaFuncSetAttribute(k_ransac_finish_block<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
         attr_set = true;
     }
-    k_ransac_block<ST><<<dim3(nc, 2), 256, smem, st>>>(pv, g, level, stage, pp);
-    k_refit_solve<<<(2 * nc + 63) / 64, 64, 0, st>>>(pv, g, pp);
-    k_ransac_finish_block<ST><<<dim3(nc, 2), 256, smem, st>>>(pv, g, stage, pp);
+    k_ransac_block<ST><<<dim3(nc, 2, np), 256, smem, st>>>(bt, level, stage, pp);
+    k_refit_solve<<<dim3((2 * nc + 63) / 64, 1, np), 64, 0, st>>>(bt, level, pp);
+    k_ransac_finish_block<ST><<<dim3(nc, 2, np), 256, smem, st>>>(bt, level, stage, pp);
 }
-void launch_ransac(const PairView& pv, const LevelGeom& g, int level, int stage, const PlaneParams& pp,
+void launch_ransac(const Batch& bt, int np, int level, int s, int max_cells, int stage, const PlaneParams& pp,
                    cudaStream_t st) {
     switch (pp.storage) {
-        case 0: launch_ransac_st<0>(pv, g, level, stage, pp, st); break;
-        case 1: launch_ransac_st<1>(pv, g, level, stage, pp, st); break;
-        case 2: launch_ransac_st<2>(pv, g, level, stage, pp, st); break;
+        case 0: launch_ransac_st<0>(bt, np, level, s, max_cells, stage, pp, st); break;
+        case 1: launch_ransac_st<1>(bt, np, level, s, max_cells, stage, pp, st); break;
+        case 2: launch_ransac_st<2>(bt, np, level, s, max_cells, stage, pp, st); break;
     }
 }
 
-void launch_assign(const PairView& pv, const LevelGeom& g, int stage, int which, int write_resid,
-                   const PlaneParams& pp, int grid_blocks, cudaStream_t st) {
-    const dim3 grid(grid_blocks, 2);
+void launch_assign(const Batch& bt, int np, int level, int stage, int which, int write_resid, const PlaneParams& pp,
+                   int grid_blocks, cudaStream_t st) {
+    const dim3 grid(grid_blocks, 2, np);
     switch (pp.storage) {
-        case 0: k_assign<0><<<grid, 256, 0, st>>>(pv, g, stage, which, write_resid, pp); break;
-        case 1: k_assign<1><<<grid, 256, 0, st>>>(pv, g, stage, which, write_resid, pp); break;
-        case 2: k_assign<2><<<grid, 256, 0, st>>>(pv, g, stage, which, write_resid, pp); break;
+        case 0: k_assign<0><<<grid, 256, 0, st>>>(bt, level, stage, which, write_resid, pp); break;
+        case 1: k_assign<1><<<grid, 256, 0, st>>>(bt, level, stage, which, write_resid, pp); break;
+        case 2: k_assign<2><<<grid, 256, 0, st>>>(bt, level, stage, which, write_resid, pp); break;
     }
 }
 
-void launch_cues(const PairView& pv, const LevelGeom& g, int stage, int which, const PlaneParams& pp,
+void launch_cues(const Batch& bt, int np, int level, int max_cells, int stage, int which, const PlaneParams& pp,
                  int grid_blocks, cudaStream_t st) {
-    const int cb = (g.ncells() + 255) / 256;
-    k_cue_zero<<<dim3(cb, 2), 256, 0, st>>>(pv, g, stage);
-    k_cue_counts<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv, g, stage, which, pp);
-    k_cue_invalidate<<<dim3(cb, 2), 256, 0, st>>>(pv, g, stage, pp);
+    const int cb = (max_cells + 255) / 256;
+    k_cue_zero<<<dim3(cb, 2, np), 256, 0, st>>>(bt, level, stage);
+    k_cue_counts<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt, level, stage, which, pp);
+    k_cue_invalidate<<<dim3(cb, 2, np), 256, 0, st>>>(bt, level, stage, pp);
 }
 
-void launch_many_to_one(const PairView& pv, const PlaneParams& pp, int grid_blocks, cudaStream_t st) {
-    cudaMemsetAsync(pv.m2o_key[0], 0xFF, sizeof(unsigned long long) * pv.n, st);
-    cudaMemsetAsync(pv.m2o_key[1], 0xFF, sizeof(unsigned long long) * pv.n, st);
-    k_m2o_claim<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
-    k_m2o_resolve<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv, pp);
+void launch_many_to_one(const Batch& bt, int np, const PlaneParams& pp, int grid_blocks, cudaStream_t st) {
+    k_m2o_init<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt);
+    k_m2o_claim<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt);
+    k_m2o_resolve<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt, pp);
 }
 
-void launch_merge_update(const PairView& pv, const PlaneParams& pp, int grid_blocks, cudaStream_t st) {
-    k_merge_update<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv, pp);
+void launch_merge_update(const Batch& bt, int np, const PlaneParams& pp, int grid_blocks, cudaStream_t st) {
+    k_merge_update<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt, pp);
 }
 
-void launch_fill(const PairView& pv, const PlaneParams& pp, int iters, int grid_blocks, Labels tmp, cudaStream_t st) {
-    (void)tmp;
+// Label sets of a pair: 0 acc, 1 tent, 2 st1, 3 lvl.
+__device__ __forceinline__ Labels label_set(const PairView& pv, int set, int dir) {
+    return set == 0 ? pv.acc[dir] : (set == 1 ? pv.tent[dir] : (set == 2 ? pv.st1[dir] : pv.lvl[dir]));
+}
+__global__ void k_copy_labels(const __grid_constant__ Batch bt, int from, int to) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const int dir = blockIdx.y;
+    const Labels a = label_set(pv, from, dir), b = label_set(pv, to, dir);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x) {
+        b.m[i] = a.m[i];
+        b.L[i] = a.L[i];
+        b.v[i] = a.v[i];
+        b.r[i] = a.r[i];
+    }
+}
+void launch_copy_labels(const Batch& bt, int np, int from, int to, int grid_blocks, cudaStream_t st) {
+    k_copy_labels<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt, from, to);
+}
+
+void launch_fill(const Batch& bt, int np, const PlaneParams& pp, int iters, int grid_blocks, cudaStream_t st) {
     // ping-pong between acc and tent (tent is free after the last level)
-    Labels a0 = pv.acc[0], a1 = pv.acc[1], b0 = pv.tent[0], b1 = pv.tent[1];
+    const dim3 grid(grid_blocks, 2, np);
     for (int it = 0; it < iters; ++it) {
-        const dim3 grid(grid_blocks, 2);
         switch (pp.storage) {
-            case 0: k_fill<0><<<grid, 256, 0, st>>>(pv, a0, a1, b0, b1, pp); break;
-            case 1: k_fill<1><<<grid, 256, 0, st>>>(pv, a0, a1, b0, b1, pp); break;
-            case 2: k_fill<2><<<grid, 256, 0, st>>>(pv, a0, a1, b0, b1, pp); break;
-        }
-        Labels t0 = a0, t1 = a1;
-        a0 = b0;
-        a1 = b1;
-        b0 = t0;
-        b1 = t1;
-    }
-    if (iters & 1) {  // result sits in tent: copy back into acc
-        for (int d = 0; d < 2; ++d) {
-            const Labels s = d ? pv.tent[1] : pv.tent[0], t = d ? pv.acc[1] : pv.acc[0];
-            cudaMemcpyAsync(t.m, s.m, sizeof(int) * pv.n, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(t.L, s.L, sizeof(float) * pv.n, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(t.v, s.v, sizeof(int2) * pv.n, cudaMemcpyDeviceToDevice, st);
-            cudaMemcpyAsync(t.r, s.r, sizeof(float2) * pv.n, cudaMemcpyDeviceToDevice, st);
+            case 0: k_fill<0><<<grid, 256, 0, st>>>(bt, it & 1, pp); break;
+            case 1: k_fill<1><<<grid, 256, 0, st>>>(bt, it & 1, pp); break;
+            case 2: k_fill<2><<<grid, 256, 0, st>>>(bt, it & 1, pp); break;
         }
     }
+    if (iters & 1) launch_copy_labels(bt, np, 1, 0, grid_blocks, st);  // the result sits in tent
 }
 
-void launch_grey_q(const float* f, int W, int H, int64_t stride, int* q, cudaStream_t st) {
-    k_grey_q<<<152 * 4, 256, 0, st>>>(f, W, H, stride, q);
-}
-
-void launch_fill_seeds(const PairView& pv, const int* q, long long* dist, int* seed, int rounds, int grid_blocks,
-                       cudaStream_t st) {
-    k_seed_init<<<grid_blocks, 256, 0, st>>>(pv.acc[0].m, pv.n, dist, seed);
+void launch_fill_seeds(const Batch& bt, int np, int max_w, int max_h, int rounds, int grid_blocks, cudaStream_t st) {
+    k_seed_init<<<dim3(grid_blocks, 1, np), 256, 0, st>>>(bt);
     for (int r = 0; r < rounds; ++r) {
-        k_seed_lines<<<(pv.H + 31) / 32, 32, 0, st>>>(q, dist, seed, pv.W, pv.H, 0);
-        k_seed_lines<<<(pv.W + 31) / 32, 32, 0, st>>>(q, dist, seed, pv.W, pv.H, 1);
+        k_seed_lines<<<dim3((max_h + 31) / 32, 1, np), 32, 0, st>>>(bt, 0);
+        k_seed_lines<<<dim3((max_w + 31) / 32, 1, np), 32, 0, st>>>(bt, 1);
     }
 }
 
-void launch_final(const PairView& pv, const PlaneParams& pp, const int* seed, float* flow, uint8_t* occ,
-                  int grid_blocks, cudaStream_t st) {
+void launch_final(const Batch& bt, int np, const PlaneParams& pp, int interp, const FinalOut& out, int grid_blocks,
+                  cudaStream_t st) {
+    const dim3 grid(grid_blocks, 1, np);
     switch (pp.storage) {
-        case 0: k_final<0><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, seed, flow, occ); break;
-        case 1: k_final<1><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, seed, flow, occ); break;
-        case 2: k_final<2><<<grid_blocks, 256, 0, st>>>(pv, 0, pp, seed, flow, occ); break;
+        case 0: k_final<0><<<grid, 256, 0, st>>>(bt, pp, interp, out); break;
+        case 1: k_final<1><<<grid, 256, 0, st>>>(bt, pp, interp, out); break;
+        case 2: k_final<2><<<grid, 256, 0, st>>>(bt, pp, interp, out); break;
     }
 }
 
-__global__ void k_reset_labels(PairView pv, float eps) {
+// Clears the models of every window of every level (model ids below m_models).
+__global__ void k_reset_models(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const int dir = blockIdx.y;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < pv.m_models; id += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) pv.mh[dir][(size_t)id * 9 + q] = 0.0;
+        pv.mef[dir][id] = Mef{};
+#pragma unroll
+        for (int q = 0; q < kMI; ++q) pv.mi[dir][(size_t)id * kMI + q] = 0;
+    }
+}
+void launch_reset_models(const Batch& bt, int np, int max_models, cudaStream_t st) {
+    k_reset_models<<<dim3((max_models + 255) / 256, 2, np), 256, 0, st>>>(bt);
+}
+
+__global__ void k_reset_labels(const __grid_constant__ Batch bt, float eps) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x) {
         pv.acc[dir].m[i] = -1;
@@ -1975,38 +2033,40 @@ __global__ void k_reset_labels(PairView pv, float eps) {
         pv.frozen[dir][i] = 0;
     }
 }
-__global__ void k_frozen_from_labels(PairView pv) {
+__global__ void k_frozen_from_labels(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x)
         pv.frozen[dir][i] = pv.acc[dir].m[i] >= 0;
 }
-void launch_frozen_from_labels(const PairView& pv, int grid_blocks, cudaStream_t st) {
-    k_frozen_from_labels<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+void launch_frozen_from_labels(const Batch& bt, int np, int grid_blocks, cudaStream_t st) {
+    k_frozen_from_labels<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt);
 }
 
-void launch_reset_labels(const PairView& pv, float eps, int grid_blocks, cudaStream_t st) {
-    k_reset_labels<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv, eps);
+void launch_reset_labels(const Batch& bt, int np, float eps, int grid_blocks, cudaStream_t st) {
+    k_reset_labels<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt, eps);
 }
 
 template <int ST>
-__global__ void k_frames_export(PairView pv, float* dst) {
+__global__ void k_frames_export(const __grid_constant__ Batch bt, float* dst) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < pv.n; i += gridDim.x * blockDim.x) {
         const float4 a = ldpix<ST>(pv.img[dir], i);
         reinterpret_cast<float4*>(dst)[(size_t)dir * pv.n + i] = a;
     }
 }
-void launch_frames_export(const PairView& pv, int storage, float* dst, cudaStream_t st) {
-    const dim3 grid((pv.n + 255) / 256, 2);
+void launch_frames_export(const Batch& bt, int n, int storage, float* dst, cudaStream_t st) {
+    const dim3 grid((n + 255) / 256, 2);
     switch (storage) {
-        case 0: k_frames_export<0><<<grid, 256, 0, st>>>(pv, dst); break;
-        case 1: k_frames_export<1><<<grid, 256, 0, st>>>(pv, dst); break;
-        case 2: k_frames_export<2><<<grid, 256, 0, st>>>(pv, dst); break;
+        case 0: k_frames_export<0><<<grid, 256, 0, st>>>(bt, dst); break;
+        case 1: k_frames_export<1><<<grid, 256, 0, st>>>(bt, dst); break;
+        case 2: k_frames_export<2><<<grid, 256, 0, st>>>(bt, dst); break;
     }
 }
 
-void launch_import_models(const PairView& pv, const LevelGeom* geoms, int nlev, int m, cudaStream_t st) {
-    k_import_models<<<dim3((m + 255) / 256, 2), 256, 0, st>>>(pv, const_cast<LevelGeom*>(geoms), nlev, m);
+void launch_import_models(const Batch& bt, int nlev, int m, cudaStream_t st) {
+    k_import_models<<<dim3((m + 255) / 256, 2), 256, 0, st>>>(bt, nlev, m);
 }
 
 void launch_labels_export(const Labels& l, int n, int* om, float* oL, double* of, cudaStream_t st) {

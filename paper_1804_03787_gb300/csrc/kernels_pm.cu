@@ -33,12 +33,24 @@ __device__ __forceinline__ int v_bin(float v) {
     return (int)fminf(x, 255.f);
 }
 
-// V histogram of each frame (blockIdx.y = frame); hist holds 2 x 256 zeroed counts.
-__global__ void k_vhist(const float* f1, const float* f2, int W, int H, int64_t stride, int* hist) {
+// Clears the V histograms of the jobs that equalise (blockIdx.z = job).
+__global__ void k_vhist_zero(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    if (j.hist)
+        for (int k = threadIdx.x; k < 2 * 256; k += blockDim.x) j.hist[k] = 0;
+}
+
+// V histogram of each frame (blockIdx.y = frame, blockIdx.z = job); hist holds 2 x 256 zeroed counts.
+__global__ void k_vhist(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    if (!j.hist) return;  // block-uniform
+    const int W = j.W, H = j.H;
+    const int64_t stride = j.stride;
+    int* hist = j.hist;
     __shared__ int h[256];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    const float* f = blockIdx.y ? f2 : f1;
+    const float* f = blockIdx.y ? j.f2 : j.f1;
     const int n = W * H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
@@ -50,8 +62,13 @@ __global__ void k_vhist(const float* f1, const float* f2, int W, int H, int64_t 
         if (h[k]) atomicAdd(&hist[blockIdx.y * 256 + k], h[k]);
 }
 
-// Equalised V per bin (blockIdx.x = frame, 256 threads): an inclusive scan of the counts.
-__global__ void k_vlut(const int* hist, int n, float* lut) {
+// Equalised V per bin (blockIdx.x = frame, blockIdx.z = job, 256 threads): an inclusive scan of the counts.
+__global__ void k_vlut(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    if (!j.hist) return;  // block-uniform
+    const int* hist = j.hist;
+    const int n = j.W * j.H;
+    float* lut = j.lut;
     __shared__ int c[256];
     __shared__ int cmin;
     const int t = threadIdx.x;
@@ -93,11 +110,13 @@ __device__ __forceinline__ float3 equalize_px(float r, float g, float b, const f
 // non-negative double increase with it, negative ones are mirrored; + 0.0
 // turns -0 into +0.  The 24 comparisons per pixel then run on the integer
 // pipe with exactly the outcomes of comparing the doubles.
-__global__ void k_grey_keys(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1,
-                            long long* k2) {
-    const int n = W * H;
-    const float* f = blockIdx.y ? f2 : f1;
-    long long* k = blockIdx.y ? k2 : k1;
+__global__ void k_grey_keys(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    if (!j.k1) return;  // block-uniform
+    const int W = j.W, n = j.W * j.H;
+    const int64_t stride = j.stride;
+    const float* f = blockIdx.y ? j.f2 : j.f1;
+    long long* k = blockIdx.y ? j.k2 : j.k1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
         const float* p = f + (int64_t)y * stride + 3 * x;
@@ -109,10 +128,12 @@ __global__ void k_grey_keys(const float* f1, const float* f2, int W, int H, int6
 
 // 5x5 census code per pixel: bit k (raster order without the centre, neighbours clamped into the frame) set iff
 // the neighbour's grey is below the centre's.
-__global__ void k_census(const long long* k1, const long long* k2, int W, int H, uint32_t* c1, uint32_t* c2) {
-    const int n = W * H;
-    const long long* k = blockIdx.y ? k2 : k1;
-    uint32_t* c = blockIdx.y ? c2 : c1;
+__global__ void k_census(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    if (!j.k1) return;  // block-uniform
+    const int W = j.W, H = j.H, n = j.W * j.H;
+    const long long* k = blockIdx.y ? j.k2 : j.k1;
+    uint32_t* c = blockIdx.y ? j.c2 : j.c1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
         const long long kc = k[i];
@@ -131,16 +152,16 @@ __global__ void k_census(const long long* k1, const long long* k2, int W, int H,
     }
 }
 
-void launch_census(const float* f1, const float* f2, int W, int H, int64_t stride, long long* k1, long long* k2,
-                   uint32_t* c1, uint32_t* c2, cudaStream_t st) {
-    const dim3 grid(152 * 4, 2);
-    k_grey_keys<<<grid, 256, 0, st>>>(f1, f2, W, H, stride, k1, k2);
-    k_census<<<grid, 256, 0, st>>>(k1, k2, W, H, c1, c2);
-}
-
-// Deterministic FP64 sums of both frames (after equalisation when lut is set): fixed grid, fixed tree.
-__global__ void k_frame_sums(const float* f1, const float* f2, int W, int H, int64_t stride, const float* lut,
-                             double* partial) {
+// Deterministic FP64 sums of both frames (after equalisation when lut is set): fixed grid, fixed tree
+// (blockIdx.z = job).
+__global__ void k_frame_sums(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    const float* f1 = j.f1;
+    const float* f2 = j.f2;
+    const int W = j.W, H = j.H;
+    const int64_t stride = j.stride;
+    const float* lut = j.hist ? j.lut : nullptr;
+    double* partial = j.partial;
     __shared__ double sh[2][256];
     double a = 0, b = 0;
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
@@ -176,7 +197,10 @@ __global__ void k_frame_sums(const float* f1, const float* f2, int W, int H, int
     }
 }
 
-__global__ void k_gain(const double* partial, int nblk, int enable, double* gain) {
+__global__ void k_gain(const __grid_constant__ IngestJobs J, int nblk, int enable) {
+    const IngestJob& j = J.j[blockIdx.z];
+    const double* partial = j.partial;
+    double* gain = j.gain;
     if (threadIdx.x != 0) return;
     double a = 0, b = 0;
     for (int i = 0; i < nblk; ++i) {
@@ -206,9 +230,16 @@ __device__ __forceinline__ void store_pix(void* base, int i, float r, float g, f
 }
 
 template <int ST>
-__global__ void k_pack(const float* f1, const float* f2, int W, int H, int64_t stride, const double* gain,
-                       const float* lut, void* o1, void* o2) {
-    const double g = *gain;
+__global__ void k_pack(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    const float* f1 = j.f1;
+    const float* f2 = j.f2;
+    const int W = j.W, H = j.H;
+    const int64_t stride = j.stride;
+    const float* lut = j.hist ? j.lut : nullptr;
+    void* o1 = j.o1;
+    void* o2 = j.o2;
+    const double g = *j.gain;
     const int n = W * H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
@@ -586,7 +617,8 @@ __device__ __forceinline__ void patch_sum_pair_in(const LanePatch<R>& l1, const 
 }
 
 template <int R, int ST, bool CENSUS>
-__global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint32_t k1) {
+__global__ void __launch_bounds__(256) k_pm_init(const __grid_constant__ Batch bt, uint32_t k0, uint32_t k1) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int W = pv.W, H = pv.H, n = pv.n;
@@ -644,7 +676,9 @@ __global__ void __launch_bounds__(256) k_pm_init(PairView pv, uint32_t k0, uint3
 
 // ---------------------------------------------------------------- recost (level >= 1)
 template <int R, int ST>
-__global__ void __launch_bounds__(256) k_pm_recost(PairView pv, LevelGeom g, int level) {
+__global__ void __launch_bounds__(256) k_pm_recost(const __grid_constant__ Batch bt, int level) {
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int W = pv.W, H = pv.H;
@@ -748,9 +782,11 @@ __device__ __forceinline__ void load_patch_tile(LanePatch<R>& lp, const void* ti
 // keeps the instruction cache warm) and accepts with the strict-less rule.
 // CENSUS (level 0 only): the census data term on the frames' code images.
 template <int R, int ST, bool PLANES, bool CENSUS>
-__global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, int level, int it, int phase, int nrad,
-                                                  uint32_t k0, uint32_t k1) {
+__global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Batch bt, int level, int it, int phase, uint32_t k0,
+                                                  uint32_t k1) {
     static_assert(!(PLANES && CENSUS), "the census data term is for square patches");
+    const PairView& pv = bt.view(blockIdx.z);
+    const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int W = pv.W, H = pv.H;
@@ -770,6 +806,8 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
     const int total = !PLANES ? H * hw : pv.list_count[dir * 2 + phase];
     const int* list = !PLANES ? nullptr : pv.list[dir] + phase * pv.n;
     const int R0 = max(W, H);
+    int nrad = 0;  // search radii R0 >> k >= 1
+    while ((R0 >> nrad) >= 1) ++nrad;
     const uint32_t tag = stream_tag(RNG_SEARCH, dir, level, 0);
     // Level 0: a block takes tiles of 8 x 8 pixels of this colour (16 x 8 image pixels), its eight warps one
     // row of the tile per round, so that successive rounds reuse the target region already in the SM's L1.
@@ -972,7 +1010,11 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(PairView pv, LevelGeom g, i
 
 // Unfrozen pixels of each colour, for the restricted sweeps (order is free:
 // pixels of one colour are independent within a half-iteration).
-__global__ void k_build_lists(PairView pv) {
+__global__ void k_lists_zero(const __grid_constant__ Batch bt) {
+    if (threadIdx.x < 4) bt.view(blockIdx.z).list_count[threadIdx.x] = 0;
+}
+__global__ void k_build_lists(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const int n = pv.n, W = pv.W;
     const int lane = threadIdx.x & 31;
@@ -999,27 +1041,24 @@ __global__ void k_build_lists(PairView pv) {
 // ---------------------------------------------------------------- launchers
 template <int R, int ST>
 static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
-    const dim3 grid(L.grid_blocks, 2), block(256);
+    const dim3 grid(L.grid_blocks, 2, L.np), block(256);
     switch (L.op) {
         case PmLaunch::INIT:  // census codes do not depend on the texel storage: one instance serves all
             if (L.census)
-                k_pm_init<R, 0, true><<<grid, block, 0, st>>>(*L.pv, L.k0, L.k1);
+                k_pm_init<R, 0, true><<<grid, block, 0, st>>>(L.bt, L.k0, L.k1);
             else
-                k_pm_init<R, ST, false><<<grid, block, 0, st>>>(*L.pv, L.k0, L.k1);
+                k_pm_init<R, ST, false><<<grid, block, 0, st>>>(L.bt, L.k0, L.k1);
             break;
         case PmLaunch::RECOST:
-            k_pm_recost<R, ST><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level);
+            k_pm_recost<R, ST><<<grid, block, 0, st>>>(L.bt, L.level);
             break;
         case PmLaunch::SWEEP:
             if (L.level == 0 && L.census)
-                k_pm_sweep<R, 0, false, true><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0,
-                                                                     L.k1);
+                k_pm_sweep<R, 0, false, true><<<grid, block, 0, st>>>(L.bt, 0, L.it, L.phase, L.k0, L.k1);
             else if (L.level == 0)
-                k_pm_sweep<R, ST, false, false><<<grid, block, 0, st>>>(*L.pv, L.geom, 0, L.it, L.phase, L.nrad, L.k0,
-                                                                       L.k1);
+                k_pm_sweep<R, ST, false, false><<<grid, block, 0, st>>>(L.bt, 0, L.it, L.phase, L.k0, L.k1);
             else
-                k_pm_sweep<R, ST, true, false><<<grid, block, 0, st>>>(*L.pv, L.geom, L.level, L.it, L.phase, L.nrad,
-                                                                      L.k0, L.k1);
+                k_pm_sweep<R, ST, true, false><<<grid, block, 0, st>>>(L.bt, L.level, L.it, L.phase, L.k0, L.k1);
             break;
     }
 }
@@ -1043,41 +1082,66 @@ void launch_pm(const PmLaunch& L, cudaStream_t st) {
     }
 }
 
-void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
-                   double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
-                   cudaStream_t st) {
-    const int blocks = 152 * 4;
-    const float* lut = nullptr;
-    if (eq_hist && eq_lut) {
-        cudaMemsetAsync(eq_hist, 0, 2 * 256 * sizeof(int), st);
-        k_vhist<<<dim3(blocks, 2), 256, 0, st>>>(f1, f2, W, H, stride, eq_hist);
-        k_vlut<<<2, 256, 0, st>>>(eq_hist, W * H, eq_lut);
-        lut = eq_lut;
-    }
-    k_frame_sums<<<nblk, 256, 0, st>>>(f1, f2, W, H, stride, lut, partial);
-    k_gain<<<1, 32, 0, st>>>(partial, nblk, gain_enable, gain);
-    switch (storage) {
-        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, lut, o1, o2); break;
-        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, lut, o1, o2); break;
-        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, lut, o1, o2); break;
+// Greys of frame 1 as given, for the edge-aware fill (the jobs that ask for them).
+__global__ void k_grey_q(const __grid_constant__ IngestJobs J) {
+    const IngestJob& j = J.j[blockIdx.z];
+    if (!j.gq) return;
+    const int W = j.W, n = j.W * j.H;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int y = i / W, x = i - y * W;
+        const float* p = j.f1 + (int64_t)y * j.stride + 3 * x;
+        j.gq[i] = (int)floor(1024.0 * (((double)p[0] + (double)p[1]) + (double)p[2]));
     }
 }
 
-void launch_pack(const float* f1, const float* f2, int W, int H, int64_t stride, int storage, const double* gain,
-                 void* o1, void* o2, cudaStream_t st) {
+// The ingest of nj pairs, each kernel one launch over the jobs (blockIdx.z).  Per job the grid and the order
+// of every reduction are those of a single pair's ingest, so each result is the same alone and in a batch.
+void launch_ingest_jobs(const IngestJobs& J, int nj, int max_n, int max_h, int gain_enable, int storage,
+                        cudaStream_t st) {
+    (void)max_n;
+    (void)max_h;
     const int blocks = 152 * 4;
-    switch (storage) {
-        case 0: k_pack<0><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
-        case 1: k_pack<1><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
-        case 2: k_pack<2><<<blocks, 256, 0, st>>>(f1, f2, W, H, stride, gain, nullptr, o1, o2); break;
+    bool eq = false, census = false, grey = false;
+    for (int k = 0; k < nj; ++k) {
+        eq |= J.j[k].hist != nullptr;
+        census |= J.j[k].k1 != nullptr;
+        grey |= J.j[k].gq != nullptr;
     }
+    if (census) {
+        k_grey_keys<<<dim3(blocks, 2, nj), 256, 0, st>>>(J);
+        k_census<<<dim3(blocks, 2, nj), 256, 0, st>>>(J);
+    }
+    if (grey) k_grey_q<<<dim3(blocks, 1, nj), 256, 0, st>>>(J);
+    if (eq) {
+        k_vhist_zero<<<dim3(1, 1, nj), 256, 0, st>>>(J);
+        k_vhist<<<dim3(blocks, 2, nj), 256, 0, st>>>(J);
+        k_vlut<<<dim3(2, 1, nj), 256, 0, st>>>(J);
+    }
+    k_frame_sums<<<dim3(kIngestPartialBlocks, 1, nj), 256, 0, st>>>(J);
+    k_gain<<<dim3(1, 1, nj), 32, 0, st>>>(J, kIngestPartialBlocks, gain_enable);
+    switch (storage) {
+        case 0: k_pack<0><<<dim3(blocks, 1, nj), 256, 0, st>>>(J); break;
+        case 1: k_pack<1><<<dim3(blocks, 1, nj), 256, 0, st>>>(J); break;
+        case 2: k_pack<2><<<dim3(blocks, 1, nj), 256, 0, st>>>(J); break;
+    }
+}
+
+void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t stride, int gain_enable, int storage,
+                   double* partial, int nblk, double* gain, void* o1, void* o2, int* eq_hist, float* eq_lut,
+                   cudaStream_t st) {
+    (void)nblk;  // always kIngestPartialBlocks
+    IngestJobs J{};
+    J.j[0] = IngestJob{f1, f2, W, H, stride, partial, gain, o1, o2, eq_lut ? eq_hist : nullptr, eq_lut,
+                       nullptr, nullptr, nullptr, nullptr, nullptr};
+    launch_ingest_jobs(J, 1, W * H, H, gain_enable, storage, st);
 }
 
 // Padded copy of each ingested frame: texel (x, y) of the copy, for x in
 // [-kPad, W + kPad) and y in [-kPad, H + kPad), is the frame's texel at the
 // clamped coordinates (T: one texel, 16 or 8 bytes).
 template <typename T>
-__global__ void k_pad_frames(PairView pv) {
+__global__ void k_pad_frames(const __grid_constant__ Batch bt) {
+    const PairView& pv = bt.view(blockIdx.z);
     const int dir = blockIdx.y;
     const T* src = reinterpret_cast<const T*>(pv.img[dir]);
     T* dst = reinterpret_cast<T*>(const_cast<void*>(pv.imgp[dir]));
@@ -1095,13 +1159,15 @@ __global__ void k_pad_frames(PairView pv) {
 // 32 x 8 tile and its r-halo, sums each row's 2r + 1 texels, then each column's 2r + 1 row sums, in a fixed order
 // (at most 16 FP32 roundings per sum, which the sweep's test allows for).
 template <int R, int ST>
-__global__ void __launch_bounds__(256) k_box_sums(PairView pv) {
+__global__ void __launch_bounds__(256) k_box_sums(const __grid_constant__ Batch bt) {
     constexpr int BX = 32, BY = 8, TWB = BX + 2 * R, THB = BY + 2 * R;
     __shared__ float3 tex[THB][TWB];
     __shared__ float3 hs[THB][BX];
-    const int dir = blockIdx.z;
+    const PairView& pv = bt.view(blockIdx.z >> 1);  // blockIdx.z = 2 pair + direction
+    const int dir = blockIdx.z & 1;
     const int W = pv.W, H = pv.H, Wp = pv.Wp, Hp = H + 2 * kPad;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    if (x0 >= W || y0 >= H) return;  // past this pair's frame (block-uniform)
     for (int e = threadIdx.x; e < THB * TWB; e += blockDim.x) {
         const int ly = e / TWB, lx = e - ly * TWB;
         const int gx = min(x0 - R + lx + kPad, Wp - 1), gy = min(y0 - R + ly + kPad, Hp - 1);
@@ -1137,33 +1203,33 @@ __global__ void __launch_bounds__(256) k_box_sums(PairView pv) {
     }
 }
 template <int ST>
-static void launch_box_st(const PairView& pv, int radius, dim3, cudaStream_t st) {
-    const dim3 grid((pv.W + 31) / 32, (pv.H + 7) / 8, 2);
+static void launch_box_st(const Batch& bt, dim3 grid, int radius, cudaStream_t st) {
     switch (radius) {
-        case 1: k_box_sums<1, ST><<<grid, 256, 0, st>>>(pv); break;
-        case 2: k_box_sums<2, ST><<<grid, 256, 0, st>>>(pv); break;
-        case 3: k_box_sums<3, ST><<<grid, 256, 0, st>>>(pv); break;
-        case 4: k_box_sums<4, ST><<<grid, 256, 0, st>>>(pv); break;
+        case 1: k_box_sums<1, ST><<<grid, 256, 0, st>>>(bt); break;
+        case 2: k_box_sums<2, ST><<<grid, 256, 0, st>>>(bt); break;
+        case 3: k_box_sums<3, ST><<<grid, 256, 0, st>>>(bt); break;
+        case 4: k_box_sums<4, ST><<<grid, 256, 0, st>>>(bt); break;
     }
 }
-void launch_box_sums(const PairView& pv, int radius, int storage, int grid_blocks, cudaStream_t st) {
-    const dim3 grid(grid_blocks, 2);
+void launch_box_sums(const Batch& bt, int np, int max_w, int max_h, int radius, int storage, cudaStream_t st) {
+    const dim3 grid((max_w + 31) / 32, (max_h + 7) / 8, 2 * np);
     switch (storage) {
-        case 0: launch_box_st<0>(pv, radius, grid, st); break;
-        case 1: launch_box_st<1>(pv, radius, grid, st); break;
-        case 2: launch_box_st<2>(pv, radius, grid, st); break;
+        case 0: launch_box_st<0>(bt, grid, radius, st); break;
+        case 1: launch_box_st<1>(bt, grid, radius, st); break;
+        case 2: launch_box_st<2>(bt, grid, radius, st); break;
     }
 }
 
-void launch_pad_frames(const PairView& pv, int storage, int grid_blocks, cudaStream_t st) {
+void launch_pad_frames(const Batch& bt, int np, int storage, int grid_blocks, cudaStream_t st) {
     if (storage == 0)
-        k_pad_frames<uint4><<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+        k_pad_frames<uint4><<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt);
     else
-        k_pad_frames<uint2><<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+        k_pad_frames<uint2><<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt);
 }
 
-void launch_build_lists(const PairView& pv, int grid_blocks, cudaStream_t st) {
-    k_build_lists<<<dim3(grid_blocks, 2), 256, 0, st>>>(pv);
+void launch_build_lists(const Batch& bt, int np, int grid_blocks, cudaStream_t st) {
+    k_lists_zero<<<dim3(1, 1, np), 32, 0, st>>>(bt);
+    k_build_lists<<<dim3(grid_blocks, 2, np), 256, 0, st>>>(bt);
 }
 
 // Exported patch costs: the raw sums divided by 3T (the same division, so the same bits, as a mean taken
@@ -1176,16 +1242,6 @@ void launch_cost_export(const float* src, float* dst, int n, int radius, int cen
     k_cost_export<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n, (float)((census ? 24 : 3) * d * d));
 }
 
-struct GeomPack {
-    LevelGeom g[GPM_MAX_SCALES];
-};
-__global__ void k_set_geoms(GeomPack p, LevelGeom* dst) {
-    if (threadIdx.x < GPM_MAX_SCALES) dst[threadIdx.x] = p.g[threadIdx.x];
-}
-void launch_set_geoms(const LevelGeom* host_geoms, LevelGeom* dst, cudaStream_t st) {
-    GeomPack p;
-    for (int l = 0; l < GPM_MAX_SCALES; ++l) p.g[l] = host_geoms[l];
-    k_set_geoms<<<1, 32, 0, st>>>(p, dst);
-}
+
 
 }  // namespace gpm

@@ -45,7 +45,8 @@ class Params(C.Structure):
                 ("storage", C.c_int32), ("equalize", C.c_int32), ("eps", C.c_float), ("ransac_px", C.c_float),
                 ("fb_px", C.c_float), ("eta", C.c_float), ("kappa", C.c_float), ("beta", C.c_float),
                 ("occ_thresh", C.c_float), ("scale_min", C.c_float), ("scale_max", C.c_float),
-                ("census", C.c_int32), ("seed", C.c_uint64), ("interp", C.c_int32)]
+                ("census", C.c_int32), ("seed", C.c_uint64), ("interp", C.c_int32),
+                ("sweep_blocks_per_sm", C.c_int32)]
 
 
 class Limits(C.Structure):

@@ -37,9 +37,10 @@ def test_binding_lists_the_same_symbols():
 def test_struct_layouts_match_header(lib):
     """Sizes of the ctypes mirrors agree with the C structs (x86-64 and aarch64 LP64)."""
     from paper_1804_03787_gb300 import gpm
-    # 18 ints, 9 floats, census, the 8-byte seed, interp and tail padding to the seed's alignment
+    # 18 ints, 9 floats, census, the 8-byte seed, interp and the sweep launch shape (no tail padding)
     assert ctypes.sizeof(gpm.Params) == 4 * (2 + 8 + 8) + 4 * 9 + 4 + 8 + 4 + 4
     assert gpm.Params.seed.offset == 112 and gpm.Params.interp.offset == 120
+    assert gpm.Params.sweep_blocks_per_sm.offset == 124
     assert ctypes.sizeof(gpm.Limits) == 24
     assert ctypes.sizeof(gpm.Pair) == 40
 
@@ -163,7 +164,7 @@ def test_create_with_failing_allocator_is_enomem_and_frees_what_it_took(lib):
 
 def test_create_without_a_device_is_ecuda():
     """GPM_ECUDA: on a host without a CUDA device a context cannot be made, even when the allocator callback
-    succeeds (its blocks are handed back)."""
+    succeeds (its blocks, one per pair, are handed back)."""
     import torch
     if torch.cuda.is_available():
         pytest.skip("a CUDA device is present")
