@@ -328,13 +328,15 @@ def poisson_trace(rate_hz: float, duration_s: float, pool: list, seed: int = 0, 
 
 
 def serving_specs(n: int, seed: int = 0) -> list[dict]:
-    """Scene recipes of the serving workload: log-uniform sizes 320x240 to 1920x1080, 4-10 layers, motion up
-    to 128 px.  Each is a keyword dict for scene.make_scene."""
+    """Scene recipes of the serving workload: log-uniform sizes 320x240 to 1920x1080, 4-7 layers, motion up to
+    width / 13 px (25 px at 320, 128 px at 1664 and above), so that the occluded fraction stays near the
+    benchmark scenes' (about 10 %, 4-14 % over the 32-scene pool of seed 0).  Each is a keyword dict for
+    scene.make_scene."""
     rng = np.random.default_rng(seed + 7)
     out = []
     for k, (w, h) in enumerate(log_uniform_sizes(n, seed=seed)):
-        out.append(dict(width=w, height=h, seed=3000 + seed * 100 + k, n_layers=int(rng.integers(4, 11)),
-                        max_disp=128.0, affine=False, area_frac=(0.02, 0.08)))
+        out.append(dict(width=w, height=h, seed=3000 + seed * 100 + k, n_layers=int(rng.integers(4, 8)),
+                        max_disp=float(min(128.0, w / 13.0)), affine=False, area_frac=(0.02, 0.08)))
     return out
 
 

@@ -35,7 +35,16 @@ def test_roofline_block_takes_the_top_class_and_divides_by_its_launch_time():
     assert hv["algorithmic_bytes_per_launch"] == 1024 * 436 * 48
     assert hv["achieved_gbs"] == pytest.approx(1024 * 436 * 48 / (100 / 160 * 1e-3) / 1e9)
     assert hv["frac"] == pytest.approx(hv["achieved_gbs"] / 6783.0)
-    assert blk["traffic"] is None                                                   # the kernel changed since
+    assert blk["traffic"] == bench.TRAFFIC_PER_LAUNCH["pm_sweep"][0]                # ncu capture of this kernel
+    assert blk["traffic_source"].startswith("profiles/") and blk["issue_view"]["issue_slots_busy"] > 0
+
+
+def test_roofline_block_takes_a_single_kernel_over_the_ransac_class():
+    """The RANSAC class holds three kernels (fit, refit solve, finish): with the largest class share it still
+    yields to the largest single-kernel class."""
+    prof = {"pm_sweep": (100.0, 160), "ransac": (140.0, 240), "pm_sweep_plane": (90.0, 640)}
+    blk = bench.roofline_block(prof, _counts(sweep0=1e9, taps0=5e10), 152, {"sm_mhz": 2000.0}, {}, steps=10)
+    assert blk["kernel"] == "pm_sweep" and blk["share"] == pytest.approx(100 / 330)
 
 
 def test_roofline_block_prefers_the_timed_region_and_the_measured_peak():
