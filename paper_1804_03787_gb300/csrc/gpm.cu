@@ -330,6 +330,7 @@ void pm_sweeps(gpm_ctx* c, const Dims& D, int level) {
     L.storage = c->P.storage;
     L.level = level;
     L.grid_blocks = pm_grid(c);
+    L.tiles0 = sweep0_tiles(D.max_w, D.max_h);
     L.k0 = (uint32_t)(c->P.seed & 0xFFFFFFFFull);
     L.k1 = (uint32_t)(c->P.seed >> 32);
     L.census = level == 0 ? c->P.census : 0;

@@ -15,10 +15,13 @@ struct PmLaunch {
     Batch bt;
     int np;
     int radius, storage, level, it, phase, grid_blocks;
+    int tiles0;  // level-0 sweep: its tiles for the largest pair (sweep0_tiles)
     int census;  // level 0: census data term (codes in pv.code)
     uint32_t k0, k1;
 };
 void launch_pm(const PmLaunch& L, cudaStream_t st);
+// Tiles (blocks per direction and pair) of the level-0 sweep of a W x H frame.
+int sweep0_tiles(int W, int H);
 // Blocks of the FP64 frame sums behind the gain (a fixed grid, so a fixed summation order): partial holds
 // 2 * kIngestPartialBlocks doubles.
 constexpr int kIngestPartialBlocks = 128;

@@ -737,17 +737,6 @@ __device__ __forceinline__ float box_threshold(float bc) {
     return fmaf(bc, 1.52587890625e-05f, bc) + 3.814697265625e-06f;
 }
 
-// Level-0 tiles of the sweep: 8 x 8 pixels of one colour, 16 x 8 image pixels; the staged source region is the
-// tile grown by r, in rows of TW texels (TW congruent to 2r + 1 modulo 8, so that eight consecutive taps of a
-// patch fall on eight distinct 16-byte bank groups).
-template <int R>
-struct Tile0 {
-    static constexpr int TX = 16, TY = 8;
-    static constexpr int TW0 = TX + 2 * R;
-    static constexpr int TW = TW0 + ((2 * R + 1 - TW0) % 8 + 8) % 8;
-    static constexpr int TH = TY + 2 * R;
-};
-
 // load_patch for a square colour patch whose source texels are staged in shared memory (tile origin (x0, y0) in
 // image coordinates, row length TW): the same taps, target indices into the padded copy (row length Wp).
 template <int R, int ST, int TW>
@@ -771,7 +760,8 @@ __device__ __forceinline__ void load_patch_tile(LanePatch<R>& lp, const void* ti
 
 // ---------------------------------------------------------------- sweep
 // PLANES: levels >= 1 (restricted pixel list, plane-distorted patches, plane
-// candidates); level 0 is compiled without any of that.
+// candidates); otherwise level 0 with the census data term (level 0 with
+// colour patches runs k_pm_sweep0).
 //
 // Candidates come in two lists, one candidate per lane, in the fixed order:
 // (A) propagation from the left, right, upper and lower neighbours (lanes
@@ -785,6 +775,7 @@ template <int R, int ST, bool PLANES, bool CENSUS>
 __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Batch bt, int level, int it, int phase, uint32_t k0,
                                                   uint32_t k1) {
     static_assert(!(PLANES && CENSUS), "the census data term is for square patches");
+    static_assert(PLANES || CENSUS, "level 0 with colour patches runs k_pm_sweep0");
     const PairView& pv = bt.view(blockIdx.z);
     const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
@@ -792,14 +783,6 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
     const int W = pv.W, H = pv.H;
     const void* src = CENSUS ? (const void*)pv.code[dir] : pv.img[dir];
     const void* tgt = CENSUS ? (const void*)pv.code[1 - dir] : pv.img[1 - dir];
-    // square colour patches read the target from its padded copy: no clamping and no interior test per candidate
-    constexpr bool PADDED = !PLANES && !CENSUS;
-    const void* tgtp = PADDED ? pv.imgp[1 - dir] : tgt;
-    const int Wt = PADDED ? pv.Wp : pv.W;
-    // square colour patches: each tile's source texels and their r-halo are staged in shared memory
-    using TL = Tile0<R>;
-    using Tex = typename TexelOf<ST>::type;
-    __shared__ Tex stile[PADDED ? TL::TH * TL::TW : 1];
     int2* __restrict__ nnf = pv.nnf[dir];
     const int nw = gridDim.x * (blockDim.x >> 5);
     const int hw = (W + 1) >> 1;
@@ -814,29 +797,12 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
     // Plane levels: the compacted pixel list, grid-strided.
     const int wid = threadIdx.x >> 5;
     const int ntx = (hw + 7) >> 3, ntiles = ntx * ((H + 7) >> 3);
-    unsigned npr = 0;  // candidates dropped by the patch-sum bound (counted by lane 0)
-    int x0t = 0, y0t = 0;
     for (int rnd = 0;; ++rnd) {
         int x, y, i;
         if (!PLANES) {
             const int tile = blockIdx.x + (rnd >> 3) * gridDim.x;
             if (tile >= ntiles) break;  // block-uniform
             const int ty = tile / ntx, tx = tile - ty * ntx;
-            if (PADDED && (rnd & 7) == 0) {
-                // stage the tile's source region (padded-copy coordinates; entries past the padded edge are
-                // clamped and unused)
-                x0t = 16 * tx;
-                y0t = 8 * ty;
-                __syncthreads();
-                const Tex* sp = reinterpret_cast<const Tex*>(pv.imgp[dir]);
-                const int Wp = pv.Wp, Hp = H + 2 * kPad;
-                for (int e = threadIdx.x; e < TL::TH * TL::TW; e += blockDim.x) {
-                    const int ly = e / TL::TW, lx = e - ly * TL::TW;
-                    const int gx = min(x0t - R + lx + kPad, Wp - 1), gy = min(y0t - R + ly + kPad, Hp - 1);
-                    stile[e] = sp[gy * Wp + gx];
-                }
-                __syncthreads();
-            }
             y = 8 * ty + (rnd & 7);
             const int xh = 8 * tx + wid;
             if (y >= H || xh >= hw) continue;
@@ -851,10 +817,7 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
             x = i - y * W;
         }
         LanePatch<R> lp;
-        if (PADDED)
-            load_patch_tile<R, ST, TL::TW>(lp, stile, x0t, y0t, W, H, x, y, lane, Wt);
-        else
-            load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
+        load_patch<R, ST, CENSUS>(lp, src, W, H, x, y, lane);
         if (PLANES) {
             const Mef* G = home_plane(g, pv.mef[dir], x, y);
             if (G) warp_taps<R>(lp, *G, x, y, W, H, lane);
@@ -863,9 +826,6 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
         float bc = pv.cost[dir][i];  // raw sum of the incumbent
         int ithr = CENSUS ? 0 : abandon_threshold(bc);
         int nev = 0, ntap = 0;
-        // square colour patches of pixels whose patch stays inside the frame: the patch-sum bound applies
-        const bool prune = PADDED && x >= R && y >= R && x < W - R && y < H - R;  // warp-uniform
-        const float4 b1 = prune ? pv.box[dir][i] : make_float4(0.f, 0.f, 0.f, 0.f);
         // list A
         int2 cand = make_int2(0, 0);
         bool ok = false;
@@ -898,16 +858,6 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
                 }
             }
         }
-        if (prune) {
-            bool cut = false;
-            if (ok && !(cand.x == best.x && cand.y == best.y) &&
-                box_lb(b1, pv.box[1 - dir][i + cand.y * W + cand.x]) >= box_threshold(bc)) {
-                ok = false;
-                cut = true;
-            }
-            const unsigned cm = __ballot_sync(FULL, cut);
-            if (lane == 0) npr += __popc(cm);
-        }
         unsigned todo = fresh_lanes(ok, cand, best, lane);
 #pragma unroll 1
         for (int list_b = 0; list_b < 2; ++list_b) {
@@ -930,48 +880,12 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
                 const int oy = (int)bounded_u32(wy, (uint32_t)(2 * Rk + 1)) - Rk;
                 const int tx = min(max(x + v0.x + ox, 0), W - 1), ty = min(max(y + v0.y + oy, 0), H - 1);
                 cand = make_int2(tx - x, ty - y);
-                bool okb = lane < nrad;
-                if (prune) {
-                    bool cut = false;
-                    if (okb && !(cand.x == v0.x && cand.y == v0.y) &&
-                        box_lb(b1, pv.box[1 - dir][i + cand.y * W + cand.x]) >= box_threshold(bc)) {
-                        okb = false;
-                        cut = true;
-                    }
-                    const unsigned cm = __ballot_sync(FULL, cut);
-                    if (lane == 0) npr += __popc(cm);
-                }
-                todo = fresh_lanes(okb, cand, v0, lane);
+                todo = fresh_lanes(lane < nrad, cand, v0, lane);
             }
             while (todo) {
                 const int l = __ffs(todo) - 1;
                 todo &= todo - 1;
                 const int2 c = make_int2(__shfl_sync(FULL, cand.x, l), __shfl_sync(FULL, cand.y, l));
-                if constexpr (!CENSUS && !PLANES) {
-                    // a second candidate: the two share their gathers' latency (square patches only: for plane
-                    // levels the pair's registers spill, and the sweep was slower)
-                    if (todo) {
-                        const int l2 = __ffs(todo) - 1;
-                        todo &= todo - 1;
-                        const int2 c2 = make_int2(__shfl_sync(FULL, cand.x, l2), __shfl_sync(FULL, cand.y, l2));
-                        float s1 = 0.f, s2 = 0.f;
-                        bool ok1, ok2;
-                        int nt2;
-                        tap_sum2_in<R, ST, true, false>(lp, tgtp, Wt, H, c, c2, ithr, s1, s2, ok1, ok2, nt2, lane);
-                        ntap += nt2;
-                        if (ok1 && s1 < bc) {
-                            bc = s1;
-                            best = c;
-                        }
-                        if (ok2 && s2 < bc) {
-                            bc = s2;
-                            best = c2;
-                        }
-                        ithr = abandon_threshold(bc);
-                        nev += 2;
-                        continue;
-                    }
-                }
                 if constexpr (CENSUS) {
                     int sum;  // exact integer costs: the incumbent's sum is an integer held in a float
                     if (census_sum<R>(lp, reinterpret_cast<const uint32_t*>(tgt), W, H, c, (int)bc, sum, lane) &&
@@ -982,9 +896,7 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
                 } else {
                     float sum;
                     int nch;
-                    const bool done =
-                        PADDED ? tap_sum_in<R, ST, true, false>(lp, tgtp, Wt, H, c, ithr, sum, nch, lane)
-                               : tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, nch, lane);
+                    const bool done = tap_sum<R, ST, PLANES>(lp, tgt, W, H, c, ithr, sum, nch, lane);
                     ntap += min(32 * nch, Patch<R>::T);
                     if (done && sum < bc) {
                         bc = sum;
@@ -1005,7 +917,230 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
             }
         }
     }
-    if (pv.evals && lane == 0 && npr) atomicAdd(&pv.evals[GPM_COUNT_SWEEP0_PRUNED], (unsigned long long)npr);
+}
+
+// ---------------------------------------------------------------- level-0 sweep, two layouts
+// Tiles of the level-0 sweep: 16 pixels of one colour by 8 rows (32 x 8 image pixels), each of the block's four
+// warps owning two rows, one pixel per lane.  The staged source region is the tile grown by r, in rows of TW
+// texels (TW congruent to 2r + 1 modulo 8, so that eight consecutive taps of a patch row fall on eight distinct
+// 16-byte bank groups).
+template <int R>
+struct Tile0L {
+    static constexpr int TXC = 16, TY = 8, TX = 2 * TXC, WARPS = 4;
+    static constexpr int TW0 = TX + 2 * R;
+    static constexpr int TW = TW0 + ((2 * R + 1 - TW0) % 8 + 8) % 8;
+    static constexpr int TH = TY + 2 * R;
+};
+// Search radii R0 >> k >= 1 for frames below 2^15 pixels a side: at most 15.
+constexpr int kMaxRadii = 16;
+
+int sweep0_tiles(int W, int H) {
+    const int hw = (W + 1) >> 1;
+    return ((hw + Tile0L<1>::TXC - 1) / Tile0L<1>::TXC) * ((H + Tile0L<1>::TY - 1) / Tile0L<1>::TY);
+}
+
+// A candidate offset in one word (|c.x|, |c.y| < 2^15 for frames below 2^15 pixels a side).
+__device__ __forceinline__ uint32_t pack_off(int2 c) { return (uint32_t)(uint16_t)c.x | ((uint32_t)c.y << 16); }
+__device__ __forceinline__ int2 unpack_off(uint32_t k) { return make_int2((int)(int16_t)(k & 0xFFFFu), (int)k >> 16); }
+
+// Appends candidate c to a pixel's list (column `lane` of list[k][32]) unless an earlier entry holds it.
+__device__ __forceinline__ void list_push(uint32_t (*list)[32], int& n, int2 c, int lane) {
+    const uint32_t key = pack_off(c);
+    bool dup = false;
+    for (int k = 0; k < n; ++k) dup |= list[k][lane] == key;
+    if (!dup) list[n++][lane] = key;
+}
+
+// The warp (one tap per lane) evaluates the n listed candidates of one pixel in list order, two at a time, with
+// the strict-less rule of k_pm_sweep: best / bc are warp-uniform on entry and on return.
+template <int R, int ST>
+__device__ __forceinline__ void eval_listed(const LanePatch<R>& lp, const void* tgtp, int Wp, int H,
+                                            const uint32_t (*list)[32], int p, int n, int2& best, float& bc,
+                                            unsigned& nev, unsigned& ntap, int lane) {
+    int ithr = abandon_threshold(bc);
+    for (int k = 0; k < n; k += 2) {
+        const int2 c1 = unpack_off(list[k][p]);
+        if (k + 1 < n) {
+            const int2 c2 = unpack_off(list[k + 1][p]);
+            float s1 = 0.f, s2 = 0.f;
+            bool ok1, ok2;
+            int nt2;
+            tap_sum2_in<R, ST, true, false>(lp, tgtp, Wp, H, c1, c2, ithr, s1, s2, ok1, ok2, nt2, lane);
+            ntap += nt2;
+            if (ok1 && s1 < bc) {
+                bc = s1;
+                best = c1;
+            }
+            if (ok2 && s2 < bc) {
+                bc = s2;
+                best = c2;
+            }
+            ithr = abandon_threshold(bc);
+            nev += 2;
+        } else {
+            float sum;
+            int nch;
+            const bool done = tap_sum_in<R, ST, true, false>(lp, tgtp, Wp, H, c1, ithr, sum, nch, lane);
+            ntap += min(32 * nch, Patch<R>::T);
+            if (done && sum < bc) {
+                bc = sum;
+                best = c1;
+            }
+            ++nev;
+        }
+    }
+}
+
+// Level-0 sweep with square colour patches: the same candidates, order, costs and strict-less rule as
+// k_pm_sweep (Sec. 3.1.1: propagation from the four neighbours, then random search around the best offset
+// after it), so the NNF and its costs are bitwise those of k_pm_sweep.  The per-pixel scalar work runs with
+// one pixel per lane: the neighbours' offsets, the Philox words and the search candidates, the patch-sum bound
+// and the removal of repeats, into a list per pixel in shared memory.  The patch costs run with one tap per
+// lane, the warp walking its 32 pixels' lists in turn.  Lists: (A) propagation, evaluated from the incumbent;
+// (B) random search around the best offset after A, built once A is evaluated for all 32 pixels.
+template <int R, int ST>
+__global__ void __launch_bounds__(128, 8) k_pm_sweep0(const __grid_constant__ Batch bt, int it, int phase,
+                                                      uint32_t k0, uint32_t k1) {
+    using TL = Tile0L<R>;
+    using Tex = typename TexelOf<ST>::type;
+    __shared__ Tex stile[TL::TH * TL::TW];
+    __shared__ uint32_t slist[TL::WARPS][kMaxRadii][32];
+    const PairView& pv = bt.view(blockIdx.z);
+    const int dir = blockIdx.y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int W = pv.W, H = pv.H, Wp = pv.Wp;
+    const int hw = (W + 1) >> 1;
+    const int ntx = (hw + TL::TXC - 1) / TL::TXC, nty = (H + TL::TY - 1) / TL::TY;
+    if ((int)blockIdx.x >= ntx * nty) return;  // block-uniform: the grid covers the largest pair of the batch
+    const int tyi = blockIdx.x / ntx, txi = blockIdx.x - tyi * ntx;
+    const int x0 = TL::TX * txi, y0 = TL::TY * tyi;
+    {
+        // the tile's source region, from the padded copy (entries past its edge are clamped and unused)
+        const Tex* sp = reinterpret_cast<const Tex*>(pv.imgp[dir]);
+        const int Hp = H + 2 * kPad;
+        for (int e = threadIdx.x; e < TL::TH * TL::TW; e += blockDim.x) {
+            const int ly = e / TL::TW, lx = e - ly * TL::TW;
+            const int gx = min(x0 - R + lx + kPad, Wp - 1), gy = min(y0 - R + ly + kPad, Hp - 1);
+            stile[e] = sp[gy * Wp + gx];
+        }
+    }
+    __syncthreads();
+    const void* tgtp = pv.imgp[1 - dir];
+    uint32_t(*list)[32] = slist[wid];
+    int2* __restrict__ nnf = pv.nnf[dir];
+    const float4* __restrict__ boxt = pv.box[1 - dir];
+    // the lane's pixel
+    const int yq = y0 + 2 * wid + (lane >> 4);
+    const int xq = 2 * (TL::TXC * txi + (lane & 15)) + ((yq + phase) & 1);
+    const bool mine = yq < H && xq < W;
+    const int iq = mine ? yq * W + xq : 0;
+    int2 best = make_int2(0, 0);
+    float bc = 0.f;
+    if (mine) {
+        best = nnf[iq];
+        bc = pv.cost[dir][iq];
+    }
+    // interior pixels: the patch-sum bound applies
+    const bool prune = mine && xq >= R && yq >= R && xq < W - R && yq < H - R;
+    const float4 b1 = prune ? pv.box[dir][iq] : make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned npr = 0, nev = 0, ntap = 0;
+    // list A, one pixel per lane: the four neighbours' offsets whose target is in the frame, neither the
+    // incumbent nor a repeat, and not excluded by the bound
+    int n = 0;
+    if (mine) {
+        const float thr = box_threshold(bc);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int nx = xq + (k == 0 ? -1 : (k == 1 ? 1 : 0));
+            const int ny = yq + (k == 2 ? -1 : (k == 3 ? 1 : 0));
+            if (nx < 0 || nx >= W || ny < 0 || ny >= H) continue;
+            const int2 c = nnf[ny * W + nx];
+            const int tx = xq + c.x, ty = yq + c.y;
+            if (tx < 0 || tx >= W || ty < 0 || ty >= H || (c.x == best.x && c.y == best.y)) continue;
+            if (prune && box_lb(b1, boxt[iq + c.y * W + c.x]) >= thr) {
+                ++npr;
+                continue;
+            }
+            list_push(list, n, c, lane);
+        }
+    }
+    __syncwarp();
+    // list A, one tap per lane, pixel by pixel
+    for (int p = 0; p < 32; ++p) {
+        const int np_ = __shfl_sync(FULL, n, p);
+        if (np_ == 0) continue;  // warp-uniform
+        const int yp = y0 + 2 * wid + (p >> 4);
+        const int xp = 2 * (TL::TXC * txi + (p & 15)) + ((yp + phase) & 1);
+        LanePatch<R> lp;
+        load_patch_tile<R, ST, TL::TW>(lp, stile, x0, y0, W, H, xp, yp, lane, Wp);
+        int2 b = make_int2(__shfl_sync(FULL, best.x, p), __shfl_sync(FULL, best.y, p));
+        float c = __shfl_sync(FULL, bc, p);
+        eval_listed<R, ST>(lp, tgtp, Wp, H, list, p, np_, b, c, nev, ntap, lane);
+        if (lane == p) {
+            best = b;
+            bc = c;
+        }
+    }
+    __syncwarp();
+    // list B, one pixel per lane: random search around v0, the best offset after list A (Philox words two radii
+    // per call, as in k_pm_sweep)
+    n = 0;
+    if (mine) {
+        const int2 v0 = best;
+        const int R0 = max(W, H);
+        int nrad = 0;
+        while ((R0 >> nrad) >= 1) ++nrad;
+        const uint32_t tag = stream_tag(RNG_SEARCH, dir, 0, 0);
+        const float thr = box_threshold(bc);
+        for (int call = 0; 2 * call < nrad; ++call) {
+            const uint4 rw = philox((uint32_t)iq, ((uint32_t)it << 8) | (uint32_t)call, tag, pv.pair_id, k0, k1);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 2 * call + h;
+                if (k >= nrad) break;
+                const uint32_t wx = h ? rw.z : rw.x, wy = h ? rw.w : rw.y;
+                const int Rk = R0 >> k;
+                const int ox = (int)bounded_u32(wx, (uint32_t)(2 * Rk + 1)) - Rk;
+                const int oy = (int)bounded_u32(wy, (uint32_t)(2 * Rk + 1)) - Rk;
+                const int tx = min(max(xq + v0.x + ox, 0), W - 1), ty = min(max(yq + v0.y + oy, 0), H - 1);
+                const int2 c = make_int2(tx - xq, ty - yq);
+                if (c.x == v0.x && c.y == v0.y) continue;
+                if (prune && box_lb(b1, boxt[iq + c.y * W + c.x]) >= thr) {
+                    ++npr;
+                    continue;
+                }
+                list_push(list, n, c, lane);
+            }
+        }
+    }
+    __syncwarp();
+    for (int p = 0; p < 32; ++p) {
+        const int np_ = __shfl_sync(FULL, n, p);
+        if (np_ == 0) continue;
+        const int yp = y0 + 2 * wid + (p >> 4);
+        const int xp = 2 * (TL::TXC * txi + (p & 15)) + ((yp + phase) & 1);
+        LanePatch<R> lp;
+        load_patch_tile<R, ST, TL::TW>(lp, stile, x0, y0, W, H, xp, yp, lane, Wp);
+        int2 b = make_int2(__shfl_sync(FULL, best.x, p), __shfl_sync(FULL, best.y, p));
+        float c = __shfl_sync(FULL, bc, p);
+        eval_listed<R, ST>(lp, tgtp, Wp, H, list, p, np_, b, c, nev, ntap, lane);
+        if (lane == p) {
+            best = b;
+            bc = c;
+        }
+    }
+    if (mine) {
+        nnf[iq] = best;
+        pv.cost[dir][iq] = bc;
+    }
+    if (pv.evals) {
+        const unsigned npw = __reduce_add_sync(FULL, npr);
+        if (lane == 0) {
+            atomicAdd(&pv.evals[GPM_COUNT_SWEEP0], (unsigned long long)nev);
+            atomicAdd(&pv.evals[GPM_COUNT_SWEEP0_TAPS], (unsigned long long)ntap);
+            if (npw) atomicAdd(&pv.evals[GPM_COUNT_SWEEP0_PRUNED], (unsigned long long)npw);
+        }
+    }
 }
 
 // Unfrozen pixels of each colour, for the restricted sweeps (order is free:
@@ -1056,7 +1191,8 @@ static void launch_pm_r(const PmLaunch& L, cudaStream_t st) {
             if (L.level == 0 && L.census)
                 k_pm_sweep<R, 0, false, true><<<grid, block, 0, st>>>(L.bt, 0, L.it, L.phase, L.k0, L.k1);
             else if (L.level == 0)
-                k_pm_sweep<R, ST, false, false><<<grid, block, 0, st>>>(L.bt, 0, L.it, L.phase, L.k0, L.k1);
+                k_pm_sweep0<R, ST><<<dim3(L.tiles0, 2, L.np), dim3(32 * Tile0L<R>::WARPS), 0, st>>>(L.bt, L.it, L.phase,
+                                                                                                  L.k0, L.k1);
             else
                 k_pm_sweep<R, ST, true, false><<<grid, block, 0, st>>>(L.bt, L.level, L.it, L.phase, L.k0, L.k1);
             break;
