@@ -498,7 +498,7 @@ __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* t
     for (int j = 0; j < Patch<R>::NT; ++j) {
         const int t = lane + 32 * j;
         if (t < Patch<R>::T) s += absdiff3(lp.a[j], tap_sample<R, ST, IN>(lp, tgt, W, H, j, c, off));
-        if (j + 1 < Patch<R>::NT && (EVERY_CHUNK || j == 0)) {
+        if (j + 1 < Patch<R>::NT && EVERY_CHUNK) {
             // floor(min(s * 2^19, 2^23 - 1)): exact scaling, clamp (keeps a lower bound), truncation in the
             // mantissa of 2^23
             const unsigned q =
@@ -514,7 +514,8 @@ __device__ __forceinline__ bool tap_sum_in(const LanePatch<R>& lp, const void* t
     return true;
 }
 // EVERY_CHUNK: test the bound after every chunk but the last (plane levels, where a chunk costs four gathers per
-// tap); otherwise after the first chunk only (square patches, where a further test costs about what it saves).
+// tap); otherwise never (level 0, where the patch-sum bound has already removed most losing candidates and a
+// test, with its reduction and the predication it puts on every later gather, cost more than it saved).
 template <int R, int ST, bool EVERY_CHUNK>
 __device__ __forceinline__ bool tap_sum(const LanePatch<R>& lp, const void* tgt, int W, int H, int2 c, int ithr,
                                         float& sum, int& nch, int lane) {
@@ -547,7 +548,7 @@ __device__ __forceinline__ void tap_sum2_in(const LanePatch<R>& lp, const void* 
             if (ok1) s1 += absdiff3(lp.a[j], v1);
             if (ok2) s2 += absdiff3(lp.a[j], v2);
         }
-        if (j + 1 < Patch<R>::NT && (EVERY_CHUNK || j == 0)) {
+        if (j + 1 < Patch<R>::NT && EVERY_CHUNK) {
             const unsigned q1 =
                 (unsigned)(__float_as_int(__fadd_rz(fminf(s1 * 524288.f, 8388607.f), 8388608.f)) - 0x4B000000);
             const unsigned q2 =
@@ -951,43 +952,72 @@ __device__ __forceinline__ void list_push(uint32_t (*list)[32], int& n, int2 c, 
     if (!dup) list[n++][lane] = key;
 }
 
-// The warp (one tap per lane) evaluates the n listed candidates of one pixel in list order, two at a time, with
-// the strict-less rule of k_pm_sweep: best / bc are warp-uniform on entry and on return.
-template <int R, int ST>
-__device__ __forceinline__ void eval_listed(const LanePatch<R>& lp, const void* tgtp, int Wp, int H,
-                                            const uint32_t (*list)[32], int p, int n, int2& best, float& bc,
-                                            unsigned& nev, unsigned& ntap, int lane) {
-    int ithr = abandon_threshold(bc);
-    for (int k = 0; k < n; k += 2) {
-        const int2 c1 = unpack_off(list[k][p]);
-        if (k + 1 < n) {
-            const int2 c2 = unpack_off(list[k + 1][p]);
-            float s1 = 0.f, s2 = 0.f;
-            bool ok1, ok2;
-            int nt2;
-            tap_sum2_in<R, ST, true, false>(lp, tgtp, Wp, H, c1, c2, ithr, s1, s2, ok1, ok2, nt2, lane);
-            ntap += nt2;
-            if (ok1 && s1 < bc) {
-                bc = s1;
-                best = c1;
-            }
-            if (ok2 && s2 < bc) {
-                bc = s2;
-                best = c2;
-            }
-            ithr = abandon_threshold(bc);
-            nev += 2;
-        } else {
-            float sum;
-            int nch;
-            const bool done = tap_sum_in<R, ST, true, false>(lp, tgtp, Wp, H, c1, ithr, sum, nch, lane);
-            ntap += min(32 * nch, Patch<R>::T);
-            if (done && sum < bc) {
-                bc = sum;
-                best = c1;
-            }
-            ++nev;
+// Raw tap sums of N candidate offsets of one square patch (off[q] = c.y * Wp + c.x into the padded target copy),
+// all in full: each lane accumulates its taps in the order of tap_sum_in and the totals are warp_sum_q23's, so
+// each sum is bitwise tap_sum_in's; the N candidates' gathers of a chunk are in flight together.
+template <int R, int ST, int N>
+__device__ __forceinline__ void tap_sums_sq(const LanePatch<R>& lp, const void* tgtp, const int* off, float* sum,
+                                            int lane) {
+    float s[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) s[q] = 0.f;
+#pragma unroll
+    for (int j = 0; j < Patch<R>::NT; ++j) {
+        if (lane + 32 * j < Patch<R>::T) {
+            float4 v[N];
+#pragma unroll
+            for (int q = 0; q < N; ++q) v[q] = ldpix<ST>(tgtp, lp.tidx[j] + off[q]);
+#pragma unroll
+            for (int q = 0; q < N; ++q) s[q] += absdiff3(lp.a[j], make_float3(v[q].x, v[q].y, v[q].z));
         }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) sum[q] = warp_sum_q23(s[q]);
+}
+
+// Maximum number of one pixel's candidates whose costs are summed together.
+constexpr int kSweep0Group = 3;
+
+template <int R, int ST, int N>
+__device__ __forceinline__ void eval_group(const LanePatch<R>& lp, const void* tgtp, int Wp,
+                                           const uint32_t (*list)[32], int p, int k, int2& best, float& bc) {
+    int2 c[N];
+    int off[N];
+    float sum[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        c[q] = unpack_off(list[k + q][p]);
+        off[q] = c[q].y * Wp + c[q].x;
+    }
+    tap_sums_sq<R, ST, N>(lp, tgtp, off, sum, (int)(threadIdx.x & 31));
+#pragma unroll
+    for (int q = 0; q < N; ++q)
+        if (sum[q] < bc) {
+            bc = sum[q];
+            best = c[q];
+        }
+}
+
+// The warp (one tap per lane) evaluates the n listed candidates of one pixel in list order, up to kSweep0Group
+// at a time, with the strict-less rule of k_pm_sweep (every cost summed in full, then the updates in list
+// order): best / bc are warp-uniform on entry and on return.
+template <int R, int ST>
+__device__ __forceinline__ void eval_listed(const LanePatch<R>& lp, const void* tgtp, int Wp,
+                                            const uint32_t (*list)[32], int p, int n, int2& best, float& bc,
+                                            unsigned& nev, unsigned& ntap) {
+    for (int k = 0; k < n;) {
+        const int g = min(n - k, kSweep0Group);
+        if (g >= 4)
+            eval_group<R, ST, 4>(lp, tgtp, Wp, list, p, k, best, bc);
+        else if (g == 3)
+            eval_group<R, ST, 3>(lp, tgtp, Wp, list, p, k, best, bc);
+        else if (g == 2)
+            eval_group<R, ST, 2>(lp, tgtp, Wp, list, p, k, best, bc);
+        else
+            eval_group<R, ST, 1>(lp, tgtp, Wp, list, p, k, best, bc);
+        k += g;
+        nev += g;
+        ntap += g * Patch<R>::T;
     }
 }
 
@@ -999,7 +1029,7 @@ __device__ __forceinline__ void eval_listed(const LanePatch<R>& lp, const void* 
 // lane, the warp walking its 32 pixels' lists in turn.  Lists: (A) propagation, evaluated from the incumbent;
 // (B) random search around the best offset after A, built once A is evaluated for all 32 pixels.
 template <int R, int ST>
-__global__ void __launch_bounds__(128, 8) k_pm_sweep0(const __grid_constant__ Batch bt, int it, int phase,
+__global__ void __launch_bounds__(128, 6) k_pm_sweep0(const __grid_constant__ Batch bt, int it, int phase,
                                                       uint32_t k0, uint32_t k1) {
     using TL = Tile0L<R>;
     using Tex = typename TexelOf<ST>::type;
@@ -1075,7 +1105,7 @@ __global__ void __launch_bounds__(128, 8) k_pm_sweep0(const __grid_constant__ Ba
         load_patch_tile<R, ST, TL::TW>(lp, stile, x0, y0, W, H, xp, yp, lane, Wp);
         int2 b = make_int2(__shfl_sync(FULL, best.x, p), __shfl_sync(FULL, best.y, p));
         float c = __shfl_sync(FULL, bc, p);
-        eval_listed<R, ST>(lp, tgtp, Wp, H, list, p, np_, b, c, nev, ntap, lane);
+        eval_listed<R, ST>(lp, tgtp, Wp, list, p, np_, b, c, nev, ntap);
         if (lane == p) {
             best = b;
             bc = c;
@@ -1123,7 +1153,7 @@ __global__ void __launch_bounds__(128, 8) k_pm_sweep0(const __grid_constant__ Ba
         load_patch_tile<R, ST, TL::TW>(lp, stile, x0, y0, W, H, xp, yp, lane, Wp);
         int2 b = make_int2(__shfl_sync(FULL, best.x, p), __shfl_sync(FULL, best.y, p));
         float c = __shfl_sync(FULL, bc, p);
-        eval_listed<R, ST>(lp, tgtp, Wp, H, list, p, np_, b, c, nev, ntap, lane);
+        eval_listed<R, ST>(lp, tgtp, Wp, list, p, np_, b, c, nev, ntap);
         if (lane == p) {
             best = b;
             bc = c;
