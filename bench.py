@@ -303,13 +303,13 @@ def measure_fp32_peak(nsm: int, gpu_id: str, launches: int = 24):
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the kernel class, from the
 # captures summarised in profiles/ (null where the kernel changed since, or no capture matches the class).
 TRAFFIC_PER_LAUNCH = {
-    "pm_sweep": (39686400 + 146176, "profiles/pm_sweep_level0_1024x436.md"),
+    "pm_sweep": (39698432 + 256, "profiles/pm_sweep0_level0_1024x436.md"),
     "pm_sweep_plane": (17857536 + 1024, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Issue-slot utilisation of the kernel (ncu smsp__issue_active, one launch of the same workload): the sweeps are
 # bound by gather latency and issue, which the ALU fraction alone does not show.
 ISSUE_PER_LAUNCH = {
-    "pm_sweep": (0.5202, "profiles/pm_sweep_level0_1024x436.md"),
+    "pm_sweep": (0.5727, "profiles/pm_sweep0_level0_1024x436.md"),
     "pm_sweep_plane": (0.5999, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
@@ -912,6 +912,8 @@ def run_ours(args):
             "evals_per_step_by_kind": {"level0_sweep": evals[gpm.COUNT_SWEEP0] / args.steps,
                                        "plane_sweeps": evals[gpm.COUNT_SWEEP_PLANE] / args.steps,
                                        "init_and_recost": evals[gpm.COUNT_INIT] / args.steps},
+            "taps_per_step_by_kind": {"level0_sweep": evals[gpm.COUNT_SWEEP0_TAPS] / args.steps,
+                                      "plane_sweeps": evals[gpm.COUNT_SWEEP_PLANE_TAPS] / args.steps},
             "ransac_tests_per_step": evals[gpm.COUNT_RANSAC] / args.steps,
             "ransac_certification": {
                 "tests_decided_in_fp64_per_step": evals[gpm.COUNT_RANSAC_FP64] / args.steps,

@@ -755,6 +755,87 @@ struct DistSum {
     __device__ __forceinline__ double total() const { return s; }
 };
 
+// Refit inputs on the winner's inliers, for ransac_fit (out of line: once per window, and its 24 integer
+// moments would otherwise crowd the registers of the hypothesis loop).
+template <class G>
+__device__ __noinline__ void winner_moments(const G& grp, const float4* match, int N, const Mef* wmef,
+                                            const double* whl, float t2, int wscore, RefitWork* rw) {
+    const int tid = grp.rank();
+    // Hartley centroids (exact integer sums), mean distances, and the DLT moments as exact integers about the
+    // rounded centroids
+    const Mef wm = *wmef;
+    // the winner's inlier test, certified: an uncertain one is decided in FP64 with the exact winner
+    auto winner_inlier = [&](const float4& mt) -> bool {
+        bool unc;
+        const bool in = cert_inlier(wm, mt, t2, unc);
+        return unc ? hyp_inlier_fp64(whl, mt.x, mt.y, mt.z, mt.w, (double)t2) : in;
+    };
+    // the winner's inliers among this thread's matches (bit c: match tid + c G::size; N <= 64 G::size for
+    // every group: 256 matches per warp window, 96 x 96 per block window)
+    static_assert(kMaxCell * kMaxCell <= 64 * 256 && 16 * 16 <= 64 * 32, "inlier mask too small");
+    unsigned long long inm = 0;
+    int sx = 0, sy = 0, tx = 0, ty = 0;
+    for (int j = tid, c = 0; j < N; j += G::size, ++c) {
+        const float4 mt = match[j];
+        if (winner_inlier(mt)) {
+            inm |= 1ull << c;
+            sx += exact_int(mt.x);
+            sy += exact_int(mt.y);
+            tx += exact_int(mt.x + mt.z);
+            ty += exact_int(mt.y + mt.w);
+        }
+    }
+    sx = grp.sum(sx);
+    sy = grp.sum(sy);
+    tx = grp.sum(tx);
+    ty = grp.sum(ty);
+    const float fn = (float)wscore;
+    const float fmx = __fdiv_rn((float)sx, fn), fmy = __fdiv_rn((float)sy, fn);
+    const float fmqx = __fdiv_rn((float)tx, fn), fmqy = __fdiv_rn((float)ty, fn);
+    const int cx = __float2int_rn(fmx), cy = __float2int_rn(fmy), cu = __float2int_rn(fmqx), cv = __float2int_rn(fmqy);
+    // Hartley scales: distances to the exact centroids, as n |p - mean| = |n p - sum| from exact integers
+    // (the least-squares refit of a noisy support moves with its normalisation, so the scale must carry no
+    // more than float rounding)
+    const int nw = wscore;  // n |coordinate| < 2^31 for frames up to 32767 px and windows up to 96 px
+    DistSum dsum, dtsum;
+    long long R[24];
+#pragma unroll
+    for (int q = 0; q < 24; ++q) R[q] = 0;
+    for (; inm; inm &= inm - 1) {
+        const float4 mt = match[tid + (__ffsll((long long)inm) - 1) * G::size];
+        dsum.add(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
+        dtsum.add(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
+        const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
+        const int U = exact_int(mt.x + mt.z) - cu, V = exact_int(mt.y + mt.w) - cv;
+        const int zz[6] = {X * X, X * Y, X, Y * Y, Y, 1};
+        const int w3 = U * U + V * V;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            R[q] += zz[q];
+            R[6 + q] += (long long)U * zz[q];
+            R[12 + q] += (long long)V * zz[q];
+            R[18 + q] += (long long)w3 * zz[q];
+        }
+    }
+    const double ds = grp.sum(dsum.total()) / (double)nw;  // sums of |p - mean|
+    const double dt = grp.sum(dtsum.total()) / (double)nw;
+#pragma unroll
+    for (int q = 0; q < 24; ++q) {
+        const long long t = grp.sum(R[q]);
+        if (tid == q) rw->mom[q] = t;
+    }
+    if (tid == 0) {
+        rw->ds = ds;
+        rw->dt = dt;
+        rw->cx = cx;
+        rw->cy = cy;
+        rw->cu = cu;
+        rw->cv = cv;
+        rw->nin = wscore;
+        rw->status = 2;
+    }
+}
+
 template <class G, int ST, bool LANE>
 __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g, int level, int stage,
                            const PlaneParams& pp, int dir, int cell, float4* match, Mef* hyp, int* gbest, int* kfull,
@@ -1058,80 +1139,7 @@ __device__ void ransac_fit(const G& grp, const PairView& pv, const LevelGeom& g,
     grp.sync();
     if (wscore < 4) return;
 
-    // refit inputs on the winner's inliers: Hartley centroids (exact integer
-    // sums), mean distances, and the DLT moments as exact integers about the
-    // rounded centroids
-    const Mef wm = *wmef;
-    // the winner's inlier test, certified: an uncertain one is decided in FP64 with the exact winner
-    auto winner_inlier = [&](const float4& mt) -> bool {
-        bool unc;
-        const bool in = cert_inlier(wm, mt, t2, unc);
-        return unc ? hyp_inlier_fp64(whl, mt.x, mt.y, mt.z, mt.w, (double)t2) : in;
-    };
-    // the winner's inliers among this thread's matches (bit c: match tid + c G::size; N <= 64 G::size for
-    // every group: 256 matches per warp window, 96 x 96 per block window)
-    static_assert(kMaxCell * kMaxCell <= 64 * 256 && 16 * 16 <= 64 * 32, "inlier mask too small");
-    unsigned long long inm = 0;
-    int sx = 0, sy = 0, tx = 0, ty = 0;
-    for (int j = tid, c = 0; j < N; j += G::size, ++c) {
-        const float4 mt = match[j];
-        if (winner_inlier(mt)) {
-            inm |= 1ull << c;
-            sx += exact_int(mt.x);
-            sy += exact_int(mt.y);
-            tx += exact_int(mt.x + mt.z);
-            ty += exact_int(mt.y + mt.w);
-        }
-    }
-    sx = grp.sum(sx);
-    sy = grp.sum(sy);
-    tx = grp.sum(tx);
-    ty = grp.sum(ty);
-    const float fn = (float)wscore;
-    const float fmx = __fdiv_rn((float)sx, fn), fmy = __fdiv_rn((float)sy, fn);
-    const float fmqx = __fdiv_rn((float)tx, fn), fmqy = __fdiv_rn((float)ty, fn);
-    const int cx = __float2int_rn(fmx), cy = __float2int_rn(fmy), cu = __float2int_rn(fmqx), cv = __float2int_rn(fmqy);
-    // Hartley scales: distances to the exact centroids, as n |p - mean| = |n p - sum| from exact integers
-    // (the least-squares refit of a noisy support moves with its normalisation, so the scale must carry no
-    // more than float rounding)
-    const int nw = wscore;  // n |coordinate| < 2^31 for frames up to 32767 px and windows up to 96 px
-    DistSum dsum, dtsum;
-    long long R[24];
-#pragma unroll
-    for (int q = 0; q < 24; ++q) R[q] = 0;
-    for (; inm; inm &= inm - 1) {
-        const float4 mt = match[tid + (__ffsll((long long)inm) - 1) * G::size];
-        dsum.add(nw * exact_int(mt.x) - sx, nw * exact_int(mt.y) - sy);
-        dtsum.add(nw * exact_int(mt.x + mt.z) - tx, nw * exact_int(mt.y + mt.w) - ty);
-        const int X = exact_int(mt.x) - cx, Y = exact_int(mt.y) - cy;
-        const int U = exact_int(mt.x + mt.z) - cu, V = exact_int(mt.y + mt.w) - cv;
-        const int zz[6] = {X * X, X * Y, X, Y * Y, Y, 1};
-        const int w3 = U * U + V * V;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            R[q] += zz[q];
-            R[6 + q] += (long long)U * zz[q];
-            R[12 + q] += (long long)V * zz[q];
-            R[18 + q] += (long long)w3 * zz[q];
-        }
-    }
-    const double ds = grp.sum(dsum.total()) / (double)nw;  // sums of |p - mean|
-    const double dt = grp.sum(dtsum.total()) / (double)nw;
-#pragma unroll
-    for (int q = 0; q < 24; ++q) {
-        const long long t = grp.sum(R[q]);
-        if (tid == q) rw->mom[q] = t;
-    }
-    if (tid == 0) {
-        rw->ds = ds;
-        rw->dt = dt;
-        rw->cx = cx;
-        rw->cy = cy;
-        rw->cu = cu;
-        rw->cv = cv;
-        rw->nin = wscore;
-        rw->status = 2;
-    }
+    winner_moments<G>(grp, match, N, wmef, whl, t2, wscore, rw);
 }
 
 // (B) Normalised DLT refit of each window whose fit is pending, one thread
