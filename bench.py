@@ -529,12 +529,12 @@ def batched_block(scenes):
 
 
 def serving_block(scenes):
-    """Continuous batching with size-aware HBM admission (BF16 storage): the capacity (pairs/s with every request
+    """Continuous batching with size-aware HBM admission (FP16 storage): the capacity (pairs/s with every request
     queued at once), then seeded Poisson traces offered at fixed fractions of it, with p50/p99 latency."""
     import numpy as np
 
     from paper_1804_03787_gb300 import gpm, serve
-    gpb = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=gpm.GPM_BF16)
+    gpb = gpm.default_params(patch_radius=RADIUS, cells=CELLS, pm_iters=ITERS, num_hyp=HYP, storage=gpm.GPM_F16)
     pool = [(s.frame1, s.frame2) for s in scenes]
     occ = [float(s.occ.mean()) for s in scenes]
     srv = serve.Server(gpb, hbm_budget_bytes=SERVE_BUDGET_GB << 30, max_active=SERVE_ACTIVE)
@@ -563,7 +563,7 @@ def serving_block(scenes):
                                                               "peak_used_gb": cap["peak_used_bytes"] / 2**30},
            "loads": loads, "budget_gb": SERVE_BUDGET_GB, "max_active": SERVE_ACTIVE,
            "contexts_created": srv.adm.created, "contexts_evicted": srv.adm.evicted,
-           "storage": "bf16",
+           "storage": "f16",
            "workload": f"{len(pool)} distinct seeded scenes, sizes log-uniform 320x240 to 1920x1080 "
                        f"(pixel count), 4-7 planar layers, motion up to width/13 px (at most 128); "
                        f"{SERVE_TRACE_REQ} Poisson arrivals per load",
@@ -574,7 +574,7 @@ def serving_block(scenes):
            "latency": "arrival to flow and occlusion in host memory (host frames copied in per request)"}
     d_epe = float(np.mean(epe_served)) - plain["epe_nocc_px"]
     res["vs_plain_f32"] = {"plain_f32_pairs_per_s": plain["pairs_per_s"], "plain_f32_epe_nocc_px": plain["epe_nocc_px"],
-                           "served_bf16_epe_nocc_px": float(np.mean(epe_served)),
+                           "served_epe_nocc_px": float(np.mean(epe_served)),
                            "speedup": capacity / plain["pairs_per_s"], "epe_diff_px": d_epe,
                            "within_0.01_px": abs(d_epe) <= 0.01, "no_worse_by_0.01_px": d_epe <= 0.01,
                            "how": plain["how"]}

@@ -435,8 +435,8 @@ def test_reduced_precision_storage(torch, kind, storage):
 @pytest.mark.parametrize("kind,storage", [("f16", gpm.GPM_F16), ("bf16", gpm.GPM_BF16)])
 def test_reduced_precision_end_to_end(torch, kind, storage):
     """Tiny config, frames stored as FP16/BF16: the whole method against the oracle on the dequantised frames
-    (the same bars as the FP32 end-to-end test), and the accuracy change against the FP64 oracle on the original
-    frames reported and bounded."""
+    (FP16: the bars of the FP32 end-to-end test; BF16: see below), and the accuracy change against the FP64 oracle
+    on the original frames reported and loosely bounded."""
     s = scene.tiny_scene(0)
     gp = gpm.default_params(storage=storage)
     ctx = _ctx(torch, gp, 128, 96)
@@ -459,8 +459,12 @@ def test_reduced_precision_end_to_end(torch, kind, storage):
     epe_o = np.hypot(*(R.flow[0].reshape(96, 128, 2) - s.flow).transpose(2, 0, 1))[vis].mean()
     print(f"{kind}: flow agreement with the oracle on dequantised frames {agree:.4f}; EPE nocc gpu {epe_g:.4f}, "
           f"oracle (dequantised) {epe_q:.4f}, oracle (FP64 frames) {epe_o:.4f}")
-    assert agree > 0.95
-    assert abs(epe_g - epe_q) < 0.01
+    # FP16 holds the FP32 end-to-end bars.  BF16's 8-bit mantissas make many candidates' costs exactly equal sums
+    # of equal texels; FP32 and FP64 then round those sums differently and break the ties apart (measured: flow
+    # agreement 0.976, EPE 1.1e-3 apart).
+    assert agree > (0.99 if kind == "f16" else 0.97)
+    assert abs(epe_g - epe_q) <= (1e-3 if kind == "f16" else 2e-3)
+    # the accuracy change against the FP64 oracle on the original frames: reported, and bounded only loosely
     assert abs(epe_g - epe_o) < 0.1
     ctx.close()
 
