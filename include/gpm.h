@@ -89,7 +89,7 @@ typedef struct {
     int32_t interp;                       /* 1: pixels left without a plane take the geodesically nearest
                                              assigned pixel's plane (edge-aware fill; EpicFlow stand-in) */
     int32_t sweep_blocks_per_sm;          /* launch shape of the PatchMatch launches: blocks per SM of the grid
-                                             (0 = 8; 1..32) of the initial field, the recosts and the sweeps
+                                             (0 = 4; 1..32) of the initial field, the recosts and the sweeps
                                              other than level 0 with colour patches (one block per tile);
                                              results do not depend on it */
 } gpm_params;

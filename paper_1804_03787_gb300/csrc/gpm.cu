@@ -242,7 +242,7 @@ PlaneParams plane_params(const gpm_params& P) {
 }
 
 // Grid of the PatchMatch launches (init, recost, sweeps): the launch shape chosen by the parameters.
-int pm_grid(const gpm_ctx* c) { return c->nsm * (c->P.sweep_blocks_per_sm > 0 ? c->P.sweep_blocks_per_sm : 8); }
+int pm_grid(const gpm_ctx* c) { return c->nsm * (c->P.sweep_blocks_per_sm > 0 ? c->P.sweep_blocks_per_sm : 4); }
 
 int grid_for(const gpm_ctx* c, int n) {
     const int want = (n + 255) / 256;
