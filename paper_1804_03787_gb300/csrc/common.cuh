@@ -603,6 +603,19 @@ struct Batch {
         return level > 0 ? geo[z][level - 1] : LevelGeom{};
     }
 };
+// The block's pair view, copied once from the kernel's parameter table into shared memory.  Fields read from the
+// table itself, indexed by blockIdx.z, are constant-bank loads at each use (a kernel's registers cannot hold them
+// all); from shared memory they are plain loads.  Every thread of the block must call it: it ends with a barrier.
+__device__ __forceinline__ const PairView& shared_view(const Batch& bt, PairView& dst) {
+    static_assert(sizeof(PairView) % 4 == 0, "word copy");
+    const int* s = reinterpret_cast<const int*>(&bt.view(blockIdx.z));
+    int* d = reinterpret_cast<int*>(&dst);
+    const int nt = blockDim.x * blockDim.y * blockDim.z;
+    const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (int e = t; e < (int)(sizeof(PairView) / 4); e += nt) d[e] = s[e];
+    __syncthreads();
+    return dst;
+}
 // The caller's flow and occlusion buffers of the pairs of one final-map launch (kernel parameters).
 struct FinalOut {
     float* flow[kBatch];

@@ -777,7 +777,8 @@ __global__ void __launch_bounds__(256, 4) k_pm_sweep(const __grid_constant__ Bat
                                                   uint32_t k1) {
     static_assert(!(PLANES && CENSUS), "the census data term is for square patches");
     static_assert(PLANES || CENSUS, "level 0 with colour patches runs k_pm_sweep0");
-    const PairView& pv = bt.view(blockIdx.z);
+    __shared__ PairView spv;
+    const PairView& pv = shared_view(bt, spv);
     const LevelGeom g = bt.geom(blockIdx.z, level);
     const int dir = blockIdx.y;
     const int lane = threadIdx.x & 31;
