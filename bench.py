@@ -304,13 +304,13 @@ def measure_fp32_peak(nsm: int, gpu_id: str, launches: int = 24):
 # captures summarised in profiles/ (null where the kernel changed since, or no capture matches the class).
 TRAFFIC_PER_LAUNCH = {
     "pm_sweep": (39698432 + 256, "profiles/pm_sweep0_level0_1024x436.md"),
-    "pm_sweep_plane": (17857536 + 1024, "profiles/pm_sweep_plane_level1_1024x436.md"),
+    "pm_sweep_plane": (17859584 + 1024, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Issue-slot utilisation of the kernel (ncu smsp__issue_active, one launch of the same workload): the sweeps are
 # bound by gather latency and issue, which the ALU fraction alone does not show.
 ISSUE_PER_LAUNCH = {
     "pm_sweep": (0.5727, "profiles/pm_sweep0_level0_1024x436.md"),
-    "pm_sweep_plane": (0.5999, "profiles/pm_sweep_plane_level1_1024x436.md"),
+    "pm_sweep_plane": (0.6457, "profiles/pm_sweep_plane_level1_1024x436.md"),
 }
 # Algorithmic bytes of a PatchMatch sweep per pixel visit (FP32 storage): the NNF offset and cost read and
 # written (8 + 8 B) and one RGBX texel of each frame (16 + 16 B).
