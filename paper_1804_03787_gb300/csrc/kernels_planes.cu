@@ -1363,22 +1363,27 @@ __device__ void ransac_finish(const G& grp, const PairView& pv, const LevelGeom&
 // lane (the other scoring path is not compiled in).
 constexpr int ransac_warp_match_stride(bool lane) { return lane ? kLaneScoreMax : 256; }
 constexpr size_t ransac_warp_hx_bytes(bool lane) { return lane ? (32 * 9 + 9) * sizeof(i128) : 32 * 9 * sizeof(double); }
+// Windows (warps) per block of the warp-per-window fit.
+constexpr int kRansacWarps = 4;
 constexpr size_t ransac_warp_smem(bool lane) {
-    return 8 * ransac_warp_match_stride(lane) * sizeof(float4) + 8 * 32 * sizeof(Mef) + 8 * ransac_warp_hx_bytes(lane);
+    return kRansacWarps * (ransac_warp_match_stride(lane) * sizeof(float4) + 32 * sizeof(Mef) +
+                           ransac_warp_hx_bytes(lane));
 }
 template <int ST, bool LANE>
-__global__ void __launch_bounds__(256, 3) k_ransac_warp(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
+__global__ void __launch_bounds__(32 * kRansacWarps, 24 / kRansacWarps)
+    k_ransac_warp(const __grid_constant__ Batch bt, int level, int stage, PlaneParams pp) {
     const PairView& pv = bt.view(blockIdx.z);
     const LevelGeom g = bt.geom(blockIdx.z, level);
     constexpr int MS = ransac_warp_match_stride(LANE);
     extern __shared__ float4 warp_dyn[];
-    __shared__ Mef wmef[8];
+    __shared__ Mef wmef[kRansacWarps];
     const int warp = threadIdx.x >> 5;
-    const int cell = blockIdx.x * 8 + warp;
+    const int cell = blockIdx.x * kRansacWarps + warp;
     if (cell >= g.ncells()) return;
     float4* match = warp_dyn + warp * MS;
-    Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + 8 * MS) + warp * 32;
-    char* hx = reinterpret_cast<char*>(warp_dyn + 8 * MS + 8 * 32 * 4) + (size_t)warp * ransac_warp_hx_bytes(LANE);
+    Mef* hyp = reinterpret_cast<Mef*>(warp_dyn + kRansacWarps * MS) + warp * 32;
+    char* hx = reinterpret_cast<char*>(warp_dyn + kRansacWarps * MS + kRansacWarps * 32 * 4) +
+               (size_t)warp * ransac_warp_hx_bytes(LANE);
     WarpGroup grp;
     ransac_fit<WarpGroup, ST, LANE>(grp, pv, g, level, stage, pp, blockIdx.y, cell, match, hyp, nullptr, nullptr,
                                     &wmef[warp], hx);
@@ -1905,11 +1910,11 @@ static void launch_ransac_st(const Batch& bt, int np, int level, int s, int max_
                                  (int)ransac_warp_smem(true));
             wattr_set = true;
         }
-        const dim3 grid((nc + 7) / 8, 2, np);
+        const dim3 fgrid((nc + kRansacWarps - 1) / kRansacWarps, 2, np), grid((nc + 7) / 8, 2, np);
         if (s * s <= kLaneScoreMax)
-            k_ransac_warp<ST, true><<<grid, 256, ransac_warp_smem(true), st>>>(bt, level, stage, pp);
+            k_ransac_warp<ST, true><<<fgrid, 32 * kRansacWarps, ransac_warp_smem(true), st>>>(bt, level, stage, pp);
         else
-            k_ransac_warp<ST, false><<<grid, 256, ransac_warp_smem(false), st>>>(bt, level, stage, pp);
+            k_ransac_warp<ST, false><<<fgrid, 32 * kRansacWarps, ransac_warp_smem(false), st>>>(bt, level, stage, pp);
         k_refit_solve<<<dim3((2 * nc + 63) / 64, 1, np), 64, 0, st>>>(bt, level, pp);
         k_ransac_finish_warp<ST><<<grid, 256, 0, st>>>(bt, level, stage, pp);
         return;
