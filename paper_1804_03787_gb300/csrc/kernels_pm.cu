@@ -1000,8 +1000,8 @@ __device__ __forceinline__ void eval_group(const LanePatch<R>& lp, const void* t
 }
 
 // The warp (one tap per lane) evaluates the n listed candidates of one pixel in list order, up to kSweep0Group
-// at a time, with the strict-less rule of k_pm_sweep (every cost summed in full, then the updates in list
-// order): best / bc are warp-uniform on entry and on return.
+// at a time, with the strict-less rule (every cost summed in full, then the updates in list order): best / bc
+// are warp-uniform on entry and on return.
 template <int R, int ST>
 __device__ __forceinline__ void eval_listed(const LanePatch<R>& lp, const void* tgtp, int Wp,
                                             const uint32_t (*list)[32], int p, int n, int2& best, float& bc,
@@ -1022,13 +1022,15 @@ __device__ __forceinline__ void eval_listed(const LanePatch<R>& lp, const void* 
     }
 }
 
-// Level-0 sweep with square colour patches: the same candidates, order, costs and strict-less rule as
-// k_pm_sweep (Sec. 3.1.1: propagation from the four neighbours, then random search around the best offset
-// after it), so the NNF and its costs are bitwise those of k_pm_sweep.  The per-pixel scalar work runs with
-// one pixel per lane: the neighbours' offsets, the Philox words and the search candidates, the patch-sum bound
-// and the removal of repeats, into a list per pixel in shared memory.  The patch costs run with one tap per
-// lane, the warp walking its 32 pixels' lists in turn.  Lists: (A) propagation, evaluated from the incumbent;
-// (B) random search around the best offset after A, built once A is evaluated for all 32 pixels.
+// Level-0 sweep with square colour patches (Sec. 3.1), one colour of the red-black schedule per launch.  Each
+// pixel's candidates come in two lists: (A) propagation, the offsets of its left, right, upper and lower
+// neighbours; (B) random search around the best offset after A, radius R0 >> k for k = 0, 1, ... (Philox words,
+// two radii per call).  A candidate replaces the best only if its raw tap sum is strictly lower, in list order;
+// candidates that repeat the best or an earlier entry, or that the patch-sum bound rules out, cannot win and are
+// not listed.  The per-pixel scalar work runs with one pixel per lane: the neighbours' offsets, the Philox words
+// and the search candidates, the bound and the removal of repeats, into a list per pixel in shared memory.  The
+// patch costs run with one tap per lane, the warp walking its 32 pixels' lists in turn; list B is built once
+// list A is evaluated for all 32 pixels.
 template <int R, int ST>
 __global__ void __launch_bounds__(128, 6) k_pm_sweep0(const __grid_constant__ Batch bt, int it, int phase,
                                                       uint32_t k0, uint32_t k1) {
