@@ -2031,6 +2031,7 @@ __global__ void k_reset_models(const __grid_constant__ Batch bt) {
     }
 }
 void launch_reset_models(const Batch& bt, int np, int max_models, cudaStream_t st) {
+    if (max_models <= 0) return;  // no plane levels: no model table (an empty grid is not a launch)
     k_reset_models<<<dim3((max_models + 255) / 256, 2, np), 256, 0, st>>>(bt);
 }
 
@@ -2079,6 +2080,7 @@ void launch_frames_export(const Batch& bt, int n, int storage, float* dst, cudaS
 }
 
 void launch_import_models(const Batch& bt, int nlev, int m, cudaStream_t st) {
+    if (m <= 0) return;  // no model table
     k_import_models<<<dim3((m + 255) / 256, 2), 256, 0, st>>>(bt, nlev, m);
 }
 

@@ -105,6 +105,27 @@ def test_level0_patchmatch_matches_oracle_up_to_near_ties(torch, W, H, r, cells)
     ctx.close()
 
 
+@pytest.mark.parametrize("W,H,r", [(4, 4, 4), (5, 7, 1), (9, 4, 4), (37, 5, 2), (33, 9, 3)])
+def test_level0_patchmatch_tiny_ragged_frames(torch, W, H, r):
+    """Level 0 alone (no plane levels) on frames smaller than one sweep tile (32 x 8 pixels) in either axis or
+    both, some smaller than the patch: the tile's partial rows and columns, clamped taps, no patch-sum bound
+    (no pixel's patch fits in the frame) or only a few interior pixels.  Same bars as the larger cases."""
+    s = _scene(W, H, seed=W * 7 + H)
+    gp = gpm.default_params(patch_radius=r, cells=(), pm_iters=4, num_hyp=64)
+    ctx = _ctx(torch, gp, W, H)
+    ctx.match([_dev(torch, s)])
+    nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
+    P = oracle_params(gp, W, H)
+    frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    for d in range(2):
+        vx, vy, c, cone = _oracle_pm(P, frames, d)
+        diff = ((nnf[d, :, 0] != vx) | (nnf[d, :, 1] != vy)).reshape(H, W)
+        assert not (diff & ~cone).any(), f"dir {d}: {int((diff & ~cone).sum())} unexplained NNF differences"
+        same = ~diff.reshape(-1)
+        assert rel_close(cost[d][same], c[same]).all()
+    ctx.close()
+
+
 # ---------------------------------------------------------------- one level of Algorithm 1, lock-step
 def _oracle_level(P, frames, l, vx, vy, mh, mi, acc, cue):
     """One level of the oracle, stage by stage, with the per-pixel near-tie logs."""
