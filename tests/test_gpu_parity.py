@@ -117,12 +117,22 @@ def test_level0_patchmatch_tiny_ragged_frames(torch, W, H, r):
     nnf, cost = ctx.export(gpm.NNF), ctx.export(gpm.COST)
     P = oracle_params(gp, W, H)
     frames, _ = oracle_frames(P, s.frame1, s.frame2)
+    diffs = []
     for d in range(2):
         vx, vy, c, cone = _oracle_pm(P, frames, d)
         diff = ((nnf[d, :, 0] != vx) | (nnf[d, :, 1] != vy)).reshape(H, W)
         assert not (diff & ~cone).any(), f"dir {d}: {int((diff & ~cone).sum())} unexplained NNF differences"
         same = ~diff.reshape(-1)
         assert rel_close(cost[d][same], c[same]).all()
+        diffs.append(diff)
+    # the final map without plane levels (Sec. 3.4.1): no pixel has a plane, so the flow is the NNF offset and
+    # every pixel is occluded
+    flows, occs = ctx.flow_and_occlusion()
+    torch.cuda.synchronize()
+    R = O.run(P, s.frame1, s.frame2)
+    gf, of = flows[0].cpu().numpy(), R.flow[0].reshape(H, W, 2)
+    np.testing.assert_array_equal(gf[~diffs[0]], of[~diffs[0]])
+    np.testing.assert_array_equal(occs[0].cpu().numpy().reshape(-1), np.asarray(R.occ[0]).reshape(-1))
     ctx.close()
 
 
