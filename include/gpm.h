@@ -102,15 +102,17 @@ typedef struct {
     size_t hbm_budget_bytes;              /* 0 = no limit; else gpm_create fails with GPM_EBUSY above it */
 } gpm_limits;
 
-/* One frame pair.  Frames are caller-owned DEVICE buffers, H x W x 3 (HWC),
-   FP32 values in [0,1], row stride in elements (>= 3 * width). */
+/* One frame pair.  Frames are caller-owned DEVICE buffers, H x W x 3 (HWC), values in [0,1] stored as
+   `dtype` (a gpm_dtype: GPM_F32, GPM_F16 or GPM_BF16; both frames alike), row stride in elements
+   (>= 3 * width).  FP16/BF16 elements are converted to FP32 exactly on ingest, so a pair gives the same
+   results as the FP32 frames holding the same values.  Any other dtype: GPM_EINVAL. */
 typedef struct {
     int32_t width, height;
     int64_t row_stride;
-    const float* frame1;
-    const float* frame2;
+    const void* frame1;
+    const void* frame2;
     uint32_t pair_id;                     /* Philox counter word: results depend on it */
-    uint32_t reserved;
+    int32_t dtype;                        /* gpm_dtype of the frames (0 = GPM_F32) */
 } gpm_pair;
 
 /* Optional allocator (e.g. PyTorch's caching allocator).  alloc returns a

@@ -539,6 +539,8 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
         for (int i = 0; i < n_pairs; ++i) {
             const gpm_pair& p = pairs[i];
             if (!p.frame1 || !p.frame2) return fail(c, GPM_EINVAL, "NULL frame");
+            if (p.dtype != GPM_F32 && p.dtype != GPM_F16 && p.dtype != GPM_BF16)
+                return fail(c, GPM_EINVAL, "frame dtype must be GPM_F32, GPM_F16 or GPM_BF16");
             if (p.width < std::max(4, smax) || p.height < std::max(4, smax) || p.width > c->lim.max_width ||
                 p.height > c->lim.max_height)
                 return fail(c, GPM_EINVAL, "frame size outside [largest cell, limits]");
@@ -565,6 +567,7 @@ gpm_status gpm_match(gpm_ctx* c, const gpm_pair* pairs, int32_t n_pairs, int32_t
                 IngestJob& j = J.j[k];
                 j.f1 = p.frame1;
                 j.f2 = p.frame2;
+                j.dtype = p.dtype;
                 j.W = p.width;
                 j.H = p.height;
                 j.stride = p.row_stride;

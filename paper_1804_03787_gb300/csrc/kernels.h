@@ -27,8 +27,9 @@ int sweep0_tiles(int W, int H);
 constexpr int kIngestPartialBlocks = 128;
 // One pair's ingest: its frames as given and the buffers the ingest fills.
 struct IngestJob {
-    const float* f1;
-    const float* f2;
+    const void* f1;  // frames as given, elements of type `dtype` (gpm_dtype)
+    const void* f2;
+    int dtype;
     int W, H;
     int64_t stride;
     double* partial;  // 2 * kIngestPartialBlocks doubles

@@ -27,6 +27,13 @@ constexpr unsigned FULL = 0xffffffffu;
 // proportional to V, so the equalised pixel is RGB * V' / V (V' grey for
 // black pixels).  A frame with a single occupied bin is left unchanged
 // (its table holds -1).
+// Element k of an input frame as a float: FP32, FP16 or BF16 (gpm_dtype), each converted exactly.
+__device__ __forceinline__ float in_elem(const void* f, int dtype, int64_t k) {
+    if (dtype == GPM_F16) return __half2float(reinterpret_cast<const __half*>(f)[k]);
+    if (dtype == GPM_BF16) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(f)[k]);
+    return reinterpret_cast<const float*>(f)[k];
+}
+
 __device__ __forceinline__ int v_bin(float v) {
     float x = floorf(v * 256.f);
     if (!(x >= 0.f)) x = 0.f;
@@ -50,12 +57,13 @@ __global__ void k_vhist(const __grid_constant__ IngestJobs J) {
     __shared__ int h[256];
     for (int k = threadIdx.x; k < 256; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    const float* f = blockIdx.y ? j.f2 : j.f1;
+    const void* f = blockIdx.y ? j.f2 : j.f1;
     const int n = W * H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
-        const float* p = f + (int64_t)y * stride + 3 * x;
-        atomicAdd(&h[v_bin(fmaxf(p[0], fmaxf(p[1], p[2])))], 1);
+        const int64_t e = (int64_t)y * stride + 3 * x;
+        const float r = in_elem(f, j.dtype, e), g = in_elem(f, j.dtype, e + 1), b = in_elem(f, j.dtype, e + 2);
+        atomicAdd(&h[v_bin(fmaxf(r, fmaxf(g, b)))], 1);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < 256; k += blockDim.x)
@@ -115,12 +123,13 @@ __global__ void k_grey_keys(const __grid_constant__ IngestJobs J) {
     if (!j.k1) return;  // block-uniform
     const int W = j.W, n = j.W * j.H;
     const int64_t stride = j.stride;
-    const float* f = blockIdx.y ? j.f2 : j.f1;
+    const void* f = blockIdx.y ? j.f2 : j.f1;
     long long* k = blockIdx.y ? j.k2 : j.k1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
-        const float* p = f + (int64_t)y * stride + 3 * x;
-        const double g = (((double)p[0] + (double)p[1]) + (double)p[2]) + 0.0;
+        const int64_t e = (int64_t)y * stride + 3 * x;
+        const double g = (((double)in_elem(f, j.dtype, e) + (double)in_elem(f, j.dtype, e + 1)) +
+                          (double)in_elem(f, j.dtype, e + 2)) + 0.0;
         const long long b = __double_as_longlong(g);
         k[i] = b >= 0 ? b : (long long)(0x8000000000000000ull - (unsigned long long)b) - 1;
     }
@@ -156,8 +165,9 @@ __global__ void k_census(const __grid_constant__ IngestJobs J) {
 // (blockIdx.z = job).
 __global__ void k_frame_sums(const __grid_constant__ IngestJobs J) {
     const IngestJob& j = J.j[blockIdx.z];
-    const float* f1 = j.f1;
-    const float* f2 = j.f2;
+    const void* f1 = j.f1;
+    const void* f2 = j.f2;
+    const int dt = j.dtype;
     const int W = j.W, H = j.H;
     const int64_t stride = j.stride;
     const float* lut = j.hist ? j.lut : nullptr;
@@ -165,19 +175,20 @@ __global__ void k_frame_sums(const __grid_constant__ IngestJobs J) {
     __shared__ double sh[2][256];
     double a = 0, b = 0;
     for (int y = blockIdx.x; y < H; y += gridDim.x) {
-        const float* r1 = f1 + (int64_t)y * stride;
-        const float* r2 = f2 + (int64_t)y * stride;
+        const int64_t r = (int64_t)y * stride;
         if (lut) {
             for (int x = threadIdx.x; x < W; x += blockDim.x) {
-                const float3 p = equalize_px(r1[3 * x], r1[3 * x + 1], r1[3 * x + 2], lut);
-                const float3 q = equalize_px(r2[3 * x], r2[3 * x + 1], r2[3 * x + 2], lut + 256);
+                const int64_t e = r + 3 * x;
+                const float3 p = equalize_px(in_elem(f1, dt, e), in_elem(f1, dt, e + 1), in_elem(f1, dt, e + 2), lut);
+                const float3 q =
+                    equalize_px(in_elem(f2, dt, e), in_elem(f2, dt, e + 1), in_elem(f2, dt, e + 2), lut + 256);
                 a += (double)p.x + (double)p.y + (double)p.z;
                 b += (double)q.x + (double)q.y + (double)q.z;
             }
         } else {
             for (int k = threadIdx.x; k < 3 * W; k += blockDim.x) {
-                a += (double)r1[k];
-                b += (double)r2[k];
+                a += (double)in_elem(f1, dt, r + k);
+                b += (double)in_elem(f2, dt, r + k);
             }
         }
     }
@@ -232,8 +243,9 @@ __device__ __forceinline__ void store_pix(void* base, int i, float r, float g, f
 template <int ST>
 __global__ void k_pack(const __grid_constant__ IngestJobs J) {
     const IngestJob& j = J.j[blockIdx.z];
-    const float* f1 = j.f1;
-    const float* f2 = j.f2;
+    const void* f1 = j.f1;
+    const void* f2 = j.f2;
+    const int dt = j.dtype;
     const int W = j.W, H = j.H;
     const int64_t stride = j.stride;
     const float* lut = j.hist ? j.lut : nullptr;
@@ -243,9 +255,9 @@ __global__ void k_pack(const __grid_constant__ IngestJobs J) {
     const int n = W * H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
-        const float* a = f1 + (int64_t)y * stride + 3 * x;
-        const float* b = f2 + (int64_t)y * stride + 3 * x;
-        float3 p = make_float3(a[0], a[1], a[2]), q = make_float3(b[0], b[1], b[2]);
+        const int64_t e = (int64_t)y * stride + 3 * x;
+        float3 p = make_float3(in_elem(f1, dt, e), in_elem(f1, dt, e + 1), in_elem(f1, dt, e + 2));
+        float3 q = make_float3(in_elem(f2, dt, e), in_elem(f2, dt, e + 1), in_elem(f2, dt, e + 2));
         if (lut) {
             p = equalize_px(p.x, p.y, p.z, lut);
             q = equalize_px(q.x, q.y, q.z, lut + 256);
@@ -1258,8 +1270,9 @@ __global__ void k_grey_q(const __grid_constant__ IngestJobs J) {
     const int W = j.W, n = j.W * j.H;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int y = i / W, x = i - y * W;
-        const float* p = j.f1 + (int64_t)y * j.stride + 3 * x;
-        j.gq[i] = (int)floor(1024.0 * (((double)p[0] + (double)p[1]) + (double)p[2]));
+        const int64_t e = (int64_t)y * j.stride + 3 * x;
+        j.gq[i] = (int)floor(1024.0 * (((double)in_elem(j.f1, j.dtype, e) + (double)in_elem(j.f1, j.dtype, e + 1)) +
+                                       (double)in_elem(j.f1, j.dtype, e + 2)));
     }
 }
 
@@ -1300,7 +1313,7 @@ void launch_ingest(const float* f1, const float* f2, int W, int H, int64_t strid
                    cudaStream_t st) {
     (void)nblk;  // always kIngestPartialBlocks
     IngestJobs J{};
-    J.j[0] = IngestJob{f1, f2, W, H, stride, partial, gain, o1, o2, eq_lut ? eq_hist : nullptr, eq_lut,
+    J.j[0] = IngestJob{f1, f2, GPM_F32, W, H, stride, partial, gain, o1, o2, eq_lut ? eq_hist : nullptr, eq_lut,
                        nullptr, nullptr, nullptr, nullptr, nullptr};
     launch_ingest_jobs(J, 1, W * H, H, gain_enable, storage, st);
 }

@@ -56,7 +56,7 @@ class Limits(C.Structure):
 
 class Pair(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("row_stride", C.c_int64),
-                ("frame1", C.c_void_p), ("frame2", C.c_void_p), ("pair_id", C.c_uint32), ("reserved", C.c_uint32)]
+                ("frame1", C.c_void_p), ("frame2", C.c_void_p), ("pair_id", C.c_uint32), ("dtype", C.c_int32)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
@@ -183,18 +183,23 @@ class Context:
             raise GpmError(st, f"{what}: {self.lib.gpm_status_string(st).decode()}: {msg}")
 
     def match(self, frames, level: int = 0, pair_ids=None):
-        """frames: list of (frame1, frame2) CUDA float32 HxWx3 tensors (level 0 only)."""
+        """frames: list of (frame1, frame2) CUDA HxWx3 tensors, float32, float16 or bfloat16 (both frames of a pair
+        alike; level 0 only)."""
         if level == 0:
+            torch = self._torch
+            kinds = {torch.float32: GPM_F32, torch.float16: GPM_F16, torch.bfloat16: GPM_BF16}
             n = len(frames)
             arr = (Pair * n)()
             self._keep = []
             for i, (f1, f2) in enumerate(frames):
                 f1 = f1.contiguous()
                 f2 = f2.contiguous()
+                if f1.dtype != f2.dtype or f1.dtype not in kinds:
+                    raise ValueError("frames must both be float32, float16 or bfloat16")
                 self._keep += [f1, f2]
                 H, W, _ = f1.shape
                 arr[i] = Pair(W, H, 3 * W, f1.data_ptr(), f2.data_ptr(),
-                              (pair_ids[i] if pair_ids is not None else i) & 0xFFFFFFFF, 0)
+                              (pair_ids[i] if pair_ids is not None else i) & 0xFFFFFFFF, kinds[f1.dtype])
                 self._pairs = [(W, H) for (W, H) in [(f.shape[1], f.shape[0]) for f, _ in frames]]
             self._check(self.lib.gpm_match(self.h, arr, n, 0), "gpm_match")
             self._n = n

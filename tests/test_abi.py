@@ -43,6 +43,7 @@ def test_struct_layouts_match_header(lib):
     assert gpm.Params.sweep_blocks_per_sm.offset == 124
     assert ctypes.sizeof(gpm.Limits) == 24
     assert ctypes.sizeof(gpm.Pair) == 40
+    assert gpm.Pair.pair_id.offset == 32 and gpm.Pair.dtype.offset == 36  # per-pair frame dtype (gpm_dtype)
 
 
 def test_host_only_calls_without_gpu(lib):

@@ -5,6 +5,8 @@ must equal the oracle's bit for bit (PatchMatch keeps the random initial field o
 plane, every pixel is occluded).  Identical frames are the zero-motion case.  A frame of exactly the largest
 window's size has one window per axis at that level; a ragged size just above it gets a border-flush window.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -119,6 +121,11 @@ def test_invalid_calls_are_refused(torch):
     # an empty batch
     with pytest.raises(gpm.GpmError):
         ctx.match([])
+    # a frame dtype outside gpm_dtype, through the C ABI
+    f1, f2 = _dev(torch, s.frame1, s.frame2)
+    bad = gpm.Pair(64, 48, 3 * 64, f1.data_ptr(), f2.data_ptr(), 0, 7)
+    assert ctx.lib.gpm_match(ctx.h, ctypes.byref(bad), 1, 0) == gpm.GPM_EINVAL
+    assert "dtype" in ctx.lib.gpm_last_error(ctx.h).decode()
     # the context stays usable after refused calls
     flows, occs = ctx.run([_dev(torch, s.frame1, s.frame2)])
     torch.cuda.synchronize()

@@ -500,6 +500,37 @@ def test_reduced_precision_end_to_end(torch, kind, storage):
     ctx.close()
 
 
+def test_frame_dtypes_per_pair(torch):
+    """Frames given as FP16 or BF16 (per pair, through gpm_pair.dtype) are converted exactly on ingest: the whole
+    method gives bitwise the results of the FP32 frames holding the same values, alone and with pairs of other
+    dtypes in the same call."""
+    s = scene.tiny_scene(0)
+    gp = gpm.default_params()
+    H, W = s.frame1.shape[:2]
+    ctx = _ctx(torch, gp, W, H, pairs=3)
+    ins = {}
+    for dt in (torch.float16, torch.bfloat16):
+        a = torch.from_numpy(s.frame1).cuda().to(dt)
+        b = torch.from_numpy(s.frame2).cuda().to(dt)
+        ins[dt] = ((a, b), (a.float(), b.float()))
+    ref = {}
+    for dt, (low, f32) in ins.items():
+        for form, fr in (("low", low), ("f32", f32)):
+            flows, occs = ctx.run([fr], pair_ids=[5])
+            torch.cuda.synchronize()
+            ref[(dt, form)] = (flows[0].cpu().numpy(), occs[0].cpu().numpy(), ctx.export(gpm.NNF)[0].copy())
+        for k in range(3):
+            np.testing.assert_array_equal(ref[(dt, "low")][k], ref[(dt, "f32")][k])
+    # one call: FP32, FP16 and BF16 pairs together, each as alone
+    f32 = (torch.from_numpy(s.frame1).cuda(), torch.from_numpy(s.frame2).cuda())
+    flows, occs = ctx.run([ins[torch.float16][0], f32, ins[torch.bfloat16][0]], pair_ids=[5, 5, 5])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(flows[0].cpu().numpy(), ref[(torch.float16, "f32")][0])
+    np.testing.assert_array_equal(flows[2].cpu().numpy(), ref[(torch.bfloat16, "f32")][0])
+    np.testing.assert_array_equal(occs[2].cpu().numpy(), ref[(torch.bfloat16, "f32")][1])
+    ctx.close()
+
+
 # ---------------------------------------------------------------- HSV histogram equalisation (Sec. 4.2)
 def test_equalized_ingest_matches_oracle(torch):
     """Ingest with equalize=1: both stored frames against the oracle's FP64 equalisation (then gain). The GPU
