@@ -403,6 +403,12 @@ def test_tiny_config_end_to_end(torch):
     # whole frame's EPE agrees within the final-flow bar, 1e-3 px
     assert st["label_agree"] > 0.99 and st["plane_agree"] > 0.99, st
     assert st["agree"] > 0.99 and abs(st["epe_gpu"] - st["epe_oracle"]) <= 1e-3, st
+    # the occlusion map (Sec. 3.4.1): the same bits except where a plane decision differed upstream
+    gocc = occs[0].cpu().numpy().reshape(-1)
+    oocc = np.asarray(R.occ[0]).reshape(-1)
+    occ_agree = float(np.mean(gocc == oocc))
+    print(f"tiny: occlusion bits agree on {occ_agree:.5f}")
+    assert occ_agree > 0.99, occ_agree
     ctx.close()
 
 
